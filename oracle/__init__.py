@@ -1,0 +1,227 @@
+"""FP64 CPU oracle of the damped-Newton Monge-Ampere solver for periodic L2 optimal
+transport (Saumier, Agueh & Khouider, arXiv:1009.6039).
+
+TEST INFRASTRUCTURE ONLY.  The plain C implementation lives in ``ot_oracle.c``; this module
+builds it with gcc (``build()``) and wraps it with ctypes + numpy.  Only ``tests/``, the
+smoke check and the benchmark's CPU-baseline leg may import it.  The CUDA product path
+shares no code with it.
+
+Grid convention: arrays are (N, M) float64, row index i is y = i/N, column index j is
+x = j/M.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ot_oracle.c")
+_LIB = os.path.join(_HERE, "libot_oracle.so")
+_lib = None
+
+ORC_OK, ORC_EINVAL, ORC_ENOCONV, ORC_EDIVERGED = 0, -1, -2, -3
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
+                ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("max_newton", ctypes.c_int), ("translate_inputs", ctypes.c_int),
+                ("safeguard", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("gmres_iters", ctypes.c_int), ("gmres_cycles", ctypes.c_int),
+                ("step_halvings", ctypes.c_int),
+                ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
+                ("min_det", ctypes.c_double), ("mean_fn", ctypes.c_double),
+                ("u_mean", ctypes.c_double)]
+
+
+def build(force=False):
+    """Compile the oracle with gcc (portable flags only: it must build on x86 and Arm)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ot_oracle.h"))):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+        _lib.orc_fft2.argtypes = [vp, vp, i, i, i]
+        _lib.orc_fft1.argtypes = [vp, vp, i, i]
+        _lib.orc_dft2.argtypes = [vp, vp, i, i, i, vp, vp]
+        _lib.orc_derivatives.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
+        _lib.orc_bspline_coeffs.argtypes = [vp, i, i, vp]
+        _lib.orc_bspline_eval.argtypes = [vp, i, i, d, d, vp, vp, vp]
+        _lib.orc_residual.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
+        _lib.orc_simpson_mean.argtypes = [vp, i, i]
+        _lib.orc_simpson_mean.restype = d
+        _lib.orc_rho_bar.argtypes = [vp, ctypes.c_long, i, ctypes.c_long, i, vp, vp]
+        _lib.orc_apply_op.argtypes = [vp, vp, vp, i, i, vp]
+        _lib.orc_apply_lbar_inv.argtypes = [vp, vp, i, i, vp]
+        _lib.orc_gmres_dense.argtypes = [vp, vp, i, i, d, i, vp, vp, vp, vp]
+        _lib.orc_gmres_op.argtypes = [vp, vp, vp, i, i, i, d, i, vp, vp, vp, vp]
+        _lib.orc_solve.argtypes = [vp, vp, i, i, ctypes.POINTER(Opts), vp,
+                                   ctypes.POINTER(Stats), vp, vp]
+        _lib.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def fft2(x, inverse=False):
+    """Unnormalised 2-D DFT (sign -1 forward, +1 inverse) by the oracle's own FFT."""
+    x = np.asarray(x, dtype=np.complex128)
+    re, im = _f64(x.real).copy(), _f64(x.imag).copy()
+    N, M = x.shape
+    lib().orc_fft2(_p(re), _p(im), N, M, 1 if inverse else -1)
+    return re + 1j * im
+
+
+def dft2(x, inverse=False):
+    """Brute-force O(P^2) 2-D DFT."""
+    x = np.asarray(x, dtype=np.complex128)
+    re, im = _f64(x.real), _f64(x.imag)
+    N, M = x.shape
+    ore, oim = np.empty_like(re), np.empty_like(re)
+    lib().orc_dft2(_p(re), _p(im), N, M, 1 if inverse else -1, _p(ore), _p(oim))
+    return ore + 1j * oim
+
+
+def fft1(x, inverse=False):
+    x = np.asarray(x, dtype=np.complex128)
+    re, im = _f64(x.real).copy(), _f64(x.imag).copy()
+    lib().orc_fft1(_p(re), _p(im), x.shape[0], 1 if inverse else -1)
+    return re + 1j * im
+
+
+def derivatives(u):
+    """(u_x, u_y, u_xx, u_yy, u_xy) by the 4th-order centred stencils."""
+    u = _f64(u)
+    N, M = u.shape
+    outs = [np.empty_like(u) for _ in range(5)]
+    lib().orc_derivatives(_p(u), N, M, *[_p(o) for o in outs])
+    return tuple(outs)
+
+
+def bspline_coeffs(g):
+    g = _f64(g)
+    c = np.empty_like(g)
+    if lib().orc_bspline_coeffs(_p(g), g.shape[0], g.shape[1], _p(c)) != 0:
+        raise ValueError("grid too small")
+    return c
+
+
+def bspline_eval(c, x, y):
+    """Interpolant value and gradient at torus points (x along columns, y along rows)."""
+    c = _f64(c)
+    N, M = c.shape
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    v, gx, gy = np.empty_like(x), np.empty_like(x), np.empty_like(x)
+    a, b, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    for k in range(x.size):
+        lib().orc_bspline_eval(_p(c), N, M, float(x.flat[k]), float(y.flat[k]),
+                               ctypes.byref(a), ctypes.byref(b), ctypes.byref(e))
+        v.flat[k], gx.flat[k], gy.flat[k] = a.value, b.value, e.value
+    return v, gx, gy
+
+
+def residual(f, c, u):
+    """Returns (F, coef[5,N,M], scal) with F = f - f~_n, coef = (a11, a12, a22, b1, b2),
+    scal = dict(mean_fn, res_inf, res_l2, min_det, nonfinite)."""
+    f, c, u = _f64(f), _f64(c), _f64(u)
+    N, M = u.shape
+    F = np.empty_like(u)
+    coef = np.empty((5, N, M))
+    s = np.empty(5)
+    lib().orc_residual(_p(f), _p(c), _p(u), N, M, _p(F), _p(coef), _p(s))
+    return F, coef, dict(mean_fn=s[0], res_inf=s[1], res_l2=s[2], min_det=s[3],
+                         nonfinite=int(s[4]))
+
+
+def simpson_mean(a):
+    a = _f64(a)
+    return lib().orc_simpson_mean(_p(a), a.shape[0], a.shape[1])
+
+
+def rho_bar(abar, k1, nyq1, k2, nyq2):
+    ab = _f64(abar)
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().orc_rho_bar(_p(ab), int(k1), int(nyq1), int(k2), int(nyq2), ctypes.byref(re),
+                      ctypes.byref(im))
+    return re.value + 1j * im.value
+
+
+def apply_op(coef, abar, sigma):
+    """w = L Lbar^{-1} sigma."""
+    coef, ab, sigma = _f64(coef), _f64(abar), _f64(sigma)
+    N, M = sigma.shape
+    w = np.empty_like(sigma)
+    lib().orc_apply_op(_p(coef), _p(ab), _p(sigma), N, M, _p(w))
+    return w
+
+
+def apply_lbar_inv(abar, sigma):
+    """theta = Lbar^{-1} sigma."""
+    ab, sigma = _f64(abar), _f64(sigma)
+    N, M = sigma.shape
+    th = np.empty_like(sigma)
+    lib().orc_apply_lbar_inv(_p(ab), _p(sigma), N, M, _p(th))
+    return th
+
+
+def gmres_dense(A, b, m=10, eta=1e-10, max_restarts=50):
+    A, b = _f64(A), _f64(b)
+    n = b.shape[0]
+    x = np.empty(n)
+    it, cy, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().orc_gmres_dense(_p(A), _p(b), n, m, eta, max_restarts, _p(x), ctypes.byref(it),
+                               ctypes.byref(cy), ctypes.byref(rr))
+    return x, dict(status=st, iters=it.value, cycles=cy.value, relres=rr.value)
+
+
+def gmres_op(coef, abar, h, m=10, eta=1e-4, max_restarts=50):
+    coef, ab, h = _f64(coef), _f64(abar), _f64(h)
+    N, M = h.shape
+    s = np.empty_like(h)
+    it, cy, rr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    st = lib().orc_gmres_op(_p(coef), _p(ab), _p(h), N, M, m, eta, max_restarts, _p(s),
+                            ctypes.byref(it), ctypes.byref(cy), ctypes.byref(rr))
+    return s, dict(status=st, iters=it.value, cycles=cy.value, relres=rr.value)
+
+
+def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_newton=200,
+          u0=None, translate_inputs=True, safeguard=True):
+    """Damped Newton solve.  Returns (u, stats dict, res history, gmres history)."""
+    f, g = _f64(f), _f64(g)
+    N, M = f.shape
+    o = Opts()
+    lib().orc_default_opts(ctypes.byref(o))
+    o.tau, o.tol, o.eta, o.restart = tau, tol, eta, restart
+    o.max_restarts, o.max_newton = max_restarts, max_newton
+    o.translate_inputs, o.safeguard = int(translate_inputs), int(safeguard)
+    u = np.zeros((N, M)) if u0 is None else _f64(u0).copy()
+    st = Stats()
+    hres = np.zeros(max_newton + 1)
+    hgm = np.zeros(max_newton + 1, dtype=np.int32)
+    lib().orc_solve(_p(f), _p(g), N, M, ctypes.byref(o), _p(u), ctypes.byref(st), _p(hres),
+                    _p(hgm))
+    d = {k: getattr(st, k) for k, _ in Stats._fields_}
+    n = d["newton_iters"]
+    return u, d, hres[:n + 1].copy(), hgm[:n].copy()
