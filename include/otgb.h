@@ -1,0 +1,150 @@
+/*
+ * otgb.h -- C ABI of libotgb, a GB300 (sm_103a) solver for the periodic L2 optimal
+ * transport problem by the damped-Newton Monge-Ampere method of Saumier, Agueh & Khouider
+ * (arXiv:1009.6039).
+ *
+ * Problem (Sec. 2, Sec. 3.1 Eq. ma2): given 1-periodic densities f, g > 0 on the unit
+ * square, find a 1-periodic potential phi with mean zero such that
+ *     g(x + grad phi) det(I + D^2 phi) = f,
+ * so that T(x) = x + grad phi(x) is the optimal map pushing f onto g.
+ *
+ * Conventions for every entry point:
+ *   - Planes are row-major N x M arrays of double: element (i, j) at [i * M + j], row index
+ *     i is y = i / N, column index j is x = j / M.
+ *   - Unless stated otherwise, pointers are DEVICE pointers (cudaMalloc / torch CUDA
+ *     tensors) on the current device, owned by the caller, and every call is
+ *     stream-ordered on the plan's stream and returns after the results are complete.
+ *   - Every call returns OT_OK (0) or a negative status code; ot_strerror() names it.
+ *     On an error the output buffers may have been partly written.
+ *   - N and M must be even, each of the form 2^a (>= 8) or 3 * 2^a (>= 12), M >= 16, and
+ *     at most 2048 (the supported FFT lengths; M/2 must also be supported).
+ */
+#ifndef OTGB_H
+#define OTGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define OT_OK 0
+#define OT_EINVAL (-1)       /* bad argument: size, tau < 1, tol <= 0, null pointer, or an
+                                input density that is non-finite or not positive after the
+                                mean translation of Eq. (translation) */
+#define OT_ENOCONV (-2)      /* max Newton steps reached; phi holds the last iterate */
+#define OT_EDIVERGED (-3)    /* an iterate lost convexity (det(I + D^2 phi) <= 0) or became
+                                non-finite; phi holds that last iterate */
+#define OT_ECUDA (-4)        /* a CUDA runtime call failed */
+#define OT_ENOMEM (-5)       /* device or pinned-host allocation failed */
+#define OT_EUNSUPPORTED (-6) /* grid size outside the supported FFT lengths */
+
+/* Plan options (ot_plan_set_option keys). */
+#define OT_OPT_RESTART 1        /* GMRES restart length m, 1..15 (default 10, Sec. 5.1) */
+#define OT_OPT_ETA 2            /* GMRES relative tolerance (default 1e-4, Sec. 5.1) */
+#define OT_OPT_MAX_NEWTON 3     /* Newton step cap (default 200) */
+#define OT_OPT_MAX_RESTARTS 4   /* GMRES cycle cap per Newton step (default 50) */
+#define OT_OPT_PRECISION 5      /* 0 = FP64 throughout (default); 1 = mixed: FFTs, the
+                                   preconditioner and Krylov vectors in FP32, residual,
+                                   det/cof, update and convergence test in FP64 */
+#define OT_OPT_SAFEGUARD 6      /* 1 (default): halve a Newton step whose iterate loses
+                                   convexity (a larger effective tau, Sec. 3.2 remarks);
+                                   0: plain Eq. (linma), such an iterate ends the solve */
+#define OT_OPT_TRANSLATE 7      /* 1 (default): apply Eq. (translation) d - mean(d) + 1 to
+                                   f and g on entry; 0: use them as given */
+#define OT_OPT_WARM_START 8     /* 1: phi_inout holds the initial iterate u0 on entry;
+                                   0 (default): u0 = 0, the constant start of Thm 3.2 */
+#define OT_OPT_TAU 9            /* step-size parameter tau >= 1 (Eq. linma) */
+#define OT_OPT_TOL 10           /* Newton stop: max |f - f~_n| < tol */
+
+typedef struct ot_plan ot_plan;
+
+/* Filled by the solve entry points. */
+typedef struct {
+  int32_t status;          /* same value as returned */
+  int32_t newton_iters;    /* accepted Newton updates */
+  int32_t gmres_iters;     /* Arnoldi steps, all Newton steps */
+  int32_t gmres_cycles;    /* GMRES(m) cycles begun, all Newton steps */
+  int32_t step_halvings;   /* safeguard rejections */
+  int32_t reserved;
+  double res_inf;          /* max |f - f~_n| at the returned phi */
+  double res_l2;           /* sqrt(mean (f - f~_n)^2) at the returned phi */
+  double min_det;          /* min det(I + D^2 phi) */
+  double mean_fn;          /* mean of f_n before translation (mass defect = mean_fn - 1) */
+  double phi_mean;         /* mean removed from the final iterate (gauge, Sec. 3.1) */
+  double ms_total;         /* wall time of the call on the plan's stream (ms) */
+} ot_stats;
+
+/* Create a plan for N x M grids (N rows, M columns), damping tau >= 1 (Eq. linma) and
+ * Newton tolerance tol > 0.  Allocates all device workspace (no allocation happens in
+ * the solve calls).  *out receives the plan, or NULL on error. */
+int ot_plan_create(ot_plan** out, int32_t N, int32_t M, double tau, double tol);
+
+/* Set an OT_OPT_* option.  Changing OT_OPT_PRECISION or OT_OPT_RESTART reallocates the
+ * workspace.  Returns OT_EINVAL for an unknown key or an out-of-range value. */
+int ot_plan_set_option(ot_plan* plan, int32_t key, double value);
+
+/* Run the plan on a cudaStream_t (NULL = legacy default stream). */
+int ot_plan_set_stream(ot_plan* plan, void* cuda_stream);
+
+/* Solve (Sec. 3.1 damped Newton with the Fourier implementation of Sec. 4.2).
+ * f, g: device N x M densities (read only).  phi_inout: device N x M, the mean-zero
+ * potential on return (and u0 on entry if OT_OPT_WARM_START is set).  stats may be NULL. */
+int ot_solve(ot_plan* plan, const double* f, const double* g, double* phi_inout,
+             ot_stats* stats);
+
+/* Same as ot_solve with HOST buffers (pageable or pinned): copies f, g (and phi when
+ * warm-starting) to the plan's device buffers, solves, and copies phi back. */
+int ot_solve_host(ot_plan* plan, const double* f, const double* g, double* phi_inout,
+                  ot_stats* stats);
+
+/* Solve `count` independent problems, plans[k] sized for problem k (sizes may differ);
+ * f[k], g[k], phi[k] are device pointers for plans[k]; stats (array of count) may be NULL.
+ * Returns OT_OK if every problem converged, else the first non-OK status. */
+int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* f,
+                     const double* const* g, double* const* phi, ot_stats* stats);
+
+void ot_plan_destroy(ot_plan* plan);
+const char* ot_strerror(int status);
+
+/* ---- Step-level entry points: one stage of a Newton step each, on device buffers ---- */
+
+/* Coefficients c of the periodic cubic B-spline interpolant of g (sum over the 4 x 4 taps
+ * of c times the B-spline weights reproduces g at the nodes), used to sample g at the
+ * displaced points x + grad phi (Sec. 4).  Computed in FP64 by a spectral division. */
+int ot_prefilter(ot_plan* plan, const double* g, double* c);
+
+/* Residual and linearised coefficients at the iterate u (Eq. ma2, linearmaeq,
+ * translation), with c from ot_prefilter and f as given (no translation here):
+ *   F = f - (f_n - mean f_n + 1),  f_n = G(x + grad u) det(I + D^2 u)
+ *   coef (5 planes, N x M each): a11 = G (1+u_yy), a12 = -G u_xy, a22 = G (1+u_xx),
+ *                                b1 = det dG/dx, b2 = det dG/dy
+ * scal (HOST, 10 doubles): mean f_n, max|F|, sqrt(mean F^2), min det, non-finite count,
+ * then the Simpson averages of a11, a12, a22, b1, b2 (Sec. 4.2).  F, coef may be NULL. */
+int ot_eval_residual(ot_plan* plan, const double* f, const double* c, const double* u,
+                     double* F, double* coef, double* scal);
+
+/* w = L Lbar^{-1} sigma (Sec. 4.2): coef as from ot_eval_residual, abar (HOST, 5 doubles)
+ * the averaged coefficients.  Runs in the plan's precision. */
+int ot_apply_operator(ot_plan* plan, const double* coef, const double* abar,
+                      const double* sigma, double* w);
+
+/* theta = Lbar^{-1} sigma = sum_{k != 0} rho-bar(k) sigma-hat(k) e^{2 pi i k.x} (Sec. 4.2). */
+int ot_apply_lbar_inverse(ot_plan* plan, const double* abar, const double* sigma,
+                          double* theta);
+
+/* Unnormalised 2-D real FFT of x (N x M) into the packed half spectrum spec: N x (M/2)
+ * complex values stored as interleaved (re, im) doubles; entry (k2, k1) for 1 <= k1 < M/2
+ * is X(k2, k1) = sum x(i,j) exp(-2 pi i (k1 j / M + k2 i / N)); column k1 = 0 holds
+ * A(k2) + i B(k2) where A, B are the transforms of the real k1 = 0 and k1 = M/2 row
+ * coefficients.  Runs in the plan's precision. */
+int ot_fft_forward(ot_plan* plan, const double* x, double* spec);
+
+/* Inverse of ot_fft_forward without the 1/(N M) factor (spec -> N M x). */
+int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,217 @@
+"""Python binding of libotgb, a GB300 (sm_103a) solver for periodic L2 optimal transport by
+the damped-Newton Monge-Ampere method of Saumier, Agueh & Khouider (arXiv:1009.6039).
+
+The functions named ``ot_*`` are thin ctypes wrappers with the same names and arguments as
+the C ABI in ``include/otgb.h`` (argument marshalling only; every step runs in the CUDA
+kernels of ``libotgb.so``).  ``Plan`` and ``solve`` are conveniences over them that take
+torch CUDA tensors (float64, shape (N, M), row index = y, column index = x).
+
+Importing this module loads the library and raises if it is missing: there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libotgb.so")
+
+OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6
+OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
+OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
+OT_OPT_TAU, OT_OPT_TOL = 9, 10
+
+EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_solve",
+           "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
+           "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
+           "ot_fft_forward", "ot_fft_inverse"]
+
+
+class ot_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
+                ("gmres_iters", ctypes.c_int32), ("gmres_cycles", ctypes.c_int32),
+                ("step_halvings", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
+                ("min_det", ctypes.c_double), ("mean_fn", ctypes.c_double),
+                ("phi_mean", ctypes.c_double), ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class OTError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s: %s (%d)" % (where, ot_strerror(status), status))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libotgb.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_1009_6039_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "ot_plan_create": ([ctypes.POINTER(vp), i32, i32, d, d], ctypes.c_int),
+        "ot_plan_set_option": ([vp, i32, d], ctypes.c_int),
+        "ot_plan_set_stream": ([vp, vp], ctypes.c_int),
+        "ot_solve": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
+        "ot_solve_host": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
+        "ot_solve_batched": ([i32, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_plan_destroy": ([vp], None),
+        "ot_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "ot_prefilter": ([vp, vp, vp], ctypes.c_int),
+        "ot_eval_residual": ([vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_apply_operator": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_apply_lbar_inverse": ([vp, vp, vp, vp], ctypes.c_int),
+        "ot_fft_forward": ([vp, vp, vp], ctypes.c_int),
+        "ot_fft_inverse": ([vp, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+# ---- C ABI, same names ----------------------------------------------------------------
+def ot_plan_create(N, M, tau, tol):
+    h = ctypes.c_void_p()
+    rc = _lib.ot_plan_create(ctypes.byref(h), int(N), int(M), float(tau), float(tol))
+    return rc, h
+
+
+def ot_plan_set_option(plan, key, value):
+    return _lib.ot_plan_set_option(plan, int(key), float(value))
+
+
+def ot_plan_set_stream(plan, stream_ptr):
+    return _lib.ot_plan_set_stream(plan, ctypes.c_void_p(stream_ptr))
+
+
+def ot_solve(plan, f_ptr, g_ptr, phi_ptr, stats=None):
+    return _lib.ot_solve(plan, f_ptr, g_ptr, phi_ptr,
+                         ctypes.byref(stats) if stats is not None else None)
+
+
+def ot_solve_host(plan, f_ptr, g_ptr, phi_ptr, stats=None):
+    return _lib.ot_solve_host(plan, f_ptr, g_ptr, phi_ptr,
+                              ctypes.byref(stats) if stats is not None else None)
+
+
+def ot_solve_batched(count, plans, f_ptrs, g_ptrs, phi_ptrs, stats=None):
+    arr = ctypes.c_void_p * count
+    return _lib.ot_solve_batched(int(count), arr(*[p.value for p in plans]), arr(*f_ptrs),
+                                 arr(*g_ptrs), arr(*phi_ptrs),
+                                 ctypes.cast(stats, ctypes.c_void_p) if stats is not None
+                                 else None)
+
+
+def ot_plan_destroy(plan):
+    _lib.ot_plan_destroy(plan)
+
+
+def ot_strerror(status):
+    return _lib.ot_strerror(int(status)).decode()
+
+
+def ot_prefilter(plan, g_ptr, c_ptr):
+    return _lib.ot_prefilter(plan, g_ptr, c_ptr)
+
+
+def ot_eval_residual(plan, f_ptr, c_ptr, u_ptr, F_ptr, coef_ptr, scal_host_ptr):
+    return _lib.ot_eval_residual(plan, f_ptr, c_ptr, u_ptr, F_ptr, coef_ptr, scal_host_ptr)
+
+
+def ot_apply_operator(plan, coef_ptr, abar_host_ptr, sigma_ptr, w_ptr):
+    return _lib.ot_apply_operator(plan, coef_ptr, abar_host_ptr, sigma_ptr, w_ptr)
+
+
+def ot_apply_lbar_inverse(plan, abar_host_ptr, sigma_ptr, theta_ptr):
+    return _lib.ot_apply_lbar_inverse(plan, abar_host_ptr, sigma_ptr, theta_ptr)
+
+
+def ot_fft_forward(plan, x_ptr, spec_ptr):
+    return _lib.ot_fft_forward(plan, x_ptr, spec_ptr)
+
+
+def ot_fft_inverse(plan, spec_ptr, x_ptr):
+    return _lib.ot_fft_inverse(plan, spec_ptr, x_ptr)
+
+
+# ---- conveniences over torch tensors ---------------------------------------------------
+def _check(rc, where, ok=(OT_OK,)):
+    if rc not in ok:
+        raise OTError(rc, where)
+    return rc
+
+
+def _dev(t, shape=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """An ot_plan for N x M grids; options as keyword arguments
+    (restart, eta, max_newton, max_restarts, precision ('fp64'|'mixed'), safeguard,
+    translate, warm_start)."""
+
+    _keys = {"restart": OT_OPT_RESTART, "eta": OT_OPT_ETA, "max_newton": OT_OPT_MAX_NEWTON,
+             "max_restarts": OT_OPT_MAX_RESTARTS, "precision": OT_OPT_PRECISION,
+             "safeguard": OT_OPT_SAFEGUARD, "translate": OT_OPT_TRANSLATE,
+             "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL}
+
+    def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
+        rc, h = ot_plan_create(N, M, tau, tol)
+        _check(rc, "ot_plan_create")
+        self.h, self.N, self.M = h, N, M
+        self.set(**opts)
+        if stream is not None:
+            _check(ot_plan_set_stream(h, stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                      else int(stream)), "ot_plan_set_stream")
+
+    def set(self, **opts):
+        for k, v in opts.items():
+            if k == "precision" and isinstance(v, str):
+                v = {"fp64": 0, "mixed": 1}[v]
+            _check(ot_plan_set_option(self.h, self._keys[k], float(v)), "set " + k)
+        return self
+
+    def solve(self, f, g, phi, raise_on=(OT_EINVAL, OT_ECUDA, OT_ENOMEM)):
+        st = ot_stats()
+        shp = (self.N, self.M)
+        rc = ot_solve(self.h, _dev(f, shp), _dev(g, shp), _dev(phi, shp), st)
+        if rc in raise_on:
+            raise OTError(rc, "ot_solve")
+        return rc, st.as_dict()
+
+    def close(self):
+        if self.h:
+            ot_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(f, g, tau=2.0, tol=1e-8, **opts):
+    """Solve for the mean-zero potential phi (torch float64 CUDA tensor) with
+    g(x + grad phi) det(I + D^2 phi) = f; returns (phi, stats)."""
+    import torch
+    N, M = f.shape
+    plan = Plan(N, M, tau=tau, tol=tol, **opts)
+    phi = torch.zeros_like(f)
+    rc, st = plan.solve(f, g, phi)
+    plan.close()
+    return phi, st

@@ -1,0 +1,614 @@
+// C ABI of libotgb: plans, the damped-Newton driver (Sec. 3.1, Eq. linma) with Strain's
+// FFT-preconditioned GMRES(m) (Sec. 4.2), and the step-level entry points.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "../../include/otgb.h"
+#include "otgb_internal.cuh"
+
+using namespace otgb;
+
+struct ot_plan {
+  int N = 0, M = 0;
+  double tau = 1.0, tol = 1e-8;
+  int m = 10;
+  double eta = 1e-4;
+  int max_newton = 200, max_restarts = 50;
+  int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
+  cudaStream_t stream = 0;
+  int device = 0;
+  // FP64 planes
+  double *f = nullptr, *g = nullptr, *c = nullptr, *u = nullptr, *ucand = nullptr,
+         *Fraw = nullptr;
+  // planes in the inner precision (FP64 or FP32)
+  void *coef = nullptr, *V = nullptr, *w = nullptr, *sigma = nullptr;
+  void *spec = nullptr, *q0 = nullptr, *q1 = nullptr, *q2 = nullptr;
+  // FP64 spectrum used by the prefilter when the inner precision is FP32
+  void *spec64 = nullptr, *q64 = nullptr;
+  void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
+  SpecTables tb64{}, tb32{};
+  double* partials = nullptr;
+  double* dmean = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* hsc = nullptr;  // pinned host mirror
+  int kblocks = 0;
+  bool ready = false;
+};
+
+static const char* kErr[] = {"ok", "invalid argument", "Newton did not converge",
+                             "iterate lost convexity or became non-finite", "CUDA error",
+                             "out of memory", "unsupported grid size"};
+
+extern "C" const char* ot_strerror(int s) {
+  if (s <= 0 && s >= -6) return kErr[-s];
+  return "unknown status";
+}
+
+#define CK(x)                                 \
+  do {                                        \
+    cudaError_t e_ = (x);                     \
+    if (e_ != cudaSuccess) {                  \
+      if (e_ == cudaErrorMemoryAllocation)    \
+        return OT_ENOMEM;                     \
+      return OT_ECUDA;                        \
+    }                                         \
+  } while (0)
+
+namespace otgb {
+bool fft_length_supported(int L) {
+  if (L < 8 || L > 2048) return false;
+  int r = L;
+  if (r % 3 == 0) {
+    r /= 3;
+    if (L < 12) return false;
+  }
+  return (r & (r - 1)) == 0;
+}
+}  // namespace otgb
+
+static bool size_supported(int N, int M) {
+  return N % 2 == 0 && M % 2 == 0 && M >= 16 && fft_length_supported(N) &&
+         fft_length_supported(M / 2) && (M <= 2048);
+}
+
+static void free_buffers(ot_plan* p) {
+  void* ptrs[] = {p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
+                  p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
+                  p->tw32, p->partials, p->dmean, p->sc};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->hsc) cudaFreeHost(p->hsc);
+  p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
+  p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
+  p->spec64 = p->q64 = p->tw64 = p->tw32 = nullptr;
+  p->partials = p->dmean = nullptr;
+  p->sc = nullptr;
+  p->hsc = nullptr;
+  p->ready = false;
+}
+
+// exp(-2 pi i t / L) with exact reduction of the angle's numerator
+static void roots(int L, int count, std::vector<double>& out) {
+  for (int t = 0; t < count; ++t) {
+    const double a = 2.0 * M_PI * (double)(t % L) / (double)L;
+    out.push_back(std::cos(a));
+    out.push_back(-std::sin(a));
+  }
+}
+
+static int alloc_buffers(ot_plan* p) {
+  free_buffers(p);
+  const size_t P = (size_t)p->N * p->M;
+  const size_t ts = p->precision ? sizeof(float) : sizeof(double);
+  const size_t L = p->M / 2;
+  CK(cudaMalloc(&p->f, P * 8));
+  CK(cudaMalloc(&p->g, P * 8));
+  CK(cudaMalloc(&p->c, P * 8));
+  CK(cudaMalloc(&p->u, P * 8));
+  CK(cudaMalloc(&p->ucand, P * 8));
+  CK(cudaMalloc(&p->Fraw, P * 8));
+  CK(cudaMalloc(&p->coef, 5 * P * ts));
+  CK(cudaMalloc(&p->V, (size_t)(p->m + 1) * P * ts));
+  CK(cudaMalloc(&p->w, P * ts));
+  CK(cudaMalloc(&p->sigma, P * ts));
+  // half spectra: N x M/2 complex = P elements of the inner type
+  CK(cudaMalloc(&p->spec, P * ts));
+  CK(cudaMalloc(&p->q0, P * ts));
+  CK(cudaMalloc(&p->q1, P * ts));
+  CK(cudaMalloc(&p->q2, P * ts));
+  if (p->precision) {
+    CK(cudaMalloc(&p->spec64, P * 8));
+    CK(cudaMalloc(&p->q64, P * 8));
+  } else {
+    p->spec64 = nullptr;
+    p->q64 = nullptr;
+  }
+  // twiddle tables
+  std::vector<double> tw;
+  roots((int)L, (int)L, tw);      // row FFT length M/2
+  roots(p->M, (int)L, tw);        // split W_M^k, k < M/2
+  roots(p->N, p->N, tw);          // column FFT length N
+  const size_t ntw = tw.size() / 2;
+  CK(cudaMalloc(&p->tw64, ntw * 16));
+  CK(cudaMemcpy(p->tw64, tw.data(), ntw * 16, cudaMemcpyHostToDevice));
+  std::vector<float> twf(tw.begin(), tw.end());
+  CK(cudaMalloc(&p->tw32, ntw * 8));
+  CK(cudaMemcpy(p->tw32, twf.data(), ntw * 8, cudaMemcpyHostToDevice));
+  p->tb64.twL = p->tw64;
+  p->tb64.twM = (const double2*)p->tw64 + L;
+  p->tb64.twN = (const double2*)p->tw64 + 2 * L;
+  p->tb32.twL = p->tw32;
+  p->tb32.twM = (const float2*)p->tw32 + L;
+  p->tb32.twN = (const float2*)p->tw32 + 2 * L;
+  int sms = 0;
+  CK(cudaGetDevice(&p->device));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  p->kblocks = (sms > 0 ? sms : 148) * 2;
+  size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
+  size_t nk = (size_t)p->kblocks * OTGB_MAXM;
+  if (nk > np) np = nk;
+  CK(cudaMalloc(&p->partials, np * 8));
+  CK(cudaMalloc(&p->dmean, 8));
+  CK(cudaMalloc(&p->sc, sizeof(DevScalars)));
+  CK(cudaMemset(p->sc, 0, sizeof(DevScalars)));
+  CK(cudaMallocHost(&p->hsc, sizeof(DevScalars)));
+  memset(p->hsc, 0, sizeof(DevScalars));
+  p->ready = true;
+  return OT_OK;
+}
+
+extern "C" int ot_plan_create(ot_plan** out, int32_t N, int32_t M, double tau, double tol) {
+  if (!out) return OT_EINVAL;
+  *out = nullptr;
+  if (!(tau >= 1.0) || !(tol > 0.0)) return OT_EINVAL;
+  if (!size_supported(N, M)) return OT_EUNSUPPORTED;
+  ot_plan* p = new (std::nothrow) ot_plan();
+  if (!p) return OT_ENOMEM;
+  p->N = N;
+  p->M = M;
+  p->tau = tau;
+  p->tol = tol;
+  int rc = alloc_buffers(p);
+  if (rc != OT_OK) {
+    free_buffers(p);
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return OT_OK;
+}
+
+extern "C" void ot_plan_destroy(ot_plan* p) {
+  if (!p) return;
+  free_buffers(p);
+  delete p;
+}
+
+extern "C" int ot_plan_set_stream(ot_plan* p, void* s) {
+  if (!p) return OT_EINVAL;
+  p->stream = (cudaStream_t)s;
+  return OT_OK;
+}
+
+extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
+  if (!p) return OT_EINVAL;
+  switch (key) {
+    case OT_OPT_RESTART: {
+      int m = (int)v;
+      if (m < 1 || m > OTGB_MAXM - 1 || m != v) return OT_EINVAL;
+      if (m != p->m) {
+        p->m = m;
+        return alloc_buffers(p);
+      }
+      return OT_OK;
+    }
+    case OT_OPT_ETA:
+      if (!(v > 0.0 && v < 1.0)) return OT_EINVAL;
+      p->eta = v;
+      return OT_OK;
+    case OT_OPT_MAX_NEWTON:
+      if (v < 0 || v != (int)v) return OT_EINVAL;
+      p->max_newton = (int)v;
+      return OT_OK;
+    case OT_OPT_MAX_RESTARTS:
+      if (v < 1 || v != (int)v) return OT_EINVAL;
+      p->max_restarts = (int)v;
+      return OT_OK;
+    case OT_OPT_PRECISION: {
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if ((int)v != p->precision) {
+        p->precision = (int)v;
+        return alloc_buffers(p);
+      }
+      return OT_OK;
+    }
+    case OT_OPT_SAFEGUARD:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->safeguard = (int)v;
+      return OT_OK;
+    case OT_OPT_TRANSLATE:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->translate = (int)v;
+      return OT_OK;
+    case OT_OPT_WARM_START:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->warm_start = (int)v;
+      return OT_OK;
+    case OT_OPT_TAU:
+      if (!(v >= 1.0)) return OT_EINVAL;
+      p->tau = v;
+      return OT_OK;
+    case OT_OPT_TOL:
+      if (!(v > 0.0)) return OT_EINVAL;
+      p->tol = v;
+      return OT_OK;
+  }
+  return OT_EINVAL;
+}
+
+// ------------------------------------------------------------------------------------------
+// pipelines
+// ------------------------------------------------------------------------------------------
+template <typename T> static const SpecTables& tables(ot_plan* p);
+template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
+template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
+
+static cudaError_t read_scalars(ot_plan* p) {
+  cudaError_t e = cudaMemcpyAsync(p->hsc, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                                  p->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(p->stream);
+}
+
+// c = B-spline coefficients of g, in FP64 (prefilter by the symbol (2 + cos)/3 per axis)
+static cudaError_t run_prefilter(ot_plan* p, const double* g, double* c) {
+  C2<double>* sp = (C2<double>*)(p->precision ? p->spec64 : p->spec);
+  C2<double>* qq = (C2<double>*)(p->precision ? p->q64 : p->q0);
+  cudaError_t e;
+  e = launch_row_r2c<double>(g, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
+                             p->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_col<double>(COL_PREFILTER, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64, nullptr,
+                         nullptr, p->stream);
+  if (e != cudaSuccess) return e;
+  return launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
+                                nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream);
+}
+
+// w = L Lbar^{-1} x, x = V + (*jptr) P scaled by scale[*jptr] when jptr is given
+template <typename T>
+static cudaError_t run_matvec(ot_plan* p, const T* x, const int* jptr, const double* scale,
+                              T* w, const int* skip) {
+  const size_t P = (size_t)p->N * p->M;
+  const SpecTables& tb = tables<T>(p);
+  cudaError_t e;
+  e = launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip, p->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
+                    p->N, p->M, tb, p->sc, skip, p->stream);
+  if (e != cudaSuccess) return e;
+  return launch_row_c2r<T>(ROWINV_COMBINE, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
+                           (const T*)p->coef, w, nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb,
+                           skip, p->stream);
+}
+
+// u_out = u_in + step * Lbar^{-1} sigma  (UPDATE) or out = Lbar^{-1} sigma (PLAIN)
+template <typename T>
+static cudaError_t run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* u_out,
+                                double step, T* out) {
+  const SpecTables& tb = tables<T>(p);
+  cudaError_t e;
+  e = launch_row_r2c<T>(sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, p->N, p->M, tb, nullptr,
+                        p->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N, p->M,
+                    tb, p->sc, nullptr, p->stream);
+  if (e != cudaSuccess) return e;
+  if (out)
+    return launch_row_c2r<T>(ROWINV_PLAIN, (C2<T>*)p->q0, nullptr, nullptr, nullptr, out,
+                             nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb, nullptr, p->stream);
+  return launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
+                           u_in, u_out, step, 1.0, p->N, p->M, tb, nullptr, p->stream);
+}
+
+// GMRES(m) on L Lbar^{-1} sigma = (f - f~_n)/tau, sigma from 0.  Host syncs once per cycle.
+template <typename T>
+static int run_gmres(ot_plan* p) {
+  const long P = (long)p->N * p->M;
+  T* V = (T*)p->V;
+  T* w = (T*)p->w;
+  T* sigma = (T*)p->sigma;
+  const int* skip = &p->sc->cycle_done;
+  CK(cudaMemsetAsync(sigma, 0, P * sizeof(T), p->stream));
+  CK(launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
+  for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
+    for (int j = 0; j < p->m; ++j) {
+      CK(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip));
+      CK(launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+      CK(launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+    }
+    CK(launch_gmres_finish(p->sc, p->stream));
+    CK(launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
+    CK(read_scalars(p));
+    if (p->hsc->converged || cyc + 1 == p->max_restarts) break;
+    // explicit residual for the restart: V0 = h - A sigma
+    CK(run_matvec<T>(p, sigma, nullptr, nullptr, w, nullptr));
+    CK(launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks, p->stream));
+  }
+  return OT_OK;
+}
+
+static void set_solver_scalars(ot_plan* p) {
+  memset(p->hsc, 0, sizeof(DevScalars));
+  p->hsc->m = p->m;
+  p->hsc->eta = p->eta;
+  p->hsc->tau = p->tau;
+}
+
+template <typename T>
+static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
+                      ot_stats* st) {
+  ot_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  const int N = p->N, M = p->M;
+  const long P = (long)N * M;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, p->stream));
+  set_solver_scalars(p);
+  CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  if (p->translate) {
+    CK(launch_translate_inputs(f_in, g_in, p->f, p->g, N, M, p->partials, p->sc, p->stream));
+    CK(read_scalars(p));
+    if (p->hsc->in_bad) {
+      st->status = OT_EINVAL;
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      return OT_EINVAL;
+    }
+  } else {
+    if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  CK(run_prefilter(p, p->g, p->c));
+  if (p->warm_start) {
+    if (phi != p->u) CK(cudaMemcpyAsync(p->u, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
+  }
+  CK(launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
+                        p->stream));
+  CK(read_scalars(p));
+  int status = OT_OK;
+  double s = 1.0;
+  for (int n = 0;; ++n) {
+    const DevScalars* h = p->hsc;
+    st->res_inf = h->res_inf;
+    st->min_det = h->min_det;
+    st->mean_fn = h->mean_fn;
+    if (!h->admissible) {
+      status = OT_EDIVERGED;
+      break;
+    }
+    if (h->res_inf < p->tol) break;
+    if (n >= p->max_newton) {
+      status = OT_ENOCONV;
+      break;
+    }
+    int rc = run_gmres<T>(p);
+    if (rc != OT_OK) return rc;
+    st->gmres_iters += p->hsc->iters;
+    st->gmres_cycles += p->hsc->cycles;
+    bool accepted = false;
+    for (;;) {
+      CK(run_lbar_inv<T>(p, (const T*)p->sigma, p->u, p->ucand, s, nullptr));
+      CK(launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef, p->partials,
+                            p->sc, p->stream));
+      CK(read_scalars(p));
+      if (!p->safeguard || p->hsc->admissible || s < 0x1p-30) {
+        accepted = true;
+        break;
+      }
+      s *= 0.5;
+      st->step_halvings++;
+    }
+    (void)accepted;
+    double* t = p->u;
+    p->u = p->ucand;
+    p->ucand = t;
+    st->newton_iters = n + 1;
+    s = (2.0 * s < 1.0) ? 2.0 * s : 1.0;
+  }
+  // final l2 residual, mean-zero gauge (Sec. 3.1), result
+  if (status != OT_EDIVERGED || p->hsc->k1_nonfinite == 0) {
+    CK(launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+  }
+  CK(launch_subtract_mean(p->u, N, M, p->partials, p->sc, p->dmean, p->stream));
+  if (phi != p->u) CK(cudaMemcpyAsync(phi, p->u, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(&st->phi_mean, p->dmean, 8, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaEventRecord(ev1, p->stream));
+  CK(read_scalars(p));
+  st->res_l2 = sqrt(p->hsc->res_l2sum / (double)P);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  st->ms_total = ms;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  st->status = status;
+  return status;
+}
+
+extern "C" int ot_solve(ot_plan* p, const double* f, const double* g, double* phi,
+                        ot_stats* st) {
+  if (!p || !f || !g || !phi || !p->ready) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? solve_impl<float>(p, f, g, phi, st) : solve_impl<double>(p, f, g, phi, st);
+}
+
+extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, double* phi,
+                             ot_stats* st) {
+  if (!p || !f || !g || !phi || !p->ready) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  const size_t bytes = (size_t)p->N * p->M * 8;
+  // stage f, g in the plan's translated-density buffers (translated in place)
+  CK(cudaMemcpyAsync(p->f, f, bytes, cudaMemcpyHostToDevice, p->stream));
+  CK(cudaMemcpyAsync(p->g, g, bytes, cudaMemcpyHostToDevice, p->stream));
+  if (p->warm_start) CK(cudaMemcpyAsync(p->u, phi, bytes, cudaMemcpyHostToDevice, p->stream));
+  int rc = p->precision ? solve_impl<float>(p, p->f, p->g, p->u, st)
+                        : solve_impl<double>(p, p->f, p->g, p->u, st);
+  if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
+  CK(cudaMemcpyAsync(phi, p->u, bytes, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return rc;
+}
+
+extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* f,
+                                const double* const* g, double* const* phi, ot_stats* stats) {
+  if (count < 0 || (count > 0 && (!plans || !f || !g || !phi))) return OT_EINVAL;
+  int first = OT_OK;
+  for (int k = 0; k < count; ++k) {
+    int rc = ot_solve(plans[k], f[k], g[k], phi[k], stats ? &stats[k] : nullptr);
+    if (rc != OT_OK && first == OT_OK) first = rc;
+  }
+  return first;
+}
+
+// ------------------------------------------------------------------------------------------
+// step-level entry points
+// ------------------------------------------------------------------------------------------
+extern "C" int ot_prefilter(ot_plan* p, const double* g, double* c) {
+  if (!p || !g || !c) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  CK(run_prefilter(p, g, c));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+template <typename T>
+static int eval_residual_impl(ot_plan* p, const double* f, const double* c, const double* u,
+                              double* F, double* coef, double* scal) {
+  const int N = p->N, M = p->M;
+  const long P = (long)N * M;
+  set_solver_scalars(p);
+  CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  CK(launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream));
+  CK(launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+  if (F) CK(launch_shifted_residual(p->Fraw, F, N, M, p->sc, p->stream));
+  if (coef) CK(launch_convert<T>(p->coef, sizeof(T) == 8, coef, 1, 5 * P, p->stream));
+  CK(read_scalars(p));
+  if (scal) {
+    const DevScalars* h = p->hsc;
+    scal[0] = h->mean_fn;
+    scal[1] = h->res_inf;
+    scal[2] = sqrt(h->res_l2sum / (double)P);
+    scal[3] = h->min_det;
+    scal[4] = h->k1_nonfinite;
+    for (int a = 0; a < 5; ++a) scal[5 + a] = h->abar[a];
+  }
+  return OT_OK;
+}
+
+extern "C" int ot_eval_residual(ot_plan* p, const double* f, const double* c, const double* u,
+                                double* F, double* coef, double* scal) {
+  if (!p || !f || !c || !u) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? eval_residual_impl<float>(p, f, c, u, F, coef, scal)
+                      : eval_residual_impl<double>(p, f, c, u, F, coef, scal);
+}
+
+static int upload_abar(ot_plan* p, const double* abar) {
+  set_solver_scalars(p);
+  for (int a = 0; a < 5; ++a) p->hsc->abar[a] = abar[a];
+  CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  return OT_OK;
+}
+
+template <typename T>
+static int apply_op_impl(ot_plan* p, const double* coef, const double* abar,
+                         const double* sigma, double* w) {
+  const long P = (long)p->N * p->M;
+  int rc = upload_abar(p, abar);
+  if (rc) return rc;
+  CK(launch_convert<T>(coef, 1, p->coef, sizeof(T) == 8, 5 * P, p->stream));
+  CK(launch_convert<T>(sigma, 1, p->sigma, sizeof(T) == 8, P, p->stream));
+  CK(run_matvec<T>(p, (const T*)p->sigma, nullptr, nullptr, (T*)p->w, nullptr));
+  CK(launch_convert<T>(p->w, sizeof(T) == 8, w, 1, P, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_apply_operator(ot_plan* p, const double* coef, const double* abar,
+                                 const double* sigma, double* w) {
+  if (!p || !coef || !abar || !sigma || !w) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? apply_op_impl<float>(p, coef, abar, sigma, w)
+                      : apply_op_impl<double>(p, coef, abar, sigma, w);
+}
+
+template <typename T>
+static int lbar_impl(ot_plan* p, const double* abar, const double* sigma, double* theta) {
+  const long P = (long)p->N * p->M;
+  int rc = upload_abar(p, abar);
+  if (rc) return rc;
+  CK(launch_convert<T>(sigma, 1, p->sigma, sizeof(T) == 8, P, p->stream));
+  CK(run_lbar_inv<T>(p, (const T*)p->sigma, nullptr, nullptr, 0.0, (T*)p->w));
+  CK(launch_convert<T>(p->w, sizeof(T) == 8, theta, 1, P, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_apply_lbar_inverse(ot_plan* p, const double* abar, const double* sigma,
+                                     double* theta) {
+  if (!p || !abar || !sigma || !theta) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? lbar_impl<float>(p, abar, sigma, theta)
+                      : lbar_impl<double>(p, abar, sigma, theta);
+}
+
+template <typename T>
+static int fft_fwd_impl(ot_plan* p, const double* x, double* spec) {
+  const long P = (long)p->N * p->M;
+  const SpecTables& tb = tables<T>(p);
+  CK(launch_convert<T>(x, 1, p->sigma, sizeof(T) == 8, P, p->stream));
+  CK(launch_row_r2c<T>((const T*)p->sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, p->N, p->M,
+                       tb, nullptr, p->stream));
+  CK(launch_col<T>(COL_FWD, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N, p->M, tb,
+                   nullptr, nullptr, p->stream));
+  CK(launch_convert<T>(p->q0, sizeof(T) == 8, spec, 1, P, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+template <typename T>
+static int fft_inv_impl(ot_plan* p, const double* spec, double* x) {
+  const long P = (long)p->N * p->M;
+  const SpecTables& tb = tables<T>(p);
+  CK(launch_convert<T>(spec, 1, p->spec, sizeof(T) == 8, P, p->stream));
+  CK(launch_col<T>(COL_INV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N, p->M, tb,
+                   nullptr, nullptr, p->stream));
+  CK(launch_row_c2r<T>(ROWINV_PLAIN, (C2<T>*)p->q0, nullptr, nullptr, nullptr, (T*)p->w,
+                       nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb, nullptr, p->stream));
+  CK(launch_convert<T>(p->w, sizeof(T) == 8, x, 1, P, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_fft_forward(ot_plan* p, const double* x, double* spec) {
+  if (!p || !x || !spec) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? fft_fwd_impl<float>(p, x, spec) : fft_fwd_impl<double>(p, x, spec);
+}
+
+extern "C" int ot_fft_inverse(ot_plan* p, const double* spec, double* x) {
+  if (!p || !spec || !x) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? fft_inv_impl<float>(p, spec, x) : fft_inv_impl<double>(p, spec, x);
+}

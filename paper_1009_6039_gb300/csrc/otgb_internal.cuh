@@ -1,0 +1,106 @@
+// Internal declarations shared by the CUDA translation units of libotgb.
+// Grid convention: row-major N x M planes; row index i is y = i/N, column index j is
+// x = j/M.  Half spectra are N x (M/2) complex in "packed" form: column 0 of every row
+// holds the two real row coefficients X(k1 = 0) + i X(k1 = M/2).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define OTGB_MAXM 16  // largest GMRES restart length + 1 held on the device
+
+namespace otgb {
+
+template <typename T> struct c2;
+template <> struct c2<float> { using type = float2; };
+template <> struct c2<double> { using type = double2; };
+template <typename T> using C2 = typename c2<T>::type;
+
+// Scalars of one solve, resident in device memory.  Kernels that end in a grid-wide
+// reduction write their block partials to a scratch array; the last block to finish
+// (ticket counter) reduces them in a fixed order and updates this struct, so results are
+// deterministic and no host round trip is needed.
+struct DevScalars {
+  // input translation (Eq. translation applied to f and g)
+  double in_mean[2], in_min[2];
+  int in_nonfinite[2];
+  int in_bad;
+  // residual / coefficient evaluation
+  double mean_fn, shift, res_inf, min_det, abar[5];
+  double res_l2sum;
+  int k1_nonfinite;
+  int admissible;
+  // GMRES(m) state
+  double bnorm, beta;
+  double H[(OTGB_MAXM + 1) * OTGB_MAXM];
+  double cs[OTGB_MAXM], sn[OTGB_MAXM], gv[OTGB_MAXM + 1], y[OTGB_MAXM];
+  double scale[OTGB_MAXM + 1];  // V_i is stored unnormalised; v_i = scale[i] * V_i
+  double relres;
+  int j, jend, m, cycle_done, converged, iters, cycles;
+  double eta, tau;
+  // ticket counters of the last-block reductions
+  unsigned int ticket[8];
+};
+
+enum { TK_INPUT = 0, TK_RESID = 1, TK_DOTS = 2, TK_UPDATE = 3, TK_INIT = 4, TK_NORM = 5 };
+
+// Spectral kernels (instantiated for float and double) --------------------------------
+enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MATVEC = 2, COL_LBARINV = 3, COL_PREFILTER = 4 };
+enum RowInvMode { ROWINV_PLAIN = 0, ROWINV_COMBINE = 1, ROWINV_UPDATE = 2 };
+
+struct SpecTables {
+  const void* twL;  // exp(-2 pi i t / (M/2)), t < M/2 (row transforms)
+  const void* twM;  // exp(-2 pi i k / M), k < M/2 (real-to-complex split)
+  const void* twN;  // exp(-2 pi i t / N), t < N (column transforms)
+};
+
+bool fft_length_supported(int L);
+
+template <typename T>
+cudaError_t launch_row_r2c(const T* x, size_t x_stride, const int* jptr, const double* scale,
+                           C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* out0, C2<T>* out1, C2<T>* out2,
+                       int N, int M, const SpecTables& tb, const DevScalars* sc,
+                       const int* skip, cudaStream_t st);
+template <typename T>
+cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
+                           const T* coef, T* out, const double* u_in, double* u_out,
+                           double step, double out_scale, int N, int M, const SpecTables& tb,
+                           const int* skip, cudaStream_t st);
+
+// Residual / coefficients, input translation ------------------------------------------
+cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
+                                    int N, int M, double* partials, DevScalars* sc,
+                                    cudaStream_t st);
+template <typename T>
+cudaError_t launch_residual(const double* f, const double* c, const double* u, int N, int M,
+                            double* Fraw, T* coef, double* partials, DevScalars* sc,
+                            cudaStream_t st);
+cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
+                               DevScalars* sc, cudaStream_t st);
+cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
+                                    const DevScalars* sc, cudaStream_t st);
+cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevScalars* sc,
+                                 double* mean_out, cudaStream_t st);
+int residual_partial_blocks(int N, int M);
+
+// Krylov kernels -------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
+                              double* partials, DevScalars* sc, int nblocks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
+                              int nblocks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
+                                int nblocks, cudaStream_t st);
+cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,
+                                 int nblocks, cudaStream_t st);
+template <typename T>
+cudaError_t launch_convert(const void* in, int in_is_double, void* out, int out_is_double,
+                           long n, cudaStream_t st);
+
+}  // namespace otgb

@@ -1,0 +1,633 @@
+// Spectral kernels of Strain's method (Sec. 4.2): batched 2-D real FFTs of the packed
+// half spectrum with the symbol multiplies and the coefficient apply fused in.
+//
+// A 1-D transform of length L is done by one group of L/E threads on a shared-memory
+// buffer: a Stockham auto-sort FFT whose stages have radix 8/4/2 (L = 2^a, E = 8) or a
+// first radix-3 stage followed by radix 4/2 (L = 3 * 2^a, E = 12).  Each thread holds the
+// E elements of its E/R butterflies in registers between the shared-memory read and write
+// of a stage.  Twiddles come from a table exp(-2 pi i t / L) built once per plan.
+//
+// Matvec (the dominant step, Sec. 4.2):
+//   row_r2c          sigma (N x M real)  -> X (N x M/2 complex, packed)
+//   col COL_MATVEC   X -> sigma-hat (column FFT) -> S = rho-bar sigma-hat / (N M)
+//                    -> Q0 = S, Q1 = (2 pi i k2) S, Q2 = -(2 pi k2)^2 S -> inverse column FFTs
+//   row_c2r COMBINE  five row inverse transforms (d_xx Q0, d_x Q0, d_x Q1, Q1, Q2) weighted
+//                    by a11, b1, 2 a12, b2, a22 and summed: w = L Lbar^{-1} sigma.
+#pragma once
+#include "otgb_internal.cuh"
+
+namespace otgb {
+
+#define OTGB_TWO_PI 6.283185307179586476925286766559
+#define OTGB_SQRT_HALF 0.70710678118654752440084436210485
+#define OTGB_SQRT3_HALF 0.86602540378443864676372317075294
+
+template <typename T> __device__ __forceinline__ C2<T> mk2(T x, T y) {
+  C2<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T> __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) {
+  return mk2<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T> __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) {
+  return mk2<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk2<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ C2<T> cconj(C2<T> a) {
+  return mk2<T>(a.x, -a.y);
+}
+template <typename T> __device__ __forceinline__ C2<T> cscale(C2<T> a, T s) {
+  return mk2<T>(a.x * s, a.y * s);
+}
+// multiply by SIGN * i
+template <typename T, int SIGN> __device__ __forceinline__ C2<T> mul_si(C2<T> a) {
+  return SIGN > 0 ? mk2<T>(-a.y, a.x) : mk2<T>(a.y, -a.x);
+}
+
+// In-register DFTs of size R with exponent sign SIGN (-1 forward, +1 inverse).
+template <typename T, int R, int SIGN> struct Bfly;
+
+template <typename T, int SIGN> struct Bfly<T, 2, SIGN> {
+  __device__ __forceinline__ static void run(C2<T>* v) {
+    C2<T> a = v[0], b = v[1];
+    v[0] = cadd<T>(a, b);
+    v[1] = csub<T>(a, b);
+  }
+};
+
+template <typename T, int SIGN> struct Bfly<T, 3, SIGN> {
+  __device__ __forceinline__ static void run(C2<T>* v) {
+    C2<T> a = v[0], s = cadd<T>(v[1], v[2]), d = csub<T>(v[1], v[2]);
+    C2<T> t = mk2<T>(a.x - (T)0.5 * s.x, a.y - (T)0.5 * s.y);
+    C2<T> u = cscale<T>(mul_si<T, SIGN>(d), (T)OTGB_SQRT3_HALF);
+    v[0] = cadd<T>(a, s);
+    v[1] = cadd<T>(t, u);
+    v[2] = csub<T>(t, u);
+  }
+};
+
+template <typename T, int SIGN> struct Bfly<T, 4, SIGN> {
+  __device__ __forceinline__ static void run(C2<T>* v) {
+    C2<T> t0 = cadd<T>(v[0], v[2]), t1 = csub<T>(v[0], v[2]);
+    C2<T> t2 = cadd<T>(v[1], v[3]), t3 = mul_si<T, SIGN>(csub<T>(v[1], v[3]));
+    v[0] = cadd<T>(t0, t2);
+    v[2] = csub<T>(t0, t2);
+    v[1] = cadd<T>(t1, t3);
+    v[3] = csub<T>(t1, t3);
+  }
+};
+
+template <typename T, int SIGN> struct Bfly<T, 8, SIGN> {
+  __device__ __forceinline__ static void run(C2<T>* v) {
+    C2<T> e[4] = {v[0], v[2], v[4], v[6]};
+    C2<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Bfly<T, 4, SIGN>::run(e);
+    Bfly<T, 4, SIGN>::run(o);
+    // o[k] *= exp(SIGN 2 pi i k / 8)
+    const T h = (T)OTGB_SQRT_HALF;
+    C2<T> o1 = o[1], o3 = o[3];
+    o[1] = mk2<T>(h * (o1.x - SIGN * o1.y), h * (o1.y + SIGN * o1.x));
+    o[2] = mul_si<T, SIGN>(o[2]);
+    o[3] = mk2<T>(h * (-o3.x - SIGN * o3.y), h * (-o3.y + SIGN * o3.x));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd<T>(e[k], o[k]);
+      v[k + 4] = csub<T>(e[k], o[k]);
+    }
+  }
+};
+
+// One Stockham stage of radix R on a transform of length L held in buf (all threads of
+// the block must call it; inactive threads only take part in the barriers).
+template <typename T, int E, int R, int SIGN>
+__device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t, bool active,
+                                               const C2<T>* __restrict__ tw) {
+  const int TPT = L / E;
+  const int LR = L / R;
+  C2<T> v[E];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = buf[j + r * LR];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int tstep = L / (Ns * R);
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = tw[k * r * tstep];
+        if (SIGN > 0) w.y = -w.y;
+        v[b * R + r] = cmul<T>(v[b * R + r], w);
+      }
+      Bfly<T, R, SIGN>::run(&v[b * R]);
+      const int d = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[d + r * Ns] = v[b * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full unnormalised transform X_k = sum_n x_n exp(SIGN 2 pi i k n / L), in place in buf.
+// Radix sequence: [3,] then 8s (E = 8) or 4s (E = 12), then the remaining 4 or 2.
+template <typename T, int E, int SIGN>
+__device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
+                                         const C2<T>* __restrict__ tw) {
+  int Ns = 1;
+  int rem = L;
+  if (E % 3 == 0) {
+    stockham_stage<T, E, 3, SIGN>(buf, L, Ns, t, active, tw);
+    Ns *= 3;
+    rem /= 3;
+  }
+  while (rem > 1) {
+    if (E % 8 == 0 && rem % 8 == 0) {
+      stockham_stage<T, E, 8, SIGN>(buf, L, Ns, t, active, tw);
+      Ns *= 8;
+      rem /= 8;
+    } else if (rem % 4 == 0) {
+      stockham_stage<T, E, 4, SIGN>(buf, L, Ns, t, active, tw);
+      Ns *= 4;
+      rem /= 4;
+    } else {
+      stockham_stage<T, E, 2, SIGN>(buf, L, Ns, t, active, tw);
+      Ns *= 2;
+      rem /= 2;
+    }
+  }
+}
+
+// signed frequency of index n of length L, with a Nyquist flag
+__device__ __forceinline__ int sfreq(int n, int L, bool* nyq) {
+  *nyq = (2 * n == L);
+  return (2 * n <= L) ? n : n - L;
+}
+
+// rho-bar(k) = 1 / (abar11 d11 + 2 abar12 d1 d2 + abar22 d22 + bbar1 d1 + bbar2 d2) with
+// d1 = 2 pi i k1 (0 at Nyquist), d11 = -(2 pi k1)^2; 0 where the denominator is 0.
+template <typename T>
+__device__ __forceinline__ C2<T> rho_bar(const T ab[5], int k1, bool n1, int k2, bool n2) {
+  const T tp = (T)OTGB_TWO_PI;
+  T s1 = n1 ? (T)0 : tp * (T)k1;
+  T s2 = n2 ? (T)0 : tp * (T)k2;
+  T q1 = tp * (T)k1, q2 = tp * (T)k2;
+  T dr = -ab[0] * q1 * q1 - (T)2 * ab[1] * s1 * s2 - ab[2] * q2 * q2;
+  T di = ab[3] * s1 + ab[4] * s2;
+  T den = dr * dr + di * di;
+  if (den == (T)0) return mk2<T>((T)0, (T)0);
+  return mk2<T>(dr / den, -di / den);
+}
+
+// ---------------------------------------------------------------------------------------
+// Row real-to-complex transform (forward), packed output.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct MaxThreads {
+  static constexpr int value = sizeof(T) == 8 ? 256 : 512;
+};
+
+template <typename T, int E>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __restrict__ xbase, size_t x_stride,
+                          const int* __restrict__ jptr, const double* __restrict__ scale,
+                          C2<T>* __restrict__ spec, int N, int M,
+                          const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
+                          const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int L = M / 2;
+  const int TPT = L / E;
+  const int q = threadIdx.x / TPT, t = threadIdx.x % TPT;
+  const int RB = blockDim.x / TPT;
+  const int row = blockIdx.x * RB + q;
+  const bool active = row < N;
+  C2<T>* buf = sm + q * (L + 1);
+  int jv = jptr ? *jptr : 0;
+  const T* x = xbase + (size_t)jv * x_stride;
+  const T sc = scale ? (T)scale[jv] : (T)1;
+  if (active) {
+    const C2<T>* xr = reinterpret_cast<const C2<T>*>(x + (size_t)row * M);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + e * TPT;
+      C2<T> z = xr[n];
+      buf[n] = mk2<T>(z.x * sc, z.y * sc);
+    }
+  }
+  __syncthreads();
+  fft_smem<T, E, -1>(buf, L, t, active, twL);
+  if (active) {
+    C2<T>* out = spec + (size_t)row * L;
+    for (int k = t; k <= L / 2; k += TPT) {
+      if (k == 0) {
+        C2<T> z = buf[0];
+        out[0] = mk2<T>(z.x + z.y, z.x - z.y);
+      } else {
+        C2<T> zk = buf[k], zm = buf[L - k];
+        // E = (Zk + conj Zm)/2, O = -i (Zk - conj Zm)/2, X_k = E + W_M^k O,
+        // X_{L-k} = conj(E - W_M^k O)
+        C2<T> Ev = mk2<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+        C2<T> Ov = mk2<T>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+        C2<T> wo = cmul<T>(twM[k], Ov);
+        out[k] = cadd<T>(Ev, wo);
+        if (2 * k != L) out[L - k] = cconj<T>(csub<T>(Ev, wo));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Column transforms with the spectral multiplies of Strain's method.
+// ---------------------------------------------------------------------------------------
+template <typename T, int E>
+__device__ __forceinline__ void col_load(const C2<T>* __restrict__ src, C2<T>* sm, int N,
+                                         int Lc, int Q, int col0) {
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx / Q, q = idx % Q;
+    const int col = col0 + q;
+    if (col < Lc) sm[q * (N + 1) + n] = src[(size_t)n * Lc + col];
+  }
+}
+
+template <typename T, int E>
+__device__ __forceinline__ void col_store(C2<T>* __restrict__ dst, const C2<T>* sm, int N,
+                                          int Lc, int Q, int col0) {
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx / Q, q = idx % Q;
+    const int col = col0 + q;
+    if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * (N + 1) + n];
+  }
+}
+
+template <typename T, int E, int MODE>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
+                      C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
+                      const C2<T>* __restrict__ twN, const C2<T>* __restrict__ twM,
+                      const DevScalars* __restrict__ sc, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int Lc = M / 2;
+  const int TPT = N / E;
+  const int q = threadIdx.x / TPT, t = threadIdx.x % TPT;
+  const int col0 = blockIdx.x * Q;
+  const int col = col0 + q;
+  const bool active = (q < Q) && (col < Lc);
+  C2<T>* buf = sm + q * (N + 1);
+
+  col_load<T, E>(spec, sm, N, Lc, Q, col0);
+  __syncthreads();
+  if (MODE == COL_INV) {
+    fft_smem<T, E, +1>(buf, N, t, active, twN);
+    col_store<T, E>(out0, sm, N, Lc, Q, col0);
+    return;
+  }
+  fft_smem<T, E, -1>(buf, N, t, active, twN);
+  if (MODE == COL_FWD) {
+    col_store<T, E>(out0, sm, N, Lc, Q, col0);
+    return;
+  }
+  T ab[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ab[a] = sc ? (T)sc->abar[a] : (T)0;
+  const T inv = (T)(1.0 / ((double)N * (double)M));
+  C2<T> s[E];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      C2<T> z = buf[k];
+      C2<T> r;
+      if (col == 0) {
+        // unpack the two real columns k1 = 0 and k1 = M/2 carried as X0 + i XL
+        C2<T> p = buf[(N - k) % N];
+        C2<T> A = mk2<T>((T)0.5 * (z.x + p.x), (T)0.5 * (z.y - p.y));
+        C2<T> B = mk2<T>((T)0.5 * (z.y + p.y), (T)-0.5 * (z.x - p.x));
+        if (MODE == COL_PREFILTER) {
+          // divide by the cubic B-spline symbol (2 + cos 2 pi k / L) / 3 per axis
+          const T by = ((T)2 + twN[k].x) / (T)3;
+          A = cscale<T>(A, (T)1 / by);           // k1 = 0: factor 1
+          B = cscale<T>(B, (T)3 / by);           // k1 = M/2: factor 1/3
+        } else {
+          A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
+          B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
+        }
+        r = mk2<T>(A.x - B.y, A.y + B.x);  // A + i B
+      } else {
+        if (MODE == COL_PREFILTER) {
+          const T by = ((T)2 + twN[k].x) / (T)3;
+          const T bx = ((T)2 + twM[col].x) / (T)3;
+          r = cscale<T>(z, (T)1 / (bx * by));
+        } else {
+          r = cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z);
+        }
+      }
+      s[e] = cscale<T>(r, inv);
+    }
+  }
+  __syncthreads();
+  const int nout = (MODE == COL_MATVEC) ? 3 : 1;
+#pragma unroll 1
+  for (int p = 0; p < nout; ++p) {
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = t + e * TPT;
+        bool nyq2;
+        const int k2 = sfreq(k, N, &nyq2);
+        const T q2 = (T)OTGB_TWO_PI * (T)k2;
+        C2<T> v = s[e];
+        if (p == 1) {  // (2 pi i k2) S, zero at Nyquist
+          v = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
+        } else if (p == 2) {  // -(2 pi k2)^2 S
+          v = cscale<T>(v, -q2 * q2);
+        }
+        buf[k] = v;
+      }
+    }
+    __syncthreads();
+    fft_smem<T, E, +1>(buf, N, t, active, twN);
+    col_store<T, E>(p == 0 ? out0 : (p == 1 ? out1 : out2), sm, N, Lc, Q, col0);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Row complex-to-real inverse transforms (raw: sum over the full Hermitian spectrum).
+// ---------------------------------------------------------------------------------------
+// row symbol kinds: 0 = 1, 1 = d/dx = 2 pi i k1 (0 at Nyquist), 2 = d2/dx2 = -(2 pi k1)^2
+template <typename T>
+__device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int L, int kind) {
+  const T tp = (T)OTGB_TWO_PI;
+  if (kind == 0) return X;
+  if (k == 0) {
+    // packed (X0, XL): k1 = 0 and k1 = M/2 (Nyquist)
+    if (kind == 1) return mk2<T>((T)0, (T)0);
+    const T qn = tp * (T)L;  // 2 pi (M/2)
+    return mk2<T>((T)0, -qn * qn * X.y);
+  }
+  const T q = tp * (T)k;
+  if (kind == 1) return mk2<T>(-q * X.y, q * X.x);
+  return cscale<T>(X, -q * q);
+}
+
+// complex-to-real pre-processing on a packed row in buf (in place):
+// Z_k = (X_k + conj X_{L-k}) + i (X_k - conj X_{L-k}) conj(W_M^k)
+template <typename T>
+__device__ __forceinline__ void c2r_preprocess(C2<T>* buf, int L, int t, int TPT, bool active,
+                                               const C2<T>* __restrict__ twM) {
+  if (active) {
+    for (int k = t; k <= L / 2; k += TPT) {
+      if (k == 0) {
+        C2<T> x = buf[0];
+        buf[0] = mk2<T>(x.x + x.y, x.x - x.y);
+      } else {
+        C2<T> xk = buf[k], xm = buf[L - k];
+        C2<T> Ev = mk2<T>(xk.x + xm.x, xk.y - xm.y);
+        C2<T> dv = mk2<T>(xk.x - xm.x, xk.y + xm.y);
+        C2<T> Ov = cmul<T>(dv, cconj<T>(twM[k]));
+        buf[k] = mk2<T>(Ev.x - Ov.y, Ev.y + Ov.x);
+        if (2 * k != L) buf[L - k] = mk2<T>(Ev.x + Ov.y, -Ev.y + Ov.x);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int E, int MODE>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* __restrict__ q0, const C2<T>* __restrict__ q1,
+                          const C2<T>* __restrict__ q2, const T* __restrict__ coef,
+                          T* __restrict__ out, const double* __restrict__ u_in,
+                          double* __restrict__ u_out, double step, double out_scale, int N,
+                          int M, const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
+                          const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int L = M / 2;
+  const int TPT = L / E;
+  const int q = threadIdx.x / TPT, t = threadIdx.x % TPT;
+  const int RB = blockDim.x / TPT;
+  const int row = blockIdx.x * RB + q;
+  const bool active = row < N;
+  C2<T>* buf = sm + q * (L + 1);
+  const size_t P = (size_t)N * M;
+  C2<T> acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = mk2<T>((T)0, (T)0);
+
+  const int nterm = (MODE == ROWINV_COMBINE) ? 5 : 1;
+#pragma unroll 1
+  for (int p = 0; p < nterm; ++p) {
+    // term p: source plane, row symbol, coefficient plane, multiplicity
+    const C2<T>* src = q0;
+    int kind = 0, cidx = 0;
+    T mult = (T)1;
+    if (MODE == ROWINV_COMBINE) {
+      if (p == 0) { src = q0; kind = 2; cidx = 0; }              // a11 * d_xx Lbar^-1 s
+      else if (p == 1) { src = q0; kind = 1; cidx = 3; }         // b1  * d_x  Lbar^-1 s
+      else if (p == 2) { src = q1; kind = 1; cidx = 1; mult = (T)2; }  // 2 a12 * d_xy
+      else if (p == 3) { src = q1; kind = 0; cidx = 4; }         // b2  * d_y
+      else { src = q2; kind = 0; cidx = 2; }                     // a22 * d_yy
+    }
+    if (active) {
+      const C2<T>* sr = src + (size_t)row * L;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = t + e * TPT;
+        buf[k] = row_symbol_apply<T>(sr[k], k, L, kind);
+      }
+    }
+    __syncthreads();
+    c2r_preprocess<T>(buf, L, t, TPT, active, twM);
+    fft_smem<T, E, +1>(buf, L, t, active, twL);
+    if (active) {
+      if (MODE == ROWINV_COMBINE) {
+        const C2<T>* cr = reinterpret_cast<const C2<T>*>(coef + (size_t)cidx * P +
+                                                         (size_t)row * M);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int n = t + e * TPT;
+          C2<T> z = buf[n], a = cr[n];
+          acc[e].x += mult * a.x * z.x;
+          acc[e].y += mult * a.y * z.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = buf[t + e * TPT];
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  if (MODE == ROWINV_UPDATE) {
+    const double2* ui = reinterpret_cast<const double2*>(u_in + (size_t)row * M);
+    double2* uo = reinterpret_cast<double2*>(u_out + (size_t)row * M);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + e * TPT;
+      double2 a = ui[n];
+      a.x += step * (double)acc[e].x;
+      a.y += step * (double)acc[e].y;
+      uo[n] = a;
+    }
+  } else {
+    C2<T>* o = reinterpret_cast<C2<T>*>(out + (size_t)row * M);
+    const T os = (T)out_scale;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + e * TPT;
+      o[n] = (MODE == ROWINV_PLAIN) ? cscale<T>(acc[e], os) : acc[e];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------------------
+inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
+
+template <typename K>
+inline cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+  return cudaSuccess;
+}
+
+template <typename T, int E>
+cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scale, C2<T>* spec,
+                      int N, int M, const SpecTables& tb, const int* skip, cudaStream_t st) {
+  const int L = M / 2, TPT = L / E;
+  int RB = MaxThreads<T>::value / TPT;
+  if (RB < 1) RB = 1;
+  if (RB > N) RB = N;
+  const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_row_r2c<T, E>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_r2c<T, E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
+      x, xs, jptr, scale, spec, N, M, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int MODE>
+cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int M,
+                  const SpecTables& tb, const DevScalars* sc, const int* skip,
+                  cudaStream_t st) {
+  const int Lc = M / 2, TPT = N / E;
+  int Q = MaxThreads<T>::value / TPT;
+  if (Q < 1) Q = 1;
+  while (Q > 1 && (size_t)Q * (N + 1) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
+  if (Q > Lc) Q = Lc;
+  const size_t sm = (size_t)Q * (N + 1) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
+  if (e != cudaSuccess) return e;
+  k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+      spec, o0, o1, o2, N, M, Q, (const C2<T>*)tb.twN, (const C2<T>*)tb.twM, sc, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int E, int MODE>
+cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T* coef, T* out,
+                      const double* u_in, double* u_out, double step, double out_scale, int N,
+                      int M, const SpecTables& tb, const int* skip, cudaStream_t st) {
+  const int L = M / 2, TPT = L / E;
+  int RB = MaxThreads<T>::value / TPT;
+  if (RB < 1) RB = 1;
+  if (RB > N) RB = N;
+  const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_row_c2r<T, E, MODE>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
+      q0, q1, q2, coef, out, u_in, u_out, step, out_scale, N, M, (const C2<T>*)tb.twL,
+      (const C2<T>*)tb.twM, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double* scale,
+                           C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
+                           cudaStream_t st) {
+  if (fft_E(M / 2) == 12) return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
+  return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
+}
+
+template <typename T, int E>
+cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
+                         int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
+                         cudaStream_t st) {
+  switch (mode) {
+    case COL_FWD: return col_E<T, E, COL_FWD>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_INV: return col_E<T, E, COL_INV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_MATVEC: return col_E<T, E, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_LBARINV: return col_E<T, E, COL_LBARINV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_PREFILTER:
+      return col_E<T, E, COL_PREFILTER>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
+                       int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
+                       cudaStream_t st) {
+  if (fft_E(N) == 12) return col_dispatch<T, 12>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
+  return col_dispatch<T, 8>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
+}
+
+template <typename T, int E>
+cudaError_t row_c2r_dispatch(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
+                             const T* coef, T* out, const double* u_in, double* u_out,
+                             double step, double os, int N, int M, const SpecTables& tb,
+                             const int* skip, cudaStream_t st) {
+  switch (mode) {
+    case ROWINV_PLAIN:
+      return row_c2r_E<T, E, ROWINV_PLAIN>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
+                                           tb, skip, st);
+    case ROWINV_COMBINE:
+      return row_c2r_E<T, E, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N,
+                                             M, tb, skip, st);
+    case ROWINV_UPDATE:
+      return row_c2r_E<T, E, ROWINV_UPDATE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
+                                            tb, skip, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
+                           const T* coef, T* out, const double* u_in, double* u_out,
+                           double step, double os, int N, int M, const SpecTables& tb,
+                           const int* skip, cudaStream_t st) {
+  if (fft_E(M / 2) == 12)
+    return row_c2r_dispatch<T, 12>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
+                                   tb, skip, st);
+  return row_c2r_dispatch<T, 8>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M, tb,
+                                skip, st);
+}
+
+#define OTGB_INSTANTIATE_SPECTRAL(T)                                                         \
+  template cudaError_t launch_row_r2c<T>(const T*, size_t, const int*, const double*,        \
+                                         C2<T>*, int, int, const SpecTables&, const int*,    \
+                                         cudaStream_t);                                      \
+  template cudaError_t launch_col<T>(int, const C2<T>*, C2<T>*, C2<T>*, C2<T>*, int, int,    \
+                                     const SpecTables&, const DevScalars*, const int*,       \
+                                     cudaStream_t);                                          \
+  template cudaError_t launch_row_c2r<T>(int, const C2<T>*, const C2<T>*, const C2<T>*,      \
+                                         const T*, T*, const double*, double*, double,       \
+                                         double, int, int, const SpecTables&, const int*,    \
+                                         cudaStream_t);
+
+}  // namespace otgb

@@ -1,0 +1,247 @@
+"""GPU parity: every stage of the CUDA path, called through the C ABI, against the CPU
+oracle on the same seeded inputs.
+
+Tolerances: FP64 stages are compared to the oracle's FP64 result within a few hundred ulps
+of the result's scale (different summation order, FMA contraction and FFT factorisation);
+FP32 (mixed-mode) stages within 2e-5 of the scale (FP32 round-off, 2^-24 ~ 6e-8, grown
+by the log2 P stages of the FFT and the symbol magnitudes).  Solves: ||phi_gpu -
+phi_oracle||_inf <= 1e-10 for the FP64 path after the same Newton steps, <= 1e-6 for the
+mixed path at the same residual tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import ot_inputs as I
+from gpu_util import dev, hptr, pack_spectrum, ptr, unpack_spectrum
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(8, 16), (12, 24), (16, 16), (24, 48), (128, 48), (64, 96), (12, 512), (192, 384),
+         (256, 256)]
+RNG = np.random.default_rng(7)
+
+
+@pytest.fixture(scope="module")
+def ot():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1009_6039_gb300 as m
+    return m
+
+
+def plan(ot, N, M, precision="fp64", **kw):
+    return ot.Plan(N, M, precision=precision, **kw)
+
+
+def smooth_field(N, M, amp=1.0, kmax=4):
+    y, x = np.meshgrid(np.arange(N) / N, np.arange(M) / M, indexing="ij")
+    u = np.zeros((N, M))
+    for _ in range(6):
+        k1, k2 = RNG.integers(-kmax, kmax + 1, 2)
+        ph = RNG.random() * 2 * np.pi
+        u += RNG.standard_normal() * np.cos(2 * np.pi * (k1 * x + k2 * y) + ph)
+    return amp * u
+
+
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N,M", SIZES)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_fft_forward_inverse(ot, N, M, prec):
+    x = RNG.standard_normal((N, M))
+    p = plan(ot, N, M, prec)
+    xd = dev(x)
+    sd = dev(np.zeros((N, M)))
+    assert ot.ot_fft_forward(p.h, ptr(xd), ptr(sd)) == 0
+    half = unpack_spectrum(sd.cpu().numpy(), N, M)
+    ref = O.fft2(x)[:, :M // 2 + 1]
+    tol = (2e-13 if prec == "fp64" else 2e-5) * np.abs(ref).max()
+    assert np.abs(half - ref).max() <= tol
+    # inverse (unnormalised) of the oracle's spectrum returns N M x
+    sd2 = dev(pack_spectrum(ref, N, M))
+    xo = dev(np.zeros((N, M)))
+    assert ot.ot_fft_inverse(p.h, ptr(sd2), ptr(xo)) == 0
+    back = xo.cpu().numpy() / (N * M)
+    assert np.abs(back - x).max() <= (2e-13 if prec == "fp64" else 2e-5) * np.abs(x).max()
+    p.close()
+
+
+@pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (192, 384), (256, 256)])
+def test_prefilter(ot, N, M):
+    g = 1 + 0.5 * RNG.random((N, M))
+    p = plan(ot, N, M, "mixed")  # the prefilter is FP64 in both modes
+    gd, cd = dev(g), dev(np.zeros((N, M)))
+    assert ot.ot_prefilter(p.h, ptr(gd), ptr(cd)) == 0
+    assert np.abs(cd.cpu().numpy() - O.bspline_coeffs(g)).max() <= 1e-13
+    p.close()
+
+
+@pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (64, 96), (192, 384),
+                                 (256, 256)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_residual_and_coefficients(ot, N, M, prec):
+    f = I.blob_density(N, M, 11)
+    g = I.blob_density(N, M, 12)
+    u = smooth_field(N, M, amp=2e-3)
+    c = O.bspline_coeffs(g)
+    F_ref, coef_ref, s_ref = O.residual(f, c, u)
+    p = plan(ot, N, M, prec)
+    fd, cd, ud = dev(f), dev(c), dev(u)
+    Fd, coefd = dev(np.zeros((N, M))), dev(np.zeros((5, N, M)))
+    scal = np.zeros(10)
+    assert ot.ot_eval_residual(p.h, ptr(fd), ptr(cd), ptr(ud), ptr(Fd), ptr(coefd),
+                               hptr(scal)) == 0
+    # F and the scalars are FP64 in both modes
+    assert np.abs(Fd.cpu().numpy() - F_ref).max() <= 1e-12 * max(1, np.abs(f).max())
+    assert abs(scal[0] - s_ref["mean_fn"]) <= 1e-13
+    assert abs(scal[1] - s_ref["res_inf"]) <= 1e-12
+    assert abs(scal[2] - s_ref["res_l2"]) <= 1e-12
+    assert abs(scal[3] - s_ref["min_det"]) <= 1e-12
+    assert scal[4] == 0
+    abar_ref = [O.simpson_mean(coef_ref[q]) for q in range(5)]
+    assert np.abs(scal[5:] - abar_ref).max() <= 1e-12 * np.abs(coef_ref).max()
+    tol = (1e-12 if prec == "fp64" else 1e-6) * np.abs(coef_ref).max()
+    assert np.abs(coefd.cpu().numpy() - coef_ref).max() <= tol
+    p.close()
+
+
+@pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (64, 96), (192, 384),
+                                 (256, 256)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_operator_and_lbar_inverse(ot, N, M, prec):
+    f = I.blob_density(N, M, 21)
+    g = I.blob_density(N, M, 22)
+    u = smooth_field(N, M, amp=2e-3)
+    _, coef, _ = O.residual(f, O.bspline_coeffs(g), u)
+    abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
+    sigma = RNG.standard_normal((N, M))
+    w_ref = O.apply_op(coef, abar, sigma)
+    th_ref = O.apply_lbar_inv(abar, sigma)
+    p = plan(ot, N, M, prec)
+    cd, sd, wd, td = dev(coef), dev(sigma), dev(np.zeros((N, M))), dev(np.zeros((N, M)))
+    assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
+    assert ot.ot_apply_lbar_inverse(p.h, hptr(abar), ptr(sd), ptr(td)) == 0
+    r = 1e-12 if prec == "fp64" else 3e-5
+    assert np.abs(wd.cpu().numpy() - w_ref).max() <= r * np.abs(w_ref).max()
+    assert np.abs(td.cpu().numpy() - th_ref).max() <= r * np.abs(th_ref).max()
+    p.close()
+
+
+# ---------------------------------------------------------------------------------------
+def _gpu_solve(ot, f, g, prec="fp64", tau=2.0, tol=1e-10, **kw):
+    N, M = f.shape
+    p = plan(ot, N, M, prec, tau=tau, tol=tol, **kw)
+    fd, gd = dev(f), dev(g)
+    phi = dev(np.zeros((N, M)))
+    rc, st = p.solve(fd, gd, phi)
+    p.close()
+    return rc, st, phi.cpu().numpy()
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_solve_manufactured_fp64_matches_oracle(ot, N):
+    f, g, phi_star = I.manufactured(N, N)
+    u_ref, st_ref, hres, hgm = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-4)
+    rc, st, phi = _gpu_solve(ot, f, g, "fp64", eta=1e-4)
+    assert rc == 0 and st_ref["status"] == 0
+    assert st["newton_iters"] == st_ref["newton_iters"]
+    assert abs(st["gmres_iters"] - st_ref["gmres_iters"]) <= 2
+    assert np.abs(phi - u_ref).max() <= 1e-10
+    assert st["res_inf"] < 1e-10
+    assert abs(st["res_l2"] - st_ref["res_l2"]) <= 1e-11
+
+
+@pytest.mark.parametrize("N", [32, 64])
+def test_solve_manufactured_mixed(ot, N):
+    f, g, _ = I.manufactured(N, N)
+    u_ref, st_ref, _, _ = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-4)
+    rc, st, phi = _gpu_solve(ot, f, g, "mixed", eta=1e-4)
+    assert rc == 0 and st["res_inf"] < 1e-10
+    assert np.abs(phi - u_ref).max() <= 1e-6
+    # the mixed result certifies itself through the oracle's FP64 residual
+    F, _, s = O.residual(f, O.bspline_coeffs(g), phi)
+    assert s["res_inf"] < 1e-9
+
+
+@pytest.mark.parametrize("N,M", [(32, 32), (48, 64), (64, 48)])
+def test_solve_blob_pair_fp64_with_safeguard(ot, N, M):
+    f, g = I.blob_pair(N, M, s=1000 + N + M)
+    u_ref, st_ref, _, _ = O.solve(f, g, tau=2.0, tol=1e-9, eta=1e-2, max_newton=300)
+    rc, st, phi = _gpu_solve(ot, f, g, "fp64", tol=1e-9, eta=1e-2, max_newton=300)
+    assert st_ref["status"] == 0 and rc == 0
+    assert st["newton_iters"] == st_ref["newton_iters"]
+    assert st["step_halvings"] == st_ref["step_halvings"]
+    assert np.abs(phi - u_ref).max() <= 1e-10
+
+
+def test_safeguard_off_diverges_like_oracle(ot):
+    f, g = I.blob_pair(32, 32)
+    _, st_ref, _, _ = O.solve(f, g, tau=2.0, tol=1e-6, eta=1e-2, max_newton=40,
+                              safeguard=False)
+    rc, st, _ = _gpu_solve(ot, f, g, "fp64", tol=1e-6, eta=1e-2, max_newton=40, safeguard=0)
+    assert st_ref["status"] == O.ORC_EDIVERGED and rc == ot.OT_EDIVERGED
+    assert st["newton_iters"] == st_ref["newton_iters"]
+
+
+def test_equal_densities_and_invalid_inputs(ot):
+    f = I.blob_density(32, 32, 5)
+    rc, st, phi = _gpu_solve(ot, f, f.copy(), "fp64")
+    assert rc == 0 and st["newton_iters"] == 0 and np.abs(phi).max() == 0
+    bad = f.copy()
+    bad[4, 7] = -10.0
+    with pytest.raises(ot.OTError):
+        _gpu_solve(ot, bad, f)
+    bad[4, 7] = np.nan
+    with pytest.raises(ot.OTError):
+        _gpu_solve(ot, f, bad)
+    rc, h = ot.ot_plan_create(30, 30, 2.0, 1e-8)
+    assert rc == ot.OT_EUNSUPPORTED
+    rc, h = ot.ot_plan_create(32, 32, 0.5, 1e-8)
+    assert rc == ot.OT_EINVAL
+
+
+def test_max_newton_cap(ot):
+    f, g, _ = I.manufactured(32, 32)
+    rc, st, _ = _gpu_solve(ot, f, g, "fp64", max_newton=3)
+    assert rc == ot.OT_ENOCONV and st["newton_iters"] == 3
+
+
+def test_solve_host_buffers_equal_device(ot):
+    import ctypes
+    f, g = I.blob_pair(64, 64, s=77)
+    rc, st, phi = _gpu_solve(ot, f, g, "mixed", tol=1e-8, eta=1e-2)
+    p = plan(ot, 64, 64, "mixed", tau=2.0, tol=1e-8, eta=1e-2)
+    fh, gh = np.ascontiguousarray(f), np.ascontiguousarray(g)
+    ph = np.zeros((64, 64))
+    sth = ot.ot_stats()
+    rc2 = ot.ot_solve_host(p.h, hptr(fh), hptr(gh), hptr(ph), sth)
+    p.close()
+    assert rc == rc2 == 0
+    assert np.array_equal(ph, phi)
+
+
+def test_batched_uneven_sizes(ot):
+    import ctypes
+    import torch
+    sizes = [(32, 32), (48, 96), (64, 64), (24, 48)]
+    plans, fs, gs, phis, refs = [], [], [], [], []
+    for k, (N, M) in enumerate(sizes):
+        f, g = I.blob_pair(N, M, s=4000 + k)
+        refs.append(_gpu_solve(ot, f, g, "mixed", tol=1e-8, eta=1e-2)[2])
+        plans.append(plan(ot, N, M, "mixed", tau=2.0, tol=1e-8, eta=1e-2))
+        fs.append(dev(f))
+        gs.append(dev(g))
+        phis.append(dev(np.zeros((N, M))))
+    stats = (ot.ot_stats * len(sizes))()
+    rc = ot.ot_solve_batched(len(sizes), [p.h for p in plans], [t.data_ptr() for t in fs],
+                             [t.data_ptr() for t in gs], [t.data_ptr() for t in phis],
+                             stats)
+    assert rc == 0
+    for k in range(len(sizes)):
+        assert stats[k].status == 0
+        assert np.array_equal(phis[k].cpu().numpy(), refs[k])
+    for p in plans:
+        p.close()
