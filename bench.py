@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the periodic L2 optimal-transport solver (damped Newton + Strain's
+FFT-preconditioned GMRES) on one GB300.
+
+Workload: the smoothed-noise + 16-blob density pair at 1024 x 1024 (max/min = 10, mean 1,
+seed base 3000), tau = 2, GMRES(10) tolerance 0.1, solved to max|f - f~_n| < 1e-8 from
+phi = 0 in mixed precision (FP32 FFTs/Krylov, FP64 residual/update/check).  One step = one
+full solve.  Inputs are resident in HBM; an L2 flush (256 MB write) separates timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank solves its own pair (replicas,
+weak scaling) and rank 0 prints the line.
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("OT solves/s at 1024² to ‖res‖∞≤1e-8: mixed+learned vs plain "
+          "FP64 GPU; HBM %")
+N_GRID = 1024
+TAU, TOL, ETA = 2.0, 1e-8, 1e-1
+SEED = 3000
+WORKLOAD = ("smoothed-noise+16-blob density pair 1024x1024 (max/min 10, mean 1), tau=2, "
+            "GMRES(10) eta=0.1, tol 1e-8 from phi=0, mixed FP32-inner/FP64-outer")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=N_GRID)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------------------------------
+# algorithmic bytes per launch of each kernel class (every input read once, every output
+# written once); T = bytes of the inner precision, P = N * M
+# ----------------------------------------------------------------------------------------
+def algorithmic_bytes(cls, P, T, avg_basis):
+    return {
+        "residual": (8 + 8 + 8 + 8 + 5 * T) * P,       # u, f, c in; Fraw, 5 coefs out
+        "row_r2c": 2 * T * P,                           # sigma in, half spectrum out
+        "col_matvec": 4 * T * P,                        # spectrum in, Q0 Q1 Q2 out
+        "row_c2r_combine": 9 * T * P,                   # Q0..Q2 + 5 coefs in, w out
+        "col_lbarinv": 2 * T * P,
+        "row_c2r_update": (T + 16) * P,                 # Q0 + u in, candidate u out
+        "gmres_dots": (avg_basis + 1) * T * P,          # V_0..V_j and w in
+        "gmres_update": (avg_basis + 2) * T * P,        # V_0..V_j and w in, V_j+1 out
+    }.get(cls)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while active."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.samples, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in self.samples if num(s[0]) is not None]
+        mx = [num(s[1]) for s in self.samples if num(s[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def traffic_for(kernel_cls, size):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel source and this size; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_1009_6039_gb300", "csrc", "spectral.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kernel_cls)
+    if not e or e.get("source_sha") != h or e.get("size") != size:
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle sample (test infrastructure; used only for the baseline legs)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(f, g, reps=1):
+    """Times the oracle's building blocks on the workload: one residual/coefficient
+    evaluation and one preconditioned matvec L Lbar^{-1} sigma (each `reps` times), and
+    extrapolates to a full solve with the oracle's own Newton/GMRES counts for this workload
+    (tests/golden/noise1024.json, written by the oracle), else the counts passed in."""
+    import numpy as np
+    import oracle as O
+    t0 = time.perf_counter()
+    c = O.bspline_coeffs(g)
+    t_pre = time.perf_counter() - t0
+    u = np.zeros_like(f)
+    tr = tm = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        F, coef, _ = O.residual(f, c, u)
+        tr += time.perf_counter() - t0
+        abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
+        t0 = time.perf_counter()
+        O.apply_op(coef, abar, F)
+        tm += time.perf_counter() - t0
+    return t_pre, tr / reps, tm / reps
+
+
+def golden_counts(size):
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "noise%d.json" % size)) as fh:
+            d = json.load(fh)
+        st = d["stats"]
+        return dict(newton=st["newton_iters"], gmres=st["gmres_iters"],
+                    cycles=st["gmres_cycles"], halvings=st["step_halvings"],
+                    source="oracle counts from tests/golden/noise%d.json" % size)
+    except Exception:
+        return None
+
+
+def extrapolate(t_pre, t_res, t_mv, counts):
+    # per Newton step: Simpson + theta (~ one matvec's FFT work at most) are folded into
+    # one extra matvec; residual evaluations = newton + halvings + 1
+    n_res = counts["newton"] + counts["halvings"] + 1
+    n_mv = counts["gmres"] + (counts["cycles"] - counts["newton"]) + counts["newton"]
+    return t_pre + n_res * t_res + n_mv * t_mv
+
+
+def cpu_cores():
+    return 1  # the oracle is single-threaded
+
+
+# ----------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import ot_inputs as I
+    f, g = I.noise_blob_pair(args.size, args.size, s=SEED)
+    counts = golden_counts(args.size) or dict(newton=36, gmres=164, cycles=36, halvings=0,
+                                              source="assumed counts")
+    for _ in range(args.warmup):
+        oracle_sample(f, g)
+    times = []
+    for _ in range(args.steps):
+        times.append(extrapolate(*oracle_sample(f, g), counts))
+    t = statistics.mean(times)
+    value = 1.0 / t
+    sample = ("per step: one oracle residual evaluation + one preconditioned matvec at "
+              "%dx%d, extrapolated to a solve with %d Newton steps / %d GMRES iterations (%s)"
+              % (args.size, args.size, counts["newton"], counts["gmres"], counts["source"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("mixed FP32-inner/FP64-outer",
+                                                    "FP64 CPU oracle"),
+                       "size": args.size},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    import ot_inputs as I
+    import paper_1009_6039_gb300 as ot
+
+    N = M = args.size
+    P = N * M
+    f, g = I.noise_blob_pair(N, M, s=SEED + 17 * rank)
+    fd = torch.from_numpy(f).cuda()
+    gd = torch.from_numpy(g).cuda()
+    phi = torch.zeros_like(fd)
+    stream = torch.cuda.current_stream()
+    plan = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", profile=1,
+                   stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        rc, st = plan.solve(fd, gd, phi)
+        if rc != ot.OT_OK:
+            raise RuntimeError("warm-up solve failed: %s" % st)
+    torch.cuda.synchronize()
+    plan.reset_profile()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            rc, st = plan.solve(fd, gd, phi)
+            ev[k][1].record(stream)
+            stats.append(st)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof, launches = plan.profile()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1000.0)
+    ok = all(s["status"] == 0 and s["res_inf"] < TOL for s in stats)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    fh = torch.from_numpy(f).pin_memory().numpy()
+    gh = torch.from_numpy(g).pin_memory().numpy()
+    ph = torch.zeros((N, M), dtype=torch.float64).pin_memory().numpy()
+    plan.set(profile=0)
+    e2e_ms = 0.0
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    for k in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st_h = plan.solve_host(fh, gh, ph)
+        e2e_ms += (time.perf_counter() - t0) * 1000.0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * e2e_steps / (e2e_ms / 1000.0)
+    phi_mixed = phi.clone()
+
+    # plain FP64 GPU path on the same pair (for the mixed-vs-FP64 comparison)
+    fp64 = None
+    if not args.no_fp64:
+        p64 = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="fp64", stream=stream)
+        phi64 = torch.zeros_like(fd)
+        p64.solve(fd, gd, phi64)
+        torch.cuda.synchronize()
+        steps64 = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps64):
+            rc64, st64 = p64.solve(fd, gd, phi64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / steps64
+        fp64 = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_solve": ms64,
+                "newton_iters": st64["newton_iters"], "gmres_iters": st64["gmres_iters"],
+                "res_inf": st64["res_inf"],
+                "phi_mixed_vs_fp64_inf": float((phi_mixed - phi64).abs().max().item())}
+        p64.close()
+
+    # roofline of the dominant kernel class
+    T = 4
+    s0 = stats[0]
+    avg_basis = (s0["gmres_iters"] / max(1, s0["gmres_cycles"]) + 1) / 2.0
+    dom = max((k for k in prof if algorithmic_bytes(k, P, T, avg_basis) is not None),
+              key=lambda k: prof[k][0])
+    dom_ms = prof[dom][0] / max(1, prof[dom][1])
+    bytes_launch = algorithmic_bytes(dom, P, T, avg_basis)
+    achieved = bytes_launch / (dom_ms / 1000.0) / 1e9
+    peak, peak_src = peaks()
+    total_prof_ms = sum(v[0] for v in prof.values())
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src + " hbm_gbs (copy)",
+            "traffic": traffic_for(dom, N), "algorithmic_bytes_per_launch": bytes_launch,
+            "avg_launch_ms": dom_ms,
+            "share_of_timed_kernels": prof[dom][0] / total_prof_ms if total_prof_ms else None}
+
+    # golden oracle samples of phi at this size (written by tests/golden/make_golden.py)
+    quality = {"res_inf_max": max(s["res_inf"] for s in stats),
+               "newton_iters": s0["newton_iters"], "gmres_iters": s0["gmres_iters"],
+               "step_halvings": s0["step_halvings"]}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "noise%d.json" % N)) as fh_:
+            gold = json.load(fh_)
+        ph_np = phi_mixed.cpu().numpy()
+        quality["phi_vs_oracle_samples_inf"] = float(np.abs(
+            ph_np[gold["sample_i"], gold["sample_j"]] - np.array(gold["phi_samples"])).max())
+    except Exception:
+        pass
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "M": M, "warm_start": "none (phi0 = 0)",
+                           "l2_flush": "256 MB write "
+                           "between timed steps", "parallelism": "replicas" if world > 1
+                           else "single GPU"},
+                "grid_point_newton_iters_per_s": value * P * s0["newton_iters"],
+                "all_converged": ok, "quality": quality, "fp64_gpu": fp64,
+                "e2e": {"value": e2e_value, "unit": "solves/s",
+                        "h2d_bytes_per_step": 2 * P * 8, "d2h_bytes_per_step": P * 8,
+                        "api": "ot_solve_host"},
+                "gpu_launches": int(launches), "roofline": roof,
+                "kernel_profile_ms": {k: round(v[0], 3) for k, v in prof.items()},
+                "kernel_profile_launches": {k: v[1] for k, v in prof.items()},
+                "clocks": clk.summary()}
+        if world == 1 and not args.no_cpu_baseline:
+            counts = golden_counts(N) or dict(
+                newton=s0["newton_iters"], gmres=s0["gmres_iters"],
+                cycles=s0["gmres_cycles"], halvings=s0["step_halvings"],
+                source="counts of the GPU FP64-outer solve of this pair")
+            t_pre, t_res, t_mv = oracle_sample(f, g)
+            t_cpu = extrapolate(t_pre, t_res, t_mv, counts)
+            line["cpu_baseline"] = {
+                "value": 1.0 / t_cpu, "unit": "solves/s", "cores": cpu_cores(),
+                "kind": "oracle",
+                "sample": ("one oracle residual evaluation (%.2fs) + one preconditioned matvec "
+                           "(%.2fs) + B-spline prefilter (%.2fs) at %dx%d, extrapolated to a "
+                           "solve with %d Newton steps / %d GMRES iterations (%s)"
+                           % (t_res, t_mv, t_pre, N, M, counts["newton"], counts["gmres"],
+                              counts["source"]))}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -57,6 +57,21 @@ extern "C" {
                                    0 (default): u0 = 0, the constant start of Thm 3.2 */
 #define OT_OPT_TAU 9            /* step-size parameter tau >= 1 (Eq. linma) */
 #define OT_OPT_TOL 10           /* Newton stop: max |f - f~_n| < tol */
+#define OT_OPT_PROFILE 11       /* 1: time every kernel launch with CUDA events on the
+                                   plan's stream, per class below (default 0) */
+
+/* Kernel classes of the profile (ot_plan_get_profile). */
+#define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */
+#define OT_PROF_ROW_R2C 1          /* row real-to-complex FFT pass (matvec and theta) */
+#define OT_PROF_COL_MATVEC 2       /* column FFT pass with the rho-bar and symbol multiplies */
+#define OT_PROF_ROW_C2R_COMBINE 3  /* row complex-to-real pass, coefficient apply */
+#define OT_PROF_COL_LBARINV 4      /* column pass of theta = Lbar^{-1} sigma */
+#define OT_PROF_ROW_C2R_UPDATE 5   /* row complex-to-real pass of theta, u += s theta */
+#define OT_PROF_GMRES_DOTS 6       /* Arnoldi multi-dot */
+#define OT_PROF_GMRES_UPDATE 7     /* Arnoldi update + norm + Givens */
+#define OT_PROF_GMRES_OTHER 8      /* GMRES init / restart residual / finish / combine */
+#define OT_PROF_OTHER 9            /* input translation, prefilter, final reductions */
+#define OT_PROF_CLASSES 10
 
 typedef struct ot_plan ot_plan;
 
@@ -67,7 +82,7 @@ typedef struct {
   int32_t gmres_iters;     /* Arnoldi steps, all Newton steps */
   int32_t gmres_cycles;    /* GMRES(m) cycles begun, all Newton steps */
   int32_t step_halvings;   /* safeguard rejections */
-  int32_t reserved;
+  int32_t kernel_launches; /* CUDA kernels launched by the call */
   double res_inf;          /* max |f - f~_n| at the returned phi */
   double res_l2;           /* sqrt(mean (f - f~_n)^2) at the returned phi */
   double min_det;          /* min det(I + D^2 phi) */
@@ -107,6 +122,15 @@ int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* 
 
 void ot_plan_destroy(ot_plan* plan);
 const char* ot_strerror(int status);
+
+/* Profile accumulated since the last reset: for each of the first n classes (n <=
+ * OT_PROF_CLASSES) the summed event time in ms and the number of timed launches (ms,
+ * launches may be NULL); *total_launches (may be NULL) counts every kernel launched by the
+ * plan, including the no-op launches of Arnoldi steps after GMRES converged (those are not
+ * timed).  Times are recorded only while OT_OPT_PROFILE is 1. */
+int ot_plan_get_profile(ot_plan* plan, double* ms, int64_t* launches, int32_t n,
+                        int64_t* total_launches);
+int ot_plan_reset_profile(ot_plan* plan);
 
 /* ---- Step-level entry points: one stage of a Newton step each, on device buffers ---- */
 

@@ -19,24 +19,27 @@ OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED
     0, -1, -2, -3, -4, -5, -6
 OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
-OT_OPT_TAU, OT_OPT_TOL = 9, 10
+OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE = 9, 10, 11
+PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
+                "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other"]
 
 EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_solve",
            "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
-           "ot_fft_forward", "ot_fft_inverse"]
+           "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
+           "ot_plan_reset_profile"]
 
 
 class ot_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("newton_iters", ctypes.c_int32),
                 ("gmres_iters", ctypes.c_int32), ("gmres_cycles", ctypes.c_int32),
-                ("step_halvings", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("step_halvings", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
                 ("min_det", ctypes.c_double), ("mean_fn", ctypes.c_double),
                 ("phi_mean", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class OTError(RuntimeError):
@@ -66,6 +69,8 @@ def _load():
         "ot_apply_lbar_inverse": ([vp, vp, vp, vp], ctypes.c_int),
         "ot_fft_forward": ([vp, vp, vp], ctypes.c_int),
         "ot_fft_inverse": ([vp, vp, vp], ctypes.c_int),
+        "ot_plan_get_profile": ([vp, vp, vp, i32, vp], ctypes.c_int),
+        "ot_plan_reset_profile": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -142,6 +147,14 @@ def ot_fft_inverse(plan, spec_ptr, x_ptr):
     return _lib.ot_fft_inverse(plan, spec_ptr, x_ptr)
 
 
+def ot_plan_get_profile(plan, ms_ptr, launches_ptr, n, total_ptr):
+    return _lib.ot_plan_get_profile(plan, ms_ptr, launches_ptr, int(n), total_ptr)
+
+
+def ot_plan_reset_profile(plan):
+    return _lib.ot_plan_reset_profile(plan)
+
+
 # ---- conveniences over torch tensors ---------------------------------------------------
 def _check(rc, where, ok=(OT_OK,)):
     if rc not in ok:
@@ -167,7 +180,8 @@ class Plan:
     _keys = {"restart": OT_OPT_RESTART, "eta": OT_OPT_ETA, "max_newton": OT_OPT_MAX_NEWTON,
              "max_restarts": OT_OPT_MAX_RESTARTS, "precision": OT_OPT_PRECISION,
              "safeguard": OT_OPT_SAFEGUARD, "translate": OT_OPT_TRANSLATE,
-             "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL}
+             "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL,
+             "profile": OT_OPT_PROFILE}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)
@@ -191,6 +205,32 @@ class Plan:
         rc = ot_solve(self.h, _dev(f, shp), _dev(g, shp), _dev(phi, shp), st)
         if rc in raise_on:
             raise OTError(rc, "ot_solve")
+        return rc, st.as_dict()
+
+    def profile(self):
+        """(per-class {name: (ms, launches)}, total kernel launches) since the last reset."""
+        import numpy as np
+        ms = np.zeros(len(PROF_CLASSES))
+        n = np.zeros(len(PROF_CLASSES), dtype=np.int64)
+        tot = np.zeros(1, dtype=np.int64)
+        _check(ot_plan_get_profile(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                   n.ctypes.data_as(ctypes.c_void_p), len(PROF_CLASSES),
+                                   tot.ctypes.data_as(ctypes.c_void_p)), "profile")
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}, int(tot[0])
+
+    def reset_profile(self):
+        _check(ot_plan_reset_profile(self.h), "reset_profile")
+
+    def solve_host(self, f, g, phi, raise_on=(OT_EINVAL, OT_ECUDA, OT_ENOMEM)):
+        """ot_solve_host on contiguous float64 numpy arrays (pinned or pageable)."""
+        st = ot_stats()
+        for a in (f, g, phi):
+            if a.dtype.name != "float64" or not a.flags.c_contiguous or a.shape != (self.N, self.M):
+                raise TypeError("expected contiguous float64 arrays of shape (N, M)")
+        vp = ctypes.c_void_p
+        rc = ot_solve_host(self.h, vp(f.ctypes.data), vp(g.ctypes.data), vp(phi.ctypes.data), st)
+        if rc in raise_on:
+            raise OTError(rc, "ot_solve_host")
         return rc, st.as_dict()
 
     def close(self):

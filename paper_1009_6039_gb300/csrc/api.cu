@@ -39,7 +39,67 @@ struct ot_plan {
   DevScalars* hsc = nullptr;  // pinned host mirror
   int kblocks = 0;
   bool ready = false;
+  // kernel launch count and per-class event timing (OT_OPT_PROFILE)
+  long long launches = 0;
+  int profile = 0;
+  struct Mark {
+    int cls, tag;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[OT_PROF_CLASSES] = {0};
+  long long prof_n[OT_PROF_CLASSES] = {0};
+  long long prof_skipped = 0;
 };
+
+static cudaEvent_t ev_get(ot_plan* p) {
+  if (!p->pool.empty()) {
+    cudaEvent_t e = p->pool.back();
+    p->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Accumulate the recorded marks (the stream has been synchronised).  Arnoldi-step marks
+// carry their step index j; those with j >= jend ran as no-op launches of a finished cycle
+// and are counted as skipped, not timed.
+static void prof_harvest(ot_plan* p, int jend) {
+  for (auto& mk : p->marks) {
+    if (mk.tag >= 0 && mk.tag >= jend) {
+      p->prof_skipped++;
+    } else {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, mk.a, mk.b);
+      p->prof_ms[mk.cls] += ms;
+      p->prof_n[mk.cls] += 1;
+    }
+    p->pool.push_back(mk.a);
+    p->pool.push_back(mk.b);
+  }
+  p->marks.clear();
+}
+
+// Launch wrapper: counts `nk` kernel launches; with profiling on, brackets them with events
+// on the plan's stream.
+#define LAUNCH(p, cls, tag, nk, expr)                                  \
+  do {                                                                 \
+    cudaEvent_t a_ = nullptr;                                          \
+    if ((p)->profile) {                                                \
+      a_ = ev_get(p);                                                  \
+      cudaEventRecord(a_, (p)->stream);                                \
+    }                                                                  \
+    CK(expr);                                                          \
+    (p)->launches += (nk);                                             \
+    if ((p)->profile) {                                                \
+      cudaEvent_t b_ = ev_get(p);                                      \
+      cudaEventRecord(b_, (p)->stream);                                \
+      (p)->marks.push_back({(cls), (tag), a_, b_});                     \
+    }                                                                  \
+  } while (0)
 
 static const char* kErr[] = {"ok", "invalid argument", "Newton did not converge",
                              "iterate lost convexity or became non-finite", "CUDA error",
@@ -75,6 +135,16 @@ bool fft_length_supported(int L) {
 static bool size_supported(int N, int M) {
   return N % 2 == 0 && M % 2 == 0 && M >= 16 && fft_length_supported(N) &&
          fft_length_supported(M / 2) && (M <= 2048);
+}
+
+static void free_events(ot_plan* p) {
+  for (auto& mk : p->marks) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  p->marks.clear();
+  for (auto e : p->pool) cudaEventDestroy(e);
+  p->pool.clear();
 }
 
 static void free_buffers(ot_plan* p) {
@@ -186,6 +256,7 @@ extern "C" int ot_plan_create(ot_plan** out, int32_t N, int32_t M, double tau, d
 
 extern "C" void ot_plan_destroy(ot_plan* p) {
   if (!p) return;
+  free_events(p);
   free_buffers(p);
   delete p;
 }
@@ -248,8 +319,34 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (!(v > 0.0)) return OT_EINVAL;
       p->tol = v;
       return OT_OK;
+    case OT_OPT_PROFILE:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->profile = (int)v;
+      return OT_OK;
   }
   return OT_EINVAL;
+}
+
+extern "C" int ot_plan_get_profile(ot_plan* p, double* ms, int64_t* launches, int32_t n,
+                                   int64_t* total_launches) {
+  if (!p || n < 0) return OT_EINVAL;
+  for (int k = 0; k < n && k < OT_PROF_CLASSES; ++k) {
+    if (ms) ms[k] = p->prof_ms[k];
+    if (launches) launches[k] = p->prof_n[k];
+  }
+  if (total_launches) *total_launches = p->launches;
+  return OT_OK;
+}
+
+extern "C" int ot_plan_reset_profile(ot_plan* p) {
+  if (!p) return OT_EINVAL;
+  for (int k = 0; k < OT_PROF_CLASSES; ++k) {
+    p->prof_ms[k] = 0.0;
+    p->prof_n[k] = 0;
+  }
+  p->prof_skipped = 0;
+  p->launches = 0;
+  return OT_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -259,62 +356,75 @@ template <typename T> static const SpecTables& tables(ot_plan* p);
 template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
 template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
 
-static cudaError_t read_scalars(ot_plan* p) {
-  cudaError_t e = cudaMemcpyAsync(p->hsc, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost,
-                                  p->stream);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(p->stream);
+static int read_scalars(ot_plan* p) {
+  CK(cudaMemcpyAsync(p->hsc, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  if (p->profile) prof_harvest(p, p->hsc->jend);
+  return OT_OK;
 }
 
+#define RET(x)                  \
+  do {                          \
+    int r_ = (x);               \
+    if (r_ != OT_OK) return r_; \
+  } while (0)
+
 // c = B-spline coefficients of g, in FP64 (prefilter by the symbol (2 + cos)/3 per axis)
-static cudaError_t run_prefilter(ot_plan* p, const double* g, double* c) {
+static int run_prefilter(ot_plan* p, const double* g, double* c) {
   C2<double>* sp = (C2<double>*)(p->precision ? p->spec64 : p->spec);
   C2<double>* qq = (C2<double>*)(p->precision ? p->q64 : p->q0);
-  cudaError_t e;
-  e = launch_row_r2c<double>(g, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
-                             p->stream);
-  if (e != cudaSuccess) return e;
-  e = launch_col<double>(COL_PREFILTER, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64, nullptr,
-                         nullptr, p->stream);
-  if (e != cudaSuccess) return e;
-  return launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
-                                nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream);
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_row_r2c<double>(g, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
+                                p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_col<double>(COL_PREFILTER, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64,
+                            nullptr, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
+                                nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream));
+  return OT_OK;
 }
 
 // w = L Lbar^{-1} x, x = V + (*jptr) P scaled by scale[*jptr] when jptr is given
 template <typename T>
-static cudaError_t run_matvec(ot_plan* p, const T* x, const int* jptr, const double* scale,
-                              T* w, const int* skip) {
+static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* scale, T* w,
+                      const int* skip, int tag) {
   const size_t P = (size_t)p->N * p->M;
   const SpecTables& tb = tables<T>(p);
-  cudaError_t e;
-  e = launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip, p->stream);
-  if (e != cudaSuccess) return e;
-  e = launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
-                    p->N, p->M, tb, p->sc, skip, p->stream);
-  if (e != cudaSuccess) return e;
-  return launch_row_c2r<T>(ROWINV_COMBINE, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
+  LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
+         launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip,
+                           p->stream));
+  LAUNCH(p, OT_PROF_COL_MATVEC, tag, 1,
+         launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1,
+                       (C2<T>*)p->q2, p->N, p->M, tb, p->sc, skip, p->stream));
+  LAUNCH(p, OT_PROF_ROW_C2R_COMBINE, tag, 1,
+         launch_row_c2r<T>(ROWINV_COMBINE, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
                            (const T*)p->coef, w, nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb,
-                           skip, p->stream);
+                           skip, p->stream));
+  return OT_OK;
 }
 
 // u_out = u_in + step * Lbar^{-1} sigma  (UPDATE) or out = Lbar^{-1} sigma (PLAIN)
 template <typename T>
-static cudaError_t run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* u_out,
-                                double step, T* out) {
+static int run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* u_out,
+                        double step, T* out) {
   const SpecTables& tb = tables<T>(p);
-  cudaError_t e;
-  e = launch_row_r2c<T>(sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, p->N, p->M, tb, nullptr,
-                        p->stream);
-  if (e != cudaSuccess) return e;
-  e = launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N, p->M,
-                    tb, p->sc, nullptr, p->stream);
-  if (e != cudaSuccess) return e;
-  if (out)
-    return launch_row_c2r<T>(ROWINV_PLAIN, (C2<T>*)p->q0, nullptr, nullptr, nullptr, out,
-                             nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb, nullptr, p->stream);
-  return launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
-                           u_in, u_out, step, 1.0, p->N, p->M, tb, nullptr, p->stream);
+  LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+         launch_row_r2c<T>(sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, p->N, p->M, tb,
+                           nullptr, p->stream));
+  LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+         launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N,
+                       p->M, tb, p->sc, nullptr, p->stream));
+  if (out) {
+    LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+           launch_row_c2r<T>(ROWINV_PLAIN, (C2<T>*)p->q0, nullptr, nullptr, nullptr, out,
+                             nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb, nullptr, p->stream));
+  } else {
+    LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+           launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
+                             u_in, u_out, step, 1.0, p->N, p->M, tb, nullptr, p->stream));
+  }
+  return OT_OK;
 }
 
 // GMRES(m) on L Lbar^{-1} sigma = (f - f~_n)/tau, sigma from 0.  Host syncs once per cycle.
@@ -326,20 +436,26 @@ static int run_gmres(ot_plan* p) {
   T* sigma = (T*)p->sigma;
   const int* skip = &p->sc->cycle_done;
   CK(cudaMemsetAsync(sigma, 0, P * sizeof(T), p->stream));
-  CK(launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+         launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
   for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
     for (int j = 0; j < p->m; ++j) {
-      CK(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip));
-      CK(launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
-      CK(launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+      RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j));
+      LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
+             launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+      LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+             launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
     }
-    CK(launch_gmres_finish(p->sc, p->stream));
-    CK(launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
-    CK(read_scalars(p));
+    LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
+    LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+           launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
+    RET(read_scalars(p));
     if (p->hsc->converged || cyc + 1 == p->max_restarts) break;
     // explicit residual for the restart: V0 = h - A sigma
-    CK(run_matvec<T>(p, sigma, nullptr, nullptr, w, nullptr));
-    CK(launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks, p->stream));
+    RET(run_matvec<T>(p, sigma, nullptr, nullptr, w, nullptr, -1));
+    LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+           launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks,
+                                p->stream));
   }
   return OT_OK;
 }
@@ -357,6 +473,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   ot_stats local;
   if (!st) st = &local;
   memset(st, 0, sizeof(*st));
+  const long long launches0 = p->launches;
   const int N = p->N, M = p->M;
   const long P = (long)N * M;
   cudaEvent_t ev0, ev1;
@@ -366,8 +483,10 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   set_solver_scalars(p);
   CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
   if (p->translate) {
-    CK(launch_translate_inputs(f_in, g_in, p->f, p->g, N, M, p->partials, p->sc, p->stream));
-    CK(read_scalars(p));
+    LAUNCH(p, OT_PROF_OTHER, -1, 2,
+           launch_translate_inputs(f_in, g_in, p->f, p->g, N, M, p->partials, p->sc,
+                                   p->stream));
+    RET(read_scalars(p));
     if (p->hsc->in_bad) {
       st->status = OT_EINVAL;
       cudaEventDestroy(ev0);
@@ -378,15 +497,16 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
     if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   }
-  CK(run_prefilter(p, p->g, p->c));
+  RET(run_prefilter(p, p->g, p->c));
   if (p->warm_start) {
     if (phi != p->u) CK(cudaMemcpyAsync(p->u, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   } else {
     CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
   }
-  CK(launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
-                        p->stream));
-  CK(read_scalars(p));
+  LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
+                            p->stream));
+  RET(read_scalars(p));
   int status = OT_OK;
   double s = 1.0;
   for (int n = 0;; ++n) {
@@ -409,10 +529,11 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     st->gmres_cycles += p->hsc->cycles;
     bool accepted = false;
     for (;;) {
-      CK(run_lbar_inv<T>(p, (const T*)p->sigma, p->u, p->ucand, s, nullptr));
-      CK(launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef, p->partials,
-                            p->sc, p->stream));
-      CK(read_scalars(p));
+      RET(run_lbar_inv<T>(p, (const T*)p->sigma, p->u, p->ucand, s, nullptr));
+      LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+             launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef,
+                                p->partials, p->sc, p->stream));
+      RET(read_scalars(p));
       if (!p->safeguard || p->hsc->admissible || s < 0x1p-30) {
         accepted = true;
         break;
@@ -429,17 +550,20 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   }
   // final l2 residual, mean-zero gauge (Sec. 3.1), result
   if (status != OT_EDIVERGED || p->hsc->k1_nonfinite == 0) {
-    CK(launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
   }
-  CK(launch_subtract_mean(p->u, N, M, p->partials, p->sc, p->dmean, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 2,
+         launch_subtract_mean(p->u, N, M, p->partials, p->sc, p->dmean, p->stream));
   if (phi != p->u) CK(cudaMemcpyAsync(phi, p->u, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   CK(cudaMemcpyAsync(&st->phi_mean, p->dmean, 8, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaEventRecord(ev1, p->stream));
-  CK(read_scalars(p));
+  RET(read_scalars(p));
   st->res_l2 = sqrt(p->hsc->res_l2sum / (double)P);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   st->ms_total = ms;
+  st->kernel_launches = (int32_t)(p->launches - launches0);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   st->status = status;
@@ -487,7 +611,7 @@ extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const doub
 extern "C" int ot_prefilter(ot_plan* p, const double* g, double* c) {
   if (!p || !g || !c) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
-  CK(run_prefilter(p, g, c));
+  RET(run_prefilter(p, g, c));
   CK(cudaStreamSynchronize(p->stream));
   return OT_OK;
 }
@@ -499,11 +623,16 @@ static int eval_residual_impl(ot_plan* p, const double* f, const double* c, cons
   const long P = (long)N * M;
   set_solver_scalars(p);
   CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
-  CK(launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream));
-  CK(launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
-  if (F) CK(launch_shifted_residual(p->Fraw, F, N, M, p->sc, p->stream));
-  if (coef) CK(launch_convert<T>(p->coef, sizeof(T) == 8, coef, 1, 5 * P, p->stream));
-  CK(read_scalars(p));
+  LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+         launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
+                            p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+  if (F) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_shifted_residual(p->Fraw, F, N, M, p->sc, p->stream));
+  if (coef)
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_convert<T>(p->coef, sizeof(T) == 8, coef, 1, 5 * P, p->stream));
+  RET(read_scalars(p));
   if (scal) {
     const DevScalars* h = p->hsc;
     scal[0] = h->mean_fn;
@@ -539,7 +668,7 @@ static int apply_op_impl(ot_plan* p, const double* coef, const double* abar,
   if (rc) return rc;
   CK(launch_convert<T>(coef, 1, p->coef, sizeof(T) == 8, 5 * P, p->stream));
   CK(launch_convert<T>(sigma, 1, p->sigma, sizeof(T) == 8, P, p->stream));
-  CK(run_matvec<T>(p, (const T*)p->sigma, nullptr, nullptr, (T*)p->w, nullptr));
+  RET(run_matvec<T>(p, (const T*)p->sigma, nullptr, nullptr, (T*)p->w, nullptr, -1));
   CK(launch_convert<T>(p->w, sizeof(T) == 8, w, 1, P, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return OT_OK;
@@ -559,7 +688,7 @@ static int lbar_impl(ot_plan* p, const double* abar, const double* sigma, double
   int rc = upload_abar(p, abar);
   if (rc) return rc;
   CK(launch_convert<T>(sigma, 1, p->sigma, sizeof(T) == 8, P, p->stream));
-  CK(run_lbar_inv<T>(p, (const T*)p->sigma, nullptr, nullptr, 0.0, (T*)p->w));
+  RET(run_lbar_inv<T>(p, (const T*)p->sigma, nullptr, nullptr, 0.0, (T*)p->w));
   CK(launch_convert<T>(p->w, sizeof(T) == 8, theta, 1, P, p->stream));
   CK(cudaStreamSynchronize(p->stream));
   return OT_OK;
