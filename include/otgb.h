@@ -58,7 +58,13 @@ extern "C" {
 #define OT_OPT_TAU 9            /* step-size parameter tau >= 1 (Eq. linma) */
 #define OT_OPT_TOL 10           /* Newton stop: max |f - f~_n| < tol */
 #define OT_OPT_PROFILE 11       /* 1: time every kernel launch with CUDA events on the
-                                   plan's stream, per class below (default 0) */
+                                   plan's stream, per class below (default 0); forces the
+                                   host-driven solve (OT_OPT_GRAPH is ignored meanwhile) */
+#define OT_OPT_GRAPH 12         /* 1 (default): run the whole solve as one CUDA graph whose
+                                   Newton, GMRES-cycle, Arnoldi-step and step-halving loops
+                                   are conditional nodes driven by device-side tests (no host
+                                   round trip until the end); 0: host-driven loop that
+                                   synchronises once per GMRES cycle and per Newton step */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */
@@ -131,6 +137,13 @@ const char* ot_strerror(int status);
 int ot_plan_get_profile(ot_plan* plan, double* ms, int64_t* launches, int32_t n,
                         int64_t* total_launches);
 int ot_plan_reset_profile(ot_plan* plan);
+
+/* Steady-state duration of one kernel class (OT_PROF_RESIDUAL .. OT_PROF_GMRES_DOTS; the
+ * multi-dot is timed at Arnoldi step j = 2): after a solve, relaunches that kernel `reps`
+ * times back to back on the plan's own buffers (overwriting workspace only: the residual,
+ * spectra, w, the candidate iterate and the device scalars) between two CUDA events on the
+ * plan's stream; *ms receives the mean time per launch. */
+int ot_plan_time_kernel(ot_plan* plan, int32_t kernel_class, int32_t reps, double* ms);
 
 /* ---- Step-level entry points: one stage of a Newton step each, on device buffers ---- */
 

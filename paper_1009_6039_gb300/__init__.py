@@ -19,7 +19,7 @@ OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED
     0, -1, -2, -3, -4, -5, -6
 OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
-OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE = 9, 10, 11
+OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH = 9, 10, 11, 12
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other"]
 
@@ -27,7 +27,7 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_sol
            "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
            "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
-           "ot_plan_reset_profile"]
+           "ot_plan_reset_profile", "ot_plan_time_kernel"]
 
 
 class ot_stats(ctypes.Structure):
@@ -71,6 +71,7 @@ def _load():
         "ot_fft_inverse": ([vp, vp, vp], ctypes.c_int),
         "ot_plan_get_profile": ([vp, vp, vp, i32, vp], ctypes.c_int),
         "ot_plan_reset_profile": ([vp], ctypes.c_int),
+        "ot_plan_time_kernel": ([vp, i32, i32, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -155,6 +156,10 @@ def ot_plan_reset_profile(plan):
     return _lib.ot_plan_reset_profile(plan)
 
 
+def ot_plan_time_kernel(plan, kernel_class, reps, ms_ptr):
+    return _lib.ot_plan_time_kernel(plan, int(kernel_class), int(reps), ms_ptr)
+
+
 # ---- conveniences over torch tensors ---------------------------------------------------
 def _check(rc, where, ok=(OT_OK,)):
     if rc not in ok:
@@ -181,7 +186,7 @@ class Plan:
              "max_restarts": OT_OPT_MAX_RESTARTS, "precision": OT_OPT_PRECISION,
              "safeguard": OT_OPT_SAFEGUARD, "translate": OT_OPT_TRANSLATE,
              "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL,
-             "profile": OT_OPT_PROFILE}
+             "profile": OT_OPT_PROFILE, "graph": OT_OPT_GRAPH}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)
@@ -217,6 +222,13 @@ class Plan:
                                    n.ctypes.data_as(ctypes.c_void_p), len(PROF_CLASSES),
                                    tot.ctypes.data_as(ctypes.c_void_p)), "profile")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}, int(tot[0])
+
+    def time_kernel(self, name, reps=50):
+        """Mean ms per launch of one kernel class, relaunched back to back after a solve."""
+        ms = ctypes.c_double()
+        _check(ot_plan_time_kernel(self.h, PROF_CLASSES.index(name), reps, ctypes.byref(ms)),
+               "time_kernel")
+        return ms.value
 
     def reset_profile(self):
         _check(ot_plan_reset_profile(self.h), "reset_profile")

@@ -1,6 +1,7 @@
 // C ABI of libotgb: plans, the damped-Newton driver (Sec. 3.1, Eq. linma) with Strain's
 // FFT-preconditioned GMRES(m) (Sec. 4.2), and the step-level entry points.
 #include <math.h>
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -51,7 +52,23 @@ struct ot_plan {
   double prof_ms[OT_PROF_CLASSES] = {0};
   long long prof_n[OT_PROF_CLASSES] = {0};
   long long prof_skipped = 0;
+  // graph-launched solve (OT_OPT_GRAPH): captured once per (precision, m, translate)
+  int use_graph = 1;
+  double* uout = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
+  int gkey_prec = -1, gkey_m = -1, gkey_translate = -1;
+  unsigned long long h_newton = 0, h_cycle = 0, h_restart = 0, h_halve = 0;
+  unsigned long long h_step[OTGB_MAXM] = {0};
+  int top_kernels = 0;
+  double* gu_a = nullptr;  // iterate buffers as captured (upar = 0 names gu_a)
+  double* gu_b = nullptr;
 };
+
+template <typename T> static const SpecTables& tables(ot_plan* p);
+template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
+template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
 
 static cudaEvent_t ev_get(ot_plan* p) {
   if (!p->pool.empty()) {
@@ -147,7 +164,18 @@ static void free_events(ot_plan* p) {
   p->pool.clear();
 }
 
+static void free_graph(ot_plan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->gexec = nullptr;
+  p->graph = nullptr;
+  p->gkey_prec = p->gkey_m = p->gkey_translate = -1;
+}
+
 static void free_buffers(ot_plan* p) {
+  free_graph(p);
+  if (p->uout) cudaFree(p->uout);
+  p->uout = nullptr;
   void* ptrs[] = {p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
                   p->tw32, p->partials, p->dmean, p->sc};
@@ -183,6 +211,7 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaMalloc(&p->u, P * 8));
   CK(cudaMalloc(&p->ucand, P * 8));
   CK(cudaMalloc(&p->Fraw, P * 8));
+  CK(cudaMalloc(&p->uout, P * 8));
   CK(cudaMalloc(&p->coef, 5 * P * ts));
   CK(cudaMalloc(&p->V, (size_t)(p->m + 1) * P * ts));
   CK(cudaMalloc(&p->w, P * ts));
@@ -258,6 +287,8 @@ extern "C" void ot_plan_destroy(ot_plan* p) {
   if (!p) return;
   free_events(p);
   free_buffers(p);
+  for (int k = 0; k < 4; ++k)
+    if (p->cs[k]) cudaStreamDestroy(p->cs[k]);
   delete p;
 }
 
@@ -323,6 +354,10 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (v != 0 && v != 1) return OT_EINVAL;
       p->profile = (int)v;
       return OT_OK;
+    case OT_OPT_GRAPH:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->use_graph = (int)v;
+      return OT_OK;
   }
   return OT_EINVAL;
 }
@@ -336,6 +371,71 @@ extern "C" int ot_plan_get_profile(ot_plan* p, double* ms, int64_t* launches, in
   }
   if (total_launches) *total_launches = p->launches;
   return OT_OK;
+}
+
+template <typename T>
+static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch) {
+  const SpecTables& tb = tables<T>(p);
+  const int N = p->N, M = p->M;
+  const size_t P = (size_t)N * M;
+  auto one = [&]() -> cudaError_t {
+    switch (cls) {
+      case OT_PROF_RESIDUAL:
+        return launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials,
+                                  p->sc, p->stream);
+      case OT_PROF_ROW_R2C:
+        return launch_row_r2c<T>((const T*)p->V, P, nullptr, nullptr, (C2<T>*)p->spec, N, M,
+                                 tb, nullptr, p->stream);
+      case OT_PROF_COL_MATVEC:
+        return launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1,
+                             (C2<T>*)p->q2, N, M, tb, p->sc, nullptr, p->stream);
+      case OT_PROF_ROW_C2R_COMBINE:
+        return launch_row_c2r<T>(ROWINV_COMBINE, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
+                                 (const T*)p->coef, (T*)p->w, nullptr, nullptr, 0.0, 1.0, N, M,
+                                 tb, nullptr, p->stream);
+      case OT_PROF_COL_LBARINV:
+        return launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N,
+                             M, tb, p->sc, nullptr, p->stream);
+      case OT_PROF_ROW_C2R_UPDATE:
+        return launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr,
+                                 nullptr, p->u, p->ucand, 0.5, 1.0, N, M, tb, nullptr,
+                                 p->stream);
+      case OT_PROF_GMRES_DOTS:
+        return launch_gmres_dots<T>((const T*)p->V, (const T*)p->w, (long)P, p->partials,
+                                    p->sc, p->kblocks, p->stream);
+    }
+    return cudaErrorInvalidValue;
+  };
+  if (cls == OT_PROF_GMRES_DOTS) {
+    // a representative Arnoldi step: j = 2 (three basis vectors), cycle open
+    int jv[2] = {p->m > 2 ? 2 : p->m - 1, 0};
+    CK(cudaMemcpyAsync((char*)p->sc + offsetof(DevScalars, j), &jv[0], sizeof(int),
+                       cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync((char*)p->sc + offsetof(DevScalars, cycle_done), &jv[1], sizeof(int),
+                       cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  CK(one());  // warm
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, p->stream));
+  for (int r = 0; r < reps; ++r) CK(one());
+  CK(cudaEventRecord(b, p->stream));
+  CK(cudaEventSynchronize(b));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_per_launch = ms / reps;
+  return OT_OK;
+}
+
+extern "C" int ot_plan_time_kernel(ot_plan* p, int32_t cls, int32_t reps, double* ms) {
+  if (!p || !ms || reps < 1 || cls < 0 || cls > OT_PROF_GMRES_DOTS) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? time_kernel_impl<float>(p, cls, reps, ms)
+                      : time_kernel_impl<double>(p, cls, reps, ms);
 }
 
 extern "C" int ot_plan_reset_profile(ot_plan* p) {
@@ -352,9 +452,6 @@ extern "C" int ot_plan_reset_profile(ot_plan* p) {
 // ------------------------------------------------------------------------------------------
 // pipelines
 // ------------------------------------------------------------------------------------------
-template <typename T> static const SpecTables& tables(ot_plan* p);
-template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
-template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
 
 static int read_scalars(ot_plan* p) {
   CK(cudaMemcpyAsync(p->hsc, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p->stream));
@@ -465,6 +562,11 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->m = p->m;
   p->hsc->eta = p->eta;
   p->hsc->tau = p->tau;
+  p->hsc->tol = p->tol;
+  p->hsc->step_s = 1.0;
+  p->hsc->safeguard = p->safeguard;
+  p->hsc->max_newton = p->max_newton;
+  p->hsc->max_restarts = p->max_restarts;
 }
 
 template <typename T>
@@ -570,10 +672,246 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   return status;
 }
 
+// ------------------------------------------------------------------------------------------
+// Graph-launched solve: the same sequence as solve_impl, captured once.  The Newton loop,
+// the GMRES cycle loop, each Arnoldi step and the step-halving loop are conditional nodes
+// whose handles are set by the device-side control kernel (k_ctl) and by the Arnoldi update.
+// ------------------------------------------------------------------------------------------
+
+// Add a conditional node after the current capture frontier of stream s; *body receives its
+// body graph and *h its handle (created in the graph being captured on s).
+static int add_conditional(cudaStream_t s, cudaGraphConditionalNodeType type,
+                           unsigned long long* h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, &ed, &nd));
+  if (cst != cudaStreamCaptureStatusActive) return OT_ECUDA;
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, g, 0, 0));
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = hc;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+  CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                         cudaStreamSetCaptureDependencies));
+  *h = (unsigned long long)hc;
+  *body = cp.conditional.phGraph_out[0];
+  return OT_OK;
+}
+
+static int begin_body(ot_plan* p, int level, cudaGraph_t body) {
+  CK(cudaStreamBeginCaptureToGraph(p->cs[level], body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeRelaxed));
+  p->stream = p->cs[level];
+  return OT_OK;
+}
+
+static int end_body(ot_plan* p, int level) {
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamEndCapture(p->cs[level], &out));
+  p->stream = p->cs[level - 1];
+  return OT_OK;
+}
+
+// theta = Lbar^{-1} sigma, candidate u_(1-upar) = u_upar + s theta (s, upar from the device),
+// residual at the candidate, accept/halve
+template <typename T>
+static int capture_candidate(ot_plan* p) {
+  const SpecTables& tb = tables<T>(p);
+  const int N = p->N, M = p->M;
+  LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+         launch_row_r2c<T>((const T*)p->sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, N, M, tb,
+                           nullptr, p->stream));
+  LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+         launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N, M,
+                       tb, p->sc, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+         launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
+                           p->u, p->ucand, 1.0, 1.0, N, M, tb, nullptr, p->stream, p->sc));
+  LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
+                            p->stream, p->ucand, 1));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
+  return OT_OK;
+}
+
+template <typename T>
+static int capture_solve(ot_plan* p) {
+  const int N = p->N, M = p->M;
+  const long P = (long)N * M;
+  T* V = (T*)p->V;
+  T* w = (T*)p->w;
+  T* sigma = (T*)p->sigma;
+  long long k0 = p->launches;
+  if (p->translate)
+    LAUNCH(p, OT_PROF_OTHER, -1, 2,
+           launch_translate_inputs(p->f, p->g, p->f, p->g, N, M, p->partials, p->sc,
+                                   p->stream));
+  RET(run_prefilter(p, p->g, p->c));
+  LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
+                            p->stream, p->ucand, 0));
+  const int top = (int)(p->launches - k0) + 1;
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, top));
+  cudaGraph_t b1, b2, b3, b4, b5;
+  // ---- Newton loop
+  RET(add_conditional(p->cs[0], cudaGraphCondTypeWhile, &p->h_newton, &b1));
+  RET(begin_body(p, 1, b1));
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+         launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream,
+                              sigma));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_PRE_CYCLE, p->sc, p->stream, 2));
+  // ---- GMRES cycles
+  RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_cycle, &b2));
+  RET(begin_body(p, 2, b2));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream, 1));
+  for (int j = 0; j < p->m; ++j) {
+    RET(add_conditional(p->cs[2], cudaGraphCondTypeIf, &p->h_step[j], &b3));
+    RET(begin_body(p, 3, b3));
+    RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, nullptr, j));
+    LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
+           launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+    RET(end_body(p, 3));
+  }
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+         launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_END, p->sc, p->stream, 3));
+  RET(add_conditional(p->cs[2], cudaGraphCondTypeIf, &p->h_restart, &b4));
+  RET(begin_body(p, 3, b4));
+  RET(run_matvec<T>(p, sigma, nullptr, nullptr, w, nullptr, -1));
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+         launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks, p->stream));
+  RET(end_body(p, 3));
+  RET(end_body(p, 2));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_GMRES_DONE, p->sc, p->stream, 1));
+  // ---- candidate, then halve while inadmissible
+  RET(capture_candidate<T>(p));
+  RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_halve, &b5));
+  RET(begin_body(p, 2, b5));
+  RET(capture_candidate<T>(p));
+  RET(end_body(p, 2));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, 1));
+  RET(end_body(p, 1));
+  // ---- final residual norm and mean-zero gauge
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+  UPair up{p->u, p->ucand};
+  LAUNCH(p, OT_PROF_OTHER, -1, 2,
+         launch_final_gauge(up, p->uout, N, M, p->partials, p->sc, p->dmean, p->stream));
+  p->top_kernels = 3;  // residual_l2 + gauge (2), counted on the host
+  return OT_OK;
+}
+
+template <typename T>
+static int build_graph(ot_plan* p) {
+  free_graph(p);
+  for (int k = 0; k < 4; ++k)
+    if (!p->cs[k]) CK(cudaStreamCreateWithFlags(&p->cs[k], cudaStreamNonBlocking));
+  cudaStream_t saved = p->stream;
+  const int saved_prof = p->profile;
+  const long long saved_launches = p->launches;
+  p->profile = 0;
+  p->stream = p->cs[0];
+  CK(cudaStreamBeginCapture(p->cs[0], cudaStreamCaptureModeRelaxed));
+  int rc = capture_solve<T>(p);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->cs[0], &g);
+  p->stream = saved;
+  p->profile = saved_prof;
+  p->launches = saved_launches;
+  if (rc != OT_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != OT_OK ? rc : OT_ECUDA;
+  }
+  p->graph = g;
+  e = cudaGraphInstantiate(&p->gexec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    p->graph = nullptr;
+    p->gexec = nullptr;
+    return OT_ECUDA;
+  }
+  p->gkey_prec = p->precision;
+  p->gkey_m = p->m;
+  p->gkey_translate = p->translate;
+  p->gu_a = p->u;
+  p->gu_b = p->ucand;
+  return OT_OK;
+}
+
+template <typename T>
+static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
+                            ot_stats* st) {
+  ot_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  const long P = (long)p->N * p->M;
+  if (!p->gexec || p->gkey_prec != p->precision || p->gkey_m != p->m ||
+      p->gkey_translate != p->translate)
+    RET(build_graph<T>(p));
+  double* ua = p->gu_a;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, p->stream));
+  if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  if (p->warm_start) {
+    if (phi != ua) CK(cudaMemcpyAsync(ua, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    CK(cudaMemsetAsync(ua, 0, P * 8, p->stream));
+  }
+  set_solver_scalars(p);
+  DevScalars* h = p->hsc;
+  h->graph = 1;
+  h->h_newton = p->h_newton;
+  h->h_cycle = p->h_cycle;
+  h->h_restart = p->h_restart;
+  h->h_halve = p->h_halve;
+  for (int k = 0; k < OTGB_MAXM; ++k) h->h_step[k] = p->h_step[k];
+  CK(cudaMemcpyAsync(p->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaGraphLaunch(p->gexec, p->stream));
+  if (phi != p->uout)
+    CK(cudaMemcpyAsync(phi, p->uout, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  CK(cudaMemcpyAsync(&st->phi_mean, p->dmean, 8, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaEventRecord(ev1, p->stream));
+  RET(read_scalars(p));
+  h = p->hsc;
+  st->status = h->status;
+  st->newton_iters = h->newton_n;
+  st->gmres_iters = h->gmres_iters_total;
+  st->gmres_cycles = h->gmres_cycles_total;
+  st->step_halvings = h->halvings;
+  st->res_inf = h->res_inf;
+  st->min_det = h->min_det;
+  st->mean_fn = h->mean_fn;
+  st->res_l2 = sqrt(h->res_l2sum / (double)P);
+  st->kernel_launches = (int32_t)(h->kcount + p->top_kernels);
+  p->launches += h->kcount + p->top_kernels;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  st->ms_total = ms;
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return st->status;
+}
+
 extern "C" int ot_solve(ot_plan* p, const double* f, const double* g, double* phi,
                         ot_stats* st) {
   if (!p || !f || !g || !phi || !p->ready) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
+  if (p->use_graph && !p->profile)
+    return p->precision ? solve_graph_impl<float>(p, f, g, phi, st)
+                        : solve_graph_impl<double>(p, f, g, phi, st);
   return p->precision ? solve_impl<float>(p, f, g, phi, st) : solve_impl<double>(p, f, g, phi, st);
 }
 
@@ -585,11 +923,21 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
   // stage f, g in the plan's translated-density buffers (translated in place)
   CK(cudaMemcpyAsync(p->f, f, bytes, cudaMemcpyHostToDevice, p->stream));
   CK(cudaMemcpyAsync(p->g, g, bytes, cudaMemcpyHostToDevice, p->stream));
-  if (p->warm_start) CK(cudaMemcpyAsync(p->u, phi, bytes, cudaMemcpyHostToDevice, p->stream));
-  int rc = p->precision ? solve_impl<float>(p, p->f, p->g, p->u, st)
-                        : solve_impl<double>(p, p->f, p->g, p->u, st);
-  if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
-  CK(cudaMemcpyAsync(phi, p->u, bytes, cudaMemcpyDeviceToHost, p->stream));
+  const bool graph = p->use_graph && !p->profile;
+  if (p->warm_start)
+    CK(cudaMemcpyAsync(graph ? p->uout : p->u, phi, bytes, cudaMemcpyHostToDevice, p->stream));
+  int rc;
+  if (graph) {
+    rc = p->precision ? solve_graph_impl<float>(p, p->f, p->g, p->uout, st)
+                      : solve_graph_impl<double>(p, p->f, p->g, p->uout, st);
+    if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
+    CK(cudaMemcpyAsync(phi, p->uout, bytes, cudaMemcpyDeviceToHost, p->stream));
+  } else {
+    rc = p->precision ? solve_impl<float>(p, p->f, p->g, p->u, st)
+                      : solve_impl<double>(p, p->f, p->g, p->u, st);
+    if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
+    CK(cudaMemcpyAsync(phi, p->u, bytes, cudaMemcpyDeviceToHost, p->stream));
+  }
   CK(cudaStreamSynchronize(p->stream));
   return rc;
 }

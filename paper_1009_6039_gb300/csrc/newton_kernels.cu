@@ -11,7 +11,8 @@
 namespace otgb {
 
 #define RTX 32  // residual tile width (x / columns)
-#define RTY 8   // residual tile height (y / rows)
+#define RTY 32  // residual tile height (y / rows); 8 warps, 4 rows per thread
+#define RPT 4   // rows per thread
 
 // ---------------------------------------------------------------------------------------
 // block reductions
@@ -160,91 +161,165 @@ cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft
 }
 
 // ---------------------------------------------------------------------------------------
-// Residual + coefficients (K1).  One thread per grid point of a 32 x 8 tile; u is staged
-// in shared memory with a periodic halo of 2 for the 4th-order centred stencils.
+// Residual + coefficients (K1).  A block covers a 32 x 32 tile (each thread 4 points, one
+// column); u is staged in shared memory with a periodic halo of 2 for the 4th-order
+// centred stencils.  GB300's FP64 rate is low, so the kernel avoids FP64 divisions (all
+// reciprocal factors come in as arguments), integer divisions in the inner code, and in the
+// mixed mode evaluates the gradient of the interpolant (which enters only the Jacobian, not
+// the residual) in FP32.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int wrapi(int a, int L) {
   int r = a % L;
   return r < 0 ? r + L : r;
 }
 
-__device__ __forceinline__ void bspline_w(double t, double w[4], double dw[4]) {
+__device__ __forceinline__ int wrap_near(int a, int L) {  // a in [-L, 2L)
+  return a < 0 ? a + L : (a >= L ? a - L : a);
+}
+
+struct ResidConsts {
+  double Mh, Nh, Mh2, Nh2;  // M/12, N/12, M^2/12, N^2/12
+  double w3M, w3N;          // 1/(3M), 1/(3N): Simpson weights (2 or 4) x these
+};
+
+template <typename G>
+__device__ __forceinline__ void bspline_w(G t, G w[4], G dw[4]) {
+  const G s = (G)1 - t;
+  const G t2 = t * t, t3 = t2 * t;
+  const G sixth = (G)(1.0 / 6.0);
+  w[0] = s * s * s * sixth;
+  w[1] = ((G)3 * t3 - (G)6 * t2 + (G)4) * sixth;
+  w[2] = ((G)-3 * t3 + (G)3 * t2 + (G)3 * t + (G)1) * sixth;
+  w[3] = t3 * sixth;
+  dw[0] = (G)-0.5 * s * s;
+  dw[1] = (G)0.5 * ((G)3 * t2 - (G)4 * t);
+  dw[2] = (G)0.5 * ((G)-3 * t2 + (G)2 * t + (G)1);
+  dw[3] = (G)0.5 * t2;
+}
+
+__device__ __forceinline__ void bspline_v(double t, double w[4]) {
   const double s = 1.0 - t;
-  w[0] = s * s * s * (1.0 / 6.0);
-  w[1] = (3.0 * t * t * t - 6.0 * t * t + 4.0) * (1.0 / 6.0);
-  w[2] = (-3.0 * t * t * t + 3.0 * t * t + 3.0 * t + 1.0) * (1.0 / 6.0);
-  w[3] = t * t * t * (1.0 / 6.0);
-  dw[0] = -0.5 * s * s;
-  dw[1] = 0.5 * (3.0 * t * t - 4.0 * t);
-  dw[2] = 0.5 * (-3.0 * t * t + 2.0 * t + 1.0);
-  dw[3] = 0.5 * t * t;
+  const double t2 = t * t, t3 = t2 * t;
+  const double sixth = 1.0 / 6.0;
+  w[0] = s * s * s * sixth;
+  w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) * sixth;
+  w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) * sixth;
+  w[3] = t3 * sixth;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RTX* RTY)
+__global__ void __launch_bounds__(RTX * RTY / RPT)
     k_residual(const double* __restrict__ f, const double* __restrict__ c,
-               const double* __restrict__ u, int N, int M, double* __restrict__ Fraw,
-               T* __restrict__ coef, double* partials, DevScalars* sc) {
+               const double* __restrict__ ua, const double* __restrict__ ub, int sel, int N,
+               int M, ResidConsts K, double* __restrict__ Fraw, T* __restrict__ coef,
+               double* partials, DevScalars* sc) {
   __shared__ double tile[RTY + 4][RTX + 4];
+  const double* __restrict__ u = (ub && ((sc->upar ^ sel) & 1)) ? ub : ua;
   const int bx = blockIdx.x * RTX, by = blockIdx.y * RTY;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < (RTY + 4) * (RTX + 4); idx += RTX * RTY) {
-    const int r = idx / (RTX + 4), cc = idx % (RTX + 4);
-    tile[r][cc] = u[(size_t)wrapi(by + r - 2, N) * M + wrapi(bx + cc - 2, M)];
+  for (int idx = tid; idx < (RTY + 4) * (RTX + 4); idx += blockDim.x) {
+    const int r = idx / (RTX + 4), cc = idx - r * (RTX + 4);
+    int gi = by + r - 2, gj = bx + cc - 2;
+    while (gi < 0) gi += N;
+    while (gi >= N) gi -= N;
+    while (gj < 0) gj += M;
+    while (gj >= M) gj -= M;
+    tile[r][cc] = u[(size_t)gi * M + gj];
   }
   __syncthreads();
-  const int tx = tid % RTX, ty = tid / RTX;
-  const int i = by + ty, j = bx + tx;
-  const bool valid = (i < N) && (j < M);
   // partials: sum fn, Simpson sums of a11 a12 a22 b1 b2, max Fraw, min Fraw, min det,
   // non-finite count
   double v[10] = {0, 0, 0, 0, 0, 0, -INFINITY, INFINITY, INFINITY, 0};
   const int kind[10] = {0, 0, 0, 0, 0, 0, 1, 2, 2, 0};
-  if (valid) {
+  const int tx = tid % RTX, ty0 = tid / RTX;
+  const int j = bx + tx;
+  const size_t P = (size_t)N * M;
+  const double wx = ((j & 1) ? 4.0 : 2.0) * K.w3M;
+#pragma unroll 1
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int ty = ty0 + rr * (RTY / RPT);
+    const int i = by + ty;
+    if (i >= N || j >= M) continue;
     const int r = ty + 2, q = tx + 2;
-    const double Mh = (double)M / 12.0, Nh = (double)N / 12.0;
-    const double Mh2 = (double)M * (double)M / 12.0, Nh2 = (double)N * (double)N / 12.0;
     const double ux =
-        (-tile[r][q + 2] + 8.0 * tile[r][q + 1] - 8.0 * tile[r][q - 1] + tile[r][q - 2]) * Mh;
+        (-tile[r][q + 2] + 8.0 * tile[r][q + 1] - 8.0 * tile[r][q - 1] + tile[r][q - 2]) * K.Mh;
     const double uy =
-        (-tile[r + 2][q] + 8.0 * tile[r + 1][q] - 8.0 * tile[r - 1][q] + tile[r - 2][q]) * Nh;
+        (-tile[r + 2][q] + 8.0 * tile[r + 1][q] - 8.0 * tile[r - 1][q] + tile[r - 2][q]) * K.Nh;
     const double uxx = (-tile[r][q + 2] + 16.0 * tile[r][q + 1] - 30.0 * tile[r][q] +
-                        16.0 * tile[r][q - 1] - tile[r][q - 2]) * Mh2;
+                        16.0 * tile[r][q - 1] - tile[r][q - 2]) * K.Mh2;
     const double uyy = (-tile[r + 2][q] + 16.0 * tile[r + 1][q] - 30.0 * tile[r][q] +
-                        16.0 * tile[r - 1][q] - tile[r - 2][q]) * Nh2;
+                        16.0 * tile[r - 1][q] - tile[r - 2][q]) * K.Nh2;
     double dyc[5];
 #pragma unroll
     for (int a = -2; a <= 2; ++a)
-      dyc[a + 2] = (-tile[r + 2][q + a] + 8.0 * tile[r + 1][q + a] -
-                    8.0 * tile[r - 1][q + a] + tile[r - 2][q + a]) * Nh;
-    const double uxy = (-dyc[4] + 8.0 * dyc[3] - 8.0 * dyc[1] + dyc[0]) * Mh;
+      dyc[a + 2] = -tile[r + 2][q + a] + 8.0 * tile[r + 1][q + a] -
+                   8.0 * tile[r - 1][q + a] + tile[r - 2][q + a];
+    const double uxy = (-dyc[4] + 8.0 * dyc[3] - 8.0 * dyc[1] + dyc[0]) * (K.Mh * K.Nh);
     // g at the displaced point x + grad u, in grid units, periodic cubic B-spline
     const double gxp = (double)j + (double)M * ux, gyp = (double)i + (double)N * uy;
     const double fj = floor(gxp), fi = floor(gyp);
-    double wx[4], dwx[4], wy[4], dwy[4];
-    bspline_w(gxp - fj, wx, dwx);
-    bspline_w(gyp - fi, wy, dwy);
-    const int j0 = (int)fj, i0 = (int)fi;
-    int jj[4];
+    const double tx_ = gxp - fj, ty_ = gyp - fi;
+    const int j0 = wrapi((int)fj, M), i0 = wrapi((int)fi, N);
+    int jj[4], ii[4];
+    jj[0] = j0 == 0 ? M - 1 : j0 - 1;
+    jj[1] = j0;
+    jj[2] = wrap_near(j0 + 1, M);
+    jj[3] = wrap_near(j0 + 2, M);
+    ii[0] = i0 == 0 ? N - 1 : i0 - 1;
+    ii[1] = i0;
+    ii[2] = wrap_near(i0 + 1, N);
+    ii[3] = wrap_near(i0 + 2, N);
+    double G = 0.0, Gx, Gy;
+    if (sizeof(T) == 8) {
+      double wxv[4], dwx[4], wyv[4], dwy[4];
+      bspline_w<double>(tx_, wxv, dwx);
+      bspline_w<double>(ty_, wyv, dwy);
+      double gx = 0.0, gy = 0.0;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) jj[a] = wrapi(j0 + a - 1, M);
-    double G = 0.0, Gx = 0.0, Gy = 0.0;
+      for (int b = 0; b < 4; ++b) {
+        const double* crow = c + (size_t)ii[b] * M;
+        double sv = 0.0, sd = 0.0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const double* crow = c + (size_t)wrapi(i0 + b - 1, N) * M;
-      double sv = 0.0, sd = 0.0;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const double cv = __ldg(crow + jj[a]);
-        sv += cv * wx[a];
-        sd += cv * dwx[a];
+        for (int a = 0; a < 4; ++a) {
+          const double cv = __ldg(crow + jj[a]);
+          sv += cv * wxv[a];
+          sd += cv * dwx[a];
+        }
+        G += sv * wyv[b];
+        gx += sd * wyv[b];
+        gy += sv * dwy[b];
       }
-      G += sv * wy[b];
-      Gx += sd * wy[b];
-      Gy += sv * dwy[b];
+      Gx = gx * (double)M;
+      Gy = gy * (double)N;
+    } else {
+      // value in FP64 (it enters the residual), gradient in FP32 (Jacobian only)
+      double wxv[4], wyv[4];
+      bspline_v(tx_, wxv);
+      bspline_v(ty_, wyv);
+      float wxf[4], dwx[4], wyf[4], dwy[4];
+      bspline_w<float>((float)tx_, wxf, dwx);
+      bspline_w<float>((float)ty_, wyf, dwy);
+      float gx = 0.f, gy = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const double* crow = c + (size_t)ii[b] * M;
+        double sv = 0.0;
+        float svf = 0.f, sdf = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const double cv = __ldg(crow + jj[a]);
+          sv += cv * wxv[a];
+          const float cf = (float)cv;
+          svf += cf * wxf[a];
+          sdf += cf * dwx[a];
+        }
+        G += sv * wyv[b];
+        gx += sdf * wyf[b];
+        gy += svf * dwy[b];
+      }
+      Gx = (double)(gx * (float)M);
+      Gy = (double)(gy * (float)N);
     }
-    Gx *= (double)M;
-    Gy *= (double)N;
     const double det = (1.0 + uxx) * (1.0 + uyy) - uxy * uxy;
     const double fn = G * det;
     const size_t p = (size_t)i * M + j;
@@ -252,33 +327,34 @@ __global__ void __launch_bounds__(RTX* RTY)
     Fraw[p] = fr;
     const double a11 = G * (1.0 + uyy), a12 = -G * uxy, a22 = G * (1.0 + uxx);
     const double b1 = det * Gx, b2 = det * Gy;
-    const size_t P = (size_t)N * M;
     coef[p] = (T)a11;
     coef[P + p] = (T)a12;
     coef[2 * P + p] = (T)a22;
     coef[3 * P + p] = (T)b1;
     coef[4 * P + p] = (T)b2;
-    const double w = ((i & 1) ? 4.0 : 2.0) / (3.0 * (double)N) * ((j & 1) ? 4.0 : 2.0) /
-                     (3.0 * (double)M);
+    const double w = ((i & 1) ? 4.0 : 2.0) * K.w3N * wx;
     const bool fin = isfinite(fn);
-    v[0] = fin ? fn : 0.0;
-    v[1] = w * a11;
-    v[2] = w * a12;
-    v[3] = w * a22;
-    v[4] = w * b1;
-    v[5] = w * b2;
-    v[6] = fin ? fr : -INFINITY;
-    v[7] = fin ? fr : INFINITY;
-    v[8] = det;
-    v[9] = fin ? 0.0 : 1.0;
+    v[0] += fin ? fn : 0.0;
+    v[1] += w * a11;
+    v[2] += w * a12;
+    v[3] += w * a22;
+    v[4] += w * b1;
+    v[5] += w * b2;
+    if (fin) {
+      v[6] = fmax(v[6], fr);
+      v[7] = fmin(v[7], fr);
+    } else {
+      v[9] += 1.0;
+    }
+    v[8] = fmin(v[8], det);
   }
   block_reduce<10>(v, kind);
   if (!publish_partials<10>(v, partials, &sc->ticket[TK_RESID])) return;
   const unsigned int nb = gridDim.x * gridDim.y;
   reduce_partials<10>(v, kind, partials, nb);
   if (threadIdx.x == 0) {
-    const double P = (double)N * (double)M;
-    const double mean_fn = v[0] / P;
+    const double Pd = (double)N * (double)M;
+    const double mean_fn = v[0] / Pd;
     const double shift = mean_fn - 1.0;
     sc->mean_fn = mean_fn;
     sc->shift = shift;
@@ -296,11 +372,19 @@ int residual_partial_blocks(int N, int M) {
 }
 
 template <typename T>
-cudaError_t launch_residual(const double* f, const double* c, const double* u, int N, int M,
+cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
-                            cudaStream_t st) {
+                            cudaStream_t st, const double* ub, int sel) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
-  k_residual<T><<<grid, RTX * RTY, 0, st>>>(f, c, u, N, M, Fraw, coef, partials, sc);
+  ResidConsts K;
+  K.Mh = (double)M / 12.0;
+  K.Nh = (double)N / 12.0;
+  K.Mh2 = (double)M * (double)M / 12.0;
+  K.Nh2 = (double)N * (double)N / 12.0;
+  K.w3M = 1.0 / (3.0 * (double)M);
+  K.w3N = 1.0 / (3.0 * (double)N);
+  k_residual<T><<<grid, RTX * RTY / RPT, 0, st>>>(f, c, ua, ub, sel, N, M, K, Fraw, coef,
+                                                  partials, sc);
   return cudaGetLastError();
 }
 
@@ -387,18 +471,21 @@ cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevS
 template <typename T>
 __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restrict__ w,
                              T* __restrict__ V0, long P, int restart, double* partials,
-                             DevScalars* sc) {
+                             DevScalars* sc, T* __restrict__ sigma) {
   const double s = sc->shift, inv_tau = 1.0 / sc->tau;
   double v[1] = {0.0};
   const int kind[1] = {0};
+  T acc = (T)0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
+    if (sigma) sigma[p] = (T)0;
     double b = (Fraw[p] + s) * inv_tau;  // h = (f - f~_n) / tau
     if (restart) b -= (double)w[p];
     const T bt = (T)b;
     V0[p] = bt;
-    v[0] += (double)bt * (double)bt;
+    acc += bt * bt;
   }
+  v[0] = (double)acc;
   block_reduce<1>(v, kind);
   if (!publish_partials<1>(v, partials, &sc->ticket[TK_INIT])) return;
   reduce_partials<1>(v, kind, partials, gridDim.x);
@@ -426,56 +513,73 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
   }
 }
 
-template <typename T>
-__global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, long P,
-                             double* partials, DevScalars* sc) {
-  if (sc->cycle_done) return;
-  const int j = sc->j;
-  double v[OTGB_MAXM];
-  int kind[OTGB_MAXM];
+// Per-thread partial sums are kept in the vector precision T (a thread covers only
+// P / (2 x SMs x 256) elements); partials are combined across threads and blocks in FP64.
+template <typename T, int J>
+__device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restrict__ w, long P,
+                                       double* partials, DevScalars* sc) {
+  T acc[J];
 #pragma unroll
-  for (int i = 0; i < OTGB_MAXM; ++i) {
-    v[i] = 0.0;
-    kind[i] = 0;
-  }
+  for (int i = 0; i < J; ++i) acc[i] = (T)0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
-    const double wp = (double)w[p];
+    const T wp = w[p];
 #pragma unroll
-    for (int i = 0; i < OTGB_MAXM; ++i)
-      if (i <= j) v[i] += (double)V[(size_t)i * P + p] * wp;
+    for (int i = 0; i < J; ++i) acc[i] += V[(size_t)i * P + p] * wp;
   }
-  block_reduce<OTGB_MAXM>(v, kind);
-  if (!publish_partials<OTGB_MAXM>(v, partials, &sc->ticket[TK_DOTS])) return;
-  reduce_partials<OTGB_MAXM>(v, kind, partials, gridDim.x);
+  double v[J];
+  int kind[J];
+#pragma unroll
+  for (int i = 0; i < J; ++i) {
+    v[i] = (double)acc[i];
+    kind[i] = 0;
+  }
+  block_reduce<J>(v, kind);
+  if (!publish_partials<J>(v, partials, &sc->ticket[TK_DOTS])) return;
+  reduce_partials<J>(v, kind, partials, gridDim.x);
   if (threadIdx.x == 0) {
-    const int m = sc->m;
-    for (int i = 0; i <= j; ++i) sc->H[i * m + j] = sc->scale[i] * v[i];
+    const int m = sc->m, j = J - 1;
+#pragma unroll
+    for (int i = 0; i < J; ++i) sc->H[i * m + j] = sc->scale[i] * v[i];
     sc->ticket[TK_DOTS] = 0;
   }
 }
 
 template <typename T>
-__global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long P,
-                               double* partials, DevScalars* sc) {
+__global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, long P,
+                             double* partials, DevScalars* sc) {
   if (sc->cycle_done) return;
-  const int j = sc->j, m = sc->m;
-  double coefs[OTGB_MAXM];
+  switch (sc->j) {
+#define OTGB_DOTS_CASE(k) \
+  case k:                 \
+    dots_j<T, k + 1>(V, w, P, partials, sc); break;
+    OTGB_DOTS_CASE(0) OTGB_DOTS_CASE(1) OTGB_DOTS_CASE(2) OTGB_DOTS_CASE(3)
+    OTGB_DOTS_CASE(4) OTGB_DOTS_CASE(5) OTGB_DOTS_CASE(6) OTGB_DOTS_CASE(7)
+    OTGB_DOTS_CASE(8) OTGB_DOTS_CASE(9) OTGB_DOTS_CASE(10) OTGB_DOTS_CASE(11)
+    OTGB_DOTS_CASE(12) OTGB_DOTS_CASE(13) OTGB_DOTS_CASE(14)
+#undef OTGB_DOTS_CASE
+  }
+}
+
+template <typename T, int J>
+__device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict__ w, long P,
+                                         double* partials, DevScalars* sc) {
+  const int j = J - 1, m = sc->m;
+  T coefs[J];
 #pragma unroll
-  for (int i = 0; i < OTGB_MAXM; ++i) coefs[i] = (i <= j) ? sc->H[i * m + j] * sc->scale[i] : 0.0;
+  for (int i = 0; i < J; ++i) coefs[i] = (T)(sc->H[i * m + j] * sc->scale[i]);
   T* Vn = V + (size_t)(j + 1) * P;
-  double v[1] = {0.0};
-  const int kind[1] = {0};
+  T acc = (T)0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
-    double x = (double)w[p];
+    T x = w[p];
 #pragma unroll
-    for (int i = 0; i < OTGB_MAXM; ++i)
-      if (i <= j) x -= coefs[i] * (double)V[(size_t)i * P + p];
-    const T xt = (T)x;
-    Vn[p] = xt;
-    v[0] += (double)xt * (double)xt;
+    for (int i = 0; i < J; ++i) x -= coefs[i] * V[(size_t)i * P + p];
+    Vn[p] = x;
+    acc += x * x;
   }
+  double v[1] = {(double)acc};
+  const int kind[1] = {0};
   block_reduce<1>(v, kind);
   if (!publish_partials<1>(v, partials, &sc->ticket[TK_UPDATE])) return;
   reduce_partials<1>(v, kind, partials, gridDim.x);
@@ -507,7 +611,24 @@ __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long 
       if (j + 1 == m) sc->cycle_done = 1;
     }
     sc->j = j + 1;
+    if (sc->graph && j + 1 < m) cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
     sc->ticket[TK_UPDATE] = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long P,
+                               double* partials, DevScalars* sc) {
+  if (sc->cycle_done) return;
+  switch (sc->j) {
+#define OTGB_UPD_CASE(k) \
+  case k:                \
+    update_j<T, k + 1>(V, w, P, partials, sc); break;
+    OTGB_UPD_CASE(0) OTGB_UPD_CASE(1) OTGB_UPD_CASE(2) OTGB_UPD_CASE(3)
+    OTGB_UPD_CASE(4) OTGB_UPD_CASE(5) OTGB_UPD_CASE(6) OTGB_UPD_CASE(7)
+    OTGB_UPD_CASE(8) OTGB_UPD_CASE(9) OTGB_UPD_CASE(10) OTGB_UPD_CASE(11)
+    OTGB_UPD_CASE(12) OTGB_UPD_CASE(13) OTGB_UPD_CASE(14)
+#undef OTGB_UPD_CASE
   }
 }
 
@@ -528,28 +649,42 @@ cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st) {
 }
 
 // sigma += sum_i y_i scale_i V_i
+template <typename T, int J>
+__device__ __forceinline__ void combine_j(const T* __restrict__ V, T* __restrict__ sigma, long P,
+                                          const DevScalars* __restrict__ sc) {
+  T coefs[J];
+#pragma unroll
+  for (int i = 0; i < J; ++i) coefs[i] = (T)(sc->y[i] * sc->scale[i]);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x) {
+    T x = sigma[p];
+#pragma unroll
+    for (int i = 0; i < J; ++i) x += coefs[i] * V[(size_t)i * P + p];
+    sigma[p] = x;
+  }
+}
+
 template <typename T>
 __global__ void k_gmres_combine(const T* __restrict__ V, T* __restrict__ sigma, long P,
                                 const DevScalars* __restrict__ sc) {
-  const int n = sc->jend;
-  if (n == 0) return;
-  double coefs[OTGB_MAXM];
-#pragma unroll
-  for (int i = 0; i < OTGB_MAXM; ++i) coefs[i] = (i < n) ? sc->y[i] * sc->scale[i] : 0.0;
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
-       p += (long)gridDim.x * blockDim.x) {
-    double x = (double)sigma[p];
-#pragma unroll
-    for (int i = 0; i < OTGB_MAXM; ++i)
-      if (i < n) x += coefs[i] * (double)V[(size_t)i * P + p];
-    sigma[p] = (T)x;
+  switch (sc->jend) {
+#define OTGB_CMB_CASE(k) \
+  case k:                \
+    combine_j<T, k>(V, sigma, P, sc); break;
+    OTGB_CMB_CASE(1) OTGB_CMB_CASE(2) OTGB_CMB_CASE(3) OTGB_CMB_CASE(4)
+    OTGB_CMB_CASE(5) OTGB_CMB_CASE(6) OTGB_CMB_CASE(7) OTGB_CMB_CASE(8)
+    OTGB_CMB_CASE(9) OTGB_CMB_CASE(10) OTGB_CMB_CASE(11) OTGB_CMB_CASE(12)
+    OTGB_CMB_CASE(13) OTGB_CMB_CASE(14) OTGB_CMB_CASE(15)
+#undef OTGB_CMB_CASE
+    default: break;
   }
 }
 
 template <typename T>
 cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
-                              double* partials, DevScalars* sc, int nblocks, cudaStream_t st) {
-  k_gmres_init<T><<<nblocks, 256, 0, st>>>(Fraw, w, V0, P, restart, partials, sc);
+                              double* partials, DevScalars* sc, int nblocks, cudaStream_t st,
+                              T* sigma) {
+  k_gmres_init<T><<<nblocks, 256, 0, st>>>(Fraw, w, V0, P, restart, partials, sc, sigma);
   return cudaGetLastError();
 }
 template <typename T>
@@ -568,6 +703,116 @@ template <typename T>
 cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,
                                  int nblocks, cudaStream_t st) {
   k_gmres_combine<T><<<nblocks, 256, 0, st>>>(V, sigma, P, sc);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Device-resident Newton control (Eq. linma with the convexity safeguard), one thread.
+// Mirrors the host loop: stop tests before each solve, step halving on an inadmissible
+// candidate, s doubled (capped at 1) after an accepted step.
+// ---------------------------------------------------------------------------------------
+#define OT_STATUS_OK 0
+#define OT_STATUS_EINVAL (-1)
+#define OT_STATUS_ENOCONV (-2)
+#define OT_STATUS_EDIVERGED (-3)
+
+__device__ __forceinline__ void set_cond(const DevScalars* sc, unsigned long long h,
+                                         unsigned int v) {
+  if (sc->graph && h) cudaGraphSetConditional(h, v);
+}
+
+__global__ void k_ctl(int op, DevScalars* sc, int add) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  sc->kcount += add;
+  switch (op) {
+    case CTL_NEWTON: {
+      int cont = 0;
+      if (sc->in_bad) {
+        sc->status = OT_STATUS_EINVAL;
+      } else if (!sc->admissible) {
+        sc->status = OT_STATUS_EDIVERGED;
+      } else if (sc->res_inf < sc->tol) {
+        sc->status = OT_STATUS_OK;
+      } else if (sc->newton_n >= sc->max_newton) {
+        sc->status = OT_STATUS_ENOCONV;
+      } else {
+        sc->status = OT_STATUS_OK;
+        cont = 1;
+      }
+      set_cond(sc, sc->h_newton, cont);
+      break;
+    }
+    case CTL_ACCEPT: {
+      const double s = sc->step_s;
+      if (!sc->safeguard || sc->admissible || s < 0x1p-30) {
+        sc->upar ^= 1;
+        sc->newton_n += 1;
+        sc->step_s = (2.0 * s < 1.0) ? 2.0 * s : 1.0;
+        set_cond(sc, sc->h_halve, 0);
+      } else {
+        sc->step_s = 0.5 * s;
+        sc->halvings += 1;
+        set_cond(sc, sc->h_halve, 1);
+      }
+      break;
+    }
+    case CTL_PRE_CYCLE:
+      set_cond(sc, sc->h_cycle, sc->converged ? 0u : 1u);
+      break;
+    case CTL_CYCLE_BEGIN:
+      for (int k = 1; k < sc->m; ++k) set_cond(sc, sc->h_step[k], 0);
+      set_cond(sc, sc->h_step[0], sc->converged ? 0u : 1u);
+      break;
+    case CTL_CYCLE_END: {
+      const int cont = (!sc->converged && sc->cycles < sc->max_restarts) ? 1 : 0;
+      set_cond(sc, sc->h_cycle, cont);
+      set_cond(sc, sc->h_restart, cont);
+      if (cont) sc->kcount += 4;  // restart residual: 3 matvec passes + init
+      break;
+    }
+    case CTL_GMRES_DONE:
+      sc->kcount += 5LL * sc->iters;  // Arnoldi steps: 3 matvec passes + dots + update
+      sc->gmres_iters_total += sc->iters;
+      sc->gmres_cycles_total += sc->cycles;
+      break;
+  }
+}
+
+cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add) {
+  k_ctl<<<1, 32, 0, st>>>(op, sc, add);
+  return cudaGetLastError();
+}
+
+__global__ void k_sum_sel(UPair up, long P, double* partials, DevScalars* sc, double* mean_out) {
+  const double* __restrict__ u = (sc->upar & 1) ? up.b : up.a;
+  double v[1] = {0.0};
+  const int kind[1] = {0};
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    v[0] += u[p];
+  block_reduce<1>(v, kind);
+  if (!publish_partials<1>(v, partials, &sc->ticket[TK_NORM])) return;
+  reduce_partials<1>(v, kind, partials, gridDim.x);
+  if (threadIdx.x == 0) {
+    *mean_out = v[0] / (double)P;
+    sc->ticket[TK_NORM] = 0;
+  }
+}
+
+__global__ void k_sub_sel(UPair up, double* __restrict__ out, long P,
+                          const DevScalars* __restrict__ sc, const double* __restrict__ mean) {
+  const double* __restrict__ u = (sc->upar & 1) ? up.b : up.a;
+  const double m = *mean;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    out[p] = u[p] - m;
+}
+
+cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
+                               DevScalars* sc, double* mean_out, cudaStream_t st) {
+  const int nb = reduce_blocks();
+  k_sum_sel<<<nb, 256, 0, st>>>(u, (long)N * M, partials, sc, mean_out);
+  k_sub_sel<<<nb, 256, 0, st>>>(u, out, (long)N * M, sc, mean_out);
   return cudaGetLastError();
 }
 
@@ -596,9 +841,9 @@ cudaError_t launch_convert(const void* in, int in_d, void* out, int out_d, long 
 #define OTGB_INST_NEWTON(T)                                                                   \
   template cudaError_t launch_residual<T>(const double*, const double*, const double*, int,   \
                                           int, double*, T*, double*, DevScalars*,             \
-                                          cudaStream_t);                                      \
+                                          cudaStream_t, const double*, int);                  \
   template cudaError_t launch_gmres_init<T>(const double*, const T*, T*, long, int, double*,  \
-                                            DevScalars*, int, cudaStream_t);                  \
+                                            DevScalars*, int, cudaStream_t, T*);              \
   template cudaError_t launch_gmres_dots<T>(const T*, const T*, long, double*, DevScalars*,   \
                                             int, cudaStream_t);                               \
   template cudaError_t launch_gmres_update<T>(T*, const T*, long, double*, DevScalars*, int,  \

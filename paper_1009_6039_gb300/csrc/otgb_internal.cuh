@@ -37,8 +37,31 @@ struct DevScalars {
   double relres;
   int j, jend, m, cycle_done, converged, iters, cycles;
   double eta, tau;
+  // Newton control, resident on the device for the graph-launched solve
+  double tol, step_s;
+  int newton_n, halvings, status, upar, safeguard, max_newton, max_restarts;
+  int gmres_iters_total, gmres_cycles_total, graph;
+  long long kcount;  // kernels executed by the graph-launched solve
+  // conditional-node handles of the captured solve (0 outside a graph)
+  unsigned long long h_newton, h_cycle, h_restart, h_halve, h_step[OTGB_MAXM];
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
+};
+
+// Control operations of the device-resident Newton loop (k_ctl)
+enum CtlOp {
+  CTL_NEWTON = 0,       // set status; continue while admissible, res >= tol, n < max
+  CTL_ACCEPT = 1,       // accept the candidate (flip upar, n++, s = min(1, 2s)) or halve s
+  CTL_PRE_CYCLE = 2,    // enter the GMRES cycle loop unless already converged
+  CTL_CYCLE_BEGIN = 3,  // arm Arnoldi step 0, disarm the others
+  CTL_CYCLE_END = 4,    // another cycle (with a restart residual) unless converged / capped
+  CTL_GMRES_DONE = 5    // accumulate the GMRES counters of this Newton step
+};
+
+// The two buffers of the iterate u; `upar` in DevScalars names the current one.
+struct UPair {
+  double* a;
+  double* b;
 };
 
 enum { TK_INPUT = 0, TK_RESID = 1, TK_DOTS = 2, TK_UPDATE = 3, TK_INIT = 4, TK_NORM = 5 };
@@ -67,28 +90,36 @@ template <typename T>
 cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double out_scale, int N, int M, const SpecTables& tb,
-                           const int* skip, cudaStream_t st);
+                           const int* skip, cudaStream_t st, const DevScalars* sc = nullptr);
 
 // Residual / coefficients, input translation ------------------------------------------
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st);
+// u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate)
 template <typename T>
-cudaError_t launch_residual(const double* f, const double* c, const double* u, int N, int M,
+cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
-                            cudaStream_t st);
+                            cudaStream_t st, const double* ub = nullptr, int sel = 0);
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
                                DevScalars* sc, cudaStream_t st);
 cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
                                     const DevScalars* sc, cudaStream_t st);
 cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevScalars* sc,
                                  double* mean_out, cudaStream_t st);
+// out = u[upar] - mean(u[upar])
+cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
+                               DevScalars* sc, double* mean_out, cudaStream_t st);
+// `add`: kernels of the graph segment this control op closes (launch accounting)
+cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add = 0);
 int residual_partial_blocks(int N, int M);
 
 // Krylov kernels -------------------------------------------------------------------------
+// restart 0: V0 = h (and sigma = 0 when sigma is given); 1: V0 = h - w
 template <typename T>
 cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
-                              double* partials, DevScalars* sc, int nblocks, cudaStream_t st);
+                              double* partials, DevScalars* sc, int nblocks, cudaStream_t st,
+                              T* sigma = nullptr);
 template <typename T>
 cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
                               int nblocks, cudaStream_t st);

@@ -412,8 +412,17 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
                           T* __restrict__ out, const double* __restrict__ u_in,
                           double* __restrict__ u_out, double step, double out_scale, int N,
                           int M, const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
-                          const int* __restrict__ skip) {
+                          const int* __restrict__ skip, const DevScalars* __restrict__ sc) {
   if (skip && *skip) return;
+  if (MODE == ROWINV_UPDATE && sc) {
+    // device-resident control: step s and the current/candidate buffers come from sc
+    step = sc->step_s;
+    if (sc->upar & 1) {
+      double* t = const_cast<double*>(u_in);
+      u_in = u_out;
+      u_out = t;
+    }
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
   const int L = M / 2;
@@ -542,7 +551,8 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
 template <typename T, int E, int MODE>
 cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T* coef, T* out,
                       const double* u_in, double* u_out, double step, double out_scale, int N,
-                      int M, const SpecTables& tb, const int* skip, cudaStream_t st) {
+                      int M, const SpecTables& tb, const int* skip, cudaStream_t st,
+                      const DevScalars* sc) {
   const int L = M / 2, TPT = L / E;
   int RB = MaxThreads<T>::value / TPT;
   if (RB < 1) RB = 1;
@@ -552,7 +562,7 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   if (e != cudaSuccess) return e;
   k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, u_in, u_out, step, out_scale, N, M, (const C2<T>*)tb.twL,
-      (const C2<T>*)tb.twM, skip);
+      (const C2<T>*)tb.twM, skip, sc);
   return cudaGetLastError();
 }
 
@@ -591,17 +601,17 @@ template <typename T, int E>
 cudaError_t row_c2r_dispatch(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                              const T* coef, T* out, const double* u_in, double* u_out,
                              double step, double os, int N, int M, const SpecTables& tb,
-                             const int* skip, cudaStream_t st) {
+                             const int* skip, cudaStream_t st, const DevScalars* sc) {
   switch (mode) {
     case ROWINV_PLAIN:
       return row_c2r_E<T, E, ROWINV_PLAIN>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
-                                           tb, skip, st);
+                                           tb, skip, st, sc);
     case ROWINV_COMBINE:
       return row_c2r_E<T, E, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N,
-                                             M, tb, skip, st);
+                                             M, tb, skip, st, sc);
     case ROWINV_UPDATE:
       return row_c2r_E<T, E, ROWINV_UPDATE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
-                                            tb, skip, st);
+                                            tb, skip, st, sc);
   }
   return cudaErrorInvalidValue;
 }
@@ -610,12 +620,12 @@ template <typename T>
 cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double os, int N, int M, const SpecTables& tb,
-                           const int* skip, cudaStream_t st) {
+                           const int* skip, cudaStream_t st, const DevScalars* sc) {
   if (fft_E(M / 2) == 12)
     return row_c2r_dispatch<T, 12>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
-                                   tb, skip, st);
+                                   tb, skip, st, sc);
   return row_c2r_dispatch<T, 8>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M, tb,
-                                skip, st);
+                                skip, st, sc);
 }
 
 #define OTGB_INSTANTIATE_SPECTRAL(T)                                                         \
@@ -628,6 +638,6 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
   template cudaError_t launch_row_c2r<T>(int, const C2<T>*, const C2<T>*, const C2<T>*,      \
                                          const T*, T*, const double*, double*, double,       \
                                          double, int, int, const SpecTables&, const int*,    \
-                                         cudaStream_t);
+                                         cudaStream_t, const DevScalars*);
 
 }  // namespace otgb
