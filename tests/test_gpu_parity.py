@@ -106,7 +106,9 @@ def test_residual_and_coefficients(ot, N, M, prec):
     assert abs(scal[3] - s_ref["min_det"]) <= tol
     assert scal[4] == 0
     abar_ref = [O.simpson_mean(coef_ref[q]) for q in range(5)]
-    assert np.abs(scal[5:] - abar_ref).max() <= tol * max(1, np.abs(coef_ref).max())
+    # mixed mode: the gradient of the interpolant (b1, b2; Jacobian only) is FP32
+    atol = tol if prec == "fp64" else 1e-6
+    assert np.abs(scal[5:] - abar_ref).max() <= atol * max(1, np.abs(coef_ref).max())
     ctol = (tol if prec == "fp64" else 1e-6 * np.abs(coef_ref).max()) * max(1, np.abs(coef_ref).max())
     assert np.abs(coefd.cpu().numpy() - coef_ref).max() <= ctol
     p.close()
