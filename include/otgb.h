@@ -181,6 +181,30 @@ int ot_fft_forward(ot_plan* plan, const double* x, double* spec);
 /* Inverse of ot_fft_forward without the 1/(N M) factor (spec -> N M x). */
 int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
 
+/* ---- Allocation-free variant ------------------------------------------------------------
+ * No counterpart in the paper: a library-level addition for callers that cannot allocate
+ * device memory -- code whose device memory is all owned by its own pool (a framework's
+ * caching allocator, a fixed-budget service) and latency-critical loops that cannot afford
+ * cudaMalloc's implicit device-wide synchronisation.
+ *
+ * Same result as ot_eval_residual on an FP64 plan (F, the five coefficient planes as
+ * doubles, scal as there), but needs no plan and calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch (reduction partials and a block of device scalars,
+ * about 330 KB) is a fixed file-scope device array that every GPU loading the library holds
+ * until the process exits.  f, c, u, F, coef: device pointers (coef: 5 planes of N x M);
+ * scal: HOST, 10 doubles, may be NULL; cuda_stream: a cudaStream_t (NULL = legacy default).
+ * The call returns after the results are complete.
+ *   - Sizes: 8 <= N, M <= 2048; larger grids return OT_EUNSUPPORTED before touching
+ *     memory, smaller ones or a NULL pointer OT_EINVAL.
+ *   - The first call on a device looks up the array's device address (set-up, once per
+ *     device, with that device current); make that first call before any stream capture.
+ *   - All calls share the one array and clear what must start at zero themselves; calls
+ *     that overlap on the GPU (other streams or host threads) race on it and must be
+ *     serialised by the caller. */
+int ot_eval_residual_noalloc(int32_t N, int32_t M, const double* f, const double* c,
+                             const double* u, double* F, double* coef, double* scal,
+                             void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

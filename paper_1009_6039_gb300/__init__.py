@@ -27,7 +27,7 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_sol
            "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
            "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
-           "ot_plan_reset_profile", "ot_plan_time_kernel"]
+           "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc"]
 
 
 class ot_stats(ctypes.Structure):
@@ -72,6 +72,7 @@ def _load():
         "ot_plan_get_profile": ([vp, vp, vp, i32, vp], ctypes.c_int),
         "ot_plan_reset_profile": ([vp], ctypes.c_int),
         "ot_plan_time_kernel": ([vp, i32, i32, vp], ctypes.c_int),
+        "ot_eval_residual_noalloc": ([i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -154,6 +155,13 @@ def ot_plan_get_profile(plan, ms_ptr, launches_ptr, n, total_ptr):
 
 def ot_plan_reset_profile(plan):
     return _lib.ot_plan_reset_profile(plan)
+
+
+def ot_eval_residual_noalloc(N, M, f_ptr, c_ptr, u_ptr, F_ptr, coef_ptr, scal_host_ptr,
+                             stream_ptr=0):
+    """Allocation-free residual evaluation (no plan; fixed device scratch, N, M <= 2048)."""
+    return _lib.ot_eval_residual_noalloc(int(N), int(M), f_ptr, c_ptr, u_ptr, F_ptr, coef_ptr,
+                                         scal_host_ptr, ctypes.c_void_p(stream_ptr))
 
 
 def ot_plan_time_kernel(plan, kernel_class, reps, ms_ptr):
