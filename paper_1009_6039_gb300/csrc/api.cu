@@ -22,6 +22,7 @@ struct ot_plan {
   double eta = 1e-4;
   int max_newton = 200, max_restarts = 50;
   int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
+  int reorth = -1;  // -1: reorthogonalise in the FP32 mode only
   cudaStream_t stream = 0;
   int device = 0;
   // FP64 planes
@@ -33,6 +34,7 @@ struct ot_plan {
   // FP64 spectrum used by the prefilter when the inner precision is FP32
   void *spec64 = nullptr, *q64 = nullptr;
   void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
+  float* c32 = nullptr;  // FP32 copy of the B-spline coefficients (mixed mode)
   SpecTables tb64{}, tb32{};
   double* partials = nullptr;
   double* dmean = nullptr;
@@ -69,6 +71,14 @@ struct ot_plan {
 template <typename T> static const SpecTables& tables(ot_plan* p);
 template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
 template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
+
+template <typename T> static const float* c32_for(const ot_plan* p) {
+  return sizeof(T) == 4 ? p->c32 : nullptr;
+}
+
+static bool reorth_on(const ot_plan* p) {
+  return p->reorth < 0 ? p->precision == 1 : p->reorth == 1;
+}
 
 static cudaEvent_t ev_get(ot_plan* p) {
   if (!p->pool.empty()) {
@@ -176,7 +186,7 @@ static void free_buffers(ot_plan* p) {
   free_graph(p);
   if (p->uout) cudaFree(p->uout);
   p->uout = nullptr;
-  void* ptrs[] = {p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
+  void* ptrs[] = {p->c32, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
                   p->tw32, p->partials, p->dmean, p->sc};
   for (void* q : ptrs)
@@ -185,6 +195,7 @@ static void free_buffers(ot_plan* p) {
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
   p->spec64 = p->q64 = p->tw64 = p->tw32 = nullptr;
+  p->c32 = nullptr;
   p->partials = p->dmean = nullptr;
   p->sc = nullptr;
   p->hsc = nullptr;
@@ -224,6 +235,7 @@ static int alloc_buffers(ot_plan* p) {
   if (p->precision) {
     CK(cudaMalloc(&p->spec64, P * 8));
     CK(cudaMalloc(&p->q64, P * 8));
+    CK(cudaMalloc(&p->c32, P * 4));
   } else {
     p->spec64 = nullptr;
     p->q64 = nullptr;
@@ -358,6 +370,11 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (v != 0 && v != 1) return OT_EINVAL;
       p->use_graph = (int)v;
       return OT_OK;
+    case OT_OPT_REORTH:
+      if (v != -1 && v != 0 && v != 1) return OT_EINVAL;
+      p->reorth = (int)v;
+      free_graph(p);
+      return OT_OK;
   }
   return OT_EINVAL;
 }
@@ -381,8 +398,7 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
   auto one = [&]() -> cudaError_t {
     switch (cls) {
       case OT_PROF_RESIDUAL:
-        return launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials,
-                                  p->sc, p->stream);
+        return launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p));
       case OT_PROF_ROW_R2C:
         return launch_row_r2c<T>((const T*)p->V, P, nullptr, nullptr, (C2<T>*)p->spec, N, M,
                                  tb, nullptr, p->stream);
@@ -479,6 +495,9 @@ static int run_prefilter(ot_plan* p, const double* g, double* c) {
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
          launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
                                 nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream));
+  if (p->precision)
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_convert<float>(c, 1, p->c32, 0, (long)p->N * p->M, p->stream));
   return OT_OK;
 }
 
@@ -524,6 +543,30 @@ static int run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* 
   return OT_OK;
 }
 
+// One Arnoldi step j on the device: w = A v_j, Gram-Schmidt against V_0..V_j (classical,
+// once or twice), norm, Givens rotation (in the last block of the final update).
+template <typename T>
+static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
+  const long P = (long)p->N * p->M;
+  T* V = (T*)p->V;
+  T* w = (T*)p->w;
+  RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j));
+  LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
+         launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0));
+  if (reorth_on(p)) {
+    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1));
+    LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
+           launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1));
+    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 2));
+  } else {
+    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0));
+  }
+  return OT_OK;
+}
+
 // GMRES(m) on L Lbar^{-1} sigma = (f - f~_n)/tau, sigma from 0.  Host syncs once per cycle.
 template <typename T>
 static int run_gmres(ot_plan* p) {
@@ -536,13 +579,7 @@ static int run_gmres(ot_plan* p) {
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
          launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
   for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
-    for (int j = 0; j < p->m; ++j) {
-      RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j));
-      LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
-             launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
-      LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-             launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
-    }
+    for (int j = 0; j < p->m; ++j) RET(run_arnoldi_step<T>(p, j, skip));
     LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
     LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
            launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
@@ -565,6 +602,7 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->tol = p->tol;
   p->hsc->step_s = 1.0;
   p->hsc->safeguard = p->safeguard;
+  p->hsc->reorth = reorth_on(p) ? 1 : 0;
   p->hsc->max_newton = p->max_newton;
   p->hsc->max_restarts = p->max_restarts;
 }
@@ -606,8 +644,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
   }
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
-                            p->stream));
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
   RET(read_scalars(p));
   int status = OT_OK;
   double s = 1.0;
@@ -633,8 +670,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     for (;;) {
       RET(run_lbar_inv<T>(p, (const T*)p->sigma, p->u, p->ucand, s, nullptr));
       LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-             launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef,
-                                p->partials, p->sc, p->stream));
+             launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
       RET(read_scalars(p));
       if (!p->safeguard || p->hsc->admissible || s < 0x1p-30) {
         accepted = true;
@@ -734,8 +770,7 @@ static int capture_candidate(ot_plan* p) {
          launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
                            p->u, p->ucand, 1.0, 1.0, N, M, tb, nullptr, p->stream, p->sc));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
-                            p->stream, p->ucand, 1));
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 1, c32_for<T>(p)));
   LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
   return OT_OK;
 }
@@ -754,8 +789,7 @@ static int capture_solve(ot_plan* p) {
                                    p->stream));
   RET(run_prefilter(p, p->g, p->c));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
-                            p->stream, p->ucand, 0));
+         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 0, c32_for<T>(p)));
   const int top = (int)(p->launches - k0) + 1;
   LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, top));
   cudaGraph_t b1, b2, b3, b4, b5;
@@ -773,11 +807,7 @@ static int capture_solve(ot_plan* p) {
   for (int j = 0; j < p->m; ++j) {
     RET(add_conditional(p->cs[2], cudaGraphCondTypeIf, &p->h_step[j], &b3));
     RET(begin_body(p, 3, b3));
-    RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, nullptr, j));
-    LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
-           launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
-    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream));
+    RET(run_arnoldi_step<T>(p, j, nullptr));
     RET(end_body(p, 3));
   }
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
@@ -971,9 +1001,10 @@ static int eval_residual_impl(ot_plan* p, const double* f, const double* c, cons
   const long P = (long)N * M;
   set_solver_scalars(p);
   CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  if (sizeof(T) == 4)
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_convert<float>(c, 1, p->c32, 0, P, p->stream));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc,
-                            p->stream));
+         launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
          launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
   if (F) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_shifted_residual(p->Fraw, F, N, M, p->sc, p->stream));

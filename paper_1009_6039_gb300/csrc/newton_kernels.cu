@@ -58,6 +58,32 @@ __device__ void block_reduce(double (&v)[NV], const int (&kind)[NV]) {
   __syncthreads();
 }
 
+// Block sum of NV floats (result valid in thread 0).
+template <int NV>
+__device__ void block_sum_f(float (&v)[NV]) {
+  __shared__ float redf[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) redf[wid][a] = v[a];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      float x = lane < nw ? redf[lane][a] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[a] = x;
+    }
+  }
+  __syncthreads();
+}
+
 // Write the block's partials, take a ticket; returns true in the (whole) last block,
 // after which `partials` of all blocks are visible.
 template <int NV>
@@ -210,9 +236,10 @@ __device__ __forceinline__ void bspline_v(double t, double w[4]) {
 template <typename T>
 __global__ void __launch_bounds__(RTX * RTY / RPT)
     k_residual(const double* __restrict__ f, const double* __restrict__ c,
-               const double* __restrict__ ua, const double* __restrict__ ub, int sel, int N,
-               int M, ResidConsts K, double* __restrict__ Fraw, T* __restrict__ coef,
-               double* partials, DevScalars* sc) {
+               const float* __restrict__ c32, const double* __restrict__ ua,
+               const double* __restrict__ ub, int sel, int N, int M, ResidConsts K,
+               double* __restrict__ Fraw, T* __restrict__ coef, double* partials,
+               DevScalars* sc) {
   __shared__ double tile[RTY + 4][RTX + 4];
   const double* __restrict__ u = (ub && ((sc->upar ^ sel) & 1)) ? ub : ua;
   const int bx = blockIdx.x * RTX, by = blockIdx.y * RTY;
@@ -227,14 +254,15 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     tile[r][cc] = u[(size_t)gi * M + gj];
   }
   __syncthreads();
-  // partials: sum fn, Simpson sums of a11 a12 a22 b1 b2, max Fraw, min Fraw, min det,
-  // non-finite count
-  double v[10] = {0, 0, 0, 0, 0, 0, -INFINITY, INFINITY, INFINITY, 0};
-  const int kind[10] = {0, 0, 0, 0, 0, 0, 1, 2, 2, 0};
+  // FP64 partials: sum fn, max Fraw, min Fraw, min det, non-finite count; Simpson sums of
+  // the coefficients (Jacobian only) in the coefficient precision T
+  double v64[5] = {0.0, -INFINITY, INFINITY, INFINITY, 0.0};
+  const int kind64[5] = {0, 1, 2, 2, 0};
+  T simp[5] = {(T)0, (T)0, (T)0, (T)0, (T)0};
   const int tx = tid % RTX, ty0 = tid / RTX;
   const int j = bx + tx;
   const size_t P = (size_t)N * M;
-  const double wx = ((j & 1) ? 4.0 : 2.0) * K.w3M;
+  const T wx = (T)(((j & 1) ? 4.0 : 2.0) * K.w3M);
 #pragma unroll 1
   for (int rr = 0; rr < RPT; ++rr) {
     const int ty = ty0 + rr * (RTY / RPT);
@@ -269,7 +297,8 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     ii[1] = i0;
     ii[2] = wrap_near(i0 + 1, N);
     ii[3] = wrap_near(i0 + 2, N);
-    double G = 0.0, Gx, Gy;
+    double G = 0.0;
+    T Gx, Gy;
     if (sizeof(T) == 8) {
       double wxv[4], dwx[4], wyv[4], dwy[4];
       bspline_w<double>(tx_, wxv, dwx);
@@ -289,10 +318,11 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
         gx += sd * wyv[b];
         gy += sv * dwy[b];
       }
-      Gx = gx * (double)M;
-      Gy = gy * (double)N;
+      Gx = (T)(gx * (double)M);
+      Gy = (T)(gy * (double)N);
     } else {
-      // value in FP64 (it enters the residual), gradient in FP32 (Jacobian only)
+      // value in FP64 (it enters the residual); gradient (Jacobian only) in FP32 from the
+      // FP32 copy of the coefficients
       double wxv[4], wyv[4];
       bspline_v(tx_, wxv);
       bspline_v(ty_, wyv);
@@ -303,13 +333,13 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const double* crow = c + (size_t)ii[b] * M;
+        const float* crow32 = c32 + (size_t)ii[b] * M;
         double sv = 0.0;
         float svf = 0.f, sdf = 0.f;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const double cv = __ldg(crow + jj[a]);
-          sv += cv * wxv[a];
-          const float cf = (float)cv;
+          sv += __ldg(crow + jj[a]) * wxv[a];
+          const float cf = __ldg(crow32 + jj[a]);
           svf += cf * wxf[a];
           sdf += cf * dwx[a];
         }
@@ -317,38 +347,62 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
         gx += sdf * wyf[b];
         gy += svf * dwy[b];
       }
-      Gx = (double)(gx * (float)M);
-      Gy = (double)(gy * (float)N);
+      Gx = (T)(gx * (float)M);
+      Gy = (T)(gy * (float)N);
     }
     const double det = (1.0 + uxx) * (1.0 + uyy) - uxy * uxy;
     const double fn = G * det;
     const size_t p = (size_t)i * M + j;
     const double fr = f[p] - fn;
     Fraw[p] = fr;
-    const double a11 = G * (1.0 + uyy), a12 = -G * uxy, a22 = G * (1.0 + uxx);
-    const double b1 = det * Gx, b2 = det * Gy;
-    coef[p] = (T)a11;
-    coef[P + p] = (T)a12;
-    coef[2 * P + p] = (T)a22;
-    coef[3 * P + p] = (T)b1;
-    coef[4 * P + p] = (T)b2;
-    const double w = ((i & 1) ? 4.0 : 2.0) * K.w3N * wx;
-    const bool fin = isfinite(fn);
-    v[0] += fin ? fn : 0.0;
-    v[1] += w * a11;
-    v[2] += w * a12;
-    v[3] += w * a22;
-    v[4] += w * b1;
-    v[5] += w * b2;
-    if (fin) {
-      v[6] = fmax(v[6], fr);
-      v[7] = fmin(v[7], fr);
+    // coefficients of the linearisation (Jacobian only): precision T
+    const T Gt = (T)G, dett = (T)det;
+    const T a11 = Gt * ((T)1 + (T)uyy), a12 = -Gt * (T)uxy, a22 = Gt * ((T)1 + (T)uxx);
+    const T b1 = dett * Gx, b2 = dett * Gy;
+    coef[p] = a11;
+    coef[P + p] = a12;
+    coef[2 * P + p] = a22;
+    coef[3 * P + p] = b1;
+    coef[4 * P + p] = b2;
+    const T w = (T)((i & 1) ? 4.0 : 2.0) * (T)K.w3N * wx;
+    simp[0] += w * a11;
+    simp[1] += w * a12;
+    simp[2] += w * a22;
+    simp[3] += w * b1;
+    simp[4] += w * b2;
+    if (isfinite(fn)) {
+      v64[0] += fn;
+      v64[1] = fmax(v64[1], fr);
+      v64[2] = fmin(v64[2], fr);
     } else {
-      v[9] += 1.0;
+      v64[4] += 1.0;
     }
-    v[8] = fmin(v[8], det);
+    v64[3] = fmin(v64[3], det);
   }
-  block_reduce<10>(v, kind);
+  double v[10];
+  const int kind[10] = {0, 0, 0, 0, 0, 0, 1, 2, 2, 0};
+  block_reduce<5>(v64, kind64);
+  if (sizeof(T) == 8) {
+    double sd[5];
+    const int k5[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 5; ++a) sd[a] = (double)simp[a];
+    block_reduce<5>(sd, k5);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) v[1 + a] = sd[a];
+  } else {
+    float sf[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) sf[a] = (float)simp[a];
+    block_sum_f<5>(sf);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) v[1 + a] = (double)sf[a];
+  }
+  v[0] = v64[0];
+  v[6] = v64[1];
+  v[7] = v64[2];
+  v[8] = v64[3];
+  v[9] = v64[4];
   if (!publish_partials<10>(v, partials, &sc->ticket[TK_RESID])) return;
   const unsigned int nb = gridDim.x * gridDim.y;
   reduce_partials<10>(v, kind, partials, nb);
@@ -374,7 +428,7 @@ int residual_partial_blocks(int N, int M) {
 template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
-                            cudaStream_t st, const double* ub, int sel) {
+                            cudaStream_t st, const double* ub, int sel, const float* c32) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConsts K;
   K.Mh = (double)M / 12.0;
@@ -383,7 +437,8 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
   K.Nh2 = (double)N * (double)N / 12.0;
   K.w3M = 1.0 / (3.0 * (double)M);
   K.w3N = 1.0 / (3.0 * (double)N);
-  k_residual<T><<<grid, RTX * RTY / RPT, 0, st>>>(f, c, ua, ub, sel, N, M, K, Fraw, coef,
+  if (sizeof(T) == 4 && !c32) return cudaErrorInvalidValue;
+  k_residual<T><<<grid, RTX * RTY / RPT, 0, st>>>(f, c, c32, ua, ub, sel, N, M, K, Fraw, coef,
                                                   partials, sc);
   return cudaGetLastError();
 }
@@ -517,7 +572,7 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
 // P / (2 x SMs x 256) elements); partials are combined across threads and blocks in FP64.
 template <typename T, int J>
 __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restrict__ w, long P,
-                                       double* partials, DevScalars* sc) {
+                                       double* partials, DevScalars* sc, int pass) {
   T acc[J];
 #pragma unroll
   for (int i = 0; i < J; ++i) acc[i] = (T)0;
@@ -539,20 +594,29 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
   reduce_partials<J>(v, kind, partials, gridDim.x);
   if (threadIdx.x == 0) {
     const int m = sc->m, j = J - 1;
+    if (pass == 0) {
 #pragma unroll
-    for (int i = 0; i < J; ++i) sc->H[i * m + j] = sc->scale[i] * v[i];
+      for (int i = 0; i < J; ++i) sc->H[i * m + j] = sc->scale[i] * v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < J; ++i) {
+        sc->h2[i] = sc->scale[i] * v[i];
+        sc->H[i * m + j] += sc->h2[i];
+      }
+    }
     sc->ticket[TK_DOTS] = 0;
   }
 }
 
 template <typename T>
 __global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, long P,
-                             double* partials, DevScalars* sc) {
+                             double* partials, DevScalars* sc, int pass) {
   if (sc->cycle_done) return;
+  if (pass) w = V + (size_t)(sc->j + 1) * P;
   switch (sc->j) {
 #define OTGB_DOTS_CASE(k) \
   case k:                 \
-    dots_j<T, k + 1>(V, w, P, partials, sc); break;
+    dots_j<T, k + 1>(V, w, P, partials, sc, pass); break;
     OTGB_DOTS_CASE(0) OTGB_DOTS_CASE(1) OTGB_DOTS_CASE(2) OTGB_DOTS_CASE(3)
     OTGB_DOTS_CASE(4) OTGB_DOTS_CASE(5) OTGB_DOTS_CASE(6) OTGB_DOTS_CASE(7)
     OTGB_DOTS_CASE(8) OTGB_DOTS_CASE(9) OTGB_DOTS_CASE(10) OTGB_DOTS_CASE(11)
@@ -563,21 +627,24 @@ __global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, l
 
 template <typename T, int J>
 __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict__ w, long P,
-                                         double* partials, DevScalars* sc) {
+                                         double* partials, DevScalars* sc, int mode) {
   const int j = J - 1, m = sc->m;
   T coefs[J];
 #pragma unroll
-  for (int i = 0; i < J; ++i) coefs[i] = (T)(sc->H[i * m + j] * sc->scale[i]);
+  for (int i = 0; i < J; ++i)
+    coefs[i] = (T)((mode == 2 ? sc->h2[i] : sc->H[i * m + j]) * sc->scale[i]);
   T* Vn = V + (size_t)(j + 1) * P;
+  const T* src = (mode == 2) ? Vn : w;
   T acc = (T)0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
-    T x = w[p];
+    T x = src[p];
 #pragma unroll
     for (int i = 0; i < J; ++i) x -= coefs[i] * V[(size_t)i * P + p];
     Vn[p] = x;
     acc += x * x;
   }
+  if (mode == 1) return;  // first of two passes: the norm follows the second
   double v[1] = {(double)acc};
   const int kind[1] = {0};
   block_reduce<1>(v, kind);
@@ -618,12 +685,12 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
 
 template <typename T>
 __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long P,
-                               double* partials, DevScalars* sc) {
+                               double* partials, DevScalars* sc, int mode) {
   if (sc->cycle_done) return;
   switch (sc->j) {
 #define OTGB_UPD_CASE(k) \
   case k:                \
-    update_j<T, k + 1>(V, w, P, partials, sc); break;
+    update_j<T, k + 1>(V, w, P, partials, sc, mode); break;
     OTGB_UPD_CASE(0) OTGB_UPD_CASE(1) OTGB_UPD_CASE(2) OTGB_UPD_CASE(3)
     OTGB_UPD_CASE(4) OTGB_UPD_CASE(5) OTGB_UPD_CASE(6) OTGB_UPD_CASE(7)
     OTGB_UPD_CASE(8) OTGB_UPD_CASE(9) OTGB_UPD_CASE(10) OTGB_UPD_CASE(11)
@@ -689,14 +756,14 @@ cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int
 }
 template <typename T>
 cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
-                              int nblocks, cudaStream_t st) {
-  k_gmres_dots<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc);
+                              int nblocks, cudaStream_t st, int pass) {
+  k_gmres_dots<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc, pass);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
-                                int nblocks, cudaStream_t st) {
-  k_gmres_update<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc);
+                                int nblocks, cudaStream_t st, int mode) {
+  k_gmres_update<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc, mode);
   return cudaGetLastError();
 }
 template <typename T>
@@ -771,7 +838,8 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
       break;
     }
     case CTL_GMRES_DONE:
-      sc->kcount += 5LL * sc->iters;  // Arnoldi steps: 3 matvec passes + dots + update
+      // Arnoldi steps: 3 matvec passes + dots + update (+ dots + update when reorthogonal.)
+      sc->kcount += (sc->reorth ? 7LL : 5LL) * sc->iters;
       sc->gmres_iters_total += sc->iters;
       sc->gmres_cycles_total += sc->cycles;
       break;
@@ -841,13 +909,13 @@ cudaError_t launch_convert(const void* in, int in_d, void* out, int out_d, long 
 #define OTGB_INST_NEWTON(T)                                                                   \
   template cudaError_t launch_residual<T>(const double*, const double*, const double*, int,   \
                                           int, double*, T*, double*, DevScalars*,             \
-                                          cudaStream_t, const double*, int);                  \
+                                          cudaStream_t, const double*, int, const float*);    \
   template cudaError_t launch_gmres_init<T>(const double*, const T*, T*, long, int, double*,  \
                                             DevScalars*, int, cudaStream_t, T*);              \
   template cudaError_t launch_gmres_dots<T>(const T*, const T*, long, double*, DevScalars*,   \
-                                            int, cudaStream_t);                               \
+                                            int, cudaStream_t, int);                          \
   template cudaError_t launch_gmres_update<T>(T*, const T*, long, double*, DevScalars*, int,  \
-                                              cudaStream_t);                                  \
+                                              cudaStream_t, int);                             \
   template cudaError_t launch_gmres_combine<T>(const T*, T*, long, const DevScalars*, int,    \
                                                cudaStream_t);                                 \
   template cudaError_t launch_convert<T>(const void*, int, void*, int, long, cudaStream_t);

@@ -34,13 +34,14 @@ struct DevScalars {
   double H[(OTGB_MAXM + 1) * OTGB_MAXM];
   double cs[OTGB_MAXM], sn[OTGB_MAXM], gv[OTGB_MAXM + 1], y[OTGB_MAXM];
   double scale[OTGB_MAXM + 1];  // V_i is stored unnormalised; v_i = scale[i] * V_i
+  double h2[OTGB_MAXM];         // second Gram-Schmidt pass (reorthogonalisation)
   double relres;
   int j, jend, m, cycle_done, converged, iters, cycles;
   double eta, tau;
   // Newton control, resident on the device for the graph-launched solve
   double tol, step_s;
   int newton_n, halvings, status, upar, safeguard, max_newton, max_restarts;
-  int gmres_iters_total, gmres_cycles_total, graph;
+  int gmres_iters_total, gmres_cycles_total, graph, reorth;
   long long kcount;  // kernels executed by the graph-launched solve
   // conditional-node handles of the captured solve (0 outside a graph)
   unsigned long long h_newton, h_cycle, h_restart, h_halve, h_step[OTGB_MAXM];
@@ -97,10 +98,12 @@ cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st);
 // u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate)
+// c32 (optional, FP32 copy of c): used for the gradient of the interpolant in FP32 mode
 template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
-                            cudaStream_t st, const double* ub = nullptr, int sel = 0);
+                            cudaStream_t st, const double* ub = nullptr, int sel = 0,
+                            const float* c32 = nullptr);
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
                                DevScalars* sc, cudaStream_t st);
 cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
@@ -120,12 +123,15 @@ template <typename T>
 cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
                               double* partials, DevScalars* sc, int nblocks, cudaStream_t st,
                               T* sigma = nullptr);
+// pass 0: H[:, j] = V^T w; pass 1 (reorthogonalisation): h2 = V^T V_{j+1}, H[:, j] += h2
 template <typename T>
 cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
-                              int nblocks, cudaStream_t st);
+                              int nblocks, cudaStream_t st, int pass = 0);
+// mode 0: V_{j+1} = w - V H[:, j], norm + Givens; mode 1: the same without norm (first of
+// two passes); mode 2: V_{j+1} -= V h2 in place, norm + Givens
 template <typename T>
 cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
-                                int nblocks, cudaStream_t st);
+                                int nblocks, cudaStream_t st, int mode = 0);
 cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,
