@@ -65,9 +65,8 @@ extern "C" {
                                    are conditional nodes driven by device-side tests (no host
                                    round trip until the end); 0: host-driven loop that
                                    synchronises once per GMRES cycle and per Newton step */
-#define OT_OPT_REORTH 13        /* Gram-Schmidt passes in the Arnoldi step: -1 (default) two
-                                   passes (reorthogonalisation) in the FP32 mode, one in FP64;
-                                   0 always one; 1 always two */
+#define OT_OPT_REORTH 13        /* 0 (default): one classical Gram-Schmidt pass per Arnoldi
+                                   step; 1: two passes (reorthogonalisation) */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

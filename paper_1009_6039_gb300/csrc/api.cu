@@ -22,7 +22,7 @@ struct ot_plan {
   double eta = 1e-4;
   int max_newton = 200, max_restarts = 50;
   int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
-  int reorth = -1;  // -1: reorthogonalise in the FP32 mode only
+  int reorth = 0;  // Gram-Schmidt passes - 1 (OT_OPT_REORTH)
   cudaStream_t stream = 0;
   int device = 0;
   // FP64 planes
@@ -76,9 +76,7 @@ template <typename T> static const float* c32_for(const ot_plan* p) {
   return sizeof(T) == 4 ? p->c32 : nullptr;
 }
 
-static bool reorth_on(const ot_plan* p) {
-  return p->reorth < 0 ? p->precision == 1 : p->reorth == 1;
-}
+static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
 
 static cudaEvent_t ev_get(ot_plan* p) {
   if (!p->pool.empty()) {
@@ -371,7 +369,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       p->use_graph = (int)v;
       return OT_OK;
     case OT_OPT_REORTH:
-      if (v != -1 && v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && v != 1) return OT_EINVAL;
       p->reorth = (int)v;
       free_graph(p);
       return OT_OK;

@@ -504,15 +504,164 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
 }
 
 // ---------------------------------------------------------------------------------------
+// Concurrent-transform variants of the two dominant passes (FP32).  At 1024^2 a pass with
+// one transform group per column/row launches fewer blocks than the GPU has SMs and is
+// latency-bound, so these run the independent transforms of a column/row at the same
+// time in separate thread groups with their own shared-memory buffers.
+// ---------------------------------------------------------------------------------------
+#define OTGB_PAR_THREADS 768
+
+// Column pass of the matvec: forward column FFT (group 0), S = rho-bar sigma-hat / (N M),
+// then the inverse column FFTs of S, (2 pi i k2) S and -(2 pi k2)^2 S in groups 0, 1, 2.
+template <typename T, int E>
+__global__ void __launch_bounds__(OTGB_PAR_THREADS)
+    k_col_matvec_par(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
+                     C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
+                     const C2<T>* __restrict__ twN, const DevScalars* __restrict__ sc,
+                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int Lc = M / 2, TPT = N / E, G = Q * TPT;
+  const int grp = threadIdx.x / G, rem = threadIdx.x - grp * G;
+  const int q = rem / TPT, t = rem - q * TPT;
+  const int col0 = blockIdx.x * Q, col = col0 + q;
+  const bool active = col < Lc;
+  const int stride = Q * (N + 1);  // one group's buffers
+  C2<T>* buf = sm + grp * stride + q * (N + 1);
+  C2<T>* b0 = sm + q * (N + 1);
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx / Q, qq = idx - n * Q;
+    if (col0 + qq < Lc) sm[qq * (N + 1) + n] = spec[(size_t)n * Lc + col0 + qq];
+  }
+  __syncthreads();
+  fft_smem<T, E, -1>(b0, N, t, active && grp == 0, twN);
+  T ab[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ab[a] = (T)sc->abar[a];
+  const T inv = (T)(1.0 / ((double)N * (double)M));
+  C2<T> s[E];
+  const bool lead = active && grp == 0;
+  if (lead) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      C2<T> z = b0[k], r;
+      if (col == 0) {
+        C2<T> pz = b0[(N - k) % N];
+        C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
+        C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
+        A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
+        B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
+        r = mk2<T>(A.x - B.y, A.y + B.x);
+      } else {
+        r = cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z);
+      }
+      s[e] = cscale<T>(r, inv);
+    }
+  }
+  __syncthreads();
+  if (lead) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      const T q2 = (T)OTGB_TWO_PI * (T)k2;
+      const C2<T> v = s[e];
+      b0[k] = v;
+      b0[stride + k] = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
+      b0[2 * stride + k] = cscale<T>(v, -q2 * q2);
+    }
+  }
+  __syncthreads();
+  fft_smem<T, E, +1>(buf, N, t, active, twN);
+  for (int idx = threadIdx.x; idx < 3 * Q * N; idx += blockDim.x) {
+    const int g = idx / (Q * N), r2 = idx - g * Q * N;
+    const int n = r2 / Q, qq = r2 - n * Q;
+    if (col0 + qq < Lc) {
+      C2<T>* dst = g == 0 ? out0 : (g == 1 ? out1 : out2);
+      dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * (N + 1) + n];
+    }
+  }
+}
+
+// Row pass of the matvec: the five complex-to-real transforms of a row (d_xx Q0, d_x Q0,
+// d_x Q1, Q1, Q2) in groups 0..4, then w = a11 . + b1 . + 2 a12 . + b2 . + a22 .
+template <typename T, int E>
+__global__ void __launch_bounds__(OTGB_PAR_THREADS)
+    k_row_combine_par(const C2<T>* __restrict__ q0, const C2<T>* __restrict__ q1,
+                      const C2<T>* __restrict__ q2, const T* __restrict__ coef,
+                      T* __restrict__ out, int N, int M, int RB, const C2<T>* __restrict__ twL,
+                      const C2<T>* __restrict__ twM, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int L = M / 2, TPT = L / E, G = RB * TPT;
+  const int grp = threadIdx.x / G, rem = threadIdx.x - grp * G;
+  const int q = rem / TPT, t = rem - q * TPT;
+  const int row0 = blockIdx.x * RB, row = row0 + q;
+  const bool active = row < N;
+  const int stride = RB * (L + 1);
+  C2<T>* buf = sm + grp * stride + q * (L + 1);
+  for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
+    const int qq = idx / L, k = idx - qq * L;
+    if (row0 + qq < N) {
+      const size_t o = (size_t)(row0 + qq) * L + k;
+      const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
+      C2<T>* b = sm + qq * (L + 1) + k;
+      b[0] = row_symbol_apply<T>(x0, k, L, 2);
+      b[stride] = row_symbol_apply<T>(x0, k, L, 1);
+      b[2 * stride] = row_symbol_apply<T>(x1, k, L, 1);
+      b[3 * stride] = x1;
+      b[4 * stride] = x2;
+    }
+  }
+  __syncthreads();
+  c2r_preprocess<T>(buf, L, t, TPT, active, twM);
+  fft_smem<T, E, +1>(buf, L, t, active, twL);
+  const size_t P = (size_t)N * M;
+  for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
+    const int qq = idx / L, n = idx - qq * L;
+    const int r = row0 + qq;
+    if (r < N) {
+      const size_t o = (size_t)r * M;
+      const C2<T>* c0 = reinterpret_cast<const C2<T>*>(coef + o);
+      const C2<T>* c1 = reinterpret_cast<const C2<T>*>(coef + P + o);
+      const C2<T>* c2 = reinterpret_cast<const C2<T>*>(coef + 2 * P + o);
+      const C2<T>* c3 = reinterpret_cast<const C2<T>*>(coef + 3 * P + o);
+      const C2<T>* c4 = reinterpret_cast<const C2<T>*>(coef + 4 * P + o);
+      const C2<T>* b = sm + qq * (L + 1) + n;
+      const C2<T> y0 = b[0], y1 = b[stride], y2 = b[2 * stride], y3 = b[3 * stride],
+                  y4 = b[4 * stride];
+      const C2<T> a11 = c0[n], a12 = c1[n], a22 = c2[n], b1 = c3[n], b2 = c4[n];
+      C2<T> acc;
+      acc.x = a11.x * y0.x + b1.x * y1.x + (T)2 * a12.x * y2.x + b2.x * y3.x + a22.x * y4.x;
+      acc.y = a11.y * y0.y + b1.y * y1.y + (T)2 * a12.y * y2.y + b2.y * y3.y + a22.y * y4.y;
+      reinterpret_cast<C2<T>*>(out + o)[n] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------------------
 inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
 
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+  // the attribute is per kernel and per device; raise it to the largest size seen
+  static int done_bytes[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (bytes > 48 * 1024 && (dev >= 64 || (int)bytes > done_bytes[dev])) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess && dev < 64) done_bytes[dev] = (int)bytes;
+    return e;
+  }
   return cudaSuccess;
 }
 
@@ -522,6 +671,7 @@ cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scal
   const int L = M / 2, TPT = L / E;
   int RB = MaxThreads<T>::value / TPT;
   if (RB < 1) RB = 1;
+  while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_r2c<T, E>, sm);
@@ -539,6 +689,7 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   int Q = MaxThreads<T>::value / TPT;
   if (Q < 1) Q = 1;
   while (Q > 1 && (size_t)Q * (N + 1) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
+  while (Q > 2 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * (N + 1) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
@@ -556,6 +707,7 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   const int L = M / 2, TPT = L / E;
   int RB = MaxThreads<T>::value / TPT;
   if (RB < 1) RB = 1;
+  while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_c2r<T, E, MODE>, sm);
@@ -575,9 +727,28 @@ cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double*
 }
 
 template <typename T, int E>
+cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int M,
+                             const SpecTables& tb, const DevScalars* sc, const int* skip,
+                             cudaStream_t st) {
+  const int Lc = M / 2, TPT = N / E;
+  int Q = OTGB_PAR_THREADS / (3 * TPT);
+  if (Q < 1) Q = 1;
+  if (Q > 4) Q = 4;
+  if (Q > Lc) Q = Lc;
+  const size_t sm = (size_t)3 * Q * (N + 1) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_col_matvec_par<T, E>, sm);
+  if (e != cudaSuccess) return e;
+  k_col_matvec_par<T, E><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
+      spec, o0, o1, o2, N, M, Q, (const C2<T>*)tb.twN, sc, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
 cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
                          int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
                          cudaStream_t st) {
+  if (sizeof(T) == 4 && mode == COL_MATVEC && 3 * (N / E) <= OTGB_PAR_THREADS)
+    return col_matvec_par_E<T, E>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   switch (mode) {
     case COL_FWD: return col_E<T, E, COL_FWD>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_INV: return col_E<T, E, COL_INV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
@@ -598,10 +769,29 @@ cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>*
 }
 
 template <typename T, int E>
+cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T* coef,
+                              T* out, int N, int M, const SpecTables& tb, const int* skip,
+                              cudaStream_t st) {
+  const int L = M / 2, TPT = L / E;
+  int RB = OTGB_PAR_THREADS / (5 * TPT);
+  if (RB < 1) RB = 1;
+  if (RB > 8) RB = 8;
+  if (RB > N) RB = N;
+  const size_t sm = (size_t)5 * RB * (L + 1) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_row_combine_par<T, E>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_combine_par<T, E><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
+      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+  return cudaGetLastError();
+}
+
+template <typename T, int E>
 cudaError_t row_c2r_dispatch(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                              const T* coef, T* out, const double* u_in, double* u_out,
                              double step, double os, int N, int M, const SpecTables& tb,
                              const int* skip, cudaStream_t st, const DevScalars* sc) {
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && 5 * ((M / 2) / E) <= OTGB_PAR_THREADS)
+    return row_combine_par_E<T, E>(q0, q1, q2, coef, out, N, M, tb, skip, st);
   switch (mode) {
     case ROWINV_PLAIN:
       return row_c2r_E<T, E, ROWINV_PLAIN>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
