@@ -205,6 +205,7 @@ __device__ __forceinline__ int wrap_near(int a, int L) {  // a in [-L, 2L)
 
 struct ResidConsts {
   double Mh, Nh, Mh2, Nh2;  // M/12, N/12, M^2/12, N^2/12
+  double MNh;               // M N / 144
   double w3M, w3N;          // 1/(3M), 1/(3N): Simpson weights (2 or 4) x these
 };
 
@@ -223,14 +224,15 @@ __device__ __forceinline__ void bspline_w(G t, G w[4], G dw[4]) {
   dw[3] = (G)0.5 * t2;
 }
 
+// value weights only; w[2] from the partition of unity sum w = 1
 __device__ __forceinline__ void bspline_v(double t, double w[4]) {
   const double s = 1.0 - t;
   const double t2 = t * t, t3 = t2 * t;
   const double sixth = 1.0 / 6.0;
   w[0] = s * s * s * sixth;
-  w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) * sixth;
-  w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) * sixth;
+  w[1] = fma(0.5, t3, (2.0 / 3.0) - t2);
   w[3] = t3 * sixth;
+  w[2] = 1.0 - w[0] - w[1] - w[3];
 }
 
 template <typename T>
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
                double* __restrict__ Fraw, T* __restrict__ coef, double* partials,
                DevScalars* sc) {
   __shared__ double tile[RTY + 4][RTX + 4];
+  __shared__ double dyt[RTY][RTX + 4];  // unscaled y-difference of u (halo 2 in x)
   const double* __restrict__ u = (ub && ((sc->upar ^ sel) & 1)) ? ub : ua;
   const int bx = blockIdx.x * RTX, by = blockIdx.y * RTY;
   const int tid = threadIdx.x;
@@ -252,6 +255,11 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     while (gj < 0) gj += M;
     while (gj >= M) gj -= M;
     tile[r][cc] = u[(size_t)gi * M + gj];
+  }
+  __syncthreads();
+  for (int idx = tid; idx < RTY * (RTX + 4); idx += blockDim.x) {
+    const int r = idx / (RTX + 4), cc = idx - r * (RTX + 4);
+    dyt[r][cc] = -tile[r + 4][cc] + 8.0 * tile[r + 3][cc] - 8.0 * tile[r + 1][cc] + tile[r][cc];
   }
   __syncthreads();
   // FP64 partials: sum fn, max Fraw, min Fraw, min det, non-finite count; Simpson sums of
@@ -271,18 +279,13 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     const int r = ty + 2, q = tx + 2;
     const double ux =
         (-tile[r][q + 2] + 8.0 * tile[r][q + 1] - 8.0 * tile[r][q - 1] + tile[r][q - 2]) * K.Mh;
-    const double uy =
-        (-tile[r + 2][q] + 8.0 * tile[r + 1][q] - 8.0 * tile[r - 1][q] + tile[r - 2][q]) * K.Nh;
+    const double uy = dyt[ty][q] * K.Nh;
     const double uxx = (-tile[r][q + 2] + 16.0 * tile[r][q + 1] - 30.0 * tile[r][q] +
                         16.0 * tile[r][q - 1] - tile[r][q - 2]) * K.Mh2;
     const double uyy = (-tile[r + 2][q] + 16.0 * tile[r + 1][q] - 30.0 * tile[r][q] +
                         16.0 * tile[r - 1][q] - tile[r - 2][q]) * K.Nh2;
-    double dyc[5];
-#pragma unroll
-    for (int a = -2; a <= 2; ++a)
-      dyc[a + 2] = -tile[r + 2][q + a] + 8.0 * tile[r + 1][q + a] -
-                   8.0 * tile[r - 1][q + a] + tile[r - 2][q + a];
-    const double uxy = (-dyc[4] + 8.0 * dyc[3] - 8.0 * dyc[1] + dyc[0]) * (K.Mh * K.Nh);
+    const double uxy = (-dyt[ty][q + 2] + 8.0 * dyt[ty][q + 1] - 8.0 * dyt[ty][q - 1] +
+                        dyt[ty][q - 2]) * K.MNh;
     // g at the displaced point x + grad u, in grid units, periodic cubic B-spline
     const double gxp = (double)j + (double)M * ux, gyp = (double)i + (double)N * uy;
     const double fj = floor(gxp), fi = floor(gyp);
@@ -435,6 +438,7 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
   K.Nh = (double)N / 12.0;
   K.Mh2 = (double)M * (double)M / 12.0;
   K.Nh2 = (double)N * (double)N / 12.0;
+  K.MNh = K.Mh * K.Nh;
   K.w3M = 1.0 / (3.0 * (double)M);
   K.w3N = 1.0 / (3.0 * (double)N);
   if (sizeof(T) == 4 && !c32) return cudaErrorInvalidValue;
