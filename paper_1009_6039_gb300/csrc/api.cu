@@ -7,6 +7,7 @@
 
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -39,7 +40,8 @@ struct ot_plan {
   double* partials = nullptr;
   double* dmean = nullptr;
   DevScalars* sc = nullptr;
-  DevScalars* hsc = nullptr;  // pinned host mirror
+  DevScalars* hsc = nullptr;    // pinned host mirror
+  DevScalars* hinit = nullptr;  // pinned initial scalars of a batched solve (upload source)
   int kblocks = 0;
   bool ready = false;
   // kernel launch count and per-class event timing (OT_OPT_PROFILE)
@@ -190,6 +192,8 @@ static void free_buffers(ot_plan* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->hsc) cudaFreeHost(p->hsc);
+  if (p->hinit) cudaFreeHost(p->hinit);
+  p->hinit = nullptr;
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
   p->spec64 = p->q64 = p->tw64 = p->tw32 = nullptr;
@@ -268,6 +272,8 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaMemset(p->sc, 0, sizeof(DevScalars)));
   CK(cudaMallocHost(&p->hsc, sizeof(DevScalars)));
   memset(p->hsc, 0, sizeof(DevScalars));
+  CK(cudaMallocHost(&p->hinit, sizeof(DevScalars)));
+  memset(p->hinit, 0, sizeof(DevScalars));
   p->ready = true;
   return OT_OK;
 }
@@ -876,44 +882,44 @@ static int build_graph(ot_plan* p) {
   return OT_OK;
 }
 
-template <typename T>
-static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
-                            ot_stats* st) {
-  ot_stats local;
-  if (!st) st = &local;
-  memset(st, 0, sizeof(*st));
-  const long P = (long)p->N * p->M;
-  if (!p->gexec || p->gkey_prec != p->precision || p->gkey_m != p->m ||
-      p->gkey_translate != p->translate)
-    RET(build_graph<T>(p));
-  double* ua = p->gu_a;
-  cudaEvent_t ev0, ev1;
-  CK(cudaEventCreate(&ev0));
-  CK(cudaEventCreate(&ev1));
-  CK(cudaEventRecord(ev0, p->stream));
-  if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
-  if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
-  if (p->warm_start) {
-    if (phi != ua) CK(cudaMemcpyAsync(ua, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
-  } else {
-    CK(cudaMemsetAsync(ua, 0, P * 8, p->stream));
-  }
+// Fill the initial device scalars of a graph-launched solve into *h (host).
+static void graph_scalars(ot_plan* p, DevScalars* h) {
   set_solver_scalars(p);
-  DevScalars* h = p->hsc;
+  *h = *p->hsc;
   h->graph = 1;
   h->h_newton = p->h_newton;
   h->h_cycle = p->h_cycle;
   h->h_restart = p->h_restart;
   h->h_halve = p->h_halve;
   for (int k = 0; k < OTGB_MAXM; ++k) h->h_step[k] = p->h_step[k];
-  CK(cudaMemcpyAsync(p->sc, h, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
-  CK(cudaGraphLaunch(p->gexec, p->stream));
-  if (phi != p->uout)
-    CK(cudaMemcpyAsync(phi, p->uout, P * 8, cudaMemcpyDeviceToDevice, p->stream));
-  CK(cudaMemcpyAsync(&st->phi_mean, p->dmean, 8, cudaMemcpyDeviceToHost, p->stream));
-  CK(cudaEventRecord(ev1, p->stream));
-  RET(read_scalars(p));
-  h = p->hsc;
+}
+
+// Enqueue one graph-launched solve on stream xs: inputs into the plan's buffers, the initial
+// scalars from `init` (pinned host), the graph, phi out, and the final scalars / mean into
+// the pinned host slots.  Nothing waits here.
+template <typename T>
+static int graph_enqueue(ot_plan* p, cudaStream_t xs, const double* f_in, const double* g_in,
+                         double* phi, const DevScalars* init, DevScalars* slot,
+                         double* mean_slot) {
+  const long P = (long)p->N * p->M;
+  double* ua = p->gu_a;
+  if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, xs));
+  if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, xs));
+  if (p->warm_start) {
+    if (phi != ua) CK(cudaMemcpyAsync(ua, phi, P * 8, cudaMemcpyDeviceToDevice, xs));
+  } else {
+    CK(cudaMemsetAsync(ua, 0, P * 8, xs));
+  }
+  CK(cudaMemcpyAsync(p->sc, init, sizeof(DevScalars), cudaMemcpyHostToDevice, xs));
+  CK(cudaGraphLaunch(p->gexec, xs));
+  if (phi != p->uout) CK(cudaMemcpyAsync(phi, p->uout, P * 8, cudaMemcpyDeviceToDevice, xs));
+  CK(cudaMemcpyAsync(mean_slot, p->dmean, 8, cudaMemcpyDeviceToHost, xs));
+  CK(cudaMemcpyAsync(slot, p->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, xs));
+  return OT_OK;
+}
+
+static void graph_collect(ot_plan* p, const DevScalars* h, double mean, ot_stats* st) {
+  const long P = (long)p->N * p->M;
   st->status = h->status;
   st->newton_iters = h->newton_n;
   st->gmres_iters = h->gmres_iters_total;
@@ -923,8 +929,37 @@ static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, 
   st->min_det = h->min_det;
   st->mean_fn = h->mean_fn;
   st->res_l2 = sqrt(h->res_l2sum / (double)P);
+  st->phi_mean = mean;
   st->kernel_launches = (int32_t)(h->kcount + p->top_kernels);
   p->launches += h->kcount + p->top_kernels;
+}
+
+template <typename T>
+static int ensure_graph(ot_plan* p) {
+  if (!p->gexec || p->gkey_prec != p->precision || p->gkey_m != p->m ||
+      p->gkey_translate != p->translate)
+    return build_graph<T>(p);
+  return OT_OK;
+}
+
+template <typename T>
+static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
+                            ot_stats* st) {
+  ot_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  RET(ensure_graph<T>(p));
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, p->stream));
+  graph_scalars(p, p->hsc);
+  double mean = 0.0;
+  RET(graph_enqueue<T>(p, p->stream, f_in, g_in, phi, p->hsc, p->hsc, &st->phi_mean));
+  CK(cudaEventRecord(ev1, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  mean = st->phi_mean;
+  graph_collect(p, p->hsc, mean, st);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   st->ms_total = ms;
@@ -970,13 +1005,83 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
   return rc;
 }
 
+// Batched solve: every problem's graph is enqueued on the execution stream of its plan
+// (problems sharing a plan run back to back there; different plans run concurrently), and
+// the host synchronises once at the end.  Result slots are pinned host memory kept across
+// calls.
+static std::mutex g_batch_mutex;
+static DevScalars* g_batch_slots = nullptr;
+static double* g_batch_means = nullptr;
+static size_t g_batch_cap = 0;
+
 extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* f,
                                 const double* const* g, double* const* phi, ot_stats* stats) {
   if (count < 0 || (count > 0 && (!plans || !f || !g || !phi))) return OT_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (!plans[k] || !plans[k]->ready || !f[k] || !g[k] || !phi[k]) return OT_EINVAL;
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  if ((size_t)count > g_batch_cap) {
+    if (g_batch_slots) cudaFreeHost(g_batch_slots);
+    if (g_batch_means) cudaFreeHost(g_batch_means);
+    g_batch_slots = nullptr;
+    g_batch_means = nullptr;
+    g_batch_cap = 0;
+    CK(cudaMallocHost(&g_batch_slots, sizeof(DevScalars) * count));
+    CK(cudaMallocHost(&g_batch_means, sizeof(double) * count));
+    g_batch_cap = count;
+  }
+  std::vector<ot_plan*> uniq;
+  for (int k = 0; k < count; ++k) {
+    ot_plan* p = plans[k];
+    bool seen = false;
+    for (auto q : uniq) seen |= (q == p);
+    if (!seen) uniq.push_back(p);
+  }
+  // graphs, initial scalars and ordering after each plan's own stream
+  for (auto p : uniq) {
+    CK(cudaSetDevice(p->device));
+    if (!p->use_graph || p->profile) continue;
+    RET(p->precision ? ensure_graph<float>(p) : ensure_graph<double>(p));
+    graph_scalars(p, p->hinit);
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, p->stream));
+    CK(cudaStreamWaitEvent(p->cs[0], e, 0));
+    cudaEventDestroy(e);
+  }
   int first = OT_OK;
   for (int k = 0; k < count; ++k) {
-    int rc = ot_solve(plans[k], f[k], g[k], phi[k], stats ? &stats[k] : nullptr);
-    if (rc != OT_OK && first == OT_OK) first = rc;
+    ot_plan* p = plans[k];
+    CK(cudaSetDevice(p->device));
+    if (!p->use_graph || p->profile) {  // host-driven plans: one after another
+      ot_stats tmp;
+      int rc = ot_solve(p, f[k], g[k], phi[k], &tmp);
+      g_batch_slots[k].status = rc;
+      if (stats) stats[k] = tmp;
+      continue;
+    }
+    int rc = p->precision
+                 ? graph_enqueue<float>(p, p->cs[0], f[k], g[k], phi[k], p->hinit,
+                                        &g_batch_slots[k], &g_batch_means[k])
+                 : graph_enqueue<double>(p, p->cs[0], f[k], g[k], phi[k], p->hinit,
+                                         &g_batch_slots[k], &g_batch_means[k]);
+    if (rc != OT_OK) return rc;
+  }
+  for (auto p : uniq) {
+    CK(cudaSetDevice(p->device));
+    if (p->use_graph && !p->profile) CK(cudaStreamSynchronize(p->cs[0]));
+  }
+  for (int k = 0; k < count; ++k) {
+    ot_plan* p = plans[k];
+    if (p->use_graph && !p->profile) {
+      ot_stats tmp;
+      memset(&tmp, 0, sizeof(tmp));
+      graph_collect(p, &g_batch_slots[k], g_batch_means[k], &tmp);
+      if (stats) stats[k] = tmp;
+      if (tmp.status != OT_OK && first == OT_OK) first = tmp.status;
+    } else if (g_batch_slots[k].status != OT_OK && first == OT_OK) {
+      first = g_batch_slots[k].status;
+    }
   }
   return first;
 }

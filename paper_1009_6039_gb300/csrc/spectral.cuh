@@ -272,6 +272,7 @@ __device__ __forceinline__ void col_store(C2<T>* __restrict__ dst, const C2<T>* 
 template <typename T, int E, int MODE>
 __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
                       C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
+                      double inv_nm,
                       const C2<T>* __restrict__ twN, const C2<T>* __restrict__ twM,
                       const DevScalars* __restrict__ sc, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
   T ab[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) ab[a] = sc ? (T)sc->abar[a] : (T)0;
-  const T inv = (T)(1.0 / ((double)N * (double)M));
+  const T inv = (T)inv_nm;
   C2<T> s[E];
   if (active) {
 #pragma unroll
@@ -358,6 +359,31 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
       }
     }
     __syncthreads();
+    if (MODE == COL_MATVEC && p == 0) {
+      // column 0 of Q0 carries A' + i B' (k1 = 0 and k1 = M/2); replace B' by d11(M/2) B'
+      // with B'(k) = (S(k) - conj S(-k)) / (2i), before the inverse transform mixes them
+      C2<T> corr[E];
+      if (active && col == 0) {
+        const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
+        const T f = -qn * qn - (T)1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int k = t + e * TPT;
+          const C2<T> a = buf[k], b = buf[(N - k) % N];
+          // i (f) B' = (f / 2) (S - conj S(-k))
+          corr[e] = mk2<T>((T)0.5 * f * (a.x - b.x), (T)0.5 * f * (a.y + b.y));
+        }
+      }
+      __syncthreads();
+      if (active && col == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int k = t + e * TPT;
+          buf[k] = cadd<T>(buf[k], corr[e]);
+        }
+      }
+      __syncthreads();
+    }
     fft_smem<T, E, +1>(buf, N, t, active, twN);
     col_store<T, E>(p == 0 ? out0 : (p == 1 ? out1 : out2), sm, N, Lc, Q, col0);
     __syncthreads();
@@ -368,15 +394,18 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
 // Row complex-to-real inverse transforms (raw: sum over the full Hermitian spectrum).
 // ---------------------------------------------------------------------------------------
 // row symbol kinds: 0 = 1, 1 = d/dx = 2 pi i k1 (0 at Nyquist), 2 = d2/dx2 = -(2 pi k1)^2
+// (kind 2 expects a matvec Q0, whose packed Nyquist channel is premultiplied)
 template <typename T>
 __device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int L, int kind) {
   const T tp = (T)OTGB_TWO_PI;
   if (kind == 0) return X;
   if (k == 0) {
-    // packed (X0, XL): k1 = 0 and k1 = M/2 (Nyquist)
+    // packed (X0, XL): k1 = 0 and k1 = M/2 (Nyquist).  For d2/dx2 the Nyquist channel of
+    // Q0 already carries the factor -(2 pi M/2)^2: the column pass applies it before its
+    // inverse transform (see k_col), so that the two channels sharing one complex column
+    // have comparable magnitudes.
     if (kind == 1) return mk2<T>((T)0, (T)0);
-    const T qn = tp * (T)L;  // 2 pi (M/2)
-    return mk2<T>((T)0, -qn * qn * X.y);
+    return mk2<T>((T)0, X.y);
   }
   const T q = tp * (T)k;
   if (kind == 1) return mk2<T>(-q * X.y, q * X.x);
@@ -517,6 +546,7 @@ template <typename T, int E>
 __global__ void __launch_bounds__(OTGB_PAR_THREADS)
     k_col_matvec_par(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
                      C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
+                     double inv_nm,
                      const C2<T>* __restrict__ twN, const DevScalars* __restrict__ sc,
                      const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -539,42 +569,43 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   T ab[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) ab[a] = (T)sc->abar[a];
-  const T inv = (T)(1.0 / ((double)N * (double)M));
-  C2<T> s[E];
+  const T inv = (T)inv_nm;
+  // Q1 and Q2 go to their own buffers at once; Q0 (written over the spectrum that the
+  // partner reads of column 0 still need) is held in registers until after the barrier.
+  // Column 0's Q0 carries the Nyquist channel premultiplied by d11(M/2) = -(2 pi M/2)^2
+  // so that the two channels sharing the complex column have comparable magnitudes.
+  C2<T> s0[E];
   const bool lead = active && grp == 0;
   if (lead) {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k = t + e * TPT;
-      bool nyq2;
-      const int k2 = sfreq(k, N, &nyq2);
-      C2<T> z = b0[k], r;
-      if (col == 0) {
-        C2<T> pz = b0[(N - k) % N];
-        C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
-        C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
-        A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
-        B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
-        r = mk2<T>(A.x - B.y, A.y + B.x);
-      } else {
-        r = cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z);
-      }
-      s[e] = cscale<T>(r, inv);
-    }
-  }
-  __syncthreads();
-  if (lead) {
+    const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = t + e * TPT;
       bool nyq2;
       const int k2 = sfreq(k, N, &nyq2);
       const T q2 = (T)OTGB_TWO_PI * (T)k2;
-      const C2<T> v = s[e];
-      b0[k] = v;
+      C2<T> z = b0[k], v;
+      if (col == 0) {
+        C2<T> pz = b0[(N - k) % N];
+        C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
+        C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
+        A = cscale<T>(cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A), inv);
+        B = cscale<T>(cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B), inv);
+        v = mk2<T>(A.x - B.y, A.y + B.x);
+        const C2<T> Bn = cscale<T>(B, -qn * qn);
+        s0[e] = mk2<T>(A.x - Bn.y, A.y + Bn.x);
+      } else {
+        v = cscale<T>(cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z), inv);
+        s0[e] = v;
+      }
       b0[stride + k] = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
       b0[2 * stride + k] = cscale<T>(v, -q2 * q2);
     }
+  }
+  __syncthreads();
+  if (lead) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) b0[t + e * TPT] = s0[e];
   }
   __syncthreads();
   fft_smem<T, E, +1>(buf, N, t, active, twN);
@@ -695,7 +726,8 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
-      spec, o0, o1, o2, N, M, Q, (const C2<T>*)tb.twN, (const C2<T>*)tb.twM, sc, skip);
+      spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN,
+      (const C2<T>*)tb.twM, sc, skip);
   return cudaGetLastError();
 }
 
@@ -739,7 +771,8 @@ cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2,
   cudaError_t e = set_smem(k_col_matvec_par<T, E>, sm);
   if (e != cudaSuccess) return e;
   k_col_matvec_par<T, E><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
-      spec, o0, o1, o2, N, M, Q, (const C2<T>*)tb.twN, sc, skip);
+      spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
+      skip);
   return cudaGetLastError();
 }
 
