@@ -67,6 +67,10 @@ extern "C" {
                                    synchronises once per GMRES cycle and per Newton step */
 #define OT_OPT_REORTH 13        /* 0 (default): one classical Gram-Schmidt pass per Arnoldi
                                    step; 1: two passes (reorthogonalisation) */
+#define OT_OPT_THETA_FP64 14    /* mixed mode only: 1 (default) recovers theta = Lbar^{-1}
+                                   sigma and forms the update in FP64 (FP32 round-off in theta
+                                   is amplified ~M^2 by the stencils at the grid scale and
+                                   slows the Newton tail); 0: in FP32 */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

@@ -20,6 +20,7 @@ OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED
 OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
+OT_OPT_THETA_FP64 = 14
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other"]
 
@@ -194,7 +195,8 @@ class Plan:
              "max_restarts": OT_OPT_MAX_RESTARTS, "precision": OT_OPT_PRECISION,
              "safeguard": OT_OPT_SAFEGUARD, "translate": OT_OPT_TRANSLATE,
              "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL,
-             "profile": OT_OPT_PROFILE, "graph": OT_OPT_GRAPH, "reorth": OT_OPT_REORTH}
+             "profile": OT_OPT_PROFILE, "graph": OT_OPT_GRAPH, "reorth": OT_OPT_REORTH,
+             "theta_fp64": OT_OPT_THETA_FP64}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

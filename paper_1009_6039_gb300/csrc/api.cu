@@ -24,6 +24,7 @@ struct ot_plan {
   int max_newton = 200, max_restarts = 50;
   int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
   int reorth = 0;  // Gram-Schmidt passes - 1 (OT_OPT_REORTH)
+  int theta64 = 1;  // mixed mode: theta = Lbar^{-1} sigma and the update in FP64
   cudaStream_t stream = 0;
   int device = 0;
   // FP64 planes
@@ -379,6 +380,11 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       p->reorth = (int)v;
       free_graph(p);
       return OT_OK;
+    case OT_OPT_THETA_FP64:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->theta64 = (int)v;
+      free_graph(p);
+      return OT_OK;
   }
   return OT_EINVAL;
 }
@@ -414,9 +420,17 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
                                  (const T*)p->coef, (T*)p->w, nullptr, nullptr, 0.0, 1.0, N, M,
                                  tb, nullptr, p->stream);
       case OT_PROF_COL_LBARINV:
+        if (sizeof(T) == 4 && p->theta64)  // theta passes run in FP64 in this mode
+          return launch_col<double>(COL_LBARINV, (C2<double>*)p->spec64, (C2<double>*)p->q64,
+                                    nullptr, nullptr, N, M, p->tb64, p->sc, nullptr,
+                                    p->stream);
         return launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N,
                              M, tb, p->sc, nullptr, p->stream);
       case OT_PROF_ROW_C2R_UPDATE:
+        if (sizeof(T) == 4 && p->theta64)
+          return launch_row_c2r<double>(ROWINV_UPDATE, (C2<double>*)p->q64, nullptr, nullptr,
+                                        nullptr, nullptr, p->u, p->ucand, 0.5, 1.0, N, M,
+                                        p->tb64, nullptr, p->stream);
         return launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr,
                                  nullptr, p->u, p->ucand, 0.5, 1.0, N, M, tb, nullptr,
                                  p->stream);
@@ -547,6 +561,47 @@ static int run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* 
   return OT_OK;
 }
 
+// Newton update candidate u_out = u_in + s Lbar^{-1} sigma.  sc_driven: s and the buffer
+// pair come from the device scalars (graph); otherwise the host passes them.  In the mixed
+// mode with theta64 the three transform passes of theta run in FP64: theta is added to the
+// FP64 iterate, and FP32 round-off in theta is white noise that the fourth-order stencils
+// amplify by ~M^2 at the grid scale, where the Newton iteration damps it only slowly.
+template <typename T>
+static int run_theta(ot_plan* p, const double* u_in, double* u_out, double step,
+                     bool sc_driven) {
+  const DevScalars* scp = sc_driven ? p->sc : nullptr;
+  if (sizeof(T) == 4 && p->theta64) {
+    const long P = (long)p->N * p->M;
+    double* s64 = p->uout;  // free until the final gauge
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_convert<float>(p->sigma, 0, s64, 1, P, p->stream));
+    C2<double>* sp = (C2<double>*)p->spec64;
+    C2<double>* qq = (C2<double>*)p->q64;
+    LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+           launch_row_r2c<double>(s64, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
+                                  p->stream));
+    LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+           launch_col<double>(COL_LBARINV, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64,
+                              p->sc, nullptr, p->stream));
+    LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+           launch_row_c2r<double>(ROWINV_UPDATE, qq, nullptr, nullptr, nullptr, nullptr, u_in,
+                                  u_out, step, 1.0, p->N, p->M, p->tb64, nullptr, p->stream,
+                                  scp));
+    return OT_OK;
+  }
+  const SpecTables& tb = tables<T>(p);
+  LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+         launch_row_r2c<T>((const T*)p->sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, p->N,
+                           p->M, tb, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+         launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, p->N,
+                       p->M, tb, p->sc, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+         launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
+                           u_in, u_out, step, 1.0, p->N, p->M, tb, nullptr, p->stream, scp));
+  return OT_OK;
+}
+
 // One Arnoldi step j on the device: w = A v_j, Gram-Schmidt against V_0..V_j (classical,
 // once or twice), norm, Givens rotation (in the last block of the final update).
 template <typename T>
@@ -672,7 +727,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     st->gmres_cycles += p->hsc->cycles;
     bool accepted = false;
     for (;;) {
-      RET(run_lbar_inv<T>(p, (const T*)p->sigma, p->u, p->ucand, s, nullptr));
+      RET(run_theta<T>(p, p->u, p->ucand, s, false));
       LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
              launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
       RET(read_scalars(p));
@@ -764,18 +819,12 @@ template <typename T>
 static int capture_candidate(ot_plan* p) {
   const SpecTables& tb = tables<T>(p);
   const int N = p->N, M = p->M;
-  LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
-         launch_row_r2c<T>((const T*)p->sigma, 0, nullptr, nullptr, (C2<T>*)p->spec, N, M, tb,
-                           nullptr, p->stream));
-  LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
-         launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N, M,
-                       tb, p->sc, nullptr, p->stream));
-  LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
-         launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr, nullptr,
-                           p->u, p->ucand, 1.0, 1.0, N, M, tb, nullptr, p->stream, p->sc));
+  RET(run_theta<T>(p, p->u, p->ucand, 1.0, true));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 1, c32_for<T>(p)));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_ctl(CTL_ACCEPT, p->sc, p->stream,
+                    (sizeof(T) == 4 && p->theta64) ? 6 : 5));
   return OT_OK;
 }
 

@@ -120,10 +120,14 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
   __syncthreads();
   if (active) {
     const int tstep = L / (Ns * R);
+    // Ns = 2^a or 3 * 2^a: j / Ns by a shift (and a division by the constant 3)
+    const int a = __ffs(Ns) - 1;
+    const bool pow2 = (Ns >> a) == 1;
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
       const int j = t + b * TPT;
-      const int k = j % Ns;
+      const int qd = pow2 ? (j >> a) : ((j >> a) / 3);
+      const int k = j - qd * Ns;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         C2<T> w = tw[k * r * tstep];
@@ -131,7 +135,7 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
         v[b * R + r] = cmul<T>(v[b * R + r], w);
       }
       Bfly<T, R, SIGN>::run(&v[b * R]);
-      const int d = (j / Ns) * Ns * R + k;
+      const int d = qd * Ns * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r) buf[d + r * Ns] = v[b * R + r];
     }
@@ -249,11 +253,13 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __res
 // ---------------------------------------------------------------------------------------
 // Column transforms with the spectral multiplies of Strain's method.
 // ---------------------------------------------------------------------------------------
+// Q (columns per block) is a power of two
 template <typename T, int E>
 __device__ __forceinline__ void col_load(const C2<T>* __restrict__ src, C2<T>* sm, int N,
                                          int Lc, int Q, int col0) {
+  const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
-    const int n = idx / Q, q = idx % Q;
+    const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
     if (col < Lc) sm[q * (N + 1) + n] = src[(size_t)n * Lc + col];
   }
@@ -262,8 +268,9 @@ __device__ __forceinline__ void col_load(const C2<T>* __restrict__ src, C2<T>* s
 template <typename T, int E>
 __device__ __forceinline__ void col_store(C2<T>* __restrict__ dst, const C2<T>* sm, int N,
                                           int Lc, int Q, int col0) {
+  const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
-    const int n = idx / Q, q = idx % Q;
+    const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
     if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * (N + 1) + n];
   }
@@ -560,8 +567,9 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   const int stride = Q * (N + 1);  // one group's buffers
   C2<T>* buf = sm + grp * stride + q * (N + 1);
   C2<T>* b0 = sm + q * (N + 1);
+  const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
-    const int n = idx / Q, qq = idx - n * Q;
+    const int n = idx >> lq, qq = idx & (Q - 1);
     if (col0 + qq < Lc) sm[qq * (N + 1) + n] = spec[(size_t)n * Lc + col0 + qq];
   }
   __syncthreads();
@@ -609,12 +617,12 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   }
   __syncthreads();
   fft_smem<T, E, +1>(buf, N, t, active, twN);
-  for (int idx = threadIdx.x; idx < 3 * Q * N; idx += blockDim.x) {
-    const int g = idx / (Q * N), r2 = idx - g * Q * N;
-    const int n = r2 / Q, qq = r2 - n * Q;
-    if (col0 + qq < Lc) {
-      C2<T>* dst = g == 0 ? out0 : (g == 1 ? out1 : out2);
-      dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * (N + 1) + n];
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    C2<T>* dst = g == 0 ? out0 : (g == 1 ? out1 : out2);
+    for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+      const int n = idx >> lq, qq = idx & (Q - 1);
+      if (col0 + qq < Lc) dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * (N + 1) + n];
     }
   }
 }
@@ -637,8 +645,10 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   const bool active = row < N;
   const int stride = RB * (L + 1);
   C2<T>* buf = sm + grp * stride + q * (L + 1);
+  const int la = __ffs(L) - 1;
+  const bool lp2 = (L >> la) == 1;
   for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
-    const int qq = idx / L, k = idx - qq * L;
+    const int qq = lp2 ? (idx >> la) : ((idx >> la) / 3), k = idx - qq * L;
     if (row0 + qq < N) {
       const size_t o = (size_t)(row0 + qq) * L + k;
       const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
@@ -655,7 +665,7 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   fft_smem<T, E, +1>(buf, L, t, active, twL);
   const size_t P = (size_t)N * M;
   for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
-    const int qq = idx / L, n = idx - qq * L;
+    const int qq = lp2 ? (idx >> la) : ((idx >> la) / 3), n = idx - qq * L;
     const int r = row0 + qq;
     if (r < N) {
       const size_t o = (size_t)r * M;
@@ -806,9 +816,8 @@ cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                               T* out, int N, int M, const SpecTables& tb, const int* skip,
                               cudaStream_t st) {
   const int L = M / 2, TPT = L / E;
-  int RB = OTGB_PAR_THREADS / (5 * TPT);
-  if (RB < 1) RB = 1;
-  if (RB > 8) RB = 8;
+  int RB = 1;
+  while (RB * 2 * 5 * TPT <= OTGB_PAR_THREADS && RB < 8) RB *= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)5 * RB * (L + 1) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_combine_par<T, E>, sm);
