@@ -420,10 +420,9 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
                                  (const T*)p->coef, (T*)p->w, nullptr, nullptr, 0.0, 1.0, N, M,
                                  tb, nullptr, p->stream);
       case OT_PROF_COL_LBARINV:
-        if (sizeof(T) == 4 && p->theta64)  // theta passes run in FP64 in this mode
-          return launch_col<double>(COL_LBARINV, (C2<double>*)p->spec64, (C2<double>*)p->q64,
-                                    nullptr, nullptr, N, M, p->tb64, p->sc, nullptr,
-                                    p->stream);
+        if (sizeof(T) == 4 && p->theta64)  // FP32 forward / FP64 inverse in this mode
+          return launch_col_lbarinv_mixed((const float2*)p->spec, (double2*)p->q64, N, M,
+                                          p->tb32, p->tb64, p->sc, p->stream);
         return launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N,
                              M, tb, p->sc, nullptr, p->stream);
       case OT_PROF_ROW_C2R_UPDATE:
@@ -571,18 +570,14 @@ static int run_theta(ot_plan* p, const double* u_in, double* u_out, double step,
                      bool sc_driven) {
   const DevScalars* scp = sc_driven ? p->sc : nullptr;
   if (sizeof(T) == 4 && p->theta64) {
-    const long P = (long)p->N * p->M;
-    double* s64 = p->uout;  // free until the final gauge
-    LAUNCH(p, OT_PROF_OTHER, -1, 1,
-           launch_convert<float>(p->sigma, 0, s64, 1, P, p->stream));
-    C2<double>* sp = (C2<double>*)p->spec64;
     C2<double>* qq = (C2<double>*)p->q64;
     LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
-           launch_row_r2c<double>(s64, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
-                                  p->stream));
+           launch_row_r2c<float>((const float*)p->sigma, 0, nullptr, nullptr,
+                                 (C2<float>*)p->spec, p->N, p->M, p->tb32, nullptr,
+                                 p->stream));
     LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
-           launch_col<double>(COL_LBARINV, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64,
-                              p->sc, nullptr, p->stream));
+           launch_col_lbarinv_mixed((const float2*)p->spec, (double2*)qq, p->N, p->M,
+                                    p->tb32, p->tb64, p->sc, p->stream));
     LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
            launch_row_c2r<double>(ROWINV_UPDATE, qq, nullptr, nullptr, nullptr, nullptr, u_in,
                                   u_out, step, 1.0, p->N, p->M, p->tb64, nullptr, p->stream,
@@ -823,8 +818,7 @@ static int capture_candidate(ot_plan* p) {
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 1, c32_for<T>(p)));
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_ctl(CTL_ACCEPT, p->sc, p->stream,
-                    (sizeof(T) == 4 && p->theta64) ? 6 : 5));
+         launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
   return OT_OK;
 }
 

@@ -93,6 +93,11 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
                            double step, double out_scale, int N, int M, const SpecTables& tb,
                            const int* skip, cudaStream_t st, const DevScalars* sc = nullptr);
 
+// theta = Lbar^{-1} sigma column pass, FP32 forward / FP64 inverse (mixed mode)
+cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, int M,
+                                     const SpecTables& tb32, const SpecTables& tb64,
+                                     const DevScalars* sc, cudaStream_t st);
+
 // Residual / coefficients, input translation ------------------------------------------
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,

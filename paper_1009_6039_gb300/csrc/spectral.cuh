@@ -687,6 +687,72 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
 }
 
 // ---------------------------------------------------------------------------------------
+// Column pass of theta = Lbar^{-1} sigma for the mixed mode: the forward column FFT and the
+// rho-bar multiply in FP32 (their round-off is damped by rho-bar ~ 1/k^2), the inverse
+// column FFT in FP64 into an FP64 Q0 for the FP64 row pass that forms the update.  FP32
+// round-off in those last passes would be white noise in theta, which the fourth-order
+// stencils amplify by ~M^2 at the grid scale.
+// ---------------------------------------------------------------------------------------
+template <int E>
+__global__ void __launch_bounds__(256)
+    k_col_lbarinv_mixed(const float2* __restrict__ spec, double2* __restrict__ out, int N,
+                        int M, int Q, double inv_nm, const float2* __restrict__ twN32,
+                        const double2* __restrict__ twN64, const DevScalars* __restrict__ sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sm = reinterpret_cast<double2*>(smem_raw);
+  const int Lc = M / 2, TPT = N / E;
+  const int q = threadIdx.x / TPT, t = threadIdx.x - q * TPT;
+  const int col0 = blockIdx.x * Q, col = col0 + q;
+  const bool active = (q < Q) && (col < Lc);
+  double2* db = sm + q * (N + 1);
+  float2* fb = reinterpret_cast<float2*>(db);  // FP32 phase uses the first half
+  const int lq = __ffs(Q) - 1;
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx >> lq, qq = idx & (Q - 1);
+    if (col0 + qq < Lc)
+      reinterpret_cast<float2*>(sm + qq * (N + 1))[n] = spec[(size_t)n * Lc + col0 + qq];
+  }
+  __syncthreads();
+  fft_smem<float, E, -1>(fb, N, t, active, twN32);
+  float ab[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
+  const float inv = (float)inv_nm;
+  double2 s[E];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      float2 z = fb[k], r;
+      if (col == 0) {
+        float2 pz = fb[(N - k) % N];
+        float2 A = mk2<float>(0.5f * (z.x + pz.x), 0.5f * (z.y - pz.y));
+        float2 B = mk2<float>(0.5f * (z.y + pz.y), -0.5f * (z.x - pz.x));
+        A = cmul<float>(rho_bar<float>(ab, 0, false, k2, nyq2), A);
+        B = cmul<float>(rho_bar<float>(ab, M / 2, true, k2, nyq2), B);
+        r = mk2<float>(A.x - B.y, A.y + B.x);
+      } else {
+        r = cmul<float>(rho_bar<float>(ab, col, false, k2, nyq2), z);
+      }
+      s[e] = mk2<double>((double)(r.x * inv), (double)(r.y * inv));
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) db[t + e * TPT] = s[e];
+  }
+  __syncthreads();
+  fft_smem<double, E, +1>(db, N, t, active, twN64);
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx >> lq, qq = idx & (Q - 1);
+    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * (N + 1) + n];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------------------
 inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
@@ -858,6 +924,24 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
                                    tb, skip, st, sc);
   return row_c2r_dispatch<T, 8>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M, tb,
                                 skip, st, sc);
+}
+
+template <int E>
+cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
+                                const SpecTables& tb32, const SpecTables& tb64,
+                                const DevScalars* sc, cudaStream_t st) {
+  const int Lc = M / 2, TPT = N / E;
+  int Q = 256 / TPT;
+  if (Q < 1) Q = 1;
+  while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
+  if (Q > Lc) Q = Lc;
+  const size_t sm = (size_t)Q * (N + 1) * sizeof(double2);
+  cudaError_t e = set_smem(k_col_lbarinv_mixed<E>, sm);
+  if (e != cudaSuccess) return e;
+  k_col_lbarinv_mixed<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+      spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
+      (const double2*)tb64.twN, sc);
+  return cudaGetLastError();
 }
 
 #define OTGB_INSTANTIATE_SPECTRAL(T)                                                         \
