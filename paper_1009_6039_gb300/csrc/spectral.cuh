@@ -172,6 +172,171 @@ __device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Warp-synchronous transforms for power-of-two lengths L <= 2048 (FP32 passes).  A thread
+// holds W = 32 elements; the L/32 threads of one transform are at most one warp for
+// L <= 1024 (synchronised with __syncwarp) and two warps for L = 2048 (a named barrier per
+// transform pair).  Stages: radix 32, then the remaining factor (32, 16, 8, 4 or 2),
+// each one shared-memory round trip.  Shared memory is padded by one element per 32 so
+// the stride-32 patterns of the stages hit distinct banks.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+// Twiddle load that the compiler may not hoist out of loops (a hoisted set of butterfly
+// twiddles would occupy ~80 registers across the output loop of the column pass).
+template <typename T> __device__ __forceinline__ C2<T> ldtw(const C2<T>* p);
+template <> __device__ __forceinline__ float2 ldtw<float>(const float2* p) {
+  float2 r;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
+template <> __device__ __forceinline__ double2 ldtw<double>(const double2* p) {
+  double2 r;
+  asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+  return r;
+}
+
+// radix-16 DFT as 4 x 4 with internal twiddles W16^t = tw[t * step16]
+template <typename T, int SIGN> struct Bfly16 {
+  __device__ __forceinline__ static void run(C2<T>* v, const C2<T>* __restrict__ tw,
+                                             int step16) {
+    C2<T> a[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+      C2<T> x[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+      Bfly<T, 4, SIGN>::run(x);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        if (n1 * k1 == 0) {
+          a[n1][k1] = x[k1];
+        } else {
+          C2<T> w = ldtw<T>(tw + (n1 * k1) * step16);
+          if (SIGN > 0) w.y = -w.y;
+          a[n1][k1] = cmul<T>(x[k1], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C2<T> x[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      Bfly<T, 4, SIGN>::run(x);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = x[k2];
+    }
+  }
+};
+
+// radix-32 DFT as 8 x 4: X[k1 + 4 k2] = sum_n1 W8^{n1 k2} W32^{n1 k1} (DFT4 of v[n1 + 8m])
+template <typename T, int SIGN> struct Bfly32 {
+  __device__ __forceinline__ static void run(C2<T>* v, const C2<T>* __restrict__ tw,
+                                             int step32) {
+    C2<T> a[8][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) {
+      C2<T> x[4] = {v[n1], v[n1 + 8], v[n1 + 16], v[n1 + 24]};
+      Bfly<T, 4, SIGN>::run(x);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) {
+        if (n1 * k1 == 0) {
+          a[n1][k1] = x[k1];
+        } else {
+          C2<T> w = ldtw<T>(tw + (n1 * k1) * step32);
+          if (SIGN > 0) w.y = -w.y;
+          a[n1][k1] = cmul<T>(x[k1], w);
+        }
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C2<T> x[8];
+#pragma unroll
+      for (int n1 = 0; n1 < 8; ++n1) x[n1] = a[n1][k1];
+      Bfly<T, 8, SIGN>::run(x);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) v[k1 + 4 * k2] = x[k2];
+    }
+  }
+};
+
+// synchronisation of the threads of one transform (TPT = L/32 threads, aligned groups)
+__device__ __forceinline__ void wsync(int TPT) {
+  if (TPT <= 32) {
+    __syncwarp();
+  } else {
+    // two warps per transform (L = 2048): named barrier 1 + pair index
+    const int id = 1 + (threadIdx.x >> 6);
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(64) : "memory");
+  }
+}
+
+// One stage of radix R (W = 32 elements per thread, W/R butterflies) on padded buf.
+template <typename T, int R, int SIGN>
+__device__ __forceinline__ void wstage(C2<T>* buf, int L, int Ns, int t, bool active,
+                                       const C2<T>* __restrict__ tw) {
+  constexpr int W = 32;
+  const int TPT = L / W;
+  const int LR = L / R;
+  C2<T> v[W];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < W / R; ++b) {
+      const int j = t + b * TPT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b * R + r] = buf[pad32(j + r * LR)];
+    }
+  }
+  wsync(TPT);
+  if (active) {
+    const int tstep = L / (Ns * R);
+    const int a = __ffs(Ns) - 1;
+#pragma unroll
+    for (int b = 0; b < W / R; ++b) {
+      const int j = t + b * TPT;
+      const int qd = j >> a;
+      const int k = j - (qd << a);
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C2<T> w = ldtw<T>(tw + k * r * tstep);
+          if (SIGN > 0) w.y = -w.y;
+          v[b * R + r] = cmul<T>(v[b * R + r], w);
+        }
+      }
+      if (R == 32)
+        Bfly32<T, SIGN>::run(&v[b * R], tw, L / 32);
+      else if (R == 16)
+        Bfly16<T, SIGN>::run(&v[b * R], tw, L / 16);
+      else
+        Bfly<T, (R == 8 ? 8 : (R == 4 ? 4 : 2)), SIGN>::run(&v[b * R]);
+      const int d = qd * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad32(d + r * Ns)] = v[b * R + r];
+    }
+  }
+  wsync(TPT);
+}
+
+// Full transform of a power-of-two length 32 <= L <= 2048, in place in padded buf.
+template <typename T, int SIGN>
+__device__ __forceinline__ void fft_warp(C2<T>* buf, int L, int t, bool active,
+                                         const C2<T>* __restrict__ tw) {
+  wstage<T, 32, SIGN>(buf, L, 1, t, active, tw);
+  int rem = L / 32, Ns = 32;
+  if (rem >= 32) {
+    wstage<T, 32, SIGN>(buf, L, Ns, t, active, tw);
+    rem /= 32;
+    Ns *= 32;
+  }
+  if (rem == 16) wstage<T, 16, SIGN>(buf, L, Ns, t, active, tw);
+  else if (rem == 8) wstage<T, 8, SIGN>(buf, L, Ns, t, active, tw);
+  else if (rem == 4) wstage<T, 4, SIGN>(buf, L, Ns, t, active, tw);
+  else if (rem == 2) wstage<T, 2, SIGN>(buf, L, Ns, t, active, tw);
+}
+
+__host__ __device__ inline bool warp_fft_ok(int L) {
+  return L >= 32 && L <= 2048 && (L & (L - 1)) == 0;
+}
+
 // signed frequency of index n of length L, with a Nyquist flag
 __device__ __forceinline__ int sfreq(int n, int L, bool* nyq) {
   *nyq = (2 * n == L);
@@ -753,6 +918,217 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------------------
+// Warp-FFT versions of the three matvec passes (FP32, power-of-two lengths).  Each thread
+// holds 32 elements of one transform; the threads of a transform are one warp (or part of
+// one) for lengths up to 1024, so its stages synchronise with __syncwarp.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_row_r2c_w(const T* __restrict__ xbase, size_t x_stride, const int* __restrict__ jptr,
+                const double* __restrict__ scale, C2<T>* __restrict__ spec, int N, int M,
+                int RB, const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
+                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int L = M / 2, TPT = L / 32, LP = L + L / 32;
+  const int q = threadIdx.x / TPT, t = threadIdx.x - q * TPT;
+  const int row = blockIdx.x * RB + q;
+  const bool active = row < N;
+  C2<T>* buf = sm + q * LP;
+  const int jv = jptr ? *jptr : 0;
+  const T* x = xbase + (size_t)jv * x_stride;
+  const T sc = scale ? (T)scale[jv] : (T)1;
+  if (active) {
+    const C2<T>* xr = reinterpret_cast<const C2<T>*>(x + (size_t)row * M);
+#pragma unroll 8
+    for (int e = 0; e < 32; ++e) {
+      const int n = t + e * TPT;
+      const C2<T> z = xr[n];
+      buf[pad32(n)] = mk2<T>(z.x * sc, z.y * sc);
+    }
+  }
+  wsync(TPT);
+  fft_warp<T, -1>(buf, L, t, active, twL);
+  if (active) {
+    C2<T>* out = spec + (size_t)row * L;
+    for (int k = t; k <= L / 2; k += TPT) {
+      if (k == 0) {
+        const C2<T> z = buf[0];
+        out[0] = mk2<T>(z.x + z.y, z.x - z.y);
+      } else {
+        const C2<T> zk = buf[pad32(k)], zm = buf[pad32(L - k)];
+        const C2<T> Ev = mk2<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+        const C2<T> Ov = mk2<T>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+        const C2<T> wo = cmul<T>(twM[k], Ov);
+        out[k] = cadd<T>(Ev, wo);
+        if (2 * k != L) out[L - k] = cconj<T>(csub<T>(Ev, wo));
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(384)
+    k_col_matvec_w(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
+                   C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
+                   double inv_nm, const C2<T>* __restrict__ twN,
+                   const DevScalars* __restrict__ sc, const int* __restrict__ skip) {
+  // threads: 3 groups (outputs Q0, Q1, Q2) x Q columns x N/32 threads per transform;
+  // buffers [group][column][N + N/32]; group 0's buffer first holds the forward transform
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int Lc = M / 2, TPT = N / 32, NP = N + N / 32, G = Q * TPT;
+  const int grp = threadIdx.x / G, rem = threadIdx.x - grp * G;
+  const int q = rem / TPT, t = rem - q * TPT;
+  const int col0 = blockIdx.x * Q, col = col0 + q;
+  const bool active = col < Lc;
+  const int stride = Q * NP;
+  C2<T>* b0 = sm + q * NP;
+  C2<T>* buf = b0 + grp * stride;
+  const int lq = __ffs(Q) - 1;
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx >> lq, qq = idx & (Q - 1);
+    if (col0 + qq < Lc) sm[qq * NP + pad32(n)] = spec[(size_t)n * Lc + col0 + qq];
+  }
+  __syncthreads();
+  fft_warp<T, -1>(b0, N, t, active && grp == 0, twN);
+  __syncthreads();
+  T ab[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ab[a] = (T)sc->abar[a];
+  const T inv = (T)inv_nm;
+  const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
+  // every group forms S = rho-bar sigma-hat / (N M) and its own symbol; groups 1 and 2
+  // write at once, group 0 (which overwrites the spectrum) after the barrier.  Column 0 of
+  // Q0 carries its Nyquist channel times d11(M/2), so that the two channels sharing the
+  // complex column have comparable magnitudes through the inverse transform.
+  C2<T> s0[32];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      const T q2 = (T)OTGB_TWO_PI * (T)k2;
+      const C2<T> z = b0[pad32(k)];
+      C2<T> v;
+      if (col == 0) {
+        const C2<T> pz = b0[pad32((N - k) & (N - 1))];
+        C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
+        C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
+        A = cscale<T>(cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A), inv);
+        B = cscale<T>(cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B), inv);
+        if (grp == 0) B = cscale<T>(B, -qn * qn);
+        v = mk2<T>(A.x - B.y, A.y + B.x);
+      } else {
+        v = cscale<T>(cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z), inv);
+      }
+      if (grp == 1) v = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
+      else if (grp == 2) v = cscale<T>(v, -q2 * q2);
+      if (grp == 0) s0[e] = v;
+      else buf[pad32(k)] = v;
+    }
+  }
+  __syncthreads();
+  if (active && grp == 0) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e) buf[pad32(t + e * TPT)] = s0[e];
+  }
+  __syncthreads();
+  fft_warp<T, +1>(buf, N, t, active, twN);
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    C2<T>* dst = g == 0 ? out0 : (g == 1 ? out1 : out2);
+    for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+      const int n = idx >> lq, qq = idx & (Q - 1);
+      if (col0 + qq < Lc) dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * NP + pad32(n)];
+    }
+  }
+}
+
+// c2r pre-processing on a padded row buffer (threads of one transform)
+template <typename T>
+__device__ __forceinline__ void c2r_pre_w(C2<T>* buf, int L, int t, int TPT, bool active,
+                                          const C2<T>* __restrict__ twM) {
+  if (active) {
+    for (int k = t; k <= L / 2; k += TPT) {
+      if (k == 0) {
+        const C2<T> x = buf[0];
+        buf[0] = mk2<T>(x.x + x.y, x.x - x.y);
+      } else {
+        const C2<T> xk = buf[pad32(k)], xm = buf[pad32(L - k)];
+        const C2<T> Ev = mk2<T>(xk.x + xm.x, xk.y - xm.y);
+        const C2<T> dv = mk2<T>(xk.x - xm.x, xk.y + xm.y);
+        const C2<T> Ov = cmul<T>(dv, cconj<T>(twM[k]));
+        buf[pad32(k)] = mk2<T>(Ev.x - Ov.y, Ev.y + Ov.x);
+        if (2 * k != L) buf[pad32(L - k)] = mk2<T>(Ev.x + Ov.y, -Ev.y + Ov.x);
+      }
+    }
+  }
+  wsync(TPT);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(320)
+    k_row_combine_w(const C2<T>* __restrict__ q0, const C2<T>* __restrict__ q1,
+                    const C2<T>* __restrict__ q2, const T* __restrict__ coef,
+                    T* __restrict__ out, int N, int M, int RB, const C2<T>* __restrict__ twL,
+                    const C2<T>* __restrict__ twM, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
+  const int L = M / 2, TPT = L / 32, LP = L + L / 32;
+  // transform index: (term, row) = (g / RB, g % RB); buffers [term][row][LP]
+  const int g = threadIdx.x / TPT, t = threadIdx.x - g * TPT;
+  const int term = g / RB, q = g - term * RB;
+  const int row0 = blockIdx.x * RB, row = row0 + q;
+  const bool active = row < N;
+  const int stride = RB * LP;
+  C2<T>* buf = sm + term * stride + q * LP;
+  const int la = __ffs(L) - 1;
+  for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
+    const int qq = idx >> la, k = idx & (L - 1);
+    if (row0 + qq < N) {
+      const size_t o = (size_t)(row0 + qq) * L + k;
+      const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
+      C2<T>* b = sm + qq * LP + pad32(k);
+      b[0] = row_symbol_apply<T>(x0, k, L, 2);
+      b[stride] = row_symbol_apply<T>(x0, k, L, 1);
+      b[2 * stride] = row_symbol_apply<T>(x1, k, L, 1);
+      b[3 * stride] = x1;
+      b[4 * stride] = x2;
+    }
+  }
+  __syncthreads();
+  c2r_pre_w<T>(buf, L, t, TPT, active, twM);
+  fft_warp<T, +1>(buf, L, t, active, twL);
+  __syncthreads();
+  const size_t P = (size_t)N * M;
+  for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
+    const int qq = idx >> la, n = idx & (L - 1);
+    const int r = row0 + qq;
+    if (r < N) {
+      const size_t o = (size_t)r * M;
+      const C2<T>* b = sm + qq * LP + pad32(n);
+      const C2<T> y0 = b[0], y1 = b[stride], y2 = b[2 * stride], y3 = b[3 * stride],
+                  y4 = b[4 * stride];
+      const C2<T> a11 = reinterpret_cast<const C2<T>*>(coef + o)[n];
+      const C2<T> a12 = reinterpret_cast<const C2<T>*>(coef + P + o)[n];
+      const C2<T> a22 = reinterpret_cast<const C2<T>*>(coef + 2 * P + o)[n];
+      const C2<T> b1 = reinterpret_cast<const C2<T>*>(coef + 3 * P + o)[n];
+      const C2<T> b2 = reinterpret_cast<const C2<T>*>(coef + 4 * P + o)[n];
+      C2<T> acc;
+      acc.x = a11.x * y0.x + b1.x * y1.x + (T)2 * a12.x * y2.x + b2.x * y3.x + a22.x * y4.x;
+      acc.y = a11.y * y0.y + b1.y * y1.y + (T)2 * a12.y * y2.y + b2.y * y3.y + a22.y * y4.y;
+      reinterpret_cast<C2<T>*>(out + o)[n] = acc;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------------------
 inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
@@ -827,9 +1203,27 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
 }
 
 template <typename T>
+cudaError_t row_r2c_w_launch(const T* x, size_t xs, const int* jptr, const double* scale,
+                             C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
+                             cudaStream_t st) {
+  const int L = M / 2, TPT = L / 32;
+  int RB = 64 / TPT;  // two warps per block at most
+  if (RB < 1) RB = 1;
+  if (RB > N) RB = N;
+  const size_t sm = (size_t)RB * (L + L / 32) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_row_r2c_w<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_r2c_w<T><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
+      x, xs, jptr, scale, spec, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double* scale,
                            C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
                            cudaStream_t st) {
+  if (sizeof(T) == 4 && warp_fft_ok(M / 2))
+    return row_r2c_w_launch<T>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   if (fft_E(M / 2) == 12) return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
 }
@@ -852,10 +1246,29 @@ cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2,
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t col_matvec_w_launch(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
+                                int M, const SpecTables& tb, const DevScalars* sc,
+                                const int* skip, cudaStream_t st) {
+  const int Lc = M / 2, TPT = N / 32;
+  int Q = 1;
+  while (Q * 2 * 3 * TPT <= 384 && Q < 2) Q *= 2;
+  if (Q > Lc) Q = Lc;
+  const size_t sm = (size_t)3 * Q * (N + N / 32) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_col_matvec_w<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_col_matvec_w<T><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
+      spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
+      skip);
+  return cudaGetLastError();
+}
+
 template <typename T, int E>
 cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
                          int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
                          cudaStream_t st) {
+  if (sizeof(T) == 4 && mode == COL_MATVEC && warp_fft_ok(N) && 3 * (N / 32) <= 384)
+    return col_matvec_w_launch<T>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   if (sizeof(T) == 4 && mode == COL_MATVEC && 3 * (N / E) <= OTGB_PAR_THREADS)
     return col_matvec_par_E<T, E>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   switch (mode) {
@@ -893,11 +1306,29 @@ cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t row_combine_w_launch(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
+                                 const T* coef, T* out, int N, int M, const SpecTables& tb,
+                                 const int* skip, cudaStream_t st) {
+  const int L = M / 2, TPT = L / 32;
+  int RB = 1;
+  while (RB * 2 * 5 * TPT <= 320 && RB < 8) RB *= 2;
+  if (RB > N) RB = N;
+  const size_t sm = (size_t)5 * RB * (L + L / 32) * sizeof(C2<T>);
+  cudaError_t e = set_smem(k_row_combine_w<T>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_combine_w<T><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
+      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+  return cudaGetLastError();
+}
+
 template <typename T, int E>
 cudaError_t row_c2r_dispatch(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                              const T* coef, T* out, const double* u_in, double* u_out,
                              double step, double os, int N, int M, const SpecTables& tb,
                              const int* skip, cudaStream_t st, const DevScalars* sc) {
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && warp_fft_ok(M / 2) && 5 * (M / 64) <= 320)
+    return row_combine_w_launch<T>(q0, q1, q2, coef, out, N, M, tb, skip, st);
   if (sizeof(T) == 4 && mode == ROWINV_COMBINE && 5 * ((M / 2) / E) <= OTGB_PAR_THREADS)
     return row_combine_par_E<T, E>(q0, q1, q2, coef, out, N, M, tb, skip, st);
   switch (mode) {
