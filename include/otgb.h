@@ -71,6 +71,15 @@ extern "C" {
                                    sigma and forms the update in FP64 (FP32 round-off in theta
                                    is amplified ~M^2 by the stencils at the grid scale and
                                    slows the Newton tail); 0: in FP32 */
+#define OT_OPT_AUTOTUNE 15      /* mixed mode: 1 (default) times the kernel variants of the
+                                   FP32 transform passes at the first solve of each grid size
+                                   and keeps the fastest (cached per size in the process) */
+#define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
+                                   autotuning: value r + 3 c + 9 b with r (row R2C), c
+                                   (column matvec) and b (row combine) each 0 = generic,
+                                   1 = concurrent transforms (r: same as 0), 2 = warp-
+                                   synchronous radix-32 (where the size allows, else the
+                                   next variant that does); turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */
@@ -134,6 +143,10 @@ int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* 
 
 void ot_plan_destroy(ot_plan* plan);
 const char* ot_strerror(int status);
+
+/* Description of the last failed CUDA call made by the library on this thread ("" if none):
+ * the call site and the CUDA error name and text. */
+const char* ot_last_error(void);
 
 /* Profile accumulated since the last reset: for each of the first n classes (n <=
  * OT_PROF_CLASSES) the summed event time in ms and the number of timed launches (ms,

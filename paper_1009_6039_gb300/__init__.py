@@ -20,7 +20,7 @@ OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED
 OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
-OT_OPT_THETA_FP64 = 14
+OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT = 14, 15, 16
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other"]
 
@@ -28,7 +28,8 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_sol
            "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
            "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
-           "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc"]
+           "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc",
+           "ot_last_error"]
 
 
 class ot_stats(ctypes.Structure):
@@ -45,7 +46,8 @@ class ot_stats(ctypes.Structure):
 
 class OTError(RuntimeError):
     def __init__(self, status, where):
-        super().__init__("%s: %s (%d)" % (where, ot_strerror(status), status))
+        detail = ot_last_error() if status == OT_ECUDA else ""
+        super().__init__("%s: %s (%d) %s" % (where, ot_strerror(status), status, detail))
         self.status = status
 
 
@@ -74,6 +76,7 @@ def _load():
         "ot_plan_reset_profile": ([vp], ctypes.c_int),
         "ot_plan_time_kernel": ([vp, i32, i32, vp], ctypes.c_int),
         "ot_eval_residual_noalloc": ([i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +127,10 @@ def ot_plan_destroy(plan):
 
 def ot_strerror(status):
     return _lib.ot_strerror(int(status)).decode()
+
+
+def ot_last_error():
+    return _lib.ot_last_error().decode()
 
 
 def ot_prefilter(plan, g_ptr, c_ptr):
@@ -196,7 +203,8 @@ class Plan:
              "safeguard": OT_OPT_SAFEGUARD, "translate": OT_OPT_TRANSLATE,
              "warm_start": OT_OPT_WARM_START, "tau": OT_OPT_TAU, "tol": OT_OPT_TOL,
              "profile": OT_OPT_PROFILE, "graph": OT_OPT_GRAPH, "reorth": OT_OPT_REORTH,
-             "theta_fp64": OT_OPT_THETA_FP64}
+             "theta_fp64": OT_OPT_THETA_FP64, "autotune": OT_OPT_AUTOTUNE,
+             "fft_variant": OT_OPT_FFT_VARIANT}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

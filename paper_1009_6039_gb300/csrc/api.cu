@@ -2,6 +2,7 @@
 // FFT-preconditioned GMRES(m) (Sec. 4.2), and the step-level entry points.
 #include <math.h>
 #include <stddef.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -25,6 +26,7 @@ struct ot_plan {
   int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
   int reorth = 0;  // Gram-Schmidt passes - 1 (OT_OPT_REORTH)
   int theta64 = 1;  // mixed mode: theta = Lbar^{-1} sigma and the update in FP64
+  int autotune = 1, tuned = 0;  // FP32 matvec kernel variants timed at the first solve
   cudaStream_t stream = 0;
   int device = 0;
   // FP64 planes
@@ -138,10 +140,20 @@ extern "C" const char* ot_strerror(int s) {
   return "unknown status";
 }
 
+// last CUDA failure seen by this thread (ot_last_error)
+static thread_local char g_last_error[160] = "";
+static void record_error(cudaError_t e, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "api.cu:%d: %s (%s)", line,
+           cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+extern "C" const char* ot_last_error(void) { return g_last_error; }
+
 #define CK(x)                                 \
   do {                                        \
     cudaError_t e_ = (x);                     \
     if (e_ != cudaSuccess) {                  \
+      record_error(e_, __LINE__);             \
       if (e_ == cudaErrorMemoryAllocation)    \
         return OT_ENOMEM;                     \
       return OT_ECUDA;                        \
@@ -383,6 +395,27 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
     case OT_OPT_THETA_FP64:
       if (v != 0 && v != 1) return OT_EINVAL;
       p->theta64 = (int)v;
+      free_graph(p);
+      return OT_OK;
+    case OT_OPT_FFT_VARIANT: {
+      // r2c + 3 col + 9 combine, each 0 generic, 1 concurrent, 2 warp (r2c: 1 = generic)
+      if (v < 0 || v > 26 || v != (double)(int)v) return OT_EINVAL;
+      const int k = (int)v;
+      p->tb32.var_r2c = k % 3 == 2 ? VAR_WARP : VAR_GENERIC;
+      p->tb32.var_col = (k / 3) % 3;
+      p->tb32.var_comb = k / 9;
+      p->autotune = 0;
+      p->tuned = 1;
+      free_graph(p);
+      return OT_OK;
+    }
+    case OT_OPT_AUTOTUNE:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->autotune = (int)v;
+      if (!p->autotune) {
+        p->tb32.var_r2c = p->tb32.var_col = p->tb32.var_comb = VAR_DEFAULT;
+        p->tuned = 0;
+      }
       free_graph(p);
       return OT_OK;
   }
@@ -661,12 +694,15 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->max_restarts = p->max_restarts;
 }
 
+static int run_autotune(ot_plan* p);
+
 template <typename T>
 static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
                       ot_stats* st) {
   ot_stats local;
   if (!st) st = &local;
   memset(st, 0, sizeof(*st));
+  RET(run_autotune(p));
   const long long launches0 = p->launches;
   const int N = p->N, M = p->M;
   const long P = (long)N * M;
@@ -887,8 +923,110 @@ static int capture_solve(ot_plan* p) {
   return OT_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Autotuner of the FP32 matvec passes: each variant (generic / concurrent transforms /
+// warp-synchronous radix-32) of the row R2C, column and row combine passes is launched back
+// to back on the plan's own buffers and timed with CUDA events; the fastest is kept, and
+// the choice is cached per (N, M) for the process.
+// ------------------------------------------------------------------------------------------
+static std::mutex g_tune_mutex;
+static std::vector<std::vector<int>> g_tune_cache;  // {N, M, r2c, col, comb}
+
+static int run_autotune(ot_plan* p) {
+  if (!p->precision || !p->autotune || p->tuned) return OT_OK;
+  const int N = p->N, M = p->M;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (auto& e : g_tune_cache)
+      if (e[0] == N && e[1] == M) {
+        p->tb32.var_r2c = e[2];
+        p->tb32.var_col = e[3];
+        p->tb32.var_comb = e[4];
+        p->tuned = 1;
+        return OT_OK;
+      }
+  }
+  const long P = (long)N * M;
+  cudaStream_t st = p->stream;
+  CK(cudaMemsetAsync(p->V, 0, P * 4, st));
+  CK(cudaMemsetAsync(p->spec, 0, P * 4, st));
+  CK(cudaMemsetAsync(p->q0, 0, P * 4, st));
+  CK(cudaMemsetAsync(p->q1, 0, P * 4, st));
+  CK(cudaMemsetAsync(p->q2, 0, P * 4, st));
+  CK(cudaMemsetAsync(p->coef, 0, 5 * P * 4, st));
+  CK(cudaMemsetAsync(p->sc, 0, sizeof(DevScalars), st));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  SpecTables& tb = p->tb32;
+  auto timed = [&](int cls) -> float {
+    auto one = [&]() -> cudaError_t {
+      if (cls == 0)
+        return launch_row_r2c<float>((const float*)p->V, P, nullptr, nullptr,
+                                     (C2<float>*)p->spec, N, M, tb, nullptr, st);
+      if (cls == 1)
+        return launch_col<float>(COL_MATVEC, (C2<float>*)p->spec, (C2<float>*)p->q0,
+                                 (C2<float>*)p->q1, (C2<float>*)p->q2, N, M, tb, p->sc,
+                                 nullptr, st);
+      return launch_row_c2r<float>(ROWINV_COMBINE, (C2<float>*)p->q0, (C2<float>*)p->q1,
+                                   (C2<float>*)p->q2, (const float*)p->coef, (float*)p->w,
+                                   nullptr, nullptr, 0.0, 1.0, N, M, tb, nullptr, st);
+    };
+    for (int r = 0; r < 2; ++r)
+      if (one() != cudaSuccess) return 1e30f;
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 10; ++r)
+      if (one() != cudaSuccess) return 1e30f;
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  };
+  int* vars[3] = {&tb.var_r2c, &tb.var_col, &tb.var_comb};
+  const int cand[3][3] = {{VAR_GENERIC, VAR_WARP, VAR_WARP},
+                          {VAR_GENERIC, VAR_PAR, VAR_WARP},
+                          {VAR_GENERIC, VAR_PAR, VAR_WARP}};
+  for (int cls = 0; cls < 3; ++cls) {
+    int best = VAR_GENERIC;
+    float tbest = 1e30f;
+    for (int k = 0; k < 3; ++k) {
+      *vars[cls] = cand[cls][k];
+      const float tms = timed(cls);
+      if (tms < tbest) {
+        tbest = tms;
+        best = cand[cls][k];
+      }
+    }
+    *vars[cls] = best;
+  }
+  cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  p->tuned = 1;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb});
+  return OT_OK;
+}
+
+// End every capture still open on the plan's capture streams (after a failed capture).
+static void abandon_captures(ot_plan* p) {
+  for (int k = 3; k >= 0; --k) {
+    if (!p->cs[k]) continue;
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p->cs[k], &cst) == cudaSuccess &&
+        cst != cudaStreamCaptureStatusNone) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(p->cs[k], &g);
+      if (g && k == 0) cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();
+}
+
 template <typename T>
 static int build_graph(ot_plan* p) {
+  RET(run_autotune(p));
   free_graph(p);
   for (int k = 0; k < 4; ++k)
     if (!p->cs[k]) CK(cudaStreamCreateWithFlags(&p->cs[k], cudaStreamNonBlocking));
@@ -899,6 +1037,13 @@ static int build_graph(ot_plan* p) {
   p->stream = p->cs[0];
   CK(cudaStreamBeginCapture(p->cs[0], cudaStreamCaptureModeRelaxed));
   int rc = capture_solve<T>(p);
+  if (rc != OT_OK) {
+    p->stream = saved;
+    p->profile = saved_prof;
+    p->launches = saved_launches;
+    abandon_captures(p);
+    return rc;
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(p->cs[0], &g);
   p->stream = saved;

@@ -75,7 +75,12 @@ struct SpecTables {
   const void* twL;  // exp(-2 pi i t / (M/2)), t < M/2 (row transforms)
   const void* twM;  // exp(-2 pi i k / M), k < M/2 (real-to-complex split)
   const void* twN;  // exp(-2 pi i t / N), t < N (column transforms)
+  // kernel variants of the FP32 matvec passes (chosen by the plan's autotuner):
+  // -1 default, 0 generic (8 or 12 elements per thread, one transform after the other),
+  // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32
+  int var_r2c = -1, var_col = -1, var_comb = -1;
 };
+enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2 };
 
 bool fft_length_supported(int L);
 

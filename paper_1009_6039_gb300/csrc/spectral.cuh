@@ -1222,7 +1222,7 @@ template <typename T>
 cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double* scale,
                            C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
                            cudaStream_t st) {
-  if (sizeof(T) == 4 && warp_fft_ok(M / 2))
+  if (sizeof(T) == 4 && tb.var_r2c == VAR_WARP && warp_fft_ok(M / 2))
     return row_r2c_w_launch<T>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   if (fft_E(M / 2) == 12) return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
@@ -1267,9 +1267,11 @@ template <typename T, int E>
 cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
                          int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
                          cudaStream_t st) {
-  if (sizeof(T) == 4 && mode == COL_MATVEC && warp_fft_ok(N) && 3 * (N / 32) <= 384)
+  if (sizeof(T) == 4 && mode == COL_MATVEC && tb.var_col == VAR_WARP && warp_fft_ok(N) &&
+      3 * (N / 32) <= 384)
     return col_matvec_w_launch<T>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
-  if (sizeof(T) == 4 && mode == COL_MATVEC && 3 * (N / E) <= OTGB_PAR_THREADS)
+  if (sizeof(T) == 4 && mode == COL_MATVEC && tb.var_col != VAR_GENERIC &&
+      3 * (N / E) <= OTGB_PAR_THREADS)
     return col_matvec_par_E<T, E>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   switch (mode) {
     case COL_FWD: return col_E<T, E, COL_FWD>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
@@ -1327,9 +1329,11 @@ cudaError_t row_c2r_dispatch(int mode, const C2<T>* q0, const C2<T>* q1, const C
                              const T* coef, T* out, const double* u_in, double* u_out,
                              double step, double os, int N, int M, const SpecTables& tb,
                              const int* skip, cudaStream_t st, const DevScalars* sc) {
-  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && warp_fft_ok(M / 2) && 5 * (M / 64) <= 320)
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && tb.var_comb != VAR_GENERIC &&
+      tb.var_comb != VAR_PAR && warp_fft_ok(M / 2) && 5 * (M / 64) <= 320)
     return row_combine_w_launch<T>(q0, q1, q2, coef, out, N, M, tb, skip, st);
-  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && 5 * ((M / 2) / E) <= OTGB_PAR_THREADS)
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && tb.var_comb != VAR_GENERIC &&
+      5 * ((M / 2) / E) <= OTGB_PAR_THREADS)
     return row_combine_par_E<T, E>(q0, q1, q2, coef, out, N, M, tb, skip, st);
   switch (mode) {
     case ROWINV_PLAIN:

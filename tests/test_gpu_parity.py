@@ -138,6 +138,39 @@ def test_operator_and_lbar_inverse(ot, N, M, prec):
     p.close()
 
 
+@pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512)])
+@pytest.mark.parametrize("variant", [0, 13, 26, 2 + 3 * 0 + 9 * 1])
+def test_fp32_kernel_variants(ot, N, M, variant):
+    # every FP32 transform kernel variant the autotuner can pick computes the same operator
+    f = I.blob_density(N, M, 23)
+    g = I.blob_density(N, M, 24)
+    u = smooth_field(N, M, amp=2e-3)
+    _, coef, _ = O.residual(f, O.bspline_coeffs(g), u)
+    abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
+    sigma = RNG.standard_normal((N, M))
+    w_ref = O.apply_op(coef, abar, sigma)
+    p = plan(ot, N, M, "mixed", fft_variant=variant)
+    cd, sd, wd = dev(coef), dev(sigma), dev(np.zeros((N, M)))
+    assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
+    assert np.abs(wd.cpu().numpy() - w_ref).max() <= 5e-6 * np.abs(w_ref).max()
+    assert np.linalg.norm(wd.cpu().numpy() - w_ref) <= 2e-6 * np.linalg.norm(w_ref)
+    p.close()
+
+
+def test_autotuned_solve_matches_fixed_variant(ot):
+    f, g = I.blob_pair(256, 256, s=41)
+    out = []
+    for kw in ({"autotune": 1}, {"fft_variant": 0}):
+        p = plan(ot, 256, 256, "mixed", tau=4.0, tol=1e-8, eta=1e-1, max_newton=400, **kw)
+        phi = dev(np.zeros((256, 256)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["status"] == 0
+        out.append(phi.cpu().numpy())
+    # both converge to ||res||_inf <= 1e-8; the potentials agree to the mixed-mode bound
+    assert np.abs(out[0] - out[1]).max() <= 1e-6
+
+
 # ---------------------------------------------------------------------------------------
 def _gpu_solve(ot, f, g, prec="fp64", tau=2.0, tol=1e-10, **kw):
     N, M = f.shape
