@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
 #pragma unroll
   for (int a = 0; a < 5; ++a) ab[a] = sc ? (T)sc->abar[a] : (T)0;
   const T inv = (T)inv_nm;
-  C2<T> s[E];
+  C2<T> s[E], s0[E];
   if (active) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -496,6 +496,15 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
         } else {
           A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
           B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
+          // the matvec's Q0 carries its Nyquist channel premultiplied by d11(M/2) =
+          // -(2 pi M/2)^2, so that the two channels sharing the complex column have
+          // comparable magnitudes; formed here from the unpacked channels (recovering one
+          // channel from the packed sum would cost eps times the other's magnitude)
+          if (MODE == COL_MATVEC) {
+            const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
+            const C2<T> Bn = cscale<T>(B, -qn * qn);
+            s0[e] = cscale<T>(mk2<T>(A.x - Bn.y, A.y + Bn.x), inv);
+          }
         }
         r = mk2<T>(A.x - B.y, A.y + B.x);  // A + i B
       } else {
@@ -521,7 +530,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
         bool nyq2;
         const int k2 = sfreq(k, N, &nyq2);
         const T q2 = (T)OTGB_TWO_PI * (T)k2;
-        C2<T> v = s[e];
+        C2<T> v = (MODE == COL_MATVEC && p == 0 && col == 0) ? s0[e] : s[e];
         if (p == 1) {  // (2 pi i k2) S, zero at Nyquist
           v = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
         } else if (p == 2) {  // -(2 pi k2)^2 S
@@ -531,31 +540,6 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
       }
     }
     __syncthreads();
-    if (MODE == COL_MATVEC && p == 0) {
-      // column 0 of Q0 carries A' + i B' (k1 = 0 and k1 = M/2); replace B' by d11(M/2) B'
-      // with B'(k) = (S(k) - conj S(-k)) / (2i), before the inverse transform mixes them
-      C2<T> corr[E];
-      if (active && col == 0) {
-        const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
-        const T f = -qn * qn - (T)1;
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int k = t + e * TPT;
-          const C2<T> a = buf[k], b = buf[(N - k) % N];
-          // i (f) B' = (f / 2) (S - conj S(-k))
-          corr[e] = mk2<T>((T)0.5 * f * (a.x - b.x), (T)0.5 * f * (a.y + b.y));
-        }
-      }
-      __syncthreads();
-      if (active && col == 0) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const int k = t + e * TPT;
-          buf[k] = cadd<T>(buf[k], corr[e]);
-        }
-      }
-      __syncthreads();
-    }
     fft_smem<T, E, +1>(buf, N, t, active, twN);
     col_store<T, E>(p == 0 ? out0 : (p == 1 ? out1 : out2), sm, N, Lc, Q, col0);
     __syncthreads();
