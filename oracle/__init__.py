@@ -73,6 +73,8 @@ def lib():
         _lib.orc_solve.argtypes = [vp, vp, i, i, ctypes.POINTER(Opts), vp,
                                    ctypes.POINTER(Stats), vp, vp]
         _lib.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        _lib.orc_fd_poisson.argtypes = [vp, i, i, vp]
+        _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
     return _lib
 
 
@@ -225,3 +227,21 @@ def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_n
     d = {k: getattr(st, k) for k, _ in Stats._fields_}
     n = d["newton_iters"]
     return u, d, hres[:n + 1].copy(), hgm[:n].copy()
+
+
+def fd_poisson(src):
+    """Mean-zero solution of (D_xx + D_yy) out = src - mean(src) (4th-order stencils)."""
+    src = _f64(src)
+    out = np.empty_like(src)
+    if lib().orc_fd_poisson(_p(src), src.shape[0], src.shape[1], _p(out)) != 0:
+        raise ValueError("fft failed")
+    return out
+
+
+def ws_features(f, g, c, h):
+    """(N, M, 16) features of the warm-start network at the potential h."""
+    f, g, c, h = _f64(f), _f64(g), _f64(c), _f64(h)
+    N, M = f.shape
+    X = np.empty((N, M, 16))
+    lib().orc_ws_features(_p(f), _p(g), _p(c), _p(h), N, M, _p(X))
+    return X

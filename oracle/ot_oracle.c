@@ -913,3 +913,84 @@ out:
   free(cand);
   return status;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Learned warm start: FD Poisson solve and per-point features (not in the paper; the     */
+/* network's inputs are built from the paper's quantities: the stencils, the interpolant   */
+/* G, T = x + grad h and det(I + D^2 h) of Eq. ma2, at the linearised potential h).        */
+/* ------------------------------------------------------------------------------------ */
+
+/* Eigenvalue of the 4th-order second-difference stencil for frequency k on L points. */
+static double fd2_eig(long k, int L) {
+  double th = TWO_PI * (double)k / (double)L;
+  return (-2.0 * cos(2.0 * th) + 32.0 * cos(th) - 30.0) / 12.0 * (double)L * (double)L;
+}
+
+/* out = the mean-zero solution of (D_xx + D_yy) out = src - mean(src), by division of the
+ * spectrum by the stencil eigenvalues (the zero frequency is set to 0). */
+int orc_fd_poisson(const double *src, int N, int M, double *out) {
+  long P = (long)N * M;
+  double *re = (double *)malloc(sizeof(double) * P);
+  double *im = (double *)calloc(P, sizeof(double));
+  for (long p = 0; p < P; ++p) re[p] = src[p];
+  int rc = orc_fft2(re, im, N, M, -1);
+  for (int i = 0; i < N && rc == 0; ++i)
+    for (int j = 0; j < M; ++j) {
+      long p = (long)i * M + j;
+      double lam = fd2_eig(j, M) + fd2_eig(i, N);
+      if (i == 0 && j == 0) {
+        re[p] = im[p] = 0.0;
+      } else {
+        re[p] /= lam;
+        im[p] /= lam;
+      }
+    }
+  if (rc == 0) rc = orc_fft2(re, im, N, M, +1);
+  for (long p = 0; p < P; ++p) out[p] = re[p] / (double)P;
+  free(re);
+  free(im);
+  return rc;
+}
+
+/* Features of the warm-start network at every grid point, ORC_WS_K per point:
+ *   h = the linearised potential (orc_fd_poisson of log f - log g), T = x + grad h,
+ *   G, grad G = the B-spline interpolant of g at T, det = det(I + D^2 h),
+ *   lg = log max(G, floor), ld = log max(det, floor), iG = 1 / max(G, floor):
+ *   [log f, log g, lg, log f - lg - ld, hxx + hyy, hxx - hyy, 2 hxy, hxx hyy - hxy^2,
+ *    10 hx, 10 hy, 0.1 Gx iG, 0.1 Gy iG, (Gx hx + Gy hy) iG, (hxx - hyy)^2 + 4 hxy^2,
+ *    (log f - lg - ld)(hxx + hyy), 0]. */
+void orc_ws_features(const double *f, const double *g, const double *c, const double *h,
+                     int N, int M, double *X) {
+  const double floor_v = 1e-3;
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < M; ++j) {
+      long p = (long)i * M + j;
+      double hx = d1x(h, N, M, i, j), hy = d1y(h, N, M, i, j);
+      double hxx = d2x(h, N, M, i, j), hyy = d2y(h, N, M, i, j);
+      double hxy = dxy(h, N, M, i, j);
+      double G, Gx, Gy;
+      orc_bspline_eval_grid(c, N, M, (double)j + (double)M * hx, (double)i + (double)N * hy,
+                            &G, &Gx, &Gy);
+      double det = (1.0 + hxx) * (1.0 + hyy) - hxy * hxy;
+      double Gc = G > floor_v ? G : floor_v;
+      double lf = log(f[p]), lg = log(Gc), ld = log(det > floor_v ? det : floor_v);
+      double r = lf - lg - ld;
+      double *x = X + p * ORC_WS_K;
+      x[0] = lf;
+      x[1] = log(g[p]);
+      x[2] = lg;
+      x[3] = r;
+      x[4] = hxx + hyy;
+      x[5] = hxx - hyy;
+      x[6] = 2.0 * hxy;
+      x[7] = hxx * hyy - hxy * hxy;
+      x[8] = 10.0 * hx;
+      x[9] = 10.0 * hy;
+      x[10] = 0.1 * Gx / Gc;
+      x[11] = 0.1 * Gy / Gc;
+      x[12] = (Gx * hx + Gy * hy) / Gc;
+      x[13] = (hxx - hyy) * (hxx - hyy) + 4.0 * hxy * hxy;
+      x[14] = r * (hxx + hyy);
+      x[15] = 0.0;
+    }
+}

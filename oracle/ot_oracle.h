@@ -65,6 +65,12 @@ int orc_gmres_op(const double *coef, const double abar[5], const double *h, int 
 int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_opts *o,
               double *u, orc_stats *st, double *hist_res, int *hist_gmres);
 
+/* learned warm start: FD Poisson solve and network features */
+#define ORC_WS_K 16
+int orc_fd_poisson(const double *src, int N, int M, double *out);
+void orc_ws_features(const double *f, const double *g, const double *c, const double *h,
+                     int N, int M, double *X);
+
 #ifdef __cplusplus
 }
 #endif

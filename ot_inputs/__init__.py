@@ -144,3 +144,25 @@ def noise_blob_pair(N, M, s=3000, ratio=10.0, sigma_px=8.0):
     """Smoothed-noise workload: f from seed 2s, g from seed 2s+1, max/min = ratio, mean 1."""
     return (noise_blob_density(N, M, 2 * s, ratio, sigma_px),
             noise_blob_density(N, M, 2 * s + 1, ratio, sigma_px))
+
+
+# ----------------------------------------------------------------------------------------
+# Learned warm start: initial network parameters and minibatch row draws
+# ----------------------------------------------------------------------------------------
+def ws_init_params(seed, K=16, H=128):
+    """Flat float32 parameters W0[H,K], b0[H], W1[H,H], b1[H], W2[H,H], b2[H], w3[H], b3:
+    weights uniform in +-1/sqrt(fan_in) (w3 scaled by 0.1), biases 0."""
+    rng = SplitMix64(seed)
+    parts = []
+    for fan_out, fan_in, scale in ((H, K, 1.0), (H, H, 1.0), (H, H, 1.0)):
+        w = (2.0 * rng.uniform(fan_out * fan_in) - 1.0) * scale / np.sqrt(fan_in)
+        parts += [w, np.zeros(fan_out)]
+    parts += [(2.0 * rng.uniform(H) - 1.0) * 0.1 / np.sqrt(H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def ws_batch_rows(seed, step, n_rows, batch):
+    """Row indices (int64) of minibatch `step`: SplitMix64 stream seeded by
+    seed * 1000003 + step, each output taken modulo n_rows."""
+    z = SplitMix64(int(seed) * 1000003 + int(step)).next_u64(batch)
+    return (z % np.uint64(n_rows)).astype(np.int64)
