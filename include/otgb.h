@@ -54,7 +54,9 @@ extern "C" {
 #define OT_OPT_TRANSLATE 7      /* 1 (default): apply Eq. (translation) d - mean(d) + 1 to
                                    f and g on entry; 0: use them as given */
 #define OT_OPT_WARM_START 8     /* 1: phi_inout holds the initial iterate u0 on entry;
-                                   0 (default): u0 = 0, the constant start of Thm 3.2 */
+                                   0 (default): u0 = 0, the constant start of Thm 3.2;
+                                   2: u0 = the learned warm start (ot_ws_set_weights or
+                                   ot_warmstart_load first, else OT_EINVAL) */
 #define OT_OPT_TAU 9            /* step-size parameter tau >= 1 (Eq. linma) */
 #define OT_OPT_TOL 10           /* Newton stop: max |f - f~_n| < tol */
 #define OT_OPT_PROFILE 11       /* 1: time every kernel launch with CUDA events on the
@@ -92,7 +94,8 @@ extern "C" {
 #define OT_PROF_GMRES_UPDATE 7     /* Arnoldi update + norm + Givens */
 #define OT_PROF_GMRES_OTHER 8      /* GMRES init / restart residual / finish / combine */
 #define OT_PROF_OTHER 9            /* input translation, prefilter, final reductions */
-#define OT_PROF_CLASSES 10
+#define OT_PROF_WARMSTART 10       /* learned warm start (features, network, Poisson solves) */
+#define OT_PROF_CLASSES 11
 
 typedef struct ot_plan ot_plan;
 
@@ -110,6 +113,8 @@ typedef struct {
   double mean_fn;          /* mean of f_n before translation (mass defect = mean_fn - 1) */
   double phi_mean;         /* mean removed from the final iterate (gauge, Sec. 3.1) */
   double ms_total;         /* wall time of the call on the plan's stream (ms) */
+  double ws_alpha;         /* learned warm start: scale applied to the network's potential
+                              (1, 1/2, 1/4, 1/8 or 0 = zero start); -1 without it */
 } ot_stats;
 
 /* Create a plan for N x M grids (N rows, M columns), damping tau >= 1 (Eq. linma) and
@@ -199,6 +204,77 @@ int ot_fft_forward(ot_plan* plan, const double* x, double* spec);
 
 /* Inverse of ot_fft_forward without the 1/(N M) factor (spec -> N M x). */
 int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
+
+/* ---- Learned warm start -----------------------------------------------------------------
+ * Not in the paper, which starts Newton from u0 = 0 and needs only an admissible start,
+ * det(I + D^2 u0) > 0 (Thm 3.2).  After the input translation (Eq. translation):
+ *   h  = P(log f - log g), P the mean-zero inverse of the 4th-order stencil Laplacian
+ *        D_xx + D_yy of Sec. 4.1 (the linearisation of log det(I + D^2 u) + log g(x + grad u)
+ *        = log f about u = 0);
+ *   X  = 16 features per grid point at h: [log f, log g, lg, r, hxx + hyy, hxx - hyy, 2 hxy,
+ *        hxx hyy - hxy^2, 10 hx, 10 hy, 0.1 Gx / Gc, 0.1 Gy / Gc, (Gx hx + Gy hy) / Gc,
+ *        (hxx - hyy)^2 + 4 hxy^2, r (hxx + hyy), 0], where G, Gx, Gy are the cubic B-spline
+ *        interpolant of g and its gradient at T = x + grad h, Gc = max(G, 1e-3),
+ *        lg = log Gc, r = log f - lg - log max(det(I + D^2 h), 1e-3);
+ *   s  = MLP(X): 16 -> 128 -> 128 -> 128 -> 1, SiLU, per point, trained to predict
+ *        s* = (D_xx + D_yy)(phi* - h) for converged potentials phi*;
+ *   u0 = alpha (h + P(G s)), G the Gaussian low-pass exp(-((k1/(M/4))^2 + (k2/(N/4))^2)/2)
+ *        on frequency (k1, k2), alpha the largest of 1, 1/2, 1/4, 1/8 with
+ *        det(I + alpha D^2 u0) > 0 at every point, else 0.
+ * Inference runs the three matrix products on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation); training runs in FP32.  Parameters are one FP32 vector of
+ * ot_ws_param_count() values: W0[128,16], b0[128], W1[128,128], b1[128], W2[128,128],
+ * b2[128], w3[128], b3 (weights row-major [out][in]). */
+int64_t ot_ws_param_count(void);
+
+/* Upload the network parameters (HOST array of `count` floats) to the plan and allow
+ * OT_OPT_WARM_START = 2.  Allocates the warm-start workspace on first use (about 100 bytes
+ * per grid point).  OT_EINVAL if count != ot_ws_param_count(). */
+int ot_ws_set_weights(ot_plan* plan, const float* params_host, int64_t count);
+
+/* Parameter file: 8 bytes "OTWS0001", an int64 count, then count little-endian floats.
+ * ot_warmstart_load reads one into the plan (as ot_ws_set_weights); ot_ws_save_weights
+ * writes one from a HOST array.  OT_EINVAL on a missing, short or mismatched file. */
+int ot_warmstart_load(ot_plan* plan, const char* weights_path);
+int ot_ws_save_weights(const char* weights_path, const float* params_host, int64_t count);
+
+/* The warm start alone for densities f, g (translated as by the solve when
+ * OT_OPT_TRANSLATE is set): phi0 receives u0; *alpha_out (HOST, may be NULL) the scale. */
+int ot_ws_predict(ot_plan* plan, const double* f, const double* g, double* phi0,
+                  double* alpha_out);
+
+/* Training data of one pair: X (N*M x 16 floats) receives the features at h and, when
+ * phi_star is not NULL, target (N*M floats) receives s* = (D_xx + D_yy)(phi_star - h).
+ * f, g are translated as by the solve.  Needs no weights. */
+int ot_ws_features(ot_plan* plan, const double* f, const double* g, const double* phi_star,
+                   float* X, float* target);
+
+/* out[r] = MLP(X[r, 0..15]) for r < rows with the plan's weights (the BF16 tensor-core
+ * kernel of the solve).  OT_ECUDA if the kernel reported a timeout. */
+int ot_ws_mlp_forward(ot_plan* plan, const float* X, int64_t rows, float* out);
+
+/* u = P(src) (the FD Poisson solve of h; src, u: N x M); lowpass != 0: u = P(G src). */
+int ot_ws_poisson(ot_plan* plan, const double* src, int32_t lowpass, double* u);
+
+/* Trainer: Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error of the network
+ * over minibatches of `batch` rows (a multiple of 64, 64..1048576), FP32 master parameters,
+ * on its own stream (ot_ws_trainer_set_stream; default the legacy stream). */
+typedef struct ot_ws_trainer ot_ws_trainer;
+int ot_ws_trainer_create(ot_ws_trainer** out, int32_t batch, const float* params_host,
+                         int64_t count);
+int ot_ws_trainer_set_stream(ot_ws_trainer* tr, void* cuda_stream);
+/* Gradient of the loss over the rows idx[0..batch) (device int64, each < the row count of
+ * X and t) of X (rows x 16) and t (rows): grad_host (HOST, count floats, may be NULL) and
+ * loss_host (HOST, may be NULL) receive it; the parameters do not change. */
+int ot_ws_trainer_grad(ot_ws_trainer* tr, const float* X, const float* t, const int64_t* idx,
+                       float* grad_host, double* loss_host);
+/* One Adam step with learning rate lr on the rows idx[0..batch).  With loss_host NULL the
+ * call only enqueues work and does not synchronise; otherwise it returns the step's loss
+ * (before the update). */
+int ot_ws_trainer_step(ot_ws_trainer* tr, const float* X, const float* t, const int64_t* idx,
+                       float lr, double* loss_host);
+int ot_ws_trainer_get_params(ot_ws_trainer* tr, float* params_host, int64_t count);
+void ot_ws_trainer_destroy(ot_ws_trainer* tr);
 
 /* ---- Allocation-free variant ------------------------------------------------------------
  * No counterpart in the paper: a library-level addition for callers that cannot allocate

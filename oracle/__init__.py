@@ -73,7 +73,7 @@ def lib():
         _lib.orc_solve.argtypes = [vp, vp, i, i, ctypes.POINTER(Opts), vp,
                                    ctypes.POINTER(Stats), vp, vp]
         _lib.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
-        _lib.orc_fd_poisson.argtypes = [vp, i, i, vp]
+        _lib.orc_fd_poisson.argtypes = [vp, i, i, i, vp]
         _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
     return _lib
 
@@ -229,11 +229,13 @@ def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_n
     return u, d, hres[:n + 1].copy(), hgm[:n].copy()
 
 
-def fd_poisson(src):
-    """Mean-zero solution of (D_xx + D_yy) out = src - mean(src) (4th-order stencils)."""
+def fd_poisson(src, lowpass=False):
+    """Mean-zero solution of (D_xx + D_yy) out = src - mean(src) (4th-order stencils); with
+    lowpass, of the source filtered by exp(-((k1/(M/4))^2 + (k2/(N/4))^2)/2)."""
     src = _f64(src)
     out = np.empty_like(src)
-    if lib().orc_fd_poisson(_p(src), src.shape[0], src.shape[1], _p(out)) != 0:
+    if lib().orc_fd_poisson(_p(src), src.shape[0], src.shape[1], int(bool(lowpass)),
+                            _p(out)) != 0:
         raise ValueError("fft failed")
     return out
 

@@ -927,8 +927,10 @@ static double fd2_eig(long k, int L) {
 }
 
 /* out = the mean-zero solution of (D_xx + D_yy) out = src - mean(src), by division of the
- * spectrum by the stencil eigenvalues (the zero frequency is set to 0). */
-int orc_fd_poisson(const double *src, int N, int M, double *out) {
+ * spectrum by the stencil eigenvalues (the zero frequency is set to 0).  lowpass != 0 also
+ * multiplies frequency (k1, k2) (signed, |k| <= L/2) by the Gaussian
+ * exp(-((k1 / (M/4))^2 + (k2 / (N/4))^2) / 2). */
+int orc_fd_poisson(const double *src, int N, int M, int lowpass, double *out) {
   long P = (long)N * M;
   double *re = (double *)malloc(sizeof(double) * P);
   double *im = (double *)calloc(P, sizeof(double));
@@ -938,11 +940,17 @@ int orc_fd_poisson(const double *src, int N, int M, double *out) {
     for (int j = 0; j < M; ++j) {
       long p = (long)i * M + j;
       double lam = fd2_eig(j, M) + fd2_eig(i, N);
+      double w = 1.0;
+      if (lowpass) {
+        double k1 = (double)(2 * j <= M ? j : j - M) / (0.25 * M);
+        double k2 = (double)(2 * i <= N ? i : i - N) / (0.25 * N);
+        w = exp(-0.5 * (k1 * k1 + k2 * k2));
+      }
       if (i == 0 && j == 0) {
         re[p] = im[p] = 0.0;
       } else {
-        re[p] /= lam;
-        im[p] /= lam;
+        re[p] *= w / lam;
+        im[p] *= w / lam;
       }
     }
   if (rc == 0) rc = orc_fft2(re, im, N, M, +1);

@@ -67,7 +67,7 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
 
 /* learned warm start: FD Poisson solve and network features */
 #define ORC_WS_K 16
-int orc_fd_poisson(const double *src, int N, int M, double *out);
+int orc_fd_poisson(const double *src, int N, int M, int lowpass, double *out);
 void orc_ws_features(const double *f, const double *g, const double *c, const double *h,
                      int N, int M, double *X);
 

@@ -11,10 +11,13 @@ map (f, g) -> u0 built on the paper's quantities:
            at h, the Hessian of h, the displacement grad h, grad log G at T = x + grad h ...);
   3. s   = a per-point MLP 16 -> 128 -> 128 -> 128 -> 1 (SiLU) of X, trained to predict the
            source correction s* = Lap_h(phi* - h) of the converged potential phi*;
-  4. u0  = alpha P(log f - log g + s), alpha the largest of 1, 1/2, 1/4, 1/8 with
+  4. u0  = alpha (h + P(G s)), G the Gaussian low-pass exp(-((k1/(M/4))^2 + (k2/(N/4))^2)/2)
+           on the network's output, alpha the largest of 1, 1/2, 1/4, 1/8 with
            det(I + alpha D^2 u0) > 0 everywhere (else 0: the zero start).
 
-With s = s* exactly, step 4 returns phi* itself.  Network parameters are one flat vector:
+Without the low-pass, s = s* would return phi* itself.  The low-pass keeps the network's
+pointwise errors out of the high frequencies, where the damped iteration's contraction
+(spectral operator against stencil residual) is slowest.  Network parameters are one flat vector:
 W0[H,16], b0[H], W1[H,H], b1[H], W2[H,H], b2[H], w3[H], b3[1] (row-major, H = 128).
 
 Inference on the GPU runs the matrix products in BF16 with FP32 accumulation: the network
@@ -113,9 +116,10 @@ def adam_step(params, m, v, grad, t, lr):
 
 
 def normalise(f, g):
+    """The solver's input translation (Eq. translation): d <- d - mean(d) + 1."""
     f = np.asarray(f, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
-    return f / f.mean(), g / g.mean()
+    return f - f.mean() + 1.0, g - g.mean() + 1.0
 
 
 def linear_potential(f, g):
@@ -147,10 +151,10 @@ def admissible_scale(u):
 
 
 def predict(params, f, g, bf16=True):
-    """(u0, alpha, s): the warm start for the raw densities f, g (normalised here)."""
+    """(u0, alpha, s): the warm start for the raw densities f, g (translated here)."""
     f, g = normalise(f, g)
     X, h, src = features(f, g)
     s, _ = mlp_forward(params, X, bf16=bf16)
-    u = O.fd_poisson(src + s.reshape(f.shape))
+    u = h + O.fd_poisson(s.reshape(f.shape), lowpass=True)
     a = admissible_scale(u)
     return a * u, a, s.reshape(f.shape)

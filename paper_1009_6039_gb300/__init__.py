@@ -22,14 +22,19 @@ OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT = 14, 15, 16
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
-                "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other"]
+                "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
+                "warmstart"]
 
 EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_solve",
            "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
            "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
            "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc",
-           "ot_last_error"]
+           "ot_last_error", "ot_ws_param_count", "ot_ws_set_weights", "ot_warmstart_load",
+           "ot_ws_save_weights", "ot_ws_predict", "ot_ws_features", "ot_ws_mlp_forward",
+           "ot_ws_poisson", "ot_ws_trainer_create", "ot_ws_trainer_set_stream",
+           "ot_ws_trainer_grad", "ot_ws_trainer_step", "ot_ws_trainer_get_params",
+           "ot_ws_trainer_destroy"]
 
 
 class ot_stats(ctypes.Structure):
@@ -38,7 +43,8 @@ class ot_stats(ctypes.Structure):
                 ("step_halvings", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
                 ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
                 ("min_det", ctypes.c_double), ("mean_fn", ctypes.c_double),
-                ("phi_mean", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("phi_mean", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ws_alpha", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +83,20 @@ def _load():
         "ot_plan_time_kernel": ([vp, i32, i32, vp], ctypes.c_int),
         "ot_eval_residual_noalloc": ([i32, i32, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "ot_last_error": ([], ctypes.c_char_p),
+        "ot_ws_param_count": ([], ctypes.c_int64),
+        "ot_ws_set_weights": ([vp, vp, ctypes.c_int64], ctypes.c_int),
+        "ot_warmstart_load": ([vp, ctypes.c_char_p], ctypes.c_int),
+        "ot_ws_save_weights": ([ctypes.c_char_p, vp, ctypes.c_int64], ctypes.c_int),
+        "ot_ws_predict": ([vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_ws_features": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_ws_mlp_forward": ([vp, vp, ctypes.c_int64, vp], ctypes.c_int),
+        "ot_ws_poisson": ([vp, vp, i32, vp], ctypes.c_int),
+        "ot_ws_trainer_create": ([ctypes.POINTER(vp), i32, vp, ctypes.c_int64], ctypes.c_int),
+        "ot_ws_trainer_set_stream": ([vp, vp], ctypes.c_int),
+        "ot_ws_trainer_grad": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_ws_trainer_step": ([vp, vp, vp, vp, ctypes.c_float, vp], ctypes.c_int),
+        "ot_ws_trainer_get_params": ([vp, vp, ctypes.c_int64], ctypes.c_int),
+        "ot_ws_trainer_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -176,6 +196,64 @@ def ot_plan_time_kernel(plan, kernel_class, reps, ms_ptr):
     return _lib.ot_plan_time_kernel(plan, int(kernel_class), int(reps), ms_ptr)
 
 
+def ot_ws_param_count():
+    return int(_lib.ot_ws_param_count())
+
+
+def ot_ws_set_weights(plan, params_host_ptr, count):
+    return _lib.ot_ws_set_weights(plan, params_host_ptr, int(count))
+
+
+def ot_warmstart_load(plan, path):
+    return _lib.ot_warmstart_load(plan, os.fsencode(path))
+
+
+def ot_ws_save_weights(path, params_host_ptr, count):
+    return _lib.ot_ws_save_weights(os.fsencode(path), params_host_ptr, int(count))
+
+
+def ot_ws_predict(plan, f_ptr, g_ptr, phi0_ptr, alpha_host_ptr=None):
+    return _lib.ot_ws_predict(plan, f_ptr, g_ptr, phi0_ptr, alpha_host_ptr)
+
+
+def ot_ws_features(plan, f_ptr, g_ptr, phi_star_ptr, X_ptr, target_ptr):
+    return _lib.ot_ws_features(plan, f_ptr, g_ptr, phi_star_ptr, X_ptr, target_ptr)
+
+
+def ot_ws_mlp_forward(plan, X_ptr, rows, out_ptr):
+    return _lib.ot_ws_mlp_forward(plan, X_ptr, int(rows), out_ptr)
+
+
+def ot_ws_poisson(plan, src_ptr, lowpass, u_ptr):
+    return _lib.ot_ws_poisson(plan, src_ptr, int(lowpass), u_ptr)
+
+
+def ot_ws_trainer_create(batch, params_host_ptr, count):
+    h = ctypes.c_void_p()
+    rc = _lib.ot_ws_trainer_create(ctypes.byref(h), int(batch), params_host_ptr, int(count))
+    return rc, h
+
+
+def ot_ws_trainer_set_stream(tr, stream_ptr):
+    return _lib.ot_ws_trainer_set_stream(tr, ctypes.c_void_p(stream_ptr))
+
+
+def ot_ws_trainer_grad(tr, X_ptr, t_ptr, idx_ptr, grad_host_ptr, loss_host_ptr):
+    return _lib.ot_ws_trainer_grad(tr, X_ptr, t_ptr, idx_ptr, grad_host_ptr, loss_host_ptr)
+
+
+def ot_ws_trainer_step(tr, X_ptr, t_ptr, idx_ptr, lr, loss_host_ptr=None):
+    return _lib.ot_ws_trainer_step(tr, X_ptr, t_ptr, idx_ptr, float(lr), loss_host_ptr)
+
+
+def ot_ws_trainer_get_params(tr, params_host_ptr, count):
+    return _lib.ot_ws_trainer_get_params(tr, params_host_ptr, int(count))
+
+
+def ot_ws_trainer_destroy(tr):
+    _lib.ot_ws_trainer_destroy(tr)
+
+
 # ---- conveniences over torch tensors ---------------------------------------------------
 def _check(rc, where, ok=(OT_OK,)):
     if rc not in ok:
@@ -191,6 +269,72 @@ def _dev(t, shape=None):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev32(t, shape):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+        raise TypeError("expected a contiguous float32 CUDA tensor of shape %s" % (shape,))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Trainer:
+    """Adam trainer of the warm-start network (ot_ws_trainer) over minibatches of `batch`
+    rows of device tensors X (rows x 16, float32) and t (rows, float32)."""
+
+    def __init__(self, batch, params, stream=None):
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        rc, h = ot_ws_trainer_create(batch, ctypes.c_void_p(a.ctypes.data), a.size)
+        _check(rc, "ot_ws_trainer_create")
+        self.h, self.batch = h, batch
+        if stream is not None:
+            _check(ot_ws_trainer_set_stream(h, stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                            else int(stream)), "ot_ws_trainer_set_stream")
+
+    @staticmethod
+    def _idx(idx, batch):
+        import torch
+        if not (isinstance(idx, torch.Tensor) and idx.is_cuda and idx.dtype == torch.int64
+                and idx.is_contiguous() and idx.numel() == batch):
+            raise TypeError("expected %d int64 CUDA row indices" % batch)
+        return ctypes.c_void_p(idx.data_ptr())
+
+    def grad(self, X, t, idx):
+        import numpy as np
+        g = np.empty(ot_ws_param_count(), dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(ot_ws_trainer_grad(self.h, _dev32(X, (X.shape[0], 16)), _dev32(t, (t.shape[0],)),
+                                  self._idx(idx, self.batch), ctypes.c_void_p(g.ctypes.data),
+                                  ctypes.byref(loss)), "ot_ws_trainer_grad")
+        return loss.value, g
+
+    def step(self, X, t, idx, lr, want_loss=False):
+        loss = ctypes.c_double()
+        _check(ot_ws_trainer_step(self.h, _dev32(X, (X.shape[0], 16)), _dev32(t, (t.shape[0],)),
+                                  self._idx(idx, self.batch), lr,
+                                  ctypes.byref(loss) if want_loss else None),
+               "ot_ws_trainer_step")
+        return loss.value if want_loss else None
+
+    def params(self):
+        import numpy as np
+        p = np.empty(ot_ws_param_count(), dtype=np.float32)
+        _check(ot_ws_trainer_get_params(self.h, ctypes.c_void_p(p.ctypes.data), p.size),
+               "ot_ws_trainer_get_params")
+        return p
+
+    def close(self):
+        if self.h:
+            ot_ws_trainer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
@@ -262,6 +406,45 @@ class Plan:
         if rc in raise_on:
             raise OTError(rc, "ot_solve_host")
         return rc, st.as_dict()
+
+    # ---- learned warm start
+    def set_weights(self, params):
+        """Upload network parameters (numpy float32, ot_ws_param_count() values)."""
+        import numpy as np
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(ot_ws_set_weights(self.h, ctypes.c_void_p(a.ctypes.data), a.size),
+               "ot_ws_set_weights")
+        return self
+
+    def load_weights(self, path):
+        _check(ot_warmstart_load(self.h, path), "ot_warmstart_load")
+        return self
+
+    def ws_predict(self, f, g, phi0):
+        """Learned warm start alone: phi0 (float64 CUDA tensor) <- u0; returns alpha."""
+        shp = (self.N, self.M)
+        a = ctypes.c_double()
+        _check(ot_ws_predict(self.h, _dev(f, shp), _dev(g, shp), _dev(phi0, shp),
+                             ctypes.byref(a)), "ot_ws_predict")
+        return a.value
+
+    def ws_features(self, f, g, X, target=None, phi_star=None):
+        """Features (float32 CUDA tensor N*M x 16) and, with phi_star, the target (N*M)."""
+        shp = (self.N, self.M)
+        _check(ot_ws_features(self.h, _dev(f, shp), _dev(g, shp),
+                              _dev(phi_star, shp) if phi_star is not None else None,
+                              _dev32(X, (self.N * self.M, 16)),
+                              _dev32(target, (self.N * self.M,)) if target is not None
+                              else None), "ot_ws_features")
+
+    def ws_mlp_forward(self, X, out):
+        rows = X.shape[0]
+        _check(ot_ws_mlp_forward(self.h, _dev32(X, (rows, 16)), rows, _dev32(out, (rows,))),
+               "ot_ws_mlp_forward")
+
+    def ws_poisson(self, src, u, lowpass=False):
+        shp = (self.N, self.M)
+        _check(ot_ws_poisson(self.h, _dev(src, shp), lowpass, _dev(u, shp)), "ot_ws_poisson")
 
     def close(self):
         if self.h:

@@ -71,6 +71,12 @@ struct ot_plan {
   int top_kernels = 0;
   double* gu_a = nullptr;  // iterate buffers as captured (upar = 0 names gu_a)
   double* gu_b = nullptr;
+  // learned warm start (OT_OPT_WARM_START = 2)
+  float* ws_params = nullptr;         // FP32 parameters
+  unsigned char* ws_wpack = nullptr;  // BF16 weights in the tensor-core operand layout
+  double *ws_src = nullptr, *ws_h = nullptr, *ws_tmp = nullptr;  // FP64 planes
+  float *ws_X = nullptr, *ws_s = nullptr;  // features (P x 16), network output (P)
+  int ws_have = 0, gkey_ws = -1, sms = 0;
 };
 
 template <typename T> static const SpecTables& tables(ot_plan* p);
@@ -201,9 +207,12 @@ static void free_buffers(ot_plan* p) {
   p->uout = nullptr;
   void* ptrs[] = {p->c32, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
-                  p->tw32, p->partials, p->dmean, p->sc};
+                  p->tw32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
+                  p->ws_X, p->ws_s};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  p->ws_src = p->ws_h = p->ws_tmp = nullptr;
+  p->ws_X = p->ws_s = nullptr;
   if (p->hsc) cudaFreeHost(p->hsc);
   if (p->hinit) cudaFreeHost(p->hinit);
   p->hinit = nullptr;
@@ -276,6 +285,7 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaGetDevice(&p->device));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   p->kblocks = (sms > 0 ? sms : 148) * 2;
+  p->sms = sms > 0 ? sms : 148;
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
   size_t nk = (size_t)p->kblocks * OTGB_MAXM;
   if (nk > np) np = nk;
@@ -316,6 +326,8 @@ extern "C" void ot_plan_destroy(ot_plan* p) {
   if (!p) return;
   free_events(p);
   free_buffers(p);
+  if (p->ws_params) cudaFree(p->ws_params);
+  if (p->ws_wpack) cudaFree(p->ws_wpack);
   for (int k = 0; k < 4; ++k)
     if (p->cs[k]) cudaStreamDestroy(p->cs[k]);
   delete p;
@@ -368,8 +380,10 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       p->translate = (int)v;
       return OT_OK;
     case OT_OPT_WARM_START:
-      if (v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
+      if (v == 2 && !p->ws_have) return OT_EINVAL;
       p->warm_start = (int)v;
+      free_graph(p);
       return OT_OK;
     case OT_OPT_TAU:
       if (!(v >= 1.0)) return OT_EINVAL;
@@ -692,9 +706,70 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->reorth = reorth_on(p) ? 1 : 0;
   p->hsc->max_newton = p->max_newton;
   p->hsc->max_restarts = p->max_restarts;
+  p->hsc->ws_alpha = -1.0;
 }
 
 static int run_autotune(ot_plan* p);
+
+// ------------------------------------------------------------------------------------------
+// Learned warm start
+// ------------------------------------------------------------------------------------------
+static int alloc_ws(ot_plan* p) {
+  if (p->ws_src) return OT_OK;
+  const size_t P = (size_t)p->N * p->M;
+  CK(cudaMalloc(&p->ws_src, P * 8));
+  CK(cudaMalloc(&p->ws_h, P * 8));
+  CK(cudaMalloc(&p->ws_tmp, P * 8));
+  CK(cudaMalloc(&p->ws_X, P * OTGB_WS_K * 4));
+  CK(cudaMalloc(&p->ws_s, P * 4));
+  return OT_OK;
+}
+
+// u = P(src): FD Poisson solve in FP64 (row R2C, column pass dividing by the stencil
+// Laplacian's eigenvalues, row C2R)
+static int run_ws_poisson(ot_plan* p, const double* src, double* u, bool lp = false) {
+  C2<double>* sp = (C2<double>*)(p->precision ? p->spec64 : p->spec);
+  C2<double>* qq = (C2<double>*)(p->precision ? p->q64 : p->q0);
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_row_r2c<double>(src, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
+                                p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_col<double>(lp ? COL_POISSON_LP : COL_POISSON, sp, qq, nullptr, nullptr, p->N,
+                            p->M, p->tb64, nullptr, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, u, nullptr,
+                                nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream));
+  return OT_OK;
+}
+
+// ws_src = log f - log g, ws_h = P(ws_src), ws_X = features at ws_h (f, g, c: the plan's
+// translated densities and B-spline coefficients)
+static int run_ws_features(ot_plan* p) {
+  RET(alloc_ws(p));
+  const long P = (long)p->N * p->M;
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_source(p->f, p->g, p->ws_src, P, p->stream));
+  RET(run_ws_poisson(p, p->ws_src, p->ws_h));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_ws_features(p->f, p->g, p->c, p->ws_h, p->N, p->M, p->ws_X, p->stream));
+  return OT_OK;
+}
+
+// u = alpha (h + P(G MLP(X))), G the Gaussian low-pass; alpha and the network's error flag
+// in sc
+static int run_warmstart(ot_plan* p, double* u) {
+  const long P = (long)p->N * p->M;
+  RET(run_ws_features(p));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_ws_mlp(p->ws_wpack, p->ws_params, p->ws_X, P, p->ws_s, &p->sc->ws_err, p->sms,
+                       p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_widen(p->ws_s, p->ws_src, P, p->stream));
+  RET(run_ws_poisson(p, p->ws_src, p->ws_tmp, true));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_sum(p->ws_h, p->ws_tmp, u, P, p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 2,
+         launch_ws_admissible(u, p->N, p->M, p->partials, &p->sc->ticket[TK_WS],
+                              &p->sc->ws_err, &p->sc->ws_alpha, p->stream));
+  return OT_OK;
+}
 
 template <typename T>
 static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
@@ -728,8 +803,10 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   }
   RET(run_prefilter(p, p->g, p->c));
-  if (p->warm_start) {
+  if (p->warm_start == 1) {
     if (phi != p->u) CK(cudaMemcpyAsync(p->u, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  } else if (p->warm_start == 2) {
+    RET(run_warmstart(p, p->u));
   } else {
     CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
   }
@@ -788,6 +865,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   CK(cudaEventRecord(ev1, p->stream));
   RET(read_scalars(p));
   st->res_l2 = sqrt(p->hsc->res_l2sum / (double)P);
+  st->ws_alpha = p->hsc->ws_alpha;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   st->ms_total = ms;
@@ -871,6 +949,7 @@ static int capture_solve(ot_plan* p) {
            launch_translate_inputs(p->f, p->g, p->f, p->g, N, M, p->partials, p->sc,
                                    p->stream));
   RET(run_prefilter(p, p->g, p->c));
+  if (p->warm_start == 2) RET(run_warmstart(p, p->u));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 0, c32_for<T>(p)));
   const int top = (int)(p->launches - k0) + 1;
@@ -1065,6 +1144,7 @@ static int build_graph(ot_plan* p) {
   p->gkey_prec = p->precision;
   p->gkey_m = p->m;
   p->gkey_translate = p->translate;
+  p->gkey_ws = p->warm_start;
   p->gu_a = p->u;
   p->gu_b = p->ucand;
   return OT_OK;
@@ -1093,11 +1173,11 @@ static int graph_enqueue(ot_plan* p, cudaStream_t xs, const double* f_in, const 
   double* ua = p->gu_a;
   if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, xs));
   if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, xs));
-  if (p->warm_start) {
+  if (p->warm_start == 1) {
     if (phi != ua) CK(cudaMemcpyAsync(ua, phi, P * 8, cudaMemcpyDeviceToDevice, xs));
-  } else {
+  } else if (p->warm_start == 0) {
     CK(cudaMemsetAsync(ua, 0, P * 8, xs));
-  }
+  }  // 2: the captured warm start writes ua
   CK(cudaMemcpyAsync(p->sc, init, sizeof(DevScalars), cudaMemcpyHostToDevice, xs));
   CK(cudaGraphLaunch(p->gexec, xs));
   if (phi != p->uout) CK(cudaMemcpyAsync(phi, p->uout, P * 8, cudaMemcpyDeviceToDevice, xs));
@@ -1119,13 +1199,14 @@ static void graph_collect(ot_plan* p, const DevScalars* h, double mean, ot_stats
   st->res_l2 = sqrt(h->res_l2sum / (double)P);
   st->phi_mean = mean;
   st->kernel_launches = (int32_t)(h->kcount + p->top_kernels);
+  st->ws_alpha = h->ws_alpha;
   p->launches += h->kcount + p->top_kernels;
 }
 
 template <typename T>
 static int ensure_graph(ot_plan* p) {
   if (!p->gexec || p->gkey_prec != p->precision || p->gkey_m != p->m ||
-      p->gkey_translate != p->translate)
+      p->gkey_translate != p->translate || p->gkey_ws != p->warm_start)
     return build_graph<T>(p);
   return OT_OK;
 }
@@ -1175,7 +1256,7 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
   CK(cudaMemcpyAsync(p->f, f, bytes, cudaMemcpyHostToDevice, p->stream));
   CK(cudaMemcpyAsync(p->g, g, bytes, cudaMemcpyHostToDevice, p->stream));
   const bool graph = p->use_graph && !p->profile;
-  if (p->warm_start)
+  if (p->warm_start == 1)
     CK(cudaMemcpyAsync(graph ? p->uout : p->u, phi, bytes, cudaMemcpyHostToDevice, p->stream));
   int rc;
   if (graph) {
@@ -1410,4 +1491,228 @@ extern "C" int ot_fft_inverse(ot_plan* p, const double* spec, double* x) {
   if (!p || !spec || !x) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
   return p->precision ? fft_inv_impl<float>(p, spec, x) : fft_inv_impl<double>(p, spec, x);
+}
+
+// ------------------------------------------------------------------------------------------
+// Learned warm start: entry points
+// ------------------------------------------------------------------------------------------
+extern "C" int64_t ot_ws_param_count(void) { return ws_param_count(); }
+
+extern "C" int ot_ws_set_weights(ot_plan* p, const float* params_host, int64_t count) {
+  if (!p || !p->ready || !params_host || count != ws_param_count()) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  if (!p->ws_params) CK(cudaMalloc(&p->ws_params, ws_param_count() * sizeof(float)));
+  if (!p->ws_wpack) CK(cudaMalloc(&p->ws_wpack, ws_packed_bytes()));
+  RET(alloc_ws(p));
+  CK(cudaMemcpyAsync(p->ws_params, params_host, count * sizeof(float), cudaMemcpyHostToDevice,
+                     p->stream));
+  CK(launch_ws_pack(p->ws_params, p->ws_wpack, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  p->ws_have = 1;
+  return OT_OK;
+}
+
+static const char kWsMagic[8] = {'O', 'T', 'W', 'S', '0', '0', '0', '1'};
+
+extern "C" int ot_warmstart_load(ot_plan* p, const char* path) {
+  if (!p || !path) return OT_EINVAL;
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return OT_EINVAL;
+  char magic[8];
+  int64_t count = 0;
+  std::vector<float> w;
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kWsMagic, 8) == 0 &&
+            fread(&count, sizeof(count), 1, fp) == 1 && count == ws_param_count();
+  if (ok) {
+    w.resize((size_t)count);
+    ok = fread(w.data(), sizeof(float), (size_t)count, fp) == (size_t)count;
+  }
+  fclose(fp);
+  if (!ok) return OT_EINVAL;
+  return ot_ws_set_weights(p, w.data(), count);
+}
+
+extern "C" int ot_ws_save_weights(const char* path, const float* params_host, int64_t count) {
+  if (!path || !params_host || count != ws_param_count()) return OT_EINVAL;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return OT_EINVAL;
+  bool ok = fwrite(kWsMagic, 1, 8, fp) == 8 && fwrite(&count, sizeof(count), 1, fp) == 1 &&
+            fwrite(params_host, sizeof(float), (size_t)count, fp) == (size_t)count;
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? OT_OK : OT_EINVAL;
+}
+
+// translate (or copy) the inputs into the plan's f, g and prefilter g
+static int ws_prepare_inputs(ot_plan* p, const double* f, const double* g) {
+  const long P = (long)p->N * p->M;
+  set_solver_scalars(p);
+  CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  if (p->translate) {
+    LAUNCH(p, OT_PROF_OTHER, -1, 2,
+           launch_translate_inputs(f, g, p->f, p->g, p->N, p->M, p->partials, p->sc,
+                                   p->stream));
+    RET(read_scalars(p));
+    if (p->hsc->in_bad) return OT_EINVAL;
+  } else {
+    CK(cudaMemcpyAsync(p->f, f, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->g, g, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  }
+  return run_prefilter(p, p->g, p->c);
+}
+
+extern "C" int ot_ws_predict(ot_plan* p, const double* f, const double* g, double* phi0,
+                             double* alpha_out) {
+  if (!p || !p->ready || !f || !g || !phi0 || !p->ws_have) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  RET(ws_prepare_inputs(p, f, g));
+  RET(run_warmstart(p, phi0));
+  RET(read_scalars(p));
+  if (alpha_out) *alpha_out = p->hsc->ws_alpha;
+  return p->hsc->ws_err ? OT_ECUDA : OT_OK;
+}
+
+extern "C" int ot_ws_features(ot_plan* p, const double* f, const double* g,
+                              const double* phi_star, float* X, float* target) {
+  if (!p || !p->ready || !f || !g || !X || (phi_star && !target)) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  const long P = (long)p->N * p->M;
+  RET(ws_prepare_inputs(p, f, g));
+  RET(run_ws_features(p));
+  CK(cudaMemcpyAsync(X, p->ws_X, P * OTGB_WS_K * sizeof(float), cudaMemcpyDeviceToDevice,
+                     p->stream));
+  if (phi_star)
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 2,
+           launch_ws_target(phi_star, p->ws_h, p->N, p->M, p->ws_tmp, target, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_ws_mlp_forward(ot_plan* p, const float* X, int64_t rows, float* out) {
+  if (!p || !p->ready || !p->ws_have || rows < 0 || (rows > 0 && (!X || !out)))
+    return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  CK(cudaMemsetAsync(&p->sc->ws_err, 0, sizeof(int), p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_ws_mlp(p->ws_wpack, p->ws_params, X, rows, out, &p->sc->ws_err, p->sms,
+                       p->stream));
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, &p->sc->ws_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return err ? OT_ECUDA : OT_OK;
+}
+
+extern "C" int ot_ws_poisson(ot_plan* p, const double* src, int32_t lowpass, double* u) {
+  if (!p || !p->ready || !src || !u) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  RET(run_ws_poisson(p, src, u, lowpass != 0));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+struct ot_ws_trainer {
+  int B = 0, device = 0, t = 0;
+  cudaStream_t stream = 0;
+  float *params = nullptr, *m = nullptr, *v = nullptr;
+  WsTrainBuffers b{};
+  std::vector<void*> allocs;
+};
+
+extern "C" void ot_ws_trainer_destroy(ot_ws_trainer* tr) {
+  if (!tr) return;
+  cudaSetDevice(tr->device);
+  for (void* q : tr->allocs) cudaFree(q);
+  delete tr;
+}
+
+extern "C" int ot_ws_trainer_create(ot_ws_trainer** out, int32_t batch,
+                                    const float* params_host, int64_t count) {
+  if (!out) return OT_EINVAL;
+  *out = nullptr;
+  if (batch < 64 || batch > (1 << 20) || batch % 64 != 0 || !params_host ||
+      count != ws_param_count())
+    return OT_EINVAL;
+  ot_ws_trainer* tr = new (std::nothrow) ot_ws_trainer();
+  if (!tr) return OT_ENOMEM;
+  tr->B = batch;
+  cudaGetDevice(&tr->device);
+  const long n = ws_param_count(), B = batch, H = OTGB_WS_H;
+  const long S = (B + WS_ROW_CHUNK - 1) / WS_ROW_CHUNK;
+  bool failed = false;
+  auto get = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    tr->allocs.push_back(q);
+    return q;
+  };
+  tr->params = (float*)get(n * 4);
+  tr->m = (float*)get(n * 4);
+  tr->v = (float*)get(n * 4);
+  WsTrainBuffers& b = tr->b;
+  b.grad = (float*)get(n * 4);
+  b.Xb = (float*)get(B * OTGB_WS_K * 4);
+  b.tb = (float*)get(B * 4);
+  float** planes[] = {&b.Z0, &b.A0, &b.Z1, &b.A1, &b.Z2, &b.A2, &b.dZ1, &b.dZ2};
+  for (float** q : planes) *q = (float*)get(B * H * 4);
+  b.dy = (float*)get(B * 4);
+  b.part = (float*)get(S * H * H * 4);
+  b.loss_part = (double*)get(((B + 7) / 8) * 8);
+  b.loss = (double*)get(8);
+  if (failed) {
+    cudaGetLastError();
+    ot_ws_trainer_destroy(tr);
+    return OT_ENOMEM;
+  }
+  if (cudaMemcpy(tr->params, params_host, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(tr->m, 0, n * 4) != cudaSuccess || cudaMemset(tr->v, 0, n * 4) != cudaSuccess) {
+    ot_ws_trainer_destroy(tr);
+    return OT_ECUDA;
+  }
+  *out = tr;
+  return OT_OK;
+}
+
+extern "C" int ot_ws_trainer_set_stream(ot_ws_trainer* tr, void* s) {
+  if (!tr) return OT_EINVAL;
+  tr->stream = (cudaStream_t)s;
+  return OT_OK;
+}
+
+extern "C" int ot_ws_trainer_grad(ot_ws_trainer* tr, const float* X, const float* t,
+                                  const int64_t* idx, float* grad_host, double* loss_host) {
+  if (!tr || !X || !t || !idx) return OT_EINVAL;
+  CK(cudaSetDevice(tr->device));
+  CK(launch_ws_grad(tr->params, X, t, (const long long*)idx, tr->B, tr->b, tr->stream));
+  if (grad_host)
+    CK(cudaMemcpyAsync(grad_host, tr->b.grad, ws_param_count() * 4, cudaMemcpyDeviceToHost,
+                       tr->stream));
+  if (loss_host)
+    CK(cudaMemcpyAsync(loss_host, tr->b.loss, 8, cudaMemcpyDeviceToHost, tr->stream));
+  CK(cudaStreamSynchronize(tr->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_ws_trainer_step(ot_ws_trainer* tr, const float* X, const float* t,
+                                  const int64_t* idx, float lr, double* loss_host) {
+  if (!tr || !X || !t || !idx || !(lr > 0.f)) return OT_EINVAL;
+  CK(cudaSetDevice(tr->device));
+  CK(launch_ws_grad(tr->params, X, t, (const long long*)idx, tr->B, tr->b, tr->stream));
+  tr->t += 1;
+  CK(launch_ws_adam(tr->params, tr->m, tr->v, tr->b.grad, ws_param_count(), lr, tr->t,
+                    tr->stream));
+  if (loss_host) {
+    CK(cudaMemcpyAsync(loss_host, tr->b.loss, 8, cudaMemcpyDeviceToHost, tr->stream));
+    CK(cudaStreamSynchronize(tr->stream));
+  }
+  return OT_OK;
+}
+
+extern "C" int ot_ws_trainer_get_params(ot_ws_trainer* tr, float* params_host, int64_t count) {
+  if (!tr || !params_host || count != ws_param_count()) return OT_EINVAL;
+  CK(cudaSetDevice(tr->device));
+  CK(cudaMemcpyAsync(params_host, tr->params, count * 4, cudaMemcpyDeviceToHost, tr->stream));
+  CK(cudaStreamSynchronize(tr->stream));
+  return OT_OK;
 }

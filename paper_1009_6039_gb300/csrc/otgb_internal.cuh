@@ -45,6 +45,10 @@ struct DevScalars {
   long long kcount;  // kernels executed by the graph-launched solve
   // conditional-node handles of the captured solve (0 outside a graph)
   unsigned long long h_newton, h_cycle, h_restart, h_halve, h_step[OTGB_MAXM];
+  // learned warm start: the scale alpha applied to the network's potential, and an error
+  // flag set by the network kernel (a bounded wait that gave up)
+  double ws_alpha;
+  int ws_err;
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
 };
@@ -65,10 +69,20 @@ struct UPair {
   double* b;
 };
 
-enum { TK_INPUT = 0, TK_RESID = 1, TK_DOTS = 2, TK_UPDATE = 3, TK_INIT = 4, TK_NORM = 5 };
+enum { TK_INPUT = 0, TK_RESID = 1, TK_DOTS = 2, TK_UPDATE = 3, TK_INIT = 4, TK_NORM = 5, TK_WS = 6 };
 
 // Spectral kernels (instantiated for float and double) --------------------------------
-enum ColMode { COL_FWD = 0, COL_INV = 1, COL_MATVEC = 2, COL_LBARINV = 3, COL_PREFILTER = 4 };
+// COL_POISSON: divide by the eigenvalues of the 4th-order stencil Laplacian (0 at k = 0);
+// COL_POISSON_LP: the same times the Gaussian exp(-((k1/(M/4))^2 + (k2/(N/4))^2) / 2)
+enum ColMode {
+  COL_FWD = 0,
+  COL_INV = 1,
+  COL_MATVEC = 2,
+  COL_LBARINV = 3,
+  COL_PREFILTER = 4,
+  COL_POISSON = 5,
+  COL_POISSON_LP = 6
+};
 enum RowInvMode { ROWINV_PLAIN = 0, ROWINV_COMBINE = 1, ROWINV_UPDATE = 2 };
 
 struct SpecTables {
@@ -149,5 +163,50 @@ cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars*
 template <typename T>
 cudaError_t launch_convert(const void* in, int in_is_double, void* out, int out_is_double,
                            long n, cudaStream_t st);
+
+// Learned warm start ---------------------------------------------------------------------
+#define OTGB_WS_K 16    // features per grid point
+#define OTGB_WS_H 128   // hidden units per layer (three hidden layers)
+#define WS_ROW_CHUNK 2048  // rows per partial sum of the weight gradients
+constexpr long ws_param_count() {
+  return (long)OTGB_WS_H * OTGB_WS_K + OTGB_WS_H +
+         2 * ((long)OTGB_WS_H * OTGB_WS_H + OTGB_WS_H) + OTGB_WS_H + 1;
+}
+// buffers of one training step with B rows (FP32 unless noted)
+struct WsTrainBuffers {
+  float *Xb, *tb;                  // gathered rows (B x 16) and targets (B)
+  float *Z0, *A0, *Z1, *A1, *Z2, *A2;  // pre-activations / activations (B x H each)
+  float *dy, *dZ1, *dZ2;           // output gradient (B), layer gradients (B x H)
+  float *part;                     // partial sums: ceil(B / WS_ROW_CHUNK) x H x H
+  float *grad;                     // gradient (ws_param_count())
+  double *loss_part, *loss;        // ceil(B / 8) partials, mean squared error
+};
+cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
+                             cudaStream_t st);
+cudaError_t launch_ws_features(const double* f, const double* g, const double* c,
+                               const double* h, int N, int M, float* X, cudaStream_t st);
+// t = (D_xx + D_yy)(phi - h); scratch: N x M FP64
+cudaError_t launch_ws_target(const double* phi, const double* h, int N, int M, double* scratch,
+                             float* t, cudaStream_t st);
+// out = (double)s
+cudaError_t launch_ws_widen(const float* s, double* out, long P, cudaStream_t st);
+// u = h + t
+cudaError_t launch_ws_sum(const double* h, const double* t, double* u, long P, cudaStream_t st);
+int ws_admissible_blocks();
+// alpha = largest of 1, 1/2, 1/4, 1/8 with det(I + alpha D^2 u) > 0 (0 if none or *err);
+// then u *= alpha.  partials: 4 x ws_admissible_blocks() doubles; *ticket must start at 0.
+cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
+                                 unsigned int* ticket, const int* err, double* alpha,
+                                 cudaStream_t st);
+size_t ws_packed_bytes();
+cudaError_t launch_ws_pack(const float* params, unsigned char* wpack, cudaStream_t st);
+// BF16 tensor-core forward of the network: out[r] = MLP(X[r, :]); *err set on a timeout
+cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const float* X,
+                          long rows, float* out, int* err, int sms, cudaStream_t st);
+// gradient of the mean squared error over the rows idx[0..B) of (X, t) into tb.grad
+cudaError_t launch_ws_grad(const float* params, const float* X, const float* t,
+                           const long long* idx, int B, WsTrainBuffers& tb, cudaStream_t st);
+cudaError_t launch_ws_adam(float* p, float* m, float* v, const float* g, long n, float lr,
+                           int t, cudaStream_t st);
 
 }  // namespace otgb

@@ -338,6 +338,24 @@ __host__ __device__ inline bool warp_fft_ok(int L) {
 }
 
 // signed frequency of index n of length L, with a Nyquist flag
+// Eigenvalue of the 4th-order second-difference stencil (-1, 16, -30, 16, -1) / (12 h^2)
+// on L points at the frequency with cosine c:  L^2 (-2 cos 2t + 32 cos t - 30) / 12
+// = L^2 (1 - c)(c - 7) / 3.
+template <typename T>
+__device__ __forceinline__ T fd_lap(T c, int L) {
+  return ((T)1 - c) * (c - (T)7) / (T)3 * (T)L * (T)L;
+}
+template <typename T>
+__device__ __forceinline__ T inv_or_zero(T x) {
+  return x == (T)0 ? (T)0 : (T)1 / x;
+}
+// Gaussian low-pass exp(-((k1 / (M/4))^2 + (k2 / (N/4))^2) / 2) of COL_POISSON_LP (1 else)
+template <typename T, int MODE>
+__device__ __forceinline__ T lowpass(int k1, int k2, int M, int N) {
+  if (MODE != COL_POISSON_LP) return (T)1;
+  const double a = (double)k1 / (0.25 * M), b = (double)k2 / (0.25 * N);
+  return (T)exp(-0.5 * (a * a + b * b));
+}
 __device__ __forceinline__ int sfreq(int n, int L, bool* nyq) {
   *nyq = (2 * n == L);
   return (2 * n <= L) ? n : n - L;
@@ -493,6 +511,11 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
           const T by = ((T)2 + twN[k].x) / (T)3;
           A = cscale<T>(A, (T)1 / by);           // k1 = 0: factor 1
           B = cscale<T>(B, (T)3 / by);           // k1 = M/2: factor 1/3
+        } else if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
+          const T ly = fd_lap<T>(twN[k].x, N);
+          A = cscale<T>(A, inv_or_zero<T>(ly) * lowpass<T, MODE>(0, k2, M, N));
+          B = cscale<T>(B, inv_or_zero<T>(fd_lap<T>((T)-1, M) + ly) *
+                               lowpass<T, MODE>(M / 2, k2, M, N));
         } else {
           A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
           B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
@@ -512,6 +535,9 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
           const T by = ((T)2 + twN[k].x) / (T)3;
           const T bx = ((T)2 + twM[col].x) / (T)3;
           r = cscale<T>(z, (T)1 / (bx * by));
+        } else if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
+          r = cscale<T>(z, inv_or_zero<T>(fd_lap<T>(twM[col].x, M) + fd_lap<T>(twN[k].x, N)) *
+                               lowpass<T, MODE>(col, k2, M, N));
         } else {
           r = cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z);
         }
@@ -1264,6 +1290,10 @@ cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T
     case COL_LBARINV: return col_E<T, E, COL_LBARINV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_PREFILTER:
       return col_E<T, E, COL_PREFILTER>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_POISSON:
+      return col_E<T, E, COL_POISSON>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
+    case COL_POISSON_LP:
+      return col_E<T, E, COL_POISSON_LP>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   }
   return cudaErrorInvalidValue;
 }

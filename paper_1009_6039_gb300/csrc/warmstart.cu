@@ -1,0 +1,826 @@
+// Learned warm start: the kernels of the network's input features, of its training (FP32)
+// and of its inference (BF16 on the tcgen05 tensor cores with an FP32 accumulator in TMEM).
+//
+// The paper starts Newton from u0 = 0; the damped iteration only needs an admissible start,
+// det(I + D^2 u0) > 0 (Theorem convproof).  The warm start is
+//   h  = P(log f - log g)        P: mean-zero inverse of the 4th-order stencil Laplacian
+//   x  = 16 features per point at h (below)
+//   s  = MLP(x), 16 -> 128 -> 128 -> 128 -> 1, SiLU, trained to predict Lap_h(phi* - h)
+//   u0 = alpha (h + P(G s)), G the Gaussian low-pass exp(-((k1/(M/4))^2 + (k2/(N/4))^2)/2),
+//        alpha the largest of 1, 1/2, 1/4, 1/8 with det(I + alpha D^2 u0) > 0 everywhere,
+//        else 0 (the zero start).
+// Parameters: one flat FP32 vector W0[H,16], b0[H], W1[H,H], b1[H], W2[H,H], b2[H], w3[H], b3.
+#include <math.h>
+#include <stdint.h>
+
+#include <cuda_bf16.h>
+
+#include "otgb_internal.cuh"
+
+namespace otgb {
+
+namespace {
+
+constexpr int K = OTGB_WS_K, H = OTGB_WS_H;
+constexpr float kFloor = 1e-3f;
+
+__device__ __forceinline__ long wrapi(long a, long L) {
+  const long r = a % L;
+  return r < 0 ? r + L : r;
+}
+
+// 4th-order centred stencils of a periodic FP64 field (spacing 1/M along j, 1/N along i)
+struct Stencil {
+  const double* u;
+  int N, M;
+  __device__ double at(long i, long j) const { return u[wrapi(i, N) * M + wrapi(j, M)]; }
+  __device__ double dx(long i, long j) const {
+    return (-at(i, j + 2) + 8.0 * at(i, j + 1) - 8.0 * at(i, j - 1) + at(i, j - 2)) *
+           (double)M / 12.0;
+  }
+  __device__ double dy(long i, long j) const {
+    return (-at(i + 2, j) + 8.0 * at(i + 1, j) - 8.0 * at(i - 1, j) + at(i - 2, j)) *
+           (double)N / 12.0;
+  }
+  __device__ double dxx(long i, long j) const {
+    return (-at(i, j + 2) + 16.0 * at(i, j + 1) - 30.0 * at(i, j) + 16.0 * at(i, j - 1) -
+            at(i, j - 2)) * (double)M * (double)M / 12.0;
+  }
+  __device__ double dyy(long i, long j) const {
+    return (-at(i + 2, j) + 16.0 * at(i + 1, j) - 30.0 * at(i, j) + 16.0 * at(i - 1, j) -
+            at(i - 2, j)) * (double)N * (double)N / 12.0;
+  }
+  __device__ double dxy(long i, long j) const {
+    return (-dy(i, j + 2) + 8.0 * dy(i, j + 1) - 8.0 * dy(i, j - 1) + dy(i, j - 2)) *
+           (double)M / 12.0;
+  }
+};
+
+// Cubic B-spline basis weights (and their derivatives) at fractional offset t in [0, 1)
+// for the four taps at offsets -1, 0, 1, 2.
+__device__ __forceinline__ void cubic_bspline(double t, double w[4], double dw[4]) {
+  const double t2 = t * t, t3 = t2 * t, s = 1.0 - t;
+  w[0] = s * s * s / 6.0;
+  w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) / 6.0;
+  w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) / 6.0;
+  w[3] = t3 / 6.0;
+  dw[0] = -s * s / 2.0;
+  dw[1] = (3.0 * t2 - 4.0 * t) / 2.0;
+  dw[2] = (-3.0 * t2 + 2.0 * t + 1.0) / 2.0;
+  dw[3] = t2 / 2.0;
+}
+
+// value and gradient (per unit length) of the interpolant with coefficients c at grid
+// position (xp along j, yp along i)
+__device__ void interp(const double* c, int N, int M, double xp, double yp, double* G,
+                       double* Gx, double* Gy) {
+  const double fx = floor(xp), fy = floor(yp);
+  double wx[4], dwx[4], wy[4], dwy[4];
+  cubic_bspline(xp - fx, wx, dwx);
+  cubic_bspline(yp - fy, wy, dwy);
+  const long j0 = (long)fx - 1, i0 = (long)fy - 1;
+  double v = 0.0, gx = 0.0, gy = 0.0;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const double* row = c + wrapi(i0 + b, N) * M;
+    double rv = 0.0, rd = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const double cv = row[wrapi(j0 + a, M)];
+      rv += cv * wx[a];
+      rd += cv * dwx[a];
+    }
+    v += rv * wy[b];
+    gx += rd * wy[b];
+    gy += rv * dwy[b];
+  }
+  *G = v;
+  *Gx = gx * (double)M;
+  *Gy = gy * (double)N;
+}
+
+__global__ void k_ws_source(const double* __restrict__ f, const double* __restrict__ g,
+                            double* __restrict__ src, long P) {
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    src[p] = log(f[p]) - log(g[p]);
+}
+
+// features at the potential h (FP64 arithmetic, stored as FP32):
+//  [log f, log g, lg, r = log f - lg - ld, hxx + hyy, hxx - hyy, 2 hxy, hxx hyy - hxy^2,
+//   10 hx, 10 hy, 0.1 Gx / Gc, 0.1 Gy / Gc, (Gx hx + Gy hy) / Gc, (hxx - hyy)^2 + 4 hxy^2,
+//   r (hxx + hyy), 0],   Gc = max(G, floor), lg = log Gc, ld = log max(det, floor),
+// G, Gx, Gy the interpolant of g at T = x + grad h, det = det(I + D^2 h).
+__global__ void k_ws_features(const double* __restrict__ f, const double* __restrict__ g,
+                              const double* __restrict__ c, const double* __restrict__ h,
+                              int N, int M, float* __restrict__ X) {
+  const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long i = blockIdx.y;
+  if (j >= M) return;
+  const Stencil S{h, N, M};
+  const double hx = S.dx(i, j), hy = S.dy(i, j), hxx = S.dxx(i, j), hyy = S.dyy(i, j);
+  const double hxy = S.dxy(i, j);
+  double G, Gx, Gy;
+  interp(c, N, M, (double)j + (double)M * hx, (double)i + (double)N * hy, &G, &Gx, &Gy);
+  const double det = (1.0 + hxx) * (1.0 + hyy) - hxy * hxy;
+  const double Gc = fmax(G, (double)kFloor);
+  const long p = i * M + j;
+  const double lf = log(f[p]), lg = log(Gc), ld = log(fmax(det, (double)kFloor));
+  const double r = lf - lg - ld;
+  float x[16];
+  x[0] = (float)lf;
+  x[1] = (float)log(g[p]);
+  x[2] = (float)lg;
+  x[3] = (float)r;
+  x[4] = (float)(hxx + hyy);
+  x[5] = (float)(hxx - hyy);
+  x[6] = (float)(2.0 * hxy);
+  x[7] = (float)(hxx * hyy - hxy * hxy);
+  x[8] = (float)(10.0 * hx);
+  x[9] = (float)(10.0 * hy);
+  x[10] = (float)(0.1 * Gx / Gc);
+  x[11] = (float)(0.1 * Gy / Gc);
+  x[12] = (float)((Gx * hx + Gy * hy) / Gc);
+  x[13] = (float)((hxx - hyy) * (hxx - hyy) + 4.0 * hxy * hxy);
+  x[14] = (float)(r * (hxx + hyy));
+  x[15] = 0.f;
+  float4* o = reinterpret_cast<float4*>(X + p * 16);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+
+// training target s* = (D_xx + D_yy)(phi - h)
+__global__ void k_ws_target(const double* __restrict__ phi, const double* __restrict__ h,
+                            int N, int M, double* __restrict__ diff, float* __restrict__ t,
+                            int stage) {
+  const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long i = blockIdx.y;
+  if (j >= M) return;
+  const long p = i * M + j;
+  if (stage == 0) {
+    diff[p] = phi[p] - h[p];
+  } else {
+    const Stencil S{diff, N, M};
+    t[p] = (float)(S.dxx(i, j) + S.dyy(i, j));
+  }
+}
+
+__global__ void k_ws_widen(const float* __restrict__ s, double* __restrict__ out, long P) {
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    out[p] = (double)s[p];
+}
+
+__global__ void k_ws_sum(const double* __restrict__ h, const double* __restrict__ t,
+                         double* __restrict__ u, long P) {
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    u[p] = h[p] + t[p];
+}
+
+// min over the grid of det(I + alpha D^2 u) for each alpha in {1, 1/2, 1/4, 1/8}; the last
+// block picks the largest admissible alpha (0 if none, or if the network reported an error)
+// and writes it to *alpha.
+__global__ void k_ws_admissible(const double* __restrict__ u, int N, int M,
+                                double* __restrict__ partials, unsigned int* ticket,
+                                const int* __restrict__ err, double* alpha) {
+  __shared__ double red[4][32];
+  __shared__ bool last;
+  double mn[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  const long P = (long)N * M;
+  const Stencil S{u, N, M};
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x) {
+    const long i = p / M, j = p - i * M;
+    const double uxx = S.dxx(i, j), uyy = S.dyy(i, j), uxy = S.dxy(i, j);
+    double a = 1.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q, a *= 0.5)
+      mn[q] = fmin(mn[q], (1.0 + a * uxx) * (1.0 + a * uyy) - a * a * uxy * uxy);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    double v = mn[q];
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 4; ++q) {
+      double v = INFINITY;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmin(v, red[q][w]);
+      partials[blockIdx.x * 4 + q] = v;
+    }
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double a = 1.0, pick = 0.0;
+  for (int q = 0; q < 4; ++q, a *= 0.5) {
+    double v = INFINITY;
+    for (unsigned int b = 0; b < gridDim.x; ++b)
+      v = fmin(v, ((volatile const double*)partials)[b * 4 + q]);
+    if (v > 0.0) {
+      pick = a;
+      break;
+    }
+  }
+  if (err && *err) pick = 0.0;
+  *alpha = pick;
+  *ticket = 0u;
+}
+
+__global__ void k_ws_scale(double* __restrict__ u, long P, const double* __restrict__ alpha) {
+  const double a = *alpha;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    u[p] *= a;
+}
+
+// ---------------------------------------------------------------------------------------
+// BF16 inference on the tensor cores (tcgen05).
+//
+// One CTA of 128 threads takes 128-row tiles of X: thread r owns row r, which is TMEM lane
+// r of the accumulator (warp w reads lanes 32w..32w+31).  Per tile: X (converted to BF16)
+// -> MMA with W0 (K = 16) -> TMEM -> bias + SiLU -> BF16 activations in shared memory ->
+// 8 MMAs with W1 (K = 128) -> ... -> W2 -> bias + SiLU -> dot with w3 in FP32 -> s.
+//
+// Operands are K-major BF16 in the no-swizzle canonical layout: 8-row x 16-byte core
+// matrices, the two core matrices of a 16-wide K block 128 bytes apart (LBO) and
+// consecutive 8-row groups 256 bytes apart (SBO); each K block of a 128-row operand is a
+// contiguous 4 KB.  Byte offset of element (r, k):
+//   (k / 16) * 4096 + (r / 8) * 256 + ((k / 8) % 2) * 128 + (r % 8) * 16 + (k % 8) * 2.
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int op_offset(int r, int k) {
+  return (k >> 4) * 4096 + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+constexpr int SM_W0 = 0;                       // 4 KB
+constexpr int SM_W1 = SM_W0 + 4096;            // 32 KB
+constexpr int SM_W2 = SM_W1 + 32768;           // 32 KB
+constexpr int SM_A = SM_W2 + 32768;            // 32 KB activations / X tile
+constexpr int SM_BIAS = SM_A + 32768;          // b0, b1, b2, w3 (4 x 128 FP32), b3
+constexpr int SM_BAR = SM_BIAS + 4 * 128 * 4 + 16;
+constexpr int SM_TMEM = SM_BAR + 8;
+constexpr int SM_TOTAL = SM_TMEM + 8 + 128;    // + alignment slack
+constexpr int PACKED_W_BYTES = SM_A - SM_W0;   // 69632: W0, W1, W2 in operand layout
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1 (bit 46),
+// base offset 0, no swizzle
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// bounded wait for the mbarrier phase with parity `par` (about a million polls, far more
+// than an MMA group takes); false if it gave up
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par) {
+  for (long it = 0; it < (1l << 20); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(par)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// store 8 consecutive BF16 values of row r starting at column k0 (a multiple of 8)
+__device__ __forceinline__ void st_row8(unsigned char* base, int r, int k0, const float* v) {
+  uint4 q;
+  q.x = pack_bf16(v[0], v[1]);
+  q.y = pack_bf16(v[2], v[3]);
+  q.z = pack_bf16(v[4], v[5]);
+  q.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(base + op_offset(r, k0)) = q;
+}
+
+// layer readout: 128 accumulator columns of this thread's row -> bias + SiLU -> BF16 tile
+__device__ __forceinline__ void readout_hidden(uint32_t trow, const float* bias,
+                                               unsigned char* sA, int r) {
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    float v[32];
+    tmem_ld32(trow + 32 * c, v);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = silu_f(v[q] + bias[32 * c + q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) st_row8(sA, r, 32 * c + 8 * q, v + 8 * q);
+  }
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_ws_mlp_tc(const unsigned char* __restrict__ wpack, const float* __restrict__ params,
+                const float* __restrict__ X, long rows, float* __restrict__ out,
+                int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sm =
+      (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int r = threadIdx.x, warp = r >> 5;
+  float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
+  const uint32_t bar = smem_u32(sm + SM_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
+
+  // weights (pre-packed BF16 operand layout) and FP32 biases into shared memory
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(wpack);
+    uint4* dst = reinterpret_cast<uint4*>(sm + SM_W0);
+    for (int q = r; q < PACKED_W_BYTES / 16; q += blockDim.x) dst[q] = src[q];
+    sb[r] = params[H * K + r];                          // b0
+    sb[128 + r] = params[H * K + H + H * H + r];        // b1
+    sb[256 + r] = params[H * K + 2 * H + 2 * H * H + r];  // b2
+    sb[384 + r] = params[H * K + 3 * H + 2 * H * H + r];  // w3
+    if (r == 0) sb[512] = params[H * K + 4 * H + 2 * H * H];  // b3
+  }
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+            smem_u32(tmem_slot))
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (r == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  unsigned char* sA = sm + SM_A;
+  const uint32_t aA = smem_u32(sA), aW0 = smem_u32(sm + SM_W0), aW1 = smem_u32(sm + SM_W1),
+                 aW2 = smem_u32(sm + SM_W2);
+  uint32_t phase = 0;
+  bool ok = true;
+  const long ntiles = (rows + 127) / 128;
+  for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long row = tile * 128 + r;
+    // X row -> BF16 (K block 0 of the A operand)
+    {
+      float v[16];
+      if (row < rows) {
+        const float4* xr = reinterpret_cast<const float4*>(X + row * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 t = __ldg(xr + q);
+          v[4 * q] = t.x;
+          v[4 * q + 1] = t.y;
+          v[4 * q + 2] = t.z;
+          v[4 * q + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+      }
+      st_row8(sA, r, 0, v);
+      st_row8(sA, r, 8, v + 8);
+    }
+    // layer 0: D = X W0^T
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (r == 0) {
+      fence_after();
+      mma_bf16(tmem, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
+      mma_commit(bar);
+    }
+    ok = __syncthreads_and(bar_wait(bar, phase));
+    fence_after();
+    if (!ok) break;
+    phase ^= 1;
+    readout_hidden(trow, sb, sA, r);
+    // layers 1 and 2: D = A W^T, K = 128 in eight K blocks of 16
+#pragma unroll 1
+    for (int layer = 1; layer <= 2 && ok; ++layer) {
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      if (r == 0) {
+        fence_after();
+        const uint32_t aW = layer == 1 ? aW1 : aW2;
+#pragma unroll
+        for (int kb = 0; kb < 8; ++kb)
+          mma_bf16(tmem, mdesc(aA + kb * 4096, 128, 256), mdesc(aW + kb * 4096, 128, 256),
+                   kb > 0 ? 1u : 0u);
+        mma_commit(bar);
+      }
+      ok = __syncthreads_and(bar_wait(bar, phase));
+      fence_after();
+      if (!ok) break;
+      phase ^= 1;
+      if (layer == 1) {
+        readout_hidden(trow, sb + 128, sA, r);
+      } else {
+        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32
+        float acc = sb[512];
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+          float v[32];
+          tmem_ld32(trow + 32 * c, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            acc = fmaf(sb[384 + 32 * c + q], silu_f(v[q] + sb[256 + 32 * c + q]), acc);
+        }
+        if (row < rows) out[row] = acc;
+      }
+    }
+    fence_before();
+    __syncthreads();
+  }
+  if (!ok) {
+    if (err) atomicExch(err, 1);
+    // let an MMA still in flight finish before its TMEM goes away (bounded)
+    bar_wait(bar, phase);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem)
+                 : "memory");
+}
+
+// FP32 parameters -> BF16 W0, W1, W2 in the operand layout (rows = output units)
+__global__ void k_ws_pack(const float* __restrict__ params, unsigned char* __restrict__ wpack) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // one 8-element group
+  const int n0 = H * K / 8, n1 = H * H / 8;
+  if (idx >= n0 + 2 * n1) return;
+  int layer, g = idx;
+  if (g < n0) {
+    layer = 0;
+  } else if (g < n0 + n1) {
+    layer = 1;
+    g -= n0;
+  } else {
+    layer = 2;
+    g -= n0 + n1;
+  }
+  const int kd = layer == 0 ? K : H;
+  const int row = g / (kd / 8), k0 = (g % (kd / 8)) * 8;
+  const float* w = params + (layer == 0 ? 0 : (layer == 1 ? H * K + H : H * K + 2 * H + H * H));
+  float v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = w[row * kd + k0 + q];
+  unsigned char* base = wpack + (layer == 0 ? 0 : (layer == 1 ? 4096 : 4096 + 32768));
+  st_row8(base, row, k0, v);
+}
+
+// ---------------------------------------------------------------------------------------
+// Training (FP32 on the CUDA cores: a few GFLOP per step, run offline).
+// C[m, n] = sum_k A(m, k) B(k, n) over a 64 x 64 tile per block, 4 x 4 per thread,
+// with A(m, k) = TA ? A[k lda + m] : A[m lda + k] and B(k, n) = TB ? B[n ldb + k] : B[k ldb + n].
+// blockIdx.z selects a slice [z kchunk, (z + 1) kchunk) of k (partial sums to C + z Mr ldc).
+// Epilogues: 0 plain; 1 Z = acc + bias[n], C2 = SiLU(Z); 2 C = acc SiLU'(zp[m, n]).
+// ---------------------------------------------------------------------------------------
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(256)
+    k_gemm(int Mr, int Nc, int Kd, const float* __restrict__ A, int lda,
+           const float* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
+           const float* __restrict__ bias, float* __restrict__ C2, const float* __restrict__ zp,
+           int kchunk) {
+  __shared__ float As[16][64 + 4], Bs[16][64 + 4];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int kbeg = blockIdx.z * kchunk, kend = min(Kd, kbeg + kchunk);
+  float acc[4][4] = {};
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    for (int q = threadIdx.x; q < 16 * 64; q += 256) {
+      const int kk = TA ? q / 64 : q % 16, mm = TA ? q % 64 : q / 16;
+      const int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < Mr && k < kend) ? (TA ? A[(long)k * lda + m] : A[(long)m * lda + k]) : 0.f;
+      const int kb = TB ? q % 16 : q / 64, nn = TB ? q / 16 : q % 64;
+      const int n = n0 + nn, k2 = k0 + kb;
+      Bs[kb][nn] = (n < Nc && k2 < kend) ? (TB ? B[(long)n * ldb + k2] : B[(long)k2 * ldb + n]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty * 4 + q];
+        b[q] = Bs[kk][tx * 4 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+  float* Cz = C + (long)blockIdx.z * Mr * ldc;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int m = m0 + ty * 4 + p;
+    if (m >= Mr) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int n = n0 + tx * 4 + q;
+      if (n >= Nc) continue;
+      const long o = (long)m * ldc + n;
+      float v = acc[p][q];
+      if (EPI == 1) {
+        v += bias[n];
+        Cz[o] = v;
+        C2[o] = v / (1.0f + expf(-v));
+      } else if (EPI == 2) {
+        const float z = zp[o], s = 1.0f / (1.0f + expf(-z));
+        Cz[o] = v * s * (1.0f + z * (1.0f - s));
+      } else {
+        Cz[o] = v;
+      }
+    }
+  }
+}
+
+// sum of S partial planes of n values each (fixed order) into out
+__global__ void k_sum_partials(const float* __restrict__ part, int S, long n,
+                               float* __restrict__ out) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n;
+       q += (long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < S; ++z) s += part[(long)z * n + q];
+    out[q] = s;
+  }
+}
+
+// column sums of a (rows x cols) matrix over row chunks of `chunk` rows: part[z, col]
+__global__ void k_colsum(const float* __restrict__ A, int rows, int cols, int chunk,
+                         float* __restrict__ part) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= cols) return;
+  const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
+  float s = 0.f;
+  for (int rr = r0; rr < r1; ++rr) s += A[(long)rr * cols + col];
+  part[(long)blockIdx.y * cols + col] = s;
+}
+
+__global__ void k_gather_rows(const float* __restrict__ X, const float* __restrict__ t,
+                              const long long* __restrict__ idx, int B, float* __restrict__ Xb,
+                              float* __restrict__ tb) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B * 4) return;
+  const int b = q >> 2, part = q & 3;
+  const long long r = idx[b];
+  reinterpret_cast<float4*>(Xb)[(long)b * 4 + part] =
+      reinterpret_cast<const float4*>(X)[r * 4 + part];
+  if (part == 0) tb[b] = t[r];
+}
+
+// output layer: y = A2 w3 + b3, e = y - t, dy = 2 e / B, dZ2 = dy w3 SiLU'(Z2); loss partials
+__global__ void k_ws_out(const float* __restrict__ A2, const float* __restrict__ Z2,
+                         const float* __restrict__ params, const float* __restrict__ tb, int B,
+                         float* __restrict__ dy, float* __restrict__ dZ2,
+                         double* __restrict__ loss_part) {
+  const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const float* w3 = params + H * K + 3 * H + 2 * H * H;
+  const float b3 = params[H * K + 4 * H + 2 * H * H];
+  double e2 = 0.0;
+  if (b < B) {
+    float s = 0.f;
+    for (int j = lane; j < H; j += 32) s = fmaf(A2[(long)b * H + j], w3[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float e = s + b3 - tb[b];
+    const float d = 2.0f * e / (float)B;
+    if (lane == 0) dy[b] = d;
+    for (int j = lane; j < H; j += 32) {
+      const float z = Z2[(long)b * H + j], sg = 1.0f / (1.0f + expf(-z));
+      dZ2[(long)b * H + j] = d * w3[j] * sg * (1.0f + z * (1.0f - sg));
+    }
+    e2 = (double)e * (double)e;
+  }
+  __shared__ double red[8];
+  if (lane == 0) red[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sum_f64(const double* __restrict__ part, int n, double scale,
+                          double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int q = 0; q < n; ++q) s += part[q];
+  *out = s * scale;
+}
+
+__global__ void k_adam(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, long n, float lr, float b1, float b2,
+                       float c1, float c2, float eps) {
+  for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n;
+       q += (long)gridDim.x * blockDim.x) {
+    const float gq = g[q];
+    const float mq = b1 * m[q] + (1.0f - b1) * gq;
+    const float vq = b2 * v[q] + (1.0f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+  }
+}
+
+inline dim3 grid2(int N, int M) { return dim3((M + 127) / 128, N); }
+inline int nblk(long P, int t = 256) {
+  long b = (P + t - 1) / t;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
+                             cudaStream_t st) {
+  k_ws_source<<<nblk(P), 256, 0, st>>>(f, g, src, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_features(const double* f, const double* g, const double* c,
+                               const double* h, int N, int M, float* X, cudaStream_t st) {
+  k_ws_features<<<grid2(N, M), 128, 0, st>>>(f, g, c, h, N, M, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_target(const double* phi, const double* h, int N, int M, double* scratch,
+                             float* t, cudaStream_t st) {
+  k_ws_target<<<grid2(N, M), 128, 0, st>>>(phi, h, N, M, scratch, t, 0);
+  k_ws_target<<<grid2(N, M), 128, 0, st>>>(phi, h, N, M, scratch, t, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_widen(const float* s, double* out, long P, cudaStream_t st) {
+  k_ws_widen<<<nblk(P), 256, 0, st>>>(s, out, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_sum(const double* h, const double* t, double* u, long P, cudaStream_t st) {
+  k_ws_sum<<<nblk(P), 256, 0, st>>>(h, t, u, P);
+  return cudaGetLastError();
+}
+
+int ws_admissible_blocks() { return 2 * 152; }
+
+cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
+                                 unsigned int* ticket, const int* err, double* alpha,
+                                 cudaStream_t st) {
+  k_ws_admissible<<<ws_admissible_blocks(), 256, 0, st>>>(u, N, M, partials, ticket, err, alpha);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long P = (long)N * M;
+  k_ws_scale<<<nblk(P), 256, 0, st>>>(u, P, alpha);
+  return cudaGetLastError();
+}
+
+size_t ws_packed_bytes() { return PACKED_W_BYTES; }
+
+cudaError_t launch_ws_pack(const float* params, unsigned char* wpack, cudaStream_t st) {
+  const int n = (H * K + 2 * H * H) / 8;
+  k_ws_pack<<<(n + 255) / 256, 256, 0, st>>>(params, wpack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const float* X,
+                          long rows, float* out, int* err, int sms, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_ws_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SM_TOTAL);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const long tiles = (rows + 127) / 128;
+  const long grid = tiles < 2L * sms ? tiles : 2L * sms;
+  k_ws_mlp_tc<<<(unsigned)grid, 128, SM_TOTAL, st>>>(wpack, params, X, rows, out, err);
+  return cudaGetLastError();
+}
+
+// one training step's kernels (gradient only; the trainer adds Adam)
+cudaError_t launch_ws_grad(const float* params, const float* X, const float* t,
+                           const long long* idx, int B, WsTrainBuffers& tb, cudaStream_t st) {
+  const long HH = (long)H * H;
+  const long oW0 = 0, ob0 = H * K, oW1 = ob0 + H, ob1 = oW1 + HH, oW2 = ob1 + H, ob2 = oW2 + HH,
+             ow3 = ob2 + H, ob3 = ow3 + H;
+  k_gather_rows<<<(B * 4 + 255) / 256, 256, 0, st>>>(X, t, idx, B, tb.Xb, tb.tb);
+  const dim3 gf(H / 64, (B + 63) / 64, 1);
+  // forward
+  k_gemm<false, true, 1><<<gf, 256, 0, st>>>(B, H, K, tb.Xb, K, params + oW0, K, tb.Z0, H,
+                                             params + ob0, tb.A0, nullptr, K);
+  k_gemm<false, true, 1><<<gf, 256, 0, st>>>(B, H, H, tb.A0, H, params + oW1, H, tb.Z1, H,
+                                             params + ob1, tb.A1, nullptr, H);
+  k_gemm<false, true, 1><<<gf, 256, 0, st>>>(B, H, H, tb.A1, H, params + oW2, H, tb.Z2, H,
+                                             params + ob2, tb.A2, nullptr, H);
+  const int nout = (B + 7) / 8;
+  k_ws_out<<<nout, 256, 0, st>>>(tb.A2, tb.Z2, params, tb.tb, B, tb.dy, tb.dZ2, tb.loss_part);
+  k_sum_f64<<<1, 32, 0, st>>>(tb.loss_part, nout, 1.0 / (double)B, tb.loss);
+  // backward: weight gradients over row chunks, data gradients through the layers
+  const int chunk = WS_ROW_CHUNK, S = (B + chunk - 1) / chunk;
+  float* g = tb.grad;
+  auto wgrad = [&](const float* dZ, const float* Ain, int kin, long ow, long ob) {
+    const dim3 gw((kin + 63) / 64, H / 64, S);
+    k_gemm<true, false, 0><<<gw, 256, 0, st>>>(H, kin, B, dZ, H, Ain, kin, tb.part, kin,
+                                               nullptr, nullptr, nullptr, chunk);
+    k_sum_partials<<<nblk((long)H * kin), 256, 0, st>>>(tb.part, S, (long)H * kin, g + ow);
+    k_colsum<<<dim3((H + 127) / 128, S), 128, 0, st>>>(dZ, B, H, chunk, tb.part);
+    k_sum_partials<<<1, 128, 0, st>>>(tb.part, S, H, g + ob);
+  };
+  // w3, b3: column sums of A2 dy and of dy
+  {
+    const dim3 gw(1, H / 64, S);
+    k_gemm<true, false, 0><<<gw, 256, 0, st>>>(H, 1, B, tb.A2, H, tb.dy, 1, tb.part, 1, nullptr,
+                                               nullptr, nullptr, chunk);
+    k_sum_partials<<<1, 128, 0, st>>>(tb.part, S, H, g + ow3);
+    k_colsum<<<dim3(1, S), 128, 0, st>>>(tb.dy, B, 1, chunk, tb.part);
+    k_sum_partials<<<1, 32, 0, st>>>(tb.part, S, 1, g + ob3);
+  }
+  wgrad(tb.dZ2, tb.A1, H, oW2, ob2);
+  k_gemm<false, false, 2><<<gf, 256, 0, st>>>(B, H, H, tb.dZ2, H, params + oW2, H, tb.dZ1, H,
+                                              nullptr, nullptr, tb.Z1, H);
+  wgrad(tb.dZ1, tb.A0, H, oW1, ob1);
+  k_gemm<false, false, 2><<<gf, 256, 0, st>>>(B, H, H, tb.dZ1, H, params + oW1, H, tb.dZ2, H,
+                                              nullptr, nullptr, tb.Z0, H);
+  wgrad(tb.dZ2, tb.Xb, K, oW0, ob0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_adam(float* p, float* m, float* v, const float* g, long n, float lr,
+                           int t, cudaStream_t st) {
+  const double b1 = 0.9, b2 = 0.999;
+  const float c1 = (float)(1.0 - pow(b1, t)), c2 = (float)(1.0 - pow(b2, t));
+  k_adam<<<nblk(n), 256, 0, st>>>(p, m, v, g, n, lr, (float)b1, (float)b2, c1, c2, 1e-8f);
+  return cudaGetLastError();
+}
+
+}  // namespace otgb

@@ -21,10 +21,10 @@ import oracle as O  # noqa: E402
 import ot_inputs as I  # noqa: E402
 
 CASES = {
-    "blob256": dict(kind="blob_pair", N=256, M=256, seed=1000, tau=2.0, tol=1e-10, eta=1e-1),
-    "noise1024": dict(kind="noise_blob_pair", N=1024, M=1024, seed=3000, tau=2.0, tol=1e-8,
+    "blob256": dict(kind="blob_pair", N=256, M=256, seed=1000, tau=4.0, tol=1e-10, eta=1e-1),
+    "noise1024": dict(kind="noise_blob_pair", N=1024, M=1024, seed=3000, tau=1.0, tol=1e-8,
                       eta=1e-1),
-    "noise2048": dict(kind="noise_blob_pair", N=2048, M=2048, seed=3000, tau=2.0, tol=1e-8,
+    "noise2048": dict(kind="noise_blob_pair", N=2048, M=2048, seed=3000, tau=1.0, tol=1e-8,
                       eta=1e-1),
 }
 

@@ -32,6 +32,20 @@ def test_fd_poisson_inverts_the_stencil_laplacian(N, M):
     assert np.abs(O.fd_poisson(np.full((N, M), 3.0))).max() < 1e-15
 
 
+def test_fd_poisson_lowpass_on_single_modes():
+    # a Fourier mode is an eigenfunction of both the stencil Laplacian and the filter
+    N, M = 32, 48
+    x, y = I.grid(N, M)
+    for k1, k2 in ((1, 0), (3, -2), (12, 8), (24, 16), (0, 16)):
+        mode = np.cos(2 * np.pi * (k1 * x + k2 * y))
+        u = O.fd_poisson(mode, lowpass=True)
+        d = O.derivatives(u)
+        w = np.exp(-0.5 * ((k1 / (M / 4)) ** 2 + (k2 / (N / 4)) ** 2))
+        assert np.abs(d[2] + d[3] - w * mode).max() < 1e-11
+    src = RNG.standard_normal((N, M))
+    assert np.abs(O.fd_poisson(src, lowpass=True)).max() < np.abs(O.fd_poisson(src)).max()
+
+
 def test_features_with_uniform_target():
     # g = 1: G(T) = 1 (the B-spline reproduces constants), so log G, grad G vanish; the
     # Laplacian feature equals the Poisson source up to its mean
@@ -78,7 +92,7 @@ def test_features_with_equal_densities():
 
 
 def test_exact_source_recovers_the_potential():
-    # with the network replaced by the exact correction s*, step 4 returns phi* itself
+    # with the exact correction s* (and no low-pass) h + P(s*) is phi* itself
     N, M = 48, 32
     f, g = W.normalise(*I.blob_pair(N, M, s=7))
     h, src = W.linear_potential(f, g)
@@ -86,6 +100,7 @@ def test_exact_source_recovers_the_potential():
     s = W.target(phi, h).reshape(N, M)
     u = O.fd_poisson(src + s)
     assert np.abs(u - (phi - phi.mean())).max() < 1e-12
+    assert np.abs(h + O.fd_poisson(s) - (phi - phi.mean())).max() < 1e-12
 
 
 def test_silu_and_its_derivative():
