@@ -24,33 +24,41 @@ namespace {
 constexpr int K = OTGB_WS_K, H = OTGB_WS_H;
 constexpr float kFloor = 1e-3f;
 
-__device__ __forceinline__ long wrapi(long a, long L) {
-  const long r = a % L;
+// index a mod L for any int a (the displaced-point gather can leave the grid by many cells)
+__device__ __forceinline__ int wrapi(int a, int L) {
+  const int r = a % L;
   return r < 0 ? r + L : r;
 }
+// index i + d mod L for 0 <= i < L and |d| < L (stencil neighbours): no division
+__device__ __forceinline__ int wrap_near(int a, int L) {
+  return a < 0 ? a + L : (a >= L ? a - L : a);
+}
 
-// 4th-order centred stencils of a periodic FP64 field (spacing 1/M along j, 1/N along i)
+// 4th-order centred stencils of a periodic FP64 field (spacing 1/M along j, 1/N along i),
+// at grid points 0 <= i < N, 0 <= j < M
 struct Stencil {
   const double* u;
   int N, M;
-  __device__ double at(long i, long j) const { return u[wrapi(i, N) * M + wrapi(j, M)]; }
-  __device__ double dx(long i, long j) const {
+  __device__ double at(int i, int j) const {
+    return u[(size_t)wrap_near(i, N) * M + wrap_near(j, M)];
+  }
+  __device__ double dx(int i, int j) const {
     return (-at(i, j + 2) + 8.0 * at(i, j + 1) - 8.0 * at(i, j - 1) + at(i, j - 2)) *
            (double)M / 12.0;
   }
-  __device__ double dy(long i, long j) const {
+  __device__ double dy(int i, int j) const {
     return (-at(i + 2, j) + 8.0 * at(i + 1, j) - 8.0 * at(i - 1, j) + at(i - 2, j)) *
            (double)N / 12.0;
   }
-  __device__ double dxx(long i, long j) const {
+  __device__ double dxx(int i, int j) const {
     return (-at(i, j + 2) + 16.0 * at(i, j + 1) - 30.0 * at(i, j) + 16.0 * at(i, j - 1) -
             at(i, j - 2)) * (double)M * (double)M / 12.0;
   }
-  __device__ double dyy(long i, long j) const {
+  __device__ double dyy(int i, int j) const {
     return (-at(i + 2, j) + 16.0 * at(i + 1, j) - 30.0 * at(i, j) + 16.0 * at(i - 1, j) -
             at(i - 2, j)) * (double)N * (double)N / 12.0;
   }
-  __device__ double dxy(long i, long j) const {
+  __device__ double dxy(int i, int j) const {
     return (-dy(i, j + 2) + 8.0 * dy(i, j + 1) - 8.0 * dy(i, j - 1) + dy(i, j - 2)) *
            (double)M / 12.0;
   }
@@ -78,15 +86,15 @@ __device__ void interp(const double* c, int N, int M, double xp, double yp, doub
   double wx[4], dwx[4], wy[4], dwy[4];
   cubic_bspline(xp - fx, wx, dwx);
   cubic_bspline(yp - fy, wy, dwy);
-  const long j0 = (long)fx - 1, i0 = (long)fy - 1;
+  const int j0 = wrapi((int)fx - 1, M), i0 = wrapi((int)fy - 1, N);
   double v = 0.0, gx = 0.0, gy = 0.0;
 #pragma unroll
   for (int b = 0; b < 4; ++b) {
-    const double* row = c + wrapi(i0 + b, N) * M;
+    const double* row = c + (size_t)wrap_near(i0 + b, N) * M;
     double rv = 0.0, rd = 0.0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const double cv = row[wrapi(j0 + a, M)];
+      const double cv = row[wrap_near(j0 + a, M)];
       rv += cv * wx[a];
       rd += cv * dwx[a];
     }
@@ -106,7 +114,8 @@ __global__ void k_ws_source(const double* __restrict__ f, const double* __restri
     src[p] = log(f[p]) - log(g[p]);
 }
 
-// features at the potential h (FP64 arithmetic, stored as FP32):
+// features at the potential h (FP64 stencils and interpolation, FP32 logarithms, stored as
+// FP32):
 //  [log f, log g, lg, r = log f - lg - ld, hxx + hyy, hxx - hyy, 2 hxy, hxx hyy - hxy^2,
 //   10 hx, 10 hy, 0.1 Gx / Gc, 0.1 Gy / Gc, (Gx hx + Gy hy) / Gc, (hxx - hyy)^2 + 4 hxy^2,
 //   r (hxx + hyy), 0],   Gc = max(G, floor), lg = log Gc, ld = log max(det, floor),
@@ -114,8 +123,8 @@ __global__ void k_ws_source(const double* __restrict__ f, const double* __restri
 __global__ void k_ws_features(const double* __restrict__ f, const double* __restrict__ g,
                               const double* __restrict__ c, const double* __restrict__ h,
                               int N, int M, float* __restrict__ X) {
-  const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const long i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
   if (j >= M) return;
   const Stencil S{h, N, M};
   const double hx = S.dx(i, j), hy = S.dy(i, j), hxx = S.dxx(i, j), hyy = S.dyy(i, j);
@@ -124,14 +133,16 @@ __global__ void k_ws_features(const double* __restrict__ f, const double* __rest
   interp(c, N, M, (double)j + (double)M * hx, (double)i + (double)N * hy, &G, &Gx, &Gy);
   const double det = (1.0 + hxx) * (1.0 + hyy) - hxy * hxy;
   const double Gc = fmax(G, (double)kFloor);
-  const long p = i * M + j;
-  const double lf = log(f[p]), lg = log(Gc), ld = log(fmax(det, (double)kFloor));
-  const double r = lf - lg - ld;
+  const size_t p = (size_t)i * M + j;
+  // the logarithms only feed the FP32 features: FP32 logf
+  const float lf = logf((float)f[p]), lg = logf((float)Gc);
+  const float ld = logf((float)fmax(det, (double)kFloor));
+  const float r = lf - lg - ld;
   float x[16];
-  x[0] = (float)lf;
-  x[1] = (float)log(g[p]);
-  x[2] = (float)lg;
-  x[3] = (float)r;
+  x[0] = lf;
+  x[1] = logf((float)g[p]);
+  x[2] = lg;
+  x[3] = r;
   x[4] = (float)(hxx + hyy);
   x[5] = (float)(hxx - hyy);
   x[6] = (float)(2.0 * hxy);
@@ -142,7 +153,7 @@ __global__ void k_ws_features(const double* __restrict__ f, const double* __rest
   x[11] = (float)(0.1 * Gy / Gc);
   x[12] = (float)((Gx * hx + Gy * hy) / Gc);
   x[13] = (float)((hxx - hyy) * (hxx - hyy) + 4.0 * hxy * hxy);
-  x[14] = (float)(r * (hxx + hyy));
+  x[14] = r * (float)(hxx + hyy);
   x[15] = 0.f;
   float4* o = reinterpret_cast<float4*>(X + p * 16);
 #pragma unroll
@@ -153,10 +164,10 @@ __global__ void k_ws_features(const double* __restrict__ f, const double* __rest
 __global__ void k_ws_target(const double* __restrict__ phi, const double* __restrict__ h,
                             int N, int M, double* __restrict__ diff, float* __restrict__ t,
                             int stage) {
-  const long j = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const long i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
   if (j >= M) return;
-  const long p = i * M + j;
+  const size_t p = (size_t)i * M + j;
   if (stage == 0) {
     diff[p] = phi[p] - h[p];
   } else {
@@ -191,7 +202,7 @@ __global__ void k_ws_admissible(const double* __restrict__ u, int N, int M,
   const Stencil S{u, N, M};
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
-    const long i = p / M, j = p - i * M;
+    const int i = (int)(p / M), j = (int)(p - (long)i * M);
     const double uxx = S.dxx(i, j), uyy = S.dyy(i, j), uxy = S.dxy(i, j);
     double a = 1.0;
 #pragma unroll

@@ -3,8 +3,9 @@ the gain of a trained network over the zero start.
 
 Tolerances:
   - FD Poisson solve (FP64 FFTs): 1e-12 of the result's scale.
-  - Features (FP64 arithmetic stored as FP32): 1e-5 of each feature's scale (FP32 storage
-    rounding 6e-8 plus FP64 stencil round-off amplified by M^2).
+  - Features (FP64 stencils and interpolation, FP32 logarithms, stored as FP32): 1e-5 of
+    each feature's scale (FP32 logf and storage rounding, a few 1e-7 relative, plus FP64
+    stencil round-off amplified by M^2).
   - Network on the tensor cores vs the oracle with the same BF16 roundings: FP32 instead of
     FP64 accumulation and __expf differ by ~1e-6 relative; where that moves a value across a
     BF16 rounding boundary the activation changes by one BF16 ulp (2^-8 relative), so single
