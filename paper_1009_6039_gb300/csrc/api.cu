@@ -38,7 +38,9 @@ struct ot_plan {
   // FP64 spectrum used by the prefilter when the inner precision is FP32
   void *spec64 = nullptr, *q64 = nullptr;
   void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
-  float* c32 = nullptr;  // FP32 copy of the B-spline coefficients (mixed mode)
+  // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
+  // residual; hi is also the FP32 copy used for the interpolant's gradient)
+  float2 *fdd = nullptr, *cdd = nullptr;
   SpecTables tb64{}, tb32{};
   double* partials = nullptr;
   double* dmean = nullptr;
@@ -83,9 +85,17 @@ template <typename T> static const SpecTables& tables(ot_plan* p);
 template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
 template <> const SpecTables& tables<float>(ot_plan* p) { return p->tb32; }
 
-template <typename T> static const float* c32_for(const ot_plan* p) {
-  return sizeof(T) == 4 ? p->c32 : nullptr;
-}
+// residual + coefficients of the iterate: FP64 kernel, or the double-float kernel in mixed
+// mode (which reads the split copies of the plan's f and c)
+template <typename T>
+static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
+                                   const double* ua, double* Fraw, const double* ub = nullptr,
+                                   int sel = 0) {
+  if (sizeof(T) == 4)
+    return launch_residual_dd(p->fdd, p->cdd, ua, p->N, p->M, Fraw, (float*)p->coef,
+                              p->partials, p->sc, p->stream, ub, sel);
+  return launch_residual<double>(f, c, ua, p->N, p->M, Fraw, (double*)p->coef, p->partials,
+                                 p->sc, p->stream, ub, sel);}
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
 
@@ -205,7 +215,7 @@ static void free_buffers(ot_plan* p) {
   free_graph(p);
   if (p->uout) cudaFree(p->uout);
   p->uout = nullptr;
-  void* ptrs[] = {p->c32, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
+  void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
                   p->tw32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
                   p->ws_X, p->ws_s};
@@ -219,7 +229,7 @@ static void free_buffers(ot_plan* p) {
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
   p->spec64 = p->q64 = p->tw64 = p->tw32 = nullptr;
-  p->c32 = nullptr;
+  p->fdd = p->cdd = nullptr;
   p->partials = p->dmean = nullptr;
   p->sc = nullptr;
   p->hsc = nullptr;
@@ -259,7 +269,8 @@ static int alloc_buffers(ot_plan* p) {
   if (p->precision) {
     CK(cudaMalloc(&p->spec64, P * 8));
     CK(cudaMalloc(&p->q64, P * 8));
-    CK(cudaMalloc(&p->c32, P * 4));
+    CK(cudaMalloc(&p->fdd, P * 8));
+    CK(cudaMalloc(&p->cdd, P * 8));
   } else {
     p->spec64 = nullptr;
     p->q64 = nullptr;
@@ -455,7 +466,7 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
   auto one = [&]() -> cudaError_t {
     switch (cls) {
       case OT_PROF_RESIDUAL:
-        return launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p));
+        return residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, nullptr, 0);
       case OT_PROF_ROW_R2C:
         return launch_row_r2c<T>((const T*)p->V, P, nullptr, nullptr, (C2<T>*)p->spec, N, M,
                                  tb, nullptr, p->stream);
@@ -559,9 +570,10 @@ static int run_prefilter(ot_plan* p, const double* g, double* c) {
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
          launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
                                 nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream));
-  if (p->precision)
-    LAUNCH(p, OT_PROF_OTHER, -1, 1,
-           launch_convert<float>(c, 1, p->c32, 0, (long)p->N * p->M, p->stream));
+  if (p->precision) {
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(c, p->cdd, (long)p->N * p->M, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(p->f, p->fdd, (long)p->N * p->M, p->stream));
+  }
   return OT_OK;
 }
 
@@ -811,7 +823,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
   }
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
+         residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, nullptr, 0));
   RET(read_scalars(p));
   int status = OT_OK;
   double s = 1.0;
@@ -837,7 +849,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     for (;;) {
       RET(run_theta<T>(p, p->u, p->ucand, s, false));
       LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-             launch_residual<T>(p->f, p->c, p->ucand, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
+             residual_launch<T>(p, p->f, p->c, p->ucand, p->Fraw, nullptr, 0));
       RET(read_scalars(p));
       if (!p->safeguard || p->hsc->admissible || s < 0x1p-30) {
         accepted = true;
@@ -930,7 +942,7 @@ static int capture_candidate(ot_plan* p) {
   const int N = p->N, M = p->M;
   RET(run_theta<T>(p, p->u, p->ucand, 1.0, true));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 1, c32_for<T>(p)));
+         residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, p->ucand, 1));
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
          launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
   return OT_OK;
@@ -951,7 +963,7 @@ static int capture_solve(ot_plan* p) {
   RET(run_prefilter(p, p->g, p->c));
   if (p->warm_start == 2) RET(run_warmstart(p, p->u));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(p->f, p->c, p->u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, p->ucand, 0, c32_for<T>(p)));
+         residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, p->ucand, 0));
   const int top = (int)(p->launches - k0) + 1;
   LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, top));
   cudaGraph_t b1, b2, b3, b4, b5;
@@ -1373,10 +1385,12 @@ static int eval_residual_impl(ot_plan* p, const double* f, const double* c, cons
   const long P = (long)N * M;
   set_solver_scalars(p);
   CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
-  if (sizeof(T) == 4)
-    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_convert<float>(c, 1, p->c32, 0, P, p->stream));
+  if (sizeof(T) == 4) {
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(c, p->cdd, P, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(f, p->fdd, P, p->stream));
+  }
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
-         launch_residual<T>(f, c, u, N, M, p->Fraw, (T*)p->coef, p->partials, p->sc, p->stream, nullptr, 0, c32_for<T>(p)));
+         residual_launch<T>(p, f, c, u, p->Fraw, nullptr, 0));
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
          launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
   if (F) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_shifted_residual(p->Fraw, F, N, M, p->sc, p->stream));

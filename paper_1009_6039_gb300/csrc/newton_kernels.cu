@@ -6,6 +6,7 @@
 // order is fixed, so results are bit-reproducible from run to run.
 #include <math.h>
 
+#include "dd.cuh"
 #include "otgb_internal.cuh"
 
 namespace otgb {
@@ -422,6 +423,260 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     sc->admissible = (v[9] == 0.0 && isfinite(sc->res_inf) && v[8] > 0.0) ? 1 : 0;
     sc->ticket[TK_RESID] = 0;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Mixed-mode residual: the same evaluation with every FP64-accuracy quantity (the stencils
+// of u, the displaced point, the B-spline value gather, det, f_n and F) in double-float
+// arithmetic on the FP32 pipes (dd.cuh, unit round-off 2^-48), the Jacobian coefficients,
+// the interpolant's gradient and the Simpson sums in FP32.  Inputs: u (FP64), f and c
+// pre-split into (hi, lo) float pairs; output F_raw in FP64.
+// ---------------------------------------------------------------------------------------
+struct ResidConstsDD {
+  dd Mh, Nh, Mh2, Nh2, MNh;  // M/12, N/12, M^2/12, N^2/12, MN/144
+  dd inv36;                  // 1/36 (the value weights are computed x6 per axis)
+  float M, N;
+  float w3M, w3N;            // 1/(3M), 1/(3N)
+};
+
+__device__ __forceinline__ dd ldd(const float2* __restrict__ a, size_t i) {
+  const float2 v = __ldg(a + i);
+  return dd{v.x, v.y};
+}
+
+// 6 x the cubic B-spline value weights at t in [0, 1) (taps -1, 0, 1, 2): s^3,
+// 3 t^3 - 6 t^2 + 4, 6 - (the other three), t^3, with s = 1 - t; all coefficients exact
+__device__ __forceinline__ void bspline6_dd(dd t, dd w[4]) {
+  const dd s = dd_add_f(dd_neg(t), 1.0f);
+  const dd t2 = dd_mul(t, t), t3 = dd_mul(t2, t);
+  w[0] = dd_mul(dd_mul(s, s), s);
+  w[1] = dd_add_f(dd_sub(dd_mul_f(t3, 3.0f), dd_mul_f(t2, 6.0f)), 4.0f);
+  w[3] = t3;
+  w[2] = dd_add_f(dd_neg(dd_add(dd_add(w[0], w[1]), w[3])), 6.0f);
+}
+
+// floor of a dd position p (|p| < 2^23): integer part k and fraction t in [0, 1) as dd.
+// p.hi - floor(p.hi) is not exact for -1 < p.hi < 0 (the result needs more bits than
+// p.hi), so the subtraction is an error-free dd add.
+__device__ __forceinline__ int dd_floor(dd p, dd* t) {
+  float fl = floorf(p.hi);
+  dd fr = dd_add_f(p, -fl);
+  if (fr.hi < 0.0f) {
+    fl -= 1.0f;
+    fr = dd_add_f(fr, 1.0f);
+  } else if (fr.hi >= 1.0f) {
+    fl += 1.0f;
+    fr = dd_add_f(fr, -1.0f);
+  }
+  *t = fr;
+  return (int)fl;
+}
+
+__global__ void __launch_bounds__(RTX * RTY / RPT)
+    k_residual_dd(const float2* __restrict__ fdd, const float2* __restrict__ cdd,
+                  const double* __restrict__ ua, const double* __restrict__ ub, int sel, int N,
+                  int M, ResidConstsDD K, double* __restrict__ Fraw, float* __restrict__ coef,
+                  double* partials, DevScalars* sc) {
+  __shared__ dd tile[RTY + 4][RTX + 4];
+  __shared__ dd dyt[RTY][RTX + 4];  // unscaled y-difference of u (halo 2 in x)
+  const double* __restrict__ u = (ub && ((sc->upar ^ sel) & 1)) ? ub : ua;
+  const int bx = blockIdx.x * RTX, by = blockIdx.y * RTY;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < (RTY + 4) * (RTX + 4); idx += blockDim.x) {
+    const int r = idx / (RTX + 4), cc = idx - r * (RTX + 4);
+    int gi = by + r - 2, gj = bx + cc - 2;
+    while (gi < 0) gi += N;
+    while (gi >= N) gi -= N;
+    while (gj < 0) gj += M;
+    while (gj >= M) gj -= M;
+    tile[r][cc] = dd_from_double(u[(size_t)gi * M + gj]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < RTY * (RTX + 4); idx += blockDim.x) {
+    const int r = idx / (RTX + 4), cc = idx - r * (RTX + 4);
+    // (u[+2] - u[-2]) is subtracted from 8 (u[+1] - u[-1]), all in y
+    dyt[r][cc] = dd_sub(dd_scale2(dd_sub(tile[r + 3][cc], tile[r + 1][cc]), 8.0f),
+                        dd_sub(tile[r + 4][cc], tile[r][cc]));
+  }
+  __syncthreads();
+  // partials: sum fn (dd), max Fraw, min Fraw (dd), min det (dd), non-finite count
+  dd sum_fn = dd{0.f, 0.f}, fmax_ = dd{-INFINITY, 0.f}, fmin_ = dd{INFINITY, 0.f},
+     dmin = dd{INFINITY, 0.f};
+  float nonfinite = 0.f;
+  float simp[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  const int tx = tid % RTX, ty0 = tid / RTX;
+  const int j = bx + tx;
+  const size_t P = (size_t)N * M;
+  const float wx = ((j & 1) ? 4.0f : 2.0f) * K.w3M;
+#pragma unroll 1
+  for (int rr = 0; rr < RPT; ++rr) {
+    const int ty = ty0 + rr * (RTY / RPT);
+    const int i = by + ty;
+    if (i >= N || j >= M) continue;
+    const int r = ty + 2, q = tx + 2;
+    const dd c0 = tile[r][q];
+    const dd xp1 = tile[r][q + 1], xm1 = tile[r][q - 1], xp2 = tile[r][q + 2],
+             xm2 = tile[r][q - 2];
+    const dd ux =
+        dd_mul(dd_sub(dd_scale2(dd_sub(xp1, xm1), 8.0f), dd_sub(xp2, xm2)), K.Mh);
+    const dd uy = dd_mul(dyt[ty][q], K.Nh);
+    // 16 (u[+1] + u[-1]) - (u[+2] + u[-2]) - 30 u
+    const dd uxx = dd_mul(dd_sub(dd_sub(dd_scale2(dd_add(xp1, xm1), 16.0f), dd_add(xp2, xm2)),
+                                 dd_mul_f(c0, 30.0f)),
+                          K.Mh2);
+    const dd yp1 = tile[r + 1][q], ym1 = tile[r - 1][q], yp2 = tile[r + 2][q],
+             ym2 = tile[r - 2][q];
+    const dd uyy = dd_mul(dd_sub(dd_sub(dd_scale2(dd_add(yp1, ym1), 16.0f), dd_add(yp2, ym2)),
+                                 dd_mul_f(c0, 30.0f)),
+                          K.Nh2);
+    const dd uxy = dd_mul(dd_sub(dd_scale2(dd_sub(dyt[ty][q + 1], dyt[ty][q - 1]), 8.0f),
+                                 dd_sub(dyt[ty][q + 2], dyt[ty][q - 2])),
+                          K.MNh);
+    // displaced point in grid units and the periodic cubic B-spline value there
+    dd tx_, ty_;
+    const int fj = dd_floor(dd_add_f(dd_mul_f(ux, K.M), (float)j), &tx_);
+    const int fi = dd_floor(dd_add_f(dd_mul_f(uy, K.N), (float)i), &ty_);
+    const int j0 = wrapi(fj, M), i0 = wrapi(fi, N);
+    int jj[4], ii[4];
+    jj[0] = j0 == 0 ? M - 1 : j0 - 1;
+    jj[1] = j0;
+    jj[2] = wrap_near(j0 + 1, M);
+    jj[3] = wrap_near(j0 + 2, M);
+    ii[0] = i0 == 0 ? N - 1 : i0 - 1;
+    ii[1] = i0;
+    ii[2] = wrap_near(i0 + 1, N);
+    ii[3] = wrap_near(i0 + 2, N);
+    dd wxv[4], wyv[4];
+    bspline6_dd(tx_, wxv);
+    bspline6_dd(ty_, wyv);
+    // gradient weights in FP32 (Jacobian only)
+    float wxf[4], dwx[4], wyf[4], dwy[4];
+    bspline_w<float>(tx_.hi, wxf, dwx);
+    bspline_w<float>(ty_.hi, wyf, dwy);
+    dd G36 = dd{0.f, 0.f};
+    float gx = 0.f, gy = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const size_t row = (size_t)ii[b] * M;
+      dd sv = dd{0.f, 0.f};
+      float svf = 0.f, sdf = 0.f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const dd cv = ldd(cdd, row + jj[a]);
+        sv = dd_fma(cv, wxv[a], sv);
+        svf = fmaf(cv.hi, wxf[a], svf);
+        sdf = fmaf(cv.hi, dwx[a], sdf);
+      }
+      G36 = dd_fma(sv, wyv[b], G36);
+      gx = fmaf(sdf, wyf[b], gx);
+      gy = fmaf(svf, dwy[b], gy);
+    }
+    const dd G = dd_mul(G36, K.inv36);
+    const float Gx = gx * K.M, Gy = gy * K.N;
+    const dd det = dd_sub(dd_mul(dd_add_f(uxx, 1.0f), dd_add_f(uyy, 1.0f)), dd_mul(uxy, uxy));
+    const dd fn = dd_mul(G, det);
+    const size_t p = (size_t)i * M + j;
+    const dd fr = dd_sub(ldd(fdd, p), fn);
+    Fraw[p] = dd_to_double(fr);
+    // coefficients of the linearisation (Jacobian only), FP32
+    const float Gt = G.hi, dett = det.hi;
+    const float a11 = Gt * (1.0f + uyy.hi), a12 = -Gt * uxy.hi, a22 = Gt * (1.0f + uxx.hi);
+    const float b1 = dett * Gx, b2 = dett * Gy;
+    coef[p] = a11;
+    coef[P + p] = a12;
+    coef[2 * P + p] = a22;
+    coef[3 * P + p] = b1;
+    coef[4 * P + p] = b2;
+    const float w = ((i & 1) ? 4.0f : 2.0f) * K.w3N * wx;
+    simp[0] += w * a11;
+    simp[1] += w * a12;
+    simp[2] += w * a22;
+    simp[3] += w * b1;
+    simp[4] += w * b2;
+    if (isfinite(fn.hi) && isfinite(fn.lo)) {
+      sum_fn = dd_add(sum_fn, fn);
+      if (dd_gt(fr, fmax_)) fmax_ = fr;
+      if (dd_gt(fmin_, fr)) fmin_ = fr;
+    } else {
+      nonfinite += 1.0f;
+    }
+    if (dd_gt(dmin, det)) dmin = det;
+  }
+  double v64[5] = {dd_to_double(sum_fn), (double)fmax_.hi + (double)fmax_.lo,
+                   (double)fmin_.hi + (double)fmin_.lo, (double)dmin.hi + (double)dmin.lo,
+                   (double)nonfinite};
+  const int kind64[5] = {0, 1, 2, 2, 0};
+  double v[10];
+  const int kind[10] = {0, 0, 0, 0, 0, 0, 1, 2, 2, 0};
+  block_reduce<5>(v64, kind64);
+  block_sum_f<5>(simp);
+#pragma unroll
+  for (int a = 0; a < 5; ++a) v[1 + a] = (double)simp[a];
+  v[0] = v64[0];
+  v[6] = v64[1];
+  v[7] = v64[2];
+  v[8] = v64[3];
+  v[9] = v64[4];
+  if (!publish_partials<10>(v, partials, &sc->ticket[TK_RESID])) return;
+  const unsigned int nb = gridDim.x * gridDim.y;
+  reduce_partials<10>(v, kind, partials, nb);
+  if (threadIdx.x == 0) {
+    const double Pd = (double)N * (double)M;
+    const double mean_fn = v[0] / Pd;
+    const double shift = mean_fn - 1.0;
+    sc->mean_fn = mean_fn;
+    sc->shift = shift;
+    sc->res_inf = fmax(fabs(v[6] + shift), fabs(v[7] + shift));
+    for (int a = 0; a < 5; ++a) sc->abar[a] = v[1 + a];
+    sc->min_det = v[8];
+    sc->k1_nonfinite = (int)v[9];
+    sc->admissible = (v[9] == 0.0 && isfinite(sc->res_inf) && v[8] > 0.0) ? 1 : 0;
+    sc->ticket[TK_RESID] = 0;
+  }
+}
+
+// split FP64 values into (hi, lo) float pairs
+__global__ void k_split_dd(const double* __restrict__ in, float2* __restrict__ out, long n) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+       k += (long)gridDim.x * blockDim.x) {
+    const dd v = dd_from_double(in[k]);
+    out[k] = make_float2(v.hi, v.lo);
+  }
+}
+
+cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st) {
+  long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  if (nb < 1) nb = 1;
+  k_split_dd<<<(int)nb, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+static dd host_dd(double v) {
+  dd r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
+cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
+                               int M, double* Fraw, float* coef, double* partials,
+                               DevScalars* sc, cudaStream_t st, const double* ub, int sel) {
+  dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
+  ResidConstsDD K;
+  K.Mh = host_dd((double)M / 12.0);
+  K.Nh = host_dd((double)N / 12.0);
+  K.Mh2 = host_dd((double)M * (double)M / 12.0);
+  K.Nh2 = host_dd((double)N * (double)N / 12.0);
+  K.MNh = host_dd((double)M * (double)N / 144.0);
+  K.inv36 = host_dd(1.0 / 36.0);
+  K.M = (float)M;
+  K.N = (float)N;
+  K.w3M = (float)(1.0 / (3.0 * (double)M));
+  K.w3N = (float)(1.0 / (3.0 * (double)N));
+  k_residual_dd<<<grid, RTX * RTY / RPT, 0, st>>>(fdd, cdd, ua, ub, sel, N, M, K, Fraw, coef,
+                                                  partials, sc);
+  return cudaGetLastError();
 }
 
 int residual_partial_blocks(int N, int M) {

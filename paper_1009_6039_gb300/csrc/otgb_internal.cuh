@@ -128,6 +128,13 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
                             cudaStream_t st, const double* ub = nullptr, int sel = 0,
                             const float* c32 = nullptr);
+// mixed mode: the residual in double-float arithmetic from (hi, lo) float pairs of f and c
+cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
+                               int M, double* Fraw, float* coef, double* partials,
+                               DevScalars* sc, cudaStream_t st, const double* ub = nullptr,
+                               int sel = 0);
+// out[k] = (hi, lo) float pair of in[k]
+cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st);
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
                                DevScalars* sc, cudaStream_t st);
 cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
