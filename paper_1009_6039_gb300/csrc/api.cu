@@ -78,6 +78,7 @@ struct ot_plan {
   unsigned char* ws_wpack = nullptr;  // BF16 weights in the tensor-core operand layout
   double *ws_src = nullptr, *ws_h = nullptr, *ws_tmp = nullptr;  // FP64 planes
   float *ws_X = nullptr, *ws_s = nullptr;  // features (P x 16), network output (P)
+  float* ws_c32 = nullptr;                 // FP32 B-spline coefficients for the features
   int ws_have = 0, gkey_ws = -1, sms = 0;
 };
 
@@ -218,11 +219,11 @@ static void free_buffers(ot_plan* p) {
   void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
                   p->tw32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
-                  p->ws_X, p->ws_s};
+                  p->ws_X, p->ws_s, p->ws_c32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->ws_src = p->ws_h = p->ws_tmp = nullptr;
-  p->ws_X = p->ws_s = nullptr;
+  p->ws_X = p->ws_s = p->ws_c32 = nullptr;
   if (p->hsc) cudaFreeHost(p->hsc);
   if (p->hinit) cudaFreeHost(p->hinit);
   p->hinit = nullptr;
@@ -734,6 +735,7 @@ static int alloc_ws(ot_plan* p) {
   CK(cudaMalloc(&p->ws_tmp, P * 8));
   CK(cudaMalloc(&p->ws_X, P * OTGB_WS_K * 4));
   CK(cudaMalloc(&p->ws_s, P * 4));
+  CK(cudaMalloc(&p->ws_c32, P * 4));
   return OT_OK;
 }
 
@@ -762,7 +764,9 @@ static int run_ws_features(ot_plan* p) {
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_source(p->f, p->g, p->ws_src, P, p->stream));
   RET(run_ws_poisson(p, p->ws_src, p->ws_h));
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
-         launch_ws_features(p->f, p->g, p->c, p->ws_h, p->N, p->M, p->ws_X, p->stream));
+         launch_convert<float>(p->c, 1, p->ws_c32, 0, P, p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_ws_features(p->f, p->g, p->ws_c32, p->ws_h, p->N, p->M, p->ws_X, p->stream));
   return OT_OK;
 }
 

@@ -472,7 +472,7 @@ __device__ __forceinline__ int dd_floor(dd p, dd* t) {
   return (int)fl;
 }
 
-__global__ void __launch_bounds__(RTX * RTY / RPT)
+__global__ void __launch_bounds__(RTX * RTY / RPT, 3)
     k_residual_dd(const float2* __restrict__ fdd, const float2* __restrict__ cdd,
                   const double* __restrict__ ua, const double* __restrict__ ub, int sel, int N,
                   int M, ResidConstsDD K, double* __restrict__ Fraw, float* __restrict__ coef,

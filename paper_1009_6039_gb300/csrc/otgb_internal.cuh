@@ -190,7 +190,8 @@ struct WsTrainBuffers {
 };
 cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
                              cudaStream_t st);
-cudaError_t launch_ws_features(const double* f, const double* g, const double* c,
+// c32: FP32 copy of the B-spline coefficients of g
+cudaError_t launch_ws_features(const double* f, const double* g, const float* c32,
                                const double* h, int N, int M, float* X, cudaStream_t st);
 // t = (D_xx + D_yy)(phi - h); scratch: N x M FP64
 cudaError_t launch_ws_target(const double* phi, const double* h, int N, int M, double* scratch,
@@ -199,9 +200,10 @@ cudaError_t launch_ws_target(const double* phi, const double* h, int N, int M, d
 cudaError_t launch_ws_widen(const float* s, double* out, long P, cudaStream_t st);
 // u = h + t
 cudaError_t launch_ws_sum(const double* h, const double* t, double* u, long P, cudaStream_t st);
-int ws_admissible_blocks();
+int ws_admissible_blocks(int N, int M);
 // alpha = largest of 1, 1/2, 1/4, 1/8 with det(I + alpha D^2 u) > 0 (0 if none or *err);
-// then u *= alpha.  partials: 4 x ws_admissible_blocks() doubles; *ticket must start at 0.
+// then u *= alpha.  partials: 4 x ws_admissible_blocks(N, M) doubles; *ticket must start
+// at 0.
 cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
                                  unsigned int* ticket, const int* err, double* alpha,
                                  cudaStream_t st);

@@ -15,6 +15,7 @@
 
 #include <cuda_bf16.h>
 
+#include "dd.cuh"
 #include "otgb_internal.cuh"
 
 namespace otgb {
@@ -64,100 +65,164 @@ struct Stencil {
   }
 };
 
-// Cubic B-spline basis weights (and their derivatives) at fractional offset t in [0, 1)
-// for the four taps at offsets -1, 0, 1, 2.
-__device__ __forceinline__ void cubic_bspline(double t, double w[4], double dw[4]) {
-  const double t2 = t * t, t3 = t2 * t, s = 1.0 - t;
-  w[0] = s * s * s / 6.0;
-  w[1] = (3.0 * t3 - 6.0 * t2 + 4.0) / 6.0;
-  w[2] = (-3.0 * t3 + 3.0 * t2 + 3.0 * t + 1.0) / 6.0;
-  w[3] = t3 / 6.0;
-  dw[0] = -s * s / 2.0;
-  dw[1] = (3.0 * t2 - 4.0 * t) / 2.0;
-  dw[2] = (-3.0 * t2 + 2.0 * t + 1.0) / 2.0;
-  dw[3] = t2 / 2.0;
-}
-
-// value and gradient (per unit length) of the interpolant with coefficients c at grid
-// position (xp along j, yp along i)
-__device__ void interp(const double* c, int N, int M, double xp, double yp, double* G,
-                       double* Gx, double* Gy) {
-  const double fx = floor(xp), fy = floor(yp);
-  double wx[4], dwx[4], wy[4], dwy[4];
-  cubic_bspline(xp - fx, wx, dwx);
-  cubic_bspline(yp - fy, wy, dwy);
-  const int j0 = wrapi((int)fx - 1, M), i0 = wrapi((int)fy - 1, N);
-  double v = 0.0, gx = 0.0, gy = 0.0;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const double* row = c + (size_t)wrap_near(i0 + b, N) * M;
-    double rv = 0.0, rd = 0.0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const double cv = row[wrap_near(j0 + a, M)];
-      rv += cv * wx[a];
-      rd += cv * dwx[a];
-    }
-    v += rv * wy[b];
-    gx += rd * wy[b];
-    gy += rv * dwy[b];
-  }
-  *G = v;
-  *Gx = gx * (double)M;
-  *Gy = gy * (double)N;
-}
-
+// log f - log g with FP32 logarithms (h only seeds the features and the warm start)
 __global__ void k_ws_source(const double* __restrict__ f, const double* __restrict__ g,
                             double* __restrict__ src, long P) {
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x)
-    src[p] = log(f[p]) - log(g[p]);
+    src[p] = (double)(logf((float)f[p]) - logf((float)g[p]));
 }
 
-// features at the potential h (FP64 stencils and interpolation, FP32 logarithms, stored as
-// FP32):
+// ---------------------------------------------------------------------------------------
+// Tiled stencils in double-float arithmetic: a block of 256 threads owns a 32 x 32 tile of
+// grid points (4 rows per thread) and stages the field with a halo of 2 (as dd) and its
+// unscaled y-differences in shared memory.
+// ---------------------------------------------------------------------------------------
+constexpr int TW = 32, TRPT = 4;
+struct TileDD {
+  dd t[TW + 4][TW + 4];
+  dd dy[TW][TW + 4];
+};
+struct StencilK {
+  dd Mh, Nh, Mh2, Nh2, MNh;  // M/12, N/12, M^2/12, N^2/12, MN/144
+};
+
+__device__ void tile_load_dd(TileDD& T, const double* __restrict__ u, int N, int M, int by,
+                             int bx) {
+  for (int idx = threadIdx.x; idx < (TW + 4) * (TW + 4); idx += blockDim.x) {
+    const int r = idx / (TW + 4), cc = idx - r * (TW + 4);
+    const int gi = wrap_near(by + r - 2, N), gj = wrap_near(bx + cc - 2, M);
+    T.t[r][cc] = dd_from_double(u[(size_t)gi * M + gj]);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < TW * (TW + 4); idx += blockDim.x) {
+    const int r = idx / (TW + 4), cc = idx - r * (TW + 4);
+    T.dy[r][cc] = dd_sub(dd_scale2(dd_sub(T.t[r + 3][cc], T.t[r + 1][cc]), 8.0f),
+                         dd_sub(T.t[r + 4][cc], T.t[r][cc]));
+  }
+  __syncthreads();
+}
+
+// 4th-order stencils at tile point (ty, tx)
+__device__ __forceinline__ void tile_stencils_dd(const TileDD& T, int ty, int tx,
+                                                 const StencilK& K, dd* ux, dd* uy, dd* uxx,
+                                                 dd* uyy, dd* uxy) {
+  const int r = ty + 2, q = tx + 2;
+  const dd c0 = T.t[r][q];
+  const dd xp1 = T.t[r][q + 1], xm1 = T.t[r][q - 1], xp2 = T.t[r][q + 2], xm2 = T.t[r][q - 2];
+  const dd yp1 = T.t[r + 1][q], ym1 = T.t[r - 1][q], yp2 = T.t[r + 2][q], ym2 = T.t[r - 2][q];
+  const dd c30 = dd_mul_f(c0, 30.0f);
+  *ux = dd_mul(dd_sub(dd_scale2(dd_sub(xp1, xm1), 8.0f), dd_sub(xp2, xm2)), K.Mh);
+  *uy = dd_mul(T.dy[ty][q], K.Nh);
+  *uxx = dd_mul(dd_sub(dd_sub(dd_scale2(dd_add(xp1, xm1), 16.0f), dd_add(xp2, xm2)), c30),
+                K.Mh2);
+  *uyy = dd_mul(dd_sub(dd_sub(dd_scale2(dd_add(yp1, ym1), 16.0f), dd_add(yp2, ym2)), c30),
+                K.Nh2);
+  *uxy = dd_mul(dd_sub(dd_scale2(dd_sub(T.dy[ty][q + 1], T.dy[ty][q - 1]), 8.0f),
+                       dd_sub(T.dy[ty][q + 2], T.dy[ty][q - 2])),
+                K.MNh);
+}
+
+// integer part and fraction (FP32) of the dd grid position p
+__device__ __forceinline__ int dd_floor_frac(dd p, float* t) {
+  float fl = floorf(p.hi);
+  dd fr = dd_add_f(p, -fl);
+  if (fr.hi < 0.0f) {
+    fl -= 1.0f;
+    fr = dd_add_f(fr, 1.0f);
+  } else if (fr.hi >= 1.0f) {
+    fl += 1.0f;
+    fr = dd_add_f(fr, -1.0f);
+  }
+  *t = fminf(fr.hi, 0.99999994f);
+  return (int)fl;
+}
+
+__device__ __forceinline__ void cubic_bspline_f(float t, float w[4], float dw[4]) {
+  const float t2 = t * t, t3 = t2 * t, s = 1.0f - t;
+  w[0] = s * s * s * (1.0f / 6.0f);
+  w[1] = (3.0f * t3 - 6.0f * t2 + 4.0f) * (1.0f / 6.0f);
+  w[2] = (-3.0f * t3 + 3.0f * t2 + 3.0f * t + 1.0f) * (1.0f / 6.0f);
+  w[3] = t3 * (1.0f / 6.0f);
+  dw[0] = -0.5f * s * s;
+  dw[1] = 0.5f * (3.0f * t2 - 4.0f * t);
+  dw[2] = 0.5f * (-3.0f * t2 + 2.0f * t + 1.0f);
+  dw[3] = 0.5f * t2;
+}
+
+// features at the potential h: stencils of h and the displaced point in double-float, the
+// interpolant of g (FP32 coefficients), its gradient and the logarithms in FP32:
 //  [log f, log g, lg, r = log f - lg - ld, hxx + hyy, hxx - hyy, 2 hxy, hxx hyy - hxy^2,
 //   10 hx, 10 hy, 0.1 Gx / Gc, 0.1 Gy / Gc, (Gx hx + Gy hy) / Gc, (hxx - hyy)^2 + 4 hxy^2,
 //   r (hxx + hyy), 0],   Gc = max(G, floor), lg = log Gc, ld = log max(det, floor),
 // G, Gx, Gy the interpolant of g at T = x + grad h, det = det(I + D^2 h).
-__global__ void k_ws_features(const double* __restrict__ f, const double* __restrict__ g,
-                              const double* __restrict__ c, const double* __restrict__ h,
-                              int N, int M, float* __restrict__ X) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= M) return;
-  const Stencil S{h, N, M};
-  const double hx = S.dx(i, j), hy = S.dy(i, j), hxx = S.dxx(i, j), hyy = S.dyy(i, j);
-  const double hxy = S.dxy(i, j);
-  double G, Gx, Gy;
-  interp(c, N, M, (double)j + (double)M * hx, (double)i + (double)N * hy, &G, &Gx, &Gy);
-  const double det = (1.0 + hxx) * (1.0 + hyy) - hxy * hxy;
-  const double Gc = fmax(G, (double)kFloor);
-  const size_t p = (size_t)i * M + j;
-  // the logarithms only feed the FP32 features: FP32 logf
-  const float lf = logf((float)f[p]), lg = logf((float)Gc);
-  const float ld = logf((float)fmax(det, (double)kFloor));
-  const float r = lf - lg - ld;
-  float x[16];
-  x[0] = lf;
-  x[1] = logf((float)g[p]);
-  x[2] = lg;
-  x[3] = r;
-  x[4] = (float)(hxx + hyy);
-  x[5] = (float)(hxx - hyy);
-  x[6] = (float)(2.0 * hxy);
-  x[7] = (float)(hxx * hyy - hxy * hxy);
-  x[8] = (float)(10.0 * hx);
-  x[9] = (float)(10.0 * hy);
-  x[10] = (float)(0.1 * Gx / Gc);
-  x[11] = (float)(0.1 * Gy / Gc);
-  x[12] = (float)((Gx * hx + Gy * hy) / Gc);
-  x[13] = (float)((hxx - hyy) * (hxx - hyy) + 4.0 * hxy * hxy);
-  x[14] = r * (float)(hxx + hyy);
-  x[15] = 0.f;
-  float4* o = reinterpret_cast<float4*>(X + p * 16);
+__global__ void __launch_bounds__(256)
+    k_ws_features(const double* __restrict__ f, const double* __restrict__ g,
+                  const float* __restrict__ c32, const double* __restrict__ h, int N, int M,
+                  StencilK K, float* __restrict__ X) {
+  __shared__ TileDD T;
+  const int bx = blockIdx.x * TW, by = blockIdx.y * TW;
+  tile_load_dd(T, h, N, M, by, bx);
+  const int tx = threadIdx.x % TW, ty0 = threadIdx.x / TW;
+  const int j = bx + tx;
+#pragma unroll 1
+  for (int rr = 0; rr < TRPT; ++rr) {
+    const int ty = ty0 + rr * (TW / TRPT);
+    const int i = by + ty;
+    if (i >= N || j >= M) continue;
+    dd ux, uy, uxx, uyy, uxy;
+    tile_stencils_dd(T, ty, tx, K, &ux, &uy, &uxx, &uyy, &uxy);
+    float txf, tyf;
+    const int fj = dd_floor_frac(dd_add_f(dd_mul_f(ux, (float)M), (float)j), &txf);
+    const int fi = dd_floor_frac(dd_add_f(dd_mul_f(uy, (float)N), (float)i), &tyf);
+    const int j0 = wrapi(fj, M), i0 = wrapi(fi, N);
+    float wx[4], dwx[4], wy[4], dwy[4];
+    cubic_bspline_f(txf, wx, dwx);
+    cubic_bspline_f(tyf, wy, dwy);
+    float G = 0.f, gx = 0.f, gy = 0.f;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    for (int b = 0; b < 4; ++b) {
+      const float* row = c32 + (size_t)wrap_near(i0 - 1 + b, N) * M;
+      float rv = 0.f, rd = 0.f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float cv = __ldg(row + wrap_near(j0 - 1 + a, M));
+        rv = fmaf(cv, wx[a], rv);
+        rd = fmaf(cv, dwx[a], rd);
+      }
+      G = fmaf(rv, wy[b], G);
+      gx = fmaf(rd, wy[b], gx);
+      gy = fmaf(rv, dwy[b], gy);
+    }
+    const float Gx = gx * (float)M, Gy = gy * (float)N;
+    const float hx = ux.hi, hy = uy.hi, hxx = uxx.hi, hyy = uyy.hi, hxy = uxy.hi;
+    const float det = (1.0f + hxx) * (1.0f + hyy) - hxy * hxy;
+    const float Gc = fmaxf(G, kFloor);
+    const size_t p = (size_t)i * M + j;
+    const float lf = logf((float)f[p]), lg = logf(Gc), ld = logf(fmaxf(det, kFloor));
+    const float r = lf - lg - ld;
+    float x[16];
+    x[0] = lf;
+    x[1] = logf((float)g[p]);
+    x[2] = lg;
+    x[3] = r;
+    x[4] = hxx + hyy;
+    x[5] = hxx - hyy;
+    x[6] = 2.0f * hxy;
+    x[7] = hxx * hyy - hxy * hxy;
+    x[8] = 10.0f * hx;
+    x[9] = 10.0f * hy;
+    x[10] = 0.1f * Gx / Gc;
+    x[11] = 0.1f * Gy / Gc;
+    x[12] = (Gx * hx + Gy * hy) / Gc;
+    x[13] = (hxx - hyy) * (hxx - hyy) + 4.0f * hxy * hxy;
+    x[14] = r * (hxx + hyy);
+    x[15] = 0.f;
+    float4* o = reinterpret_cast<float4*>(X + p * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  }
 }
 
 // training target s* = (D_xx + D_yy)(phi - h)
@@ -189,42 +254,54 @@ __global__ void k_ws_sum(const double* __restrict__ h, const double* __restrict_
     u[p] = h[p] + t[p];
 }
 
-// min over the grid of det(I + alpha D^2 u) for each alpha in {1, 1/2, 1/4, 1/8}; the last
-// block picks the largest admissible alpha (0 if none, or if the network reported an error)
-// and writes it to *alpha.
-__global__ void k_ws_admissible(const double* __restrict__ u, int N, int M,
-                                double* __restrict__ partials, unsigned int* ticket,
-                                const int* __restrict__ err, double* alpha) {
-  __shared__ double red[4][32];
+// min over the grid of det(I + alpha D^2 u) for each alpha in {1, 1/2, 1/4, 1/8} (tiled
+// double-float stencils; alpha scales exactly); the last block picks the largest admissible
+// alpha (0 if none, or if the network reported an error) and writes it to *alpha.
+__global__ void __launch_bounds__(256)
+    k_ws_admissible(const double* __restrict__ u, int N, int M, StencilK K,
+                    double* __restrict__ partials, unsigned int* ticket,
+                    const int* __restrict__ err, double* alpha) {
+  __shared__ TileDD T;
+  __shared__ float red[4][8];
   __shared__ bool last;
-  double mn[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-  const long P = (long)N * M;
-  const Stencil S{u, N, M};
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
-       p += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(p / M), j = (int)(p - (long)i * M);
-    const double uxx = S.dxx(i, j), uyy = S.dyy(i, j), uxy = S.dxy(i, j);
-    double a = 1.0;
+  const int bx = blockIdx.x * TW, by = blockIdx.y * TW;
+  tile_load_dd(T, u, N, M, by, bx);
+  float mn[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  const int tx = threadIdx.x % TW, ty0 = threadIdx.x / TW;
+  const int j = bx + tx;
+#pragma unroll 1
+  for (int rr = 0; rr < TRPT; ++rr) {
+    const int ty = ty0 + rr * (TW / TRPT);
+    const int i = by + ty;
+    if (i >= N || j >= M) continue;
+    dd ux, uy, uxx, uyy, uxy;
+    tile_stencils_dd(T, ty, tx, K, &ux, &uy, &uxx, &uyy, &uxy);
+    float a = 1.0f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q, a *= 0.5)
-      mn[q] = fmin(mn[q], (1.0 + a * uxx) * (1.0 + a * uyy) - a * a * uxy * uxy);
+    for (int q = 0; q < 4; ++q, a *= 0.5f) {
+      const dd d = dd_sub(dd_mul(dd_add_f(dd_scale2(uxx, a), 1.0f), dd_add_f(dd_scale2(uyy, a), 1.0f)),
+                          dd_scale2(dd_mul(uxy, uxy), a * a));
+      mn[q] = fminf(mn[q], d.hi);  // d.hi carries the sign (d.hi == 0 counts as not > 0)
+    }
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    double v = mn[q];
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    float v = mn[q];
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) red[q][wid] = v;
   }
   __syncthreads();
+  const unsigned int nb = gridDim.x * gridDim.y;
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
   if (threadIdx.x == 0) {
     for (int q = 0; q < 4; ++q) {
-      double v = INFINITY;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmin(v, red[q][w]);
-      partials[blockIdx.x * 4 + q] = v;
+      float v = INFINITY;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, red[q][w]);
+      partials[(size_t)bid * 4 + q] = (double)v;
     }
     __threadfence();
-    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    last = atomicAdd(ticket, 1u) == nb - 1;
   }
   __syncthreads();
   if (!last || threadIdx.x != 0) return;
@@ -232,8 +309,8 @@ __global__ void k_ws_admissible(const double* __restrict__ u, int N, int M,
   double a = 1.0, pick = 0.0;
   for (int q = 0; q < 4; ++q, a *= 0.5) {
     double v = INFINITY;
-    for (unsigned int b = 0; b < gridDim.x; ++b)
-      v = fmin(v, ((volatile const double*)partials)[b * 4 + q]);
+    for (unsigned int b = 0; b < nb; ++b)
+      v = fmin(v, ((volatile const double*)partials)[(size_t)b * 4 + q]);
     if (v > 0.0) {
       pick = a;
       break;
@@ -715,9 +792,28 @@ cudaError_t launch_ws_source(const double* f, const double* g, double* src, long
   return cudaGetLastError();
 }
 
-cudaError_t launch_ws_features(const double* f, const double* g, const double* c,
+static dd host_dd(double v) {
+  dd r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
+static StencilK stencil_consts(int N, int M) {
+  StencilK K;
+  K.Mh = host_dd((double)M / 12.0);
+  K.Nh = host_dd((double)N / 12.0);
+  K.Mh2 = host_dd((double)M * (double)M / 12.0);
+  K.Nh2 = host_dd((double)N * (double)N / 12.0);
+  K.MNh = host_dd((double)M * (double)N / 144.0);
+  return K;
+}
+
+static dim3 tiles(int N, int M) { return dim3((M + TW - 1) / TW, (N + TW - 1) / TW); }
+
+cudaError_t launch_ws_features(const double* f, const double* g, const float* c32,
                                const double* h, int N, int M, float* X, cudaStream_t st) {
-  k_ws_features<<<grid2(N, M), 128, 0, st>>>(f, g, c, h, N, M, X);
+  k_ws_features<<<tiles(N, M), 256, 0, st>>>(f, g, c32, h, N, M, stencil_consts(N, M), X);
   return cudaGetLastError();
 }
 
@@ -738,12 +834,13 @@ cudaError_t launch_ws_sum(const double* h, const double* t, double* u, long P, c
   return cudaGetLastError();
 }
 
-int ws_admissible_blocks() { return 2 * 152; }
+int ws_admissible_blocks(int N, int M) { return ((M + TW - 1) / TW) * ((N + TW - 1) / TW); }
 
 cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
                                  unsigned int* ticket, const int* err, double* alpha,
                                  cudaStream_t st) {
-  k_ws_admissible<<<ws_admissible_blocks(), 256, 0, st>>>(u, N, M, partials, ticket, err, alpha);
+  k_ws_admissible<<<tiles(N, M), 256, 0, st>>>(u, N, M, stencil_consts(N, M), partials, ticket,
+                                               err, alpha);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long P = (long)N * M;
