@@ -69,10 +69,11 @@ extern "C" {
                                    synchronises once per GMRES cycle and per Newton step */
 #define OT_OPT_REORTH 13        /* 0 (default): one classical Gram-Schmidt pass per Arnoldi
                                    step; 1: two passes (reorthogonalisation) */
-#define OT_OPT_THETA_FP64 14    /* mixed mode only: 1 (default) recovers theta = Lbar^{-1}
-                                   sigma and forms the update in FP64 (FP32 round-off in theta
-                                   is amplified ~M^2 by the stencils at the grid scale and
-                                   slows the Newton tail); 0: in FP32 */
+#define OT_OPT_THETA_FP64 14    /* mixed mode only: precision of the inverse transforms of
+                                   theta = Lbar^{-1} sigma and of the update: 2 (default)
+                                   double-float (FP32 pairs, 48-bit significand), 1 FP64,
+                                   0 FP32 (FP32 round-off in theta is amplified ~M^2 by the
+                                   stencils at the grid scale and slows the Newton tail) */
 #define OT_OPT_AUTOTUNE 15      /* mixed mode: 1 (default) times the kernel variants of the
                                    FP32 transform passes at the first solve of each grid size
                                    and keeps the fastest (cached per size in the process) */

@@ -25,7 +25,9 @@ struct ot_plan {
   int max_newton = 200, max_restarts = 50;
   int precision = 0, safeguard = 1, translate = 1, warm_start = 0;
   int reorth = 0;  // Gram-Schmidt passes - 1 (OT_OPT_REORTH)
-  int theta64 = 1;  // mixed mode: theta = Lbar^{-1} sigma and the update in FP64
+  // mixed mode: precision of theta's inverse transforms and the update (OT_OPT_THETA_FP64):
+  // 0 FP32, 1 FP64, 2 double-float (default)
+  int theta64 = 2;
   int autotune = 1, tuned = 0;  // FP32 matvec kernel variants timed at the first solve
   cudaStream_t stream = 0;
   int device = 0;
@@ -38,10 +40,11 @@ struct ot_plan {
   // FP64 spectrum used by the prefilter when the inner precision is FP32
   void *spec64 = nullptr, *q64 = nullptr;
   void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
+  void* twdd = nullptr;                    // the same as (hi, lo) float pairs
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
   float2 *fdd = nullptr, *cdd = nullptr;
-  SpecTables tb64{}, tb32{};
+  SpecTables tb64{}, tb32{}, tbdd{};
   double* partials = nullptr;
   double* dmean = nullptr;
   DevScalars* sc = nullptr;
@@ -218,7 +221,7 @@ static void free_buffers(ot_plan* p) {
   p->uout = nullptr;
   void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
-                  p->tw32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
+                  p->tw32, p->twdd, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
                   p->ws_X, p->ws_s, p->ws_c32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -229,7 +232,7 @@ static void free_buffers(ot_plan* p) {
   p->hinit = nullptr;
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
-  p->spec64 = p->q64 = p->tw64 = p->tw32 = nullptr;
+  p->spec64 = p->q64 = p->tw64 = p->tw32 = p->twdd = nullptr;
   p->fdd = p->cdd = nullptr;
   p->partials = p->dmean = nullptr;
   p->sc = nullptr;
@@ -287,6 +290,17 @@ static int alloc_buffers(ot_plan* p) {
   std::vector<float> twf(tw.begin(), tw.end());
   CK(cudaMalloc(&p->tw32, ntw * 8));
   CK(cudaMemcpy(p->tw32, twf.data(), ntw * 8, cudaMemcpyHostToDevice));
+  std::vector<float> twd(tw.size() * 2);
+  for (size_t k = 0; k < tw.size(); ++k) {
+    const float h = (float)tw[k];
+    twd[2 * k] = h;
+    twd[2 * k + 1] = (float)(tw[k] - (double)h);
+  }
+  CK(cudaMalloc(&p->twdd, ntw * 16));
+  CK(cudaMemcpy(p->twdd, twd.data(), ntw * 16, cudaMemcpyHostToDevice));
+  p->tbdd.twL = p->twdd;
+  p->tbdd.twM = (const ddc*)p->twdd + L;
+  p->tbdd.twN = (const ddc*)p->twdd + 2 * L;
   p->tb64.twL = p->tw64;
   p->tb64.twM = (const double2*)p->tw64 + L;
   p->tb64.twN = (const double2*)p->tw64 + 2 * L;
@@ -419,7 +433,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       free_graph(p);
       return OT_OK;
     case OT_OPT_THETA_FP64:
-      if (v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
       p->theta64 = (int)v;
       free_graph(p);
       return OT_OK;
@@ -479,12 +493,18 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
                                  (const T*)p->coef, (T*)p->w, nullptr, nullptr, 0.0, 1.0, N, M,
                                  tb, nullptr, p->stream);
       case OT_PROF_COL_LBARINV:
+        if (sizeof(T) == 4 && p->theta64 == 2)
+          return launch_col_lbarinv_dd((const float2*)p->spec, (ddc*)p->q64, N, M, p->tb32,
+                                       p->tbdd, p->sc, p->stream);
         if (sizeof(T) == 4 && p->theta64)  // FP32 forward / FP64 inverse in this mode
           return launch_col_lbarinv_mixed((const float2*)p->spec, (double2*)p->q64, N, M,
                                           p->tb32, p->tb64, p->sc, p->stream);
         return launch_col<T>(COL_LBARINV, (C2<T>*)p->spec, (C2<T>*)p->q0, nullptr, nullptr, N,
                              M, tb, p->sc, nullptr, p->stream);
       case OT_PROF_ROW_C2R_UPDATE:
+        if (sizeof(T) == 4 && p->theta64 == 2)
+          return launch_row_c2r_update_dd((const ddc*)p->q64, p->u, p->ucand, 0.5, N, M,
+                                          p->tbdd, nullptr, p->stream);
         if (sizeof(T) == 4 && p->theta64)
           return launch_row_c2r<double>(ROWINV_UPDATE, (C2<double>*)p->q64, nullptr, nullptr,
                                         nullptr, nullptr, p->u, p->ucand, 0.5, 1.0, N, M,
@@ -622,13 +642,28 @@ static int run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* 
 
 // Newton update candidate u_out = u_in + s Lbar^{-1} sigma.  sc_driven: s and the buffer
 // pair come from the device scalars (graph); otherwise the host passes them.  In the mixed
-// mode with theta64 the three transform passes of theta run in FP64: theta is added to the
-// FP64 iterate, and FP32 round-off in theta is white noise that the fourth-order stencils
-// amplify by ~M^2 at the grid scale, where the Newton iteration damps it only slowly.
+// mode the inverse transforms of theta run in double-float (theta64 = 2) or FP64 (1): theta
+// is added to the FP64 iterate, and FP32 round-off in theta is white noise that the
+// fourth-order stencils amplify by ~M^2 at the grid scale, where the Newton iteration damps
+// it only slowly.  The forward transform of sigma and rho-bar stay FP32 (their round-off is
+// damped by rho-bar ~ 1/k^2).
 template <typename T>
 static int run_theta(ot_plan* p, const double* u_in, double* u_out, double step,
                      bool sc_driven) {
   const DevScalars* scp = sc_driven ? p->sc : nullptr;
+  if (sizeof(T) == 4 && p->theta64 == 2) {
+    LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+           launch_row_r2c<float>((const float*)p->sigma, 0, nullptr, nullptr,
+                                 (C2<float>*)p->spec, p->N, p->M, p->tb32, nullptr,
+                                 p->stream));
+    LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+           launch_col_lbarinv_dd((const float2*)p->spec, (ddc*)p->q64, p->N, p->M, p->tb32,
+                                 p->tbdd, p->sc, p->stream));
+    LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+           launch_row_c2r_update_dd((const ddc*)p->q64, u_in, u_out, step, p->N, p->M,
+                                    p->tbdd, scp, p->stream));
+    return OT_OK;
+  }
   if (sizeof(T) == 4 && p->theta64) {
     C2<double>* qq = (C2<double>*)p->q64;
     LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,

@@ -13,9 +13,15 @@ namespace otgb {
 
 struct dd {
   float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  // constants: the nearest float and the nearest float to the remainder (folded at compile
+  // time for literal arguments)
+  __host__ __device__ constexpr explicit dd(double v)
+      : hi((float)v), lo((float)(v - (double)(float)v)) {}
 };
 
-__device__ __forceinline__ dd dd_make(float hi, float lo) { return dd{hi, lo}; }
+__device__ __forceinline__ dd dd_make(float hi, float lo) { return dd(hi, lo); }
 
 // split an FP64 value: hi = nearest float, lo = nearest float to the (exact) remainder
 __device__ __forceinline__ dd dd_from_double(double a) {
@@ -71,5 +77,19 @@ __device__ __forceinline__ dd dd_fma(dd a, dd b, dd c) { return dd_add(dd_mul(a,
 __device__ __forceinline__ bool dd_gt(dd a, dd b) {
   return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
 }
+
+// operators, so that the templated transforms can run on dd
+__device__ __forceinline__ dd operator+(dd a, dd b) { return dd_add(a, b); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return dd_sub(a, b); }
+__device__ __forceinline__ dd operator-(dd a) { return dd_neg(a); }
+__device__ __forceinline__ dd operator*(dd a, dd b) { return dd_mul(a, b); }
+// multiplication by a sign +-1 (exact)
+__device__ __forceinline__ dd operator*(int s, dd a) { return s >= 0 ? a : dd_neg(a); }
+__device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = dd_add(a, b); }
+
+// complex dd
+struct ddc {
+  dd x, y;
+};
 
 }  // namespace otgb

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dd.cuh"
+
 #define OTGB_MAXM 16  // largest GMRES restart length + 1 held on the device
 
 namespace otgb {
@@ -13,6 +15,7 @@ namespace otgb {
 template <typename T> struct c2;
 template <> struct c2<float> { using type = float2; };
 template <> struct c2<double> { using type = double2; };
+template <> struct c2<dd> { using type = ddc; };
 template <typename T> using C2 = typename c2<T>::type;
 
 // Scalars of one solve, resident in device memory.  Kernels that end in a grid-wide
@@ -115,6 +118,15 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
 // theta = Lbar^{-1} sigma column pass, FP32 forward / FP64 inverse (mixed mode)
 cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, int M,
                                      const SpecTables& tb32, const SpecTables& tb64,
+                                     const DevScalars* sc, cudaStream_t st);
+// the same with the inverse column transform in double-float (tbdd: dd twiddle tables)
+cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
+                                  const SpecTables& tb32, const SpecTables& tbdd,
+                                  const DevScalars* sc, cudaStream_t st);
+// theta rows in double-float and the update u_out = u_in + step theta (FP64 u); with sc,
+// step and the buffer pair come from the device scalars (graph)
+cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
+                                     double step, int N, int M, const SpecTables& tbdd,
                                      const DevScalars* sc, cudaStream_t st);
 
 // Residual / coefficients, input translation ------------------------------------------

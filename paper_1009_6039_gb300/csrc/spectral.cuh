@@ -927,6 +927,117 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Same pass with the inverse column transform in double-float (dd.cuh): the FP64-accuracy
+// part of theta on the FP32 pipes.
+template <int E>
+__global__ void __launch_bounds__(256)
+    k_col_lbarinv_dd(const float2* __restrict__ spec, ddc* __restrict__ out, int N, int M,
+                     int Q, double inv_nm, const float2* __restrict__ twN32,
+                     const ddc* __restrict__ twNdd, const DevScalars* __restrict__ sc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ddc* sm = reinterpret_cast<ddc*>(smem_raw);
+  const int Lc = M / 2, TPT = N / E;
+  const int q = threadIdx.x / TPT, t = threadIdx.x - q * TPT;
+  const int col0 = blockIdx.x * Q, col = col0 + q;
+  const bool active = (q < Q) && (col < Lc);
+  ddc* db = sm + q * (N + 1);
+  float2* fb = reinterpret_cast<float2*>(db);  // FP32 phase uses the first quarter
+  const int lq = __ffs(Q) - 1;
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx >> lq, qq = idx & (Q - 1);
+    if (col0 + qq < Lc)
+      reinterpret_cast<float2*>(sm + qq * (N + 1))[n] = spec[(size_t)n * Lc + col0 + qq];
+  }
+  __syncthreads();
+  fft_smem<float, E, -1>(fb, N, t, active, twN32);
+  float ab[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
+  const float inv = (float)inv_nm;
+  float2 s[E];
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = t + e * TPT;
+      bool nyq2;
+      const int k2 = sfreq(k, N, &nyq2);
+      float2 z = fb[k], r;
+      if (col == 0) {
+        float2 pz = fb[(N - k) % N];
+        float2 A = mk2<float>(0.5f * (z.x + pz.x), 0.5f * (z.y - pz.y));
+        float2 B = mk2<float>(0.5f * (z.y + pz.y), -0.5f * (z.x - pz.x));
+        A = cmul<float>(rho_bar<float>(ab, 0, false, k2, nyq2), A);
+        B = cmul<float>(rho_bar<float>(ab, M / 2, true, k2, nyq2), B);
+        r = mk2<float>(A.x - B.y, A.y + B.x);
+      } else {
+        r = cmul<float>(rho_bar<float>(ab, col, false, k2, nyq2), z);
+      }
+      s[e] = mk2<float>(r.x * inv, r.y * inv);
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      ddc v;
+      v.x = dd(s[e].x, 0.0f);
+      v.y = dd(s[e].y, 0.0f);
+      db[t + e * TPT] = v;
+    }
+  }
+  __syncthreads();
+  fft_smem<dd, E, +1>(db, N, t, active, twNdd);
+  for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
+    const int n = idx >> lq, qq = idx & (Q - 1);
+    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * (N + 1) + n];
+  }
+}
+
+// theta rows (complex-to-real) in double-float, then u_out = u_in + step theta in FP64
+template <int E>
+__global__ void __launch_bounds__(256)
+    k_row_c2r_update_dd(const ddc* __restrict__ q, const double* __restrict__ u_in,
+                        double* __restrict__ u_out, double step, int N, int M,
+                        const ddc* __restrict__ twL, const ddc* __restrict__ twM,
+                        const DevScalars* __restrict__ sc) {
+  if (sc) {
+    step = sc->step_s;
+    if (sc->upar & 1) {
+      double* tmp = const_cast<double*>(u_in);
+      u_in = u_out;
+      u_out = tmp;
+    }
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ddc* sm = reinterpret_cast<ddc*>(smem_raw);
+  const int L = M / 2, TPT = L / E;
+  const int qq = threadIdx.x / TPT, t = threadIdx.x % TPT;
+  const int RB = blockDim.x / TPT;
+  const int row = blockIdx.x * RB + qq;
+  const bool active = row < N;
+  ddc* buf = sm + qq * (L + 1);
+  if (active) {
+    const ddc* sr = q + (size_t)row * L;
+#pragma unroll
+    for (int e = 0; e < E; ++e) buf[t + e * TPT] = sr[t + e * TPT];
+  }
+  __syncthreads();
+  c2r_preprocess<dd>(buf, L, t, TPT, active, twM);
+  fft_smem<dd, E, +1>(buf, L, t, active, twL);
+  if (!active) return;
+  const double2* ui = reinterpret_cast<const double2*>(u_in + (size_t)row * M);
+  double2* uo = reinterpret_cast<double2*>(u_out + (size_t)row * M);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int n = t + e * TPT;
+    const ddc z = buf[n];
+    double2 a = ui[n];
+    a.x += step * dd_to_double(z.x);
+    a.y += step * dd_to_double(z.y);
+    uo[n] = a;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Warp-FFT versions of the three matvec passes (FP32, power-of-two lengths).  Each thread
 // holds 32 elements of one transform; the threads of a transform are one warp (or part of
@@ -1390,6 +1501,42 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
   k_col_lbarinv_mixed<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
       (const double2*)tb64.twN, sc);
+  return cudaGetLastError();
+}
+
+template <int E>
+cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
+                             const SpecTables& tb32, const SpecTables& tbdd,
+                             const DevScalars* sc, cudaStream_t st) {
+  const int Lc = M / 2, TPT = N / E;
+  int Q = 256 / TPT;
+  if (Q < 1) Q = 1;
+  while (Q > 1 && (size_t)Q * (N + 1) * sizeof(ddc) > 160 * 1024) Q /= 2;
+  while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
+  if (Q > Lc) Q = Lc;
+  const size_t sm = (size_t)Q * (N + 1) * sizeof(ddc);
+  cudaError_t e = set_smem(k_col_lbarinv_dd<E>, sm);
+  if (e != cudaSuccess) return e;
+  k_col_lbarinv_dd<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+      spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
+      (const ddc*)tbdd.twN, sc);
+  return cudaGetLastError();
+}
+
+template <int E>
+cudaError_t row_c2r_update_dd_E(const ddc* q, const double* u_in, double* u_out, double step,
+                                int N, int M, const SpecTables& tbdd, const DevScalars* sc,
+                                cudaStream_t st) {
+  const int L = M / 2, TPT = L / E;
+  int RB = 256 / TPT;
+  if (RB < 1) RB = 1;
+  while (RB > 1 && (size_t)RB * (L + 1) * sizeof(ddc) > 160 * 1024) RB /= 2;
+  while (RB > 1 && (N + RB - 1) / RB < 2 * 152) RB /= 2;
+  const size_t sm = (size_t)RB * (L + 1) * sizeof(ddc);
+  cudaError_t e = set_smem(k_row_c2r_update_dd<E>, sm);
+  if (e != cudaSuccess) return e;
+  k_row_c2r_update_dd<E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
+      q, u_in, u_out, step, N, M, (const ddc*)tbdd.twL, (const ddc*)tbdd.twM, sc);
   return cudaGetLastError();
 }
 

@@ -9,4 +9,17 @@ cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, in
   if (fft_E(N) == 12) return col_lbarinv_mixed_E<12>(spec, out, N, M, tb32, tb64, sc, st);
   return col_lbarinv_mixed_E<8>(spec, out, N, M, tb32, tb64, sc, st);
 }
+cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
+                                  const SpecTables& tb32, const SpecTables& tbdd,
+                                  const DevScalars* sc, cudaStream_t st) {
+  if (fft_E(N) == 12) return col_lbarinv_dd_E<12>(spec, out, N, M, tb32, tbdd, sc, st);
+  return col_lbarinv_dd_E<8>(spec, out, N, M, tb32, tbdd, sc, st);
+}
+cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
+                                     double step, int N, int M, const SpecTables& tbdd,
+                                     const DevScalars* sc, cudaStream_t st) {
+  if (fft_E(M / 2) == 12)
+    return row_c2r_update_dd_E<12>(q, u_in, u_out, step, N, M, tbdd, sc, st);
+  return row_c2r_update_dd_E<8>(q, u_in, u_out, step, N, M, tbdd, sc, st);
+}
 }

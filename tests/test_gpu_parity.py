@@ -368,3 +368,22 @@ def test_fp32_operator_norm_accuracy(ot, N, M):
         assert ew <= 2e-6 and et <= 2e-6, (ew, et)
     p64.close()
     p32.close()
+
+
+def test_theta_precision_modes(ot):
+    # theta's inverse transforms in double-float (default), FP64 or FP32: all reach the
+    # tolerance at the same root; double-float and FP64 take the same Newton path
+    N = M = 128
+    f, g = I.noise_blob_pair(N, M, s=3300)
+    out = {}
+    for theta in (2, 1, 0):
+        p = plan(ot, N, M, "mixed", tau=1.0, tol=1e-8, eta=0.1, theta_fp64=theta,
+                 max_newton=300)
+        phi = dev(np.zeros((N, M)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["res_inf"] < 1e-8
+        out[theta] = (phi.cpu().numpy(), st)
+    assert abs(out[2][1]["newton_iters"] - out[1][1]["newton_iters"]) <= 1
+    assert np.abs(out[2][0] - out[1][0]).max() <= 1e-9
+    assert np.abs(out[0][0] - out[1][0]).max() <= 1e-6
