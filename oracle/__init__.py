@@ -74,6 +74,7 @@ def lib():
                                    ctypes.POINTER(Stats), vp, vp]
         _lib.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
         _lib.orc_fd_poisson.argtypes = [vp, i, i, i, vp]
+        _lib.orc_set_fd_symbols.argtypes = [i]
         _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
     return _lib
 
@@ -247,3 +248,19 @@ def ws_features(f, g, c, h):
     X = np.empty((N, M, 16))
     lib().orc_ws_features(_p(f), _p(g), _p(c), _p(h), N, M, _p(X))
     return X
+
+
+class fd_symbols:
+    """Context manager: the linear operator (apply_op, apply_lbar_inv, gmres_op, solve) uses
+    the Fourier symbols of the 4th-order stencils instead of the spectral ones."""
+
+    def __init__(self, on=True):
+        self.on = on
+
+    def __enter__(self):
+        lib().orc_set_fd_symbols(int(bool(self.on)))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_fd_symbols(0)
+        return False

@@ -470,49 +470,71 @@ static long signed_freq(int n, int L, int *is_nyq) {
   return n <= L / 2 ? n : (long)n - L;
 }
 
-/* first-derivative symbol 2 pi i k (purely imaginary; 0 at Nyquist): returns its
- * imaginary part */
-static double sym1(long k, int nyq) { return nyq ? 0.0 : TWO_PI * (double)k; }
+/* Symbols of the derivatives in the linear operator: 0 (default) the paper's spectral
+ * symbols 2 pi i k and -(2 pi k)^2 (Sec. 4.2); 1 the Fourier symbols of the 4th-order
+ * stencils of the residual (reading R1), which make L the exact linearisation of the
+ * discrete F. */
+static int g_fd = 0;
+void orc_set_fd_symbols(int on) { g_fd = on ? 1 : 0; }
 
-/* second-derivative symbol -(2 pi k)^2 (real, kept at Nyquist) */
-static double sym2(long k) { return -(TWO_PI * (double)k) * (TWO_PI * (double)k); }
+/* first-derivative symbol (purely imaginary): returns its imaginary part.  Spectral:
+ * 2 pi k, 0 at Nyquist; stencil: (8 sin t - sin 2t) / (6 h), t = 2 pi k / L, h = 1/L. */
+static double sym1(long k, int L, int nyq, int fd) {
+  if (fd) {
+    double t = TWO_PI * (double)k / (double)L;
+    return (8.0 * sin(t) - sin(2.0 * t)) / 6.0 * (double)L;
+  }
+  return nyq ? 0.0 : TWO_PI * (double)k;
+}
 
-/* symbol of d_p d_q at frequency (k1, k2) (p, q in {1, 2}, 1 = x, 2 = y) as a complex
- * number (re, im).  Same-axis pairs use the second-derivative symbol; the mixed pair is
- * the product of the two first-derivative symbols. */
-static void sym_pq(int p, int q, long k1, int n1, long k2, int n2, double *re, double *im) {
+/* second-derivative symbol (real).  Spectral: -(2 pi k)^2, kept at Nyquist; stencil:
+ * (-2 cos 2t + 32 cos t - 30) / (12 h^2). */
+static double sym2(long k, int L, int fd) {
+  if (fd) {
+    double t = TWO_PI * (double)k / (double)L;
+    return (-2.0 * cos(2.0 * t) + 32.0 * cos(t) - 30.0) / 12.0 * (double)L * (double)L;
+  }
+  return -(TWO_PI * (double)k) * (TWO_PI * (double)k);
+}
+
+/* symbol of d_p d_q at frequency (k1, k2) (p, q in {1, 2}, 1 = x along M, 2 = y along N)
+ * as a complex number (re, im).  Same-axis pairs use the second-derivative symbol; the
+ * mixed pair is the product of the two first-derivative symbols. */
+static void sym_pq(int p, int q, long k1, int n1, int M, long k2, int n2, int N, int fd,
+                   double *re, double *im) {
   if (p == q) {
-    *re = (p == 1) ? sym2(k1) : sym2(k2);
+    *re = (p == 1) ? sym2(k1, M, fd) : sym2(k2, N, fd);
     *im = 0.0;
   } else {
     /* (i s1)(i s2) = -s1 s2 */
-    *re = -sym1(k1, n1) * sym1(k2, n2);
+    *re = -sym1(k1, M, n1, fd) * sym1(k2, N, n2, fd);
     *im = 0.0;
   }
 }
 
-static void sym_p(int p, long k1, int n1, long k2, int n2, double *re, double *im) {
+static void sym_p(int p, long k1, int n1, int M, long k2, int n2, int N, int fd, double *re,
+                  double *im) {
   *re = 0.0;
-  *im = (p == 1) ? sym1(k1, n1) : sym1(k2, n2);
+  *im = (p == 1) ? sym1(k1, M, n1, fd) : sym1(k2, N, n2, fd);
 }
 
-/* rho-bar(k) = 1 / (sum_ij abar_ij (2 pi i k_i)(2 pi i k_j) + sum_i bbar_i 2 pi i k_i),
+/* rho-bar(k) = 1 / (sum_ij abar_ij d_i d_j + sum_i bbar_i d_i) with the symbols above,
  * 0 where the denominator vanishes.  abar = {a11, a12, a22, b1, b2} (a21 = a12). */
-void orc_rho_bar(const double abar[5], long k1, int n1, long k2, int n2, double *re,
-                 double *im) {
+static void rho_bar_nm(const double abar[5], long k1, int n1, int M, long k2, int n2, int N,
+                       int fd, double *re, double *im) {
   double A[2][2] = {{abar[0], abar[1]}, {abar[1], abar[2]}};
   double B[2] = {abar[3], abar[4]};
   double dr = 0.0, di = 0.0;
   for (int p = 1; p <= 2; ++p)
     for (int q = 1; q <= 2; ++q) {
       double sr, si;
-      sym_pq(p, q, k1, n1, k2, n2, &sr, &si);
+      sym_pq(p, q, k1, n1, M, k2, n2, N, fd, &sr, &si);
       dr += A[p - 1][q - 1] * sr;
       di += A[p - 1][q - 1] * si;
     }
   for (int p = 1; p <= 2; ++p) {
     double sr, si;
-    sym_p(p, k1, n1, k2, n2, &sr, &si);
+    sym_p(p, k1, n1, M, k2, n2, N, fd, &sr, &si);
     dr += B[p - 1] * sr;
     di += B[p - 1] * si;
   }
@@ -524,6 +546,12 @@ void orc_rho_bar(const double abar[5], long k1, int n1, long k2, int n2, double 
     *re = dr / den;
     *im = -di / den;
   }
+}
+
+/* rho-bar with the spectral symbols (the lengths do not enter them) */
+void orc_rho_bar(const double abar[5], long k1, int n1, long k2, int n2, double *re,
+                 double *im) {
+  rho_bar_nm(abar, k1, n1, 1, k2, n2, 1, 0, re, im);
 }
 
 /* w = L Lbar^{-1} sigma:
@@ -550,7 +578,7 @@ void orc_apply_op(const double *coef, const double abar[5], const double *sigma,
       int n1;
       long k1 = signed_freq(j, M, &n1);
       double rr, ri;
-      orc_rho_bar(abar, k1, n1, k2, n2, &rr, &ri);
+      rho_bar_nm(abar, k1, n1, M, k2, n2, N, g_fd, &rr, &ri);
       long p = (long)i * M + j;
       double a = s_re[p], b = s_im[p];
       s_re[p] = rr * a - ri * b;
@@ -577,9 +605,9 @@ void orc_apply_op(const double *coef, const double abar[5], const double *sigma,
         long k1 = signed_freq(j, M, &n1);
         double sr, si;
         if (second)
-          sym_pq(p, q, k1, n1, k2, n2, &sr, &si);
+          sym_pq(p, q, k1, n1, M, k2, n2, N, g_fd, &sr, &si);
         else
-          sym_p(p, k1, n1, k2, n2, &sr, &si);
+          sym_p(p, k1, n1, M, k2, n2, N, g_fd, &sr, &si);
         long idx = (long)i * M + j;
         t_re[idx] = sr * s_re[idx] - si * s_im[idx];
         t_im[idx] = sr * s_im[idx] + si * s_re[idx];
@@ -614,7 +642,7 @@ void orc_apply_lbar_inv(const double abar[5], const double *sigma, int N, int M,
       int n1;
       long k1 = signed_freq(j, M, &n1);
       double rr, ri;
-      orc_rho_bar(abar, k1, n1, k2, n2, &rr, &ri);
+      rho_bar_nm(abar, k1, n1, M, k2, n2, N, g_fd, &rr, &ri);
       long p = (long)i * M + j;
       double a = s_re[p], b = s_im[p];
       s_re[p] = rr * a - ri * b;

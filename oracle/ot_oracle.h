@@ -65,6 +65,9 @@ int orc_gmres_op(const double *coef, const double abar[5], const double *h, int 
 int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_opts *o,
               double *u, orc_stats *st, double *hist_res, int *hist_gmres);
 
+/* symbols of the linear operator: 0 spectral (Sec. 4.2, default), 1 those of the stencils */
+void orc_set_fd_symbols(int on);
+
 /* learned warm start: FD Poisson solve and network features */
 #define ORC_WS_K 16
 int orc_fd_poisson(const double *src, int N, int M, int lowpass, double *out);
