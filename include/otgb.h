@@ -77,6 +77,13 @@ extern "C" {
 #define OT_OPT_AUTOTUNE 15      /* mixed mode: 1 (default) times the kernel variants of the
                                    FP32 transform passes at the first solve of each grid size
                                    and keeps the fastest (cached per size in the process) */
+#define OT_OPT_SYMBOLS 17       /* derivative symbols of the linear operator L and of Lbar:
+                                   0 (default) the spectral symbols 2 pi i k, -(2 pi k)^2 of
+                                   Sec. 4.2; 1 the Fourier symbols of the 4th-order stencils
+                                   that F itself uses, (8 sin t - sin 2t)/(6h) and
+                                   (-2 cos 2t + 32 cos t - 30)/(12 h^2), t = 2 pi k h, which
+                                   make L the exact linearisation of F (Newton then converges
+                                   quadratically at tau = 1 with accurate inner solves) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 3 c + 9 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -41,6 +41,8 @@ struct ot_plan {
   void *spec64 = nullptr, *q64 = nullptr;
   void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
   void* twdd = nullptr;                    // the same as (hi, lo) float pairs
+  void *sym64 = nullptr, *sym32 = nullptr;  // derivative symbol tables (M/2 + 1 + N pairs)
+  int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
   float2 *fdd = nullptr, *cdd = nullptr;
@@ -135,6 +137,12 @@ static void prof_harvest(ot_plan* p, int jend) {
 
 // Launch wrapper: counts `nk` kernel launches; with profiling on, brackets them with events
 // on the plan's stream.
+#define RET(x)                  \
+  do {                          \
+    int r_ = (x);               \
+    if (r_ != OT_OK) return r_; \
+  } while (0)
+
 #define LAUNCH(p, cls, tag, nk, expr)                                  \
   do {                                                                 \
     cudaEvent_t a_ = nullptr;                                          \
@@ -221,7 +229,7 @@ static void free_buffers(ot_plan* p) {
   p->uout = nullptr;
   void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
-                  p->tw32, p->twdd, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
+                  p->tw32, p->twdd, p->sym64, p->sym32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
                   p->ws_X, p->ws_s, p->ws_c32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -233,6 +241,7 @@ static void free_buffers(ot_plan* p) {
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
   p->spec64 = p->q64 = p->tw64 = p->tw32 = p->twdd = nullptr;
+  p->sym64 = p->sym32 = nullptr;
   p->fdd = p->cdd = nullptr;
   p->partials = p->dmean = nullptr;
   p->sc = nullptr;
@@ -247,6 +256,42 @@ static void roots(int L, int count, std::vector<double>& out) {
     out.push_back(std::cos(a));
     out.push_back(-std::sin(a));
   }
+}
+
+// (s1, s2) of frequency index k of length L (k <= L/2 for the half axis): spectral
+// 2 pi k (0 at Nyquist) and -(2 pi k)^2 (Sec. 4.2, reading R4), or the Fourier symbols of the
+// 4th-order stencils (8 sin t - sin 2t) L / 6 and (-2 cos 2t + 32 cos t - 30) L^2 / 12,
+// t = 2 pi k / L (reading R1), which make L the exact linearisation of the discrete F.
+static void deriv_symbols(int k, int L, int stencil, double* s1, double* s2) {
+  const long ks = (2 * k <= L) ? k : (long)k - L;
+  const bool nyq = 2 * k == L;
+  if (stencil) {
+    const double t = 2.0 * M_PI * (double)k / (double)L;
+    *s1 = nyq ? 0.0 : (8.0 * std::sin(t) - std::sin(2.0 * t)) / 6.0 * (double)L;
+    *s2 = (-2.0 * std::cos(2.0 * t) + 32.0 * std::cos(t) - 30.0) / 12.0 * (double)L * (double)L;
+  } else {
+    const double q = 2.0 * M_PI * (double)ks;
+    *s1 = nyq ? 0.0 : q;
+    *s2 = -q * q;
+  }
+}
+
+static int fill_symbols(ot_plan* p) {
+  const int nx = p->M / 2 + 1, n = nx + p->N;
+  std::vector<double> d(2 * (size_t)n);
+  for (int k = 0; k < nx; ++k) deriv_symbols(k, p->M, p->symbols, &d[2 * k], &d[2 * k + 1]);
+  for (int k = 0; k < p->N; ++k)
+    deriv_symbols(k, p->N, p->symbols, &d[2 * (nx + k)], &d[2 * (nx + k) + 1]);
+  std::vector<float> f(d.begin(), d.end());
+  if (!p->sym64) CK(cudaMalloc(&p->sym64, (size_t)n * 16));
+  if (!p->sym32) CK(cudaMalloc(&p->sym32, (size_t)n * 8));
+  CK(cudaMemcpy(p->sym64, d.data(), (size_t)n * 16, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(p->sym32, f.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+  p->tb64.symx = p->sym64;
+  p->tb64.symy = (const double2*)p->sym64 + nx;
+  p->tb32.symx = p->sym32;
+  p->tb32.symy = (const float2*)p->sym32 + nx;
+  return OT_OK;
 }
 
 static int alloc_buffers(ot_plan* p) {
@@ -301,6 +346,7 @@ static int alloc_buffers(ot_plan* p) {
   p->tbdd.twL = p->twdd;
   p->tbdd.twM = (const ddc*)p->twdd + L;
   p->tbdd.twN = (const ddc*)p->twdd + 2 * L;
+  RET(fill_symbols(p));
   p->tb64.twL = p->tw64;
   p->tb64.twM = (const double2*)p->tw64 + L;
   p->tb64.twN = (const double2*)p->tw64 + 2 * L;
@@ -449,6 +495,13 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       free_graph(p);
       return OT_OK;
     }
+    case OT_OPT_SYMBOLS:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->symbols != (int)v) {
+        p->symbols = (int)v;
+        if (p->ready) RET(fill_symbols(p));
+      }
+      return OT_OK;
     case OT_OPT_AUTOTUNE:
       if (v != 0 && v != 1) return OT_EINVAL;
       p->autotune = (int)v;
@@ -572,11 +625,6 @@ static int read_scalars(ot_plan* p) {
   return OT_OK;
 }
 
-#define RET(x)                  \
-  do {                          \
-    int r_ = (x);               \
-    if (r_ != OT_OK) return r_; \
-  } while (0)
 
 // c = B-spline coefficients of g, in FP64 (prefilter by the symbol (2 + cos)/3 per axis)
 static int run_prefilter(ot_plan* p, const double* g, double* c) {

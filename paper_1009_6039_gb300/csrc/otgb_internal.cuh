@@ -92,6 +92,11 @@ struct SpecTables {
   const void* twL;  // exp(-2 pi i t / (M/2)), t < M/2 (row transforms)
   const void* twM;  // exp(-2 pi i k / M), k < M/2 (real-to-complex split)
   const void* twN;  // exp(-2 pi i t / N), t < N (column transforms)
+  // derivative symbols of the linear operator, (s1, s2) per frequency index: i s1 the first-
+  // derivative symbol (0 at Nyquist), s2 the second-derivative symbol; symx: k1 = 0..M/2,
+  // symy: k2 index 0..N-1 (spectral 2 pi k, -(2 pi k)^2, or the 4th-order stencils')
+  const void* symx = nullptr;
+  const void* symy = nullptr;
   // kernel variants of the FP32 matvec passes (chosen by the plan's autotuner):
   // -1 default, 0 generic (8 or 12 elements per thread, one transform after the other),
   // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32

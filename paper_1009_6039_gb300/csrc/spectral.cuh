@@ -361,16 +361,17 @@ __device__ __forceinline__ int sfreq(int n, int L, bool* nyq) {
   return (2 * n <= L) ? n : n - L;
 }
 
-// rho-bar(k) = 1 / (abar11 d11 + 2 abar12 d1 d2 + abar22 d22 + bbar1 d1 + bbar2 d2) with
-// d1 = 2 pi i k1 (0 at Nyquist), d11 = -(2 pi k1)^2; 0 where the denominator is 0.
+// Derivative symbols come from per-plan tables (SpecTables::symx, symy): entry k holds
+// (s1, s2) with i s1 the first-derivative symbol (0 at Nyquist) and s2 the second-
+// derivative symbol of frequency index k along x (k <= M/2) or y (k < N): the paper's
+// spectral symbols 2 pi k and -(2 pi k)^2 (Sec. 4.2), or those of the 4th-order stencils.
+//
+// rho-bar(k) = 1 / (abar11 d11 + 2 abar12 d1 d2 + abar22 d22 + bbar1 d1 + bbar2 d2), 0 where
+// the denominator is 0; sx = (s1, s2) of k1, sy of k2.
 template <typename T>
-__device__ __forceinline__ C2<T> rho_bar(const T ab[5], int k1, bool n1, int k2, bool n2) {
-  const T tp = (T)OTGB_TWO_PI;
-  T s1 = n1 ? (T)0 : tp * (T)k1;
-  T s2 = n2 ? (T)0 : tp * (T)k2;
-  T q1 = tp * (T)k1, q2 = tp * (T)k2;
-  T dr = -ab[0] * q1 * q1 - (T)2 * ab[1] * s1 * s2 - ab[2] * q2 * q2;
-  T di = ab[3] * s1 + ab[4] * s2;
+__device__ __forceinline__ C2<T> rho_bar(const T ab[5], C2<T> sx, C2<T> sy) {
+  T dr = ab[0] * sx.y - (T)2 * ab[1] * sx.x * sy.x + ab[2] * sy.y;
+  T di = ab[3] * sx.x + ab[4] * sy.x;
   T den = dr * dr + di * di;
   if (den == (T)0) return mk2<T>((T)0, (T)0);
   return mk2<T>(dr / den, -di / den);
@@ -464,7 +465,8 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
                       C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
                       double inv_nm,
                       const C2<T>* __restrict__ twN, const C2<T>* __restrict__ twM,
-                      const DevScalars* __restrict__ sc, const int* __restrict__ skip) {
+                      const DevScalars* __restrict__ sc, const int* __restrict__ skip,
+                      const C2<T>* __restrict__ symx, const C2<T>* __restrict__ symy) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
@@ -517,15 +519,14 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
           B = cscale<T>(B, inv_or_zero<T>(fd_lap<T>((T)-1, M) + ly) *
                                lowpass<T, MODE>(M / 2, k2, M, N));
         } else {
-          A = cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A);
-          B = cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B);
+          A = cmul<T>(rho_bar<T>(ab, symx[0], symy[k]), A);
+          B = cmul<T>(rho_bar<T>(ab, symx[M / 2], symy[k]), B);
           // the matvec's Q0 carries its Nyquist channel premultiplied by d11(M/2) =
           // -(2 pi M/2)^2, so that the two channels sharing the complex column have
           // comparable magnitudes; formed here from the unpacked channels (recovering one
           // channel from the packed sum would cost eps times the other's magnitude)
           if (MODE == COL_MATVEC) {
-            const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
-            const C2<T> Bn = cscale<T>(B, -qn * qn);
+            const C2<T> Bn = cscale<T>(B, symx[M / 2].y);
             s0[e] = cscale<T>(mk2<T>(A.x - Bn.y, A.y + Bn.x), inv);
           }
         }
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
           r = cscale<T>(z, inv_or_zero<T>(fd_lap<T>(twM[col].x, M) + fd_lap<T>(twN[k].x, N)) *
                                lowpass<T, MODE>(col, k2, M, N));
         } else {
-          r = cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z);
+          r = cmul<T>(rho_bar<T>(ab, symx[col], symy[k]), z);
         }
       }
       s[e] = cscale<T>(r, inv);
@@ -553,14 +554,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int k = t + e * TPT;
-        bool nyq2;
-        const int k2 = sfreq(k, N, &nyq2);
-        const T q2 = (T)OTGB_TWO_PI * (T)k2;
         C2<T> v = (MODE == COL_MATVEC && p == 0 && col == 0) ? s0[e] : s[e];
-        if (p == 1) {  // (2 pi i k2) S, zero at Nyquist
-          v = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
-        } else if (p == 2) {  // -(2 pi k2)^2 S
-          v = cscale<T>(v, -q2 * q2);
+        if (p == 1) {  // (i s1(k2)) S, zero at Nyquist
+          const T s1 = symy[k].x;
+          v = mk2<T>(-s1 * v.y, s1 * v.x);
+        } else if (p == 2) {  // s2(k2) S
+          v = cscale<T>(v, symy[k].y);
         }
         buf[k] = v;
       }
@@ -575,23 +574,23 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
 // ---------------------------------------------------------------------------------------
 // Row complex-to-real inverse transforms (raw: sum over the full Hermitian spectrum).
 // ---------------------------------------------------------------------------------------
-// row symbol kinds: 0 = 1, 1 = d/dx = 2 pi i k1 (0 at Nyquist), 2 = d2/dx2 = -(2 pi k1)^2
-// (kind 2 expects a matvec Q0, whose packed Nyquist channel is premultiplied)
+// row symbol kinds: 0 = 1, 1 = d/dx (i s1 of k1), 2 = d2/dx2 (s2 of k1) from the symbol
+// table symx (kind 2 expects a matvec Q0, whose packed Nyquist channel is premultiplied)
 template <typename T>
-__device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int L, int kind) {
-  const T tp = (T)OTGB_TWO_PI;
+__device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int kind,
+                                                  const C2<T>* __restrict__ symx) {
   if (kind == 0) return X;
   if (k == 0) {
     // packed (X0, XL): k1 = 0 and k1 = M/2 (Nyquist).  For d2/dx2 the Nyquist channel of
-    // Q0 already carries the factor -(2 pi M/2)^2: the column pass applies it before its
+    // Q0 already carries the factor s2(M/2): the column pass applies it before its
     // inverse transform (see k_col), so that the two channels sharing one complex column
     // have comparable magnitudes.
     if (kind == 1) return mk2<T>((T)0, (T)0);
     return mk2<T>((T)0, X.y);
   }
-  const T q = tp * (T)k;
-  if (kind == 1) return mk2<T>(-q * X.y, q * X.x);
-  return cscale<T>(X, -q * q);
+  const C2<T> sx = symx[k];
+  if (kind == 1) return mk2<T>(-sx.x * X.y, sx.x * X.x);
+  return cscale<T>(X, sx.y);
 }
 
 // complex-to-real pre-processing on a packed row in buf (in place):
@@ -623,7 +622,8 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
                           T* __restrict__ out, const double* __restrict__ u_in,
                           double* __restrict__ u_out, double step, double out_scale, int N,
                           int M, const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
-                          const int* __restrict__ skip, const DevScalars* __restrict__ sc) {
+                          const int* __restrict__ skip, const DevScalars* __restrict__ sc,
+                          const C2<T>* __restrict__ symx) {
   if (skip && *skip) return;
   if (MODE == ROWINV_UPDATE && sc) {
     // device-resident control: step s and the current/candidate buffers come from sc
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int k = t + e * TPT;
-        buf[k] = row_symbol_apply<T>(sr[k], k, L, kind);
+        buf[k] = row_symbol_apply<T>(sr[k], k, kind, symx);
       }
     }
     __syncthreads();
@@ -730,7 +730,8 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
                      C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
                      double inv_nm,
                      const C2<T>* __restrict__ twN, const DevScalars* __restrict__ sc,
-                     const int* __restrict__ skip) {
+                     const int* __restrict__ skip, const C2<T>* __restrict__ symx,
+                     const C2<T>* __restrict__ symy) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
@@ -760,29 +761,27 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   C2<T> s0[E];
   const bool lead = active && grp == 0;
   if (lead) {
-    const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
+    const T d11n = symx[M / 2].y;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = t + e * TPT;
-      bool nyq2;
-      const int k2 = sfreq(k, N, &nyq2);
-      const T q2 = (T)OTGB_TWO_PI * (T)k2;
+      const C2<T> sy = symy[k];
       C2<T> z = b0[k], v;
       if (col == 0) {
         C2<T> pz = b0[(N - k) % N];
         C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
         C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
-        A = cscale<T>(cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A), inv);
-        B = cscale<T>(cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B), inv);
+        A = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[0], symy[k]), A), inv);
+        B = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[M / 2], symy[k]), B), inv);
         v = mk2<T>(A.x - B.y, A.y + B.x);
-        const C2<T> Bn = cscale<T>(B, -qn * qn);
+        const C2<T> Bn = cscale<T>(B, d11n);
         s0[e] = mk2<T>(A.x - Bn.y, A.y + Bn.x);
       } else {
-        v = cscale<T>(cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z), inv);
+        v = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[col], symy[k]), z), inv);
         s0[e] = v;
       }
-      b0[stride + k] = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
-      b0[2 * stride + k] = cscale<T>(v, -q2 * q2);
+      b0[stride + k] = mk2<T>(-sy.x * v.y, sy.x * v.x);
+      b0[2 * stride + k] = cscale<T>(v, sy.y);
     }
   }
   __syncthreads();
@@ -809,7 +808,8 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
     k_row_combine_par(const C2<T>* __restrict__ q0, const C2<T>* __restrict__ q1,
                       const C2<T>* __restrict__ q2, const T* __restrict__ coef,
                       T* __restrict__ out, int N, int M, int RB, const C2<T>* __restrict__ twL,
-                      const C2<T>* __restrict__ twM, const int* __restrict__ skip) {
+                      const C2<T>* __restrict__ twM, const int* __restrict__ skip,
+                      const C2<T>* __restrict__ symx) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
@@ -828,9 +828,9 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
       const size_t o = (size_t)(row0 + qq) * L + k;
       const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
       C2<T>* b = sm + qq * (L + 1) + k;
-      b[0] = row_symbol_apply<T>(x0, k, L, 2);
-      b[stride] = row_symbol_apply<T>(x0, k, L, 1);
-      b[2 * stride] = row_symbol_apply<T>(x1, k, L, 1);
+      b[0] = row_symbol_apply<T>(x0, k, 2, symx);
+      b[stride] = row_symbol_apply<T>(x0, k, 1, symx);
+      b[2 * stride] = row_symbol_apply<T>(x1, k, 1, symx);
       b[3 * stride] = x1;
       b[4 * stride] = x2;
     }
@@ -872,7 +872,8 @@ template <int E>
 __global__ void __launch_bounds__(256)
     k_col_lbarinv_mixed(const float2* __restrict__ spec, double2* __restrict__ out, int N,
                         int M, int Q, double inv_nm, const float2* __restrict__ twN32,
-                        const double2* __restrict__ twN64, const DevScalars* __restrict__ sc) {
+                        const double2* __restrict__ twN64, const DevScalars* __restrict__ sc,
+                        const float2* __restrict__ symx, const float2* __restrict__ symy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* sm = reinterpret_cast<double2*>(smem_raw);
   const int Lc = M / 2, TPT = N / E;
@@ -898,18 +899,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = t + e * TPT;
-      bool nyq2;
-      const int k2 = sfreq(k, N, &nyq2);
       float2 z = fb[k], r;
       if (col == 0) {
         float2 pz = fb[(N - k) % N];
         float2 A = mk2<float>(0.5f * (z.x + pz.x), 0.5f * (z.y - pz.y));
         float2 B = mk2<float>(0.5f * (z.y + pz.y), -0.5f * (z.x - pz.x));
-        A = cmul<float>(rho_bar<float>(ab, 0, false, k2, nyq2), A);
-        B = cmul<float>(rho_bar<float>(ab, M / 2, true, k2, nyq2), B);
+        A = cmul<float>(rho_bar<float>(ab, symx[0], symy[k]), A);
+        B = cmul<float>(rho_bar<float>(ab, symx[M / 2], symy[k]), B);
         r = mk2<float>(A.x - B.y, A.y + B.x);
       } else {
-        r = cmul<float>(rho_bar<float>(ab, col, false, k2, nyq2), z);
+        r = cmul<float>(rho_bar<float>(ab, symx[col], symy[k]), z);
       }
       s[e] = mk2<double>((double)(r.x * inv), (double)(r.y * inv));
     }
@@ -933,7 +932,8 @@ template <int E>
 __global__ void __launch_bounds__(256)
     k_col_lbarinv_dd(const float2* __restrict__ spec, ddc* __restrict__ out, int N, int M,
                      int Q, double inv_nm, const float2* __restrict__ twN32,
-                     const ddc* __restrict__ twNdd, const DevScalars* __restrict__ sc) {
+                     const ddc* __restrict__ twNdd, const DevScalars* __restrict__ sc,
+                     const float2* __restrict__ symx, const float2* __restrict__ symy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ddc* sm = reinterpret_cast<ddc*>(smem_raw);
   const int Lc = M / 2, TPT = N / E;
@@ -959,18 +959,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = t + e * TPT;
-      bool nyq2;
-      const int k2 = sfreq(k, N, &nyq2);
       float2 z = fb[k], r;
       if (col == 0) {
         float2 pz = fb[(N - k) % N];
         float2 A = mk2<float>(0.5f * (z.x + pz.x), 0.5f * (z.y - pz.y));
         float2 B = mk2<float>(0.5f * (z.y + pz.y), -0.5f * (z.x - pz.x));
-        A = cmul<float>(rho_bar<float>(ab, 0, false, k2, nyq2), A);
-        B = cmul<float>(rho_bar<float>(ab, M / 2, true, k2, nyq2), B);
+        A = cmul<float>(rho_bar<float>(ab, symx[0], symy[k]), A);
+        B = cmul<float>(rho_bar<float>(ab, symx[M / 2], symy[k]), B);
         r = mk2<float>(A.x - B.y, A.y + B.x);
       } else {
-        r = cmul<float>(rho_bar<float>(ab, col, false, k2, nyq2), z);
+        r = cmul<float>(rho_bar<float>(ab, symx[col], symy[k]), z);
       }
       s[e] = mk2<float>(r.x * inv, r.y * inv);
     }
@@ -1094,7 +1092,8 @@ __global__ void __launch_bounds__(384)
     k_col_matvec_w(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
                    C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
                    double inv_nm, const C2<T>* __restrict__ twN,
-                   const DevScalars* __restrict__ sc, const int* __restrict__ skip) {
+                   const DevScalars* __restrict__ sc, const int* __restrict__ skip,
+                   const C2<T>* __restrict__ symx, const C2<T>* __restrict__ symy) {
   // threads: 3 groups (outputs Q0, Q1, Q2) x Q columns x N/32 threads per transform;
   // buffers [group][column][N + N/32]; group 0's buffer first holds the forward transform
   if (skip && *skip) return;
@@ -1120,7 +1119,7 @@ __global__ void __launch_bounds__(384)
 #pragma unroll
   for (int a = 0; a < 5; ++a) ab[a] = (T)sc->abar[a];
   const T inv = (T)inv_nm;
-  const T qn = (T)OTGB_TWO_PI * (T)(M / 2);
+  const T d11n = symx[M / 2].y;
   // every group forms S = rho-bar sigma-hat / (N M) and its own symbol; groups 1 and 2
   // write at once, group 0 (which overwrites the spectrum) after the barrier.  Column 0 of
   // Q0 carries its Nyquist channel times d11(M/2), so that the two channels sharing the
@@ -1130,24 +1129,22 @@ __global__ void __launch_bounds__(384)
 #pragma unroll
     for (int e = 0; e < 32; ++e) {
       const int k = t + e * TPT;
-      bool nyq2;
-      const int k2 = sfreq(k, N, &nyq2);
-      const T q2 = (T)OTGB_TWO_PI * (T)k2;
+      const C2<T> sy = symy[k];
       const C2<T> z = b0[pad32(k)];
       C2<T> v;
       if (col == 0) {
         const C2<T> pz = b0[pad32((N - k) & (N - 1))];
         C2<T> A = mk2<T>((T)0.5 * (z.x + pz.x), (T)0.5 * (z.y - pz.y));
         C2<T> B = mk2<T>((T)0.5 * (z.y + pz.y), (T)-0.5 * (z.x - pz.x));
-        A = cscale<T>(cmul<T>(rho_bar<T>(ab, 0, false, k2, nyq2), A), inv);
-        B = cscale<T>(cmul<T>(rho_bar<T>(ab, M / 2, true, k2, nyq2), B), inv);
-        if (grp == 0) B = cscale<T>(B, -qn * qn);
+        A = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[0], symy[k]), A), inv);
+        B = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[M / 2], symy[k]), B), inv);
+        if (grp == 0) B = cscale<T>(B, d11n);
         v = mk2<T>(A.x - B.y, A.y + B.x);
       } else {
-        v = cscale<T>(cmul<T>(rho_bar<T>(ab, col, false, k2, nyq2), z), inv);
+        v = cscale<T>(cmul<T>(rho_bar<T>(ab, symx[col], symy[k]), z), inv);
       }
-      if (grp == 1) v = nyq2 ? mk2<T>((T)0, (T)0) : mk2<T>(-q2 * v.y, q2 * v.x);
-      else if (grp == 2) v = cscale<T>(v, -q2 * q2);
+      if (grp == 1) v = mk2<T>(-sy.x * v.y, sy.x * v.x);
+      else if (grp == 2) v = cscale<T>(v, sy.y);
       if (grp == 0) s0[e] = v;
       else buf[pad32(k)] = v;
     }
@@ -1197,7 +1194,8 @@ __global__ void __launch_bounds__(320)
     k_row_combine_w(const C2<T>* __restrict__ q0, const C2<T>* __restrict__ q1,
                     const C2<T>* __restrict__ q2, const T* __restrict__ coef,
                     T* __restrict__ out, int N, int M, int RB, const C2<T>* __restrict__ twL,
-                    const C2<T>* __restrict__ twM, const int* __restrict__ skip) {
+                    const C2<T>* __restrict__ twM, const int* __restrict__ skip,
+                    const C2<T>* __restrict__ symx) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
@@ -1216,9 +1214,9 @@ __global__ void __launch_bounds__(320)
       const size_t o = (size_t)(row0 + qq) * L + k;
       const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
       C2<T>* b = sm + qq * LP + pad32(k);
-      b[0] = row_symbol_apply<T>(x0, k, L, 2);
-      b[stride] = row_symbol_apply<T>(x0, k, L, 1);
-      b[2 * stride] = row_symbol_apply<T>(x1, k, L, 1);
+      b[0] = row_symbol_apply<T>(x0, k, 2, symx);
+      b[stride] = row_symbol_apply<T>(x0, k, 1, symx);
+      b[2 * stride] = row_symbol_apply<T>(x1, k, 1, symx);
       b[3 * stride] = x1;
       b[4 * stride] = x2;
     }
@@ -1300,7 +1298,7 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN,
-      (const C2<T>*)tb.twM, sc, skip);
+      (const C2<T>*)tb.twM, sc, skip, (const C2<T>*)tb.symx, (const C2<T>*)tb.symy);
   return cudaGetLastError();
 }
 
@@ -1319,7 +1317,7 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   if (e != cudaSuccess) return e;
   k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, u_in, u_out, step, out_scale, N, M, (const C2<T>*)tb.twL,
-      (const C2<T>*)tb.twM, skip, sc);
+      (const C2<T>*)tb.twM, skip, sc, (const C2<T>*)tb.symx);
   return cudaGetLastError();
 }
 
@@ -1363,7 +1361,7 @@ cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2,
   if (e != cudaSuccess) return e;
   k_col_matvec_par<T, E><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
-      skip);
+      skip, (const C2<T>*)tb.symx, (const C2<T>*)tb.symy);
   return cudaGetLastError();
 }
 
@@ -1380,7 +1378,7 @@ cudaError_t col_matvec_w_launch(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* 
   if (e != cudaSuccess) return e;
   k_col_matvec_w<T><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
-      skip);
+      skip, (const C2<T>*)tb.symx, (const C2<T>*)tb.symy);
   return cudaGetLastError();
 }
 
@@ -1429,7 +1427,8 @@ cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
   cudaError_t e = set_smem(k_row_combine_par<T, E>, sm);
   if (e != cudaSuccess) return e;
   k_row_combine_par<T, E><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
-      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip,
+      (const C2<T>*)tb.symx);
   return cudaGetLastError();
 }
 
@@ -1445,7 +1444,8 @@ cudaError_t row_combine_w_launch(const C2<T>* q0, const C2<T>* q1, const C2<T>* 
   cudaError_t e = set_smem(k_row_combine_w<T>, sm);
   if (e != cudaSuccess) return e;
   k_row_combine_w<T><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
-      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+      q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip,
+      (const C2<T>*)tb.symx);
   return cudaGetLastError();
 }
 
@@ -1500,7 +1500,7 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
   if (e != cudaSuccess) return e;
   k_col_lbarinv_mixed<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
-      (const double2*)tb64.twN, sc);
+      (const double2*)tb64.twN, sc, (const float2*)tb32.symx, (const float2*)tb32.symy);
   return cudaGetLastError();
 }
 
@@ -1519,7 +1519,7 @@ cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
   if (e != cudaSuccess) return e;
   k_col_lbarinv_dd<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
-      (const ddc*)tbdd.twN, sc);
+      (const ddc*)tbdd.twN, sc, (const float2*)tb32.symx, (const float2*)tb32.symy);
   return cudaGetLastError();
 }
 

@@ -122,16 +122,18 @@ def test_residual_and_coefficients(ot, N, M, prec):
 @pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (64, 96), (192, 384),
                                  (256, 256)])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_operator_and_lbar_inverse(ot, N, M, prec):
+@pytest.mark.parametrize("symbols", [0, 1])
+def test_operator_and_lbar_inverse(ot, N, M, prec, symbols):
     f = I.blob_density(N, M, 21)
     g = I.blob_density(N, M, 22)
     u = smooth_field(N, M, amp=2e-3)
     _, coef, _ = O.residual(f, O.bspline_coeffs(g), u)
     abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
     sigma = RNG.standard_normal((N, M))
-    w_ref = O.apply_op(coef, abar, sigma)
-    th_ref = O.apply_lbar_inv(abar, sigma)
-    p = plan(ot, N, M, prec)
+    with O.fd_symbols(symbols):
+        w_ref = O.apply_op(coef, abar, sigma)
+        th_ref = O.apply_lbar_inv(abar, sigma)
+    p = plan(ot, N, M, prec, symbols=symbols)
     cd, sd, wd, td = dev(coef), dev(sigma), dev(np.zeros((N, M))), dev(np.zeros((N, M)))
     assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
     assert ot.ot_apply_lbar_inverse(p.h, hptr(abar), ptr(sd), ptr(td)) == 0
@@ -387,3 +389,25 @@ def test_theta_precision_modes(ot):
     assert abs(out[2][1]["newton_iters"] - out[1][1]["newton_iters"]) <= 1
     assert np.abs(out[2][0] - out[1][0]).max() <= 1e-9
     assert np.abs(out[0][0] - out[1][0]).max() <= 1e-6
+
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_stencil_symbol_solve_matches_oracle(ot, prec):
+    # with the stencils' symbols the operator is the exact linearisation of F; at tau = 1
+    # the FP64 path takes the oracle's Newton steps and both reach the same root
+    N = M = 32
+    f, g = I.blob_pair(N, M, s=8)
+    with O.fd_symbols():
+        u_ref, st_ref, _, _ = O.solve(f, g, tau=1.0, tol=1e-10, eta=1e-1)
+    p = plan(ot, N, M, prec, tau=1.0, tol=1e-10 if prec == "fp64" else 1e-8, eta=1e-1,
+             symbols=1, max_newton=300)
+    phi = dev(np.zeros((N, M)))
+    rc, st = p.solve(dev(f), dev(g), phi)
+    p.close()
+    assert rc == 0 and st_ref["status"] == 0
+    if prec == "fp64":
+        assert st["newton_iters"] == st_ref["newton_iters"]
+        assert np.abs(phi.cpu().numpy() - u_ref).max() <= 1e-10
+    else:
+        assert np.abs(phi.cpu().numpy() - u_ref).max() <= 1e-6

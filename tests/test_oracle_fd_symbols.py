@@ -52,11 +52,11 @@ def test_stencil_symbol_preconditioner_inverts_the_constant_coefficient_operator
 
 
 def test_stencil_symbol_solve_reaches_the_same_root():
-    N = M = 32
+    N = M = 24
     f, g = I.blob_pair(N, M, s=8)
-    u0, st0, h0, _ = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-4)
+    u0, st0, h0, _ = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-1)
     with O.fd_symbols():
-        u1, st1, h1, _ = O.solve(f, g, tau=1.0, tol=1e-10, eta=1e-4)
+        u1, st1, h1, _ = O.solve(f, g, tau=1.0, tol=1e-10, eta=1e-1)
     assert st0["status"] == 0 and st1["status"] == 0
     assert np.abs(u0 - u1).max() < 1e-10
     # exact Newton (tau = 1, consistent Jacobian, accurate inner solves) converges fast
