@@ -31,11 +31,14 @@ sys.path.insert(0, ROOT)
 METRIC = ("OT solves/s at 1024² to ‖res‖∞≤1e-8: mixed+learned vs plain "
           "FP64 GPU; HBM %")
 N_GRID = 1024
-TAU, TOL, ETA = 1.0, 1e-8, 1e-1
+TAU, TOL, ETA = 1.0, 1e-8, 1e-2
+SYMBOLS = 1  # operator symbols of the 4th-order stencils (exact Jacobian of F)
+PAPER_ETA = 1e-1  # the paper's configuration arm: spectral symbols, GMRES tolerance 0.1
 SEED = 3000
 WS_TRAIN_SEED = 10000
 WORKLOAD = ("smoothed-noise+16-blob density pair 1024x1024 (max/min 10, mean 1), tau=1, "
-            "GMRES(10) eta=0.1, tol 1e-8, mixed FP32-inner/FP64-outer, learned warm start")
+            "GMRES(10) eta=0.01, stencil-symbol operator, tol 1e-8, mixed "
+            "FP32-inner/FP64-outer, learned warm start")
 
 
 def parse():
@@ -282,7 +285,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     # learned warm start: train on other pairs of the generator (untimed set-up)
     from paper_1009_6039_gb300 import warmstart as WS
-    plan = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", stream=stream)
+    plan = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", stream=stream,
+                   symbols=SYMBOLS)
     if args.ws_weights:
         plan.load_weights(args.ws_weights)
         ws_info = {"weights": os.path.basename(args.ws_weights)}
@@ -291,7 +295,7 @@ def run_ours(args):
         pairs = [I.noise_blob_pair(N, M, s=WS_TRAIN_SEED + k)
                  for k in range(args.ws_train_pairs)]
         t1 = time.perf_counter()
-        Xtr, ttr = WS.training_data(pairs, N, M, tau=TAU, tol=TOL, eta=ETA)
+        Xtr, ttr = WS.training_data(pairs, N, M, tau=TAU, tol=TOL, eta=PAPER_ETA)
         t2 = time.perf_counter()
         ws_params = WS.fit(Xtr, ttr, steps=args.ws_fit_steps, batch=32768, seed=1)
         torch.cuda.synchronize()
@@ -383,7 +387,8 @@ def run_ours(args):
     phi_mixed = phi.clone()
 
     # the same mixed solve from phi = 0 (what the warm start saves)
-    pz = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", stream=stream)
+    pz = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", stream=stream,
+                 symbols=SYMBOLS)
     phiz = torch.zeros_like(fd)
     pz.solve(fd, gd, phiz)
     torch.cuda.synchronize()
@@ -403,6 +408,35 @@ def run_ours(args):
                   "step_halvings": stz["step_halvings"], "res_inf": stz["res_inf"],
                   "phi_vs_warm_inf": float((phiz - phi_mixed).abs().max().item())}
     pz.close()
+
+    # the paper's configuration: spectral derivative symbols (Sec. 4.2), eta = 0.1, same
+    # learned warm start
+    pp = ot.Plan(N, M, tau=TAU, tol=TOL, eta=PAPER_ETA, precision="mixed", stream=stream,
+                 symbols=0)
+    if args.ws_weights:
+        pp.load_weights(args.ws_weights)
+    else:
+        pp.set_weights(ws_params)
+    pp.set(warm_start=2)
+    php = torch.zeros_like(fd)
+    pp.solve(fd, gd, php)
+    torch.cuda.synchronize()
+    pms = 0.0
+    for _ in range(zsteps):
+        flush.zero_()
+        e0.record(stream)
+        rcp, stp = pp.solve(fd, gd, php)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms += e0.elapsed_time(e1)
+    pms /= zsteps
+    paper_arm = {"value": 1000.0 / pms, "unit": "solves/s", "ms_per_solve": pms,
+                 "config": "spectral derivative symbols (Sec. 4.2), tau=1, eta=0.1, learned "
+                           "warm start, mixed",
+                 "newton_iters": stp["newton_iters"], "gmres_iters": stp["gmres_iters"],
+                 "step_halvings": stp["step_halvings"], "res_inf": stp["res_inf"],
+                 "phi_vs_headline_inf": float((php - phi_mixed).abs().max().item())}
+    pp.close()
     # the network kernel alone (BF16 tcgen05), on this pair's features
     Xd = torch.empty((P, 16), dtype=torch.float32, device="cuda")
     plan.ws_features(fd, gd, Xd)
@@ -430,7 +464,8 @@ def run_ours(args):
     # plain FP64 GPU path on the same pair (for the mixed-vs-FP64 comparison)
     fp64 = None
     if not args.no_fp64:
-        p64 = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="fp64", stream=stream)  # phi0 = 0
+        p64 = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="fp64", stream=stream,
+                      symbols=SYMBOLS)  # phi0 = 0
         phi64 = torch.zeros_like(fd)
         p64.solve(fd, gd, phi64)
         torch.cuda.synchronize()
@@ -515,7 +550,8 @@ def run_ours(args):
                            else "single GPU"},
                 "grid_point_newton_iters_per_s": value * P * s0["newton_iters"],
                 "all_converged": ok, "quality": quality, "fp64_gpu": fp64,
-                "mixed_zero_start": zero_start, "warm_start": ws_info,
+                "mixed_zero_start": zero_start, "paper_symbols_arm": paper_arm,
+                "warm_start": ws_info,
                 "e2e": {"value": e2e_value, "unit": "solves/s",
                         "h2d_bytes_per_step": 2 * P * 8, "d2h_bytes_per_step": P * 8,
                         "api": "ot_solve_host"},

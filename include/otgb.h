@@ -84,6 +84,10 @@ extern "C" {
                                    (-2 cos 2t + 32 cos t - 30)/(12 h^2), t = 2 pi k h, which
                                    make L the exact linearisation of F (Newton then converges
                                    quadratically at tau = 1 with accurate inner solves) */
+#define OT_OPT_FORCING 18       /* GMRES tolerance per Newton step: 0 (default) the fixed
+                                   OT_OPT_ETA; 1 Eisenstat & Walker's choice 2 (eta_k =
+                                   0.9 (|F_k| / |F_k-1|)^2, safeguarded, capped by OT_OPT_ETA
+                                   and no tighter than 0.5 tol / |F_k|) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 3 c + 9 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -43,6 +43,7 @@ struct ot_plan {
   void* twdd = nullptr;                    // the same as (hi, lo) float pairs
   void *sym64 = nullptr, *sym32 = nullptr;  // derivative symbol tables (M/2 + 1 + N pairs)
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
+  int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
   float2 *fdd = nullptr, *cdd = nullptr;
@@ -495,6 +496,11 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       free_graph(p);
       return OT_OK;
     }
+    case OT_OPT_FORCING:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->forcing = (int)v;
+      free_graph(p);
+      return OT_OK;
     case OT_OPT_SYMBOLS:
       if (v != 0 && v != 1) return OT_EINVAL;
       if (p->symbols != (int)v) {
@@ -773,6 +779,7 @@ static int run_gmres(ot_plan* p) {
   T* sigma = (T*)p->sigma;
   const int* skip = &p->sc->cycle_done;
   CK(cudaMemsetAsync(sigma, 0, P * sizeof(T), p->stream));
+  if (p->forcing) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_FORCING, p->sc, p->stream, 1));
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
          launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
   for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
@@ -803,6 +810,9 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->max_newton = p->max_newton;
   p->hsc->max_restarts = p->max_restarts;
   p->hsc->ws_alpha = -1.0;
+  p->hsc->eta_max = p->eta;
+  p->hsc->res_prev = 0.0;
+  p->hsc->forcing = p->forcing;
 }
 
 static int run_autotune(ot_plan* p);
@@ -1057,6 +1067,7 @@ static int capture_solve(ot_plan* p) {
   // ---- Newton loop
   RET(add_conditional(p->cs[0], cudaGraphCondTypeWhile, &p->h_newton, &b1));
   RET(begin_body(p, 1, b1));
+  if (p->forcing) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_FORCING, p->sc, p->stream, 1));
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
          launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream,
                               sigma));

@@ -1096,6 +1096,26 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
       if (cont) sc->kcount += 4;  // restart residual: 3 matvec passes + init
       break;
     }
+    case CTL_FORCING:
+      // Eisenstat & Walker (1996), choice 2 with gamma = 0.9, alpha = 2: eta = gamma
+      // (|F_k| / |F_k-1|)^2, kept >= gamma eta_prev^2 when that exceeds 0.1, at most eta_max;
+      // and no tighter than needed to reach the Newton tolerance (0.5 tol / |F_k|)
+      if (sc->forcing) {
+        const double r = sc->res_inf, rp = sc->res_prev;
+        double e = sc->eta_max;
+        if (rp > 0.0) {
+          const double q = r / rp;
+          e = 0.9 * q * q;
+          const double sg = 0.9 * sc->eta * sc->eta;
+          if (sg > 0.1) e = fmax(e, sg);
+          e = fmin(e, sc->eta_max);
+        }
+        e = fmax(e, fmin(sc->eta_max, 0.5 * sc->tol / r));
+        e = fmax(e, 1e-6);
+        sc->eta = e;
+        sc->res_prev = r;
+      }
+      break;
     case CTL_GMRES_DONE:
       // Arnoldi steps: 3 matvec passes + dots + update (+ dots + update when reorthogonal.)
       sc->kcount += (sc->reorth ? 7LL : 5LL) * sc->iters;

@@ -43,6 +43,10 @@ struct DevScalars {
   double eta, tau;
   // Newton control, resident on the device for the graph-launched solve
   double tol, step_s;
+  // inexact-Newton forcing: forcing = 1 sets eta per step from eta_max and the residual
+  // ratio (Eisenstat & Walker's choice 2); res_prev = max|F| at the previous step
+  double eta_max, res_prev;
+  int forcing;
   int newton_n, halvings, status, upar, safeguard, max_newton, max_restarts;
   int gmres_iters_total, gmres_cycles_total, graph, reorth;
   long long kcount;  // kernels executed by the graph-launched solve
@@ -63,7 +67,8 @@ enum CtlOp {
   CTL_PRE_CYCLE = 2,    // enter the GMRES cycle loop unless already converged
   CTL_CYCLE_BEGIN = 3,  // arm Arnoldi step 0, disarm the others
   CTL_CYCLE_END = 4,    // another cycle (with a restart residual) unless converged / capped
-  CTL_GMRES_DONE = 5    // accumulate the GMRES counters of this Newton step
+  CTL_GMRES_DONE = 5,   // accumulate the GMRES counters of this Newton step
+  CTL_FORCING = 6       // GMRES tolerance of this Newton step (Eisenstat-Walker when set)
 };
 
 // The two buffers of the iterate u; `upar` in DevScalars names the current one.

@@ -23,7 +23,7 @@ import ot_inputs as I  # noqa: E402
 CASES = {
     "blob256": dict(kind="blob_pair", N=256, M=256, seed=1000, tau=4.0, tol=1e-10, eta=1e-1),
     "noise1024": dict(kind="noise_blob_pair", N=1024, M=1024, seed=3000, tau=1.0, tol=1e-8,
-                      eta=1e-1),
+                      eta=1e-2, symbols=1),
     "noise2048": dict(kind="noise_blob_pair", N=2048, M=2048, seed=3000, tau=1.0, tol=1e-8,
                       eta=1e-1),
 }
@@ -44,8 +44,10 @@ def run(name):
     case = CASES[name]
     f, g = inputs(case)
     t = time.time()
-    u, st, hres, hgm = O.solve(f, g, tau=case["tau"], tol=case["tol"], eta=case["eta"],
-                               max_newton=300)
+    # symbols: 0 the spectral derivative symbols of Sec. 4.2, 1 those of the stencils
+    with O.fd_symbols(case.get("symbols", 0)):
+        u, st, hres, hgm = O.solve(f, g, tau=case["tau"], tol=case["tol"], eta=case["eta"],
+                                   max_newton=300)
     secs = time.time() - t
     ii, jj = sample_indices(case["N"], case["M"])
     out = dict(case=case, oracle_seconds=secs, stats=st, res_history=hres.tolist(),

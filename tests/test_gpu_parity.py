@@ -411,3 +411,22 @@ def test_stencil_symbol_solve_matches_oracle(ot, prec):
         assert np.abs(phi.cpu().numpy() - u_ref).max() <= 1e-10
     else:
         assert np.abs(phi.cpu().numpy() - u_ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eisenstat_walker_forcing(ot, prec):
+    # adaptive GMRES tolerance: same root as the fixed tolerance, graph = host-driven
+    N = M = 64
+    f, g = I.noise_blob_pair(N, M, s=3400)
+    out = []
+    for forcing, graph in ((0, 1), (1, 1), (1, 0)):
+        p = plan(ot, N, M, prec, tau=1.0, tol=1e-9, eta=1e-2, symbols=1, forcing=forcing,
+                 graph=graph, max_newton=300)
+        phi = dev(np.zeros((N, M)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["res_inf"] < 1e-9
+        out.append((phi.cpu().numpy(), st))
+    assert np.abs(out[0][0] - out[1][0]).max() <= (1e-10 if prec == "fp64" else 1e-6)
+    assert np.array_equal(out[1][0], out[2][0])
+    assert out[1][1]["newton_iters"] == out[2][1]["newton_iters"]
