@@ -81,8 +81,8 @@ def algorithmic_bytes(cls, P, T, avg_basis):
         "row_r2c": 2 * T * P,                           # sigma in, half spectrum out
         "col_matvec": 4 * T * P,                        # spectrum in, Q0 Q1 Q2 out
         "row_c2r_combine": 9 * T * P,                   # Q0..Q2 + 5 coefs in, w out
-        "col_lbarinv": 2 * T * P,
-        "row_c2r_update": (T + 16) * P,                 # Q0 + u in, candidate u out
+        "col_lbarinv": (T + 8) * P,                     # half spectrum in, FP64/dd out
+        "row_c2r_update": (8 + 16) * P,                 # FP64/dd spectrum + u in, u out
         "gmres_dots": (avg_basis + 1) * T * P,          # V_0..V_j and w in
         "gmres_update": (avg_basis + 2) * T * P,        # V_0..V_j and w in, V_j+1 out
     }.get(cls)
