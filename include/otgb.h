@@ -88,12 +88,18 @@ extern "C" {
                                    OT_OPT_ETA; 1 Eisenstat & Walker's choice 2 (eta_k =
                                    0.9 (|F_k| / |F_k-1|)^2, safeguarded, capped by OT_OPT_ETA
                                    and no tighter than 0.5 tol / |F_k|) */
+#define OT_OPT_TAU_RETRY 19     /* 0..8 (default 0): when a solve ends with OT_EDIVERGED
+                                   (an iterate lost convexity), solve again from the start
+                                   with twice tau, up to this many times -- the remedy of
+                                   Sec. 3.2 / Sec. 5.3; phi and stats are those of the last
+                                   attempt (ot_solve, ot_solve_batched) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
-                                   autotuning: value r + 3 c + 9 b with r (row R2C), c
+                                   autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,
                                    1 = concurrent transforms (r: same as 0), 2 = warp-
-                                   synchronous radix-32 (where the size allows, else the
-                                   next variant that does); turns OT_OPT_AUTOTUNE off */
+                                   synchronous radix-32, 3 = generic with 4 elements per
+                                   thread (where the size allows, else a variant that does);
+                                   turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

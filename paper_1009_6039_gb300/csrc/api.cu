@@ -44,6 +44,7 @@ struct ot_plan {
   void *sym64 = nullptr, *sym32 = nullptr;  // derivative symbol tables (M/2 + 1 + N pairs)
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
+  int tau_retry = 0;  // OT_OPT_TAU_RETRY: re-solves with doubled tau after a divergence
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
   float2 *fdd = nullptr, *cdd = nullptr;
@@ -485,17 +486,22 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       free_graph(p);
       return OT_OK;
     case OT_OPT_FFT_VARIANT: {
-      // r2c + 3 col + 9 combine, each 0 generic, 1 concurrent, 2 warp (r2c: 1 = generic)
-      if (v < 0 || v > 26 || v != (double)(int)v) return OT_EINVAL;
+      // r2c + 4 col + 16 combine, each 0 generic, 1 concurrent (r2c: same as 0), 2 warp,
+      // 3 generic with 4 elements per thread
+      if (v < 0 || v > 63 || v != (double)(int)v) return OT_EINVAL;
       const int k = (int)v;
-      p->tb32.var_r2c = k % 3 == 2 ? VAR_WARP : VAR_GENERIC;
-      p->tb32.var_col = (k / 3) % 3;
-      p->tb32.var_comb = k / 9;
+      p->tb32.var_r2c = k % 4 == 1 ? VAR_GENERIC : k % 4;
+      p->tb32.var_col = (k / 4) % 4;
+      p->tb32.var_comb = k / 16;
       p->autotune = 0;
       p->tuned = 1;
       free_graph(p);
       return OT_OK;
     }
+    case OT_OPT_TAU_RETRY:
+      if (!(v >= 0 && v <= 8) || v != (double)(int)v) return OT_EINVAL;
+      p->tau_retry = (int)v;
+      return OT_OK;
     case OT_OPT_FORCING:
       if (v != 0 && v != 1) return OT_EINVAL;
       p->forcing = (int)v;
@@ -1173,13 +1179,14 @@ static int run_autotune(ot_plan* p) {
     return ms;
   };
   int* vars[3] = {&tb.var_r2c, &tb.var_col, &tb.var_comb};
-  const int cand[3][3] = {{VAR_GENERIC, VAR_WARP, VAR_WARP},
-                          {VAR_GENERIC, VAR_PAR, VAR_WARP},
-                          {VAR_GENERIC, VAR_PAR, VAR_WARP}};
+  const int ncand[3] = {3, 4, 4};
+  const int cand[3][4] = {{VAR_GENERIC, VAR_WARP, VAR_E4, VAR_E4},
+                          {VAR_GENERIC, VAR_PAR, VAR_WARP, VAR_E4},
+                          {VAR_GENERIC, VAR_PAR, VAR_WARP, VAR_E4}};
   for (int cls = 0; cls < 3; ++cls) {
     int best = VAR_GENERIC;
     float tbest = 1e30f;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < ncand[cls]; ++k) {
       *vars[cls] = cand[cls][k];
       const float tms = timed(cls);
       if (tms < tbest) {
@@ -1347,14 +1354,35 @@ static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, 
   return st->status;
 }
 
-extern "C" int ot_solve(ot_plan* p, const double* f, const double* g, double* phi,
-                        ot_stats* st) {
-  if (!p || !f || !g || !phi || !p->ready) return OT_EINVAL;
-  CK(cudaSetDevice(p->device));
+static int solve_once(ot_plan* p, const double* f, const double* g, double* phi,
+                      ot_stats* st) {
   if (p->use_graph && !p->profile)
     return p->precision ? solve_graph_impl<float>(p, f, g, phi, st)
                         : solve_graph_impl<double>(p, f, g, phi, st);
   return p->precision ? solve_impl<float>(p, f, g, phi, st) : solve_impl<double>(p, f, g, phi, st);
+}
+
+// The remedy of Sec. 3.2 / Sec. 5.3 for an iterate that loses convexity: solve again with
+// twice the step parameter tau (up to tau_retry times); phi and stats are those of the last
+// attempt.  The plan's tau is restored.
+static int solve_with_retry(ot_plan* p, const double* f, const double* g, double* phi,
+                            ot_stats* st, int rc) {
+  const double tau0 = p->tau;
+  for (int r = 0; r < p->tau_retry && rc == OT_EDIVERGED; ++r) {
+    p->tau *= 2.0;
+    rc = solve_once(p, f, g, phi, st);
+  }
+  p->tau = tau0;
+  return rc;
+}
+
+extern "C" int ot_solve(ot_plan* p, const double* f, const double* g, double* phi,
+                        ot_stats* st) {
+  if (!p || !f || !g || !phi || !p->ready) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  ot_stats local;
+  if (!st) st = &local;
+  return solve_with_retry(p, f, g, phi, st, solve_once(p, f, g, phi, st));
 }
 
 extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, double* phi,
@@ -1456,6 +1484,10 @@ extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const doub
       ot_stats tmp;
       memset(&tmp, 0, sizeof(tmp));
       graph_collect(p, &g_batch_slots[k], g_batch_means[k], &tmp);
+      if (tmp.status == OT_EDIVERGED && p->tau_retry > 0) {
+        const int rc = solve_with_retry(p, f[k], g[k], phi[k], &tmp, OT_EDIVERGED);
+        if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
+      }
       if (stats) stats[k] = tmp;
       if (tmp.status != OT_OK && first == OT_OK) first = tmp.status;
     } else if (g_batch_slots[k].status != OT_OK && first == OT_OK) {

@@ -104,10 +104,11 @@ struct SpecTables {
   const void* symy = nullptr;
   // kernel variants of the FP32 matvec passes (chosen by the plan's autotuner):
   // -1 default, 0 generic (8 or 12 elements per thread, one transform after the other),
-  // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32
+  // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32,
+  // 3 generic with 4 elements per thread (radix 4, twice the threads; power-of-two lengths)
   int var_r2c = -1, var_col = -1, var_comb = -1;
 };
-enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2 };
+enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2, VAR_E4 = 3 };
 
 bool fft_length_supported(int L);
 

@@ -1343,6 +1343,8 @@ cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double*
                            cudaStream_t st) {
   if (sizeof(T) == 4 && tb.var_r2c == VAR_WARP && warp_fft_ok(M / 2))
     return row_r2c_w_launch<T>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
+  if (sizeof(T) == 4 && tb.var_r2c == VAR_E4 && fft_E(M / 2) == 8 && M / 2 >= 4)
+    return row_r2c_E<T, 4>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   if (fft_E(M / 2) == 12) return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
 }
@@ -1411,6 +1413,8 @@ template <typename T>
 cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
                        int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
                        cudaStream_t st) {
+  if (sizeof(T) == 4 && mode == COL_MATVEC && tb.var_col == VAR_E4 && fft_E(N) == 8 && N >= 4)
+    return col_E<T, 4, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   if (fft_E(N) == 12) return col_dispatch<T, 12>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
   return col_dispatch<T, 8>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
 }
@@ -1479,6 +1483,10 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double os, int N, int M, const SpecTables& tb,
                            const int* skip, cudaStream_t st, const DevScalars* sc) {
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && tb.var_comb == VAR_E4 && fft_E(M / 2) == 8 &&
+      M / 2 >= 4)
+    return row_c2r_E<T, 4, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
+                                           tb, skip, st, sc);
   if (fft_E(M / 2) == 12)
     return row_c2r_dispatch<T, 12>(mode, q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
                                    tb, skip, st, sc);

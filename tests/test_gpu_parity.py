@@ -146,7 +146,8 @@ def test_operator_and_lbar_inverse(ot, N, M, prec, symbols):
 
 
 @pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512)])
-@pytest.mark.parametrize("variant", [0, 13, 26, 2 + 3 * 0 + 9 * 1])
+@pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
+                                     3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
     f = I.blob_density(N, M, 23)
@@ -430,3 +431,19 @@ def test_eisenstat_walker_forcing(ot, prec):
     assert np.abs(out[0][0] - out[1][0]).max() <= (1e-10 if prec == "fp64" else 1e-6)
     assert np.array_equal(out[1][0], out[2][0])
     assert out[1][1]["newton_iters"] == out[2][1]["newton_iters"]
+
+
+def test_tau_retry_after_divergence(ot):
+    # without the safeguard the blob pair diverges at tau = 2 (as in the oracle); with
+    # OT_OPT_TAU_RETRY the solve restarts with twice tau until it converges to the root
+    f, g = I.blob_pair(32, 32)
+    rc0, st0, _ = _gpu_solve(ot, f, g, "fp64", tol=1e-6, eta=1e-2, max_newton=400,
+                             safeguard=0)
+    assert rc0 == ot.OT_EDIVERGED
+    rc, st, phi = _gpu_solve(ot, f, g, "fp64", tol=1e-9, eta=1e-2, max_newton=400,
+                             safeguard=0, tau_retry=4)
+    assert rc == 0
+    # an independent safeguarded oracle solve reaches the same root
+    u_ref, st_ref, _, _ = O.solve(f, g, tau=4.0, tol=1e-10, eta=1e-2, max_newton=400)
+    assert st_ref["status"] == 0
+    assert np.abs(phi - u_ref).max() <= 1e-8
