@@ -101,11 +101,20 @@ template <typename T, int SIGN> struct Bfly<T, 8, SIGN> {
   }
 };
 
+// Shared-memory stride of one transform buffer of length L: between the stages of a
+// transform the data sit in a padded layout (one element of padding per 16, spad) so that
+// the strided stage writes spread over the banks; the transform's input and output use the
+// plain layout 0..L-1.
+__host__ __device__ constexpr int FB(int L) { return L + (L >> 4) + 1; }
+__device__ __forceinline__ int spad(int i, bool on) { return on ? i + (i >> 4) : i; }
+
 // One Stockham stage of radix R on a transform of length L held in buf (all threads of
-// the block must call it; inactive threads only take part in the barriers).
+// the block must call it; inactive threads only take part in the barriers).  pin / pout:
+// the stage reads / writes the padded layout.
 template <typename T, int E, int R, int SIGN>
 __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t, bool active,
-                                               const C2<T>* __restrict__ tw) {
+                                               const C2<T>* __restrict__ tw, bool pin,
+                                               bool pout) {
   const int TPT = L / E;
   const int LR = L / R;
   C2<T> v[E];
@@ -114,7 +123,7 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
     for (int b = 0; b < E / R; ++b) {
       const int j = t + b * TPT;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b * R + r] = buf[j + r * LR];
+      for (int r = 0; r < R; ++r) v[b * R + r] = buf[spad(j + r * LR, pin)];
     }
   }
   __syncthreads();
@@ -137,7 +146,7 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
       Bfly<T, R, SIGN>::run(&v[b * R]);
       const int d = qd * Ns * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[d + r * Ns] = v[b * R + r];
+      for (int r = 0; r < R; ++r) buf[spad(d + r * Ns, pout)] = v[b * R + r];
     }
   }
   __syncthreads();
@@ -151,21 +160,22 @@ __device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
   int Ns = 1;
   int rem = L;
   if (E % 3 == 0) {
-    stockham_stage<T, E, 3, SIGN>(buf, L, Ns, t, active, tw);
+    stockham_stage<T, E, 3, SIGN>(buf, L, Ns, t, active, tw, false, rem / 3 > 1);
     Ns *= 3;
     rem /= 3;
   }
   while (rem > 1) {
+    const bool pin = Ns > 1;
     if (E % 8 == 0 && rem % 8 == 0) {
-      stockham_stage<T, E, 8, SIGN>(buf, L, Ns, t, active, tw);
+      stockham_stage<T, E, 8, SIGN>(buf, L, Ns, t, active, tw, pin, rem / 8 > 1);
       Ns *= 8;
       rem /= 8;
     } else if (rem % 4 == 0) {
-      stockham_stage<T, E, 4, SIGN>(buf, L, Ns, t, active, tw);
+      stockham_stage<T, E, 4, SIGN>(buf, L, Ns, t, active, tw, pin, rem / 4 > 1);
       Ns *= 4;
       rem /= 4;
     } else {
-      stockham_stage<T, E, 2, SIGN>(buf, L, Ns, t, active, tw);
+      stockham_stage<T, E, 2, SIGN>(buf, L, Ns, t, active, tw, pin, rem / 2 > 1);
       Ns *= 2;
       rem /= 2;
     }
@@ -399,7 +409,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __res
   const int RB = blockDim.x / TPT;
   const int row = blockIdx.x * RB + q;
   const bool active = row < N;
-  C2<T>* buf = sm + q * (L + 1);
+  C2<T>* buf = sm + q * FB(L);
   int jv = jptr ? *jptr : 0;
   const T* x = xbase + (size_t)jv * x_stride;
   const T sc = scale ? (T)scale[jv] : (T)1;
@@ -445,7 +455,7 @@ __device__ __forceinline__ void col_load(const C2<T>* __restrict__ src, C2<T>* s
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
-    if (col < Lc) sm[q * (N + 1) + n] = src[(size_t)n * Lc + col];
+    if (col < Lc) sm[q * FB(N) + n] = src[(size_t)n * Lc + col];
   }
 }
 
@@ -456,7 +466,7 @@ __device__ __forceinline__ void col_store(C2<T>* __restrict__ dst, const C2<T>* 
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
-    if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * (N + 1) + n];
+    if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * FB(N) + n];
   }
 }
 
@@ -476,7 +486,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
   const int col0 = blockIdx.x * Q;
   const int col = col0 + q;
   const bool active = (q < Q) && (col < Lc);
-  C2<T>* buf = sm + q * (N + 1);
+  C2<T>* buf = sm + q * FB(N);
 
   col_load<T, E>(spec, sm, N, Lc, Q, col0);
   __syncthreads();
@@ -642,7 +652,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
   const int RB = blockDim.x / TPT;
   const int row = blockIdx.x * RB + q;
   const bool active = row < N;
-  C2<T>* buf = sm + q * (L + 1);
+  C2<T>* buf = sm + q * FB(L);
   const size_t P = (size_t)N * M;
   C2<T> acc[E];
 #pragma unroll
@@ -740,13 +750,13 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   const int q = rem / TPT, t = rem - q * TPT;
   const int col0 = blockIdx.x * Q, col = col0 + q;
   const bool active = col < Lc;
-  const int stride = Q * (N + 1);  // one group's buffers
-  C2<T>* buf = sm + grp * stride + q * (N + 1);
-  C2<T>* b0 = sm + q * (N + 1);
+  const int stride = Q * FB(N);  // one group's buffers
+  C2<T>* buf = sm + grp * stride + q * FB(N);
+  C2<T>* b0 = sm + q * FB(N);
   const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, qq = idx & (Q - 1);
-    if (col0 + qq < Lc) sm[qq * (N + 1) + n] = spec[(size_t)n * Lc + col0 + qq];
+    if (col0 + qq < Lc) sm[qq * FB(N) + n] = spec[(size_t)n * Lc + col0 + qq];
   }
   __syncthreads();
   fft_smem<T, E, -1>(b0, N, t, active && grp == 0, twN);
@@ -796,7 +806,7 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
     C2<T>* dst = g == 0 ? out0 : (g == 1 ? out1 : out2);
     for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
       const int n = idx >> lq, qq = idx & (Q - 1);
-      if (col0 + qq < Lc) dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * (N + 1) + n];
+      if (col0 + qq < Lc) dst[(size_t)n * Lc + col0 + qq] = sm[g * stride + qq * FB(N) + n];
     }
   }
 }
@@ -818,8 +828,8 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
   const int q = rem / TPT, t = rem - q * TPT;
   const int row0 = blockIdx.x * RB, row = row0 + q;
   const bool active = row < N;
-  const int stride = RB * (L + 1);
-  C2<T>* buf = sm + grp * stride + q * (L + 1);
+  const int stride = RB * FB(L);
+  C2<T>* buf = sm + grp * stride + q * FB(L);
   const int la = __ffs(L) - 1;
   const bool lp2 = (L >> la) == 1;
   for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
@@ -827,7 +837,7 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
     if (row0 + qq < N) {
       const size_t o = (size_t)(row0 + qq) * L + k;
       const C2<T> x0 = q0[o], x1 = q1[o], x2 = q2[o];
-      C2<T>* b = sm + qq * (L + 1) + k;
+      C2<T>* b = sm + qq * FB(L) + k;
       b[0] = row_symbol_apply<T>(x0, k, 2, symx);
       b[stride] = row_symbol_apply<T>(x0, k, 1, symx);
       b[2 * stride] = row_symbol_apply<T>(x1, k, 1, symx);
@@ -849,7 +859,7 @@ __global__ void __launch_bounds__(OTGB_PAR_THREADS)
       const C2<T>* c2 = reinterpret_cast<const C2<T>*>(coef + 2 * P + o);
       const C2<T>* c3 = reinterpret_cast<const C2<T>*>(coef + 3 * P + o);
       const C2<T>* c4 = reinterpret_cast<const C2<T>*>(coef + 4 * P + o);
-      const C2<T>* b = sm + qq * (L + 1) + n;
+      const C2<T>* b = sm + qq * FB(L) + n;
       const C2<T> y0 = b[0], y1 = b[stride], y2 = b[2 * stride], y3 = b[3 * stride],
                   y4 = b[4 * stride];
       const C2<T> a11 = c0[n], a12 = c1[n], a22 = c2[n], b1 = c3[n], b2 = c4[n];
@@ -880,13 +890,13 @@ __global__ void __launch_bounds__(256)
   const int q = threadIdx.x / TPT, t = threadIdx.x - q * TPT;
   const int col0 = blockIdx.x * Q, col = col0 + q;
   const bool active = (q < Q) && (col < Lc);
-  double2* db = sm + q * (N + 1);
+  double2* db = sm + q * FB(N);
   float2* fb = reinterpret_cast<float2*>(db);  // FP32 phase uses the first half
   const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, qq = idx & (Q - 1);
     if (col0 + qq < Lc)
-      reinterpret_cast<float2*>(sm + qq * (N + 1))[n] = spec[(size_t)n * Lc + col0 + qq];
+      reinterpret_cast<float2*>(sm + qq * FB(N))[n] = spec[(size_t)n * Lc + col0 + qq];
   }
   __syncthreads();
   fft_smem<float, E, -1>(fb, N, t, active, twN32);
@@ -922,7 +932,7 @@ __global__ void __launch_bounds__(256)
   fft_smem<double, E, +1>(db, N, t, active, twN64);
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, qq = idx & (Q - 1);
-    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * (N + 1) + n];
+    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * FB(N) + n];
   }
 }
 
@@ -940,13 +950,13 @@ __global__ void __launch_bounds__(256)
   const int q = threadIdx.x / TPT, t = threadIdx.x - q * TPT;
   const int col0 = blockIdx.x * Q, col = col0 + q;
   const bool active = (q < Q) && (col < Lc);
-  ddc* db = sm + q * (N + 1);
+  ddc* db = sm + q * FB(N);
   float2* fb = reinterpret_cast<float2*>(db);  // FP32 phase uses the first quarter
   const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, qq = idx & (Q - 1);
     if (col0 + qq < Lc)
-      reinterpret_cast<float2*>(sm + qq * (N + 1))[n] = spec[(size_t)n * Lc + col0 + qq];
+      reinterpret_cast<float2*>(sm + qq * FB(N))[n] = spec[(size_t)n * Lc + col0 + qq];
   }
   __syncthreads();
   fft_smem<float, E, -1>(fb, N, t, active, twN32);
@@ -987,7 +997,7 @@ __global__ void __launch_bounds__(256)
   fft_smem<dd, E, +1>(db, N, t, active, twNdd);
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, qq = idx & (Q - 1);
-    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * (N + 1) + n];
+    if (col0 + qq < Lc) out[(size_t)n * Lc + col0 + qq] = sm[qq * FB(N) + n];
   }
 }
 
@@ -1013,7 +1023,7 @@ __global__ void __launch_bounds__(256)
   const int RB = blockDim.x / TPT;
   const int row = blockIdx.x * RB + qq;
   const bool active = row < N;
-  ddc* buf = sm + qq * (L + 1);
+  ddc* buf = sm + qq * FB(L);
   if (active) {
     const ddc* sr = q + (size_t)row * L;
 #pragma unroll
@@ -1275,7 +1285,7 @@ cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scal
   if (RB < 1) RB = 1;
   while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
-  const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
+  const size_t sm = (size_t)RB * FB(L) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_r2c<T, E>, sm);
   if (e != cudaSuccess) return e;
   k_row_r2c<T, E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
@@ -1290,10 +1300,10 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   const int Lc = M / 2, TPT = N / E;
   int Q = MaxThreads<T>::value / TPT;
   if (Q < 1) Q = 1;
-  while (Q > 1 && (size_t)Q * (N + 1) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
+  while (Q > 1 && (size_t)Q * FB(N) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
   while (Q > 2 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)Q * (N + 1) * sizeof(C2<T>);
+  const size_t sm = (size_t)Q * FB(N) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
@@ -1312,7 +1322,7 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   if (RB < 1) RB = 1;
   while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
-  const size_t sm = (size_t)RB * (L + 1) * sizeof(C2<T>);
+  const size_t sm = (size_t)RB * FB(L) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_c2r<T, E, MODE>, sm);
   if (e != cudaSuccess) return e;
   k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
@@ -1358,7 +1368,7 @@ cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2,
   if (Q < 1) Q = 1;
   if (Q > 4) Q = 4;
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)3 * Q * (N + 1) * sizeof(C2<T>);
+  const size_t sm = (size_t)3 * Q * FB(N) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_col_matvec_par<T, E>, sm);
   if (e != cudaSuccess) return e;
   k_col_matvec_par<T, E><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
@@ -1427,7 +1437,7 @@ cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
   int RB = 1;
   while (RB * 2 * 5 * TPT <= OTGB_PAR_THREADS && RB < 8) RB *= 2;
   if (RB > N) RB = N;
-  const size_t sm = (size_t)5 * RB * (L + 1) * sizeof(C2<T>);
+  const size_t sm = (size_t)5 * RB * FB(L) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_row_combine_par<T, E>, sm);
   if (e != cudaSuccess) return e;
   k_row_combine_par<T, E><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
@@ -1503,7 +1513,7 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
   if (Q < 1) Q = 1;
   while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)Q * (N + 1) * sizeof(double2);
+  const size_t sm = (size_t)Q * FB(N) * sizeof(double2);
   cudaError_t e = set_smem(k_col_lbarinv_mixed<E>, sm);
   if (e != cudaSuccess) return e;
   k_col_lbarinv_mixed<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
@@ -1519,10 +1529,10 @@ cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
   const int Lc = M / 2, TPT = N / E;
   int Q = 256 / TPT;
   if (Q < 1) Q = 1;
-  while (Q > 1 && (size_t)Q * (N + 1) * sizeof(ddc) > 160 * 1024) Q /= 2;
+  while (Q > 1 && (size_t)Q * FB(N) * sizeof(ddc) > 160 * 1024) Q /= 2;
   while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)Q * (N + 1) * sizeof(ddc);
+  const size_t sm = (size_t)Q * FB(N) * sizeof(ddc);
   cudaError_t e = set_smem(k_col_lbarinv_dd<E>, sm);
   if (e != cudaSuccess) return e;
   k_col_lbarinv_dd<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
@@ -1538,9 +1548,9 @@ cudaError_t row_c2r_update_dd_E(const ddc* q, const double* u_in, double* u_out,
   const int L = M / 2, TPT = L / E;
   int RB = 256 / TPT;
   if (RB < 1) RB = 1;
-  while (RB > 1 && (size_t)RB * (L + 1) * sizeof(ddc) > 160 * 1024) RB /= 2;
+  while (RB > 1 && (size_t)RB * FB(L) * sizeof(ddc) > 160 * 1024) RB /= 2;
   while (RB > 1 && (N + RB - 1) / RB < 2 * 152) RB /= 2;
-  const size_t sm = (size_t)RB * (L + 1) * sizeof(ddc);
+  const size_t sm = (size_t)RB * FB(L) * sizeof(ddc);
   cudaError_t e = set_smem(k_row_c2r_update_dd<E>, sm);
   if (e != cudaSuccess) return e;
   k_row_c2r_update_dd<E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
