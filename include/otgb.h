@@ -99,6 +99,7 @@ extern "C" {
                                    1 = concurrent transforms (r: same as 0), 2 = warp-
                                    synchronous radix-32, 3 = generic with 4 elements per
                                    thread (where the size allows, else a variant that does);
+                                   + 64: the generic column pass with 4 columns per block;
                                    turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */

@@ -488,11 +488,13 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
     case OT_OPT_FFT_VARIANT: {
       // r2c + 4 col + 16 combine, each 0 generic, 1 concurrent (r2c: same as 0), 2 warp,
       // 3 generic with 4 elements per thread
-      if (v < 0 || v > 63 || v != (double)(int)v) return OT_EINVAL;
-      const int k = (int)v;
+      // + 64: the generic column pass with 4 columns per block
+      if (v < 0 || v > 127 || v != (double)(int)v) return OT_EINVAL;
+      const int k = (int)v & 63;
       p->tb32.var_r2c = k % 4 == 1 ? VAR_GENERIC : k % 4;
       p->tb32.var_col = (k / 4) % 4;
       p->tb32.var_comb = k / 16;
+      p->tb32.col_q = ((int)v & 64) ? 4 : 0;
       p->autotune = 0;
       p->tuned = 1;
       free_graph(p);
@@ -1137,6 +1139,7 @@ static int run_autotune(ot_plan* p) {
         p->tb32.var_r2c = e[2];
         p->tb32.var_col = e[3];
         p->tb32.var_comb = e[4];
+        p->tb32.col_q = e[5];
         p->tuned = 1;
         return OT_OK;
       }
@@ -1196,12 +1199,19 @@ static int run_autotune(ot_plan* p) {
     }
     *vars[cls] = best;
   }
+  // the generic column pass: also try 4 columns per block (32-byte runs per row)
+  tb.col_q = 0;
+  if (tb.var_col == VAR_GENERIC || tb.var_col == VAR_E4) {
+    const float t0 = timed(1);
+    tb.col_q = 4;
+    if (timed(1) >= t0) tb.col_q = 0;
+  }
   cudaGetLastError();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   p->tuned = 1;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb});
+  g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb, tb.col_q});
   return OT_OK;
 }
 

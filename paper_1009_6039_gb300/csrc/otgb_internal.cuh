@@ -107,6 +107,8 @@ struct SpecTables {
   // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32,
   // 3 generic with 4 elements per thread (radix 4, twice the threads; power-of-two lengths)
   int var_r2c = -1, var_col = -1, var_comb = -1;
+  // generic column matvec pass: columns per block (0: the default heuristic)
+  int col_q = 0;
 };
 enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2, VAR_E4 = 3 };
 

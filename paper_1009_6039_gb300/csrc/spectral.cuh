@@ -1302,6 +1302,13 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   if (Q < 1) Q = 1;
   while (Q > 1 && (size_t)Q * FB(N) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
   while (Q > 2 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
+  if (sizeof(T) == 4 && MODE == COL_MATVEC && tb.col_q > 0) {
+    // tuned: more columns per block make the strided column accesses longer runs
+    Q = tb.col_q;
+    while (Q > 1 && (Q * TPT > MaxThreads<T>::value ||
+                     (size_t)Q * FB(N) * sizeof(C2<T>) > 160 * 1024))
+      Q /= 2;
+  }
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * FB(N) * sizeof(C2<T>);
   cudaError_t e = set_smem(k_col<T, E, MODE>, sm);

@@ -147,7 +147,7 @@ def test_operator_and_lbar_inverse(ot, N, M, prec, symbols):
 
 @pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
-                                     3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1])
+                                     3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
     f = I.blob_density(N, M, 23)
