@@ -152,6 +152,88 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
   __syncthreads();
 }
 
+// NB independent transforms of the same length interleaved in the same threads: each stage
+// loads a twiddle once for all NB buffers, and the NB butterflies give the scheduler
+// independent work (the passes are latency-bound at the sizes of interest).
+template <typename T, int E, int R, int SIGN, int NB>
+__device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], int L, int Ns,
+                                                     int t, bool active,
+                                                     const C2<T>* __restrict__ tw, bool pin,
+                                                     bool pout) {
+  const int TPT = L / E;
+  const int LR = L / R;
+  C2<T> v[NB][E];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int src = spad(j + r * LR, pin);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q][b * R + r] = bufs[q][src];
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int tstep = L / (Ns * R);
+    const int a = __ffs(Ns) - 1;
+    const bool pow2 = (Ns >> a) == 1;
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+      const int qd = pow2 ? (j >> a) : ((j >> a) / 3);
+      const int k = j - qd * Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = tw[k * r * tstep];
+        if (SIGN > 0) w.y = -w.y;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q][b * R + r] = cmul<T>(v[q][b * R + r], w);
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) Bfly<T, R, SIGN>::run(&v[q][b * R]);
+      const int d = qd * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int dst = spad(d + r * Ns, pout);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) bufs[q][dst] = v[q][b * R + r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int E, int SIGN, int NB>
+__device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, int t,
+                                               bool active, const C2<T>* __restrict__ tw) {
+  int Ns = 1;
+  int rem = L;
+  if (E % 3 == 0) {
+    stockham_stage_multi<T, E, 3, SIGN, NB>(bufs, L, Ns, t, active, tw, false, rem / 3 > 1);
+    Ns *= 3;
+    rem /= 3;
+  }
+  while (rem > 1) {
+    const bool pin = Ns > 1;
+    if (E % 8 == 0 && rem % 8 == 0) {
+      stockham_stage_multi<T, E, 8, SIGN, NB>(bufs, L, Ns, t, active, tw, pin, rem / 8 > 1);
+      Ns *= 8;
+      rem /= 8;
+    } else if (rem % 4 == 0) {
+      stockham_stage_multi<T, E, 4, SIGN, NB>(bufs, L, Ns, t, active, tw, pin, rem / 4 > 1);
+      Ns *= 4;
+      rem /= 4;
+    } else {
+      stockham_stage_multi<T, E, 2, SIGN, NB>(bufs, L, Ns, t, active, tw, pin, rem / 2 > 1);
+      Ns *= 2;
+      rem /= 2;
+    }
+  }
+}
+
 // Full unnormalised transform X_k = sum_n x_n exp(SIGN 2 pi i k n / L), in place in buf.
 // Radix sequence: [3,] then 8s (E = 8) or 4s (E = 12), then the remaining 4 or 2.
 template <typename T, int E, int SIGN>
@@ -448,26 +530,35 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __res
 // Column transforms with the spectral multiplies of Strain's method.
 // ---------------------------------------------------------------------------------------
 // Q (columns per block) is a power of two
+// columns col0 .. col0 + Q - 1 of an N x Lc spectrum <-> shared memory, column q at
+// sm + q * cs
 template <typename T, int E>
 __device__ __forceinline__ void col_load(const C2<T>* __restrict__ src, C2<T>* sm, int N,
-                                         int Lc, int Q, int col0) {
+                                         int Lc, int Q, int col0, int cs) {
   const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
-    if (col < Lc) sm[q * FB(N) + n] = src[(size_t)n * Lc + col];
+    if (col < Lc) sm[q * cs + n] = src[(size_t)n * Lc + col];
   }
 }
 
 template <typename T, int E>
 __device__ __forceinline__ void col_store(C2<T>* __restrict__ dst, const C2<T>* sm, int N,
-                                          int Lc, int Q, int col0) {
+                                          int Lc, int Q, int col0, int cs) {
   const int lq = __ffs(Q) - 1;
   for (int idx = threadIdx.x; idx < Q * N; idx += blockDim.x) {
     const int n = idx >> lq, q = idx & (Q - 1);
     const int col = col0 + q;
-    if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * FB(N) + n];
+    if (col < Lc) dst[(size_t)n * Lc + col] = sm[q * cs + n];
   }
+}
+
+// the FP32 matvec column pass with 4 elements per thread runs its three inverse transforms
+// interleaved (3 buffers per column); with 8 or 12 the registers would spill
+template <typename T, int E, int MODE>
+__host__ __device__ constexpr int col_nbuf() {
+  return (MODE == COL_MATVEC && sizeof(T) == 4 && E == 4) ? 3 : 1;
 }
 
 template <typename T, int E, int MODE>
@@ -486,18 +577,20 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
   const int col0 = blockIdx.x * Q;
   const int col = col0 + q;
   const bool active = (q < Q) && (col < Lc);
-  C2<T>* buf = sm + q * FB(N);
+  constexpr int NBUF = col_nbuf<T, E, MODE>();
+  const int cs = NBUF * FB(N);
+  C2<T>* buf = sm + q * cs;
 
-  col_load<T, E>(spec, sm, N, Lc, Q, col0);
+  col_load<T, E>(spec, sm, N, Lc, Q, col0, cs);
   __syncthreads();
   if (MODE == COL_INV) {
     fft_smem<T, E, +1>(buf, N, t, active, twN);
-    col_store<T, E>(out0, sm, N, Lc, Q, col0);
+    col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
     return;
   }
   fft_smem<T, E, -1>(buf, N, t, active, twN);
   if (MODE == COL_FWD) {
-    col_store<T, E>(out0, sm, N, Lc, Q, col0);
+    col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
     return;
   }
   T ab[5];
@@ -557,6 +650,28 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
     }
   }
   __syncthreads();
+  if (NBUF == 3) {
+    // Q0 = S (Nyquist channel premultiplied), Q1 = (i s1(k2)) S, Q2 = s2(k2) S into the
+    // three buffers, then the three inverse transforms interleaved
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = t + e * TPT;
+        const C2<T> v = s[e];
+        const C2<T> sy = symy[k];
+        buf[k] = col == 0 ? s0[e] : v;
+        buf[FB(N) + k] = mk2<T>(-sy.x * v.y, sy.x * v.x);
+        buf[2 * FB(N) + k] = cscale<T>(v, sy.y);
+      }
+    }
+    __syncthreads();
+    C2<T>* const bufs[3] = {buf, buf + FB(N), buf + 2 * FB(N)};
+    fft_smem_multi<T, E, +1, 3>(bufs, N, t, active, twN);
+    col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
+    col_store<T, E>(out1, sm + FB(N), N, Lc, Q, col0, cs);
+    col_store<T, E>(out2, sm + 2 * FB(N), N, Lc, Q, col0, cs);
+    return;
+  }
   const int nout = (MODE == COL_MATVEC) ? 3 : 1;
 #pragma unroll 1
   for (int p = 0; p < nout; ++p) {
@@ -576,7 +691,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
     }
     __syncthreads();
     fft_smem<T, E, +1>(buf, N, t, active, twN);
-    col_store<T, E>(p == 0 ? out0 : (p == 1 ? out1 : out2), sm, N, Lc, Q, col0);
+    col_store<T, E>(p == 0 ? out0 : (p == 1 ? out1 : out2), sm, N, Lc, Q, col0, cs);
     __syncthreads();
   }
 }
@@ -601,6 +716,12 @@ __device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int kind,
   const C2<T> sx = symx[k];
   if (kind == 1) return mk2<T>(-sx.x * X.y, sx.x * X.x);
   return cscale<T>(X, sx.y);
+}
+
+// the FP32 row combine with 4 elements per thread runs its five transforms interleaved
+template <typename T, int E, int MODE>
+__host__ __device__ constexpr int row_nbuf() {
+  return (MODE == ROWINV_COMBINE && sizeof(T) == 4 && E == 4) ? 5 : 1;
 }
 
 // complex-to-real pre-processing on a packed row in buf (in place):
@@ -652,11 +773,55 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
   const int RB = blockDim.x / TPT;
   const int row = blockIdx.x * RB + q;
   const bool active = row < N;
-  C2<T>* buf = sm + q * FB(L);
+  constexpr int NBUF = row_nbuf<T, E, MODE>();
+  C2<T>* buf = sm + q * NBUF * FB(L);
   const size_t P = (size_t)N * M;
   C2<T> acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = mk2<T>((T)0, (T)0);
+
+  if (NBUF == 5) {
+    // the five terms' transforms interleaved: d_xx Q0, d_x Q0, d_x Q1, Q1, Q2 in buffers 0..4
+    if (active) {
+      const size_t o = (size_t)row * L;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int k = t + e * TPT;
+        const C2<T> x0 = q0[o + k], x1 = q1[o + k];
+        buf[k] = row_symbol_apply<T>(x0, k, 2, symx);
+        buf[FB(L) + k] = row_symbol_apply<T>(x0, k, 1, symx);
+        buf[2 * FB(L) + k] = row_symbol_apply<T>(x1, k, 1, symx);
+        buf[3 * FB(L) + k] = x1;
+        buf[4 * FB(L) + k] = q2[o + k];
+      }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int b = 0; b < 5; ++b) c2r_preprocess<T>(buf + b * FB(L), L, t, TPT, active, twM);
+    C2<T>* const bufs[5] = {buf, buf + FB(L), buf + 2 * FB(L), buf + 3 * FB(L),
+                            buf + 4 * FB(L)};
+    fft_smem_multi<T, E, +1, 5>(bufs, L, t, active, twL);
+    if (!active) return;
+    const size_t o = (size_t)row * M;
+    const C2<T>* c0 = reinterpret_cast<const C2<T>*>(coef + o);
+    const C2<T>* c1 = reinterpret_cast<const C2<T>*>(coef + P + o);
+    const C2<T>* c2 = reinterpret_cast<const C2<T>*>(coef + 2 * P + o);
+    const C2<T>* c3 = reinterpret_cast<const C2<T>*>(coef + 3 * P + o);
+    const C2<T>* c4 = reinterpret_cast<const C2<T>*>(coef + 4 * P + o);
+    C2<T>* ov = reinterpret_cast<C2<T>*>(out + o);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int n = t + e * TPT;
+      const C2<T> y0 = buf[n], y1 = buf[FB(L) + n], y2 = buf[2 * FB(L) + n],
+                  y3 = buf[3 * FB(L) + n], y4 = buf[4 * FB(L) + n];
+      const C2<T> a11 = c0[n], a12 = c1[n], a22 = c2[n], b1 = c3[n], b2 = c4[n];
+      C2<T> r;
+      r.x = a11.x * y0.x + b1.x * y1.x + (T)2 * a12.x * y2.x + b2.x * y3.x + a22.x * y4.x;
+      r.y = a11.y * y0.y + b1.y * y1.y + (T)2 * a12.y * y2.y + b2.y * y3.y + a22.y * y4.y;
+      ov[n] = r;
+    }
+    return;
+  }
 
   const int nterm = (MODE == ROWINV_COMBINE) ? 5 : 1;
 #pragma unroll 1
@@ -1298,19 +1463,18 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
                   const SpecTables& tb, const DevScalars* sc, const int* skip,
                   cudaStream_t st) {
   const int Lc = M / 2, TPT = N / E;
+  const size_t colb = (size_t)col_nbuf<T, E, MODE>() * FB(N) * sizeof(C2<T>);
   int Q = MaxThreads<T>::value / TPT;
   if (Q < 1) Q = 1;
-  while (Q > 1 && (size_t)Q * FB(N) * sizeof(C2<T>) > 160 * 1024) Q /= 2;
+  while (Q > 1 && (size_t)Q * colb > 160 * 1024) Q /= 2;
   while (Q > 2 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (sizeof(T) == 4 && MODE == COL_MATVEC && tb.col_q > 0) {
     // tuned: more columns per block make the strided column accesses longer runs
     Q = tb.col_q;
-    while (Q > 1 && (Q * TPT > MaxThreads<T>::value ||
-                     (size_t)Q * FB(N) * sizeof(C2<T>) > 160 * 1024))
-      Q /= 2;
+    while (Q > 1 && (Q * TPT > MaxThreads<T>::value || (size_t)Q * colb > 160 * 1024)) Q /= 2;
   }
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)Q * FB(N) * sizeof(C2<T>);
+  const size_t sm = (size_t)Q * colb;
   cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
@@ -1325,11 +1489,13 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
                       int M, const SpecTables& tb, const int* skip, cudaStream_t st,
                       const DevScalars* sc) {
   const int L = M / 2, TPT = L / E;
+  const size_t rowb = (size_t)row_nbuf<T, E, MODE>() * FB(L) * sizeof(C2<T>);
   int RB = MaxThreads<T>::value / TPT;
   if (RB < 1) RB = 1;
+  while (RB > 1 && RB * rowb > 160 * 1024) RB /= 2;
   while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
-  const size_t sm = (size_t)RB * FB(L) * sizeof(C2<T>);
+  const size_t sm = (size_t)RB * rowb;
   cudaError_t e = set_smem(k_row_c2r<T, E, MODE>, sm);
   if (e != cudaSuccess) return e;
   k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
