@@ -66,6 +66,22 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """Maximum of a per-rank float over the process group (identity on one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank):
+    """Seed base of the pair a rank solves (replicas: every rank its own pair)."""
+    return SEED + 17 * rank
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -278,7 +294,7 @@ def run_ours(args):
 
     N = M = args.size
     P = N * M
-    f, g = I.noise_blob_pair(N, M, s=SEED + 17 * rank)
+    f, g = I.noise_blob_pair(N, M, s=rank_seed(rank))
     fd = torch.from_numpy(f).cuda()
     gd = torch.from_numpy(g).cuda()
     phi = torch.zeros_like(fd)
@@ -349,11 +365,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof, _ = plan.profile()
     plan.set(profile=0)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     value = world * args.steps / (ms / 1000.0)
     ok = all(s["status"] == 0 and s["res_inf"] < TOL for s in stats)
     if args.kernels_only:
@@ -378,11 +390,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         rc, st_h = plan.solve_host(fh, gh, ph)
         e2e_ms += (time.perf_counter() - t0) * 1000.0
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_value = world * e2e_steps / (e2e_ms / 1000.0)
     phi_mixed = phi.clone()
 

@@ -93,6 +93,11 @@ extern "C" {
                                    with twice tau, up to this many times -- the remedy of
                                    Sec. 3.2 / Sec. 5.3; phi and stats are those of the last
                                    attempt (ot_solve, ot_solve_batched) */
+#define OT_OPT_WS_TEST_STALL 20 /* test of the failure path: 1 makes the next
+                                   ot_ws_mlp_forward skip one tensor-core MMA group, so its
+                                   bounded mbarrier wait runs out (tens of milliseconds); the
+                                   kernel sets its error flag, frees its TMEM and returns and
+                                   the call returns OT_ECUDA; resets itself after one call */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

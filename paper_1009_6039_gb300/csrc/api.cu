@@ -45,6 +45,7 @@ struct ot_plan {
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
   int tau_retry = 0;  // OT_OPT_TAU_RETRY: re-solves with doubled tau after a divergence
+  int ws_stall = 0;   // OT_OPT_WS_TEST_STALL: the next ot_ws_mlp_forward stalls (test hook)
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
   float2 *fdd = nullptr, *cdd = nullptr;
@@ -175,6 +176,10 @@ static thread_local char g_last_error[160] = "";
 static void record_error(cudaError_t e, int line) {
   snprintf(g_last_error, sizeof(g_last_error), "api.cu:%d: %s (%s)", line,
            cudaGetErrorName(e), cudaGetErrorString(e));
+}
+// a failure a kernel reported through its error flag (the CUDA context stays usable)
+static void record_kernel_error(const char* what, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "api.cu:%d: %s", line, what);
 }
 
 extern "C" const char* ot_last_error(void) { return g_last_error; }
@@ -500,6 +505,10 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       free_graph(p);
       return OT_OK;
     }
+    case OT_OPT_WS_TEST_STALL:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      p->ws_stall = (int)v;
+      return OT_OK;
     case OT_OPT_TAU_RETRY:
       if (!(v >= 0 && v <= 8) || v != (double)(int)v) return OT_EINVAL;
       p->tau_retry = (int)v;
@@ -1181,31 +1190,34 @@ static int run_autotune(ot_plan* p) {
     cudaEventElapsedTime(&ms, a, b);
     return ms;
   };
+  tb.col_q = 0;
   int* vars[3] = {&tb.var_r2c, &tb.var_col, &tb.var_comb};
   const int ncand[3] = {3, 4, 4};
   const int cand[3][4] = {{VAR_GENERIC, VAR_WARP, VAR_E4, VAR_E4},
                           {VAR_GENERIC, VAR_PAR, VAR_WARP, VAR_E4},
                           {VAR_GENERIC, VAR_PAR, VAR_WARP, VAR_E4}};
   for (int cls = 0; cls < 3; ++cls) {
-    int best = VAR_GENERIC;
+    int best = VAR_GENERIC, bestq = 0;
     float tbest = 1e30f;
     for (int k = 0; k < ncand[cls]; ++k) {
       *vars[cls] = cand[cls][k];
-      const float tms = timed(cls);
-      if (tms < tbest) {
-        tbest = tms;
-        best = cand[cls][k];
+      // the column variants with per-block column counts (0 = heuristic)
+      const bool qv = cls == 1 && (cand[cls][k] == VAR_GENERIC || cand[cls][k] == VAR_E4);
+      for (int qc : {0, 1, 4}) {
+        if (qc && !qv) break;
+        tb.col_q = qc;
+        const float tms = timed(cls);
+        if (tms < tbest) {
+          tbest = tms;
+          best = cand[cls][k];
+          bestq = qc;
+        }
       }
     }
     *vars[cls] = best;
+    if (cls == 1) tb.col_q = bestq;
   }
-  // the generic column pass: also try 4 columns per block (32-byte runs per row)
-  tb.col_q = 0;
-  if (tb.var_col == VAR_GENERIC || tb.var_col == VAR_E4) {
-    const float t0 = timed(1);
-    tb.col_q = 4;
-    if (timed(1) >= t0) tb.col_q = 0;
-  }
+
   cudaGetLastError();
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1746,13 +1758,19 @@ extern "C" int ot_ws_mlp_forward(ot_plan* p, const float* X, int64_t rows, float
     return OT_EINVAL;
   CK(cudaSetDevice(p->device));
   CK(cudaMemsetAsync(&p->sc->ws_err, 0, sizeof(int), p->stream));
+  const int stall = p->ws_stall;
+  p->ws_stall = 0;
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
          launch_ws_mlp(p->ws_wpack, p->ws_params, X, rows, out, &p->sc->ws_err, p->sms,
-                       p->stream));
+                       p->stream, stall));
   int err = 0;
   CK(cudaMemcpyAsync(&err, &p->sc->ws_err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
   CK(cudaStreamSynchronize(p->stream));
-  return err ? OT_ECUDA : OT_OK;
+  if (err) {
+    record_kernel_error("tensor-core network: bounded mbarrier wait ran out", __LINE__);
+    return OT_ECUDA;
+  }
+  return OT_OK;
 }
 
 extern "C" int ot_ws_poisson(ot_plan* p, const double* src, int32_t lowpass, double* u) {

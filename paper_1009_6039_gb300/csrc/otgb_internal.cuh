@@ -235,8 +235,10 @@ cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
 size_t ws_packed_bytes();
 cudaError_t launch_ws_pack(const float* params, unsigned char* wpack, cudaStream_t st);
 // BF16 tensor-core forward of the network: out[r] = MLP(X[r, :]); *err set on a timeout
+// (stall != 0 makes one wait run out on purpose: a test of that path)
 cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const float* X,
-                          long rows, float* out, int* err, int sms, cudaStream_t st);
+                          long rows, float* out, int* err, int sms, cudaStream_t st,
+                          int stall = 0);
 // gradient of the mean squared error over the rows idx[0..B) of (X, t) into tb.grad
 cudaError_t launch_ws_grad(const float* params, const float* X, const float* t,
                            const long long* idx, int B, WsTrainBuffers& tb, cudaStream_t st);

@@ -385,14 +385,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// bounded wait for the mbarrier phase with parity `par` (about a million polls, far more
-// than an MMA group takes); false if it gave up
+// bounded wait for the mbarrier phase with parity `par`: about four million non-blocking
+// polls (tens of milliseconds; an MMA group takes microseconds); false if it gave up
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par) {
-  for (long it = 0; it < (1l << 20); ++it) {
+  for (long it = 0; it < (1l << 22); ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(ok)
         : "r"(bar), "r"(par)
@@ -461,10 +461,12 @@ __device__ __forceinline__ void readout_hidden(uint32_t trow, const float* bias,
   }
 }
 
+// stall != 0 (a test of the failure path): the first tile's first MMA group is not issued,
+// so the wait for it runs out; the kernel then sets *err, frees its TMEM and returns
 __global__ void __launch_bounds__(128, 1)
     k_ws_mlp_tc(const unsigned char* __restrict__ wpack, const float* __restrict__ params,
                 const float* __restrict__ X, long rows, float* __restrict__ out,
-                int* __restrict__ err) {
+                int* __restrict__ err, int stall) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* sm =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(128, 1)
     fence_async_smem();
     fence_before();
     __syncthreads();
-    if (r == 0) {
+    if (r == 0 && !(stall && tile == blockIdx.x)) {
       fence_after();
       mma_bf16(tmem, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
       mma_commit(bar);
@@ -583,7 +585,8 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (!ok) {
     if (err) atomicExch(err, 1);
-    // let an MMA still in flight finish before its TMEM goes away (bounded)
+    // let an MMA still in flight finish before its TMEM goes away (bounded; with `stall`
+    // nothing is in flight and this wait runs out too)
     bar_wait(bar, phase);
   }
   fence_before();
@@ -857,7 +860,8 @@ cudaError_t launch_ws_pack(const float* params, unsigned char* wpack, cudaStream
 }
 
 cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const float* X,
-                          long rows, float* out, int* err, int sms, cudaStream_t st) {
+                          long rows, float* out, int* err, int sms, cudaStream_t st,
+                          int stall) {
   if (rows <= 0) return cudaSuccess;
   static bool attr_set[64] = {false};
   int dev = 0;
@@ -871,7 +875,7 @@ cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const
   }
   const long tiles = (rows + 127) / 128;
   const long grid = tiles < 2L * sms ? tiles : 2L * sms;
-  k_ws_mlp_tc<<<(unsigned)grid, 128, SM_TOTAL, st>>>(wpack, params, X, rows, out, err);
+  k_ws_mlp_tc<<<(unsigned)grid, 128, SM_TOTAL, st>>>(wpack, params, X, rows, out, err, stall);
   return cudaGetLastError();
 }
 
