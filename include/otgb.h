@@ -150,6 +150,11 @@ int ot_plan_create(ot_plan** out, int32_t N, int32_t M, double tau, double tol);
  * workspace.  Returns OT_EINVAL for an unknown key or an out-of-range value. */
 int ot_plan_set_option(ot_plan* plan, int32_t key, double value);
 
+/* Read an OT_OPT_* option into *value.  OT_OPT_FFT_VARIANT reads the FP32 transform
+ * kernels in use (the autotuner's choice after the first mixed solve) in the encoding that
+ * ot_plan_set_option takes, or -1 while none is chosen.  OT_EINVAL for an unknown key. */
+int ot_plan_get_option(ot_plan* plan, int32_t key, double* value);
+
 /* Run the plan on a cudaStream_t (NULL = legacy default stream). */
 int ot_plan_set_stream(ot_plan* plan, void* cuda_stream);
 

@@ -26,8 +26,8 @@ PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lba
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
 
-EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_set_stream", "ot_solve",
-           "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
+EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_plan_set_stream",
+           "ot_solve", "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
            "ot_prefilter", "ot_eval_residual", "ot_apply_operator", "ot_apply_lbar_inverse",
            "ot_fft_forward", "ot_fft_inverse", "ot_plan_get_profile",
            "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc",
@@ -67,6 +67,7 @@ def _load():
     sig = {
         "ot_plan_create": ([ctypes.POINTER(vp), i32, i32, d, d], ctypes.c_int),
         "ot_plan_set_option": ([vp, i32, d], ctypes.c_int),
+        "ot_plan_get_option": ([vp, i32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "ot_plan_set_stream": ([vp, vp], ctypes.c_int),
         "ot_solve": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
         "ot_solve_host": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
@@ -118,6 +119,10 @@ def ot_plan_create(N, M, tau, tol):
 
 def ot_plan_set_option(plan, key, value):
     return _lib.ot_plan_set_option(plan, int(key), float(value))
+
+
+def ot_plan_get_option(plan, key, value_ptr):
+    return _lib.ot_plan_get_option(plan, int(key), value_ptr)
 
 
 def ot_plan_set_stream(plan, stream_ptr):
@@ -368,6 +373,11 @@ class Plan:
                 v = {"fp64": 0, "mixed": 1}[v]
             _check(ot_plan_set_option(self.h, self._keys[k], float(v)), "set " + k)
         return self
+
+    def get(self, name):
+        v = ctypes.c_double()
+        _check(ot_plan_get_option(self.h, self._keys[name], ctypes.byref(v)), "get " + name)
+        return v.value
 
     def solve(self, f, g, phi, raise_on=(OT_EINVAL, OT_ECUDA, OT_ENOMEM)):
         st = ot_stats()

@@ -538,6 +538,43 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
   return OT_EINVAL;
 }
 
+extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
+  if (!p || !v) return OT_EINVAL;
+  switch (key) {
+    case OT_OPT_RESTART: *v = p->m; return OT_OK;
+    case OT_OPT_ETA: *v = p->eta; return OT_OK;
+    case OT_OPT_MAX_NEWTON: *v = p->max_newton; return OT_OK;
+    case OT_OPT_MAX_RESTARTS: *v = p->max_restarts; return OT_OK;
+    case OT_OPT_PRECISION: *v = p->precision; return OT_OK;
+    case OT_OPT_SAFEGUARD: *v = p->safeguard; return OT_OK;
+    case OT_OPT_TRANSLATE: *v = p->translate; return OT_OK;
+    case OT_OPT_WARM_START: *v = p->warm_start; return OT_OK;
+    case OT_OPT_TAU: *v = p->tau; return OT_OK;
+    case OT_OPT_TOL: *v = p->tol; return OT_OK;
+    case OT_OPT_PROFILE: *v = p->profile; return OT_OK;
+    case OT_OPT_GRAPH: *v = p->use_graph; return OT_OK;
+    case OT_OPT_REORTH: *v = p->reorth; return OT_OK;
+    case OT_OPT_THETA_FP64: *v = p->theta64; return OT_OK;
+    case OT_OPT_AUTOTUNE: *v = p->autotune; return OT_OK;
+    case OT_OPT_SYMBOLS: *v = p->symbols; return OT_OK;
+    case OT_OPT_FORCING: *v = p->forcing; return OT_OK;
+    case OT_OPT_TAU_RETRY: *v = p->tau_retry; return OT_OK;
+    case OT_OPT_WS_TEST_STALL: *v = p->ws_stall; return OT_OK;
+    case OT_OPT_FFT_VARIANT: {
+      // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
+      // autotuner has run (or in FP64 mode, which has one variant)
+      const SpecTables& tb = p->tb32;
+      if (!p->precision || !p->tuned || tb.var_r2c < 0 || tb.var_col < 0 || tb.var_comb < 0) {
+        *v = -1;
+        return OT_OK;
+      }
+      *v = tb.var_r2c + 4 * tb.var_col + 16 * tb.var_comb + (tb.col_q == 4 ? 64 : 0);
+      return OT_OK;
+    }
+  }
+  return OT_EINVAL;
+}
+
 extern "C" int ot_plan_get_profile(ot_plan* p, double* ms, int64_t* launches, int32_t n,
                                    int64_t* total_launches) {
   if (!p || n < 0) return OT_EINVAL;

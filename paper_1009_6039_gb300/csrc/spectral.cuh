@@ -14,6 +14,9 @@
 //   row_c2r COMBINE  five row inverse transforms (d_xx Q0, d_x Q0, d_x Q1, Q1, Q2) weighted
 //                    by a11, b1, 2 a12, b2, a22 and summed: w = L Lbar^{-1} sigma.
 #pragma once
+#include <mutex>
+#include <vector>
+
 #include "otgb_internal.cuh"
 
 namespace otgb {
@@ -1427,19 +1430,38 @@ __global__ void __launch_bounds__(320)
 // ---------------------------------------------------------------------------------------
 inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
+// The attribute belongs to the kernel (and device), so the record of sizes already set is
+// keyed by the kernel's address: kernels that share a signature must not share it.
+inline cudaError_t set_smem_fn(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  struct Done {
+    const void* fn;
+    int dev;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Done> done;
+  std::lock_guard<std::mutex> lock(mu);
+  Done* rec = nullptr;
+  for (auto& d : done)
+    if (d.fn == fn && d.dev == dev) rec = &d;
+  if (rec && rec->bytes >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  if (rec)
+    rec->bytes = bytes;
+  else
+    done.push_back({fn, dev, bytes});
+  return cudaSuccess;
+}
+
 template <typename K>
 inline cudaError_t set_smem(K kernel, size_t bytes) {
-  // the attribute is per kernel and per device; raise it to the largest size seen
-  static int done_bytes[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (bytes > 48 * 1024 && (dev >= 64 || (int)bytes > done_bytes[dev])) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e == cudaSuccess && dev < 64) done_bytes[dev] = (int)bytes;
-    return e;
-  }
-  return cudaSuccess;
+  return set_smem_fn(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 template <typename T, int E>

@@ -145,11 +145,14 @@ def test_operator_and_lbar_inverse(ot, N, M, prec, symbols):
     p.close()
 
 
-@pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512)])
+@pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512),
+                                 (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
                                      3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
+    # (at 1024^2 the concurrent column pass, launched first, needs more shared memory than
+    # the warp column pass, which has the same signature: each kernel's own limit is raised)
     f = I.blob_density(N, M, 23)
     g = I.blob_density(N, M, 24)
     u = smooth_field(N, M, amp=2e-3)
@@ -172,6 +175,10 @@ def test_autotuned_solve_matches_fixed_variant(ot):
         p = plan(ot, 256, 256, "mixed", tau=4.0, tol=1e-8, eta=1e-1, max_newton=400, **kw)
         phi = dev(np.zeros((256, 256)))
         rc, st = p.solve(dev(f), dev(g), phi)
+        # the variants in use read back in the encoding the option takes
+        v = p.get("fft_variant")
+        assert v == 0 if "fft_variant" in kw else 0 <= v <= 127
+        assert p.get("tau") == 4.0 and p.get("precision") == 1
         p.close()
         assert rc == 0 and st["status"] == 0
         out.append(phi.cpu().numpy())
