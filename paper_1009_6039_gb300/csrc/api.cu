@@ -886,9 +886,34 @@ static int alloc_ws(ot_plan* p) {
   return OT_OK;
 }
 
-// u = P(src): FD Poisson solve in FP64 (row R2C, column pass dividing by the stencil
-// Laplacian's eigenvalues, row C2R)
+// u = u_add + P(src32) in the mixed mode: FP32 forward transforms (an error relative to the
+// source in every coefficient, which P turns into a smooth error), the division and the
+// inverse transforms in double-float (FP32 round-off there would be grid-scale noise in u,
+// which the second differences of the features and of the residual amplify by ~M^2).
+// u_add may be null.
+static int run_ws_poisson32(ot_plan* p, const float* src32, double* u, const double* u_add,
+                            bool lp) {
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_row_r2c<float>(src32, 0, nullptr, nullptr, (C2<float>*)p->spec, p->N, p->M,
+                               p->tb32, nullptr, p->stream));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_col_lbarinv_dd((const float2*)p->spec, (ddc*)p->q64, p->N, p->M, p->tb32,
+                               p->tbdd, nullptr, p->stream, lp ? COL_POISSON_LP : COL_POISSON));
+  LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+         launch_row_c2r_update_dd((const ddc*)p->q64, u_add, u, 1.0, p->N, p->M, p->tbdd,
+                                  nullptr, p->stream));
+  return OT_OK;
+}
+
+// u = P(src), the FD Poisson solve (row R2C, column pass dividing by the stencil
+// Laplacian's eigenvalues, row C2R): FP64 transforms in the FP64 mode; the mixed mode rounds
+// src to FP32 (the learned start's sources are FP32 quantities) and takes run_ws_poisson32
 static int run_ws_poisson(ot_plan* p, const double* src, double* u, bool lp = false) {
+  if (p->precision) {
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+           launch_convert<float>(src, 1, p->ws_s, 0, (long)p->N * p->M, p->stream));
+    return run_ws_poisson32(p, p->ws_s, u, nullptr, lp);
+  }
   C2<double>* sp = (C2<double>*)(p->precision ? p->spec64 : p->spec);
   C2<double>* qq = (C2<double>*)(p->precision ? p->q64 : p->q0);
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
@@ -908,8 +933,16 @@ static int run_ws_poisson(ot_plan* p, const double* src, double* u, bool lp = fa
 static int run_ws_features(ot_plan* p) {
   RET(alloc_ws(p));
   const long P = (long)p->N * p->M;
-  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_source(p->f, p->g, p->ws_src, P, p->stream));
-  RET(run_ws_poisson(p, p->ws_src, p->ws_h));
+  if (p->precision) {
+    // mixed: the source in FP32 (in ws_s, which the network overwrites later)
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+           launch_ws_source32(p->f, p->g, p->ws_s, P, p->stream));
+    RET(run_ws_poisson32(p, p->ws_s, p->ws_h, nullptr, false));
+  } else {
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
+           launch_ws_source(p->f, p->g, p->ws_src, P, p->stream));
+    RET(run_ws_poisson(p, p->ws_src, p->ws_h));
+  }
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
          launch_convert<float>(p->c, 1, p->ws_c32, 0, P, p->stream));
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
@@ -925,9 +958,14 @@ static int run_warmstart(ot_plan* p, double* u) {
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
          launch_ws_mlp(p->ws_wpack, p->ws_params, p->ws_X, P, p->ws_s, &p->sc->ws_err, p->sms,
                        p->stream));
-  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_widen(p->ws_s, p->ws_src, P, p->stream));
-  RET(run_ws_poisson(p, p->ws_src, p->ws_tmp, true));
-  LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_sum(p->ws_h, p->ws_tmp, u, P, p->stream));
+  if (p->precision) {
+    // u = h + P(G s) straight from the network's FP32 output
+    RET(run_ws_poisson32(p, p->ws_s, u, p->ws_h, true));
+  } else {
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_widen(p->ws_s, p->ws_src, P, p->stream));
+    RET(run_ws_poisson(p, p->ws_src, p->ws_tmp, true));
+    LAUNCH(p, OT_PROF_WARMSTART, -1, 1, launch_ws_sum(p->ws_h, p->ws_tmp, u, P, p->stream));
+  }
   LAUNCH(p, OT_PROF_WARMSTART, -1, 2,
          launch_ws_admissible(u, p->N, p->M, p->partials, &p->sc->ticket[TK_WS],
                               &p->sc->ws_err, &p->sc->ws_alpha, p->stream));
@@ -1813,6 +1851,7 @@ extern "C" int ot_ws_mlp_forward(ot_plan* p, const float* X, int64_t rows, float
 extern "C" int ot_ws_poisson(ot_plan* p, const double* src, int32_t lowpass, double* u) {
   if (!p || !p->ready || !src || !u) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
+  RET(alloc_ws(p));
   RET(run_ws_poisson(p, src, u, lowpass != 0));
   CK(cudaStreamSynchronize(p->stream));
   return OT_OK;

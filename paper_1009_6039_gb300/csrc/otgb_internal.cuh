@@ -132,12 +132,16 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
 cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, int M,
                                      const SpecTables& tb32, const SpecTables& tb64,
                                      const DevScalars* sc, cudaStream_t st);
-// the same with the inverse column transform in double-float (tbdd: dd twiddle tables)
+// the same with the inverse column transform in double-float (tbdd: dd twiddle tables);
+// mode COL_POISSON / COL_POISSON_LP: the FD Poisson solve of the warm start instead (sc
+// unused)
 cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
                                   const SpecTables& tb32, const SpecTables& tbdd,
-                                  const DevScalars* sc, cudaStream_t st);
-// theta rows in double-float and the update u_out = u_in + step theta (FP64 u); with sc,
-// step and the buffer pair come from the device scalars (graph)
+                                  const DevScalars* sc, cudaStream_t st,
+                                  int mode = COL_LBARINV);
+// theta rows in double-float and the update u_out = u_in + step theta (FP64 u; u_in may be
+// null: u_out = step theta); with sc, step and the buffer pair come from the device scalars
+// (graph)
 cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
                                      double step, int N, int M, const SpecTables& tbdd,
                                      const DevScalars* sc, cudaStream_t st);
@@ -215,6 +219,9 @@ struct WsTrainBuffers {
 };
 cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
                              cudaStream_t st);
+// the same source in FP32 (input of the mixed-precision Poisson solve)
+cudaError_t launch_ws_source32(const double* f, const double* g, float* src, long P,
+                               cudaStream_t st);
 // c32: FP32 copy of the B-spline coefficients of g
 cudaError_t launch_ws_features(const double* f, const double* g, const float* c32,
                                const double* h, int N, int M, float* X, cudaStream_t st);

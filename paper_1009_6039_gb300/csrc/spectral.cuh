@@ -440,6 +440,14 @@ template <typename T>
 __device__ __forceinline__ T fd_lap(T c, int L) {
   return ((T)1 - c) * (c - (T)7) / (T)3 * (T)L * (T)L;
 }
+// The same eigenvalue in FP32 from a twiddle w = (cos t, -+sin t), with 1 - cos t formed as
+// sin^2 t / (1 + cos t) where cos t > 0: no cancellation at the lowest frequencies, which
+// carry most of a Poisson solution (1 - cos t from an FP32 cosine would lose ~5 digits at
+// t = 2 pi / 1024).
+__device__ __forceinline__ float fd_lap_w(float2 w, int L) {
+  const float omc = w.x > 0.f ? w.y * w.y / (1.f + w.x) : 1.f - w.x;
+  return omc * (w.x - 7.f) / 3.f * (float)L * (float)L;
+}
 template <typename T>
 __device__ __forceinline__ T inv_or_zero(T x) {
   return x == (T)0 ? (T)0 : (T)1 / x;
@@ -450,6 +458,12 @@ __device__ __forceinline__ T lowpass(int k1, int k2, int M, int N) {
   if (MODE != COL_POISSON_LP) return (T)1;
   const double a = (double)k1 / (0.25 * M), b = (double)k2 / (0.25 * N);
   return (T)exp(-0.5 * (a * a + b * b));
+}
+template <int MODE>
+__device__ __forceinline__ float lowpass_f(int k1, int k2, int M, int N) {
+  if (MODE != COL_POISSON_LP) return 1.f;
+  const float a = (float)k1 / (0.25f * (float)M), b = (float)k2 / (0.25f * (float)N);
+  return expf(-0.5f * (a * a + b * b));
 }
 __device__ __forceinline__ int sfreq(int n, int L, bool* nyq) {
   *nyq = (2 * n == L);
@@ -1105,13 +1119,16 @@ __global__ void __launch_bounds__(256)
 }
 
 // Same pass with the inverse column transform in double-float (dd.cuh): the FP64-accuracy
-// part of theta on the FP32 pipes.
-template <int E>
+// part of theta on the FP32 pipes.  MODE COL_POISSON / COL_POISSON_LP divides by the
+// eigenvalues of the fourth-order FD Laplacian instead (zero mode -> 0; _LP times the
+// Gaussian low-pass): the Poisson solves of the learned warm start in mixed precision.
+template <int E, int MODE>
 __global__ void __launch_bounds__(256)
     k_col_lbarinv_dd(const float2* __restrict__ spec, ddc* __restrict__ out, int N, int M,
                      int Q, double inv_nm, const float2* __restrict__ twN32,
-                     const ddc* __restrict__ twNdd, const DevScalars* __restrict__ sc,
-                     const float2* __restrict__ symx, const float2* __restrict__ symy) {
+                     const float2* __restrict__ twM32, const ddc* __restrict__ twNdd,
+                     const DevScalars* __restrict__ sc, const float2* __restrict__ symx,
+                     const float2* __restrict__ symy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ddc* sm = reinterpret_cast<ddc*>(smem_raw);
   const int Lc = M / 2, TPT = N / E;
@@ -1130,7 +1147,7 @@ __global__ void __launch_bounds__(256)
   fft_smem<float, E, -1>(fb, N, t, active, twN32);
   float ab[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
+  for (int a = 0; a < 5; ++a) ab[a] = MODE == COL_LBARINV ? (float)sc->abar[a] : 0.f;
   const float inv = (float)inv_nm;
   float2 s[E];
   if (active) {
@@ -1142,11 +1159,25 @@ __global__ void __launch_bounds__(256)
         float2 pz = fb[(N - k) % N];
         float2 A = mk2<float>(0.5f * (z.x + pz.x), 0.5f * (z.y - pz.y));
         float2 B = mk2<float>(0.5f * (z.y + pz.y), -0.5f * (z.x - pz.x));
-        A = cmul<float>(rho_bar<float>(ab, symx[0], symy[k]), A);
-        B = cmul<float>(rho_bar<float>(ab, symx[M / 2], symy[k]), B);
+        if (MODE == COL_LBARINV) {
+          A = cmul<float>(rho_bar<float>(ab, symx[0], symy[k]), A);
+          B = cmul<float>(rho_bar<float>(ab, symx[M / 2], symy[k]), B);
+        } else {
+          bool nyq2;
+          const int k2 = sfreq(k, N, &nyq2);
+          const float ly = fd_lap_w(twN32[k], N);
+          const float lxn = -16.f / 3.f * (float)M * (float)M;  // k1 = M/2 (cos t = -1)
+          A = cscale<float>(A, inv_or_zero<float>(ly) * lowpass_f<MODE>(0, k2, M, N));
+          B = cscale<float>(B, inv_or_zero<float>(lxn + ly) * lowpass_f<MODE>(M / 2, k2, M, N));
+        }
         r = mk2<float>(A.x - B.y, A.y + B.x);
-      } else {
+      } else if (MODE == COL_LBARINV) {
         r = cmul<float>(rho_bar<float>(ab, symx[col], symy[k]), z);
+      } else {
+        bool nyq2;
+        const int k2 = sfreq(k, N, &nyq2);
+        r = cscale<float>(z, inv_or_zero<float>(fd_lap_w(twM32[col], M) + fd_lap_w(twN32[k], N)) *
+                                 lowpass_f<MODE>(col, k2, M, N));
       }
       s[e] = mk2<float>(r.x * inv, r.y * inv);
     }
@@ -1170,6 +1201,7 @@ __global__ void __launch_bounds__(256)
 }
 
 // theta rows (complex-to-real) in double-float, then u_out = u_in + step theta in FP64
+// (u_in == nullptr: u_out = step theta)
 template <int E>
 __global__ void __launch_bounds__(256)
     k_row_c2r_update_dd(const ddc* __restrict__ q, const double* __restrict__ u_in,
@@ -1201,13 +1233,13 @@ __global__ void __launch_bounds__(256)
   c2r_preprocess<dd>(buf, L, t, TPT, active, twM);
   fft_smem<dd, E, +1>(buf, L, t, active, twL);
   if (!active) return;
-  const double2* ui = reinterpret_cast<const double2*>(u_in + (size_t)row * M);
+  const double2* ui = u_in ? reinterpret_cast<const double2*>(u_in + (size_t)row * M) : nullptr;
   double2* uo = reinterpret_cast<double2*>(u_out + (size_t)row * M);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int n = t + e * TPT;
     const ddc z = buf[n];
-    double2 a = ui[n];
+    double2 a = ui ? ui[n] : make_double2(0.0, 0.0);
     a.x += step * dd_to_double(z.x);
     a.y += step * dd_to_double(z.y);
     uo[n] = a;
@@ -1717,7 +1749,7 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
   return cudaGetLastError();
 }
 
-template <int E>
+template <int E, int MODE>
 cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
                              const SpecTables& tb32, const SpecTables& tbdd,
                              const DevScalars* sc, cudaStream_t st) {
@@ -1728,11 +1760,12 @@ cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
   while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * FB(N) * sizeof(ddc);
-  cudaError_t e = set_smem(k_col_lbarinv_dd<E>, sm);
+  cudaError_t e = set_smem(k_col_lbarinv_dd<E, MODE>, sm);
   if (e != cudaSuccess) return e;
-  k_col_lbarinv_dd<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+  k_col_lbarinv_dd<E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
-      (const ddc*)tbdd.twN, sc, (const float2*)tb32.symx, (const float2*)tb32.symy);
+      (const float2*)tb32.twM, (const ddc*)tbdd.twN, sc, (const float2*)tb32.symx,
+      (const float2*)tb32.symy);
   return cudaGetLastError();
 }
 

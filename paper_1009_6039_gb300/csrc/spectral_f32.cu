@@ -9,11 +9,25 @@ cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, in
   if (fft_E(N) == 12) return col_lbarinv_mixed_E<12>(spec, out, N, M, tb32, tb64, sc, st);
   return col_lbarinv_mixed_E<8>(spec, out, N, M, tb32, tb64, sc, st);
 }
+template <int MODE>
+static cudaError_t col_lbarinv_dd_mode(const float2* spec, ddc* out, int N, int M,
+                                       const SpecTables& tb32, const SpecTables& tbdd,
+                                       const DevScalars* sc, cudaStream_t st) {
+  if (fft_E(N) == 12) return col_lbarinv_dd_E<12, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
+  return col_lbarinv_dd_E<8, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
+}
 cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
                                   const SpecTables& tb32, const SpecTables& tbdd,
-                                  const DevScalars* sc, cudaStream_t st) {
-  if (fft_E(N) == 12) return col_lbarinv_dd_E<12>(spec, out, N, M, tb32, tbdd, sc, st);
-  return col_lbarinv_dd_E<8>(spec, out, N, M, tb32, tbdd, sc, st);
+                                  const DevScalars* sc, cudaStream_t st, int mode) {
+  switch (mode) {
+    case COL_LBARINV:
+      return col_lbarinv_dd_mode<COL_LBARINV>(spec, out, N, M, tb32, tbdd, sc, st);
+    case COL_POISSON:
+      return col_lbarinv_dd_mode<COL_POISSON>(spec, out, N, M, tb32, tbdd, sc, st);
+    case COL_POISSON_LP:
+      return col_lbarinv_dd_mode<COL_POISSON_LP>(spec, out, N, M, tb32, tbdd, sc, st);
+  }
+  return cudaErrorInvalidValue;
 }
 cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
                                      double step, int N, int M, const SpecTables& tbdd,

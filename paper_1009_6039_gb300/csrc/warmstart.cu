@@ -66,11 +66,12 @@ struct Stencil {
 };
 
 // log f - log g with FP32 logarithms (h only seeds the features and the warm start)
+template <typename T>
 __global__ void k_ws_source(const double* __restrict__ f, const double* __restrict__ g,
-                            double* __restrict__ src, long P) {
+                            T* __restrict__ src, long P) {
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x)
-    src[p] = (double)(logf((float)f[p]) - logf((float)g[p]));
+    src[p] = (T)(logf((float)f[p]) - logf((float)g[p]));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -791,7 +792,13 @@ inline int nblk(long P, int t = 256) {
 // ---------------------------------------------------------------------------------------
 cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
                              cudaStream_t st) {
-  k_ws_source<<<nblk(P), 256, 0, st>>>(f, g, src, P);
+  k_ws_source<double><<<nblk(P), 256, 0, st>>>(f, g, src, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ws_source32(const double* f, const double* g, float* src, long P,
+                               cudaStream_t st) {
+  k_ws_source<float><<<nblk(P), 256, 0, st>>>(f, g, src, P);
   return cudaGetLastError();
 }
 

@@ -2,10 +2,17 @@
 the gain of a trained network over the zero start.
 
 Tolerances:
-  - FD Poisson solve (FP64 FFTs): 1e-12 of the result's scale.
+  - FD Poisson solve: FP64 mode (FP64 FFTs) 1e-12 of the result's scale; mixed mode
+    (FP32 forward transforms, division and inverse transforms in double-float) 5e-6: the
+    forward transforms' FP32 round-off, ~2^-24 sqrt(log2 P) relative to the source's
+    coefficients, passes through the division by the Laplacian's eigenvalues as a relative
+    error of the same size in the result (a few 1e-7), plus the FP32 eigenvalues and
+    low-pass factors (1e-7 relative).
   - Features (FP64 stencils and interpolation, FP32 logarithms, stored as FP32): 1e-5 of
     each feature's scale (FP32 logf and storage rounding, a few 1e-7 relative, plus FP64
-    stencil round-off amplified by M^2).
+    stencil round-off amplified by M^2); the two features holding log det(I + D^2 h) are
+    weighted by det (clamped to [1e-3, 1]), since an error in det enters them divided by
+    det.
   - Network on the tensor cores vs the oracle with the same BF16 roundings: FP32 instead of
     FP64 accumulation and __expf differ by ~1e-6 relative; where that moves a value across a
     BF16 rounding boundary the activation changes by one BF16 ulp (2^-8 relative), so single
@@ -56,7 +63,8 @@ def test_fd_poisson(ot, N, M, prec, lowpass):
     u = dev(np.zeros((N, M)))
     p.ws_poisson(dev(src), u, lowpass=lowpass)
     ref = O.fd_poisson(src, lowpass=lowpass)
-    assert np.abs(u.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    rel = 1e-12 if prec == "fp64" else 5e-6
+    assert np.abs(u.cpu().numpy() - ref).max() <= rel * np.abs(ref).max()
     p.close()
 
 
@@ -73,9 +81,15 @@ def test_features_and_target(ot, N, M):
     t = torch.zeros(N * M, dtype=torch.float32, device="cuda")
     p.ws_features(dev(f), dev(g), X, t, phi_star=dev(phi))
     Xg = X.cpu().numpy()
+    # features 3 (r = log f - log G - log det) and 14 (r times the Laplacian of h) carry
+    # log max(det, 1e-3), det = det(I + D^2 h) = 1 + X4 + X7, whose error is the error of det
+    # over det: where h is close to losing convexity the (FP32-forward) error of h is
+    # amplified by up to 1e3, so those two are compared weighted by the clamped det
+    det = np.clip(1.0 + X_ref[:, 4] + X_ref[:, 7], 1e-3, 1.0)
     for k in range(16):
         scale = np.abs(X_ref[:, k]).max() + 1e-30
-        assert np.abs(Xg[:, k] - X_ref[:, k]).max() <= 1e-5 * max(scale, 1e-3), k
+        wk = det if k in (3, 14) else 1.0
+        assert np.max(np.abs(Xg[:, k] - X_ref[:, k]) * wk) <= 1e-5 * max(scale, 1e-3), k
     assert np.abs(t.cpu().numpy() - t_ref).max() <= 1e-5 * np.abs(t_ref).max()
     p.close()
 
