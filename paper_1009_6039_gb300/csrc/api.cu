@@ -686,23 +686,14 @@ static int read_scalars(ot_plan* p) {
 }
 
 
-// c = B-spline coefficients of g, in FP64 (prefilter by the symbol (2 + cos)/3 per axis)
+// c = B-spline coefficients of g in FP64 (recursive filters along y and x; p->Fraw is free
+// scratch before the first residual); the mixed mode also keeps c and f as (hi, lo) floats
 static int run_prefilter(ot_plan* p, const double* g, double* c) {
-  C2<double>* sp = (C2<double>*)(p->precision ? p->spec64 : p->spec);
-  C2<double>* qq = (C2<double>*)(p->precision ? p->q64 : p->q0);
-  LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_row_r2c<double>(g, 0, nullptr, nullptr, sp, p->N, p->M, p->tb64, nullptr,
-                                p->stream));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_col<double>(COL_PREFILTER, sp, qq, nullptr, nullptr, p->N, p->M, p->tb64,
-                            nullptr, nullptr, p->stream));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_row_c2r<double>(ROWINV_PLAIN, qq, nullptr, nullptr, nullptr, c, nullptr,
-                                nullptr, 0.0, 1.0, p->N, p->M, p->tb64, nullptr, p->stream));
-  if (p->precision) {
-    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(c, p->cdd, (long)p->N * p->M, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 2,
+         launch_prefilter(g, p->Fraw, c, p->precision ? p->cdd : nullptr, p->N, p->M,
+                          p->stream));
+  if (p->precision)
     LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(p->f, p->fdd, (long)p->N * p->M, p->stream));
-  }
   return OT_OK;
 }
 

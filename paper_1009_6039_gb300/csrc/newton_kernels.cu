@@ -177,6 +177,71 @@ static int reduce_blocks() {
   return nb;
 }
 
+// ---------------------------------------------------------------------------------------
+// Cubic B-spline prefilter (Sec. 4.1: the coefficients c of the interpolant of g, with
+// (c[k-1] + 4 c[k] + c[k+1]) / 6 = g[k] along each axis, periodic) as recursive filters.
+// The periodic inverse of the stencil (1, 4, 1) / 6 is 6 h * with h[k] = z z^|k| / (z^2 - 1),
+// z = sqrt(3) - 2 the root of z^2 + 4 z + 1 inside the unit circle (its DTFT is
+// 1 / (4 + 2 cos t)), and sum_k z^|k| s[i - k] = cp[i] + ca[i] - s[i] with the first-order
+// recursions cp[i] = s[i] + z cp[i - 1] (causal) and ca[i] = s[i] + z ca[i + 1]
+// (anticausal).  A thread runs both over a chunk of PRE_CH points of one line, starting each
+// from PRE_K periodic terms beyond the chunk (|z|^PRE_K < 1e-22, below FP64 round-off): the
+// circular deconvolution to FP64 round-off with a few multiply-adds per point, where the
+// spectral form takes three FP64 transform passes.
+// ---------------------------------------------------------------------------------------
+constexpr int PRE_K = 40, PRE_CH = 64;
+
+// one axis: lines `line` (stride ls) of L points (stride is); consecutive threads take
+// consecutive lines.  dd_out (optional) also receives the result split as (hi, lo) floats.
+__global__ void __launch_bounds__(256)
+    k_prefilter_axis(const double* __restrict__ s, double* __restrict__ out,
+                     float2* __restrict__ dd_out, int nlines, int L, long ls, long is, int nch,
+                     double z, double A) {
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (tid >= (long)nlines * nch) return;
+  const int line = (int)(tid % nlines), ch = (int)(tid / nlines);
+  const int i0 = ch * PRE_CH, i1 = min(L, i0 + PRE_CH);
+  const double* x = s + line * ls;
+  double* o = out + line * ls;
+  // states entering the chunk: cp[i0 - 1] and ca[i1] from the PRE_K points beyond it
+  double cp = 0.0, ca = 0.0;
+  for (int i = i0 - PRE_K; i < i0; ++i) cp = fma(z, cp, x[(long)(((i % L) + L) % L) * is]);
+  for (int i = i1 + PRE_K - 1; i >= i1; --i) ca = fma(z, ca, x[(long)(i % L) * is]);
+#pragma unroll 4
+  for (int i = i0; i < i1; ++i) {
+    cp = fma(z, cp, x[(long)i * is]);
+    o[(long)i * is] = cp;
+  }
+#pragma unroll 4
+  for (int i = i1 - 1; i >= i0; --i) {
+    const double xi = x[(long)i * is];
+    ca = fma(z, ca, xi);
+    const double v = A * (o[(long)i * is] + ca - xi);
+    o[(long)i * is] = v;
+    if (dd_out) {
+      const float hi = __double2float_rn(v);
+      dd_out[line * ls + (long)i * is] = make_float2(hi, __double2float_rn(v - (double)hi));
+    }
+  }
+}
+
+cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
+                             int M, cudaStream_t st) {
+  const double z = sqrt(3.0) - 2.0;
+  const double A = 6.0 * z / (z * z - 1.0);
+  // columns (along y): lines are the M columns, points the N rows
+  const int ny = (N + PRE_CH - 1) / PRE_CH;
+  const long ty = (long)M * ny;
+  k_prefilter_axis<<<(unsigned)((ty + 255) / 256), 256, 0, st>>>(g, scratch, nullptr, M, N, 1,
+                                                                 M, ny, z, A);
+  // rows (along x)
+  const int nx = (M + PRE_CH - 1) / PRE_CH;
+  const long tx = (long)N * nx;
+  k_prefilter_axis<<<(unsigned)((tx + 255) / 256), 256, 0, st>>>(scratch, c, cdd, N, M, M, 1,
+                                                                 nx, z, A);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st) {

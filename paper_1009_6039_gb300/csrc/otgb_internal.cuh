@@ -87,7 +87,7 @@ enum ColMode {
   COL_INV = 1,
   COL_MATVEC = 2,
   COL_LBARINV = 3,
-  COL_PREFILTER = 4,
+  // 4: unused (the B-spline prefilter runs as recursive filters, launch_prefilter)
   COL_POISSON = 5,
   COL_POISSON_LP = 6
 };
@@ -147,6 +147,10 @@ cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u
                                      const DevScalars* sc, cudaStream_t st);
 
 // Residual / coefficients, input translation ------------------------------------------
+// c = cubic B-spline coefficients of g (periodic), by recursive filters along y then x
+// (scratch: N x M FP64); cdd (optional) also receives c as (hi, lo) float pairs
+cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
+                             int M, cudaStream_t st);
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st);

@@ -628,12 +628,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
         C2<T> p = buf[(N - k) % N];
         C2<T> A = mk2<T>((T)0.5 * (z.x + p.x), (T)0.5 * (z.y - p.y));
         C2<T> B = mk2<T>((T)0.5 * (z.y + p.y), (T)-0.5 * (z.x - p.x));
-        if (MODE == COL_PREFILTER) {
-          // divide by the cubic B-spline symbol (2 + cos 2 pi k / L) / 3 per axis
-          const T by = ((T)2 + twN[k].x) / (T)3;
-          A = cscale<T>(A, (T)1 / by);           // k1 = 0: factor 1
-          B = cscale<T>(B, (T)3 / by);           // k1 = M/2: factor 1/3
-        } else if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
+        if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
           const T ly = fd_lap<T>(twN[k].x, N);
           A = cscale<T>(A, inv_or_zero<T>(ly) * lowpass<T, MODE>(0, k2, M, N));
           B = cscale<T>(B, inv_or_zero<T>(fd_lap<T>((T)-1, M) + ly) *
@@ -652,11 +647,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __res
         }
         r = mk2<T>(A.x - B.y, A.y + B.x);  // A + i B
       } else {
-        if (MODE == COL_PREFILTER) {
-          const T by = ((T)2 + twN[k].x) / (T)3;
-          const T bx = ((T)2 + twM[col].x) / (T)3;
-          r = cscale<T>(z, (T)1 / (bx * by));
-        } else if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
+        if (MODE == COL_POISSON || MODE == COL_POISSON_LP) {
           r = cscale<T>(z, inv_or_zero<T>(fd_lap<T>(twM[col].x, M) + fd_lap<T>(twN[k].x, N)) *
                                lowpass<T, MODE>(col, k2, M, N));
         } else {
@@ -1636,8 +1627,6 @@ cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T
     case COL_INV: return col_E<T, E, COL_INV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_MATVEC: return col_E<T, E, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_LBARINV: return col_E<T, E, COL_LBARINV>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
-    case COL_PREFILTER:
-      return col_E<T, E, COL_PREFILTER>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_POISSON:
       return col_E<T, E, COL_POISSON>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
     case COL_POISSON_LP:

@@ -69,7 +69,8 @@ def test_fft_forward_inverse(ot, N, M, prec):
     p.close()
 
 
-@pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (192, 384), (256, 256)])
+@pytest.mark.parametrize("N,M", [(8, 16), (12, 24), (16, 16), (24, 48), (128, 48), (192, 384),
+                                 (256, 256), (1024, 1024)])
 def test_prefilter(ot, N, M):
     g = 1 + 0.5 * RNG.random((N, M))
     p = plan(ot, N, M, "mixed")  # the prefilter is FP64 in both modes
