@@ -5,6 +5,7 @@
 // a ticket reduces them in block order and finalises the scalars in DevScalars.  The
 // order is fixed, so results are bit-reproducible from run to run.
 #include <math.h>
+#include <string.h>
 
 #include "dd.cuh"
 #include "otgb_internal.cuh"
@@ -118,6 +119,106 @@ __device__ void reduce_partials(double (&v)[NV], const int (&kind)[NV], const do
     }
   }
   block_reduce<NV>(v, kind);
+}
+
+// FP32 sum of NV values over the grid (1-D grid), for the FP32 Krylov vectors of the mixed
+// mode: block tree sums, per-block partials, and the last block to take a ticket sums them
+// in block order (fixed order: bit-reproducible).  Returns true in that block, with the
+// totals in thread 0.  GB300 runs FP32 at ~60x its FP64 rate, and FP64 tree reductions
+// (shuffle + add per level) had become a visible part of these short kernels.
+template <int NV>
+__device__ bool grid_sum_f(float (&v)[NV], double* partials, unsigned int* ticket) {
+  __shared__ bool last;
+  float* pf = reinterpret_cast<float*>(partials);
+  block_sum_f<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) pf[(size_t)blockIdx.x * NV + a] = v[a];
+    __threadfence();
+    const unsigned int k = atomicAdd(ticket, 1u);
+    last = (k == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = 0.f;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] += ((volatile const float*)pf)[(size_t)b * NV + a];
+  block_sum_f<NV>(v);
+  return true;
+}
+
+// Double-float reductions (dd.cuh) of NV values with kinds 0 sum, 1 max, 2 min, on the FP32
+// pipes: the FP64-accuracy grid reductions of the mixed-mode residual.
+__device__ __forceinline__ dd dd_combine(dd a, dd b, int kind) {
+  if (kind == 0) return dd_add(a, b);
+  if (kind == 1) return dd_gt(b, a) ? b : a;
+  return dd_gt(a, b) ? b : a;
+}
+__device__ __forceinline__ dd dd_identity(int kind) {
+  return kind == 0 ? dd{0.f, 0.f} : (kind == 1 ? dd{-INFINITY, 0.f} : dd{INFINITY, 0.f});
+}
+__device__ __forceinline__ dd warp_reduce_dd(dd v, int kind) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dd w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = dd_combine(v, w, kind);
+  }
+  return v;
+}
+// result valid in thread 0 (all of warp 0)
+template <int NV>
+__device__ void block_reduce_dd(dd (&v)[NV], const int (&kind)[NV]) {
+  __shared__ float2 redd[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = warp_reduce_dd(v[a], kind[a]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) redd[wid][a] = make_float2(v[a].hi, v[a].lo);
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const dd x = lane < nw ? dd{redd[lane][a].x, redd[lane][a].y} : dd_identity(kind[a]);
+      v[a] = warp_reduce_dd(x, kind[a]);
+    }
+  }
+  __syncthreads();
+}
+// grid-wide: per-block (hi, lo) partials, the last block to take a ticket combines them in
+// block order; true in that block, totals in thread 0 (2-D grids allowed)
+template <int NV>
+__device__ bool grid_reduce_dd(dd (&v)[NV], const int (&kind)[NV], double* partials,
+                               unsigned int* ticket) {
+  __shared__ bool last;
+  float2* pf = reinterpret_cast<float2*>(partials);
+  const unsigned int nb = gridDim.x * gridDim.y;
+  block_reduce_dd<NV>(v, kind);
+  if (threadIdx.x == 0) {
+    const size_t bid = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) pf[bid * NV + a] = make_float2(v[a].hi, v[a].lo);
+    __threadfence();
+    const unsigned int k = atomicAdd(ticket, 1u);
+    last = (k == nb - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = dd_identity(kind[a]);
+  for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const volatile float2* q = (const volatile float2*)pf + (size_t)b * NV + a;
+      v[a] = dd_combine(v[a], dd{q->x, q->y}, kind[a]);
+    }
+  block_reduce_dd<NV>(v, kind);
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -667,25 +768,23 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
     }
     if (dd_gt(dmin, det)) dmin = det;
   }
-  double v64[5] = {dd_to_double(sum_fn), (double)fmax_.hi + (double)fmax_.lo,
-                   (double)fmin_.hi + (double)fmin_.lo, (double)dmin.hi + (double)dmin.lo,
-                   (double)nonfinite};
-  const int kind64[5] = {0, 1, 2, 2, 0};
-  double v[10];
+  // grid reductions in double-float (sum f_n, the five Simpson sums, max F, min F, min det,
+  // the non-finite count)
+  dd r[10] = {sum_fn,
+              dd{simp[0], 0.f},
+              dd{simp[1], 0.f},
+              dd{simp[2], 0.f},
+              dd{simp[3], 0.f},
+              dd{simp[4], 0.f},
+              fmax_,
+              fmin_,
+              dmin,
+              dd{nonfinite, 0.f}};
   const int kind[10] = {0, 0, 0, 0, 0, 0, 1, 2, 2, 0};
-  block_reduce<5>(v64, kind64);
-  block_sum_f<5>(simp);
-#pragma unroll
-  for (int a = 0; a < 5; ++a) v[1 + a] = (double)simp[a];
-  v[0] = v64[0];
-  v[6] = v64[1];
-  v[7] = v64[2];
-  v[8] = v64[3];
-  v[9] = v64[4];
-  if (!publish_partials<10>(v, partials, &sc->ticket[TK_RESID])) return;
-  const unsigned int nb = gridDim.x * gridDim.y;
-  reduce_partials<10>(v, kind, partials, nb);
+  if (!grid_reduce_dd<10>(r, kind, partials, &sc->ticket[TK_RESID])) return;
   if (threadIdx.x == 0) {
+    double v[10];
+    for (int a = 0; a < 10; ++a) v[a] = (double)r[a].hi + (double)r[a].lo;
     const double Pd = (double)N * (double)M;
     const double mean_fn = v[0] / Pd;
     const double shift = mean_fn - 1.0;
@@ -864,10 +963,16 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
     V0[p] = bt;
     acc += bt * bt;
   }
-  v[0] = (double)acc;
-  block_reduce<1>(v, kind);
-  if (!publish_partials<1>(v, partials, &sc->ticket[TK_INIT])) return;
-  reduce_partials<1>(v, kind, partials, gridDim.x);
+  if constexpr (sizeof(T) == 4) {
+    float a[1] = {acc};
+    if (!grid_sum_f<1>(a, partials, &sc->ticket[TK_INIT])) return;
+    v[0] = (double)a[0];
+  } else {
+    v[0] = (double)acc;
+    block_reduce<1>(v, kind);
+    if (!publish_partials<1>(v, partials, &sc->ticket[TK_INIT])) return;
+    reduce_partials<1>(v, kind, partials, gridDim.x);
+  }
   if (threadIdx.x == 0) {
     const double beta = sqrt(v[0]);
     if (!restart) {
@@ -892,30 +997,75 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
   }
 }
 
-// Per-thread partial sums are kept in the vector precision T (a thread covers only
-// P / (2 x SMs x 256) elements); partials are combined across threads and blocks in FP64.
+// 16-byte vector access to the Krylov vectors (float4 / double2): when P is a multiple of
+// the width every vector V_i = V + i P stays 16-byte aligned and the loops run over whole
+// vectors (the loop over q below), else element by element (the tail loop covers all).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int W = 4;
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int W = 2;
+};
+template <typename T>
+__device__ __forceinline__ void vld(const T* __restrict__ base, long q, T (&x)[Vec16<T>::W]) {
+  const typename Vec16<T>::type v = reinterpret_cast<const typename Vec16<T>::type*>(base)[q];
+  memcpy(x, &v, sizeof(v));
+}
+template <typename T>
+__device__ __forceinline__ void vst(T* __restrict__ base, long q, const T (&x)[Vec16<T>::W]) {
+  typename Vec16<T>::type v;
+  memcpy(&v, x, sizeof(v));
+  reinterpret_cast<typename Vec16<T>::type*>(base)[q] = v;
+}
+// number of whole vectors of the 16-byte loops (0: element loop only)
+__device__ __forceinline__ long nvec(long P, int W) { return P % W == 0 ? P / W : 0; }
+
+// Per-thread partial sums are kept in the vector precision T (a thread covers a few vectors
+// of 16 bytes); partials are combined across threads and blocks in FP64.
 template <typename T, int J>
 __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restrict__ w, long P,
                                        double* partials, DevScalars* sc, int pass) {
+  constexpr int W = Vec16<T>::W;
   T acc[J];
 #pragma unroll
   for (int i = 0; i < J; ++i) acc[i] = (T)0;
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
-       p += (long)gridDim.x * blockDim.x) {
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  for (long q = tid; q < PV; q += nth) {
+    T wv[W];
+    vld<T>(w, q, wv);
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      T x[W];
+      vld<T>(V + (size_t)i * P, q, x);
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[i] += x[k] * wv[k];
+    }
+  }
+  for (long p = PV * W + tid; p < P; p += nth) {
     const T wp = w[p];
 #pragma unroll
     for (int i = 0; i < J; ++i) acc[i] += V[(size_t)i * P + p] * wp;
   }
   double v[J];
-  int kind[J];
+  if constexpr (sizeof(T) == 4) {
+    if (!grid_sum_f<J>(acc, partials, &sc->ticket[TK_DOTS])) return;
 #pragma unroll
-  for (int i = 0; i < J; ++i) {
-    v[i] = (double)acc[i];
-    kind[i] = 0;
+    for (int i = 0; i < J; ++i) v[i] = (double)acc[i];
+  } else {
+    int kind[J];
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      v[i] = (double)acc[i];
+      kind[i] = 0;
+    }
+    block_reduce<J>(v, kind);
+    if (!publish_partials<J>(v, partials, &sc->ticket[TK_DOTS])) return;
+    reduce_partials<J>(v, kind, partials, gridDim.x);
   }
-  block_reduce<J>(v, kind);
-  if (!publish_partials<J>(v, partials, &sc->ticket[TK_DOTS])) return;
-  reduce_partials<J>(v, kind, partials, gridDim.x);
   if (threadIdx.x == 0) {
     const int m = sc->m, j = J - 1;
     if (pass == 0) {
@@ -960,8 +1110,24 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   T* Vn = V + (size_t)(j + 1) * P;
   const T* src = (mode == 2) ? Vn : w;
   T acc = (T)0;
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
-       p += (long)gridDim.x * blockDim.x) {
+  constexpr int W = Vec16<T>::W;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  for (long q = tid; q < PV; q += nth) {
+    T x[W];
+    vld<T>(src, q, x);
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      T y[W];
+      vld<T>(V + (size_t)i * P, q, y);
+#pragma unroll
+      for (int k = 0; k < W; ++k) x[k] -= coefs[i] * y[k];
+    }
+    vst<T>(Vn, q, x);
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc += x[k] * x[k];
+  }
+  for (long p = PV * W + tid; p < P; p += nth) {
     T x = src[p];
 #pragma unroll
     for (int i = 0; i < J; ++i) x -= coefs[i] * V[(size_t)i * P + p];
@@ -970,10 +1136,16 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   }
   if (mode == 1) return;  // first of two passes: the norm follows the second
   double v[1] = {(double)acc};
-  const int kind[1] = {0};
-  block_reduce<1>(v, kind);
-  if (!publish_partials<1>(v, partials, &sc->ticket[TK_UPDATE])) return;
-  reduce_partials<1>(v, kind, partials, gridDim.x);
+  if constexpr (sizeof(T) == 4) {
+    float a[1] = {acc};
+    if (!grid_sum_f<1>(a, partials, &sc->ticket[TK_UPDATE])) return;
+    v[0] = (double)a[0];
+  } else {
+    const int kind[1] = {0};
+    block_reduce<1>(v, kind);
+    if (!publish_partials<1>(v, partials, &sc->ticket[TK_UPDATE])) return;
+    reduce_partials<1>(v, kind, partials, gridDim.x);
+  }
   if (threadIdx.x == 0) {
     double* H = sc->H;
     const double hn = sqrt(v[0]);
@@ -1046,8 +1218,22 @@ __device__ __forceinline__ void combine_j(const T* __restrict__ V, T* __restrict
   T coefs[J];
 #pragma unroll
   for (int i = 0; i < J; ++i) coefs[i] = (T)(sc->y[i] * sc->scale[i]);
-  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
-       p += (long)gridDim.x * blockDim.x) {
+  constexpr int W = Vec16<T>::W;
+  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  for (long q = tid; q < PV; q += nth) {
+    T x[W];
+    vld<T>(sigma, q, x);
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      T y[W];
+      vld<T>(V + (size_t)i * P, q, y);
+#pragma unroll
+      for (int k = 0; k < W; ++k) x[k] += coefs[i] * y[k];
+    }
+    vst<T>(sigma, q, x);
+  }
+  for (long p = PV * W + tid; p < P; p += nth) {
     T x = sigma[p];
 #pragma unroll
     for (int i = 0; i < J; ++i) x += coefs[i] * V[(size_t)i * P + p];

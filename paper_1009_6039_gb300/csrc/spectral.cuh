@@ -578,8 +578,11 @@ __host__ __device__ constexpr int col_nbuf() {
   return (MODE == COL_MATVEC && sizeof(T) == 4 && E == 4) ? 3 : 1;
 }
 
+// (the FP32 pass with 4 elements per thread is held to 64 registers, so that two blocks of
+// 512 threads fit on an SM: 256 blocks at 1024^2 then run in one wave)
 template <typename T, int E, int MODE>
-__global__ void __launch_bounds__(MaxThreads<T>::value) k_col(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
+__global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 4) ? 2 : 1)
+    k_col(const C2<T>* __restrict__ spec, C2<T>* __restrict__ out0,
                       C2<T>* __restrict__ out1, C2<T>* __restrict__ out2, int N, int M, int Q,
                       double inv_nm,
                       const C2<T>* __restrict__ twN, const C2<T>* __restrict__ twM,
