@@ -347,6 +347,11 @@ __host__ __device__ constexpr int op_offset(int r, int k) {
   return (k >> 4) * 4096 + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+// warpgroups of the tensor-core network kernel (readout columns split WS_WG ways)
+#ifndef WS_WG
+#define WS_WG 4
+#endif
+
 constexpr int SM_W0 = 0;                       // 4 KB
 constexpr int SM_W1 = SM_W0 + 4096;            // 32 KB
 constexpr int SM_W2 = SM_W1 + 32768;           // 32 KB
@@ -354,7 +359,8 @@ constexpr int SM_A = SM_W2 + 32768;            // 32 KB activations / X tile
 constexpr int SM_BIAS = SM_A + 32768;          // b0, b1, b2, w3 (4 x 128 FP32), b3
 constexpr int SM_BAR = SM_BIAS + 4 * 128 * 4 + 16;
 constexpr int SM_TMEM = SM_BAR + 8;
-constexpr int SM_TOTAL = SM_TMEM + 8 + 128;    // + alignment slack
+constexpr int SM_RED = SM_TMEM + 8;            // per-warpgroup partial outputs (4 x 128 FP32)
+constexpr int SM_TOTAL = SM_RED + 4 * 128 * 4 + 128;  // + alignment slack
 constexpr int PACKED_W_BYTES = SM_A - SM_W0;   // 69632: W0, W1, W2 in operand layout
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -386,17 +392,18 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// bounded wait for the mbarrier phase with parity `par`: about four million non-blocking
-// polls (tens of milliseconds; an MMA group takes microseconds); false if it gave up
+// bounded wait for the mbarrier phase with parity `par`: at most 4096 tries, each of which
+// suspends the thread for at most 10 us (the suspend-time hint) -- about 40 ms in all, where
+// an MMA group takes microseconds; false if it gave up
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par) {
-  for (long it = 0; it < (1l << 22); ++it) {
+  for (int it = 0; it < 4096; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(par)
+        : "r"(bar), "r"(par), "r"(10000)
         : "memory");
     if (ok) return true;
   }
@@ -431,6 +438,19 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// warp 0 waits (the other warps sleep in the barrier instead of polling, leaving the issue
+// slots to the other CTA's readout); the result is made visible to every thread
+__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t par, int warp) {
+  bool ok = true;
+  if (warp == 0) {
+    ok = bar_wait(bar, par);
+    fence_before();
+  }
+  ok = __syncthreads_and(ok);
+  fence_after();
+  return ok;
+}
+
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -448,31 +468,42 @@ __device__ __forceinline__ void st_row8(unsigned char* base, int r, int k0, cons
   *reinterpret_cast<uint4*>(base + op_offset(r, k0)) = q;
 }
 
-// layer readout: 128 accumulator columns of this thread's row -> bias + SiLU -> BF16 tile
+// layer readout of this thread's row r over the NC 32-column chunks of the accumulator from
+// column c0: bias + SiLU -> BF16 A tile of the next layer
+template <int NC>
 __device__ __forceinline__ void readout_hidden(uint32_t trow, const float* bias,
-                                               unsigned char* sA, int r) {
+                                               unsigned char* sA, int r, int c0) {
 #pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < NC; ++c) {
+    const int col = c0 + 32 * c;
     float v[32];
-    tmem_ld32(trow + 32 * c, v);
+    tmem_ld32(trow + col, v);
 #pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = silu_f(v[q] + bias[32 * c + q]);
+    for (int q = 0; q < 32; ++q) v[q] = silu_f(v[q] + bias[col + q]);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) st_row8(sA, r, 32 * c + 8 * q, v + 8 * q);
+    for (int q = 0; q < 4; ++q) st_row8(sA, r, col + 8 * q, v + 8 * q);
   }
 }
 
+// One CTA per 128-row tile at a time (persistent over tiles), WG warpgroups: the readouts,
+// which bound the kernel (SiLU and BF16 packing of 128 x 128 values per layer), are split
+// by columns over the warpgroups -- warp w reads TMEM lanes 32 (w % 4) .. (its rows) and
+// warpgroup w / 4 the columns 128/WG (w / 4) ..; thread 0 issues the MMAs.
 // stall != 0 (a test of the failure path): the first tile's first MMA group is not issued,
 // so the wait for it runs out; the kernel then sets *err, frees its TMEM and returns
-__global__ void __launch_bounds__(128, 1)
+template <int WG>
+__global__ void __launch_bounds__(128 * WG, 2)
     k_ws_mlp_tc(const unsigned char* __restrict__ wpack, const float* __restrict__ params,
                 const float* __restrict__ X, long rows, float* __restrict__ out,
                 int* __restrict__ err, int stall) {
+  constexpr int NT = 128 * WG, NC = 4 / WG;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* sm =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  const int r = threadIdx.x, warp = r >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, g = warp >> 2, r = tid & 127;
+  const int c0 = 32 * NC * g;  // first accumulator column of this warpgroup
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
+  float* red = reinterpret_cast<float*>(sm + SM_RED);
   const uint32_t bar = smem_u32(sm + SM_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
 
@@ -480,12 +511,14 @@ __global__ void __launch_bounds__(128, 1)
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpack);
     uint4* dst = reinterpret_cast<uint4*>(sm + SM_W0);
-    for (int q = r; q < PACKED_W_BYTES / 16; q += blockDim.x) dst[q] = src[q];
-    sb[r] = params[H * K + r];                          // b0
-    sb[128 + r] = params[H * K + H + H * H + r];        // b1
-    sb[256 + r] = params[H * K + 2 * H + 2 * H * H + r];  // b2
-    sb[384 + r] = params[H * K + 3 * H + 2 * H * H + r];  // w3
-    if (r == 0) sb[512] = params[H * K + 4 * H + 2 * H * H];  // b3
+    for (int q = tid; q < PACKED_W_BYTES / 16; q += NT) dst[q] = src[q];
+    for (int q = tid; q < H; q += NT) {
+      sb[q] = params[H * K + q];                            // b0
+      sb[128 + q] = params[H * K + H + H * H + q];          // b1
+      sb[256 + q] = params[H * K + 2 * H + 2 * H * H + q];  // b2
+      sb[384 + q] = params[H * K + 3 * H + 2 * H * H + q];  // w3
+    }
+    if (tid == 0) sb[512] = params[H * K + 4 * H + 2 * H * H];  // b3
   }
   if (warp == 0) {
     asm volatile(
@@ -494,7 +527,7 @@ __global__ void __launch_bounds__(128, 1)
         : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (r == 0) {
+  if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -503,7 +536,7 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   unsigned char* sA = sm + SM_A;
   const uint32_t aA = smem_u32(sA), aW0 = smem_u32(sm + SM_W0), aW1 = smem_u32(sm + SM_W1),
                  aW2 = smem_u32(sm + SM_W2);
@@ -512,47 +545,43 @@ __global__ void __launch_bounds__(128, 1)
   const long ntiles = (rows + 127) / 128;
   for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long row = tile * 128 + r;
-    // X row -> BF16 (K block 0 of the A operand)
-    {
-      float v[16];
+    // X row -> BF16 (K block 0 of the A operand), 8 features per warpgroup
+    for (int part = g; part < 2; part += WG) {
+      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (row < rows) {
-        const float4* xr = reinterpret_cast<const float4*>(X + row * 16);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 t = __ldg(xr + q);
-          v[4 * q] = t.x;
-          v[4 * q + 1] = t.y;
-          v[4 * q + 2] = t.z;
-          v[4 * q + 3] = t.w;
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+        const float4* xr = reinterpret_cast<const float4*>(X + row * 16 + 8 * part);
+        const float4 a = __ldg(xr), b = __ldg(xr + 1);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+        v[4] = b.x;
+        v[5] = b.y;
+        v[6] = b.z;
+        v[7] = b.w;
       }
-      st_row8(sA, r, 0, v);
-      st_row8(sA, r, 8, v + 8);
+      st_row8(sA, r, 8 * part, v);
     }
     // layer 0: D = X W0^T
     fence_async_smem();
     fence_before();
     __syncthreads();
-    if (r == 0 && !(stall && tile == blockIdx.x)) {
+    if (tid == 0 && !(stall && tile == blockIdx.x)) {
       fence_after();
       mma_bf16(tmem, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
       mma_commit(bar);
     }
-    ok = __syncthreads_and(bar_wait(bar, phase));
-    fence_after();
+    ok = block_wait(bar, phase, warp);
     if (!ok) break;
     phase ^= 1;
-    readout_hidden(trow, sb, sA, r);
+    readout_hidden<NC>(trow, sb, sA, r, c0);
     // layers 1 and 2: D = A W^T, K = 128 in eight K blocks of 16
 #pragma unroll 1
     for (int layer = 1; layer <= 2 && ok; ++layer) {
       fence_async_smem();
       fence_before();
       __syncthreads();
-      if (r == 0) {
+      if (tid == 0) {
         fence_after();
         const uint32_t aW = layer == 1 ? aW1 : aW2;
 #pragma unroll
@@ -561,24 +590,32 @@ __global__ void __launch_bounds__(128, 1)
                    kb > 0 ? 1u : 0u);
         mma_commit(bar);
       }
-      ok = __syncthreads_and(bar_wait(bar, phase));
-      fence_after();
+      ok = block_wait(bar, phase, warp);
       if (!ok) break;
       phase ^= 1;
       if (layer == 1) {
-        readout_hidden(trow, sb + 128, sA, r);
+        readout_hidden<NC>(trow, sb + 128, sA, r, c0);
       } else {
-        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32
-        float acc = sb[512];
+        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32, each warpgroup
+        // over its columns, then the WG partial sums of the row added in warpgroup order
+        float acc = 0.f;
 #pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < NC; ++c) {
+          const int col = c0 + 32 * c;
           float v[32];
-          tmem_ld32(trow + 32 * c, v);
+          tmem_ld32(trow + col, v);
 #pragma unroll
           for (int q = 0; q < 32; ++q)
-            acc = fmaf(sb[384 + 32 * c + q], silu_f(v[q] + sb[256 + 32 * c + q]), acc);
+            acc = fmaf(sb[384 + col + q], silu_f(v[q] + sb[256 + col + q]), acc);
         }
-        if (row < rows) out[row] = acc;
+        red[g * 128 + r] = acc;
+        __syncthreads();
+        if (g == 0) {
+          float s = sb[512];
+#pragma unroll
+          for (int q = 0; q < WG; ++q) s += red[q * 128 + r];
+          if (row < rows) out[row] = s;
+        }
       }
     }
     fence_before();
@@ -588,7 +625,7 @@ __global__ void __launch_bounds__(128, 1)
     if (err) atomicExch(err, 1);
     // let an MMA still in flight finish before its TMEM goes away (bounded; with `stall`
     // nothing is in flight and this wait runs out too)
-    bar_wait(bar, phase);
+    if (warp == 0) bar_wait(bar, phase);
   }
   fence_before();
   __syncthreads();
@@ -875,14 +912,17 @@ cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_ws_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SM_TOTAL);
+    cudaError_t e = cudaFuncSetAttribute(k_ws_mlp_tc<WS_WG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
+  // two CTAs per SM (shared memory and TMEM allow two), so one CTA's readout overlaps the
+  // other's MMAs
   const long tiles = (rows + 127) / 128;
   const long grid = tiles < 2L * sms ? tiles : 2L * sms;
-  k_ws_mlp_tc<<<(unsigned)grid, 128, SM_TOTAL, st>>>(wpack, params, X, rows, out, err, stall);
+  k_ws_mlp_tc<WS_WG><<<(unsigned)grid, 128 * WS_WG, SM_TOTAL, st>>>(wpack, params, X, rows, out,
+                                                                   err, stall);
   return cudaGetLastError();
 }
 
