@@ -809,8 +809,10 @@ static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
            launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 2));
   } else {
+    // the multi-dot closes the step (norm by Pythagoras, Givens); the update only forms
+    // v_(j+1) and is skipped when the cycle ends
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0));
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 3));
   }
   return OT_OK;
 }

@@ -288,58 +288,102 @@ static int reduce_blocks() {
 // (anticausal).  A thread runs both over a chunk of PRE_CH points of one line, starting each
 // from PRE_K periodic terms beyond the chunk (|z|^PRE_K < 1e-22, below FP64 round-off): the
 // circular deconvolution to FP64 round-off with a few multiply-adds per point, where the
-// spectral form takes three FP64 transform passes.
+// spectral form takes three FP64 transform passes.  (256 threads = 32 lines x 8 chunks of
+// PRE_CH = 32 points per tile of 256 points.)
 // ---------------------------------------------------------------------------------------
-constexpr int PRE_K = 40, PRE_CH = 64;
+constexpr int PRE_K = 40, PRE_CH = 32;
 
-// one axis: lines `line` (stride ls) of L points (stride is); consecutive threads take
-// consecutive lines.  dd_out (optional) also receives the result split as (hi, lo) floats.
+// One axis, tiled: a block stages 32 lines x (256 points + PRE_K on each side, periodic) in
+// shared memory with coalesced loads (all of them in flight at once: the recursions
+// themselves are short serial chains, so the loads' latency is what a direct version waits
+// on), runs the two recursions per thread over a chunk of PRE_CH points of one line, and
+// writes the tile back coalesced.  XPASS: lines are rows (points along x), else columns.
+// dd_out (optional) also receives the result split as (hi, lo) floats.
+constexpr int PT_LN = 32, PT_TP = 256, PT_SW = PT_LN + 1;
+constexpr size_t PT_SMEM = (size_t)(PT_TP + 2 * PRE_K) * PT_SW * sizeof(double);
+
+template <bool XPASS>
 __global__ void __launch_bounds__(256)
-    k_prefilter_axis(const double* __restrict__ s, double* __restrict__ out,
-                     float2* __restrict__ dd_out, int nlines, int L, long ls, long is, int nch,
-                     double z, double A) {
-  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (tid >= (long)nlines * nch) return;
-  const int line = (int)(tid % nlines), ch = (int)(tid / nlines);
-  const int i0 = ch * PRE_CH, i1 = min(L, i0 + PRE_CH);
-  const double* x = s + line * ls;
-  double* o = out + line * ls;
-  // states entering the chunk: cp[i0 - 1] and ca[i1] from the PRE_K points beyond it
-  double cp = 0.0, ca = 0.0;
-  for (int i = i0 - PRE_K; i < i0; ++i) cp = fma(z, cp, x[(long)(((i % L) + L) % L) * is]);
-  for (int i = i1 + PRE_K - 1; i >= i1; --i) ca = fma(z, ca, x[(long)(i % L) * is]);
-#pragma unroll 4
-  for (int i = i0; i < i1; ++i) {
-    cp = fma(z, cp, x[(long)i * is]);
-    o[(long)i * is] = cp;
+    k_prefilter_tile(const double* __restrict__ s, double* __restrict__ out,
+                     float2* __restrict__ dd_out, int N, int M, double z, double A) {
+  extern __shared__ __align__(16) double smp[];  // [k][line], k = point - p0 + PRE_K
+  const int tid = threadIdx.x;
+  const int L = XPASS ? M : N, nlines = XPASS ? N : M;
+  const long ls = XPASS ? M : 1, ps = XPASS ? 1 : M;
+  const int line0 = blockIdx.x * PT_LN, p0 = blockIdx.y * PT_TP;
+  const int tpl = min(PT_TP, L - p0), nk = tpl + 2 * PRE_K;
+  // stage (lines fastest for columns, points fastest for rows: both coalesced)
+  for (int e = tid; e < nk * PT_LN; e += blockDim.x) {
+    const int k = XPASS ? e % nk : e / PT_LN, ln = XPASS ? e / nk : e % PT_LN;
+    const int line = line0 + ln;
+    const int pt = ((p0 - PRE_K + k) % L + L) % L;
+    smp[k * PT_SW + ln] = line < nlines ? s[line * ls + pt * ps] : 0.0;
   }
-#pragma unroll 4
-  for (int i = i1 - 1; i >= i0; --i) {
-    const double xi = x[(long)i * is];
-    ca = fma(z, ca, xi);
-    const double v = A * (o[(long)i * is] + ca - xi);
-    o[(long)i * is] = v;
+  __syncthreads();
+  const int ln = tid % PT_LN, c0 = (tid / PT_LN) * PRE_CH, n = min(PRE_CH, tpl - c0);
+  double v[PRE_CH];
+  if (n > 0) {
+    double cp = 0.0, ca = 0.0;
+    for (int k = c0; k < c0 + PRE_K; ++k) cp = fma(z, cp, smp[k * PT_SW + ln]);
+    for (int k = c0 + n + 2 * PRE_K - 1; k >= c0 + n + PRE_K; --k)
+      ca = fma(z, ca, smp[k * PT_SW + ln]);
+#pragma unroll
+    for (int i = 0; i < PRE_CH; ++i)
+      if (i < n) {
+        cp = fma(z, cp, smp[(c0 + PRE_K + i) * PT_SW + ln]);
+        v[i] = cp;
+      }
+#pragma unroll
+    for (int i = PRE_CH - 1; i >= 0; --i)
+      if (i < n) {
+        const double xi = smp[(c0 + PRE_K + i) * PT_SW + ln];
+        ca = fma(z, ca, xi);
+        v[i] = A * (v[i] + ca - xi);
+      }
+  }
+  __syncthreads();  // every chunk has read its neighbours' points
+  if (n > 0) {
+#pragma unroll
+    for (int i = 0; i < PRE_CH; ++i)
+      if (i < n) smp[(c0 + PRE_K + i) * PT_SW + ln] = v[i];
+  }
+  __syncthreads();
+  for (int e = tid; e < tpl * PT_LN; e += blockDim.x) {
+    const int k = XPASS ? e % tpl : e / PT_LN, l2 = XPASS ? e / tpl : e % PT_LN;
+    const int line = line0 + l2;
+    if (line >= nlines) continue;
+    const double r = smp[(k + PRE_K) * PT_SW + l2];
+    const long o = line * ls + (long)(p0 + k) * ps;
+    out[o] = r;
     if (dd_out) {
-      const float hi = __double2float_rn(v);
-      dd_out[line * ls + (long)i * is] = make_float2(hi, __double2float_rn(v - (double)hi));
+      const float hi = __double2float_rn(r);
+      dd_out[o] = make_float2(hi, __double2float_rn(r - (double)hi));
     }
   }
 }
 
 cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
                              int M, cudaStream_t st) {
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(k_prefilter_tile<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_prefilter_tile<true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
   const double z = sqrt(3.0) - 2.0;
   const double A = 6.0 * z / (z * z - 1.0);
-  // columns (along y): lines are the M columns, points the N rows
-  const int ny = (N + PRE_CH - 1) / PRE_CH;
-  const long ty = (long)M * ny;
-  k_prefilter_axis<<<(unsigned)((ty + 255) / 256), 256, 0, st>>>(g, scratch, nullptr, M, N, 1,
-                                                                 M, ny, z, A);
-  // rows (along x)
-  const int nx = (M + PRE_CH - 1) / PRE_CH;
-  const long tx = (long)N * nx;
-  k_prefilter_axis<<<(unsigned)((tx + 255) / 256), 256, 0, st>>>(scratch, c, cdd, N, M, M, 1,
-                                                                 nx, z, A);
+  // columns (along y), then rows (along x)
+  const dim3 gy((M + PT_LN - 1) / PT_LN, (N + PT_TP - 1) / PT_TP);
+  k_prefilter_tile<false><<<gy, 256, PT_SMEM, st>>>(g, scratch, nullptr, N, M, z, A);
+  const dim3 gx((N + PT_LN - 1) / PT_LN, (M + PT_TP - 1) / PT_TP);
+  k_prefilter_tile<true><<<gx, 256, PT_SMEM, st>>>(scratch, c, cdd, N, M, z, A);
   return cudaGetLastError();
 }
 
@@ -1023,15 +1067,108 @@ __device__ __forceinline__ void vst(T* __restrict__ base, long q, const T (&x)[V
 // number of whole vectors of the 16-byte loops (0: element loop only)
 __device__ __forceinline__ long nvec(long P, int W) { return P % W == 0 ? P / W : 0; }
 
+// Close Arnoldi step j (one thread): H(j+1, j) = hn, the previous Givens rotations and a new
+// one on column j, the residual estimate |g_(j+1)|, convergence / end of cycle, v_(j+1) =
+// w / hn, and the conditional handle of step j + 1.  weak: hn came out below the resolution
+// of the Pythagorean norm; the cycle ends without a convergence claim (the restart
+// recomputes the residual explicitly).
+__device__ void arnoldi_close(DevScalars* sc, int j, double hn, bool weak) {
+  double* H = sc->H;
+  const int m = sc->m;
+  H[(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {  // previous rotations on column j
+    const double t0 = H[i * m + j], t1 = H[(i + 1) * m + j];
+    H[i * m + j] = sc->cs[i] * t0 + sc->sn[i] * t1;
+    H[(i + 1) * m + j] = -sc->sn[i] * t0 + sc->cs[i] * t1;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double r = sqrt(a * a + b * b);
+  sc->cs[j] = (r == 0.0) ? 1.0 : a / r;
+  sc->sn[j] = (r == 0.0) ? 0.0 : b / r;
+  H[j * m + j] = r;
+  H[(j + 1) * m + j] = 0.0;
+  sc->gv[j + 1] = -sc->sn[j] * sc->gv[j];
+  sc->gv[j] = sc->cs[j] * sc->gv[j];
+  sc->iters += 1;
+  sc->jend = j + 1;
+  sc->relres = fabs(sc->gv[j + 1]) / sc->bnorm;
+  if (weak) {
+    sc->cycle_done = 1;
+  } else if (fabs(sc->gv[j + 1]) <= sc->eta * sc->bnorm || hn == 0.0) {
+    sc->converged = 1;
+    sc->cycle_done = 1;
+  } else {
+    sc->scale[j + 1] = 1.0 / hn;
+    if (j + 1 == m) sc->cycle_done = 1;
+  }
+  sc->j = j + 1;
+  if (sc->graph && j + 1 < m)
+    cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
+}
+
+// The same for the single-reduction step, with column j of H (h, before the rotations) in
+// registers: every scalar it needs is loaded first, as independent loads, so that the one
+// thread that runs it waits for one memory round trip instead of one per dependent access.
+template <int J>
+__device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn, bool weak) {
+  constexpr int j = J - 1;
+  double cs[J], sn[J];
+#pragma unroll
+  for (int i = 0; i < j; ++i) {
+    cs[i] = sc->cs[i];
+    sn[i] = sc->sn[i];
+  }
+  const double gvj = sc->gv[j], bnorm = sc->bnorm, eta = sc->eta;
+  const int m = sc->m, iters = sc->iters, graph = sc->graph;
+  double col[J + 1];
+#pragma unroll
+  for (int i = 0; i < J; ++i) col[i] = h[i];
+  col[J] = hn;
+#pragma unroll
+  for (int i = 0; i < j; ++i) {  // previous rotations on column j
+    const double t0 = col[i], t1 = col[i + 1];
+    col[i] = cs[i] * t0 + sn[i] * t1;
+    col[i + 1] = -sn[i] * t0 + cs[i] * t1;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double r = sqrt(a * a + b * b);
+  const double c = (r == 0.0) ? 1.0 : a / r, sj = (r == 0.0) ? 0.0 : b / r;
+  col[j] = r;
+  col[j + 1] = 0.0;
+#pragma unroll
+  for (int i = 0; i <= J; ++i) sc->H[i * m + j] = col[i];
+  sc->cs[j] = c;
+  sc->sn[j] = sj;
+  const double g1 = -sj * gvj;
+  sc->gv[j + 1] = g1;
+  sc->gv[j] = c * gvj;
+  sc->iters = iters + 1;
+  sc->jend = j + 1;
+  sc->relres = fabs(g1) / bnorm;
+  int done = 0;
+  if (weak) {
+    done = 1;
+  } else if (fabs(g1) <= eta * bnorm || hn == 0.0) {
+    sc->converged = 1;
+    done = 1;
+  } else {
+    sc->scale[j + 1] = 1.0 / hn;
+    if (j + 1 == m) done = 1;
+  }
+  if (done) sc->cycle_done = 1;
+  sc->j = j + 1;
+  if (graph && j + 1 < m) cudaGraphSetConditional(sc->h_step[j + 1], done ? 0u : 1u);
+}
+
 // Per-thread partial sums are kept in the vector precision T (a thread covers a few vectors
 // of 16 bytes); partials are combined across threads and blocks in FP64.
 template <typename T, int J>
 __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restrict__ w, long P,
                                        double* partials, DevScalars* sc, int pass) {
   constexpr int W = Vec16<T>::W;
-  T acc[J];
+  T acc[J + 1];  // V_i . w (i < J) and w . w
 #pragma unroll
-  for (int i = 0; i < J; ++i) acc[i] = (T)0;
+  for (int i = 0; i <= J; ++i) acc[i] = (T)0;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
   for (long q = tid; q < PV; q += nth) {
@@ -1044,31 +1181,52 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
 #pragma unroll
       for (int k = 0; k < W; ++k) acc[i] += x[k] * wv[k];
     }
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[J] += wv[k] * wv[k];
   }
   for (long p = PV * W + tid; p < P; p += nth) {
     const T wp = w[p];
 #pragma unroll
     for (int i = 0; i < J; ++i) acc[i] += V[(size_t)i * P + p] * wp;
+    acc[J] += wp * wp;
   }
-  double v[J];
+  double v[J + 1];
   if constexpr (sizeof(T) == 4) {
-    if (!grid_sum_f<J>(acc, partials, &sc->ticket[TK_DOTS])) return;
+    if (!grid_sum_f<J + 1>(acc, partials, &sc->ticket[TK_DOTS])) return;
 #pragma unroll
-    for (int i = 0; i < J; ++i) v[i] = (double)acc[i];
+    for (int i = 0; i <= J; ++i) v[i] = (double)acc[i];
   } else {
-    int kind[J];
+    int kind[J + 1];
 #pragma unroll
-    for (int i = 0; i < J; ++i) {
+    for (int i = 0; i <= J; ++i) {
       v[i] = (double)acc[i];
       kind[i] = 0;
     }
-    block_reduce<J>(v, kind);
-    if (!publish_partials<J>(v, partials, &sc->ticket[TK_DOTS])) return;
-    reduce_partials<J>(v, kind, partials, gridDim.x);
+    block_reduce<J + 1>(v, kind);
+    if (!publish_partials<J + 1>(v, partials, &sc->ticket[TK_DOTS])) return;
+    reduce_partials<J + 1>(v, kind, partials, gridDim.x);
   }
   if (threadIdx.x == 0) {
     const int m = sc->m, j = J - 1;
-    if (pass == 0) {
+    if (pass == 0 && !sc->reorth) {
+      // one reduction per Arnoldi step: with v_i orthonormal, ||w - sum h_i v_i||^2 =
+      // ||w||^2 - sum h_i^2 (Pythagoras), so the norm and the Givens rotation finish here
+      // and the update of w is a plain elementwise pass (mode 3) that ends no reduction.
+      // The difference loses accuracy when w lies almost in span(v_0..v_j); below 1e-6
+      // ||w||^2 (the FP32 sums' resolution) the cycle ends and the restart's explicit
+      // residual decides.
+      double h[J], hs = 0.0;
+#pragma unroll
+      for (int i = 0; i < J; ++i) h[i] = sc->scale[i] * v[i];
+#pragma unroll
+      for (int i = 0; i < J; ++i) {
+        sc->hcol[i] = h[i];
+        hs += h[i] * h[i];
+      }
+      const double ww = v[J], hn2 = ww - hs;
+      const bool weak = !(hn2 > 1e-6 * ww);
+      arnoldi_close_j<J>(sc, h, weak ? 0.0 : sqrt(hn2), weak);
+    } else if (pass == 0) {
 #pragma unroll
       for (int i = 0; i < J; ++i) sc->H[i * m + j] = sc->scale[i] * v[i];
     } else {
@@ -1106,7 +1264,8 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   T coefs[J];
 #pragma unroll
   for (int i = 0; i < J; ++i)
-    coefs[i] = (T)((mode == 2 ? sc->h2[i] : sc->H[i * m + j]) * sc->scale[i]);
+    coefs[i] = (T)((mode == 2 ? sc->h2[i] : (mode == 3 ? sc->hcol[i] : sc->H[i * m + j])) *
+                   sc->scale[i]);
   T* Vn = V + (size_t)(j + 1) * P;
   const T* src = (mode == 2) ? Vn : w;
   T acc = (T)0;
@@ -1134,7 +1293,9 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     Vn[p] = x;
     acc += x * x;
   }
-  if (mode == 1) return;  // first of two passes: the norm follows the second
+  // mode 1: first of two passes, the norm follows the second; mode 3: the norm and the
+  // rotation were finished by the multi-dot (Pythagoras)
+  if (mode == 1 || mode == 3) return;
   double v[1] = {(double)acc};
   if constexpr (sizeof(T) == 4) {
     float a[1] = {acc};
@@ -1147,34 +1308,7 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     reduce_partials<1>(v, kind, partials, gridDim.x);
   }
   if (threadIdx.x == 0) {
-    double* H = sc->H;
-    const double hn = sqrt(v[0]);
-    H[(j + 1) * m + j] = hn;
-    for (int i = 0; i < j; ++i) {  // previous rotations on column j
-      const double t0 = H[i * m + j], t1 = H[(i + 1) * m + j];
-      H[i * m + j] = sc->cs[i] * t0 + sc->sn[i] * t1;
-      H[(i + 1) * m + j] = -sc->sn[i] * t0 + sc->cs[i] * t1;
-    }
-    const double a = H[j * m + j], b = H[(j + 1) * m + j];
-    const double r = sqrt(a * a + b * b);
-    sc->cs[j] = (r == 0.0) ? 1.0 : a / r;
-    sc->sn[j] = (r == 0.0) ? 0.0 : b / r;
-    H[j * m + j] = r;
-    H[(j + 1) * m + j] = 0.0;
-    sc->gv[j + 1] = -sc->sn[j] * sc->gv[j];
-    sc->gv[j] = sc->cs[j] * sc->gv[j];
-    sc->iters += 1;
-    sc->jend = j + 1;
-    sc->relres = fabs(sc->gv[j + 1]) / sc->bnorm;
-    if (fabs(sc->gv[j + 1]) <= sc->eta * sc->bnorm || hn == 0.0) {
-      sc->converged = 1;
-      sc->cycle_done = 1;
-    } else {
-      sc->scale[j + 1] = 1.0 / hn;
-      if (j + 1 == m) sc->cycle_done = 1;
-    }
-    sc->j = j + 1;
-    if (sc->graph && j + 1 < m) cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
+    arnoldi_close(sc, j, sqrt(v[0]), false);
     sc->ticket[TK_UPDATE] = 0;
   }
 }
@@ -1183,7 +1317,8 @@ template <typename T>
 __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long P,
                                double* partials, DevScalars* sc, int mode) {
   if (sc->cycle_done) return;
-  switch (sc->j) {
+  // mode 3 runs after the multi-dot closed the step (sc->j already advanced)
+  switch (mode == 3 ? sc->j - 1 : sc->j) {
 #define OTGB_UPD_CASE(k) \
   case k:                \
     update_j<T, k + 1>(V, w, P, partials, sc, mode); break;
@@ -1195,15 +1330,24 @@ __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long 
   }
 }
 
-// y = R^{-1} g by back substitution (one thread)
+// y = R^{-1} g by back substitution: the 32 threads stage R and g in shared memory (one
+// round of independent loads), thread 0 solves there
 __global__ void k_gmres_finish(DevScalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double R[OTGB_MAXM * OTGB_MAXM], g[OTGB_MAXM], y[OTGB_MAXM];
+  if (blockIdx.x != 0) return;
   const int n = sc->jend, m = sc->m;
-  for (int i = n - 1; i >= 0; --i) {
-    double s = sc->gv[i];
-    for (int k = i + 1; k < n; ++k) s -= sc->H[i * m + k] * sc->y[k];
-    sc->y[i] = s / sc->H[i * m + i];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = sc->H[(e / n) * m + e % n];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) g[e] = sc->gv[e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < n; ++k) s -= R[i * n + k] * y[k];
+      y[i] = s / R[i * n + i];
+    }
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) sc->y[e] = y[e];
 }
 
 cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st) {

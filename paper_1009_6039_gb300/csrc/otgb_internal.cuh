@@ -38,6 +38,7 @@ struct DevScalars {
   double cs[OTGB_MAXM], sn[OTGB_MAXM], gv[OTGB_MAXM + 1], y[OTGB_MAXM];
   double scale[OTGB_MAXM + 1];  // V_i is stored unnormalised; v_i = scale[i] * V_i
   double h2[OTGB_MAXM];         // second Gram-Schmidt pass (reorthogonalisation)
+  double hcol[OTGB_MAXM];       // column j of H before the rotations (the update's weights)
   double relres;
   int j, jend, m, cycle_done, converged, iters, cycles;
   double eta, tau;
