@@ -189,6 +189,11 @@ __device__ void block_reduce_dd(dd (&v)[NV], const int (&kind)[NV]) {
   }
   __syncthreads();
 }
+// a double as (hi, lo) floats; infinities keep lo = 0
+__device__ __forceinline__ dd dd_of_double(double a) {
+  const float h = __double2float_rn(a);
+  return dd{h, isfinite(h) ? __double2float_rn(a - (double)h) : 0.0f};
+}
 // grid-wide: per-block (hi, lo) partials, the last block to take a ticket combines them in
 // block order; true in that block, totals in thread 0 (2-D grids allowed)
 template <int NV>
@@ -239,10 +244,14 @@ __global__ void k_input_stats(const double* __restrict__ f, const double* __rest
     v[4] += isfinite(a) ? 0.0 : 1.0;
     v[5] += isfinite(b) ? 0.0 : 1.0;
   }
-  block_reduce<6>(v, kind);
-  if (!publish_partials<6>(v, partials, &sc->ticket[TK_INPUT])) return;
-  reduce_partials<6>(v, kind, partials, gridDim.x);
+  // per-thread FP64, then the block and grid reductions in double-float (FP32 pipes)
+  dd r[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) r[a] = dd_of_double(v[a]);
+  if (!grid_reduce_dd<6>(r, kind, partials, &sc->ticket[TK_INPUT])) return;
   if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) v[a] = (double)r[a].hi + (double)r[a].lo;
     sc->in_mean[0] = v[0] / (double)P;
     sc->in_mean[1] = v[1] / (double)P;
     sc->in_min[0] = v[2];
@@ -1001,9 +1010,17 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
     if (sigma) sigma[p] = (T)0;
-    double b = (Fraw[p] + s) * inv_tau;  // h = (f - f~_n) / tau
-    if (restart) b -= (double)w[p];
-    const T bt = (T)b;
+    T bt;
+    if constexpr (sizeof(T) == 4) {
+      // the shifted residual in FP64 (one add), the rest in the vector precision
+      float b = __double2float_rn(Fraw[p] + s) * (float)inv_tau;  // h = (f - f~_n) / tau
+      if (restart) b -= w[p];
+      bt = b;
+    } else {
+      double b = (Fraw[p] + s) * inv_tau;
+      if (restart) b -= (double)w[p];
+      bt = (T)b;
+    }
     V0[p] = bt;
     acc += bt * bt;
   }
