@@ -174,6 +174,22 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 RESIDUAL_FP64_FLOPS_PER_POINT = 117
 
 
+def variant_names(v):
+    """The FP32 transform kernels the autotuner chose (OT_OPT_FFT_VARIANT encoding)."""
+    if v is None or v < 0:
+        return None
+    v = int(v)
+    r, c, b = v % 4, (v // 4) % 4, (v // 16) % 4
+    row = {0: "k_row_r2c<float, 8>", 1: "k_row_r2c<float, 8>", 2: "k_row_r2c_w<float>",
+           3: "k_row_r2c<float, 4>"}
+    col = {0: "k_col<float, 8, 2>", 1: "k_col_matvec_par<float, 8>", 2: "k_col_matvec_w<float>",
+           3: "k_col<float, 4, 2>"}
+    comb = {0: "k_row_c2r<float, 8, 1>", 1: "k_row_combine_par<float, 8>",
+            2: "k_row_combine_w<float>", 3: "k_row_c2r<float, 4, 1>"}
+    return {"code": v, "row_r2c": row[r], "col_matvec": col[c], "row_c2r_combine": comb[b],
+            "col_q4": bool(v & 64)}
+
+
 def traffic_for(kernel_cls, size):
     """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
     taken on the current source of that kernel and this size; else None."""
@@ -525,7 +541,8 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": bytes_launch}
     roof.update({"traffic": traffic_for(dom, N), "avg_launch_ms": dom_ms,
                  "launches_per_solve": prof[dom][1],
-                 "share_of_solve_ms": per_solve[dom] / (ms / args.steps)})
+                 "share_of_solve_ms": per_solve[dom] / (ms / args.steps),
+                 "fft_variant": variant_names(plan.get("fft_variant"))})
     kernels = {k: {"ms_per_launch": round(timed[k], 5), "launches_per_solve": prof[k][1],
                    "ms_per_solve": round(per_solve[k], 3),
                    "algorithmic_GBps": round(algorithmic_bytes(k, P, T, avg_basis)

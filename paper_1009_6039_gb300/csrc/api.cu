@@ -108,6 +108,9 @@ static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
 
+// Arnoldi steps per GMRES cycle captured as plain kernels rather than IF nodes (graph)
+constexpr int kUncondSteps = 4;
+
 static cudaEvent_t ev_get(ot_plan* p) {
   if (!p->pool.empty()) {
     cudaEvent_t e = p->pool.back();
@@ -1161,7 +1164,16 @@ static int capture_solve(ot_plan* p) {
   RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_cycle, &b2));
   RET(begin_body(p, 2, b2));
   LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream, 1));
+  // The first steps of a cycle are plain kernels that skip themselves once the cycle is done
+  // (a conditional IF node costs ~5 us per execution, more than the early-exiting launches
+  // of the few steps a short cycle leaves); later steps sit in IF nodes.
+  const int K = p->m < kUncondSteps ? p->m : kUncondSteps;
   for (int j = 0; j < p->m; ++j) {
+    if (j < K) {
+      p->h_step[j] = 0;
+      RET(run_arnoldi_step<T>(p, j, &p->sc->cycle_done));
+      continue;
+    }
     RET(add_conditional(p->cs[2], cudaGraphCondTypeIf, &p->h_step[j], &b3));
     RET(begin_body(p, 3, b3));
     RET(run_arnoldi_step<T>(p, j, nullptr));
@@ -1199,9 +1211,9 @@ static int capture_solve(ot_plan* p) {
 
 // ------------------------------------------------------------------------------------------
 // Autotuner of the FP32 matvec passes: each variant (generic / concurrent transforms /
-// warp-synchronous radix-32) of the row R2C, column and row combine passes is launched back
-// to back on the plan's own buffers and timed with CUDA events; the fastest is kept, and
-// the choice is cached per (N, M) for the process.
+// warp-synchronous radix-32 / 4 elements per thread) of the row R2C, column and row combine
+// passes is launched back to back on the plan's own buffers and timed with CUDA events; the
+// fastest is kept, and the choice is cached per (N, M) for the process.
 // ------------------------------------------------------------------------------------------
 static std::mutex g_tune_mutex;
 static std::vector<std::vector<int>> g_tune_cache;  // {N, M, r2c, col, comb}
@@ -1247,10 +1259,12 @@ static int run_autotune(ot_plan* p) {
                                    (C2<float>*)p->q2, (const float*)p->coef, (float*)p->w,
                                    nullptr, nullptr, 0.0, 1.0, N, M, tb, nullptr, st);
     };
-    for (int r = 0; r < 2; ++r)
+    // 3 warm-up and 30 timed launches: the candidates are within a few percent of each other
+    // at the sizes of interest, and 10 launches let launch jitter flip the choice
+    for (int r = 0; r < 3; ++r)
       if (one() != cudaSuccess) return 1e30f;
     cudaEventRecord(a, st);
-    for (int r = 0; r < 10; ++r)
+    for (int r = 0; r < 30; ++r)
       if (one() != cudaSuccess) return 1e30f;
     cudaEventRecord(b, st);
     if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
@@ -1367,6 +1381,7 @@ static void graph_scalars(ot_plan* p, DevScalars* h) {
   h->h_restart = p->h_restart;
   h->h_halve = p->h_halve;
   for (int k = 0; k < OTGB_MAXM; ++k) h->h_step[k] = p->h_step[k];
+  h->steps_uncond = p->m < kUncondSteps ? p->m : kUncondSteps;
 }
 
 // Enqueue one graph-launched solve on stream xs: inputs into the plan's buffers, the initial

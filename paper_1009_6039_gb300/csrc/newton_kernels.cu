@@ -1119,7 +1119,7 @@ __device__ void arnoldi_close(DevScalars* sc, int j, double hn, bool weak) {
     if (j + 1 == m) sc->cycle_done = 1;
   }
   sc->j = j + 1;
-  if (sc->graph && j + 1 < m)
+  if (sc->graph && j + 1 < m && sc->h_step[j + 1])
     cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
 }
 
@@ -1137,6 +1137,7 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
   }
   const double gvj = sc->gv[j], bnorm = sc->bnorm, eta = sc->eta;
   const int m = sc->m, iters = sc->iters, graph = sc->graph;
+  const unsigned long long hnext = j + 1 < OTGB_MAXM ? sc->h_step[j + 1] : 0ull;
   double col[J + 1];
 #pragma unroll
   for (int i = 0; i < J; ++i) col[i] = h[i];
@@ -1174,7 +1175,7 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
   }
   if (done) sc->cycle_done = 1;
   sc->j = j + 1;
-  if (graph && j + 1 < m) cudaGraphSetConditional(sc->h_step[j + 1], done ? 0u : 1u);
+  if (graph && j + 1 < m && hnext) cudaGraphSetConditional(hnext, done ? 0u : 1u);
 }
 
 // Per-thread partial sums are kept in the vector precision T (a thread covers a few vectors
@@ -1502,6 +1503,9 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
       set_cond(sc, sc->h_step[0], sc->converged ? 0u : 1u);
       break;
     case CTL_CYCLE_END: {
+      // the unconditional Arnoldi steps a short cycle left also launched (and skipped)
+      if (sc->jend < sc->steps_uncond)
+        sc->kcount += (sc->reorth ? 7LL : 5LL) * (sc->steps_uncond - sc->jend);
       const int cont = (!sc->converged && sc->cycles < sc->max_restarts) ? 1 : 0;
       set_cond(sc, sc->h_cycle, cont);
       set_cond(sc, sc->h_restart, cont);
