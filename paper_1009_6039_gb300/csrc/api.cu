@@ -366,7 +366,7 @@ static int alloc_buffers(ot_plan* p) {
   int sms = 0;
   CK(cudaGetDevice(&p->device));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  p->kblocks = (sms > 0 ? sms : 148) * 2;
+  p->kblocks = (sms > 0 ? sms : 148);  // GMRES vector kernels: 1 block of 256 per SM
   p->sms = sms > 0 ? sms : 148;
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
   size_t nk = (size_t)p->kblocks * OTGB_MAXM;
