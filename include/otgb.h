@@ -202,7 +202,10 @@ int ot_plan_time_kernel(ot_plan* plan, int32_t kernel_class, int32_t reps, doubl
 
 /* Coefficients c of the periodic cubic B-spline interpolant of g (sum over the 4 x 4 taps
  * of c times the B-spline weights reproduces g at the nodes), used to sample g at the
- * displaced points x + grad phi (Sec. 4).  Computed in FP64 by a spectral division. */
+ * displaced points x + grad phi (Sec. 4).  Computed in FP64 as the exact periodic inverse of
+ * the stencil (1, 4, 1)/6 along each axis, by first-order recursive filters (pole
+ * sqrt(3) - 2); c and g are device N x M row-major; the plan's residual buffer is used as
+ * scratch.  Returns OT_EINVAL for null pointers or an unready plan. */
 int ot_prefilter(ot_plan* plan, const double* g, double* c);
 
 /* Residual and linearised coefficients at the iterate u (Eq. ma2, linearmaeq,

@@ -1606,7 +1606,7 @@ extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const doub
 // step-level entry points
 // ------------------------------------------------------------------------------------------
 extern "C" int ot_prefilter(ot_plan* p, const double* g, double* c) {
-  if (!p || !g || !c) return OT_EINVAL;
+  if (!p || !p->ready || !g || !c) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
   RET(run_prefilter(p, g, c));
   CK(cudaStreamSynchronize(p->stream));
