@@ -241,7 +241,7 @@ int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
  * Not in the paper, which starts Newton from u0 = 0 and needs only an admissible start,
  * det(I + D^2 u0) > 0 (Thm 3.2).  After the input translation (Eq. translation):
  *   h  = P(log f - log g), P the mean-zero inverse of the 4th-order stencil Laplacian
- *        D_xx + D_yy of Sec. 4.1 (the linearisation of log det(I + D^2 u) + log g(x + grad u)
+ *        D_xx + D_yy of Sec. 4 (the linearisation of log det(I + D^2 u) + log g(x + grad u)
  *        = log f about u = 0);
  *   X  = 16 features per grid point at h: [log f, log g, lg, r, hxx + hyy, hxx - hyy, 2 hxy,
  *        hxx hyy - hxy^2, 10 hx, 10 hy, 0.1 Gx / Gc, 0.1 Gy / Gc, (Gx hx + Gy hy) / Gc,

@@ -288,7 +288,7 @@ static int reduce_blocks() {
 }
 
 // ---------------------------------------------------------------------------------------
-// Cubic B-spline prefilter (Sec. 4.1: the coefficients c of the interpolant of g, with
+// Cubic B-spline prefilter (Sec. 4, interpolation of g: the coefficients c, with
 // (c[k-1] + 4 c[k] + c[k+1]) / 6 = g[k] along each axis, periodic) as recursive filters.
 // The periodic inverse of the stencil (1, 4, 1) / 6 is 6 h * with h[k] = z z^|k| / (z^2 - 1),
 // z = sqrt(3) - 2 the root of z^2 + 4 z + 1 inside the unit circle (its DTFT is
