@@ -223,6 +223,24 @@ def test_solve_manufactured_mixed(ot, N):
     assert s["res_inf"] < 1e-9
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("symbols", [0, 1])
+def test_solve_uniform_target_breakdown_path(ot, prec, symbols):
+    # g = 1: at u = 0 the coefficients are a = I, b = 0, so L = Lbar and the preconditioned
+    # operator is the identity.  The first Arnoldi step then has w in span(v_0): the
+    # single-reduction step finds ||w||^2 - h^2 at round-off level, ends the cycle without a
+    # convergence claim, and the restart's explicit residual (zero) finishes the linear solve.
+    # The solve must still reach the oracle's root.
+    N = 64
+    f = I.blob_density(N, N, 31)
+    g = np.ones((N, N))
+    with O.fd_symbols(symbols):
+        u_ref, st_ref, _, _ = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-4)
+    rc, st, phi = _gpu_solve(ot, f, g, prec, eta=1e-4, symbols=symbols)
+    assert st_ref["status"] == 0 and rc == 0 and st["res_inf"] < 1e-10
+    assert np.abs(phi - u_ref).max() <= (1e-10 if prec == "fp64" else 1e-6)
+
+
 @pytest.mark.parametrize("N,M", [(32, 32), (48, 64), (64, 48)])
 def test_solve_blob_pair_fp64_with_safeguard(ot, N, M):
     # Long safeguarded runs with an inexact inner solve (eta = 1e-2) may take a different
