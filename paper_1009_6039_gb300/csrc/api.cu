@@ -39,7 +39,7 @@ struct ot_plan {
   void *spec = nullptr, *q0 = nullptr, *q1 = nullptr, *q2 = nullptr;
   // FP64 spectrum used by the prefilter when the inner precision is FP32
   void *spec64 = nullptr, *q64 = nullptr;
-  void *tw64 = nullptr, *tw32 = nullptr;  // twiddle tables (L, M/2, N entries)
+  void *tw64 = nullptr, *tw32 = nullptr;  // twiddles: M/2 row (base + 3 stage tables), W_M, N column (base + 3)
   void* twdd = nullptr;                    // the same as (hi, lo) float pairs
   void *sym64 = nullptr, *sym32 = nullptr;  // derivative symbol tables (M/2 + 1 + N pairs)
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
@@ -268,6 +268,46 @@ static void roots(int L, int count, std::vector<double>& out) {
   }
 }
 
+// Stage-ordered twiddles of the Stockham transform of length L with E elements per thread
+// (the kernels' radix sequence: a radix-3 stage first for E = 12, then radix 8 while it
+// divides for E = 8, else 4, else 2): stage (Ns, R) holds exp(-2 pi i k r / (Ns R)),
+// r = 1..R-1, k = 0..Ns-1, at (Ns - 1) + (r - 1) Ns + k.  L entries; zero where the width
+// does not apply to L (E = 12 needs the factor 3, E = 4 and 8 exclude it).
+static void stage_roots(int L, int E, std::vector<double>& out) {
+  std::vector<double> t(2 * (size_t)L, 0.0);
+  if ((E == 12) == (L % 3 == 0)) {
+    int Ns = 1, rem = L;
+    auto stage = [&](int R) {
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const double a = 2.0 * M_PI * (double)k * (double)r / ((double)Ns * (double)R);
+          const size_t i = (size_t)(Ns - 1) + (size_t)(r - 1) * Ns + k;
+          t[2 * i] = std::cos(a);
+          t[2 * i + 1] = -std::sin(a);
+        }
+      Ns *= R;
+      rem /= R;
+    };
+    if (E % 3 == 0) stage(3);
+    while (rem > 1) {
+      if (E % 8 == 0 && rem % 8 == 0)
+        stage(8);
+      else if (rem % 4 == 0)
+        stage(4);
+      else
+        stage(2);
+    }
+  }
+  out.insert(out.end(), t.begin(), t.end());
+}
+
+// a transform length's base table followed by its stage tables for E = 4, 8, 12 (the
+// layout fft_smem expects)
+static void transform_roots(int L, std::vector<double>& out) {
+  roots(L, L, out);
+  for (int E : {4, 8, 12}) stage_roots(L, E, out);
+}
+
 // (s1, s2) of frequency index k of length L (k <= L/2 for the half axis): spectral
 // 2 pi k (0 at Nyquist) and -(2 pi k)^2 (Sec. 4.2, reading R4), or the Fourier symbols of the
 // 4th-order stencils (8 sin t - sin 2t) L / 6 and (-2 cos 2t + 32 cos t - 30) L^2 / 12,
@@ -335,10 +375,11 @@ static int alloc_buffers(ot_plan* p) {
     p->q64 = nullptr;
   }
   // twiddle tables
+  // [row FFT length M/2 (4 L) | split W_M^k, k < M/2 (L) | column FFT length N (4 N)]
   std::vector<double> tw;
-  roots((int)L, (int)L, tw);      // row FFT length M/2
-  roots(p->M, (int)L, tw);        // split W_M^k, k < M/2
-  roots(p->N, p->N, tw);          // column FFT length N
+  transform_roots((int)L, tw);
+  roots(p->M, (int)L, tw);
+  transform_roots(p->N, tw);
   const size_t ntw = tw.size() / 2;
   CK(cudaMalloc(&p->tw64, ntw * 16));
   CK(cudaMemcpy(p->tw64, tw.data(), ntw * 16, cudaMemcpyHostToDevice));
@@ -354,15 +395,15 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaMalloc(&p->twdd, ntw * 16));
   CK(cudaMemcpy(p->twdd, twd.data(), ntw * 16, cudaMemcpyHostToDevice));
   p->tbdd.twL = p->twdd;
-  p->tbdd.twM = (const ddc*)p->twdd + L;
-  p->tbdd.twN = (const ddc*)p->twdd + 2 * L;
+  p->tbdd.twM = (const ddc*)p->twdd + 4 * L;
+  p->tbdd.twN = (const ddc*)p->twdd + 5 * L;
   RET(fill_symbols(p));
   p->tb64.twL = p->tw64;
-  p->tb64.twM = (const double2*)p->tw64 + L;
-  p->tb64.twN = (const double2*)p->tw64 + 2 * L;
+  p->tb64.twM = (const double2*)p->tw64 + 4 * L;
+  p->tb64.twN = (const double2*)p->tw64 + 5 * L;
   p->tb32.twL = p->tw32;
-  p->tb32.twM = (const float2*)p->tw32 + L;
-  p->tb32.twN = (const float2*)p->tw32 + 2 * L;
+  p->tb32.twM = (const float2*)p->tw32 + 4 * L;
+  p->tb32.twN = (const float2*)p->tw32 + 5 * L;
   int sms = 0;
   CK(cudaGetDevice(&p->device));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));

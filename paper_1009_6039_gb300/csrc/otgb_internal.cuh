@@ -96,6 +96,8 @@ enum ColMode {
 enum RowInvMode { ROWINV_PLAIN = 0, ROWINV_COMBINE = 1, ROWINV_UPDATE = 2 };
 
 struct SpecTables {
+  // twL and twN are each followed by the stage-ordered tables of widths 4, 8, 12 (one
+  // transform length each; see stage_table_slot in spectral.cuh)
   const void* twL;  // exp(-2 pi i t / (M/2)), t < M/2 (row transforms)
   const void* twM;  // exp(-2 pi i k / M), k < M/2 (real-to-complex split)
   const void* twN;  // exp(-2 pi i t / N), t < N (column transforms)

@@ -111,12 +111,22 @@ template <typename T, int SIGN> struct Bfly<T, 8, SIGN> {
 __host__ __device__ constexpr int FB(int L) { return L + (L >> 4) + 1; }
 __device__ __forceinline__ int spad(int i, bool on) { return on ? i + (i >> 4) : i; }
 
+// Stage-ordered twiddle tables.  A base table of length L (exp(-2 pi i t / L), t < L) is
+// followed by one stage table per thread width E = 4, 8, 12 (L entries each; only the width
+// the length allows is filled): the stage with span Ns and radix R holds exp(-2 pi i k r /
+// (Ns R)) for r = 1..R-1, k = 0..Ns-1 at (Ns - 1) + (r - 1) Ns + k (the stages before it hold
+// sum Ns'(R' - 1) = Ns - 1 entries).  The threads of a warp take consecutive k, so a stage's
+// twiddle loads are contiguous instead of the strided k r L / (Ns R) of the base table.
+template <int E> __host__ __device__ constexpr int stage_table_slot() {
+  return E == 4 ? 1 : (E == 8 ? 2 : 3);
+}
+
 // One Stockham stage of radix R on a transform of length L held in buf (all threads of
 // the block must call it; inactive threads only take part in the barriers).  pin / pout:
-// the stage reads / writes the padded layout.
+// the stage reads / writes the padded layout.  st: the stage table of this width.
 template <typename T, int E, int R, int SIGN>
 __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t, bool active,
-                                               const C2<T>* __restrict__ tw, bool pin,
+                                               const C2<T>* __restrict__ st, bool pin,
                                                bool pout) {
   const int TPT = L / E;
   const int LR = L / R;
@@ -131,7 +141,6 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
   }
   __syncthreads();
   if (active) {
-    const int tstep = L / (Ns * R);
     // Ns = 2^a or 3 * 2^a: j / Ns by a shift (and a division by the constant 3)
     const int a = __ffs(Ns) - 1;
     const bool pow2 = (Ns >> a) == 1;
@@ -140,11 +149,13 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
       const int j = t + b * TPT;
       const int qd = pow2 ? (j >> a) : ((j >> a) / 3);
       const int k = j - qd * Ns;
+      if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C2<T> w = tw[k * r * tstep];
-        if (SIGN > 0) w.y = -w.y;
-        v[b * R + r] = cmul<T>(v[b * R + r], w);
+        for (int r = 1; r < R; ++r) {
+          C2<T> w = st[(Ns - 1) + (r - 1) * Ns + k];
+          if (SIGN > 0) w.y = -w.y;
+          v[b * R + r] = cmul<T>(v[b * R + r], w);
+        }
       }
       Bfly<T, R, SIGN>::run(&v[b * R]);
       const int d = qd * Ns * R + k;
@@ -161,7 +172,7 @@ __device__ __forceinline__ void stockham_stage(C2<T>* buf, int L, int Ns, int t,
 template <typename T, int E, int R, int SIGN, int NB>
 __device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], int L, int Ns,
                                                      int t, bool active,
-                                                     const C2<T>* __restrict__ tw, bool pin,
+                                                     const C2<T>* __restrict__ st, bool pin,
                                                      bool pout) {
   const int TPT = L / E;
   const int LR = L / R;
@@ -180,7 +191,6 @@ __device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], i
   }
   __syncthreads();
   if (active) {
-    const int tstep = L / (Ns * R);
     const int a = __ffs(Ns) - 1;
     const bool pow2 = (Ns >> a) == 1;
 #pragma unroll
@@ -188,12 +198,14 @@ __device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], i
       const int j = t + b * TPT;
       const int qd = pow2 ? (j >> a) : ((j >> a) / 3);
       const int k = j - qd * Ns;
+      if (Ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C2<T> w = tw[k * r * tstep];
-        if (SIGN > 0) w.y = -w.y;
+        for (int r = 1; r < R; ++r) {
+          C2<T> w = st[(Ns - 1) + (r - 1) * Ns + k];
+          if (SIGN > 0) w.y = -w.y;
 #pragma unroll
-        for (int q = 0; q < NB; ++q) v[q][b * R + r] = cmul<T>(v[q][b * R + r], w);
+          for (int q = 0; q < NB; ++q) v[q][b * R + r] = cmul<T>(v[q][b * R + r], w);
+        }
       }
 #pragma unroll
       for (int q = 0; q < NB; ++q) Bfly<T, R, SIGN>::run(&v[q][b * R]);
@@ -211,7 +223,8 @@ __device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], i
 
 template <typename T, int E, int SIGN, int NB>
 __device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, int t,
-                                               bool active, const C2<T>* __restrict__ tw) {
+                                               bool active, const C2<T>* __restrict__ twb) {
+  const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
   int Ns = 1;
   int rem = L;
   if (E % 3 == 0) {
@@ -241,7 +254,8 @@ __device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, 
 // Radix sequence: [3,] then 8s (E = 8) or 4s (E = 12), then the remaining 4 or 2.
 template <typename T, int E, int SIGN>
 __device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
-                                         const C2<T>* __restrict__ tw) {
+                                         const C2<T>* __restrict__ twb) {
+  const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
   int Ns = 1;
   int rem = L;
   if (E % 3 == 0) {
