@@ -305,14 +305,27 @@ __global__ void __launch_bounds__(256)
     last = atomicAdd(ticket, 1u) == nb - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
+  // the last block: all its threads take the per-block minima (strided, then a block tree)
+  float v4[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+  for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      v4[q] = fminf(v4[q], (float)((volatile const double*)partials)[(size_t)b * 4 + q]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float v = v4[q];
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[q][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   double a = 1.0, pick = 0.0;
   for (int q = 0; q < 4; ++q, a *= 0.5) {
-    double v = INFINITY;
-    for (unsigned int b = 0; b < nb; ++b)
-      v = fmin(v, ((volatile const double*)partials)[(size_t)b * 4 + q]);
-    if (v > 0.0) {
+    float v = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fminf(v, red[q][w]);
+    if (v > 0.0f) {
       pick = a;
       break;
     }
