@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--ws-weights", default=None,
                     help="load the warm-start network from this file instead of training")
     ap.add_argument("--ws-save", default=None, help="save the trained network to this file")
+    ap.add_argument("--fft-variant", type=int, default=None,
+                    help="fix the FP32 transform kernels (OT_OPT_FFT_VARIANT code) instead of "
+                         "autotuning; for profiler runs, where the autotuner's event timing is "
+                         "distorted")
     ap.add_argument("--batch-pairs", type=int, default=512)
     ap.add_argument("--plans-per-size", type=int, default=4)
     return ap.parse_args()
@@ -319,6 +323,8 @@ def run_ours(args):
     from paper_1009_6039_gb300 import warmstart as WS
     plan = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="mixed", stream=stream,
                    symbols=SYMBOLS)
+    if args.fft_variant is not None:
+        plan.set(fft_variant=args.fft_variant)
     if args.ws_weights:
         plan.load_weights(args.ws_weights)
         ws_info = {"weights": os.path.basename(args.ws_weights)}
