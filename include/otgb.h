@@ -237,7 +237,17 @@ int ot_fft_forward(ot_plan* plan, const double* x, double* spec);
 /* Inverse of ot_fft_forward without the 1/(N M) factor (spec -> N M x). */
 int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
 
-/* ---- Learned warm start -----------------------------------------------------------------
+/* Transport outputs (Sec. 5.2): *dist = d(f, g) = int |x - T(x)|^2 f dx = int |grad phi|^2 f dx
+ * with T = x + grad phi, as the grid mean of |grad phi|^2 f (the periodic trapezoid rule) with
+ * the 4th-order centred differences of F; and, when div_out is not NULL, div_out = phi_xx +
+ * phi_yy, the divergence of the displacement T(x) - x (the map the paper plots).  f, phi,
+ * div_out: device N x M row-major (f as given: pass the density the solve used, e.g. its
+ * translated form when it was not of mean 1); dist: HOST.  Double-float arithmetic (unit
+ * round-off 2^-48).  OT_EINVAL for null f, phi or dist or an unready plan. */
+int ot_transport_outputs(ot_plan* plan, const double* f, const double* phi, double* dist,
+                         double* div_out);
+
+/* ---- Learned warm start -----------------------------------------------------------------/* ---- Learned warm start -----------------------------------------------------------------
  * Not in the paper, which starts Newton from u0 = 0 and needs only an admissible start,
  * det(I + D^2 u0) > 0 (Thm 3.2).  After the input translation (Eq. translation):
  *   h  = P(log f - log g), P the mean-zero inverse of the 4th-order stencil Laplacian

@@ -122,6 +122,16 @@ def derivatives(u):
     return tuple(outs)
 
 
+def transport_outputs(f, u):
+    """Sec. 5.2: the transport distance d(f, g) = int |x - T(x)|^2 f dx = int |grad u|^2 f dx
+    with T = x + grad u, as the grid mean of |grad u|^2 f (the periodic trapezoid rule), and
+    the divergence of the displacement grad u, u_xx + u_yy; derivatives by the 4th-order
+    centred stencils of derivatives().  Returns (d, div)."""
+    f = _f64(f)
+    ux, uy, uxx, uyy, _ = derivatives(u)
+    return float(np.mean((ux * ux + uy * uy) * f)), uxx + uyy
+
+
 def bspline_coeffs(g):
     g = _f64(g)
     c = np.empty_like(g)

@@ -33,7 +33,7 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_pla
            "ot_plan_reset_profile", "ot_plan_time_kernel", "ot_eval_residual_noalloc",
            "ot_last_error", "ot_ws_param_count", "ot_ws_set_weights", "ot_warmstart_load",
            "ot_ws_save_weights", "ot_ws_predict", "ot_ws_features", "ot_ws_mlp_forward",
-           "ot_ws_poisson", "ot_ws_trainer_create", "ot_ws_trainer_set_stream",
+           "ot_ws_poisson", "ot_transport_outputs", "ot_ws_trainer_create", "ot_ws_trainer_set_stream",
            "ot_ws_trainer_grad", "ot_ws_trainer_step", "ot_ws_trainer_get_params",
            "ot_ws_trainer_destroy"]
 
@@ -93,6 +93,7 @@ def _load():
         "ot_ws_features": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "ot_ws_mlp_forward": ([vp, vp, ctypes.c_int64, vp], ctypes.c_int),
         "ot_ws_poisson": ([vp, vp, i32, vp], ctypes.c_int),
+        "ot_transport_outputs": ([vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp], ctypes.c_int),
         "ot_ws_trainer_create": ([ctypes.POINTER(vp), i32, vp, ctypes.c_int64], ctypes.c_int),
         "ot_ws_trainer_set_stream": ([vp, vp], ctypes.c_int),
         "ot_ws_trainer_grad": ([vp, vp, vp, vp, vp, vp], ctypes.c_int),
@@ -228,6 +229,10 @@ def ot_ws_features(plan, f_ptr, g_ptr, phi_star_ptr, X_ptr, target_ptr):
 
 def ot_ws_mlp_forward(plan, X_ptr, rows, out_ptr):
     return _lib.ot_ws_mlp_forward(plan, X_ptr, int(rows), out_ptr)
+
+
+def ot_transport_outputs(plan, f_ptr, phi_ptr, dist_ptr, div_ptr=None):
+    return _lib.ot_transport_outputs(plan, f_ptr, phi_ptr, dist_ptr, div_ptr)
 
 
 def ot_ws_poisson(plan, src_ptr, lowpass, u_ptr):
@@ -458,6 +463,16 @@ class Plan:
     def ws_poisson(self, src, u, lowpass=False):
         shp = (self.N, self.M)
         _check(ot_ws_poisson(self.h, _dev(src, shp), lowpass, _dev(u, shp)), "ot_ws_poisson")
+
+    def transport_outputs(self, f, phi, div=None):
+        """d(f, g) = mean |grad phi|^2 f (Sec. 5.2); fills div (device N x M) with
+        phi_xx + phi_yy when given.  Returns d."""
+        shp = (self.N, self.M)
+        d = ctypes.c_double()
+        _check(ot_transport_outputs(self.h, _dev(f, shp), _dev(phi, shp), ctypes.byref(d),
+                                    _dev(div, shp) if div is not None else None),
+               "ot_transport_outputs")
+        return d.value
 
     def close(self):
         if self.h:

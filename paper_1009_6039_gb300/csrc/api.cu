@@ -1908,6 +1908,18 @@ extern "C" int ot_ws_mlp_forward(ot_plan* p, const float* X, int64_t rows, float
   return OT_OK;
 }
 
+extern "C" int ot_transport_outputs(ot_plan* p, const double* f, const double* phi,
+                                    double* dist, double* div_out) {
+  if (!p || !p->ready || !f || !phi || !dist) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_transport(f, phi, p->N, p->M, div_out, p->partials,
+                          &p->sc->ticket[TK_TRANSPORT], &p->sc->dist, p->stream));
+  CK(cudaMemcpyAsync(dist, &p->sc->dist, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
 extern "C" int ot_ws_poisson(ot_plan* p, const double* src, int32_t lowpass, double* u) {
   if (!p || !p->ready || !src || !u) return OT_EINVAL;
   CK(cudaSetDevice(p->device));

@@ -57,6 +57,8 @@ struct DevScalars {
   // learned warm start: the scale alpha applied to the network's potential, and an error
   // flag set by the network kernel (a bounded wait that gave up)
   double ws_alpha;
+  // transport distance d(f, g) of ot_transport_outputs
+  double dist;
   int ws_err;
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
@@ -79,7 +81,16 @@ struct UPair {
   double* b;
 };
 
-enum { TK_INPUT = 0, TK_RESID = 1, TK_DOTS = 2, TK_UPDATE = 3, TK_INIT = 4, TK_NORM = 5, TK_WS = 6 };
+enum {
+  TK_INPUT = 0,
+  TK_RESID = 1,
+  TK_DOTS = 2,
+  TK_UPDATE = 3,
+  TK_INIT = 4,
+  TK_NORM = 5,
+  TK_WS = 6,
+  TK_TRANSPORT = 7
+};
 
 // Spectral kernels (instantiated for float and double) --------------------------------
 // COL_POISSON: divide by the eigenvalues of the 4th-order stencil Laplacian (0 at k = 0);
@@ -226,6 +237,11 @@ struct WsTrainBuffers {
   double *loss_part, *loss;        // ceil(B / 8) partials, mean squared error
 };
 cudaError_t launch_ws_source(const double* f, const double* g, double* src, long P,
+                             cudaStream_t st);
+// transport outputs: *dist (device) = mean |grad u|^2 f, div (optional) = u_xx + u_yy;
+// partials: one (hi, lo) pair per 32 x 32 tile
+cudaError_t launch_transport(const double* f, const double* u, int N, int M, double* div,
+                             double* partials, unsigned int* ticket, double* dist,
                              cudaStream_t st);
 // the same source in FP32 (input of the mixed-precision Poisson solve)
 cudaError_t launch_ws_source32(const double* f, const double* g, float* src, long P,

@@ -1,5 +1,6 @@
 // Learned warm start: the kernels of the network's input features, of its training (FP32)
-// and of its inference (BF16 on the tcgen05 tensor cores with an FP32 accumulator in TMEM).
+// and of its inference (BF16 on the tcgen05 tensor cores with an FP32 accumulator in TMEM);
+// also the transport outputs of Sec. 5.2, which share the tiled double-float stencils.
 //
 // The paper starts Newton from u0 = 0; the damped iteration only needs an admissible start,
 // det(I + D^2 u0) > 0 (Theorem convproof).  The warm start is
@@ -835,6 +836,75 @@ inline int nblk(long P, int t = 256) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
+// ---------------------------------------------------------------------------------------
+// Transport outputs (Sec. 5.2): the distance d(f, g) = int |x - T(x)|^2 f dx =
+// int |grad u|^2 f dx, T = x + grad u, as the grid mean of |grad u|^2 f (the periodic
+// trapezoid rule), and the divergence of the displacement, div = u_xx + u_yy, with the
+// residual's 4th-order stencils on the same double-float tiles.  Per-block (hi, lo) partial
+// sums; the last block to take a ticket adds them in block order with all its threads.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = dd_add(v, dd{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+__global__ void __launch_bounds__(256)
+    k_transport(const double* __restrict__ f, const double* __restrict__ u, int N, int M,
+                StencilK K, double* __restrict__ div, float2* __restrict__ partials,
+                unsigned int* ticket, double* dist) {
+  __shared__ TileDD T;
+  __shared__ float2 red[8];
+  __shared__ bool last;
+  const int bx = blockIdx.x * TW, by = blockIdx.y * TW;
+  tile_load_dd(T, u, N, M, by, bx);
+  const int tx = threadIdx.x % TW, ty0 = threadIdx.x / TW;
+  const int j = bx + tx;
+  dd acc = dd{0.f, 0.f};
+#pragma unroll 1
+  for (int rr = 0; rr < TRPT; ++rr) {
+    const int ty = ty0 + rr * (TW / TRPT);
+    const int i = by + ty;
+    if (i >= N || j >= M) continue;
+    dd ux, uy, uxx, uyy, uxy;
+    tile_stencils_dd(T, ty, tx, K, &ux, &uy, &uxx, &uyy, &uxy);
+    const size_t p = (size_t)i * M + j;
+    const dd g2 = dd_add(dd_mul(ux, ux), dd_mul(uy, uy));
+    acc = dd_add(acc, dd_mul(g2, dd_from_double(f[p])));
+    if (div) div[p] = dd_to_double(dd_add(uxx, uyy));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  acc = warp_sum_dd(acc);
+  if (lane == 0) red[wid] = make_float2(acc.hi, acc.lo);
+  __syncthreads();
+  const unsigned int nb = gridDim.x * gridDim.y;
+  if (threadIdx.x == 0) {
+    dd b = dd{0.f, 0.f};
+    for (int w = 0; w < nw; ++w) b = dd_add(b, dd{red[w].x, red[w].y});
+    partials[blockIdx.y * gridDim.x + blockIdx.x] = make_float2(b.hi, b.lo);
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == nb - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  dd s = dd{0.f, 0.f};
+  for (unsigned int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const volatile float2* q = (const volatile float2*)partials + b;
+    s = dd_add(s, dd{q->x, q->y});
+  }
+  s = warp_sum_dd(s);
+  if (lane == 0) red[wid] = make_float2(s.hi, s.lo);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    dd t = dd{0.f, 0.f};
+    for (int w = 0; w < nw; ++w) t = dd_add(t, dd{red[w].x, red[w].y});
+    *dist = dd_to_double(t) / ((double)N * (double)M);
+    *ticket = 0u;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -905,6 +975,14 @@ cudaError_t launch_ws_admissible(double* u, int N, int M, double* partials,
   if (e != cudaSuccess) return e;
   const long P = (long)N * M;
   k_ws_scale<<<nblk(P), 256, 0, st>>>(u, P, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transport(const double* f, const double* u, int N, int M, double* div,
+                             double* partials, unsigned int* ticket, double* dist,
+                             cudaStream_t st) {
+  k_transport<<<tiles(N, M), 256, 0, st>>>(f, u, N, M, stencil_consts(N, M), div,
+                                           reinterpret_cast<float2*>(partials), ticket, dist);
   return cudaGetLastError();
 }
 

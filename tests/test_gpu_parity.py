@@ -146,6 +146,27 @@ def test_operator_and_lbar_inverse(ot, N, M, prec, symbols):
     p.close()
 
 
+@pytest.mark.parametrize("N,M", [(16, 16), (24, 48), (128, 48), (192, 384), (256, 256),
+                                 (1024, 1024)])
+def test_transport_outputs(ot, N, M):
+    # Sec. 5.2 outputs: d = mean |grad u|^2 f and div = u_xx + u_yy, in double-float on the
+    # GPU.  d: the stencils' rounding (2^-48 relative to max|u| times sum|taps| M / 12) is
+    # far below the value (|grad u| ~ 2 pi k |u|), plus a log2(P)-deep double-float sum:
+    # 1e-11 relative.  div: the second-difference stencils cancel, 64 eps max|u| max(N,M)^2.
+    f = I.blob_density(N, M, 41)
+    u = smooth_field(N, M, amp=2e-3)
+    d_ref, div_ref = O.transport_outputs(f, u)
+    p = plan(ot, N, M, "mixed")
+    div = dev(np.zeros((N, M)))
+    d = p.transport_outputs(dev(f), dev(u), div)
+    assert abs(d - d_ref) <= 1e-11 * d_ref
+    tol = 64 * 2.0 ** -48 * np.abs(u).max() * max(N, M) ** 2
+    assert np.abs(div.cpu().numpy() - div_ref).max() <= tol
+    # without the map: the distance alone
+    assert abs(p.transport_outputs(dev(f), dev(u)) - d) <= 1e-15 * d
+    p.close()
+
+
 @pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512),
                                  (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
