@@ -98,6 +98,12 @@ extern "C" {
                                    bounded mbarrier wait runs out (tens of milliseconds); the
                                    kernel sets its error flag, frees its TMEM and returns and
                                    the call returns OT_ECUDA; resets itself after one call */
+#define OT_OPT_OPERATOR 21      /* linear operator of the Newton step: 0 (default) the full
+                                   linearisation of Eq. linearmaeq (a : D^2 theta + b . grad
+                                   theta, b = det(I + D^2 u) grad g(x + grad u)); 1 the
+                                   simplified g(x + grad u) Tr(Adj(I + D^2 u) D^2 theta) that
+                                   Sec. 3.3 reports working in practice (b = 0; the same root,
+                                   a different Newton path) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -75,6 +75,7 @@ def lib():
         _lib.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
         _lib.orc_fd_poisson.argtypes = [vp, i, i, i, vp]
         _lib.orc_set_fd_symbols.argtypes = [i]
+        _lib.orc_set_simplified.argtypes = [i]
         _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
     return _lib
 
@@ -273,4 +274,21 @@ class fd_symbols:
 
     def __exit__(self, *exc):
         lib().orc_set_fd_symbols(0)
+        return False
+
+
+class simplified_operator:
+    """Context manager: the residual's coefficients (and so the operator of apply_op and the
+    solve) drop the grad g term, b = 0: the simplified equation g(x + grad u) Tr(Adj(I +
+    D^2 u) D^2 theta) = (f - f_n) / tau that Sec. 3.3 reports working in practice."""
+
+    def __init__(self, on=True):
+        self.on = on
+
+    def __enter__(self):
+        lib().orc_set_simplified(int(bool(self.on)))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_simplified(0)
         return False

@@ -394,6 +394,11 @@ void orc_bspline_eval(const double *c, int N, int M, double x, double y, double 
  * coef (optional) holds 5 planes in the order a11, a12, a22, b1, b2.
  * scal (optional): [0] mean f_n, [1] max|F|, [2] sqrt(mean F^2), [3] min det,
  *                  [4] count of non-finite f_n. */
+/* simplified operator (Sec. 3.3 remark): g(x + grad u) Tr(Adj(I + D^2 u) D^2 theta), i.e. the
+ * coefficients b1 = b2 = 0; F itself is unchanged */
+static int g_simplified = 0;
+void orc_set_simplified(int on) { g_simplified = on ? 1 : 0; }
+
 int orc_residual(const double *f, const double *c, const double *u, int N, int M, double *F,
                  double *coef, double *scal) {
   long P = (long)N * M;
@@ -418,8 +423,8 @@ int orc_residual(const double *f, const double *c, const double *u, int N, int M
         coef[0 * P + p] = G * (1.0 + uyy);
         coef[1 * P + p] = -G * uxy;
         coef[2 * P + p] = G * (1.0 + uxx);
-        coef[3 * P + p] = det * Gx;
-        coef[4 * P + p] = det * Gy;
+        coef[3 * P + p] = g_simplified ? 0.0 : det * Gx;
+        coef[4 * P + p] = g_simplified ? 0.0 : det * Gy;
       }
     }
   double mean_fn = sum_fn / (double)P;

@@ -67,6 +67,8 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
 
 /* symbols of the linear operator: 0 spectral (Sec. 4.2, default), 1 those of the stencils */
 void orc_set_fd_symbols(int on);
+/* 1: residual coefficients b1 = b2 = 0 (the simplified operator of the Sec. 3.3 remark) */
+void orc_set_simplified(int on);
 
 /* learned warm start: FD Poisson solve and network features */
 #define ORC_WS_K 16

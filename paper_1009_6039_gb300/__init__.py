@@ -21,7 +21,7 @@ OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
-OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL = 18, 19, 20
+OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -361,7 +361,7 @@ class Plan:
              "theta_fp64": OT_OPT_THETA_FP64, "autotune": OT_OPT_AUTOTUNE,
              "fft_variant": OT_OPT_FFT_VARIANT, "symbols": OT_OPT_SYMBOLS,
              "forcing": OT_OPT_FORCING, "tau_retry": OT_OPT_TAU_RETRY,
-             "ws_test_stall": OT_OPT_WS_TEST_STALL}
+             "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

@@ -46,6 +46,7 @@ struct ot_plan {
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
   int tau_retry = 0;  // OT_OPT_TAU_RETRY: re-solves with doubled tau after a divergence
+  int op_simple = 0;  // OT_OPT_OPERATOR: 1 drops the grad g term of the linearisation
   int ws_stall = 0;   // OT_OPT_WS_TEST_STALL: the next ot_ws_mlp_forward stalls (test hook)
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
   // residual; hi is also the FP32 copy used for the interpolant's gradient)
@@ -103,9 +104,10 @@ static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
                                    int sel = 0) {
   if (sizeof(T) == 4)
     return launch_residual_dd(p->fdd, p->cdd, ua, p->N, p->M, Fraw, (float*)p->coef,
-                              p->partials, p->sc, p->stream, ub, sel);
+                              p->partials, p->sc, p->stream, ub, sel, p->op_simple);
   return launch_residual<double>(f, c, ua, p->N, p->M, Fraw, (double*)p->coef, p->partials,
-                                 p->sc, p->stream, ub, sel);}
+                                 p->sc, p->stream, ub, sel, nullptr, p->op_simple);
+}
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
 
@@ -554,6 +556,13 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (v != 0 && v != 1) return OT_EINVAL;
       p->ws_stall = (int)v;
       return OT_OK;
+    case OT_OPT_OPERATOR:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->op_simple != (int)v) {
+        p->op_simple = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_TAU_RETRY:
       if (!(v >= 0 && v <= 8) || v != (double)(int)v) return OT_EINVAL;
       p->tau_retry = (int)v;
@@ -605,6 +614,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_FORCING: *v = p->forcing; return OT_OK;
     case OT_OPT_TAU_RETRY: *v = p->tau_retry; return OT_OK;
     case OT_OPT_WS_TEST_STALL: *v = p->ws_stall; return OT_OK;
+    case OT_OPT_OPERATOR: *v = p->op_simple; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
       // autotuner has run (or in FP64 mode, which has one variant)

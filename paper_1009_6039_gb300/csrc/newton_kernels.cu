@@ -427,6 +427,7 @@ struct ResidConsts {
   double Mh, Nh, Mh2, Nh2;  // M/12, N/12, M^2/12, N^2/12
   double MNh;               // M N / 144
   double w3M, w3N;          // 1/(3M), 1/(3N): Simpson weights (2 or 4) x these
+  int nob;                  // 1: the simplified operator (b = 0, Sec. 3.3 remark)
 };
 
 template <typename G>
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     // coefficients of the linearisation (Jacobian only): precision T
     const T Gt = (T)G, dett = (T)det;
     const T a11 = Gt * ((T)1 + (T)uyy), a12 = -Gt * (T)uxy, a22 = Gt * ((T)1 + (T)uxx);
-    const T b1 = dett * Gx, b2 = dett * Gy;
+    const T b1 = K.nob ? (T)0 : dett * Gx, b2 = K.nob ? (T)0 : dett * Gy;
     coef[p] = a11;
     coef[P + p] = a12;
     coef[2 * P + p] = a22;
@@ -656,6 +657,7 @@ struct ResidConstsDD {
   dd inv36;                  // 1/36 (the value weights are computed x6 per axis)
   float M, N;
   float w3M, w3N;            // 1/(3M), 1/(3N)
+  int nob;                   // 1: the simplified operator (b = 0)
 };
 
 __device__ __forceinline__ dd ldd(const float2* __restrict__ a, size_t i) {
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
     // coefficients of the linearisation (Jacobian only), FP32
     const float Gt = G.hi, dett = det.hi;
     const float a11 = Gt * (1.0f + uyy.hi), a12 = -Gt * uxy.hi, a22 = Gt * (1.0f + uxx.hi);
-    const float b1 = dett * Gx, b2 = dett * Gy;
+    const float b1 = K.nob ? 0.0f : dett * Gx, b2 = K.nob ? 0.0f : dett * Gy;
     coef[p] = a11;
     coef[P + p] = a12;
     coef[2 * P + p] = a22;
@@ -878,7 +880,8 @@ static dd host_dd(double v) {
 
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
-                               DevScalars* sc, cudaStream_t st, const double* ub, int sel) {
+                               DevScalars* sc, cudaStream_t st, const double* ub, int sel,
+                               int simplified) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConstsDD K;
   K.Mh = host_dd((double)M / 12.0);
@@ -891,6 +894,7 @@ cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const doubl
   K.N = (float)N;
   K.w3M = (float)(1.0 / (3.0 * (double)M));
   K.w3N = (float)(1.0 / (3.0 * (double)N));
+  K.nob = simplified ? 1 : 0;
   k_residual_dd<<<grid, RTX * RTY / RPT, 0, st>>>(fdd, cdd, ua, ub, sel, N, M, K, Fraw, coef,
                                                   partials, sc);
   return cudaGetLastError();
@@ -903,7 +907,8 @@ int residual_partial_blocks(int N, int M) {
 template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
-                            cudaStream_t st, const double* ub, int sel, const float* c32) {
+                            cudaStream_t st, const double* ub, int sel, const float* c32,
+                            int simplified) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConsts K;
   K.Mh = (double)M / 12.0;
@@ -913,6 +918,7 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
   K.MNh = K.Mh * K.Nh;
   K.w3M = 1.0 / (3.0 * (double)M);
   K.w3N = 1.0 / (3.0 * (double)N);
+  K.nob = simplified ? 1 : 0;
   if (sizeof(T) == 4 && !c32) return cudaErrorInvalidValue;
   k_residual<T><<<grid, RTX * RTY / RPT, 0, st>>>(f, c, c32, ua, ub, sel, N, M, K, Fraw, coef,
                                                   partials, sc);
@@ -1604,7 +1610,7 @@ cudaError_t launch_convert(const void* in, int in_d, void* out, int out_d, long 
 #define OTGB_INST_NEWTON(T)                                                                   \
   template cudaError_t launch_residual<T>(const double*, const double*, const double*, int,   \
                                           int, double*, T*, double*, DevScalars*,             \
-                                          cudaStream_t, const double*, int, const float*);    \
+                                          cudaStream_t, const double*, int, const float*, int); \
   template cudaError_t launch_gmres_init<T>(const double*, const T*, T*, long, int, double*,  \
                                             DevScalars*, int, cudaStream_t, T*);              \
   template cudaError_t launch_gmres_dots<T>(const T*, const T*, long, double*, DevScalars*,   \

@@ -169,18 +169,19 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st);
-// u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate)
+// u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate);
+// simplified: b = 0 in the coefficients (the operator without the grad g term)
 // c32 (optional, FP32 copy of c): used for the gradient of the interpolant in FP32 mode
 template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
                             cudaStream_t st, const double* ub = nullptr, int sel = 0,
-                            const float* c32 = nullptr);
+                            const float* c32 = nullptr, int simplified = 0);
 // mixed mode: the residual in double-float arithmetic from (hi, lo) float pairs of f and c
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
                                DevScalars* sc, cudaStream_t st, const double* ub = nullptr,
-                               int sel = 0);
+                               int sel = 0, int simplified = 0);
 // out[k] = (hi, lo) float pair of in[k]
 cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st);
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,

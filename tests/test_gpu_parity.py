@@ -245,6 +245,36 @@ def test_solve_manufactured_mixed(ot, N):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_simplified_operator(ot, prec):
+    # OT_OPT_OPERATOR = 1 (Sec. 3.3 remark): the coefficients lose the grad g term (b = 0),
+    # F and a are unchanged; the solve follows another Newton path to the oracle's root
+    N, M = 64, 96
+    f = I.blob_density(N, M, 51)
+    g = I.blob_density(N, M, 52)
+    u = smooth_field(N, M, amp=2e-3)
+    c = O.bspline_coeffs(g)
+    with O.simplified_operator():
+        F_ref, coef_ref, _ = O.residual(f, c, u)
+    p = plan(ot, N, M, prec, operator=1)
+    assert p.get("operator") == 1
+    fd, cd, ud = dev(f), dev(c), dev(u)
+    Fd, coefd = dev(np.zeros((N, M))), dev(np.zeros((5, N, M)))
+    scal = np.zeros(10)
+    assert ot.ot_eval_residual(p.h, ptr(fd), ptr(cd), ptr(ud), ptr(Fd), ptr(coefd),
+                               hptr(scal)) == 0
+    cg = coefd.cpu().numpy()
+    assert not cg[3:].any()
+    rel = 1e-12 if prec == "fp64" else 1e-6
+    assert np.abs(cg[:3] - coef_ref[:3]).max() <= rel * np.abs(coef_ref[:3]).max()
+    p.close()
+    fm, gm, _ = I.manufactured(32, 32)
+    u_full, st_full, _, _ = O.solve(fm, gm, tau=2.0, tol=1e-10, eta=1e-2)
+    rc, st, phi = _gpu_solve(ot, fm, gm, prec, eta=1e-2, operator=1)
+    assert st_full["status"] == 0 and rc == 0 and st["res_inf"] < 1e-10
+    assert np.abs(phi - u_full).max() <= (1e-9 if prec == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("symbols", [0, 1])
 def test_solve_uniform_target_breakdown_path(ot, prec, symbols):
     # g = 1: at u = 0 the coefficients are a = I, b = 0, so L = Lbar and the preconditioned

@@ -61,3 +61,22 @@ def test_stencil_symbol_solve_reaches_the_same_root():
     assert np.abs(u0 - u1).max() < 1e-10
     # exact Newton (tau = 1, consistent Jacobian, accurate inner solves) converges fast
     assert st1["newton_iters"] < st0["newton_iters"]
+
+
+def test_simplified_operator_drops_only_the_grad_g_term():
+    # Sec. 3.3 remark: g(x + grad u) Tr(Adj(I + D^2 u) D^2 theta) = (f - f_n) / tau, i.e. the
+    # coefficients b = 0; F and a are untouched, and the root (defined by F alone) is the same
+    f, g = I.blob_pair(24, 32, s=11)
+    u = 1e-3 * np.random.default_rng(2).standard_normal((24, 32))
+    c = O.bspline_coeffs(g)
+    F0, a0, s0 = O.residual(f, c, u)
+    with O.simplified_operator():
+        F1, a1, s1 = O.residual(f, c, u)
+    assert np.array_equal(F0, F1) and np.array_equal(a0[:3], a1[:3])
+    assert not a1[3:].any() and np.abs(a0[3:]).max() > 1.0
+    fm, gm, _ = I.manufactured(32, 32)
+    u_full, st_full, _, _ = O.solve(fm, gm, tau=2.0, tol=1e-10, eta=1e-2)
+    with O.simplified_operator():
+        u_simp, st_simp, _, _ = O.solve(fm, gm, tau=2.0, tol=1e-10, eta=1e-2)
+    assert st_full["status"] == 0 and st_simp["status"] == 0
+    assert np.abs(u_full - u_simp).max() <= 1e-9
