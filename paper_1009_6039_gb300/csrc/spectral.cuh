@@ -1499,9 +1499,34 @@ inline cudaError_t set_smem_fn(const void* fn, size_t bytes) {
   return cudaSuccess;
 }
 
+// The largest block a kernel can be launched with (its launch bounds and registers), queried
+// once per kernel and device.
+inline int max_block_threads(const void* fn) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  struct Rec {
+    const void* fn;
+    int dev, threads;
+  };
+  static std::mutex mu;
+  static std::vector<Rec> recs;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& r : recs)
+    if (r.fn == fn && r.dev == dev) return r.threads;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 0;
+  recs.push_back({fn, dev, a.maxThreadsPerBlock});
+  return a.maxThreadsPerBlock;
+}
+
+// Check a launch configuration on the host and raise the kernel's shared-memory limit: a
+// block larger than the kernel allows is returned as an error here, never launched (a
+// launch the runtime rejects inside a stream capture invalidates the capture).
 template <typename K>
-inline cudaError_t set_smem(K kernel, size_t bytes) {
-  return set_smem_fn(reinterpret_cast<const void*>(kernel), bytes);
+inline cudaError_t prepare_launch(K kernel, long threads, size_t bytes) {
+  const void* fn = reinterpret_cast<const void*>(kernel);
+  if (threads < 1 || threads > max_block_threads(fn)) return cudaErrorInvalidConfiguration;
+  return set_smem_fn(fn, bytes);
 }
 
 template <typename T, int E>
@@ -1513,7 +1538,7 @@ cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scal
   while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)RB * FB(L) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_row_r2c<T, E>, sm);
+  cudaError_t e = prepare_launch(k_row_r2c<T, E>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_r2c<T, E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       x, xs, jptr, scale, spec, N, M, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
@@ -1537,7 +1562,7 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   }
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * colb;
-  cudaError_t e = set_smem(k_col<T, E, MODE>, sm);
+  cudaError_t e = prepare_launch(k_col<T, E, MODE>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN,
@@ -1558,7 +1583,7 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   while (RB > 1 && RB * TPT > 128 && (N + RB - 1) / RB < 4 * 152) RB /= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)RB * rowb;
-  cudaError_t e = set_smem(k_row_c2r<T, E, MODE>, sm);
+  cudaError_t e = prepare_launch(k_row_c2r<T, E, MODE>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, u_in, u_out, step, out_scale, N, M, (const C2<T>*)tb.twL,
@@ -1575,7 +1600,7 @@ cudaError_t row_r2c_w_launch(const T* x, size_t xs, const int* jptr, const doubl
   if (RB < 1) RB = 1;
   if (RB > N) RB = N;
   const size_t sm = (size_t)RB * (L + L / 32) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_row_r2c_w<T>, sm);
+  cudaError_t e = prepare_launch(k_row_r2c_w<T>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_r2c_w<T><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       x, xs, jptr, scale, spec, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
@@ -1604,7 +1629,7 @@ cudaError_t col_matvec_par_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2,
   if (Q > 4) Q = 4;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)3 * Q * FB(N) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_col_matvec_par<T, E>, sm);
+  cudaError_t e = prepare_launch(k_col_matvec_par<T, E>, 3 * Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col_matvec_par<T, E><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
@@ -1621,7 +1646,7 @@ cudaError_t col_matvec_w_launch(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* 
   while (Q * 2 * 3 * TPT <= 384 && Q < 2) Q *= 2;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)3 * Q * (N + N / 32) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_col_matvec_w<T>, sm);
+  cudaError_t e = prepare_launch(k_col_matvec_w<T>, 3 * Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col_matvec_w<T><<<(Lc + Q - 1) / Q, 3 * Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN, sc,
@@ -1671,7 +1696,7 @@ cudaError_t row_combine_par_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
   while (RB * 2 * 5 * TPT <= OTGB_PAR_THREADS && RB < 8) RB *= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)5 * RB * FB(L) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_row_combine_par<T, E>, sm);
+  cudaError_t e = prepare_launch(k_row_combine_par<T, E>, 5 * RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_combine_par<T, E><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip,
@@ -1688,7 +1713,7 @@ cudaError_t row_combine_w_launch(const C2<T>* q0, const C2<T>* q1, const C2<T>* 
   while (RB * 2 * 5 * TPT <= 320 && RB < 8) RB *= 2;
   if (RB > N) RB = N;
   const size_t sm = (size_t)5 * RB * (L + L / 32) * sizeof(C2<T>);
-  cudaError_t e = set_smem(k_row_combine_w<T>, sm);
+  cudaError_t e = prepare_launch(k_row_combine_w<T>, 5 * RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_combine_w<T><<<(N + RB - 1) / RB, 5 * RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, N, M, RB, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip,
@@ -1747,7 +1772,7 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
   while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * FB(N) * sizeof(double2);
-  cudaError_t e = set_smem(k_col_lbarinv_mixed<E>, sm);
+  cudaError_t e = prepare_launch(k_col_lbarinv_mixed<E>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col_lbarinv_mixed<E><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
@@ -1766,7 +1791,7 @@ cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
   while (Q > 1 && (Lc + Q - 1) / Q < 2 * 152) Q /= 2;
   if (Q > Lc) Q = Lc;
   const size_t sm = (size_t)Q * FB(N) * sizeof(ddc);
-  cudaError_t e = set_smem(k_col_lbarinv_dd<E, MODE>, sm);
+  cudaError_t e = prepare_launch(k_col_lbarinv_dd<E, MODE>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col_lbarinv_dd<E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
@@ -1785,7 +1810,7 @@ cudaError_t row_c2r_update_dd_E(const ddc* q, const double* u_in, double* u_out,
   while (RB > 1 && (size_t)RB * FB(L) * sizeof(ddc) > 160 * 1024) RB /= 2;
   while (RB > 1 && (N + RB - 1) / RB < 2 * 152) RB /= 2;
   const size_t sm = (size_t)RB * FB(L) * sizeof(ddc);
-  cudaError_t e = set_smem(k_row_c2r_update_dd<E>, sm);
+  cudaError_t e = prepare_launch(k_row_c2r_update_dd<E>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
   k_row_c2r_update_dd<E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
       q, u_in, u_out, step, N, M, (const ddc*)tbdd.twL, (const ddc*)tbdd.twM, sc);

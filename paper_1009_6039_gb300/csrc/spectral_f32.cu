@@ -14,7 +14,9 @@ static cudaError_t col_lbarinv_dd_mode(const float2* spec, ddc* out, int N, int 
                                        const SpecTables& tb32, const SpecTables& tbdd,
                                        const DevScalars* sc, cudaStream_t st) {
   if (fft_E(N) == 12) return col_lbarinv_dd_E<12, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
-  if (N >= 16) return col_lbarinv_dd_E<4, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
+  // 4 elements per thread while a column fits one block of 256 threads (the kernel's bound)
+  if (N >= 16 && N / 4 <= 256)
+    return col_lbarinv_dd_E<4, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
   return col_lbarinv_dd_E<8, MODE>(spec, out, N, M, tb32, tbdd, sc, st);
 }
 cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
@@ -35,7 +37,8 @@ cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u
                                      const DevScalars* sc, cudaStream_t st) {
   if (fft_E(M / 2) == 12)
     return row_c2r_update_dd_E<12>(q, u_in, u_out, step, N, M, tbdd, sc, st);
-  if (M / 2 >= 16) return row_c2r_update_dd_E<4>(q, u_in, u_out, step, N, M, tbdd, sc, st);
+  if (M / 2 >= 16 && (M / 2) / 4 <= 256)
+    return row_c2r_update_dd_E<4>(q, u_in, u_out, step, N, M, tbdd, sc, st);
   return row_c2r_update_dd_E<8>(q, u_in, u_out, step, N, M, tbdd, sc, st);
 }
 }

@@ -167,6 +167,31 @@ def test_transport_outputs(ot, N, M):
     p.close()
 
 
+@pytest.mark.parametrize("N,M", [(2048, 32), (32, 2048), (1536, 48), (48, 1536)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_longest_transforms(ot, N, M, prec):
+    # the longest supported transform lengths (columns N <= 2048, rows M <= 2048, and a
+    # radix-3 length): the launch configurations at their largest blocks (the default variants
+    # at these shapes include the concurrent column pass and the two-warp row transforms),
+    # through the operator and Lbar^-1
+    f = I.blob_density(N, M, 61)
+    g = I.blob_density(N, M, 62)
+    u = smooth_field(N, M, amp=2e-3)
+    _, coef, _ = O.residual(f, O.bspline_coeffs(g), u)
+    abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
+    sigma = RNG.standard_normal((N, M))
+    w_ref = O.apply_op(coef, abar, sigma)
+    th_ref = O.apply_lbar_inv(abar, sigma)
+    p = plan(ot, N, M, prec)
+    cd, sd, wd, td = dev(coef), dev(sigma), dev(np.zeros((N, M))), dev(np.zeros((N, M)))
+    assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
+    assert ot.ot_apply_lbar_inverse(p.h, hptr(abar), ptr(sd), ptr(td)) == 0
+    r = 1e-12 if prec == "fp64" else 5e-6
+    assert np.abs(wd.cpu().numpy() - w_ref).max() <= r * np.abs(w_ref).max()
+    assert np.abs(td.cpu().numpy() - th_ref).max() <= r * np.abs(th_ref).max()
+    p.close()
+
+
 @pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512),
                                  (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
