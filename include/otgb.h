@@ -39,6 +39,8 @@ extern "C" {
 #define OT_ECUDA (-4)        /* a CUDA runtime call failed */
 #define OT_ENOMEM (-5)       /* device or pinned-host allocation failed */
 #define OT_EUNSUPPORTED (-6) /* grid size outside the supported FFT lengths */
+#define OT_ETIMEOUT (-7)     /* a bounded device-side wait gave up (the kernel returned and
+                                reported it through its flag; the context stays usable) */
 
 /* Plan options (ot_plan_set_option keys). */
 #define OT_OPT_RESTART 1        /* GMRES restart length m, 1..15 (default 10, Sec. 5.1) */
@@ -97,7 +99,7 @@ extern "C" {
                                    ot_ws_mlp_forward skip one tensor-core MMA group, so its
                                    bounded mbarrier wait runs out (tens of milliseconds); the
                                    kernel sets its error flag, frees its TMEM and returns and
-                                   the call returns OT_ECUDA; resets itself after one call */
+                                   the call returns OT_ETIMEOUT; resets itself after one call */
 #define OT_OPT_OPERATOR 21      /* linear operator of the Newton step: 0 (default) the full
                                    linearisation of Eq. linearmaeq (a : D^2 theta + b . grad
                                    theta, b = det(I + D^2 u) grad g(x + grad u)); 1 the
@@ -298,7 +300,7 @@ int ot_ws_features(ot_plan* plan, const double* f, const double* g, const double
                    float* X, float* target);
 
 /* out[r] = MLP(X[r, 0..15]) for r < rows with the plan's weights (the BF16 tensor-core
- * kernel of the solve).  OT_ECUDA if the kernel reported a timeout. */
+ * kernel of the solve).  OT_ETIMEOUT if the kernel reported a timeout. */
 int ot_ws_mlp_forward(ot_plan* plan, const float* X, int64_t rows, float* out);
 
 /* u = P(src) (the FD Poisson solve of h; src, u: N x M); lowpass != 0: u = P(G src). */

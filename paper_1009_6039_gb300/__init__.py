@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libotgb.so")
 
 OT_OK, OT_EINVAL, OT_ENOCONV, OT_EDIVERGED, OT_ECUDA, OT_ENOMEM, OT_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6
+OT_ETIMEOUT = -7
 OT_OPT_RESTART, OT_OPT_ETA, OT_OPT_MAX_NEWTON, OT_OPT_MAX_RESTARTS = 1, 2, 3, 4
 OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 7, 8
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
@@ -53,7 +54,7 @@ class ot_stats(ctypes.Structure):
 
 class OTError(RuntimeError):
     def __init__(self, status, where):
-        detail = ot_last_error() if status == OT_ECUDA else ""
+        detail = ot_last_error() if status in (OT_ECUDA, OT_ETIMEOUT) else ""
         super().__init__("%s: %s (%d) %s" % (where, ot_strerror(status), status, detail))
         self.status = status
 

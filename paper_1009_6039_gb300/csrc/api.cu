@@ -170,10 +170,11 @@ static void prof_harvest(ot_plan* p, int jend) {
 
 static const char* kErr[] = {"ok", "invalid argument", "Newton did not converge",
                              "iterate lost convexity or became non-finite", "CUDA error",
-                             "out of memory", "unsupported grid size"};
+                             "out of memory", "unsupported grid size",
+                             "a bounded device-side wait gave up"};
 
 extern "C" const char* ot_strerror(int s) {
-  if (s <= 0 && s >= -6) return kErr[-s];
+  if (s <= 0 && s >= -7) return kErr[-s];
   return "unknown status";
 }
 
@@ -1879,7 +1880,11 @@ extern "C" int ot_ws_predict(ot_plan* p, const double* f, const double* g, doubl
   RET(run_warmstart(p, phi0));
   RET(read_scalars(p));
   if (alpha_out) *alpha_out = p->hsc->ws_alpha;
-  return p->hsc->ws_err ? OT_ECUDA : OT_OK;
+  if (p->hsc->ws_err) {
+    record_kernel_error("tensor-core network: bounded mbarrier wait ran out", __LINE__);
+    return OT_ETIMEOUT;
+  }
+  return OT_OK;
 }
 
 extern "C" int ot_ws_features(ot_plan* p, const double* f, const double* g,
@@ -1913,7 +1918,7 @@ extern "C" int ot_ws_mlp_forward(ot_plan* p, const float* X, int64_t rows, float
   CK(cudaStreamSynchronize(p->stream));
   if (err) {
     record_kernel_error("tensor-core network: bounded mbarrier wait ran out", __LINE__);
-    return OT_ECUDA;
+    return OT_ETIMEOUT;
   }
   return OT_OK;
 }

@@ -47,6 +47,7 @@ def test_strerror_without_gpu(lib):
     assert lib.ot_strerror(0) == "ok"
     assert "converge" in lib.ot_strerror(lib.OT_ENOCONV)
     assert lib.ot_strerror(-99) == "unknown status"
+    assert "wait" in lib.ot_strerror(lib.OT_ETIMEOUT)
 
 
 def test_build_is_arm_portable():

@@ -285,7 +285,7 @@ def test_network_wait_timeout_is_reported_and_recoverable(ot):
     p = ot.Plan(32, 32, precision="mixed").set_weights(params)
     out = torch.zeros(rows, dtype=torch.float32, device="cuda")
     p.set(ws_test_stall=1)
-    assert ot.ot_ws_mlp_forward(p.h, ctypes_ptr(X), rows, ctypes_ptr(out)) == ot.OT_ECUDA
+    assert ot.ot_ws_mlp_forward(p.h, ctypes_ptr(X), rows, ctypes_ptr(out)) == ot.OT_ETIMEOUT
     assert "mbarrier wait" in ot.ot_last_error()
     p.ws_mlp_forward(X, out)
     y_ref, _ = W.mlp_forward(params.astype(np.float64), X.cpu().numpy().astype(np.float64),
