@@ -59,3 +59,20 @@ def test_build_is_arm_portable():
                 assert "immintrin" not in s and "xmmintrin" not in s, fn
     b = open(os.path.join(ROOT, "paper_1009_6039_gb300", "build.py")).read()
     assert "march" not in b
+
+
+def test_binding_constants_match_the_header(lib):
+    # every OT_OPT_*, OT_PROF_* and status code of the header has the same value in the binding
+    src = open(os.path.join(ROOT, "include", "otgb.h")).read()
+    defs = dict((k, int(v)) for k, v in re.findall(
+        r"#define\s+(OT_(?:OPT|PROF|E|OK)[A-Z0-9_]*)\s+\(?(-?\d+)\)?", src))
+    assert len(defs) > 30
+    for name, value in defs.items():
+        if name.startswith("OT_PROF_"):
+            if name == "OT_PROF_CLASSES":
+                assert len(lib.PROF_CLASSES) == value
+            continue
+        assert getattr(lib, name) == value, name
+    # the Plan option names cover every option key
+    keys = {v for k, v in defs.items() if k.startswith("OT_OPT_")}
+    assert keys == set(lib.Plan._keys.values())
