@@ -96,10 +96,14 @@ extern "C" {
                                    Sec. 3.2 / Sec. 5.3; phi and stats are those of the last
                                    attempt (ot_solve, ot_solve_batched) */
 #define OT_OPT_WS_TEST_STALL 20 /* test of the failure path: 1 makes the next
-                                   ot_ws_mlp_forward skip one tensor-core MMA group, so its
-                                   bounded mbarrier wait runs out (tens of milliseconds); the
-                                   kernel sets its error flag, frees its TMEM and returns and
-                                   the call returns OT_ETIMEOUT; resets itself after one call */
+                                   ot_ws_mlp_forward, or the network launch of the next
+                                   host-driven solve (OT_OPT_GRAPH = 0) with the learned warm
+                                   start, skip one tensor-core MMA group, so its bounded
+                                   mbarrier wait runs out (tens of milliseconds); the kernel
+                                   sets its error flag, frees its TMEM and returns;
+                                   ot_ws_mlp_forward then returns OT_ETIMEOUT, the solve goes on
+                                   from the zero start with ws_alpha = -2; resets itself after
+                                   one use */
 #define OT_OPT_OPERATOR 21      /* linear operator of the Newton step: 0 (default) the full
                                    linearisation of Eq. linearmaeq (a : D^2 theta + b . grad
                                    theta, b = det(I + D^2 u) grad g(x + grad u)); 1 the
@@ -146,7 +150,9 @@ typedef struct {
   double phi_mean;         /* mean removed from the final iterate (gauge, Sec. 3.1) */
   double ms_total;         /* wall time of the call on the plan's stream (ms) */
   double ws_alpha;         /* learned warm start: scale applied to the network's potential
-                              (1, 1/2, 1/4, 1/8 or 0 = zero start); -1 without it */
+                              (1, 1/2, 1/4, 1/8 or 0 = zero start); -1 without it; -2 if
+                              the network kernel's bounded wait gave up (the solve went on
+                              from the zero start and ot_last_error names it) */
 } ot_stats;
 
 /* Create a plan for N x M grids (N rows, M columns), damping tau >= 1 (Eq. linma) and
@@ -255,7 +261,7 @@ int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
 int ot_transport_outputs(ot_plan* plan, const double* f, const double* phi, double* dist,
                          double* div_out);
 
-/* ---- Learned warm start -----------------------------------------------------------------/* ---- Learned warm start -----------------------------------------------------------------
+/* ---- Learned warm start -----------------------------------------------------------------
  * Not in the paper, which starts Newton from u0 = 0 and needs only an admissible start,
  * det(I + D^2 u0) > 0 (Thm 3.2).  After the input translation (Eq. translation):
  *   h  = P(log f - log g), P the mean-zero inverse of the 4th-order stencil Laplacian
@@ -337,12 +343,14 @@ void ot_ws_trainer_destroy(ot_ws_trainer* tr);
  * allocating routine: its scratch (reduction partials and a block of device scalars,
  * about 330 KB) is a fixed file-scope device array that every GPU loading the library holds
  * until the process exits.  f, c, u, F, coef: device pointers (coef: 5 planes of N x M);
- * scal: HOST, 10 doubles, may be NULL; cuda_stream: a cudaStream_t (NULL = legacy default).
- * The call returns after the results are complete.
+ * scal: HOST, 10 doubles, may be NULL; cuda_stream: a cudaStream_t of the current device
+ * (NULL = its legacy default stream); a stream of another device returns OT_EINVAL.
+ * The call synchronises cuda_stream and returns after the results are complete, so it
+ * cannot be called while that stream is being captured into a CUDA graph.
  *   - Sizes: 8 <= N, M <= 2048; larger grids return OT_EUNSUPPORTED before touching
  *     memory, smaller ones or a NULL pointer OT_EINVAL.
  *   - The first call on a device looks up the array's device address (set-up, once per
- *     device, with that device current); make that first call before any stream capture.
+ *     device, with that device current).
  *   - All calls share the one array and clear what must start at zero themselves; calls
  *     that overlap on the GPU (other streams or host threads) race on it and must be
  *     serialised by the caller. */

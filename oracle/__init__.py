@@ -65,7 +65,6 @@ def lib():
         _lib.orc_residual.argtypes = [vp, vp, vp, i, i, vp, vp, vp]
         _lib.orc_simpson_mean.argtypes = [vp, i, i]
         _lib.orc_simpson_mean.restype = d
-        _lib.orc_rho_bar.argtypes = [vp, ctypes.c_long, i, ctypes.c_long, i, vp, vp]
         _lib.orc_apply_op.argtypes = [vp, vp, vp, i, i, vp]
         _lib.orc_apply_lbar_inv.argtypes = [vp, vp, i, i, vp]
         _lib.orc_gmres_dense.argtypes = [vp, vp, i, i, d, i, vp, vp, vp, vp]
@@ -172,14 +171,6 @@ def residual(f, c, u):
 def simpson_mean(a):
     a = _f64(a)
     return lib().orc_simpson_mean(_p(a), a.shape[0], a.shape[1])
-
-
-def rho_bar(abar, k1, nyq1, k2, nyq2):
-    ab = _f64(abar)
-    re, im = ctypes.c_double(), ctypes.c_double()
-    lib().orc_rho_bar(_p(ab), int(k1), int(nyq1), int(k2), int(nyq2), ctypes.byref(re),
-                      ctypes.byref(im))
-    return re.value + 1j * im.value
 
 
 def apply_op(coef, abar, sigma):

@@ -553,12 +553,6 @@ static void rho_bar_nm(const double abar[5], long k1, int n1, int M, long k2, in
   }
 }
 
-/* rho-bar with the spectral symbols (the lengths do not enter them) */
-void orc_rho_bar(const double abar[5], long k1, int n1, long k2, int n2, double *re,
-                 double *im) {
-  rho_bar_nm(abar, k1, n1, 1, k2, n2, 1, 0, re, im);
-}
-
 /* w = L Lbar^{-1} sigma:
  *   sigma-hat = FFT(sigma); S = rho-bar sigma-hat;
  *   alpha_pq = IFFT(sym_pq S), beta_p = IFFT(sym_p S)   (all d(d+1) = 6 of them);

@@ -51,8 +51,6 @@ void orc_bspline_eval_grid(const double *c, int N, int M, double gx_pos, double 
 int orc_residual(const double *f, const double *c, const double *u, int N, int M, double *F,
                  double *coef, double *scal);
 double orc_simpson_mean(const double *a, int N, int M);
-void orc_rho_bar(const double abar[5], long k1, int n1, long k2, int n2, double *re,
-                 double *im);
 void orc_apply_op(const double *coef, const double abar[5], const double *sigma, int N, int M,
                   double *w);
 void orc_apply_lbar_inv(const double abar[5], const double *sigma, int N, int M,

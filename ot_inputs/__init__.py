@@ -147,6 +147,18 @@ def noise_blob_pair(N, M, s=3000, ratio=10.0, sigma_px=8.0):
             noise_blob_density(N, M, 2 * s + 1, ratio, sigma_px))
 
 
+BATCH_SIZES = (128, 192, 256, 384, 512)
+
+
+def batch_workload(count, base=4000):
+    """Batched workload of `count` blob pairs of uneven square sizes: pair k has size n_k
+    drawn uniformly from BATCH_SIZES by SplitMix64(base) (one draw per pair, in order) and
+    densities blob_pair(n_k, n_k, s=base + k).  Returns the list of (n_k, base + k)."""
+    draws = SplitMix64(base).uniform(count)
+    return [(BATCH_SIZES[min(len(BATCH_SIZES) - 1, int(d * len(BATCH_SIZES)))], base + k)
+            for k, d in enumerate(draws)]
+
+
 # ----------------------------------------------------------------------------------------
 # Learned warm start: initial network parameters and minibatch row draws
 # ----------------------------------------------------------------------------------------

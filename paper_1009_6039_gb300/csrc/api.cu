@@ -191,6 +191,15 @@ static void record_kernel_error(const char* what, int line) {
 
 extern "C" const char* ot_last_error(void) { return g_last_error; }
 
+// The learned warm start's network kernel gave up a bounded wait during a solve: the
+// admissibility step then chose the zero start and the solve went on from it.  The stats
+// say so (ws_alpha = -2) and ot_last_error names it.
+static void note_ws_timeout(ot_stats* st, int line) {
+  st->ws_alpha = -2.0;
+  record_kernel_error("learned warm start: the network kernel's bounded wait gave up; "
+                      "solved from the zero start", line);
+}
+
 #define CK(x)                                 \
   do {                                        \
     cudaError_t e_ = (x);                     \
@@ -1000,13 +1009,13 @@ static int run_ws_features(ot_plan* p) {
 }
 
 // u = alpha (h + P(G MLP(X))), G the Gaussian low-pass; alpha and the network's error flag
-// in sc
-static int run_warmstart(ot_plan* p, double* u) {
+// in sc (stall: the failure-path test hook of the network kernel)
+static int run_warmstart(ot_plan* p, double* u, int stall = 0) {
   const long P = (long)p->N * p->M;
   RET(run_ws_features(p));
   LAUNCH(p, OT_PROF_WARMSTART, -1, 1,
          launch_ws_mlp(p->ws_wpack, p->ws_params, p->ws_X, P, p->ws_s, &p->sc->ws_err, p->sms,
-                       p->stream));
+                       p->stream, stall));
   if (p->precision) {
     // u = h + P(G s) straight from the network's FP32 output
     RET(run_ws_poisson32(p, p->ws_s, u, p->ws_h, true));
@@ -1056,7 +1065,9 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   if (p->warm_start == 1) {
     if (phi != p->u) CK(cudaMemcpyAsync(p->u, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   } else if (p->warm_start == 2) {
-    RET(run_warmstart(p, p->u));
+    const int stall = p->ws_stall;
+    p->ws_stall = 0;
+    RET(run_warmstart(p, p->u, stall));
   } else {
     CK(cudaMemsetAsync(p->u, 0, P * 8, p->stream));
   }
@@ -1116,6 +1127,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   RET(read_scalars(p));
   st->res_l2 = sqrt(p->hsc->res_l2sum / (double)P);
   st->ws_alpha = p->hsc->ws_alpha;
+  if (p->hsc->ws_err) note_ws_timeout(st, __LINE__);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   st->ms_total = ms;
@@ -1485,6 +1497,7 @@ static void graph_collect(ot_plan* p, const DevScalars* h, double mean, ot_stats
   st->phi_mean = mean;
   st->kernel_launches = (int32_t)(h->kcount + p->top_kernels);
   st->ws_alpha = h->ws_alpha;
+  if (h->ws_err) note_ws_timeout(st, __LINE__);
   p->launches += h->kcount + p->top_kernels;
 }
 

@@ -959,9 +959,20 @@ __global__ void k_shifted(const double* __restrict__ Fraw, double* __restrict__ 
     F[p] = Fraw[p] + s;
 }
 
+// in-place form (F += shift): one pointer, so no aliasing of restrict-qualified arguments
+__global__ void k_shift_inplace(double* F, long P, const DevScalars* __restrict__ sc) {
+  const double s = sc->shift;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    F[p] += s;
+}
+
 cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
                                     const DevScalars* sc, cudaStream_t st) {
-  k_shifted<<<reduce_blocks(), 256, 0, st>>>(Fraw, F, (long)N * M, sc);
+  if (Fraw == F)
+    k_shift_inplace<<<reduce_blocks(), 256, 0, st>>>(F, (long)N * M, sc);
+  else
+    k_shifted<<<reduce_blocks(), 256, 0, st>>>(Fraw, F, (long)N * M, sc);
   return cudaGetLastError();
 }
 

@@ -60,6 +60,15 @@ extern "C" int ot_eval_residual_noalloc(int32_t N, int32_t M, const double* f, c
   if (N < 8 || M < 8) return OT_EINVAL;
   if (N > kMaxSide || M > kMaxSide) return OT_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (st) {
+    // the scratch array is the current device's: a stream of another device is refused
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return OT_EINVAL;
+    }
+    if (sdev != cur) return OT_EINVAL;
+  }
   unsigned char* base = nullptr;
   int rc = scratch_for_current_device(&base);
   if (rc != OT_OK) return rc;

@@ -338,9 +338,11 @@ __global__ void __launch_bounds__(256)
 
 __global__ void k_ws_scale(double* __restrict__ u, long P, const double* __restrict__ alpha) {
   const double a = *alpha;
+  // a = 0 is the zero start: written as such, so that a non-finite prediction (e.g. after a
+  // network timeout) cannot leak into it through 0 * inf
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x)
-    u[p] *= a;
+    u[p] = (a == 0.0) ? 0.0 : u[p] * a;
 }
 
 // ---------------------------------------------------------------------------------------

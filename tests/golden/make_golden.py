@@ -25,8 +25,15 @@ CASES = {
     "noise1024": dict(kind="noise_blob_pair", N=1024, M=1024, seed=3000, tau=1.0, tol=1e-8,
                       eta=1e-2, symbols=1),
     "noise2048": dict(kind="noise_blob_pair", N=2048, M=2048, seed=3000, tau=1.0, tol=1e-8,
-                      eta=1e-1),
+                      eta=1e-2, symbols=1),
 }
+# pairs of the batched workload (ot_inputs.batch_workload(512)): the first pair of each size
+# and the two 512^2 pairs that lose convexity at tau = 1; the batched solver's settings
+# (stencil symbols, tau = 1, eta = 0.1, tol 1e-8), a diverged solve repeated with twice tau
+# up to twice (the remedy of Sec. 3.2 / Sec. 5.3)
+for _k in (0, 2, 5, 7, 9, 200, 297):
+    CASES["batch%d" % _k] = dict(kind="blob_pair", batch_index=_k, seed=4000 + _k, tau=1.0,
+                                 tol=1e-8, eta=1e-1, symbols=1, tau_retry=2, max_newton=1000)
 
 
 def sample_indices(N, M, count=512):
@@ -36,6 +43,10 @@ def sample_indices(N, M, count=512):
 
 
 def inputs(case):
+    if "batch_index" in case:
+        n, s = I.batch_workload(512)[case["batch_index"]]
+        assert s == case["seed"]
+        case["N"] = case["M"] = n
     gen = {"blob_pair": I.blob_pair, "noise_blob_pair": I.noise_blob_pair}[case["kind"]]
     return gen(case["N"], case["M"], s=case["seed"])
 
@@ -45,12 +56,20 @@ def run(name):
     f, g = inputs(case)
     t = time.time()
     # symbols: 0 the spectral derivative symbols of Sec. 4.2, 1 those of the stencils
+    tau = case["tau"]
+    attempts = []
     with O.fd_symbols(case.get("symbols", 0)):
-        u, st, hres, hgm = O.solve(f, g, tau=case["tau"], tol=case["tol"], eta=case["eta"],
-                                   max_newton=300)
+        for _ in range(1 + case.get("tau_retry", 0)):
+            u, st, hres, hgm = O.solve(f, g, tau=tau, tol=case["tol"], eta=case["eta"],
+                                       max_newton=case.get("max_newton", 300))
+            attempts.append(dict(tau=tau, stats=st))
+            if st["status"] != O.ORC_EDIVERGED:
+                break
+            tau *= 2.0
     secs = time.time() - t
     ii, jj = sample_indices(case["N"], case["M"])
-    out = dict(case=case, oracle_seconds=secs, stats=st, res_history=hres.tolist(),
+    out = dict(case=case, oracle_seconds=secs, stats=st, attempts=attempts,
+               res_history=hres.tolist(),
                gmres_history=hgm.tolist(), sample_i=ii.tolist(), sample_j=jj.tolist(),
                phi_samples=u[ii, jj].tolist(), phi_absmax=float(np.abs(u).max()),
                command="python tests/golden/make_golden.py " + name)

@@ -297,3 +297,29 @@ def test_network_wait_timeout_is_reported_and_recoverable(ot):
 def ctypes_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
+
+
+def test_network_timeout_inside_a_solve_falls_back_to_zero_start(ot):
+    # the same failure inside a solve: the admissibility step takes the zero start, the
+    # stats report ws_alpha = -2 and ot_last_error names the warm start; the solve reaches
+    # the root of the zero-start solve
+    N = M = 64
+    f, g = I.noise_blob_pair(N, M, s=3600)
+    kw = dict(tau=1.0, tol=1e-8, eta=1e-2, precision="mixed", symbols=1, graph=0)
+    p0 = ot.Plan(N, M, **kw)
+    phi0 = dev(np.zeros((N, M)))
+    rc0, st0 = p0.solve(dev(f), dev(g), phi0)
+    p0.close()
+    p = ot.Plan(N, M, **kw).set_weights(random_params(16))
+    p.set(warm_start=2, ws_test_stall=1)
+    phi = dev(np.zeros((N, M)))
+    rc, st = p.solve(dev(f), dev(g), phi)
+    assert rc == 0 and rc0 == 0
+    assert st["ws_alpha"] == -2.0
+    assert "warm start" in ot.ot_last_error()
+    assert st["newton_iters"] == st0["newton_iters"]
+    assert np.abs(phi.cpu().numpy() - phi0.cpu().numpy()).max() <= 1e-9
+    # the hook reset itself: the next solve uses the network again
+    rc2, st2 = p.solve(dev(f), dev(g), phi)
+    assert rc2 == 0 and st2["ws_alpha"] >= 0.0
+    p.close()

@@ -37,8 +37,12 @@ def _field(N, M, seed):
     return u
 
 
-@pytest.mark.parametrize("N,M", [(64, 96), (256, 256)])
-def test_noalloc_matches_plan_entry_point_twice(ot, N, M):
+# (2048, 2048) fills the fixed scratch exactly (4096 tiles of 32 x 32, 10 partials each);
+# (2048, 48) and (48, 2048) have ragged edge tiles along one axis
+@pytest.mark.parametrize("N,M,on_stream", [(64, 96, False), (256, 256, False),
+                                           (256, 256, True), (2048, 48, False),
+                                           (48, 2048, False), (2048, 2048, True)])
+def test_noalloc_matches_plan_entry_point_twice(ot, N, M, on_stream):
     import torch
 
     def dev(a):
@@ -48,6 +52,11 @@ def test_noalloc_matches_plan_entry_point_twice(ot, N, M):
         return ctypes.c_void_p(t.data_ptr())
 
     plan = ot.Plan(N, M, precision="fp64")
+    # on_stream: both entry points run on a non-default torch stream, passed by handle
+    stream = torch.cuda.Stream() if on_stream else None
+    handle = stream.cuda_stream if on_stream else 0
+    if on_stream:
+        assert ot.ot_plan_set_stream(plan.h, handle) == 0
     for call, seed in enumerate((1, 2)):  # two calls in a row on the shared scratch
         f = I.blob_density(N, M, 40 + seed)
         g = I.blob_density(N, M, 50 + seed)
@@ -59,9 +68,11 @@ def test_noalloc_matches_plan_entry_point_twice(ot, N, M):
         s_ref, s_new = np.zeros(10), np.zeros(10)
         assert ot.ot_eval_residual(plan.h, ptr(fd), ptr(cd), ptr(ud), ptr(F_ref),
                                    ptr(coef_ref), s_ref.ctypes.data_as(ctypes.c_void_p)) == 0
+        torch.cuda.synchronize()
         assert ot.ot_eval_residual_noalloc(N, M, ptr(fd), ptr(cd), ptr(ud), ptr(F_new),
                                            ptr(coef_new),
-                                           s_new.ctypes.data_as(ctypes.c_void_p)) == 0
+                                           s_new.ctypes.data_as(ctypes.c_void_p),
+                                           handle) == 0
         # the tolerance of the residual parity test (rounding bound of the stencils)
         eps = np.finfo(float).eps
         tol = 32 * eps * np.abs(u).max() * max(N, M) ** 2 * max(1, np.abs(g).max()) + 1e-13
