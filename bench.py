@@ -36,7 +36,7 @@ SYMBOLS = 1  # operator symbols of the 4th-order stencils (exact Jacobian of F)
 PAPER_ETA = 1e-1  # the paper's configuration arm: spectral symbols, GMRES tolerance 0.1
 SEED = 3000
 WS_TRAIN_SEED = 10000
-WORKLOAD = ("smoothed-noise+16-blob density pair 1024x1024 (max/min 10, mean 1), tau=1, "
+WORKLOAD = ("smoothed-noise+16-blob density pair {n}x{n} (max/min 10, mean 1), tau=1, "
             "GMRES(10) eta=0.01, stencil-symbol operator, tol 1e-8, mixed "
             "FP32-inner/FP64-outer, learned warm start")
 
@@ -216,29 +216,67 @@ def traffic_for(kernel_cls, size):
 
 
 # ----------------------------------------------------------------------------------------
-# CPU oracle sample (test infrastructure; used only for the baseline legs)
+# CPU oracle legs (test infrastructure; used only for the baseline legs).  The oracle runs
+# as it stands, in processes started with `spawn` (never forked from a CUDA process); each
+# process is single-threaded, so a leg's core count is its number of processes.
 # ----------------------------------------------------------------------------------------
-def oracle_sample(f, g, reps=1):
-    """Times the oracle's building blocks on the workload: one residual/coefficient
-    evaluation and one preconditioned matvec L Lbar^{-1} sigma (each `reps` times), and
-    extrapolates to a full solve with the oracle's own Newton/GMRES counts for this workload
-    (tests/golden/noise1024.json, written by the oracle), else the counts passed in."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_job(job):
+    """One oracle job in a worker process (spawned): 'sample' times one B-spline prefilter,
+    one residual/coefficient evaluation and one preconditioned matvec L Lbar^{-1} F on the
+    workload's pair; 'solve' runs a full oracle solve (max_newton caps it for a fixed number
+    of Newton steps).  Returns a dict of seconds and counts."""
     import numpy as np
     import oracle as O
-    t0 = time.perf_counter()
-    c = O.bspline_coeffs(g)
-    t_pre = time.perf_counter() - t0
-    u = np.zeros_like(f)
-    tr = tm = 0.0
-    for _ in range(reps):
+    import ot_inputs as I
+    kind, case = job
+    gen = {"noise": I.noise_blob_pair, "blob": I.blob_pair}
+    if case["gen"] == "manufactured":
+        f, g, _ = I.manufactured(case["N"], case["N"])
+    else:
+        f, g = gen[case["gen"]](case["N"], case["N"], s=case["seed"])
+    if kind == "sample":
         t0 = time.perf_counter()
-        F, coef, _ = O.residual(f, c, u)
-        tr += time.perf_counter() - t0
+        c = O.bspline_coeffs(g)
+        t1 = time.perf_counter()
+        F, coef, _ = O.residual(f, c, np.zeros_like(f))
+        t2 = time.perf_counter()
         abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
-        t0 = time.perf_counter()
-        O.apply_op(coef, abar, F)
-        tm += time.perf_counter() - t0
-    return t_pre, tr / reps, tm / reps
+        with O.fd_symbols(case.get("symbols", 0)):
+            O.apply_op(coef, abar, F)
+        t3 = time.perf_counter()
+        return {"t_pre": t1 - t0, "t_res": t2 - t1, "t_mv": t3 - t2, "wall": t3 - t0}
+    t0 = time.perf_counter()
+    with O.fd_symbols(case.get("symbols", 0)):
+        _, st, _, _ = O.solve(f, g, tau=case["tau"], tol=case["tol"], eta=case["eta"],
+                              max_newton=case.get("max_newton", 300))
+    st["seconds"] = time.perf_counter() - t0
+    return st
+
+
+def oracle_pool(n):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(n)
+
+
+WORKLOAD_CASE = dict(gen="noise", seed=SEED, tau=TAU, tol=TOL, eta=ETA, symbols=SYMBOLS)
 
 
 def golden_counts(size):
@@ -248,61 +286,213 @@ def golden_counts(size):
         st = d["stats"]
         return dict(newton=st["newton_iters"], gmres=st["gmres_iters"],
                     cycles=st["gmres_cycles"], halvings=st["step_halvings"],
-                    source="oracle counts from tests/golden/noise%d.json" % size)
+                    source="the oracle's own counts for this pair, tests/golden/noise%d.json"
+                    % size)
     except Exception:
         return None
 
 
 def extrapolate(t_pre, t_res, t_mv, counts):
-    # per Newton step: Simpson + theta (~ one matvec's FFT work at most) are folded into
-    # one extra matvec; residual evaluations = newton + halvings + 1
+    """Seconds of a full oracle solve from the timed building blocks: residual evaluations =
+    Newton steps + step halvings + 1; matvecs = GMRES iterations + one per restart (explicit
+    residual) + one per Newton step (theta = Lbar^-1 sigma and the Simpson sums, at most one
+    matvec's transforms)."""
     n_res = counts["newton"] + counts["halvings"] + 1
     n_mv = counts["gmres"] + (counts["cycles"] - counts["newton"]) + counts["newton"]
     return t_pre + n_res * t_res + n_mv * t_mv
 
 
-def cpu_cores():
-    return 1  # the oracle is single-threaded
+def sample_round(pool, procs, size):
+    """One round of `procs` concurrent oracle samples at size^2 (one per process, all cores
+    busy at once); returns (wall seconds of the round, summed solves/s over the processes,
+    mean per-process timings)."""
+    counts = golden_counts(size) or dict(newton=13, gmres=91, cycles=13, halvings=7,
+                                         source="assumed counts")
+    case = dict(WORKLOAD_CASE, N=size)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_job, [("sample", case)] * procs, chunksize=1)
+    wall = time.perf_counter() - t0
+    rate = sum(1.0 / extrapolate(r["t_pre"], r["t_res"], r["t_mv"], counts) for r in res)
+    mean = {k: statistics.mean(r[k] for r in res) for k in ("t_pre", "t_res", "t_mv")}
+    return wall, rate, mean, counts
+
+
+def workload_config(size, world):
+    return {"workload": WORKLOAD.format(n=size), "N": size, "M": size,
+            "warm_start": "learned (network trained before timing)",
+            "l2_flush": "256 MB write between timed steps",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 # ----------------------------------------------------------------------------------------
 def run_reference(args):
+    """The CPU oracle on this workload: every step is one bounded sample of the solve on all
+    host cores (one process per core, each timing a prefilter, a residual evaluation and a
+    matvec on the pair at full size); `ms_per_step` is the measured wall time of that round,
+    and `value` the solves/s that the timed building blocks give for the oracle's own
+    Newton/GMRES counts of this pair (extrapolated, as `extrapolation` says)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import ot_inputs as I
-    f, g = I.noise_blob_pair(args.size, args.size, s=SEED)
-    counts = golden_counts(args.size) or dict(newton=36, gmres=164, cycles=36, halvings=0,
-                                              source="assumed counts")
-    for _ in range(args.warmup):
-        oracle_sample(f, g)
-    times = []
-    for _ in range(args.steps):
-        times.append(extrapolate(*oracle_sample(f, g), counts))
-    t = statistics.mean(times)
-    value = 1.0 / t
-    sample = ("per step: one oracle residual evaluation + one preconditioned matvec at "
-              "%dx%d, extrapolated to a solve with %d Newton steps / %d GMRES iterations (%s)"
-              % (args.size, args.size, counts["newton"], counts["gmres"], counts["source"]))
+    procs = host_cores()
+    pool = oracle_pool(procs)
+    try:
+        for _ in range(args.warmup):
+            sample_round(pool, procs, args.size)
+        walls, rates = [], []
+        for _ in range(args.steps):
+            wall, rate, mean, counts = sample_round(pool, procs, args.size)
+            walls.append(wall)
+            rates.append(rate)
+    finally:
+        pool.close()
+        pool.join()
+    value = statistics.mean(rates)
+    sample = ("per step: %d concurrent single-threaded oracle processes, each timing one "
+              "B-spline prefilter (%.2fs), one residual evaluation (%.2fs) and one "
+              "preconditioned matvec (%.2fs) at %dx%d" % (procs, mean["t_pre"], mean["t_res"],
+                                                        mean["t_mv"], args.size, args.size))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1000.0, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("mixed FP32-inner/FP64-outer",
-                                                    "FP64 CPU oracle"),
-                       "size": args.size},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(),
-                             "kind": "oracle", "sample": sample},
+            "ms_per_step": statistics.mean(walls) * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.size, world),
+            "extrapolation": ("value = sum over the processes of 1 / (t_prefilter + "
+                              "(newton + halvings + 1) t_residual + (gmres + cycles) t_matvec) "
+                              "with %d Newton steps, %d step halvings, %d GMRES iterations in "
+                              "%d cycles (%s)" % (counts["newton"], counts["halvings"],
+                                                  counts["gmres"], counts["cycles"],
+                                                  counts["source"])),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": procs,
+                             "kind": "oracle", "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_ours(args):
+# the oracle jobs of the benchmark's CPU-baseline leg: the two small configurations solved in
+# full, and the timed pair for a fixed 3 Newton steps (per-step time measured)
+CPU_FULL_JOBS = {
+    "config1_manufactured_64": dict(gen="manufactured", N=64, tau=2.0, tol=1e-10, eta=1e-4),
+    "config2_blob_256": dict(gen="blob", N=256, seed=1000, tau=4.0, tol=1e-10, eta=1e-1),
+    "config3_noise_1024_3_newton_steps": dict(WORKLOAD_CASE, N=N_GRID, max_newton=3),
+}
+
+
+def cpu_baseline_start():
+    """Start the long oracle jobs in spawned processes before the GPU work (they run on
+    three host cores while the GPU is measured)."""
+    pool = oracle_pool(len(CPU_FULL_JOBS))
+    jobs = {k: pool.apply_async(_oracle_job, (("solve", v),)) for k, v in CPU_FULL_JOBS.items()}
+    return pool, jobs
+
+
+def cpu_baseline_finish(pool, jobs, size):
+    """All-core sample round at the workload size (after the GPU timing), then the results of
+    the long jobs."""
+    procs = host_cores()
+    spool = oracle_pool(procs)
+    try:
+        sample_round(spool, procs, size)  # warm-up (imports, page faults)
+        wall, rate, mean, counts = sample_round(spool, procs, size)
+        _, rate1, mean1, _ = sample_round(spool, 1, size)
+    finally:
+        spool.close()
+        spool.join()
+    out = {"value": rate, "unit": "solves/s", "cores": procs, "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": ("%d concurrent single-threaded oracle processes (one per core), each "
+                      "timing one B-spline prefilter (%.2fs), one residual evaluation (%.2fs) "
+                      "and one preconditioned matvec (%.2fs) at %dx%d (round wall %.1fs); "
+                      "solves/s extrapolated with the oracle's counts (%d Newton, %d halvings, "
+                      "%d GMRES in %d cycles; %s)"
+                      % (procs, mean["t_pre"], mean["t_res"], mean["t_mv"], size, size, wall,
+                         counts["newton"], counts["halvings"], counts["gmres"],
+                         counts["cycles"], counts["source"])),
+           "single_core": {"value": rate1, "unit": "solves/s", "cores": 1,
+                           "t_residual_s": mean1["t_res"], "t_matvec_s": mean1["t_mv"]}}
+    runs = {}
+    for k, r in jobs.items():
+        try:
+            st = r.get(timeout=900)
+        except Exception as e:  # noqa: BLE001
+            runs[k] = {"error": repr(e)}
+            continue
+        runs[k] = {"seconds": st["seconds"], "newton_iters": st["newton_iters"],
+                   "gmres_iters": st["gmres_iters"], "res_inf": st["res_inf"],
+                   "status": st["status"], "cores": 1, "settings": CPU_FULL_JOBS[k]}
+        if k.startswith("config3"):
+            per = st["seconds"] / max(1, st["newton_iters"])
+            runs[k]["seconds_per_newton_step"] = per
+            if counts.get("newton"):
+                runs[k]["extrapolated_solve_seconds"] = per * counts["newton"]
+                runs[k]["note"] = ("extrapolated: measured seconds per Newton step x the "
+                                   "oracle's %d Newton steps for this pair" % counts["newton"])
+        else:
+            runs[k]["solves_per_s"] = 1.0 / st["seconds"]
+    pool.close()
+    pool.join()
+    out["oracle_runs"] = runs
+    return out
+
+
+def run_config2(ot, stream, flush, reps=3):
     import numpy as np
     import torch
+    import ot_inputs as I
+    N = 256
+    f, g = I.blob_pair(N, N, s=1000)
+    fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    phi = torch.zeros_like(fd)
+    p = ot.Plan(N, N, tau=4.0, tol=1e-10, eta=0.1, precision="fp64", stream=stream,
+                max_newton=400)
+    p.solve(fd, gd, phi)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0.record(stream)
+        rc, st = p.solve(fd, gd, phi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= reps
+    # per-kernel-class times: one host-driven solve with every launch bracketed by events
+    p.set(profile=1)
+    p.reset_profile()
+    flush.zero_()
+    p.solve(fd, gd, phi)
+    torch.cuda.synchronize()
+    prof, _ = p.profile()
+    p.close()
+    out = {"value": 1000.0 / ms, "unit": "solves/s", "ms_per_solve": ms, "solves_timed": reps,
+           "settings": "blob_pair(256, 256, s=1000), FP64, tau=4, tol 1e-10, eta=0.1, spectral "
+                       "symbols, phi0 = 0",
+           "status": st["status"], "newton_iters": st["newton_iters"],
+           "gmres_iters": st["gmres_iters"], "step_halvings": st["step_halvings"],
+           "res_inf": st["res_inf"],
+           "kernel_ms_per_solve_host_driven": {k: round(v[0], 3) for k, v in prof.items()},
+           "kernel_launches_per_solve": {k: v[1] for k, v in prof.items()}}
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "blob256.json")) as fh:
+            gold = json.load(fh)
+        ph = phi.cpu().numpy()
+        out["phi_vs_oracle_samples_inf"] = float(np.abs(
+            ph[gold["sample_i"], gold["sample_j"]] - np.array(gold["phi_samples"])).max())
+        out["oracle_newton_iters"] = gold["stats"]["newton_iters"]
+    except Exception:
+        pass
+    return out
+
+
+def run_ours(args):
     rank, world, local = dist_env()
+    cpu_jobs = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.kernels_only:
+        cpu_jobs = cpu_baseline_start()  # spawned before the first CUDA call
+    import numpy as np
+    import torch
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -499,19 +689,28 @@ def run_ours(args):
         phi64 = torch.zeros_like(fd)
         p64.solve(fd, gd, phi64)
         torch.cuda.synchronize()
-        steps64 = 2
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        steps64 = 5
+        ms64 = 0.0
         for _ in range(steps64):
+            flush.zero_()
+            e0.record(stream)
             rc64, st64 = p64.solve(fd, gd, phi64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / steps64
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 += e0.elapsed_time(e1)
+        ms64 /= steps64
         fp64 = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_solve": ms64,
+                "solves_timed": steps64,
                 "newton_iters": st64["newton_iters"], "gmres_iters": st64["gmres_iters"],
                 "res_inf": st64["res_inf"],
                 "phi_mixed_vs_fp64_inf": float((phi_mixed - phi64).abs().max().item())}
         p64.close()
+
+    # the 256^2 blob-mixture pair on the plain FP64 path (tau = 4, tol 1e-10, the paper's
+    # spectral symbols, eta = 0.1): Newton count, solve time and per-kernel-class times
+    config2 = None
+    if not args.no_fp64:
+        config2 = run_config2(ot, stream, flush)
 
     # roofline of the dominant kernel class: per-solve launches from the profiled solve,
     # per-launch duration from back-to-back relaunches on this stream (CUDA events)
@@ -574,14 +773,11 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64+bf16", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": N, "M": M,
-                           "warm_start": "learned (network trained before timing)",
-                           "l2_flush": "256 MB write "
-                           "between timed steps", "parallelism": "replicas" if world > 1
-                           else "single GPU"},
+                "config": workload_config(N, world),
                 "grid_point_newton_iters_per_s": value * P * s0["newton_iters"],
                 "all_converged": ok, "quality": quality, "fp64_gpu": fp64,
                 "mixed_zero_start": zero_start, "paper_symbols_arm": paper_arm,
+                "config2_fp64_blob256": config2,
                 "warm_start": ws_info,
                 "e2e": {"value": e2e_value, "unit": "solves/s",
                         "h2d_bytes_per_step": 2 * P * 8, "d2h_bytes_per_step": P * 8,
@@ -592,21 +788,8 @@ def run_ours(args):
                                    "ms_total_host_driven": st_p["ms_total"]},
                 "kernels": kernels,
                 "clocks": clk.summary()}
-        if world == 1 and not args.no_cpu_baseline:
-            counts = golden_counts(N) or dict(
-                newton=s0["newton_iters"], gmres=s0["gmres_iters"],
-                cycles=s0["gmres_cycles"], halvings=s0["step_halvings"],
-                source="counts of the GPU FP64-outer solve of this pair")
-            t_pre, t_res, t_mv = oracle_sample(f, g)
-            t_cpu = extrapolate(t_pre, t_res, t_mv, counts)
-            line["cpu_baseline"] = {
-                "value": 1.0 / t_cpu, "unit": "solves/s", "cores": cpu_cores(),
-                "kind": "oracle",
-                "sample": ("one oracle residual evaluation (%.2fs) + one preconditioned matvec "
-                           "(%.2fs) + B-spline prefilter (%.2fs) at %dx%d, extrapolated to a "
-                           "solve with %d Newton steps / %d GMRES iterations (%s)"
-                           % (t_res, t_mv, t_pre, N, M, counts["newton"], counts["gmres"],
-                              counts["source"]))}
+        if cpu_jobs is not None:
+            line["cpu_baseline"] = cpu_baseline_finish(*cpu_jobs, N)
         print(json.dumps(line), flush=True)
     plan.close()
     if world > 1:

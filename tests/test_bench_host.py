@@ -56,3 +56,29 @@ def test_traffic_record_is_reported_only_for_the_current_source(tmp_path, monkey
     assert bench.traffic_for("residual", 1024) is None        # no record
     src.write_text("__global__ void k() { /* changed */ }\n")
     assert bench.traffic_for("col_matvec", 1024) is None      # source changed since
+
+
+def test_reference_arm_line_describes_the_region_it_timed():
+    # the reference arm (the CPU oracle on all host cores): its steps x ms_per_step must fit
+    # in the wall time of the run, its config must be the benchmark's own, and its core count
+    # the processes it used
+    import subprocess
+    import sys
+    import time
+    t0 = time.time()
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl",
+                          "reference", "--steps", "2", "--warmup", "1", "--size", "64"],
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    wall = time.time() - t0
+    line = json.loads(out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["steps"] * line["ms_per_step"] / 1000.0 <= wall
+    assert line["config"] == bench.workload_config(64, 1)
+    assert line["cpu_baseline"]["cores"] == bench.host_cores()
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_extrapolation_counts_every_residual_and_matvec():
+    counts = dict(newton=13, halvings=7, gmres=91, cycles=13)
+    # 21 residual evaluations, 91 + 0 + 13 matvecs
+    assert bench.extrapolate(1.0, 2.0, 3.0, counts) == 1.0 + 21 * 2.0 + 104 * 3.0
