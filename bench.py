@@ -190,6 +190,10 @@ def variant_names(v):
            3: "k_col<float, 4, 2>"}
     comb = {0: "k_row_c2r<float, 8, 1>", 1: "k_row_combine_par<float, 8>",
             2: "k_row_combine_w<float>", 3: "k_row_c2r<float, 4, 1>"}
+    if v & 128:
+        return {"code": v, "row_r2c": "k_mvT_r2c<M/2>", "col_matvec": "k_mvT_col<N>",
+                "row_c2r_combine": "k_mvT_combine<M/2>", "col_q4": False,
+                "register_resident": True}
     return {"code": v, "row_r2c": row[r], "col_matvec": col[c], "row_c2r_combine": comb[b],
             "col_q4": bool(v & 64)}
 

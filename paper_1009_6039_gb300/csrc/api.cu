@@ -42,6 +42,7 @@ struct ot_plan {
   void *spec64 = nullptr, *q64 = nullptr;
   void *tw64 = nullptr, *tw32 = nullptr;  // twiddles: M/2 row (base + 3 stage tables), W_M, N column (base + 3)
   void* twdd = nullptr;                    // the same as (hi, lo) float pairs
+  void* tw2 = nullptr;  // FP32 exchange twiddles of the register-resident matvec passes
   void *sym64 = nullptr, *sym32 = nullptr;  // derivative symbol tables (M/2 + 1 + N pairs)
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
@@ -252,7 +253,7 @@ static void free_buffers(ot_plan* p) {
   p->uout = nullptr;
   void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
                   p->sigma, p->spec, p->q0, p->q1, p->q2, p->spec64, p->q64, p->tw64,
-                  p->tw32, p->twdd, p->sym64, p->sym32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
+                  p->tw32, p->twdd, p->tw2, p->sym64, p->sym32, p->partials, p->dmean, p->sc, p->ws_src, p->ws_h, p->ws_tmp,
                   p->ws_X, p->ws_s, p->ws_c32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -263,7 +264,8 @@ static void free_buffers(ot_plan* p) {
   p->hinit = nullptr;
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
-  p->spec64 = p->q64 = p->tw64 = p->tw32 = p->twdd = nullptr;
+  p->spec64 = p->q64 = p->tw64 = p->tw32 = p->twdd = p->tw2 = nullptr;
+  p->tb32.t2rA = p->tb32.t2rB = p->tb32.t2cA = p->tb32.t2cB = nullptr;
   p->sym64 = p->sym32 = nullptr;
   p->fdd = p->cdd = nullptr;
   p->partials = p->dmean = nullptr;
@@ -357,6 +359,39 @@ static int fill_symbols(ot_plan* p) {
   return OT_OK;
 }
 
+// Exchange twiddles W_L^{t ka} = exp(-2 pi i t ka / L) (t < L/32, ka < 32) of the two-level
+// register transforms, for the row length L = M/2 and the column length N, in the two layouts
+// the kernels read contiguously: A at [ka * (L/32) + t], B at [t * 32 + ka].
+static int fill_reg_twiddles(ot_plan* p) {
+  const int Ls[2] = {p->M / 2, p->N};
+  std::vector<float> h;
+  for (int L : Ls) {
+    const int T = L / 32;
+    std::vector<float> A(2 * (size_t)L), B(2 * (size_t)L);
+    for (int ka = 0; ka < 32; ++ka)
+      for (int t = 0; t < T; ++t) {
+        const long e = ((long)t * ka) % L;
+        const double a = 2.0 * M_PI * (double)e / (double)L;
+        const float c = (float)std::cos(a), sn = (float)-std::sin(a);
+        A[2 * ((size_t)ka * T + t)] = c;
+        A[2 * ((size_t)ka * T + t) + 1] = sn;
+        B[2 * ((size_t)t * 32 + ka)] = c;
+        B[2 * ((size_t)t * 32 + ka) + 1] = sn;
+      }
+    h.insert(h.end(), A.begin(), A.end());
+    h.insert(h.end(), B.begin(), B.end());
+  }
+  CK(cudaMalloc(&p->tw2, h.size() * sizeof(float)));
+  CK(cudaMemcpy(p->tw2, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  const float2* b = (const float2*)p->tw2;
+  const size_t Lr = p->M / 2;
+  p->tb32.t2rA = b;
+  p->tb32.t2rB = b + Lr;
+  p->tb32.t2cA = b + 2 * Lr;
+  p->tb32.t2cB = b + 2 * Lr + p->N;
+  return OT_OK;
+}
+
 static int alloc_buffers(ot_plan* p) {
   free_buffers(p);
   const size_t P = (size_t)p->N * p->M;
@@ -411,6 +446,7 @@ static int alloc_buffers(ot_plan* p) {
   p->tbdd.twM = (const ddc*)p->twdd + 4 * L;
   p->tbdd.twN = (const ddc*)p->twdd + 5 * L;
   RET(fill_symbols(p));
+  if (p->precision && mvT_supported(p->N, p->M)) RET(fill_reg_twiddles(p));
   p->tb64.twL = p->tw64;
   p->tb64.twM = (const double2*)p->tw64 + 4 * L;
   p->tb64.twN = (const double2*)p->tw64 + 5 * L;
@@ -551,8 +587,11 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       // r2c + 4 col + 16 combine, each 0 generic, 1 concurrent (r2c: same as 0), 2 warp,
       // 3 generic with 4 elements per thread
       // + 64: the generic column pass with 4 columns per block
-      if (v < 0 || v > 127 || v != (double)(int)v) return OT_EINVAL;
+      // + 128: the register-resident passes on the transposed spectrum for all three (where
+      // the lengths allow them; the other bits then apply elsewhere)
+      if (v < 0 || v > 255 || v != (double)(int)v) return OT_EINVAL;
       const int k = (int)v & 63;
+      p->tb32.mv_reg = ((int)v & 128) ? 1 : 0;
       p->tb32.var_r2c = k % 4 == 1 ? VAR_GENERIC : k % 4;
       p->tb32.var_col = (k / 4) % 4;
       p->tb32.var_comb = k / 16;
@@ -594,6 +633,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       p->autotune = (int)v;
       if (!p->autotune) {
         p->tb32.var_r2c = p->tb32.var_col = p->tb32.var_comb = VAR_DEFAULT;
+        p->tb32.mv_reg = 0;
         p->tuned = 0;
       }
       free_graph(p);
@@ -633,7 +673,8 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
         *v = -1;
         return OT_OK;
       }
-      *v = tb.var_r2c + 4 * tb.var_col + 16 * tb.var_comb + (tb.col_q == 4 ? 64 : 0);
+      *v = tb.var_r2c + 4 * tb.var_col + 16 * tb.var_comb + (tb.col_q == 4 ? 64 : 0) +
+           (tb.mv_reg && tb.t2rA ? 128 : 0);
       return OT_OK;
     }
   }
@@ -656,7 +697,18 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
   const SpecTables& tb = tables<T>(p);
   const int N = p->N, M = p->M;
   const size_t P = (size_t)N * M;
+  const bool reg = sizeof(T) == 4 && tb.mv_reg && tb.t2rA;
   auto one = [&]() -> cudaError_t {
+    if (reg && cls == OT_PROF_ROW_R2C)
+      return launch_mvT_r2c((const float*)p->V, P, nullptr, nullptr, (float2*)p->spec, N, M, tb,
+                            nullptr, p->stream);
+    if (reg && cls == OT_PROF_COL_MATVEC)
+      return launch_mvT_col((const float2*)p->spec, (float2*)p->q0, (float2*)p->q1,
+                            (float2*)p->q2, N, M, tb, p->sc, nullptr, p->stream);
+    if (reg && cls == OT_PROF_ROW_C2R_COMBINE)
+      return launch_mvT_combine((const float2*)p->q0, (const float2*)p->q1,
+                                (const float2*)p->q2, (const float*)p->coef, (float*)p->w, N, M,
+                                tb, nullptr, p->stream);
     switch (cls) {
       case OT_PROF_RESIDUAL:
         return residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, nullptr, 0);
@@ -768,6 +820,20 @@ static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* sca
                       const int* skip, int tag) {
   const size_t P = (size_t)p->N * p->M;
   const SpecTables& tb = tables<T>(p);
+  if (sizeof(T) == 4 && tb.mv_reg && tb.t2rA) {
+    // register-resident passes on the transposed half spectrum
+    LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
+           launch_mvT_r2c((const float*)x, P, jptr, scale, (float2*)p->spec, p->N, p->M, tb,
+                          skip, p->stream));
+    LAUNCH(p, OT_PROF_COL_MATVEC, tag, 1,
+           launch_mvT_col((const float2*)p->spec, (float2*)p->q0, (float2*)p->q1,
+                          (float2*)p->q2, p->N, p->M, tb, p->sc, skip, p->stream));
+    LAUNCH(p, OT_PROF_ROW_C2R_COMBINE, tag, 1,
+           launch_mvT_combine((const float2*)p->q0, (const float2*)p->q1,
+                              (const float2*)p->q2, (const float*)p->coef, (float*)w, p->N,
+                              p->M, tb, skip, p->stream));
+    return OT_OK;
+  }
   LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
          launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip,
                            p->stream));
@@ -1281,7 +1347,7 @@ static int capture_solve(ot_plan* p) {
 // fastest is kept, and the choice is cached per (N, M) for the process.
 // ------------------------------------------------------------------------------------------
 static std::mutex g_tune_mutex;
-static std::vector<std::vector<int>> g_tune_cache;  // {N, M, r2c, col, comb}
+static std::vector<std::vector<int>> g_tune_cache;  // {N, M, r2c, col, comb, col_q, mv_reg}
 
 static int run_autotune(ot_plan* p) {
   if (!p->precision || !p->autotune || p->tuned) return OT_OK;
@@ -1294,6 +1360,7 @@ static int run_autotune(ot_plan* p) {
         p->tb32.var_col = e[3];
         p->tb32.var_comb = e[4];
         p->tb32.col_q = e[5];
+        p->tb32.mv_reg = e[6];
         p->tuned = 1;
         return OT_OK;
       }
@@ -1313,6 +1380,17 @@ static int run_autotune(ot_plan* p) {
   SpecTables& tb = p->tb32;
   auto timed = [&](int cls) -> float {
     auto one = [&]() -> cudaError_t {
+      if (tb.mv_reg) {
+        if (cls == 0)
+          return launch_mvT_r2c((const float*)p->V, P, nullptr, nullptr, (float2*)p->spec, N,
+                                M, tb, nullptr, st);
+        if (cls == 1)
+          return launch_mvT_col((const float2*)p->spec, (float2*)p->q0, (float2*)p->q1,
+                                (float2*)p->q2, N, M, tb, p->sc, nullptr, st);
+        return launch_mvT_combine((const float2*)p->q0, (const float2*)p->q1,
+                                  (const float2*)p->q2, (const float*)p->coef, (float*)p->w, N,
+                                  M, tb, nullptr, st);
+      }
       if (cls == 0)
         return launch_row_r2c<float>((const float*)p->V, P, nullptr, nullptr,
                                      (C2<float>*)p->spec, N, M, tb, nullptr, st);
@@ -1338,6 +1416,7 @@ static int run_autotune(ot_plan* p) {
     return ms;
   };
   tb.col_q = 0;
+  tb.mv_reg = 0;
   int* vars[3] = {&tb.var_r2c, &tb.var_col, &tb.var_comb};
   const int ncand[3] = {3, 4, 4};
   const int cand[3][4] = {{VAR_GENERIC, VAR_WARP, VAR_E4, VAR_E4},
@@ -1346,6 +1425,7 @@ static int run_autotune(ot_plan* p) {
   // every candidate is timed in two rounds and keeps its faster time: the first launches
   // of a process run while the clocks and caches settle, which would otherwise penalise
   // whichever candidate is timed first
+  float tsum = 0.f;  // the chosen per-pass variants' times, summed
   for (int cls = 0; cls < 3; ++cls) {
     int best = VAR_GENERIC, bestq = 0;
     float tbest = 1e30f;
@@ -1373,6 +1453,16 @@ static int run_autotune(ot_plan* p) {
       }
     *vars[cls] = best;
     if (cls == 1) tb.col_q = bestq;
+    tsum += tbest;
+  }
+  // the register-resident passes on the transposed spectrum replace all three at once:
+  // kept when their summed time is below the per-pass choice's (two rounds, faster kept)
+  if (tb.t2rA) {
+    tb.mv_reg = 1;
+    float treg[2] = {0.f, 0.f};
+    for (int round = 0; round < 2; ++round)
+      for (int cls = 0; cls < 3; ++cls) treg[round] += timed(cls);
+    tb.mv_reg = std::min(treg[0], treg[1]) < tsum ? 1 : 0;
   }
 
   cudaGetLastError();
@@ -1380,7 +1470,7 @@ static int run_autotune(ot_plan* p) {
   cudaEventDestroy(b);
   p->tuned = 1;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb, tb.col_q});
+  g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb, tb.col_q, tb.mv_reg});
   return OT_OK;
 }
 

@@ -124,6 +124,15 @@ struct SpecTables {
   int var_r2c = -1, var_col = -1, var_comb = -1;
   // generic column matvec pass: columns per block (0: the default heuristic)
   int col_q = 0;
+  // register-resident matvec passes on the transposed half spectrum (FP32, power-of-two
+  // lengths 64..1024; spectral_reg.cu): mv_reg = 1 uses them for all three passes.
+  // Exchange twiddles W_L^{t ka} of the two-level transforms, for the row length L = M/2
+  // (t2r) and the column length N (t2c): A at [ka * (L/32) + t], B at [t * 32 + ka].
+  int mv_reg = 0;
+  const void* t2rA = nullptr;
+  const void* t2rB = nullptr;
+  const void* t2cA = nullptr;
+  const void* t2cB = nullptr;
 };
 enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2, VAR_E4 = 3 };
 
@@ -142,6 +151,20 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double out_scale, int N, int M, const SpecTables& tb,
                            const int* skip, cudaStream_t st, const DevScalars* sc = nullptr);
+
+// register-resident FP32 matvec passes on the transposed half spectrum specT (M/2 x N,
+// entry (k1, k2) at k1 N + k2): mvT_supported(N, M) when N and M/2 are powers of two in
+// 64..1024
+bool mvT_supported(int N, int M);
+cudaError_t launch_mvT_r2c(const float* x, size_t x_stride, const int* jptr,
+                           const double* scale, float2* specT, int N, int M,
+                           const SpecTables& tb, const int* skip, cudaStream_t st);
+cudaError_t launch_mvT_col(const float2* specT, float2* out0, float2* out1, float2* out2,
+                           int N, int M, const SpecTables& tb, const DevScalars* sc,
+                           const int* skip, cudaStream_t st);
+cudaError_t launch_mvT_combine(const float2* q0T, const float2* q1T, const float2* q2T,
+                               const float* coef, float* out, int N, int M,
+                               const SpecTables& tb, const int* skip, cudaStream_t st);
 
 // theta = Lbar^{-1} sigma column pass, FP32 forward / FP64 inverse (mixed mode)
 cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, int M,

@@ -195,7 +195,7 @@ def test_longest_transforms(ot, N, M, prec):
 @pytest.mark.parametrize("N,M", [(24, 48), (128, 48), (192, 384), (256, 256), (512, 512),
                                  (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
-                                     3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64])
+                                     3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64, 128])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
     # (at 1024^2 the concurrent column pass, launched first, needs more shared memory than
@@ -215,6 +215,31 @@ def test_fp32_kernel_variants(ot, N, M, variant):
     p.close()
 
 
+@pytest.mark.parametrize("N,M", [(64, 128), (128, 2048), (1024, 128), (256, 512),
+                                 (512, 256), (1024, 1024)])
+def test_register_resident_matvec(ot, N, M):
+    # the register-resident passes on the transposed spectrum (OT_OPT_FFT_VARIANT bit 128)
+    # at every length they cover (N and M/2 powers of two in 64..1024), rectangular grids
+    # included: the same operator as the oracle within the FP32 bounds of the other variants,
+    # and the kernels in use read back through the option
+    f = I.blob_density(N, M, 25)
+    g = I.blob_density(N, M, 26)
+    u = smooth_field(N, M, amp=2e-3)
+    _, coef, _ = O.residual(f, O.bspline_coeffs(g), u)
+    abar = np.array([O.simpson_mean(coef[q]) for q in range(5)])
+    sigma = RNG.standard_normal((N, M))
+    for symbols in (0, 1):
+        with O.fd_symbols(symbols):
+            w_ref = O.apply_op(coef, abar, sigma)
+        p = plan(ot, N, M, "mixed", fft_variant=128, symbols=symbols)
+        assert int(p.get("fft_variant")) & 128
+        cd, sd, wd = dev(coef), dev(sigma), dev(np.zeros((N, M)))
+        assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
+        assert np.abs(wd.cpu().numpy() - w_ref).max() <= 5e-6 * np.abs(w_ref).max()
+        assert np.linalg.norm(wd.cpu().numpy() - w_ref) <= 2e-6 * np.linalg.norm(w_ref)
+        p.close()
+
+
 def test_autotuned_solve_matches_fixed_variant(ot):
     f, g = I.blob_pair(256, 256, s=41)
     out = []
@@ -224,7 +249,7 @@ def test_autotuned_solve_matches_fixed_variant(ot):
         rc, st = p.solve(dev(f), dev(g), phi)
         # the variants in use read back in the encoding the option takes
         v = p.get("fft_variant")
-        assert v == 0 if "fft_variant" in kw else 0 <= v <= 127
+        assert v == 0 if "fft_variant" in kw else 0 <= v <= 255
         assert p.get("tau") == 4.0 and p.get("precision") == 1
         p.close()
         assert rc == 0 and st["status"] == 0
@@ -440,8 +465,9 @@ def test_warm_start_from_solution_takes_no_step(ot):
     assert np.abs(phid.cpu().numpy() - phi).max() < 1e-15
 
 
-@pytest.mark.parametrize("N,M", [(256, 256), (192, 384), (1024, 1024)])
-def test_fp32_operator_norm_accuracy(ot, N, M):
+@pytest.mark.parametrize("N,M,variant", [(256, 256, 0), (192, 384, 0), (1024, 1024, 0),
+                                         (1024, 1024, 128)])
+def test_fp32_operator_norm_accuracy(ot, N, M, variant):
     # The FP32 operator must stay at FP32 round-off in the 2-norm (a few 1e-7 per FFT pass,
     # ~1e-6 for the whole matvec), also for inputs whose spectrum spans many decades
     # (a smooth field plus small high-frequency noise, like a Newton residual late in the
@@ -451,7 +477,7 @@ def test_fp32_operator_norm_accuracy(ot, N, M):
     g = I.blob_density(N, M, 32)
     u = smooth_field(N, M, amp=2e-3)
     c = O.bspline_coeffs(g)
-    p64, p32 = plan(ot, N, M, "fp64"), plan(ot, N, M, "mixed")
+    p64, p32 = plan(ot, N, M, "fp64"), plan(ot, N, M, "mixed", fft_variant=variant)
     fd, cd, ud = dev(f), dev(c), dev(u)
     coefd, scal = dev(np.zeros((5, N, M))), np.zeros(10)
     assert ot.ot_eval_residual(p64.h, ptr(fd), ptr(cd), ptr(ud), ptr(dev(np.zeros((N, M)))),
