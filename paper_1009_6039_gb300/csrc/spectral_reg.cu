@@ -164,7 +164,6 @@ __device__ __forceinline__ void fft2l_inv(float2 (&v)[32], float2* sbuf, int t,
 template <int L> __host__ __device__ constexpr int mv_rows() {
   return (L / 32) >= 16 ? 4 : 64 / (L / 32);
 }
-template <int L> __host__ __device__ constexpr int mv_cols() { return 64 / (L / 32); }
 
 // ---------------------------------------------------------------------------------------
 // Row pass: sigma (N x M real, M = 2L) -> packed half spectrum, transposed (specT[k][row]).
@@ -227,10 +226,16 @@ __global__ void __launch_bounds__(128)
 }
 
 // ---------------------------------------------------------------------------------------
-// Column pass (column length NL = N): one group of T = NL/32 threads per column k1.
+// Column pass (column length NL = N): CB columns per block, three groups of T = NL/32
+// threads per column (one warp per group and column set).  Group 0 runs the forward column
+// transform and forms S = rho-bar sigma-hat / (N M) in shared memory; after one block
+// barrier group p runs inverse transform p (Q0 = S, Q1 = (i s1(k2)) S, Q2 = s2(k2) S), so
+// the three inverse transforms of a column run at the same time.
 // ---------------------------------------------------------------------------------------
+template <int NL> __host__ __device__ constexpr int mv_cols() { return 32 / (NL / 32); }
+
 template <int NL>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(96)
     k_mvT_col(const float2* __restrict__ specT, float2* __restrict__ o0,
               float2* __restrict__ o1, float2* __restrict__ o2, int M, float inv_nm,
               const float2* __restrict__ twA, const float2* __restrict__ twB,
@@ -238,83 +243,84 @@ __global__ void __launch_bounds__(128)
               const float2* __restrict__ symx, const float2* __restrict__ symy) {
   if (skip && *skip) return;
   constexpr int T = NL / 32, CB = mv_cols<NL>(), SB = xbuf_len<NL>();
-  static_assert(SB >= NL, "exchange buffer holds a column");
+  static_assert(SB >= NL && CB * T == 32, "one warp per group; a column fits the buffer");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   const int Lc = M / 2;
-  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
-  const int col = blockIdx.x * CB + g;
+  const int grp = threadIdx.x >> 5, rem = threadIdx.x & 31;
+  const int c = rem / T, t = rem - c * T;
+  const int col = blockIdx.x * CB + c;
   const bool active = col < Lc;
-  float2* sbuf = sm + g * SB;
-  float2* sS = sm + CB * SB + g * NL;  // S of this column (natural order k2)
-  float2* s0buf = sm + CB * (SB + NL);  // Q0 of column 0 (its Nyquist channel premultiplied)
-  const float2* src = specT + (size_t)(active ? col : 0) * NL;
-  float2 v[32];
+  float2* sbuf = sm + (grp * CB + c) * SB;
+  float2* sS = sm + 3 * CB * SB + c * NL;  // S of this column (natural order k2)
+  float2* s0buf = sm + CB * (3 * SB + NL);  // Q0 of column 0 (its Nyquist channel premultiplied)
+  if (grp == 0) {
+    const float2* src = specT + (size_t)(active ? col : 0) * NL;
+    float2 v[32];
 #pragma unroll
-  for (int m = 0; m < 32; ++m) v[m] = active ? src[t + T * m] : make_float2(0.f, 0.f);
-  fft2l_fwd<NL>(v, sbuf, t, twA);
-  // thread t holds sigma-hat(k1 = col, k2 = k) at v[j T + kb], k = t + T j + 32 kb.
-  // Column 0 carries the two real columns k1 = 0 and k1 = M/2 as A + i B: unpacking needs
-  // the entry at N - k, which another thread holds (every group exchanges, so that all
-  // lanes of a warp take the same path).
+    for (int m = 0; m < 32; ++m) v[m] = active ? src[t + T * m] : make_float2(0.f, 0.f);
+    fft2l_fwd<NL>(v, sbuf, t, twA);
+    // thread t holds sigma-hat(k1 = col, k2 = k) at v[j T + kb], k = t + T j + 32 kb.
+    // Column 0 carries the two real columns k1 = 0 and k1 = M/2 as A + i B: unpacking needs
+    // the entry at N - k, which another thread holds (every column exchanges, so that all
+    // lanes of the warp take the same path).
 #pragma unroll
-  for (int j = 0; j < 32 / T; ++j)
+    for (int j = 0; j < 32 / T; ++j)
 #pragma unroll
-    for (int kb = 0; kb < T; ++kb) sbuf[t + T * j + 32 * kb] = v[j * T + kb];
-  __syncwarp();
-  float ab[5];
+      for (int kb = 0; kb < T; ++kb) sbuf[t + T * j + 32 * kb] = v[j * T + kb];
+    __syncwarp();
+    float ab[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
-  const float2 sxc = symx[active ? col : 0];
-  const float2 sx0 = symx[0], sxn = symx[M / 2];
-  const float d11n = sxn.y;
-#pragma unroll
-  for (int j = 0; j < 32 / T; ++j) {
-#pragma unroll
-    for (int kb = 0; kb < T; ++kb) {
-      const int k = t + T * j + 32 * kb;
-      const float2 z = v[j * T + kb];
-      const float2 sy = symy[k];
-      if (col == 0) {
-        const float2 p = sbuf[(NL - k) & (NL - 1)];
-        float2 A = make_float2(0.5f * (z.x + p.x), 0.5f * (z.y - p.y));
-        float2 B = make_float2(0.5f * (z.y + p.y), -0.5f * (z.x - p.x));
-        A = cmul<float>(rho_bar<float>(ab, sx0, sy), A);
-        B = cmul<float>(rho_bar<float>(ab, sxn, sy), B);
-        const float2 Bn = cscale<float>(B, d11n);
-        s0buf[k] = cscale<float>(make_float2(A.x - Bn.y, A.y + Bn.x), inv_nm);
-        sS[k] = cscale<float>(make_float2(A.x - B.y, A.y + B.x), inv_nm);
-      } else {
-        sS[k] = cscale<float>(cmul<float>(rho_bar<float>(ab, sxc, sy), z), inv_nm);
-      }
-    }
-  }
-  __syncwarp();
-  // the three inverse column transforms, S read back from shared memory (each thread its
-  // own entries) so that only one 32-element array is live in registers
-#pragma unroll 1
-  for (int p = 0; p < 3; ++p) {
-    float2 u[32];
+    for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
+    const float2 sxc = symx[active ? col : 0];
+    const float2 sx0 = symx[0], sxn = symx[M / 2];
+    const float d11n = sxn.y;
 #pragma unroll
     for (int j = 0; j < 32 / T; ++j) {
 #pragma unroll
       for (int kb = 0; kb < T; ++kb) {
         const int k = t + T * j + 32 * kb;
-        const float2 s = sS[k];
-        if (p == 0) {
-          u[j * T + kb] = (col == 0) ? s0buf[k] : s;
+        const float2 z = v[j * T + kb];
+        const float2 sy = symy[k];
+        if (col == 0) {
+          const float2 q = sbuf[(NL - k) & (NL - 1)];
+          float2 A = make_float2(0.5f * (z.x + q.x), 0.5f * (z.y - q.y));
+          float2 B = make_float2(0.5f * (z.y + q.y), -0.5f * (z.x - q.x));
+          A = cmul<float>(rho_bar<float>(ab, sx0, sy), A);
+          B = cmul<float>(rho_bar<float>(ab, sxn, sy), B);
+          const float2 Bn = cscale<float>(B, d11n);
+          s0buf[k] = cscale<float>(make_float2(A.x - Bn.y, A.y + Bn.x), inv_nm);
+          sS[k] = cscale<float>(make_float2(A.x - B.y, A.y + B.x), inv_nm);
         } else {
-          const float2 sy = symy[k];
-          u[j * T + kb] = (p == 1) ? make_float2(-sy.x * s.y, sy.x * s.x) : cscale<float>(s, sy.y);
+          sS[k] = cscale<float>(cmul<float>(rho_bar<float>(ab, sxc, sy), z), inv_nm);
         }
       }
     }
-    fft2l_inv<NL>(u, sbuf, t, twB);
-    if (active) {
-      float2* dst = (p == 0 ? o0 : (p == 1 ? o1 : o2)) + (size_t)col * NL;
+  }
+  __syncthreads();
+  // inverse transform p = grp of this column; each thread reads the entries of S it would
+  // hold in the transform's input distribution
+  float2 u[32];
 #pragma unroll
-      for (int m = 0; m < 32; ++m) dst[t + T * m] = u[m];
+  for (int j = 0; j < 32 / T; ++j) {
+#pragma unroll
+    for (int kb = 0; kb < T; ++kb) {
+      const int k = t + T * j + 32 * kb;
+      const float2 s = sS[k];
+      if (grp == 0) {
+        u[j * T + kb] = (col == 0) ? s0buf[k] : s;
+      } else {
+        const float2 sy = symy[k];
+        u[j * T + kb] =
+            (grp == 1) ? make_float2(-sy.x * s.y, sy.x * s.x) : cscale<float>(s, sy.y);
+      }
     }
+  }
+  fft2l_inv<NL>(u, sbuf, t, twB);
+  if (active) {
+    float2* dst = (grp == 0 ? o0 : (grp == 1 ? o1 : o2)) + (size_t)col * NL;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) dst[t + T * m] = u[m];
   }
 }
 
@@ -323,83 +329,87 @@ __global__ void __launch_bounds__(128)
 // w = a11 d_xx + b1 d_x (on Q0) + 2 a12 d_x + b2 (on Q1) + a22 (on Q2).  The complex-to-real
 // step of a packed row: Z_k = (X_k + conj X_{L-k}) + i (X_k - conj X_{L-k}) conj(W_M^k)
 // (Z_0 = (X_0.x + X_0.y) + i (X_0.x - X_0.y)); the inverse length-L transform of Z gives the
-// real pairs (y[2n], y[2n+1]).
+// real pairs (y[2n], y[2n+1]).  RB = 32/T rows per block and five groups (one warp each),
+// one per term: the five transforms of a row run at the same time, each group leaves its
+// weighted term in its exchange buffer, and the block sums them.
 // ---------------------------------------------------------------------------------------
+template <int L> __host__ __device__ constexpr int mv_rows5() { return 32 / (L / 32); }
+
 template <int L>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(160)
     k_mvT_combine(const float2* __restrict__ q0T, const float2* __restrict__ q1T,
                   const float2* __restrict__ q2T, const float* __restrict__ coef,
                   float* __restrict__ out, int N, const float2* __restrict__ twB,
                   const float2* __restrict__ twM, const int* __restrict__ skip,
                   const float2* __restrict__ symx) {
   if (skip && *skip) return;
-  constexpr int T = L / 32, RB = mv_rows<L>(), M = 2 * L, SB = xbuf_len<L>(), NB = L + 1;
+  constexpr int T = L / 32, RB = mv_rows5<L>(), M = 2 * L, SB = xbuf_len<L>(), NB = L + 1;
+  static_assert(RB * T == 32 && SB >= L, "one warp per term group; a row fits the buffer");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
-  const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+  const int term = threadIdx.x >> 5, rem = threadIdx.x & 31;
+  const int g = rem / T, t = rem - g * T;
   const int row0 = blockIdx.x * RB, row = row0 + g;
   const bool active = row < N;
-  float2* sbuf = sm + g * SB;
-  float2* qs = sm + RB * SB;  // [plane][row][NB]
+  float2* qs = sm;                                   // [plane][row][NB]
+  float2* sbuf = sm + 3 * RB * NB + (term * RB + g) * SB;
   for (int idx = threadIdx.x; idx < 3 * L * RB; idx += blockDim.x) {
-    const int p = idx / (L * RB), rem = idx - p * (L * RB);
-    const int k = rem / RB, r = rem - k * RB;
+    const int p = idx / (L * RB), r0 = idx - p * (L * RB);
+    const int k = r0 / RB, r = r0 - k * RB;
     const float2* q = p == 0 ? q0T : (p == 1 ? q1T : q2T);
     qs[(p * RB + r) * NB + k] =
         (row0 + r < N) ? q[(size_t)k * N + row0 + r] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // w of this row, accumulated over the five terms in shared memory (each thread its own
-  // entries), so that only one 32-element array is live in registers
-  float2* acc = sm + RB * SB + 3 * RB * NB + g * L;
-  const size_t P = (size_t)N * M;
-  const size_t orow = (size_t)(active ? row : 0) * M;
-#pragma unroll 1
-  for (int term = 0; term < 5; ++term) {
-    // term: source plane, row symbol kind (0: 1, 1: d/dx, 2: d2/dx2), coefficient plane
-    const int plane = term < 2 ? 0 : (term < 4 ? 1 : 2);
-    const int kind = term == 0 ? 2 : ((term == 1 || term == 2) ? 1 : 0);
-    const int cidx = term == 0 ? 0 : (term == 1 ? 3 : (term == 2 ? 1 : (term == 3 ? 4 : 2)));
-    const float mult = term == 2 ? 2.f : 1.f;
-    const float2* qr = qs + (plane * RB + g) * NB;
-    float2 v[32];
+  // term: source plane, row symbol kind (0: 1, 1: d/dx, 2: d2/dx2), coefficient plane
+  const int plane = term < 2 ? 0 : (term < 4 ? 1 : 2);
+  const int kind = term == 0 ? 2 : ((term == 1 || term == 2) ? 1 : 0);
+  const int cidx = term == 0 ? 0 : (term == 1 ? 3 : (term == 2 ? 1 : (term == 3 ? 4 : 2)));
+  const float mult = term == 2 ? 2.f : 1.f;
+  const float2* qr = qs + (plane * RB + g) * NB;
+  float2 v[32];
 #pragma unroll
-    for (int j = 0; j < 32 / T; ++j) {
+  for (int j = 0; j < 32 / T; ++j) {
 #pragma unroll
-      for (int kb = 0; kb < T; ++kb) {
-        const int k = t + T * j + 32 * kb;
-        const float2 X = row_symbol_apply<float>(qr[k], k, kind, symx);
-        float2 Z;
-        if (k == 0) {
-          Z = make_float2(X.x + X.y, X.x - X.y);
-        } else {
-          const float2 Xm = row_symbol_apply<float>(qr[L - k], L - k, kind, symx);
-          const float2 Ev = make_float2(X.x + Xm.x, X.y - Xm.y);
-          const float2 dv = make_float2(X.x - Xm.x, X.y + Xm.y);
-          const float2 Ov = cmul<float>(dv, cconj<float>(twM[k]));
-          Z = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
-        }
-        v[j * T + kb] = Z;
-      }
-    }
-    fft2l_inv<L>(v, sbuf, t, twB);
-    const float2* cr = reinterpret_cast<const float2*>(coef + (size_t)cidx * P + orow);
-#pragma unroll
-    for (int m = 0; m < 32; ++m) {
-      const float2 a = active ? cr[t + T * m] : make_float2(0.f, 0.f);
-      const float2 y = make_float2(mult * a.x * v[m].x, mult * a.y * v[m].y);
-      if (term == 0) {
-        acc[t + T * m] = y;
+    for (int kb = 0; kb < T; ++kb) {
+      const int k = t + T * j + 32 * kb;
+      const float2 X = row_symbol_apply<float>(qr[k], k, kind, symx);
+      float2 Z;
+      if (k == 0) {
+        Z = make_float2(X.x + X.y, X.x - X.y);
       } else {
-        const float2 s = acc[t + T * m];
-        acc[t + T * m] = make_float2(s.x + y.x, s.y + y.y);
+        const float2 Xm = row_symbol_apply<float>(qr[L - k], L - k, kind, symx);
+        const float2 Ev = make_float2(X.x + Xm.x, X.y - Xm.y);
+        const float2 dv = make_float2(X.x - Xm.x, X.y + Xm.y);
+        const float2 Ov = cmul<float>(dv, cconj<float>(twM[k]));
+        Z = make_float2(Ev.x - Ov.y, Ev.y + Ov.x);
       }
+      v[j * T + kb] = Z;
     }
   }
-  if (!active) return;
-  float2* o = reinterpret_cast<float2*>(out + orow);
+  fft2l_inv<L>(v, sbuf, t, twB);
+  // the weighted term into this group's exchange buffer (free after the transform)
+  const size_t P = (size_t)N * M;
+  const float2* cr =
+      reinterpret_cast<const float2*>(coef + (size_t)cidx * P + (size_t)(active ? row : 0) * M);
 #pragma unroll
-  for (int m = 0; m < 32; ++m) o[t + T * m] = acc[t + T * m];
+  for (int m = 0; m < 32; ++m) {
+    const float2 a = active ? cr[t + T * m] : make_float2(0.f, 0.f);
+    sbuf[t + T * m] = make_float2(mult * a.x * v[m].x, mult * a.y * v[m].y);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < RB * L; idx += blockDim.x) {
+    const int r = idx / L, n = idx - r * L;
+    if (row0 + r >= N) continue;
+    float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const float2 y = sm[3 * RB * NB + (q * RB + r) * SB + n];
+      sum.x += y.x;
+      sum.y += y.y;
+    }
+    reinterpret_cast<float2*>(out + (size_t)(row0 + r) * M)[n] = sum;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -420,12 +430,12 @@ template <int NL>
 cudaError_t col_L(const float2* specT, float2* o0, float2* o1, float2* o2, int M,
                   const SpecTables& tb, const DevScalars* sc, const int* skip,
                   cudaStream_t st) {
-  constexpr int T = NL / 32, CB = mv_cols<NL>();
+  constexpr int CB = mv_cols<NL>();
   const int Lc = M / 2;
-  const size_t sm = ((size_t)CB * (xbuf_len<NL>() + NL) + NL) * sizeof(float2);
-  cudaError_t e = prepare_launch(k_mvT_col<NL>, CB * T, sm);
+  const size_t sm = ((size_t)CB * (3 * xbuf_len<NL>() + NL) + NL) * sizeof(float2);
+  cudaError_t e = prepare_launch(k_mvT_col<NL>, 96, sm);
   if (e != cudaSuccess) return e;
-  k_mvT_col<NL><<<(Lc + CB - 1) / CB, CB * T, sm, st>>>(
+  k_mvT_col<NL><<<(Lc + CB - 1) / CB, 96, sm, st>>>(
       specT, o0, o1, o2, M, (float)(1.0 / ((double)NL * (double)M)), (const float2*)tb.t2cA,
       (const float2*)tb.t2cB, sc, skip, (const float2*)tb.symx, (const float2*)tb.symy);
   return cudaGetLastError();
@@ -435,11 +445,11 @@ template <int L>
 cudaError_t combine_L(const float2* q0T, const float2* q1T, const float2* q2T,
                       const float* coef, float* out, int N, const SpecTables& tb,
                       const int* skip, cudaStream_t st) {
-  constexpr int T = L / 32, RB = mv_rows<L>();
-  const size_t sm = (size_t)RB * (xbuf_len<L>() + 3 * (L + 1) + L) * sizeof(float2);
-  cudaError_t e = prepare_launch(k_mvT_combine<L>, RB * T, sm);
+  constexpr int RB = mv_rows5<L>();
+  const size_t sm = (size_t)RB * (3 * (L + 1) + 5 * xbuf_len<L>()) * sizeof(float2);
+  cudaError_t e = prepare_launch(k_mvT_combine<L>, 160, sm);
   if (e != cudaSuccess) return e;
-  k_mvT_combine<L><<<(N + RB - 1) / RB, RB * T, sm, st>>>(
+  k_mvT_combine<L><<<(N + RB - 1) / RB, 160, sm, st>>>(
       q0T, q1T, q2T, coef, out, N, (const float2*)tb.t2rB, (const float2*)tb.twM, skip,
       (const float2*)tb.symx);
   return cudaGetLastError();
