@@ -54,7 +54,8 @@ extern "C" {
                                    convexity (a larger effective tau, Sec. 3.2 remarks);
                                    0: plain Eq. (linma), such an iterate ends the solve */
 #define OT_OPT_TRANSLATE 7      /* 1 (default): apply Eq. (translation) d - mean(d) + 1 to
-                                   f and g on entry; 0: use them as given */
+                                   f and g on entry; 0: use them as given (they must then be
+                                   positive and finite as they are, else OT_EINVAL) */
 #define OT_OPT_WARM_START 8     /* 1: phi_inout holds the initial iterate u0 on entry;
                                    0 (default): u0 = 0, the constant start of Thm 3.2;
                                    2: u0 = the learned warm start (ot_ws_set_weights or
@@ -110,6 +111,15 @@ extern "C" {
                                    simplified g(x + grad u) Tr(Adj(I + D^2 u) D^2 theta) that
                                    Sec. 3.3 reports working in practice (b = 0; the same root,
                                    a different Newton path) */
+#define OT_OPT_PHASE_TIMES 22  /* 1: the solve records the device time of each phase
+                                   (ms_residual, ms_fft, ms_krylov, ms_update, ms_other of
+                                   ot_stats) with a one-thread stamp kernel (%globaltimer) at
+                                   every phase change, in the graph and the host-driven solve
+                                   alike (a few microseconds per phase change; the stamps are
+                                   not in kernel_launches); 0 (default): those fields are -1 */
+#define OT_OPT_TRANSPORT 23     /* 1: the solve ends with the transport distance d(f, g) of
+                                   Sec. 5.2 (as ot_transport_outputs, on the translated f) in
+                                   ot_stats.transport_dist; 0 (default): it is -1 */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,
@@ -153,6 +163,16 @@ typedef struct {
                               (1, 1/2, 1/4, 1/8 or 0 = zero start); -1 without it; -2 if
                               the network kernel's bounded wait gave up (the solve went on
                               from the zero start and ot_last_error names it) */
+  double mass_defect_f;    /* mean(f) - 1 of the input f, before Eq. (translation) */
+  double mass_defect_g;    /* mean(g) - 1 of the input g */
+  double transport_dist;   /* d(f, g) = mean |grad phi|^2 f (Sec. 5.2) with OT_OPT_TRANSPORT,
+                              else -1 */
+  double ms_residual;      /* with OT_OPT_PHASE_TIMES (else -1): device ms in the residual
+                              and coefficient evaluations (Eq. ma2, linearmaeq), */
+  double ms_fft;           /* the preconditioned matvecs' transform passes (Sec. 4.2), */
+  double ms_krylov;        /* the GMRES vector kernels (Arnoldi, Givens, restarts), */
+  double ms_update;        /* theta = Lbar^{-1} sigma and the candidate u + s theta, */
+  double ms_other;         /* and the rest (inputs, prefilter, warm start, control, gauge) */
 } ot_stats;
 
 /* Create a plan for N x M grids (N rows, M columns), damping tau >= 1 (Eq. linma) and

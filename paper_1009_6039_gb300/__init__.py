@@ -23,6 +23,7 @@ OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
 OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
+OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT = 22, 23
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -46,7 +47,11 @@ class ot_stats(ctypes.Structure):
                 ("res_inf", ctypes.c_double), ("res_l2", ctypes.c_double),
                 ("min_det", ctypes.c_double), ("mean_fn", ctypes.c_double),
                 ("phi_mean", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ws_alpha", ctypes.c_double)]
+                ("ws_alpha", ctypes.c_double), ("mass_defect_f", ctypes.c_double),
+                ("mass_defect_g", ctypes.c_double), ("transport_dist", ctypes.c_double),
+                ("ms_residual", ctypes.c_double), ("ms_fft", ctypes.c_double),
+                ("ms_krylov", ctypes.c_double), ("ms_update", ctypes.c_double),
+                ("ms_other", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -362,7 +367,8 @@ class Plan:
              "theta_fp64": OT_OPT_THETA_FP64, "autotune": OT_OPT_AUTOTUNE,
              "fft_variant": OT_OPT_FFT_VARIANT, "symbols": OT_OPT_SYMBOLS,
              "forcing": OT_OPT_FORCING, "tau_retry": OT_OPT_TAU_RETRY,
-             "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR}
+             "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR,
+             "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

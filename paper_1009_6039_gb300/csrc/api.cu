@@ -91,6 +91,9 @@ struct ot_plan {
   float *ws_X = nullptr, *ws_s = nullptr;  // features (P x 16), network output (P)
   float* ws_c32 = nullptr;                 // FP32 B-spline coefficients for the features
   int ws_have = 0, gkey_ws = -1, sms = 0;
+  // OT_OPT_PHASE_TIMES: stamp kernels at phase changes while a solve is issued or captured
+  int phase_times = 0, stamping = 0, last_phase = -1, phase_force = -1;
+  int transport = 0;  // OT_OPT_TRANSPORT: d(f, g) of Sec. 5.2 at the end of each solve
 };
 
 template <typename T> static const SpecTables& tables(ot_plan* p);
@@ -155,6 +158,7 @@ static void prof_harvest(ot_plan* p, int jend) {
 
 #define LAUNCH(p, cls, tag, nk, expr)                                  \
   do {                                                                 \
+    if ((p)->stamping) RET(stamp_phase(p, cls));                       \
     cudaEvent_t a_ = nullptr;                                          \
     if ((p)->profile) {                                                \
       a_ = ev_get(p);                                                  \
@@ -168,6 +172,24 @@ static void prof_harvest(ot_plan* p, int jend) {
       (p)->marks.push_back({(cls), (tag), a_, b_});                     \
     }                                                                  \
   } while (0)
+
+// Phase of a kernel class for OT_OPT_PHASE_TIMES (a forced phase overrides it: the theta
+// passes are tagged with the transform classes but belong to the update)
+static int phase_of(int cls) {
+  switch (cls) {
+    case OT_PROF_RESIDUAL: return PH_RESIDUAL;
+    case OT_PROF_ROW_R2C:
+    case OT_PROF_COL_MATVEC:
+    case OT_PROF_ROW_C2R_COMBINE: return PH_FFT;
+    case OT_PROF_COL_LBARINV:
+    case OT_PROF_ROW_C2R_UPDATE: return PH_UPDATE;
+    case OT_PROF_GMRES_DOTS:
+    case OT_PROF_GMRES_UPDATE:
+    case OT_PROF_GMRES_OTHER: return PH_KRYLOV;
+  }
+  return PH_OTHER;
+}
+static int stamp_phase(ot_plan* p, int cls);
 
 static const char* kErr[] = {"ok", "invalid argument", "Newton did not converge",
                              "iterate lost convexity or became non-finite", "CUDA error",
@@ -211,6 +233,17 @@ static void note_ws_timeout(ot_stats* st, int line) {
       return OT_ECUDA;                        \
     }                                         \
   } while (0)
+
+// a stamp kernel before the first launch of a new phase (the host tracks the phase of the
+// launch sequence it issues or captures; -1 = unknown, e.g. at a conditional body's start)
+static int stamp_phase(ot_plan* p, int cls) {
+  const int ph = p->phase_force >= 0 ? p->phase_force : phase_of(cls);
+  if (ph == p->last_phase) return OT_OK;
+  CK(launch_stamp(p->sc, ph, p->stream));
+  p->last_phase = ph;
+  return OT_OK;
+}
+
 
 namespace otgb {
 bool fft_length_supported(int L) {
@@ -550,6 +583,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
     case OT_OPT_TRANSLATE:
       if (v != 0 && v != 1) return OT_EINVAL;
       p->translate = (int)v;
+      free_graph(p);
       return OT_OK;
     case OT_OPT_WARM_START:
       if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
@@ -628,6 +662,20 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
         if (p->ready) RET(fill_symbols(p));
       }
       return OT_OK;
+    case OT_OPT_PHASE_TIMES:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->phase_times != (int)v) {
+        p->phase_times = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
+    case OT_OPT_TRANSPORT:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->transport != (int)v) {
+        p->transport = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_AUTOTUNE:
       if (v != 0 && v != 1) return OT_EINVAL;
       p->autotune = (int)v;
@@ -665,6 +713,8 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_TAU_RETRY: *v = p->tau_retry; return OT_OK;
     case OT_OPT_WS_TEST_STALL: *v = p->ws_stall; return OT_OK;
     case OT_OPT_OPERATOR: *v = p->op_simple; return OT_OK;
+    case OT_OPT_PHASE_TIMES: *v = p->phase_times; return OT_OK;
+    case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
       // autotuner has run (or in FP64 mode, which has one variant)
@@ -878,8 +928,19 @@ static int run_lbar_inv(ot_plan* p, const T* sigma, const double* u_in, double* 
 // it only slowly.  The forward transform of sigma and rho-bar stay FP32 (their round-off is
 // damped by rho-bar ~ 1/k^2).
 template <typename T>
+static int run_theta_impl(ot_plan* p, const double* u_in, double* u_out, double step,
+                          bool sc_driven);
+template <typename T>
 static int run_theta(ot_plan* p, const double* u_in, double* u_out, double step,
                      bool sc_driven) {
+  p->phase_force = PH_UPDATE;
+  const int rc = run_theta_impl<T>(p, u_in, u_out, step, sc_driven);
+  p->phase_force = -1;
+  return rc;
+}
+template <typename T>
+static int run_theta_impl(ot_plan* p, const double* u_in, double* u_out, double step,
+                          bool sc_driven) {
   const DevScalars* scp = sc_driven ? p->sc : nullptr;
   if (sizeof(T) == 4 && p->theta64 == 2) {
     LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
@@ -991,6 +1052,18 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->eta_max = p->eta;
   p->hsc->res_prev = 0.0;
   p->hsc->forcing = p->forcing;
+  p->hsc->stamp_cls = -1;
+  p->hsc->in_plain = p->translate ? 0 : 1;
+}
+
+// the stats fields every solve path fills from the final device scalars
+static void fill_common_stats(ot_plan* p, const DevScalars* h, ot_stats* st) {
+  st->mass_defect_f = h->in_mean[0] - 1.0;
+  st->mass_defect_g = h->in_mean[1] - 1.0;
+  st->transport_dist = p->transport ? h->dist : -1.0;
+  double* ms[PH_COUNT] = {&st->ms_residual, &st->ms_fft, &st->ms_krylov, &st->ms_update,
+                          &st->ms_other};
+  for (int k = 0; k < PH_COUNT; ++k) *ms[k] = p->phase_times ? 1e-6 * (double)h->phase_ns[k] : -1.0;
 }
 
 static int run_autotune(ot_plan* p);
@@ -1126,6 +1199,16 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   } else {
     if (f_in != p->f) CK(cudaMemcpyAsync(p->f, f_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
     if (g_in != p->g) CK(cudaMemcpyAsync(p->g, g_in, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    // inputs used as given: their statistics and the positivity check only
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_input_stats(p->f, p->g, N, M, p->partials, p->sc, p->stream));
+    RET(read_scalars(p));
+    if (p->hsc->in_bad) {
+      st->status = OT_EINVAL;
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      return OT_EINVAL;
+    }
   }
   RET(run_prefilter(p, p->g, p->c));
   if (p->warm_start == 1) {
@@ -1187,6 +1270,11 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   }
   LAUNCH(p, OT_PROF_OTHER, -1, 2,
          launch_subtract_mean(p->u, N, M, p->partials, p->sc, p->dmean, p->stream));
+  if (p->transport)
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_transport(p->f, p->u, N, M, nullptr, p->partials,
+                            &p->sc->ticket[TK_TRANSPORT], &p->sc->dist, p->stream));
+  if (p->stamping) CK(launch_stamp(p->sc, -1, p->stream));
   if (phi != p->u) CK(cudaMemcpyAsync(phi, p->u, P * 8, cudaMemcpyDeviceToDevice, p->stream));
   CK(cudaMemcpyAsync(&st->phi_mean, p->dmean, 8, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaEventRecord(ev1, p->stream));
@@ -1194,6 +1282,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   st->res_l2 = sqrt(p->hsc->res_l2sum / (double)P);
   st->ws_alpha = p->hsc->ws_alpha;
   if (p->hsc->ws_err) note_ws_timeout(st, __LINE__);
+  fill_common_stats(p, p->hsc, st);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   st->ms_total = ms;
@@ -1240,6 +1329,7 @@ static int begin_body(ot_plan* p, int level, cudaGraph_t body) {
   CK(cudaStreamBeginCaptureToGraph(p->cs[level], body, nullptr, nullptr, 0,
                                    cudaStreamCaptureModeRelaxed));
   p->stream = p->cs[level];
+  p->last_phase = -1;
   return OT_OK;
 }
 
@@ -1247,6 +1337,7 @@ static int end_body(ot_plan* p, int level) {
   cudaGraph_t out = nullptr;
   CK(cudaStreamEndCapture(p->cs[level], &out));
   p->stream = p->cs[level - 1];
+  p->last_phase = -1;
   return OT_OK;
 }
 
@@ -1276,6 +1367,9 @@ static int capture_solve(ot_plan* p) {
     LAUNCH(p, OT_PROF_OTHER, -1, 2,
            launch_translate_inputs(p->f, p->g, p->f, p->g, N, M, p->partials, p->sc,
                                    p->stream));
+  else
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_input_stats(p->f, p->g, N, M, p->partials, p->sc, p->stream));
   RET(run_prefilter(p, p->g, p->c));
   if (p->warm_start == 2) RET(run_warmstart(p, p->u));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
@@ -1337,6 +1431,13 @@ static int capture_solve(ot_plan* p) {
   LAUNCH(p, OT_PROF_OTHER, -1, 2,
          launch_final_gauge(up, p->uout, N, M, p->partials, p->sc, p->dmean, p->stream));
   p->top_kernels = 3;  // residual_l2 + gauge (2), counted on the host
+  if (p->transport) {
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_transport(p->f, p->uout, N, M, nullptr, p->partials,
+                            &p->sc->ticket[TK_TRANSPORT], &p->sc->dist, p->stream));
+    p->top_kernels += 1;
+  }
+  if (p->stamping) CK(launch_stamp(p->sc, -1, p->stream));
   return OT_OK;
 }
 
@@ -1501,7 +1602,10 @@ static int build_graph(ot_plan* p) {
   p->profile = 0;
   p->stream = p->cs[0];
   CK(cudaStreamBeginCapture(p->cs[0], cudaStreamCaptureModeRelaxed));
+  p->stamping = p->phase_times;
+  p->last_phase = -1;
   int rc = capture_solve<T>(p);
+  p->stamping = 0;
   if (rc != OT_OK) {
     p->stream = saved;
     p->profile = saved_prof;
@@ -1588,6 +1692,7 @@ static void graph_collect(ot_plan* p, const DevScalars* h, double mean, ot_stats
   st->kernel_launches = (int32_t)(h->kcount + p->top_kernels);
   st->ws_alpha = h->ws_alpha;
   if (h->ws_err) note_ws_timeout(st, __LINE__);
+  fill_common_stats(p, h, st);
   p->launches += h->kcount + p->top_kernels;
 }
 
@@ -1625,12 +1730,23 @@ static int solve_graph_impl(ot_plan* p, const double* f_in, const double* g_in, 
   return st->status;
 }
 
+// host-driven solve, with phase stamps while OT_OPT_PHASE_TIMES is set
+static int host_solve(ot_plan* p, const double* f, const double* g, double* phi,
+                      ot_stats* st) {
+  p->stamping = p->phase_times;
+  p->last_phase = -1;
+  const int rc =
+      p->precision ? solve_impl<float>(p, f, g, phi, st) : solve_impl<double>(p, f, g, phi, st);
+  p->stamping = 0;
+  return rc;
+}
+
 static int solve_once(ot_plan* p, const double* f, const double* g, double* phi,
                       ot_stats* st) {
   if (p->use_graph && !p->profile)
     return p->precision ? solve_graph_impl<float>(p, f, g, phi, st)
                         : solve_graph_impl<double>(p, f, g, phi, st);
-  return p->precision ? solve_impl<float>(p, f, g, phi, st) : solve_impl<double>(p, f, g, phi, st);
+  return host_solve(p, f, g, phi, st);
 }
 
 // The remedy of Sec. 3.2 / Sec. 5.3 for an iterate that loses convexity: solve again with
@@ -1674,8 +1790,7 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
     if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
     CK(cudaMemcpyAsync(phi, p->uout, bytes, cudaMemcpyDeviceToHost, p->stream));
   } else {
-    rc = p->precision ? solve_impl<float>(p, p->f, p->g, p->u, st)
-                      : solve_impl<double>(p, p->f, p->g, p->u, st);
+    rc = host_solve(p, p->f, p->g, p->u, st);
     if (rc == OT_ECUDA || rc == OT_ENOMEM || rc == OT_EINVAL) return rc;
     CK(cudaMemcpyAsync(phi, p->u, bytes, cudaMemcpyDeviceToHost, p->stream));
   }

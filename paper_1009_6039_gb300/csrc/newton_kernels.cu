@@ -258,8 +258,11 @@ __global__ void k_input_stats(const double* __restrict__ f, const double* __rest
     sc->in_min[1] = v[3];
     sc->in_nonfinite[0] = (int)v[4];
     sc->in_nonfinite[1] = (int)v[5];
-    bool bad = v[4] > 0 || v[5] > 0 || !(v[2] - sc->in_mean[0] + 1.0 > 0.0) ||
-               !(v[3] - sc->in_mean[1] + 1.0 > 0.0);
+    // translated inputs must be positive after the translation, inputs used as given
+    // (in_plain) as they are
+    const double sf = sc->in_plain ? 0.0 : 1.0 - sc->in_mean[0];
+    const double sg = sc->in_plain ? 0.0 : 1.0 - sc->in_mean[1];
+    bool bad = v[4] > 0 || v[5] > 0 || !(v[2] + sf > 0.0) || !(v[3] + sg > 0.0);
     sc->in_bad = bad ? 1 : 0;
     sc->ticket[TK_INPUT] = 0;
   }
@@ -393,6 +396,27 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
   k_prefilter_tile<false><<<gy, 256, PT_SMEM, st>>>(g, scratch, nullptr, N, M, z, A);
   const dim3 gx((N + PT_LN - 1) / PT_LN, (M + PT_TP - 1) / PT_TP);
   k_prefilter_tile<true><<<gx, 256, PT_SMEM, st>>>(scratch, c, cdd, N, M, z, A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_input_stats(const double* f, const double* g, int N, int M,
+                               double* partials, DevScalars* sc, cudaStream_t st) {
+  k_input_stats<<<reduce_blocks(), 256, 0, st>>>(f, g, (long)N * M, partials, sc);
+  return cudaGetLastError();
+}
+
+// %globaltimer: the GPU's nanosecond clock (PTX special register)
+__global__ void k_stamp(DevScalars* sc, int cls) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  const int prev = sc->stamp_cls;
+  if (prev >= 0 && prev < PH_COUNT && t > sc->stamp_t) sc->phase_ns[prev] += t - sc->stamp_t;
+  sc->stamp_t = t;
+  sc->stamp_cls = cls;
+}
+
+cudaError_t launch_stamp(DevScalars* sc, int cls, cudaStream_t st) {
+  k_stamp<<<1, 1, 0, st>>>(sc, cls);
   return cudaGetLastError();
 }
 

@@ -60,9 +60,20 @@ struct DevScalars {
   // transport distance d(f, g) of ot_transport_outputs
   double dist;
   int ws_err;
+  // device time per phase of a solve (OT_OPT_PHASE_TIMES): a one-thread stamp kernel at each
+  // phase change adds the %globaltimer interval since the previous stamp to the phase that
+  // stamp opened (PH_* below); stamp_cls = -1 before the first stamp
+  unsigned long long stamp_t;
+  unsigned long long phase_ns[5];
+  int stamp_cls;
+  // 1 while the input statistics run without the translation (OT_OPT_TRANSLATE = 0): the
+  // inputs must then be positive as given
+  int in_plain;
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
 };
+// phases of OT_OPT_PHASE_TIMES
+enum { PH_RESIDUAL = 0, PH_FFT = 1, PH_KRYLOV = 2, PH_UPDATE = 3, PH_OTHER = 4, PH_COUNT = 5 };
 
 // Control operations of the device-resident Newton loop (k_ctl)
 enum CtlOp {
@@ -192,6 +203,12 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
                                     cudaStream_t st);
+// the statistics of f and g alone (means, minima, non-finite counts) for inputs used as given
+// (sc->in_plain must be 1: then in_bad flags a non-positive or non-finite value)
+cudaError_t launch_input_stats(const double* f, const double* g, int N, int M,
+                               double* partials, DevScalars* sc, cudaStream_t st);
+// phase stamp (OT_OPT_PHASE_TIMES): cls opens a phase, -1 closes the last one
+cudaError_t launch_stamp(DevScalars* sc, int cls, cudaStream_t st);
 // u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate);
 // simplified: b = 0 in the coefficients (the operator without the grad g term)
 // c32 (optional, FP32 copy of c): used for the gradient of the interpolant in FP32 mode

@@ -76,3 +76,40 @@ def test_binding_constants_match_the_header(lib):
     # the Plan option names cover every option key
     keys = {v for k, v in defs.items() if k.startswith("OT_OPT_")}
     assert keys == set(lib.Plan._keys.values())
+
+
+def _struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "otgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct\s*\{(.*?)\}\s*%s;" % name, src, flags=re.S).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, names = decl.split(None, 1)
+        fields += [(typ, n.strip()) for n in names.split(",")]
+    return fields
+
+
+def test_stats_struct_layout_matches_the_header(lib, tmp_path):
+    # the binding's ot_stats has the header's fields in the header's order, with the offsets
+    # and size a C compiler gives them
+    import ctypes
+    fields = _struct_fields("ot_stats")
+    ctypes_of = {"int32_t": ctypes.c_int32, "double": ctypes.c_double}
+    assert [n for _, n in fields] == [n for n, _ in lib.ot_stats._fields_]
+    for (typ, n), (m, ct) in zip(fields, lib.ot_stats._fields_):
+        assert ctypes_of[typ] is ct, n
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "otgb.h"\nint main(void) {\n'
+                    + "".join('  printf("%%zu\\n", offsetof(ot_stats, %s));\n' % n
+                              for _, n in fields)
+                    + '  printf("%zu\\n", sizeof(ot_stats));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[:-1] == [getattr(lib.ot_stats, n).offset for _, n in fields]
+    assert out[-1] == ctypes.sizeof(lib.ot_stats)

@@ -575,3 +575,49 @@ def test_tau_retry_after_divergence(ot):
     u_ref, st_ref, _, _ = O.solve(f, g, tau=4.0, tol=1e-10, eta=1e-2, max_newton=400)
     assert st_ref["status"] == 0
     assert np.abs(phi - u_ref).max() <= 1e-8
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_solve_fills_every_stats_field(ot, graph):
+    # mass defects of the inputs (Eq. translation), the transport distance of Sec. 5.2 at the
+    # returned potential, and the device time per phase (stamps at the phase changes, in the
+    # graph-launched and the host-driven solve alike)
+    N = M = 64
+    f, g = I.noise_blob_pair(N, M, s=3700)
+    f2, g2 = 1.3 * f, 0.8 * g
+    p = plan(ot, N, M, "mixed", tau=1.0, tol=1e-8, eta=1e-2, symbols=1, graph=graph,
+             phase_times=1, transport=1)
+    phi = dev(np.zeros((N, M)))
+    rc, st = p.solve(dev(f2), dev(g2), phi)
+    assert rc == 0
+    assert abs(st["mass_defect_f"] - (f2.mean() - 1.0)) <= 1e-13
+    assert abs(st["mass_defect_g"] - (g2.mean() - 1.0)) <= 1e-13
+    ph = phi.cpu().numpy()
+    d_ref, _ = O.transport_outputs(f2 - f2.mean() + 1.0, ph)
+    assert abs(st["transport_dist"] - d_ref) <= 1e-10 * d_ref
+    ms = [st[k] for k in ("ms_residual", "ms_fft", "ms_krylov", "ms_update", "ms_other")]
+    assert all(m > 0.0 for m in ms), ms
+    assert sum(ms) <= 1.05 * st["ms_total"] + 0.02, (ms, st["ms_total"])
+    # the same solve without the options: same result, the fields read -1
+    p.set(phase_times=0, transport=0)
+    phi2 = dev(np.zeros((N, M)))
+    rc2, st2 = p.solve(dev(f2), dev(g2), phi2)
+    p.close()
+    assert rc2 == 0 and np.array_equal(phi2.cpu().numpy(), ph)
+    assert st2["transport_dist"] == -1.0 and st2["ms_fft"] == -1.0 and st2["ms_other"] == -1.0
+    assert st2["mass_defect_f"] == st["mass_defect_f"]
+
+
+def test_untranslated_inputs_are_checked(ot):
+    # OT_OPT_TRANSLATE = 0: inputs are used as given, so they must be positive as they are;
+    # the statistics still report the mass defects
+    N = M = 32
+    f = I.blob_density(N, N, 5)
+    for graph in (1, 0):
+        rc, st, phi = _gpu_solve(ot, f, f.copy(), "fp64", translate=0, graph=graph)
+        assert rc == 0 and st["newton_iters"] == 0
+        assert abs(st["mass_defect_f"]) <= 1e-14
+        bad = f.copy()
+        bad[3, 3] = -0.5
+        with pytest.raises(ot.OTError):
+            _gpu_solve(ot, bad, f, "fp64", translate=0, graph=graph)
