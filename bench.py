@@ -54,7 +54,7 @@ def parse():
                     help="warm-up and timed solves only (profiling target)")
     ap.add_argument("--workload", default="single", choices=["single", "batch"],
                     help="single: one 1024^2 pair per step (default); batch: 512 pairs of "
-                         "sizes 128^2..512^2 per step through ot_solve_batched")
+                         "sizes 128^2..512^2 per step, one plan set (ot_solve_batched)")
     ap.add_argument("--ws-train-pairs", type=int, default=16,
                     help="pairs solved to train the warm-start network before timing")
     ap.add_argument("--ws-fit-steps", type=int, default=1500)
@@ -66,7 +66,6 @@ def parse():
                          "autotuning; for profiler runs, where the autotuner's event timing is "
                          "distorted")
     ap.add_argument("--batch-pairs", type=int, default=512)
-    ap.add_argument("--plans-per-size", type=int, default=4)
     return ap.parse_args()
 
 
@@ -802,23 +801,18 @@ def run_ours(args):
     return 0
 
 
-BATCH_SIZES = (128, 192, 256, 384, 512)
 BATCH_TAU = 1.0
 BATCH_ETA = 1e-1
 BATCH_MAX_NEWTON = 1000
 
 
 def run_batch(args):
-    """Batched workload: `batch_pairs` seeded blob-mixture pairs (seed base 4000) with sizes
-    drawn uniformly from {128, 192, 256, 384, 512}^2, tau = 1, eta = 0.1, the stencil-symbol
-    operator, tol 1e-8, mixed
-    precision; each step is one ot_solve_batched call over all pairs, spread over a pool of
-    `plans_per_size` plans per size (problems on one plan run back to back on its stream,
-    different plans concurrently).  With the paper's spectral symbols these pairs (peaks up to
-    ~20x the floor) stall at tau = 2 in both the oracle and the GPU path and need tau = 4
-    (~100 Newton steps); with the stencil-symbol operator (exact Jacobian) tau = 1 with the
-    step-halving safeguard converges in 11-23 steps."""
-    import numpy as np
+    """Batched workload: `batch_pairs` seeded blob-mixture pairs (ot_inputs.batch_workload,
+    seed base 4000) with sizes drawn uniformly from {128, 192, 256, 384, 512}^2, tau = 1,
+    eta = 0.1, the stencil-symbol operator, tol 1e-8, mixed precision, a pair that loses
+    convexity solved again with 2 tau (up to twice); each step is one ot_solve_batched call on
+    a plan set holding all pairs (one graph launch: every size class runs each kernel for all
+    its pairs, with per-pair loop control on the device)."""
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -826,62 +820,63 @@ def run_batch(args):
     __graft_entry__.build()
     import ot_inputs as I
     import paper_1009_6039_gb300 as ot
-    rng = I.SplitMix64(4000 + 7919 * rank)
-    draws = rng.uniform(args.batch_pairs)
-    sizes = [BATCH_SIZES[min(4, int(d * 5))] for d in draws]
-    pool = {n: [ot.Plan(n, n, tau=BATCH_TAU, tol=TOL, eta=BATCH_ETA, precision="mixed",
-                        max_newton=BATCH_MAX_NEWTON, symbols=SYMBOLS, tau_retry=2)
-                for _ in range(args.plans_per_size)] for n in BATCH_SIZES}
-    plans, fs, gs, phis = [], [], [], []
-    used = {n: 0 for n in BATCH_SIZES}
-    for k, n in enumerate(sizes):
-        f, g = I.blob_pair(n, n, s=4000 + k)
+    work = I.batch_workload(args.batch_pairs, base=4000 + 7919 * rank)
+    sizes = [n for n, _ in work]
+    fs, gs, phis = [], [], []
+    for n, s in work:
+        f, g = I.blob_pair(n, n, s=s)
         fs.append(torch.from_numpy(f).cuda())
         gs.append(torch.from_numpy(g).cuda())
         phis.append(torch.zeros((n, n), dtype=torch.float64, device="cuda"))
-        plans.append(pool[n][used[n] % args.plans_per_size])
-        used[n] += 1
-    count = len(sizes)
-    stats = (ot.ot_stats * count)()
-    handles = [p.h for p in plans]
-    fp = [t.data_ptr() for t in fs]
-    gp = [t.data_ptr() for t in gs]
-    pp = [t.data_ptr() for t in phis]
+    stream = torch.cuda.current_stream()
+    ps = ot.PlanSet([(n, n) for n in sizes], tau=BATCH_TAU, tol=TOL, stream=stream,
+                    eta=BATCH_ETA, max_newton=BATCH_MAX_NEWTON, symbols=SYMBOLS, tau_retry=2)
     for _ in range(args.warmup):
-        rc = ot.ot_solve_batched(count, handles, fp, gp, pp, stats)
-        if rc in (ot.OT_EINVAL, ot.OT_ECUDA, ot.OT_ENOMEM):
-            raise ot.OTError(rc, "ot_solve_batched")
+        ps.solve(fs, gs, phis)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        rc = ot.ot_solve_batched(count, handles, fp, gp, pp, stats)
-        if rc in (ot.OT_EINVAL, ot.OT_ECUDA, ot.OT_ENOMEM):
-            raise ot.OTError(rc, "ot_solve_batched")
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
-    conv = sum(1 for k in range(count) if stats[k].status == 0)
-    diverged = sum(1 for k in range(count) if stats[k].status == ot.OT_EDIVERGED)
-    newton = sum(stats[k].newton_iters for k in range(count))
-    pts = sum(n * n * stats[k].newton_iters for k, n in enumerate(sizes))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            rc, stats = ps.solve(fs, gs, phis)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, world)
+    secs = ms / 1000.0
+    count = len(sizes)
+    conv = sum(1 for s_ in stats if s_["status"] == 0)
+    diverged = sum(1 for s_ in stats if s_["status"] == ot.OT_EDIVERGED)
+    newton = sum(s_["newton_iters"] for s_ in stats)
+    pts = sum(n * n * s_["newton_iters"] for n, s_ in zip(sizes, stats))
     value = world * count * args.steps / secs
-    if rank == 0:
-        print(json.dumps({
-            "metric": "OT solves/s, batch of uneven sizes", "value": value,
-            "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": secs * 1000.0 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "%d blob-mixture pairs, sizes uniform over %s^2, tau=1, "
-                                   "eta=0.1, stencil-symbol operator, tol 1e-8, mixed, "
-                                   "a diverged pair is re-solved with 2 tau (up to twice), "
-                                   "%d plans per size"
-                                   % (count, list(BATCH_SIZES), args.plans_per_size),
-                       "sizes_histogram": {str(n): sizes.count(n) for n in BATCH_SIZES}},
-            "converged": conv, "diverged": diverged, "total_newton_iters": newton,
-            "grid_point_newton_iters_per_s": world * pts * args.steps / secs,
-            "timing": "host wall clock around the batched calls (synchronised)"}), flush=True)
-    for lst in pool.values():
-        for p in lst:
-            p.close()
+    out = {
+        "metric": "OT solves/s, batch of uneven sizes", "value": value,
+        "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "%d blob-mixture pairs, sizes uniform over %s^2, tau=1, "
+                               "eta=0.1, stencil-symbol operator, tol 1e-8, mixed, a diverged "
+                               "pair re-solved with 2 tau (up to twice), one plan set"
+                               % (count, list(I.BATCH_SIZES)),
+                   "sizes_histogram": {str(n): sizes.count(n) for n in I.BATCH_SIZES},
+                   "l2_flush": "256 MB write between timed steps"},
+        "converged": conv, "diverged": diverged, "total_newton_iters": newton,
+        "max_res_inf": max(s_["res_inf"] for s_ in stats),
+        "grid_point_newton_iters_per_s": world * pts * args.steps / secs,
+        "timing": "CUDA events around each ot_solve_batched call on the set's stream",
+        "clocks": clk.summary()}
+    ps.close()
+    return out
+
+
+def main_batch(args):
+    out = run_batch(args)
+    if dist_env()[0] == 0:
+        print(json.dumps(out), flush=True)
     return 0
 
 
@@ -890,7 +885,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
-        return run_batch(args)
+        return main_batch(args)
     return run_ours(args)
 
 

@@ -203,11 +203,51 @@ int ot_solve(ot_plan* plan, const double* f, const double* g, double* phi_inout,
 int ot_solve_host(ot_plan* plan, const double* f, const double* g, double* phi_inout,
                   ot_stats* stats);
 
-/* Solve `count` independent problems, plans[k] sized for problem k (sizes may differ);
- * f[k], g[k], phi[k] are device pointers for plans[k]; stats (array of count) may be NULL.
- * Returns OT_OK if every problem converged, else the first non-OK status. */
-int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* f,
-                     const double* const* g, double* const* phi, ot_stats* stats);
+/* Solve `count` independent problems on existing plans, plans[k] sized for problem k (sizes
+ * may differ; problems sharing a plan run one after the other on its stream, different plans
+ * concurrently); f[k], g[k], phi[k] are device pointers for plans[k]; stats (array of count)
+ * may be NULL.  Keeps a process-wide pinned result buffer, grown when a call has more
+ * problems than any before.  Returns OT_OK if every problem converged, else the first
+ * non-OK status. */
+int ot_solve_plans(int32_t count, ot_plan* const* plans, const double* const* f,
+                   const double* const* g, double* const* phi, ot_stats* stats);
+
+/* ---- Plan sets: many problems of uneven sizes in one graph launch ------------------------
+ * Not in the paper, which solves one image pair at a time: the damped Newton iteration of
+ * Sec. 3.1 with the solver of Sec. 4.2 run for many independent pairs at once.  The pairs are
+ * grouped by size; each size class runs every kernel of the mixed-precision solve for all its
+ * pairs together (one launch serves the class, each pair's buffers in its own slab), with
+ * per-pair state on the device: a pair leaves the Newton loop, a GMRES cycle or the step-
+ * halving loop on its own test while the others go on, and each loop of the captured graph
+ * runs while any pair of the class needs it.  The classes are parallel branches of one CUDA
+ * graph, so a call is one graph launch (plus one more per OT_OPT_TAU_RETRY round).
+ *
+ * ot_plan_set_create: count problems, problem k of N[k] x M[k] (each size as for
+ * ot_plan_create; at most 1024 problems of one size, else OT_EUNSUPPORTED), damping tau >= 1,
+ * tolerance tol > 0.  Device memory is allocated at the first ot_solve_batched (and after an
+ * OT_OPT_RESTART change): about 170 bytes per grid point of every problem plus the shared
+ * tables.  The solve is always the mixed-precision one (OT_OPT_PRECISION = 1, THETA_FP64 = 2)
+ * from u0 = 0. */
+typedef struct ot_plan_set ot_plan_set;
+int ot_plan_set_create(ot_plan_set** out, int32_t count, const int32_t* N, const int32_t* M,
+                       double tau, double tol);
+/* Options for every problem of the set: OT_OPT_TAU, TOL, ETA, RESTART, MAX_NEWTON,
+ * MAX_RESTARTS, SAFEGUARD, TRANSLATE, SYMBOLS, FORCING, OPERATOR, REORTH as for a plan;
+ * OT_OPT_TAU_RETRY: rounds in which the problems that lost convexity are solved again from
+ * u0 = 0 with twice their last tau (the others sit the round out); OT_OPT_PRECISION accepts
+ * only 1 and OT_OPT_THETA_FP64 only 2.  Any other key: OT_EINVAL. */
+int ot_batch_set_option(ot_plan_set* set, int32_t key, double value);
+int ot_batch_set_stream(ot_plan_set* set, void* cuda_stream);
+/* Solve the set's problems: count, N, M must repeat the set's sizes (else OT_EINVAL); f[k],
+ * g[k] (read) and phi[k] (written, mean zero) are device pointers to N[k] x M[k] planes owned
+ * by the caller; stats (HOST array of count, may be NULL) receives each problem's statistics
+ * (ms_total: the whole call; kernel_launches: the launches of the problem's size class).
+ * Returns after the results are complete: OT_OK if every problem converged, else the first
+ * non-OK status (the per-problem statuses are in stats). */
+int ot_solve_batched(ot_plan_set* set, int32_t count, const int32_t* N, const int32_t* M,
+                     const double* const* f, const double* const* g, double* const* phi,
+                     ot_stats* stats);
+void ot_plan_set_destroy(ot_plan_set* set);
 
 void ot_plan_destroy(ot_plan* plan);
 const char* ot_strerror(int status);

@@ -37,7 +37,8 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_pla
            "ot_ws_save_weights", "ot_ws_predict", "ot_ws_features", "ot_ws_mlp_forward",
            "ot_ws_poisson", "ot_transport_outputs", "ot_ws_trainer_create", "ot_ws_trainer_set_stream",
            "ot_ws_trainer_grad", "ot_ws_trainer_step", "ot_ws_trainer_get_params",
-           "ot_ws_trainer_destroy"]
+           "ot_ws_trainer_destroy", "ot_solve_plans", "ot_plan_set_create",
+           "ot_batch_set_option", "ot_batch_set_stream", "ot_plan_set_destroy"]
 
 
 class ot_stats(ctypes.Structure):
@@ -77,7 +78,12 @@ def _load():
         "ot_plan_set_stream": ([vp, vp], ctypes.c_int),
         "ot_solve": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
         "ot_solve_host": ([vp, vp, vp, vp, ctypes.POINTER(ot_stats)], ctypes.c_int),
-        "ot_solve_batched": ([i32, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_solve_plans": ([i32, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_solve_batched": ([vp, i32, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "ot_plan_set_create": ([ctypes.POINTER(vp), i32, vp, vp, d, d], ctypes.c_int),
+        "ot_batch_set_option": ([vp, i32, d], ctypes.c_int),
+        "ot_batch_set_stream": ([vp, vp], ctypes.c_int),
+        "ot_plan_set_destroy": ([vp], None),
         "ot_plan_destroy": ([vp], None),
         "ot_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "ot_prefilter": ([vp, vp, vp], ctypes.c_int),
@@ -146,12 +152,41 @@ def ot_solve_host(plan, f_ptr, g_ptr, phi_ptr, stats=None):
                               ctypes.byref(stats) if stats is not None else None)
 
 
-def ot_solve_batched(count, plans, f_ptrs, g_ptrs, phi_ptrs, stats=None):
+def ot_solve_plans(count, plans, f_ptrs, g_ptrs, phi_ptrs, stats=None):
     arr = ctypes.c_void_p * count
-    return _lib.ot_solve_batched(int(count), arr(*[p.value for p in plans]), arr(*f_ptrs),
-                                 arr(*g_ptrs), arr(*phi_ptrs),
+    return _lib.ot_solve_plans(int(count), arr(*[p.value for p in plans]), arr(*f_ptrs),
+                               arr(*g_ptrs), arr(*phi_ptrs),
+                               ctypes.cast(stats, ctypes.c_void_p) if stats is not None
+                               else None)
+
+
+def ot_plan_set_create(count, N, M, tau, tol):
+    h = ctypes.c_void_p()
+    ai = ctypes.c_int32 * count
+    rc = _lib.ot_plan_set_create(ctypes.byref(h), int(count), ai(*N), ai(*M), float(tau),
+                                 float(tol))
+    return rc, h
+
+
+def ot_batch_set_option(pset, key, value):
+    return _lib.ot_batch_set_option(pset, int(key), float(value))
+
+
+def ot_batch_set_stream(pset, stream_ptr):
+    return _lib.ot_batch_set_stream(pset, ctypes.c_void_p(stream_ptr))
+
+
+def ot_solve_batched(pset, count, N, M, f_ptrs, g_ptrs, phi_ptrs, stats=None):
+    ai = ctypes.c_int32 * count
+    arr = ctypes.c_void_p * count
+    return _lib.ot_solve_batched(pset, int(count), ai(*N), ai(*M), arr(*f_ptrs), arr(*g_ptrs),
+                                 arr(*phi_ptrs),
                                  ctypes.cast(stats, ctypes.c_void_p) if stats is not None
                                  else None)
+
+
+def ot_plan_set_destroy(pset):
+    _lib.ot_plan_set_destroy(pset)
 
 
 def ot_plan_destroy(plan):
@@ -484,6 +519,55 @@ class Plan:
     def close(self):
         if self.h:
             ot_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PlanSet:
+    """An ot_plan_set: problems of sizes [(N_k, M_k)] solved together (ot_solve_batched) on
+    torch float64 CUDA tensors; options as for Plan (the subset the set takes) plus
+    tau_retry."""
+
+    def __init__(self, sizes, tau=1.0, tol=1e-8, stream=None, **opts):
+        self.N = [int(n) for n, _ in sizes]
+        self.M = [int(m) for _, m in sizes]
+        rc, h = ot_plan_set_create(len(sizes), self.N, self.M, tau, tol)
+        _check(rc, "ot_plan_set_create")
+        self.h = h
+        self.set(**opts)
+        if stream is not None:
+            _check(ot_batch_set_stream(h, stream.cuda_stream if hasattr(stream, "cuda_stream")
+                                       else int(stream)), "ot_batch_set_stream")
+
+    def set(self, **opts):
+        for k, v in opts.items():
+            if k == "precision" and isinstance(v, str):
+                v = {"fp64": 0, "mixed": 1}[v]
+            _check(ot_batch_set_option(self.h, Plan._keys[k], float(v)), "set " + k)
+        return self
+
+    def solve(self, fs, gs, phis, raise_on=(OT_EINVAL, OT_ECUDA, OT_ENOMEM)):
+        """Solve every problem; returns (rc, [stats dict per problem])."""
+        n = len(self.N)
+        if not (len(fs) == len(gs) == len(phis) == n):
+            raise ValueError("one f, g, phi per problem")
+        ptr = []
+        for lst in (fs, gs, phis):
+            ptr.append([_dev(t, (self.N[k], self.M[k])).value for k, t in enumerate(lst)])
+        st = (ot_stats * n)()
+        rc = ot_solve_batched(self.h, n, self.N, self.M, ptr[0], ptr[1], ptr[2], st)
+        if rc in raise_on:
+            raise OTError(rc, "ot_solve_batched")
+        return rc, [st[k].as_dict() for k in range(n)]
+
+    def close(self):
+        if self.h:
+            ot_plan_set_destroy(self.h)
             self.h = None
 
     def __del__(self):

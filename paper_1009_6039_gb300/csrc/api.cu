@@ -94,7 +94,24 @@ struct ot_plan {
   // OT_OPT_PHASE_TIMES: stamp kernels at phase changes while a solve is issued or captured
   int phase_times = 0, stamping = 0, last_phase = -1, phase_force = -1;
   int transport = 0;  // OT_OPT_TRANSPORT: d(f, g) of Sec. 5.2 at the end of each solve
+  // batched plan (one size class of a plan set): `batch` pairs, each with all its per-pair
+  // buffers in its own slab of `slab` bytes (the pointers above are pair 0's); cur_mask: the
+  // pairs the launches being captured serve
+  int batch = 1;
+  size_t slab = 0;
+  int cur_mask = MASK_ALL;
+  void* slab_base = nullptr;
 };
+
+// batch descriptor of a plan's launches (a single problem: the plain launch)
+static Bat btc(const ot_plan* p) {
+  Bat b;
+  b.on = p->slab_base ? 1 : 0;
+  b.n = p->batch;
+  b.slab = p->slab;
+  b.mask = b.on ? p->cur_mask : MASK_ALL;
+  return b;
+}
 
 template <typename T> static const SpecTables& tables(ot_plan* p);
 template <> const SpecTables& tables<double>(ot_plan* p) { return p->tb64; }
@@ -108,7 +125,7 @@ static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
                                    int sel = 0) {
   if (sizeof(T) == 4)
     return launch_residual_dd(p->fdd, p->cdd, ua, p->N, p->M, Fraw, (float*)p->coef,
-                              p->partials, p->sc, p->stream, ub, sel, p->op_simple);
+                              p->partials, p->sc, p->stream, ub, sel, p->op_simple, btc(p));
   return launch_residual<double>(f, c, ua, p->N, p->M, Fraw, (double*)p->coef, p->partials,
                                  p->sc, p->stream, ub, sel, nullptr, p->op_simple);
 }
@@ -282,6 +299,18 @@ static void free_graph(ot_plan* p) {
 
 static void free_buffers(ot_plan* p) {
   free_graph(p);
+  if (p->slab_base) {
+    // a batched plan's per-pair buffers live in its slabs: one allocation
+    p->f = p->g = p->c = p->u = p->ucand = p->Fraw = p->uout = nullptr;
+    p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = p->q64 = nullptr;
+    p->fdd = p->cdd = nullptr;
+    p->partials = nullptr;
+    p->sc = nullptr;
+    cudaFree(p->slab_base);
+    p->slab_base = nullptr;
+    p->batch = 1;
+    p->slab = 0;
+  }
   if (p->uout) cudaFree(p->uout);
   p->uout = nullptr;
   void* ptrs[] = {p->fdd, p->cdd, p->f, p->g, p->c, p->u, p->ucand, p->Fraw, p->coef, p->V, p->w,
@@ -425,36 +454,9 @@ static int fill_reg_twiddles(ot_plan* p) {
   return OT_OK;
 }
 
-static int alloc_buffers(ot_plan* p) {
-  free_buffers(p);
-  const size_t P = (size_t)p->N * p->M;
-  const size_t ts = p->precision ? sizeof(float) : sizeof(double);
+// Transform and symbol tables (shared by all problems of a plan), the device and its SM count.
+static int alloc_tables(ot_plan* p) {
   const size_t L = p->M / 2;
-  CK(cudaMalloc(&p->f, P * 8));
-  CK(cudaMalloc(&p->g, P * 8));
-  CK(cudaMalloc(&p->c, P * 8));
-  CK(cudaMalloc(&p->u, P * 8));
-  CK(cudaMalloc(&p->ucand, P * 8));
-  CK(cudaMalloc(&p->Fraw, P * 8));
-  CK(cudaMalloc(&p->uout, P * 8));
-  CK(cudaMalloc(&p->coef, 5 * P * ts));
-  CK(cudaMalloc(&p->V, (size_t)(p->m + 1) * P * ts));
-  CK(cudaMalloc(&p->w, P * ts));
-  CK(cudaMalloc(&p->sigma, P * ts));
-  // half spectra: N x M/2 complex = P elements of the inner type
-  CK(cudaMalloc(&p->spec, P * ts));
-  CK(cudaMalloc(&p->q0, P * ts));
-  CK(cudaMalloc(&p->q1, P * ts));
-  CK(cudaMalloc(&p->q2, P * ts));
-  if (p->precision) {
-    CK(cudaMalloc(&p->spec64, P * 8));
-    CK(cudaMalloc(&p->q64, P * 8));
-    CK(cudaMalloc(&p->fdd, P * 8));
-    CK(cudaMalloc(&p->cdd, P * 8));
-  } else {
-    p->spec64 = nullptr;
-    p->q64 = nullptr;
-  }
   // twiddle tables
   // [row FFT length M/2 (4 L) | split W_M^k, k < M/2 (L) | column FFT length N (4 N)]
   std::vector<double> tw;
@@ -491,6 +493,40 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   p->kblocks = (sms > 0 ? sms : 148);  // GMRES vector kernels: 1 block of 256 per SM
   p->sms = sms > 0 ? sms : 148;
+  return OT_OK;
+}
+
+static int alloc_buffers(ot_plan* p) {
+  free_buffers(p);
+  const size_t P = (size_t)p->N * p->M;
+  const size_t ts = p->precision ? sizeof(float) : sizeof(double);
+  const size_t L = p->M / 2;
+  CK(cudaMalloc(&p->f, P * 8));
+  CK(cudaMalloc(&p->g, P * 8));
+  CK(cudaMalloc(&p->c, P * 8));
+  CK(cudaMalloc(&p->u, P * 8));
+  CK(cudaMalloc(&p->ucand, P * 8));
+  CK(cudaMalloc(&p->Fraw, P * 8));
+  CK(cudaMalloc(&p->uout, P * 8));
+  CK(cudaMalloc(&p->coef, 5 * P * ts));
+  CK(cudaMalloc(&p->V, (size_t)(p->m + 1) * P * ts));
+  CK(cudaMalloc(&p->w, P * ts));
+  CK(cudaMalloc(&p->sigma, P * ts));
+  // half spectra: N x M/2 complex = P elements of the inner type
+  CK(cudaMalloc(&p->spec, P * ts));
+  CK(cudaMalloc(&p->q0, P * ts));
+  CK(cudaMalloc(&p->q1, P * ts));
+  CK(cudaMalloc(&p->q2, P * ts));
+  if (p->precision) {
+    CK(cudaMalloc(&p->spec64, P * 8));
+    CK(cudaMalloc(&p->q64, P * 8));
+    CK(cudaMalloc(&p->fdd, P * 8));
+    CK(cudaMalloc(&p->cdd, P * 8));
+  } else {
+    p->spec64 = nullptr;
+    p->q64 = nullptr;
+  }
+  RET(alloc_tables(p));
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
   size_t nk = (size_t)p->kblocks * OTGB_MAXM;
   if (nk > np) np = nk;
@@ -498,6 +534,52 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaMalloc(&p->dmean, 8));
   CK(cudaMalloc(&p->sc, sizeof(DevScalars)));
   CK(cudaMemset(p->sc, 0, sizeof(DevScalars)));
+  CK(cudaMallocHost(&p->hsc, sizeof(DevScalars)));
+  memset(p->hsc, 0, sizeof(DevScalars));
+  CK(cudaMallocHost(&p->hinit, sizeof(DevScalars)));
+  memset(p->hinit, 0, sizeof(DevScalars));
+  p->ready = true;
+  return OT_OK;
+}
+
+// A batched plan: B problems of this plan's size, mixed precision, every per-pair buffer in
+// the pair's slab (equal layout, 256-byte aligned offsets), tables shared.
+static int alloc_batch(ot_plan* p, int B) {
+  free_buffers(p);
+  if (!p->precision || B < 1 || B > 1024) return OT_EINVAL;
+  const size_t P = (size_t)p->N * p->M;
+  RET(alloc_tables(p));
+  // GMRES vector kernels: blocks per pair by its size (the pairs fill the GPU together)
+  long kb = (long)(P / 2048);
+  p->kblocks = (int)std::min<long>(std::max<long>(kb, 8), p->sms);
+  size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
+  np = std::max(np, (size_t)p->kblocks * OTGB_MAXM);
+  np = std::max(np, (size_t)2 * p->sms * 8);  // the 2-blocks-per-SM grid reductions
+  struct Item {
+    void** ptr;
+    size_t bytes;
+  };
+  const Item items[] = {
+      {(void**)&p->f, P * 8}, {(void**)&p->g, P * 8}, {(void**)&p->c, P * 8},
+      {(void**)&p->u, P * 8}, {(void**)&p->ucand, P * 8}, {(void**)&p->Fraw, P * 8},
+      {(void**)&p->uout, P * 8}, {&p->coef, 5 * P * 4}, {&p->V, (size_t)(p->m + 1) * P * 4},
+      {&p->w, P * 4}, {&p->sigma, P * 4}, {&p->spec, P * 4}, {&p->q0, P * 4},
+      {&p->q1, P * 4}, {&p->q2, P * 4}, {&p->q64, P * 8}, {(void**)&p->fdd, P * 8},
+      {(void**)&p->cdd, P * 8}, {(void**)&p->partials, np * 8},
+      {(void**)&p->sc, sizeof(DevScalars)}};
+  size_t off[sizeof(items) / sizeof(items[0])];
+  size_t slab = 0;
+  for (size_t k = 0; k < sizeof(items) / sizeof(items[0]); ++k) {
+    off[k] = slab;
+    slab += (items[k].bytes + 255) / 256 * 256;
+  }
+  CK(cudaMalloc(&p->slab_base, slab * (size_t)B));
+  for (size_t k = 0; k < sizeof(items) / sizeof(items[0]); ++k)
+    *items[k].ptr = (char*)p->slab_base + off[k];
+  p->batch = B;
+  p->slab = slab;
+  CK(cudaMemset2D(p->sc, slab, 0, sizeof(DevScalars), B));
+  CK(cudaMalloc(&p->dmean, 8));
   CK(cudaMallocHost(&p->hsc, sizeof(DevScalars)));
   memset(p->hsc, 0, sizeof(DevScalars));
   CK(cudaMallocHost(&p->hinit, sizeof(DevScalars)));
@@ -858,9 +940,10 @@ static int read_scalars(ot_plan* p) {
 static int run_prefilter(ot_plan* p, const double* g, double* c) {
   LAUNCH(p, OT_PROF_OTHER, -1, 2,
          launch_prefilter(g, p->Fraw, c, p->precision ? p->cdd : nullptr, p->N, p->M,
-                          p->stream));
+                          p->stream, btc(p)));
   if (p->precision)
-    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(p->f, p->fdd, (long)p->N * p->M, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_split_dd(p->f, p->fdd, (long)p->N * p->M, p->stream, btc(p)));
   return OT_OK;
 }
 
@@ -870,7 +953,8 @@ static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* sca
                       const int* skip, int tag) {
   const size_t P = (size_t)p->N * p->M;
   const SpecTables& tb = tables<T>(p);
-  if (sizeof(T) == 4 && tb.mv_reg && tb.t2rA) {
+  const DevScalars* msc = p->slab_base ? p->sc : nullptr;
+  if (sizeof(T) == 4 && tb.mv_reg && tb.t2rA && !p->slab_base) {
     // register-resident passes on the transposed half spectrum
     LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
            launch_mvT_r2c((const float*)x, P, jptr, scale, (float2*)p->spec, p->N, p->M, tb,
@@ -886,14 +970,14 @@ static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* sca
   }
   LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
          launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip,
-                           p->stream));
+                           p->stream, btc(p), msc));
   LAUNCH(p, OT_PROF_COL_MATVEC, tag, 1,
          launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1,
-                       (C2<T>*)p->q2, p->N, p->M, tb, p->sc, skip, p->stream));
+                       (C2<T>*)p->q2, p->N, p->M, tb, p->sc, skip, p->stream, btc(p)));
   LAUNCH(p, OT_PROF_ROW_C2R_COMBINE, tag, 1,
          launch_row_c2r<T>(ROWINV_COMBINE, (C2<T>*)p->q0, (C2<T>*)p->q1, (C2<T>*)p->q2,
                            (const T*)p->coef, w, nullptr, nullptr, 0.0, 1.0, p->N, p->M, tb,
-                           skip, p->stream));
+                           skip, p->stream, msc, btc(p)));
   return OT_OK;
 }
 
@@ -946,13 +1030,13 @@ static int run_theta_impl(ot_plan* p, const double* u_in, double* u_out, double 
     LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
            launch_row_r2c<float>((const float*)p->sigma, 0, nullptr, nullptr,
                                  (C2<float>*)p->spec, p->N, p->M, p->tb32, nullptr,
-                                 p->stream));
+                                 p->stream, btc(p), p->slab_base ? p->sc : nullptr));
     LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
            launch_col_lbarinv_dd((const float2*)p->spec, (ddc*)p->q64, p->N, p->M, p->tb32,
-                                 p->tbdd, p->sc, p->stream));
+                                 p->tbdd, p->sc, p->stream, COL_LBARINV, btc(p)));
     LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
            launch_row_c2r_update_dd((const ddc*)p->q64, u_in, u_out, step, p->N, p->M,
-                                    p->tbdd, scp, p->stream));
+                                    p->tbdd, scp, p->stream, btc(p)));
     return OT_OK;
   }
   if (sizeof(T) == 4 && p->theta64) {
@@ -992,19 +1076,23 @@ static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
   T* w = (T*)p->w;
   RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j));
   LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
-         launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0));
+         launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0, btc(p)));
   if (reorth_on(p)) {
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1));
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1,
+                                  btc(p)));
     LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
-           launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1));
+           launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 1,
+                                btc(p)));
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 2));
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 2,
+                                  btc(p)));
   } else {
     // the multi-dot closes the step (norm by Pythagoras, Givens); the update only forms
     // v_(j+1) and is skipped when the cycle ends
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
-           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 3));
+           launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 3,
+                                  btc(p)));
   }
   return OT_OK;
 }
@@ -1342,57 +1430,66 @@ static int end_body(ot_plan* p, int level) {
 }
 
 // theta = Lbar^{-1} sigma, candidate u_(1-upar) = u_upar + s theta (s, upar from the device),
-// residual at the candidate, accept/halve
+// residual at the candidate, accept/halve (batched: for the pairs of the current mask)
 template <typename T>
 static int capture_candidate(ot_plan* p) {
-  const SpecTables& tb = tables<T>(p);
-  const int N = p->N, M = p->M;
   RET(run_theta<T>(p, p->u, p->ucand, 1.0, true));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, p->ucand, 1));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_ACCEPT, p->sc, p->stream, 5, btc(p)));
   return OT_OK;
 }
 
+// The solve as one captured sequence.  A batched plan (a size class of a plan set) captures
+// the same sequence over all its pairs: every launch serves the pairs its mask selects (the
+// current Newton loop, GMRES cycle loop or step-halving loop of each pair), the control
+// kernel keeps each loop running while any pair needs it, and all Arnoldi steps are plain
+// self-skipping launches (a pair whose cycle ended skips them).
 template <typename T>
 static int capture_solve(ot_plan* p) {
   const int N = p->N, M = p->M;
   const long P = (long)N * M;
+  const bool batched = p->slab_base != nullptr;
   T* V = (T*)p->V;
   T* w = (T*)p->w;
   T* sigma = (T*)p->sigma;
   long long k0 = p->launches;
+  p->cur_mask = MASK_ALL;
   if (p->translate)
     LAUNCH(p, OT_PROF_OTHER, -1, 2,
            launch_translate_inputs(p->f, p->g, p->f, p->g, N, M, p->partials, p->sc,
-                                   p->stream));
+                                   p->stream, btc(p)));
   else
     LAUNCH(p, OT_PROF_OTHER, -1, 1,
-           launch_input_stats(p->f, p->g, N, M, p->partials, p->sc, p->stream));
+           launch_input_stats(p->f, p->g, N, M, p->partials, p->sc, p->stream, btc(p)));
   RET(run_prefilter(p, p->g, p->c));
   if (p->warm_start == 2) RET(run_warmstart(p, p->u));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, p->ucand, 0));
   const int top = (int)(p->launches - k0) + 1;
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, top));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, top, btc(p)));
   cudaGraph_t b1, b2, b3, b4, b5;
   // ---- Newton loop
   RET(add_conditional(p->cs[0], cudaGraphCondTypeWhile, &p->h_newton, &b1));
   RET(begin_body(p, 1, b1));
-  if (p->forcing) LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_FORCING, p->sc, p->stream, 1));
+  p->cur_mask = MASK_NEWTON;
+  if (p->forcing)
+    LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_FORCING, p->sc, p->stream, 1, btc(p)));
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
          launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream,
-                              sigma));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_PRE_CYCLE, p->sc, p->stream, 2));
+                              sigma, btc(p)));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_PRE_CYCLE, p->sc, p->stream, 2, btc(p)));
   // ---- GMRES cycles
   RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_cycle, &b2));
   RET(begin_body(p, 2, b2));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream, 1));
+  p->cur_mask = MASK_CYCLE;
+  LAUNCH(p, OT_PROF_OTHER, -1, 1,
+         launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream, batched ? 1 + 5 * p->m : 1, btc(p)));
   // The first steps of a cycle are plain kernels that skip themselves once the cycle is done
   // (a conditional IF node costs ~5 us per execution, more than the early-exiting launches
-  // of the few steps a short cycle leaves); later steps sit in IF nodes.
-  const int K = p->m < kUncondSteps ? p->m : kUncondSteps;
+  // of the few steps a short cycle leaves); later steps sit in IF nodes.  A batched plan runs
+  // every step as a plain launch (the cycles of its pairs end at different steps).
+  const int K = batched ? p->m : (p->m < kUncondSteps ? p->m : kUncondSteps);
   for (int j = 0; j < p->m; ++j) {
     if (j < K) {
       p->h_step[j] = 0;
@@ -1404,34 +1501,40 @@ static int capture_solve(ot_plan* p) {
     RET(run_arnoldi_step<T>(p, j, nullptr));
     RET(end_body(p, 3));
   }
-  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream, btc(p)));
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
-         launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_END, p->sc, p->stream, 3));
+         launch_gmres_combine<T>(V, sigma, P, p->sc, p->kblocks, p->stream, btc(p)));
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_CYCLE_END, p->sc, p->stream, 3, btc(p)));
   RET(add_conditional(p->cs[2], cudaGraphCondTypeIf, &p->h_restart, &b4));
   RET(begin_body(p, 3, b4));
   RET(run_matvec<T>(p, sigma, nullptr, nullptr, w, nullptr, -1));
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
-         launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks, p->stream));
+         launch_gmres_init<T>(p->Fraw, w, V, P, 1, p->partials, p->sc, p->kblocks, p->stream,
+                              nullptr, btc(p)));
   RET(end_body(p, 3));
   RET(end_body(p, 2));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_GMRES_DONE, p->sc, p->stream, 1));
+  p->cur_mask = MASK_NEWTON;
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_GMRES_DONE, p->sc, p->stream, 1, btc(p)));
   // ---- candidate, then halve while inadmissible
   RET(capture_candidate<T>(p));
   RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_halve, &b5));
   RET(begin_body(p, 2, b5));
+  p->cur_mask = MASK_HALVE;
   RET(capture_candidate<T>(p));
   RET(end_body(p, 2));
-  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, 1));
+  p->cur_mask = MASK_NEWTON;
+  LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_ctl(CTL_NEWTON, p->sc, p->stream, 1, btc(p)));
   RET(end_body(p, 1));
+  p->cur_mask = MASK_ALL;
   // ---- final residual norm and mean-zero gauge
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream));
+         launch_residual_l2(p->Fraw, N, M, p->partials, p->sc, p->stream, btc(p)));
   UPair up{p->u, p->ucand};
   LAUNCH(p, OT_PROF_OTHER, -1, 2,
-         launch_final_gauge(up, p->uout, N, M, p->partials, p->sc, p->dmean, p->stream));
+         launch_final_gauge(up, p->uout, N, M, p->partials, p->sc,
+                            batched ? &p->sc->gauge_mean : p->dmean, p->stream, btc(p)));
   p->top_kernels = 3;  // residual_l2 + gauge (2), counted on the host
-  if (p->transport) {
+  if (p->transport && !batched) {
     LAUNCH(p, OT_PROF_OTHER, -1, 1,
            launch_transport(p->f, p->uout, N, M, nullptr, p->partials,
                             &p->sc->ticket[TK_TRANSPORT], &p->sc->dist, p->stream));
@@ -1798,16 +1901,16 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
   return rc;
 }
 
-// Batched solve: every problem's graph is enqueued on the execution stream of its plan
-// (problems sharing a plan run back to back there; different plans run concurrently), and
-// the host synchronises once at the end.  Result slots are pinned host memory kept across
-// calls.
+// Independent solves on several plans: every problem's graph is enqueued on the execution
+// stream of its plan (problems sharing a plan run back to back there; different plans run
+// concurrently), and the host synchronises once at the end.  Result slots are pinned host
+// memory kept across calls (grown when a call has more problems than any before).
 static std::mutex g_batch_mutex;
 static DevScalars* g_batch_slots = nullptr;
 static double* g_batch_means = nullptr;
 static size_t g_batch_cap = 0;
 
-extern "C" int ot_solve_batched(int32_t count, ot_plan* const* plans, const double* const* f,
+extern "C" int ot_solve_plans(int32_t count, ot_plan* const* plans, const double* const* f,
                                 const double* const* g, double* const* phi, ot_stats* stats) {
   if (count < 0 || (count > 0 && (!plans || !f || !g || !phi))) return OT_EINVAL;
   for (int k = 0; k < count; ++k)
@@ -2268,4 +2371,338 @@ extern "C" int ot_ws_trainer_get_params(ot_ws_trainer* tr, float* params_host, i
   CK(cudaMemcpyAsync(params_host, tr->params, count * 4, cudaMemcpyDeviceToHost, tr->stream));
   CK(cudaStreamSynchronize(tr->stream));
   return OT_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Plan sets: many problems of uneven sizes in one graph launch.  The problems are grouped
+// into size classes; each class is a batched plan (every kernel of the mixed-precision solve
+// serves all its pairs at once, gridDim.z = pairs, per-pair masks), and the whole solve of
+// every class is one captured graph with one branch per class.
+// ------------------------------------------------------------------------------------------
+namespace {
+struct BatchClass {
+  int N = 0, M = 0;
+  std::vector<int> idx;        // problem indices of this class
+  ot_plan* p = nullptr;        // the batched plan
+  double** dtab = nullptr;     // device pointer table: f[B], g[B], phi[B]
+  double** htab = nullptr;     // pinned staging of the table
+  DevScalars* hsc = nullptr;   // pinned: the pairs' scalars (initial, then final)
+};
+}  // namespace
+
+struct ot_plan_set {
+  int count = 0;
+  std::vector<int> N, M;
+  double tau = 1.0, tol = 1e-8;
+  std::vector<std::pair<int, double>> opts;  // plan options, applied in order
+  int tau_retry = 0;
+  std::vector<BatchClass> cls;
+  cudaStream_t stream = 0;
+  cudaStream_t s0 = nullptr;  // origin of the capture
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int device = 0;
+};
+
+static void set_free_graph(ot_plan_set* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->gexec = nullptr;
+  s->graph = nullptr;
+}
+
+static void set_free_classes(ot_plan_set* s) {
+  set_free_graph(s);
+  for (auto& c : s->cls) {
+    if (c.p) ot_plan_destroy(c.p);
+    if (c.dtab) cudaFree(c.dtab);
+    if (c.htab) cudaFreeHost(c.htab);
+    if (c.hsc) cudaFreeHost(c.hsc);
+    c.p = nullptr;
+    c.dtab = nullptr;
+    c.htab = nullptr;
+    c.hsc = nullptr;
+  }
+}
+
+extern "C" int ot_plan_set_create(ot_plan_set** out, int32_t count, const int32_t* N,
+                                  const int32_t* M, double tau, double tol) {
+  if (!out) return OT_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !N || !M || !(tau >= 1.0) || !(tol > 0.0)) return OT_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (!size_supported(N[k], M[k])) return OT_EUNSUPPORTED;
+  ot_plan_set* s = new (std::nothrow) ot_plan_set();
+  if (!s) return OT_ENOMEM;
+  s->count = count;
+  s->N.assign(N, N + count);
+  s->M.assign(M, M + count);
+  s->tau = tau;
+  s->tol = tol;
+  for (int k = 0; k < count; ++k) {
+    BatchClass* c = nullptr;
+    for (auto& e : s->cls)
+      if (e.N == N[k] && e.M == M[k]) c = &e;
+    if (!c) {
+      s->cls.emplace_back();
+      c = &s->cls.back();
+      c->N = N[k];
+      c->M = M[k];
+    }
+    c->idx.push_back(k);
+  }
+  for (auto& c : s->cls)
+    if (c.idx.size() > 1024) {
+      delete s;
+      return OT_EUNSUPPORTED;
+    }
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return OT_ECUDA;
+  }
+  *out = s;
+  return OT_OK;
+}
+
+extern "C" void ot_plan_set_destroy(ot_plan_set* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  set_free_classes(s);
+  if (s->s0) cudaStreamDestroy(s->s0);
+  delete s;
+}
+
+extern "C" int ot_batch_set_stream(ot_plan_set* s, void* stream) {
+  if (!s) return OT_EINVAL;
+  s->stream = (cudaStream_t)stream;
+  return OT_OK;
+}
+
+extern "C" int ot_batch_set_option(ot_plan_set* s, int32_t key, double v) {
+  if (!s) return OT_EINVAL;
+  switch (key) {
+    case OT_OPT_PRECISION:  // the batched solve is the mixed-precision one
+      return v == 1 ? OT_OK : OT_EINVAL;
+    case OT_OPT_THETA_FP64:  // theta's inverse transforms in double-float
+      return v == 2 ? OT_OK : OT_EINVAL;
+    case OT_OPT_TAU_RETRY:
+      if (!(v >= 0 && v <= 8) || v != (double)(int)v) return OT_EINVAL;
+      s->tau_retry = (int)v;
+      return OT_OK;
+    case OT_OPT_TAU:
+      if (!(v >= 1.0)) return OT_EINVAL;
+      s->tau = v;
+      break;
+    case OT_OPT_TOL:
+      if (!(v > 0.0)) return OT_EINVAL;
+      s->tol = v;
+      break;
+    case OT_OPT_RESTART:
+      if (!(v >= 1 && v <= OTGB_MAXM - 1) || v != (double)(int)v) return OT_EINVAL;
+      set_free_classes(s);  // the basis size changes the slabs
+      break;
+    case OT_OPT_ETA:
+      if (!(v > 0.0 && v < 1.0)) return OT_EINVAL;
+      break;
+    case OT_OPT_MAX_NEWTON:
+    case OT_OPT_MAX_RESTARTS:
+      if (v < (key == OT_OPT_MAX_NEWTON ? 0 : 1) || v != (double)(int)v) return OT_EINVAL;
+      break;
+    case OT_OPT_SAFEGUARD:
+    case OT_OPT_TRANSLATE:
+    case OT_OPT_SYMBOLS:
+    case OT_OPT_FORCING:
+    case OT_OPT_OPERATOR:
+    case OT_OPT_REORTH:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      break;
+    default:
+      return OT_EINVAL;
+  }
+  s->opts.emplace_back(key, v);
+  set_free_graph(s);
+  for (auto& c : s->cls)
+    if (c.p) RET(ot_plan_set_option(c.p, key, v));
+  return OT_OK;
+}
+
+// Create the class plans (first use or after a basis-size change) and capture the graph: from
+// the capture origin every class forks onto its plan's own stream, gathers its pairs' inputs
+// from the pointer table, zeroes the iterates, runs the batched solve and scatters the
+// potentials; the branches join at the end.
+static int set_build(ot_plan_set* s) {
+  for (auto& c : s->cls) {
+    if (c.p) continue;
+    const int B = (int)c.idx.size();
+    RET(ot_plan_create(&c.p, c.N, c.M, s->tau, s->tol));
+    RET(ot_plan_set_option(c.p, OT_OPT_PRECISION, 1));
+    c.p->autotune = 0;  // the batched passes are the generic kernels
+    for (auto& kv : s->opts)
+      if (kv.first != OT_OPT_TAU && kv.first != OT_OPT_TOL)
+        RET(ot_plan_set_option(c.p, kv.first, kv.second));
+    RET(alloc_batch(c.p, B));
+    CK(cudaMalloc(&c.dtab, 3 * (size_t)B * sizeof(double*)));
+    CK(cudaMallocHost(&c.htab, 3 * (size_t)B * sizeof(double*)));
+    CK(cudaMallocHost(&c.hsc, (size_t)B * sizeof(DevScalars)));
+    for (int k = 0; k < 4; ++k)
+      if (!c.p->cs[k]) CK(cudaStreamCreateWithFlags(&c.p->cs[k], cudaStreamNonBlocking));
+  }
+  if (s->gexec) return OT_OK;
+  if (!s->s0) CK(cudaStreamCreateWithFlags(&s->s0, cudaStreamNonBlocking));
+  cudaEvent_t fork = nullptr;
+  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  std::vector<cudaEvent_t> joins(s->cls.size(), nullptr);
+  for (auto& e : joins) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CK(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeRelaxed));
+  int rc = OT_OK;
+  cudaError_t e = cudaEventRecord(fork, s->s0);
+  for (size_t ci = 0; ci < s->cls.size() && rc == OT_OK && e == cudaSuccess; ++ci) {
+    BatchClass& c = s->cls[ci];
+    ot_plan* p = c.p;
+    const int B = (int)c.idx.size();
+    const long P = (long)p->N * p->M;
+    p->tau = s->tau;
+    p->tol = s->tol;
+    p->stream = p->cs[0];
+    p->cur_mask = MASK_ALL;
+    if ((e = cudaStreamWaitEvent(p->cs[0], fork, 0)) != cudaSuccess) break;
+    if ((e = launch_gather(c.dtab, p->f, P, btc(p), p->stream)) != cudaSuccess) break;
+    if ((e = launch_gather(c.dtab + B, p->g, P, btc(p), p->stream)) != cudaSuccess) break;
+    if ((e = cudaMemset2DAsync(p->u, p->slab, 0, P * 8, B, p->stream)) != cudaSuccess) break;
+    rc = capture_solve<float>(p);
+    if (rc != OT_OK) break;
+    p->cur_mask = MASK_ALL;
+    if ((e = launch_scatter(p->uout, c.dtab + 2 * B, P, p->sc, btc(p), p->stream)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(joins[ci], p->cs[0])) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(s->s0, joins[ci], 0)) != cudaSuccess) break;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(s->s0, &g);
+  for (auto& c : s->cls)
+    if (c.p) c.p->stream = s->stream;
+  cudaEventDestroy(fork);
+  for (auto& j : joins) cudaEventDestroy(j);
+  if (rc != OT_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (e != cudaSuccess) record_error(e, __LINE__);
+    for (auto& c : s->cls)
+      if (c.p) abandon_captures(c.p);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != OT_OK ? rc : OT_ECUDA;
+  }
+  s->graph = g;
+  e = cudaGraphInstantiate(&s->gexec, g, 0);
+  if (e != cudaSuccess) {
+    record_error(e, __LINE__);
+    set_free_graph(s);
+    return OT_ECUDA;
+  }
+  return OT_OK;
+}
+
+// initial scalars of pair k of class c: those of a graph-launched solve with every Arnoldi
+// step a plain launch, the pair's tau (doubled per retry) and whether it sits this launch out
+static void set_pair_scalars(ot_plan* p, DevScalars* h, double tau, int excluded) {
+  const double tau0 = p->tau;
+  p->tau = tau;
+  graph_scalars(p, h);
+  p->tau = tau0;
+  h->steps_uncond = p->m;
+  h->cycle_done = 1;
+  h->excluded = excluded;
+}
+
+extern "C" int ot_solve_batched(ot_plan_set* s, int32_t count, const int32_t* N,
+                                const int32_t* M, const double* const* f,
+                                const double* const* g, double* const* phi, ot_stats* stats) {
+  if (!s || count != s->count || !N || !M || !f || !g || !phi) return OT_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (N[k] != s->N[k] || M[k] != s->M[k] || !f[k] || !g[k] || !phi[k]) return OT_EINVAL;
+  CK(cudaSetDevice(s->device));
+  RET(set_build(s));
+  cudaStream_t st = s->stream;
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
+  std::vector<double> tau(count, s->tau);
+  std::vector<int> last_status(count, OT_OK), done(count, 0);
+  std::vector<DevScalars> fin(count);
+  for (auto& c : s->cls) {
+    const int B = (int)c.idx.size();
+    for (int k = 0; k < B; ++k) {
+      c.htab[k] = const_cast<double*>(f[c.idx[k]]);
+      c.htab[B + k] = const_cast<double*>(g[c.idx[k]]);
+      c.htab[2 * B + k] = phi[c.idx[k]];
+    }
+    CK(cudaMemcpyAsync(c.dtab, c.htab, 3 * (size_t)B * sizeof(double*), cudaMemcpyHostToDevice,
+                       st));
+  }
+  // attempt 0 solves every pair; each further attempt (OT_OPT_TAU_RETRY) solves again, with
+  // twice the tau, only the pairs whose last attempt lost convexity (the others sit it out)
+  for (int attempt = 0; attempt <= s->tau_retry; ++attempt) {
+    bool any = false;
+    for (auto& c : s->cls) {
+      const int B = (int)c.idx.size();
+      for (int k = 0; k < B; ++k) {
+        const int q = c.idx[k];
+        const int run = attempt == 0 || (!done[q] && last_status[q] == OT_EDIVERGED);
+        if (attempt > 0 && run) tau[q] *= 2.0;
+        set_pair_scalars(c.p, &c.hsc[k], tau[q], run ? 0 : 1);
+        any |= run != 0;
+      }
+      CK(cudaMemcpy2DAsync(c.p->sc, c.p->slab, c.hsc, sizeof(DevScalars), sizeof(DevScalars), B,
+                           cudaMemcpyHostToDevice, st));
+    }
+    if (!any) break;
+    CK(cudaGraphLaunch(s->gexec, st));
+    for (auto& c : s->cls)
+      CK(cudaMemcpy2DAsync(c.hsc, sizeof(DevScalars), c.p->sc, c.p->slab, sizeof(DevScalars),
+                           c.idx.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (auto& c : s->cls)
+      for (size_t k = 0; k < c.idx.size(); ++k) {
+        if (c.hsc[k].excluded) continue;
+        const int q = c.idx[k];
+        fin[q] = c.hsc[k];
+        last_status[q] = c.hsc[k].status;
+        if (c.hsc[k].status != OT_EDIVERGED) done[q] = 1;
+      }
+  }
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  int first = OT_OK;
+  for (auto& c : s->cls)
+    for (size_t k = 0; k < c.idx.size(); ++k) {
+      const int q = c.idx[k];
+      const DevScalars& h = fin[q];
+      if (h.status != OT_OK && first == OT_OK) first = h.status;
+      if (!stats) continue;
+      ot_stats& o = stats[q];
+      memset(&o, 0, sizeof(o));
+      o.status = h.status;
+      o.newton_iters = h.newton_n;
+      o.gmres_iters = h.gmres_iters_total;
+      o.gmres_cycles = h.gmres_cycles_total;
+      o.step_halvings = h.halvings;
+      o.kernel_launches = (int32_t)(c.hsc[0].kcount + c.p->top_kernels);
+      o.res_inf = h.res_inf;
+      o.res_l2 = sqrt(h.res_l2sum / ((double)c.N * (double)c.M));
+      o.min_det = h.min_det;
+      o.mean_fn = h.mean_fn;
+      o.phi_mean = h.gauge_mean;
+      o.ms_total = ms;
+      o.ws_alpha = -1.0;
+      o.mass_defect_f = h.in_mean[0] - 1.0;
+      o.mass_defect_g = h.in_mean[1] - 1.0;
+      o.transport_dist = -1.0;
+      o.ms_residual = o.ms_fft = o.ms_krylov = o.ms_update = o.ms_other = -1.0;
+    }
+  return first;
 }

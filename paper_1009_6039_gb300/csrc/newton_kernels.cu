@@ -231,7 +231,12 @@ __device__ bool grid_reduce_dd(dd (&v)[NV], const int (&kind)[NV], double* parti
 // Sec. 5.2): d <- d - mean(d) + 1; rejects non-finite input or a non-positive result.
 // ---------------------------------------------------------------------------------------
 __global__ void k_input_stats(const double* __restrict__ f, const double* __restrict__ g,
-                              long P, double* partials, DevScalars* sc) {
+                              long P, double* partials, DevScalars* sc, Bat bat) {
+  f = badv(f, bat);
+  g = badv(g, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
   double v[6] = {0.0, 0.0, INFINITY, INFINITY, 0.0, 0.0};
   const int kind[6] = {0, 0, 2, 2, 0, 0};
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
@@ -270,7 +275,13 @@ __global__ void k_input_stats(const double* __restrict__ f, const double* __rest
 
 __global__ void k_input_apply(const double* __restrict__ f, const double* __restrict__ g,
                               double* __restrict__ ft, double* __restrict__ gt, long P,
-                              const DevScalars* __restrict__ sc) {
+                              const DevScalars* __restrict__ sc, Bat bat) {
+  f = badv(f, bat);
+  g = badv(g, bat);
+  ft = badv(ft, bat);
+  gt = badv(gt, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
   const double sf = 1.0 - sc->in_mean[0], sg = 1.0 - sc->in_mean[1];
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x) {
@@ -317,8 +328,11 @@ constexpr size_t PT_SMEM = (size_t)(PT_TP + 2 * PRE_K) * PT_SW * sizeof(double);
 template <bool XPASS>
 __global__ void __launch_bounds__(256)
     k_prefilter_tile(const double* __restrict__ s, double* __restrict__ out,
-                     float2* __restrict__ dd_out, int N, int M, double z, double A) {
+                     float2* __restrict__ dd_out, int N, int M, double z, double A, Bat bat) {
   extern __shared__ __align__(16) double smp[];  // [k][line], k = point - p0 + PRE_K
+  s = badv(s, bat);
+  out = badv(out, bat);
+  dd_out = badv(dd_out, bat);
   const int tid = threadIdx.x;
   const int L = XPASS ? M : N, nlines = XPASS ? N : M;
   const long ls = XPASS ? M : 1, ps = XPASS ? 1 : M;
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(256)
 }
 
 cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
-                             int M, cudaStream_t st) {
+                             int M, cudaStream_t st, Bat bat) {
   static bool attr_set[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -393,15 +407,17 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
   const double A = 6.0 * z / (z * z - 1.0);
   // columns (along y), then rows (along x)
   const dim3 gy((M + PT_LN - 1) / PT_LN, (N + PT_TP - 1) / PT_TP);
-  k_prefilter_tile<false><<<gy, 256, PT_SMEM, st>>>(g, scratch, nullptr, N, M, z, A);
+  k_prefilter_tile<false><<<bgrid(gy, bat), 256, PT_SMEM, st>>>(g, scratch, nullptr, N, M, z, A,
+                                                                 bat);
   const dim3 gx((N + PT_LN - 1) / PT_LN, (M + PT_TP - 1) / PT_TP);
-  k_prefilter_tile<true><<<gx, 256, PT_SMEM, st>>>(scratch, c, cdd, N, M, z, A);
+  k_prefilter_tile<true><<<bgrid(gx, bat), 256, PT_SMEM, st>>>(scratch, c, cdd, N, M, z, A, bat);
   return cudaGetLastError();
 }
 
 cudaError_t launch_input_stats(const double* f, const double* g, int N, int M,
-                               double* partials, DevScalars* sc, cudaStream_t st) {
-  k_input_stats<<<reduce_blocks(), 256, 0, st>>>(f, g, (long)N * M, partials, sc);
+                               double* partials, DevScalars* sc, cudaStream_t st, Bat bat) {
+  k_input_stats<<<bgrid(dim3(reduce_blocks()), bat), 256, 0, st>>>(f, g, (long)N * M, partials,
+                                                                   sc, bat);
   return cudaGetLastError();
 }
 
@@ -422,11 +438,11 @@ cudaError_t launch_stamp(DevScalars* sc, int cls, cudaStream_t st) {
 
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, Bat bat) {
   const long P = (long)N * M;
-  const int nb = reduce_blocks();
-  k_input_stats<<<nb, 256, 0, st>>>(f, g, P, partials, sc);
-  k_input_apply<<<nb, 256, 0, st>>>(f, g, ft, gt, P, sc);
+  const dim3 nb = bgrid(dim3(reduce_blocks()), bat);
+  k_input_stats<<<nb, 256, 0, st>>>(f, g, P, partials, sc, bat);
+  k_input_apply<<<nb, 256, 0, st>>>(f, g, ft, gt, P, sc, bat);
   return cudaGetLastError();
 }
 
@@ -721,9 +737,18 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
     k_residual_dd(const float2* __restrict__ fdd, const float2* __restrict__ cdd,
                   const double* __restrict__ ua, const double* __restrict__ ub, int sel, int N,
                   int M, ResidConstsDD K, double* __restrict__ Fraw, float* __restrict__ coef,
-                  double* partials, DevScalars* sc) {
+                  double* partials, DevScalars* sc, Bat bat) {
   __shared__ dd tile[RTY + 4][RTX + 4];
   __shared__ dd dyt[RTY][RTX + 4];  // unscaled y-difference of u (halo 2 in x)
+  fdd = badv(fdd, bat);
+  cdd = badv(cdd, bat);
+  ua = badv(ua, bat);
+  ub = badv(ub, bat);
+  Fraw = badv(Fraw, bat);
+  coef = badv(coef, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
   const double* __restrict__ u = (ub && ((sc->upar ^ sel) & 1)) ? ub : ua;
   const int bx = blockIdx.x * RTX, by = blockIdx.y * RTY;
   const int tid = threadIdx.x;
@@ -879,7 +904,10 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
 }
 
 // split FP64 values into (hi, lo) float pairs
-__global__ void k_split_dd(const double* __restrict__ in, float2* __restrict__ out, long n) {
+__global__ void k_split_dd(const double* __restrict__ in, float2* __restrict__ out, long n,
+                           Bat bat) {
+  in = badv(in, bat);
+  out = badv(out, bat);
   for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
        k += (long)gridDim.x * blockDim.x) {
     const dd v = dd_from_double(in[k]);
@@ -887,11 +915,11 @@ __global__ void k_split_dd(const double* __restrict__ in, float2* __restrict__ o
   }
 }
 
-cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st) {
+cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st, Bat bat) {
   long nb = (n + 255) / 256;
   if (nb > 4096) nb = 4096;
   if (nb < 1) nb = 1;
-  k_split_dd<<<(int)nb, 256, 0, st>>>(in, out, n);
+  k_split_dd<<<bgrid(dim3((int)nb), bat), 256, 0, st>>>(in, out, n, bat);
   return cudaGetLastError();
 }
 
@@ -905,7 +933,7 @@ static dd host_dd(double v) {
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
                                DevScalars* sc, cudaStream_t st, const double* ub, int sel,
-                               int simplified) {
+                               int simplified, Bat bat) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConstsDD K;
   K.Mh = host_dd((double)M / 12.0);
@@ -919,8 +947,8 @@ cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const doubl
   K.w3M = (float)(1.0 / (3.0 * (double)M));
   K.w3N = (float)(1.0 / (3.0 * (double)N));
   K.nob = simplified ? 1 : 0;
-  k_residual_dd<<<grid, RTX * RTY / RPT, 0, st>>>(fdd, cdd, ua, ub, sel, N, M, K, Fraw, coef,
-                                                  partials, sc);
+  k_residual_dd<<<bgrid(grid, bat), RTX * RTY / RPT, 0, st>>>(fdd, cdd, ua, ub, sel, N, M, K,
+                                                                Fraw, coef, partials, sc, bat);
   return cudaGetLastError();
 }
 
@@ -951,7 +979,11 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
 
 // sum of (Fraw + shift)^2 -> res_l2sum
 __global__ void k_residual_l2(const double* __restrict__ Fraw, long P, double* partials,
-                              DevScalars* sc) {
+                              DevScalars* sc, Bat bat) {
+  Fraw = badv(Fraw, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
   const double s = sc->shift;
   double v[1] = {0.0};
   const int kind[1] = {0};
@@ -970,8 +1002,9 @@ __global__ void k_residual_l2(const double* __restrict__ Fraw, long P, double* p
 }
 
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
-                               DevScalars* sc, cudaStream_t st) {
-  k_residual_l2<<<reduce_blocks(), 256, 0, st>>>(Fraw, (long)N * M, partials, sc);
+                               DevScalars* sc, cudaStream_t st, Bat bat) {
+  k_residual_l2<<<bgrid(dim3(reduce_blocks()), bat), 256, 0, st>>>(Fraw, (long)N * M, partials,
+                                                                   sc, bat);
   return cudaGetLastError();
 }
 
@@ -1043,7 +1076,14 @@ cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevS
 template <typename T>
 __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restrict__ w,
                              T* __restrict__ V0, long P, int restart, double* partials,
-                             DevScalars* sc, T* __restrict__ sigma) {
+                             DevScalars* sc, T* __restrict__ sigma, Bat bat) {
+  Fraw = badv(Fraw, bat);
+  w = badv(w, bat);
+  V0 = badv(V0, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  sigma = badv(sigma, bat);
+  if (bskip(sc, bat)) return;
   const double s = sc->shift, inv_tau = 1.0 / sc->tau;
   double v[1] = {0.0};
   const int kind[1] = {0};
@@ -1301,8 +1341,12 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
 
 template <typename T>
 __global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, long P,
-                             double* partials, DevScalars* sc, int pass) {
-  if (sc->cycle_done) return;
+                             double* partials, DevScalars* sc, int pass, Bat bat) {
+  V = badv(V, bat);
+  w = badv(w, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat) || sc->cycle_done) return;
   if (pass) w = V + (size_t)(sc->j + 1) * P;
   switch (sc->j) {
 #define OTGB_DOTS_CASE(k) \
@@ -1374,8 +1418,12 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
 
 template <typename T>
 __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long P,
-                               double* partials, DevScalars* sc, int mode) {
-  if (sc->cycle_done) return;
+                               double* partials, DevScalars* sc, int mode, Bat bat) {
+  V = badv(V, bat);
+  w = badv(w, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat) || sc->cycle_done) return;
   // mode 3 runs after the multi-dot closed the step (sc->j already advanced)
   switch (mode == 3 ? sc->j - 1 : sc->j) {
 #define OTGB_UPD_CASE(k) \
@@ -1391,9 +1439,10 @@ __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long 
 
 // y = R^{-1} g by back substitution: the 32 threads stage R and g in shared memory (one
 // round of independent loads), thread 0 solves there
-__global__ void k_gmres_finish(DevScalars* sc) {
+__global__ void k_gmres_finish(DevScalars* sc, Bat bat) {
   __shared__ double R[OTGB_MAXM * OTGB_MAXM], g[OTGB_MAXM], y[OTGB_MAXM];
-  if (blockIdx.x != 0) return;
+  sc = badv(sc, bat);
+  if (blockIdx.x != 0 || bskip(sc, bat)) return;
   const int n = sc->jend, m = sc->m;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) R[e] = sc->H[(e / n) * m + e % n];
   for (int e = threadIdx.x; e < n; e += blockDim.x) g[e] = sc->gv[e];
@@ -1409,8 +1458,8 @@ __global__ void k_gmres_finish(DevScalars* sc) {
   for (int e = threadIdx.x; e < n; e += blockDim.x) sc->y[e] = y[e];
 }
 
-cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st) {
-  k_gmres_finish<<<1, 32, 0, st>>>(sc);
+cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st, Bat bat) {
+  k_gmres_finish<<<bgrid(dim3(1), bat), 32, 0, st>>>(sc, bat);
   return cudaGetLastError();
 }
 
@@ -1446,7 +1495,11 @@ __device__ __forceinline__ void combine_j(const T* __restrict__ V, T* __restrict
 
 template <typename T>
 __global__ void k_gmres_combine(const T* __restrict__ V, T* __restrict__ sigma, long P,
-                                const DevScalars* __restrict__ sc) {
+                                const DevScalars* __restrict__ sc, Bat bat) {
+  V = badv(V, bat);
+  sigma = badv(sigma, bat);
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
   switch (sc->jend) {
 #define OTGB_CMB_CASE(k) \
   case k:                \
@@ -1463,26 +1516,28 @@ __global__ void k_gmres_combine(const T* __restrict__ V, T* __restrict__ sigma, 
 template <typename T>
 cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
                               double* partials, DevScalars* sc, int nblocks, cudaStream_t st,
-                              T* sigma) {
-  k_gmres_init<T><<<nblocks, 256, 0, st>>>(Fraw, w, V0, P, restart, partials, sc, sigma);
+                              T* sigma, Bat bat) {
+  k_gmres_init<T><<<bgrid(dim3(nblocks), bat), 256, 0, st>>>(Fraw, w, V0, P, restart, partials,
+                                                             sc, sigma, bat);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
-                              int nblocks, cudaStream_t st, int pass) {
-  k_gmres_dots<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc, pass);
+                              int nblocks, cudaStream_t st, int pass, Bat bat) {
+  k_gmres_dots<T><<<bgrid(dim3(nblocks), bat), 256, 0, st>>>(V, w, P, partials, sc, pass, bat);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
-                                int nblocks, cudaStream_t st, int mode) {
-  k_gmres_update<T><<<nblocks, 256, 0, st>>>(V, w, P, partials, sc, mode);
+                                int nblocks, cudaStream_t st, int mode, Bat bat) {
+  k_gmres_update<T><<<bgrid(dim3(nblocks), bat), 256, 0, st>>>(V, w, P, partials, sc, mode,
+                                                               bat);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,
-                                 int nblocks, cudaStream_t st) {
-  k_gmres_combine<T><<<nblocks, 256, 0, st>>>(V, sigma, P, sc);
+                                 int nblocks, cudaStream_t st, Bat bat) {
+  k_gmres_combine<T><<<bgrid(dim3(nblocks), bat), 256, 0, st>>>(V, sigma, P, sc, bat);
   return cudaGetLastError();
 }
 
@@ -1501,12 +1556,14 @@ __device__ __forceinline__ void set_cond(const DevScalars* sc, unsigned long lon
   if (sc->graph && h) cudaGraphSetConditional(h, v);
 }
 
-__global__ void k_ctl(int op, DevScalars* sc, int add) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One control operation on one problem's scalars.  handles = 0: a batched solve, whose
+// conditional handles are set once for all pairs by k_ctl_batch (and whose Arnoldi steps are
+// not conditional); the return value is what the operation's handle would receive.
+__device__ int ctl_apply(int op, DevScalars* sc, int add, bool handles) {
   sc->kcount += add;
+  int cont = 0;
   switch (op) {
     case CTL_NEWTON: {
-      int cont = 0;
       if (sc->in_bad) {
         sc->status = OT_STATUS_EINVAL;
       } else if (!sc->admissible) {
@@ -1519,7 +1576,8 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
         sc->status = OT_STATUS_OK;
         cont = 1;
       }
-      set_cond(sc, sc->h_newton, cont);
+      sc->active = cont;
+      if (handles) set_cond(sc, sc->h_newton, cont);
       break;
     }
     case CTL_ACCEPT: {
@@ -1528,29 +1586,37 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
         sc->upar ^= 1;
         sc->newton_n += 1;
         sc->step_s = (2.0 * s < 1.0) ? 2.0 * s : 1.0;
-        set_cond(sc, sc->h_halve, 0);
       } else {
         sc->step_s = 0.5 * s;
         sc->halvings += 1;
-        set_cond(sc, sc->h_halve, 1);
+        cont = 1;
       }
+      sc->halve = cont;
+      if (handles) set_cond(sc, sc->h_halve, cont);
       break;
     }
     case CTL_PRE_CYCLE:
-      set_cond(sc, sc->h_cycle, sc->converged ? 0u : 1u);
+      cont = sc->converged ? 0 : 1;
+      sc->in_cycle = cont;
+      if (handles) set_cond(sc, sc->h_cycle, cont);
       break;
     case CTL_CYCLE_BEGIN:
-      for (int k = 1; k < sc->m; ++k) set_cond(sc, sc->h_step[k], 0);
-      set_cond(sc, sc->h_step[0], sc->converged ? 0u : 1u);
+      if (handles) {
+        for (int k = 1; k < sc->m; ++k) set_cond(sc, sc->h_step[k], 0);
+        set_cond(sc, sc->h_step[0], sc->converged ? 0u : 1u);
+      }
       break;
     case CTL_CYCLE_END: {
       // the unconditional Arnoldi steps a short cycle left also launched (and skipped)
-      if (sc->jend < sc->steps_uncond)
+      if (handles && sc->jend < sc->steps_uncond)
         sc->kcount += (sc->reorth ? 7LL : 5LL) * (sc->steps_uncond - sc->jend);
-      const int cont = (!sc->converged && sc->cycles < sc->max_restarts) ? 1 : 0;
-      set_cond(sc, sc->h_cycle, cont);
-      set_cond(sc, sc->h_restart, cont);
-      if (cont) sc->kcount += 4;  // restart residual: 3 matvec passes + init
+      cont = (!sc->converged && sc->cycles < sc->max_restarts) ? 1 : 0;
+      sc->in_cycle = cont;
+      if (handles) {
+        set_cond(sc, sc->h_cycle, cont);
+        set_cond(sc, sc->h_restart, cont);
+        if (cont) sc->kcount += 4;  // restart residual: 3 matvec passes + init
+      }
       break;
     }
     case CTL_FORCING:
@@ -1575,19 +1641,63 @@ __global__ void k_ctl(int op, DevScalars* sc, int add) {
       break;
     case CTL_GMRES_DONE:
       // Arnoldi steps: 3 matvec passes + dots + update (+ dots + update when reorthogonal.)
-      sc->kcount += (sc->reorth ? 7LL : 5LL) * sc->iters;
+      if (handles) sc->kcount += (sc->reorth ? 7LL : 5LL) * sc->iters;
       sc->gmres_iters_total += sc->iters;
       sc->gmres_cycles_total += sc->cycles;
       break;
   }
+  return cont;
 }
 
-cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add) {
-  k_ctl<<<1, 32, 0, st>>>(op, sc, add);
+__global__ void k_ctl(int op, DevScalars* sc, int add) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ctl_apply(op, sc, add, true);
+}
+
+// The same operation for every pair of a batched solve the mask selects (one thread per
+// pair), then the operation's conditional handle set to "any pair continues".  Kernel
+// launches are counted on pair 0 (the launches are shared by the pairs).
+__global__ void k_ctl_batch(int op, DevScalars* sc, int add, Bat bat) {
+  int cont = 0;
+  const int b = threadIdx.x;
+  if (b < bat.n) {
+    DevScalars* s = reinterpret_cast<DevScalars*>(reinterpret_cast<uintptr_t>(sc) +
+                                                  (size_t)b * bat.slab);
+    if (!bskip(s, bat)) cont = ctl_apply(op, s, b == 0 ? add : 0, false);
+  }
+  const int any = __syncthreads_or(cont);
+  if (threadIdx.x == 0) {
+    switch (op) {
+      case CTL_NEWTON: set_cond(sc, sc->h_newton, any); break;
+      case CTL_ACCEPT: set_cond(sc, sc->h_halve, any); break;
+      case CTL_PRE_CYCLE: set_cond(sc, sc->h_cycle, any); break;
+      case CTL_CYCLE_END:
+        set_cond(sc, sc->h_cycle, any);
+        set_cond(sc, sc->h_restart, any);
+        if (any) sc->kcount += 4;
+        break;
+    }
+  }
+}
+
+cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add, Bat bat) {
+  if (bat.on) {
+    if (bat.n > 1024) return cudaErrorInvalidValue;
+    k_ctl_batch<<<1, (bat.n + 31) / 32 * 32, 0, st>>>(op, sc, add, bat);
+  } else {
+    k_ctl<<<1, 32, 0, st>>>(op, sc, add);
+  }
   return cudaGetLastError();
 }
 
-__global__ void k_sum_sel(UPair up, long P, double* partials, DevScalars* sc, double* mean_out) {
+__global__ void k_sum_sel(UPair up, long P, double* partials, DevScalars* sc, double* mean_out,
+                          Bat bat) {
+  up.a = badv(up.a, bat);
+  up.b = badv(up.b, bat);
+  partials = badv(partials, bat);
+  sc = badv(sc, bat);
+  mean_out = badv(mean_out, bat);
+  if (bskip(sc, bat)) return;
   const double* __restrict__ u = (sc->upar & 1) ? up.b : up.a;
   double v[1] = {0.0};
   const int kind[1] = {0};
@@ -1604,7 +1714,14 @@ __global__ void k_sum_sel(UPair up, long P, double* partials, DevScalars* sc, do
 }
 
 __global__ void k_sub_sel(UPair up, double* __restrict__ out, long P,
-                          const DevScalars* __restrict__ sc, const double* __restrict__ mean) {
+                          const DevScalars* __restrict__ sc, const double* __restrict__ mean,
+                          Bat bat) {
+  up.a = badv(up.a, bat);
+  up.b = badv(up.b, bat);
+  out = badv(out, bat);
+  sc = badv(sc, bat);
+  mean = badv(mean, bat);
+  if (bskip(sc, bat)) return;
   const double* __restrict__ u = (sc->upar & 1) ? up.b : up.a;
   const double m = *mean;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
@@ -1613,10 +1730,43 @@ __global__ void k_sub_sel(UPair up, double* __restrict__ out, long P,
 }
 
 cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
-                               DevScalars* sc, double* mean_out, cudaStream_t st) {
-  const int nb = reduce_blocks();
-  k_sum_sel<<<nb, 256, 0, st>>>(u, (long)N * M, partials, sc, mean_out);
-  k_sub_sel<<<nb, 256, 0, st>>>(u, out, (long)N * M, sc, mean_out);
+                               DevScalars* sc, double* mean_out, cudaStream_t st, Bat bat) {
+  const dim3 nb = bgrid(dim3(reduce_blocks()), bat);
+  k_sum_sel<<<nb, 256, 0, st>>>(u, (long)N * M, partials, sc, mean_out, bat);
+  k_sub_sel<<<nb, 256, 0, st>>>(u, out, (long)N * M, sc, mean_out, bat);
+  return cudaGetLastError();
+}
+
+// batched solve: copies between the pairs' slabs and the caller's per-pair planes
+__global__ void k_gather(const double* const* __restrict__ tab, double* __restrict__ dst, long P,
+                         Bat bat) {
+  const double* __restrict__ src = tab[blockIdx.z];
+  dst = badv(dst, bat);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    dst[p] = src[p];
+}
+
+__global__ void k_scatter(const double* __restrict__ src, double* const* __restrict__ tab,
+                          long P, const DevScalars* __restrict__ sc, Bat bat) {
+  sc = badv(sc, bat);
+  if (bskip(sc, bat)) return;
+  double* __restrict__ dst = tab[blockIdx.z];
+  src = badv(src, bat);
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    dst[p] = src[p];
+}
+
+cudaError_t launch_gather(const double* const* tab, double* dst, long P, Bat bat,
+                          cudaStream_t st) {
+  k_gather<<<bgrid(dim3(reduce_blocks()), bat), 256, 0, st>>>(tab, dst, P, bat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const double* src, double* const* tab, long P, const DevScalars* sc,
+                           Bat bat, cudaStream_t st) {
+  k_scatter<<<bgrid(dim3(reduce_blocks()), bat), 256, 0, st>>>(src, tab, P, sc, bat);
   return cudaGetLastError();
 }
 
@@ -1647,13 +1797,13 @@ cudaError_t launch_convert(const void* in, int in_d, void* out, int out_d, long 
                                           int, double*, T*, double*, DevScalars*,             \
                                           cudaStream_t, const double*, int, const float*, int); \
   template cudaError_t launch_gmres_init<T>(const double*, const T*, T*, long, int, double*,  \
-                                            DevScalars*, int, cudaStream_t, T*);              \
+                                            DevScalars*, int, cudaStream_t, T*, Bat);         \
   template cudaError_t launch_gmres_dots<T>(const T*, const T*, long, double*, DevScalars*,   \
-                                            int, cudaStream_t, int);                          \
+                                            int, cudaStream_t, int, Bat);                     \
   template cudaError_t launch_gmres_update<T>(T*, const T*, long, double*, DevScalars*, int,  \
-                                              cudaStream_t, int);                             \
+                                              cudaStream_t, int, Bat);                        \
   template cudaError_t launch_gmres_combine<T>(const T*, T*, long, const DevScalars*, int,    \
-                                               cudaStream_t);                                 \
+                                               cudaStream_t, Bat);                            \
   template cudaError_t launch_convert<T>(const void*, int, void*, int, long, cudaStream_t);
 
 OTGB_INST_NEWTON(float)

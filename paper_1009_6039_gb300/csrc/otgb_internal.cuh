@@ -69,11 +69,43 @@ struct DevScalars {
   // 1 while the input statistics run without the translation (OT_OPT_TRANSLATE = 0): the
   // inputs must then be positive as given
   int in_plain;
+  // per-pair flags of a batched solve (one DevScalars per pair): the pair's Newton loop
+  // runs, it is in the current GMRES cycle loop, it repeats its candidate (step halving)
+  int active, in_cycle, halve;
+  int excluded;       // the pair sits out this launch of the batched graph (a retry of others)
+  double gauge_mean;  // mean removed by the final gauge of a batched solve
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
 };
 // phases of OT_OPT_PHASE_TIMES
 enum { PH_RESIDUAL = 0, PH_FFT = 1, PH_KRYLOV = 2, PH_UPDATE = 3, PH_OTHER = 4, PH_COUNT = 5 };
+
+// Batched launches (the size classes of a plan set): B pairs of one grid size, each pair's
+// buffers in its own slab of `slab` bytes at equal offsets, so that a pointer into pair b's
+// memory is the pair-0 pointer plus b * slab.  A batched launch has gridDim.z = B (blockIdx.z
+// is the pair); `mask` selects the pairs it serves (the other pairs' blocks return at once).
+// The default (on = 0) is a plain single-problem launch.
+enum { MASK_ALL = 0, MASK_NEWTON = 1, MASK_CYCLE = 2, MASK_HALVE = 3 };
+struct Bat {
+  int on = 0;  // a batched launch (of a plan set's size class, even of one pair)
+  int n = 1;
+  size_t slab = 0;
+  int mask = MASK_ALL;
+};
+template <typename T>
+__device__ __forceinline__ T* badv(T* p, const Bat& b) {
+  return (p && b.on)
+             ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) + (size_t)blockIdx.z * b.slab)
+             : p;
+}
+// the pair of this block does not take part in the launch (sc: this pair's scalars)
+__device__ __forceinline__ bool bskip(const DevScalars* sc, const Bat& b) {
+  if (b.on && sc->excluded) return true;
+  if (b.mask == MASK_ALL) return false;
+  if (!sc->active) return true;
+  return (b.mask == MASK_CYCLE && !sc->in_cycle) || (b.mask == MASK_HALVE && !sc->halve);
+}
+inline dim3 bgrid(dim3 g, const Bat& b) { return dim3(g.x, g.y, b.on ? b.n : 1); }
 
 // Control operations of the device-resident Newton loop (k_ctl)
 enum CtlOp {
@@ -149,19 +181,21 @@ enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2, VAR_E4 = 3 
 
 bool fft_length_supported(int L);
 
+// (bat: a batched launch, the generic kernels only; msc: the pair scalars its mask reads)
 template <typename T>
 cudaError_t launch_row_r2c(const T* x, size_t x_stride, const int* jptr, const double* scale,
                            C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
-                           cudaStream_t st);
+                           cudaStream_t st, Bat bat = Bat(), const DevScalars* msc = nullptr);
 template <typename T>
 cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* out0, C2<T>* out1, C2<T>* out2,
                        int N, int M, const SpecTables& tb, const DevScalars* sc,
-                       const int* skip, cudaStream_t st);
+                       const int* skip, cudaStream_t st, Bat bat = Bat());
 template <typename T>
 cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double out_scale, int N, int M, const SpecTables& tb,
-                           const int* skip, cudaStream_t st, const DevScalars* sc = nullptr);
+                           const int* skip, cudaStream_t st, const DevScalars* sc = nullptr,
+                           Bat bat = Bat());
 
 // register-resident FP32 matvec passes on the transposed half spectrum specT (M/2 x N,
 // entry (k1, k2) at k1 N + k2): mvT_supported(N, M) when N and M/2 are powers of two in
@@ -187,26 +221,27 @@ cudaError_t launch_col_lbarinv_mixed(const float2* spec, double2* out, int N, in
 cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
                                   const SpecTables& tb32, const SpecTables& tbdd,
                                   const DevScalars* sc, cudaStream_t st,
-                                  int mode = COL_LBARINV);
+                                  int mode = COL_LBARINV, Bat bat = Bat());
 // theta rows in double-float and the update u_out = u_in + step theta (FP64 u; u_in may be
 // null: u_out = step theta); with sc, step and the buffer pair come from the device scalars
 // (graph)
 cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
                                      double step, int N, int M, const SpecTables& tbdd,
-                                     const DevScalars* sc, cudaStream_t st);
+                                     const DevScalars* sc, cudaStream_t st, Bat bat = Bat());
 
 // Residual / coefficients, input translation ------------------------------------------
 // c = cubic B-spline coefficients of g (periodic), by recursive filters along y then x
 // (scratch: N x M FP64); cdd (optional) also receives c as (hi, lo) float pairs
 cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
-                             int M, cudaStream_t st);
+                             int M, cudaStream_t st, Bat bat = Bat());
 cudaError_t launch_translate_inputs(const double* f, const double* g, double* ft, double* gt,
                                     int N, int M, double* partials, DevScalars* sc,
-                                    cudaStream_t st);
+                                    cudaStream_t st, Bat bat = Bat());
 // the statistics of f and g alone (means, minima, non-finite counts) for inputs used as given
 // (sc->in_plain must be 1: then in_bad flags a non-positive or non-finite value)
 cudaError_t launch_input_stats(const double* f, const double* g, int N, int M,
-                               double* partials, DevScalars* sc, cudaStream_t st);
+                               double* partials, DevScalars* sc, cudaStream_t st,
+                               Bat bat = Bat());
 // phase stamp (OT_OPT_PHASE_TIMES): cls opens a phase, -1 closes the last one
 cudaError_t launch_stamp(DevScalars* sc, int cls, cudaStream_t st);
 // u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate);
@@ -221,20 +256,29 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
                                DevScalars* sc, cudaStream_t st, const double* ub = nullptr,
-                               int sel = 0, int simplified = 0);
+                               int sel = 0, int simplified = 0, Bat bat = Bat());
 // out[k] = (hi, lo) float pair of in[k]
-cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st);
+cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st,
+                            Bat bat = Bat());
 cudaError_t launch_residual_l2(const double* Fraw, int N, int M, double* partials,
-                               DevScalars* sc, cudaStream_t st);
+                               DevScalars* sc, cudaStream_t st, Bat bat = Bat());
 cudaError_t launch_shifted_residual(const double* Fraw, double* F, int N, int M,
                                     const DevScalars* sc, cudaStream_t st);
 cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevScalars* sc,
                                  double* mean_out, cudaStream_t st);
 // out = u[upar] - mean(u[upar])
 cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
-                               DevScalars* sc, double* mean_out, cudaStream_t st);
-// `add`: kernels of the graph segment this control op closes (launch accounting)
-cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add = 0);
+                               DevScalars* sc, double* mean_out, cudaStream_t st,
+                               Bat bat = Bat());
+// batched solve: dst (pair 0's plane, advanced by the slab per pair) <- tab[pair]; and the
+// reverse (tab[pair] <- src of pair), skipping excluded pairs (sc: pair 0's scalars)
+cudaError_t launch_gather(const double* const* tab, double* dst, long P, Bat bat,
+                          cudaStream_t st);
+cudaError_t launch_scatter(const double* src, double* const* tab, long P, const DevScalars* sc,
+                           Bat bat, cudaStream_t st);
+// `add`: kernels of the graph segment this control op closes (launch accounting); batched:
+// one thread per pair, the handle set to "any pair continues" (at most 1024 pairs)
+cudaError_t launch_ctl(int op, DevScalars* sc, cudaStream_t st, int add = 0, Bat bat = Bat());
 int residual_partial_blocks(int N, int M);
 
 // Krylov kernels -------------------------------------------------------------------------
@@ -242,20 +286,20 @@ int residual_partial_blocks(int N, int M);
 template <typename T>
 cudaError_t launch_gmres_init(const double* Fraw, const T* w, T* V0, long P, int restart,
                               double* partials, DevScalars* sc, int nblocks, cudaStream_t st,
-                              T* sigma = nullptr);
+                              T* sigma = nullptr, Bat bat = Bat());
 // pass 0: H[:, j] = V^T w; pass 1 (reorthogonalisation): h2 = V^T V_{j+1}, H[:, j] += h2
 template <typename T>
 cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, DevScalars* sc,
-                              int nblocks, cudaStream_t st, int pass = 0);
+                              int nblocks, cudaStream_t st, int pass = 0, Bat bat = Bat());
 // mode 0: V_{j+1} = w - V H[:, j], norm + Givens; mode 1: the same without norm (first of
 // two passes); mode 2: V_{j+1} -= V h2 in place, norm + Givens
 template <typename T>
 cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
-                                int nblocks, cudaStream_t st, int mode = 0);
-cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st);
+                                int nblocks, cudaStream_t st, int mode = 0, Bat bat = Bat());
+cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st, Bat bat = Bat());
 template <typename T>
 cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,
-                                 int nblocks, cudaStream_t st);
+                                 int nblocks, cudaStream_t st, Bat bat = Bat());
 template <typename T>
 cudaError_t launch_convert(const void* in, int in_is_double, void* out, int out_is_double,
                            long n, cudaStream_t st);

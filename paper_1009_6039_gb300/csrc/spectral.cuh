@@ -512,8 +512,14 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __res
                           const int* __restrict__ jptr, const double* __restrict__ scale,
                           C2<T>* __restrict__ spec, int N, int M,
                           const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
-                          const int* __restrict__ skip) {
-  if (skip && *skip) return;
+                          const int* __restrict__ skip, Bat bat, const DevScalars* msc) {
+  xbase = badv(xbase, bat);
+  jptr = badv(jptr, bat);
+  scale = badv(scale, bat);
+  spec = badv(spec, bat);
+  skip = badv(skip, bat);
+  msc = badv(msc, bat);
+  if ((skip && *skip) || (msc && bskip(msc, bat))) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
   const int L = M / 2;
@@ -601,8 +607,14 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
                       double inv_nm,
                       const C2<T>* __restrict__ twN, const C2<T>* __restrict__ twM,
                       const DevScalars* __restrict__ sc, const int* __restrict__ skip,
-                      const C2<T>* __restrict__ symx, const C2<T>* __restrict__ symy) {
-  if (skip && *skip) return;
+                      const C2<T>* __restrict__ symx, const C2<T>* __restrict__ symy, Bat bat) {
+  spec = badv(spec, bat);
+  out0 = badv(out0, bat);
+  out1 = badv(out1, bat);
+  out2 = badv(out2, bat);
+  sc = badv(sc, bat);
+  skip = badv(skip, bat);
+  if ((skip && *skip) || (sc && bskip(sc, bat))) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* sm = reinterpret_cast<C2<T>*>(smem_raw);
   const int Lc = M / 2;
@@ -779,8 +791,17 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
                           double* __restrict__ u_out, double step, double out_scale, int N,
                           int M, const C2<T>* __restrict__ twL, const C2<T>* __restrict__ twM,
                           const int* __restrict__ skip, const DevScalars* __restrict__ sc,
-                          const C2<T>* __restrict__ symx) {
-  if (skip && *skip) return;
+                          const C2<T>* __restrict__ symx, Bat bat) {
+  q0 = badv(q0, bat);
+  q1 = badv(q1, bat);
+  q2 = badv(q2, bat);
+  coef = badv(coef, bat);
+  out = badv(out, bat);
+  u_in = badv(u_in, bat);
+  u_out = badv(u_out, bat);
+  skip = badv(skip, bat);
+  sc = badv(sc, bat);
+  if ((skip && *skip) || (sc && bskip(sc, bat))) return;
   if (MODE == ROWINV_UPDATE && sc) {
     // device-resident control: step s and the current/candidate buffers come from sc
     step = sc->step_s;
@@ -1136,7 +1157,11 @@ __global__ void __launch_bounds__(256)
                      int Q, double inv_nm, const float2* __restrict__ twN32,
                      const float2* __restrict__ twM32, const ddc* __restrict__ twNdd,
                      const DevScalars* __restrict__ sc, const float2* __restrict__ symx,
-                     const float2* __restrict__ symy) {
+                     const float2* __restrict__ symy, Bat bat) {
+  spec = badv(spec, bat);
+  out = badv(out, bat);
+  sc = badv(sc, bat);
+  if (sc && bskip(sc, bat)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ddc* sm = reinterpret_cast<ddc*>(smem_raw);
   const int Lc = M / 2, TPT = N / E;
@@ -1215,7 +1240,12 @@ __global__ void __launch_bounds__(256)
     k_row_c2r_update_dd(const ddc* __restrict__ q, const double* __restrict__ u_in,
                         double* __restrict__ u_out, double step, int N, int M,
                         const ddc* __restrict__ twL, const ddc* __restrict__ twM,
-                        const DevScalars* __restrict__ sc) {
+                        const DevScalars* __restrict__ sc, Bat bat) {
+  q = badv(q, bat);
+  u_in = badv(u_in, bat);
+  u_out = badv(u_out, bat);
+  sc = badv(sc, bat);
+  if (sc && bskip(sc, bat)) return;
   if (sc) {
     step = sc->step_s;
     if (sc->upar & 1) {
@@ -1531,7 +1561,8 @@ inline cudaError_t prepare_launch(K kernel, long threads, size_t bytes) {
 
 template <typename T, int E>
 cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scale, C2<T>* spec,
-                      int N, int M, const SpecTables& tb, const int* skip, cudaStream_t st) {
+                      int N, int M, const SpecTables& tb, const int* skip, cudaStream_t st,
+                      Bat bat = Bat(), const DevScalars* msc = nullptr) {
   const int L = M / 2, TPT = L / E;
   int RB = MaxThreads<T>::value / TPT;
   if (RB < 1) RB = 1;
@@ -1540,15 +1571,16 @@ cudaError_t row_r2c_E(const T* x, size_t xs, const int* jptr, const double* scal
   const size_t sm = (size_t)RB * FB(L) * sizeof(C2<T>);
   cudaError_t e = prepare_launch(k_row_r2c<T, E>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
-  k_row_r2c<T, E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
-      x, xs, jptr, scale, spec, N, M, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip);
+  k_row_r2c<T, E><<<bgrid(dim3((N + RB - 1) / RB), bat), RB * TPT, sm, st>>>(
+      x, xs, jptr, scale, spec, N, M, (const C2<T>*)tb.twL, (const C2<T>*)tb.twM, skip, bat,
+      msc);
   return cudaGetLastError();
 }
 
 template <typename T, int E, int MODE>
 cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int M,
                   const SpecTables& tb, const DevScalars* sc, const int* skip,
-                  cudaStream_t st) {
+                  cudaStream_t st, Bat bat = Bat()) {
   const int Lc = M / 2, TPT = N / E;
   const size_t colb = (size_t)col_nbuf<T, E, MODE>() * FB(N) * sizeof(C2<T>);
   int Q = MaxThreads<T>::value / TPT;
@@ -1564,9 +1596,9 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
   const size_t sm = (size_t)Q * colb;
   cudaError_t e = prepare_launch(k_col<T, E, MODE>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
-  k_col<T, E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+  k_col<T, E, MODE><<<bgrid(dim3((Lc + Q - 1) / Q), bat), Q * TPT, sm, st>>>(
       spec, o0, o1, o2, N, M, Q, 1.0 / ((double)N * (double)M), (const C2<T>*)tb.twN,
-      (const C2<T>*)tb.twM, sc, skip, (const C2<T>*)tb.symx, (const C2<T>*)tb.symy);
+      (const C2<T>*)tb.twM, sc, skip, (const C2<T>*)tb.symx, (const C2<T>*)tb.symy, bat);
   return cudaGetLastError();
 }
 
@@ -1574,7 +1606,7 @@ template <typename T, int E, int MODE>
 cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T* coef, T* out,
                       const double* u_in, double* u_out, double step, double out_scale, int N,
                       int M, const SpecTables& tb, const int* skip, cudaStream_t st,
-                      const DevScalars* sc) {
+                      const DevScalars* sc, Bat bat = Bat()) {
   const int L = M / 2, TPT = L / E;
   const size_t rowb = (size_t)row_nbuf<T, E, MODE>() * FB(L) * sizeof(C2<T>);
   int RB = MaxThreads<T>::value / TPT;
@@ -1585,9 +1617,9 @@ cudaError_t row_c2r_E(const C2<T>* q0, const C2<T>* q1, const C2<T>* q2, const T
   const size_t sm = (size_t)RB * rowb;
   cudaError_t e = prepare_launch(k_row_c2r<T, E, MODE>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
-  k_row_c2r<T, E, MODE><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
+  k_row_c2r<T, E, MODE><<<bgrid(dim3((N + RB - 1) / RB), bat), RB * TPT, sm, st>>>(
       q0, q1, q2, coef, out, u_in, u_out, step, out_scale, N, M, (const C2<T>*)tb.twL,
-      (const C2<T>*)tb.twM, skip, sc, (const C2<T>*)tb.symx);
+      (const C2<T>*)tb.twM, skip, sc, (const C2<T>*)tb.symx, bat);
   return cudaGetLastError();
 }
 
@@ -1610,7 +1642,12 @@ cudaError_t row_r2c_w_launch(const T* x, size_t xs, const int* jptr, const doubl
 template <typename T>
 cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double* scale,
                            C2<T>* spec, int N, int M, const SpecTables& tb, const int* skip,
-                           cudaStream_t st) {
+                           cudaStream_t st, Bat bat, const DevScalars* msc) {
+  if (bat.on) {  // batched: the generic kernels
+    if (fft_E(M / 2) == 12)
+      return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st, bat, msc);
+    return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st, bat, msc);
+  }
   if (sizeof(T) == 4 && tb.var_r2c == VAR_WARP && warp_fft_ok(M / 2))
     return row_r2c_w_launch<T>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   if (sizeof(T) == 4 && tb.var_r2c == VAR_E4 && fft_E(M / 2) == 8 && M / 2 >= 4)
@@ -1680,7 +1717,13 @@ cudaError_t col_dispatch(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T
 template <typename T>
 cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N,
                        int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
-                       cudaStream_t st) {
+                       cudaStream_t st, Bat bat) {
+  if (bat.on) {  // batched: the generic kernels (the matvec mode only)
+    if (mode != COL_MATVEC) return cudaErrorInvalidValue;
+    if (fft_E(N) == 12)
+      return col_E<T, 12, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st, bat);
+    return col_E<T, 8, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st, bat);
+  }
   if (sizeof(T) == 4 && mode == COL_MATVEC && tb.var_col == VAR_E4 && fft_E(N) == 8 && N >= 4)
     return col_E<T, 4, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   if (fft_E(N) == 12) return col_dispatch<T, 12>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
@@ -1750,7 +1793,15 @@ template <typename T>
 cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<T>* q2,
                            const T* coef, T* out, const double* u_in, double* u_out,
                            double step, double os, int N, int M, const SpecTables& tb,
-                           const int* skip, cudaStream_t st, const DevScalars* sc) {
+                           const int* skip, cudaStream_t st, const DevScalars* sc, Bat bat) {
+  if (bat.on) {  // batched: the generic kernels (the combine mode only)
+    if (mode != ROWINV_COMBINE) return cudaErrorInvalidValue;
+    if (fft_E(M / 2) == 12)
+      return row_c2r_E<T, 12, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N,
+                                              M, tb, skip, st, sc, bat);
+    return row_c2r_E<T, 8, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
+                                           tb, skip, st, sc, bat);
+  }
   if (sizeof(T) == 4 && mode == ROWINV_COMBINE && tb.var_comb == VAR_E4 && fft_E(M / 2) == 8 &&
       M / 2 >= 4)
     return row_c2r_E<T, 4, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
@@ -1783,7 +1834,7 @@ cudaError_t col_lbarinv_mixed_E(const float2* spec, double2* out, int N, int M,
 template <int E, int MODE>
 cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
                              const SpecTables& tb32, const SpecTables& tbdd,
-                             const DevScalars* sc, cudaStream_t st) {
+                             const DevScalars* sc, cudaStream_t st, Bat bat = Bat()) {
   const int Lc = M / 2, TPT = N / E;
   int Q = 256 / TPT;
   if (Q < 1) Q = 1;
@@ -1793,17 +1844,17 @@ cudaError_t col_lbarinv_dd_E(const float2* spec, ddc* out, int N, int M,
   const size_t sm = (size_t)Q * FB(N) * sizeof(ddc);
   cudaError_t e = prepare_launch(k_col_lbarinv_dd<E, MODE>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
-  k_col_lbarinv_dd<E, MODE><<<(Lc + Q - 1) / Q, Q * TPT, sm, st>>>(
+  k_col_lbarinv_dd<E, MODE><<<bgrid(dim3((Lc + Q - 1) / Q), bat), Q * TPT, sm, st>>>(
       spec, out, N, M, Q, 1.0 / ((double)N * (double)M), (const float2*)tb32.twN,
       (const float2*)tb32.twM, (const ddc*)tbdd.twN, sc, (const float2*)tb32.symx,
-      (const float2*)tb32.symy);
+      (const float2*)tb32.symy, bat);
   return cudaGetLastError();
 }
 
 template <int E>
 cudaError_t row_c2r_update_dd_E(const ddc* q, const double* u_in, double* u_out, double step,
                                 int N, int M, const SpecTables& tbdd, const DevScalars* sc,
-                                cudaStream_t st) {
+                                cudaStream_t st, Bat bat = Bat()) {
   const int L = M / 2, TPT = L / E;
   int RB = 256 / TPT;
   if (RB < 1) RB = 1;
@@ -1812,21 +1863,21 @@ cudaError_t row_c2r_update_dd_E(const ddc* q, const double* u_in, double* u_out,
   const size_t sm = (size_t)RB * FB(L) * sizeof(ddc);
   cudaError_t e = prepare_launch(k_row_c2r_update_dd<E>, RB * TPT, sm);
   if (e != cudaSuccess) return e;
-  k_row_c2r_update_dd<E><<<(N + RB - 1) / RB, RB * TPT, sm, st>>>(
-      q, u_in, u_out, step, N, M, (const ddc*)tbdd.twL, (const ddc*)tbdd.twM, sc);
+  k_row_c2r_update_dd<E><<<bgrid(dim3((N + RB - 1) / RB), bat), RB * TPT, sm, st>>>(
+      q, u_in, u_out, step, N, M, (const ddc*)tbdd.twL, (const ddc*)tbdd.twM, sc, bat);
   return cudaGetLastError();
 }
 
 #define OTGB_INSTANTIATE_SPECTRAL(T)                                                         \
   template cudaError_t launch_row_r2c<T>(const T*, size_t, const int*, const double*,        \
                                          C2<T>*, int, int, const SpecTables&, const int*,    \
-                                         cudaStream_t);                                      \
+                                         cudaStream_t, Bat, const DevScalars*);              \
   template cudaError_t launch_col<T>(int, const C2<T>*, C2<T>*, C2<T>*, C2<T>*, int, int,    \
                                      const SpecTables&, const DevScalars*, const int*,       \
-                                     cudaStream_t);                                          \
+                                     cudaStream_t, Bat);                                     \
   template cudaError_t launch_row_c2r<T>(int, const C2<T>*, const C2<T>*, const C2<T>*,      \
                                          const T*, T*, const double*, double*, double,       \
                                          double, int, int, const SpecTables&, const int*,    \
-                                         cudaStream_t, const DevScalars*);
+                                         cudaStream_t, const DevScalars*, Bat);
 
 }  // namespace otgb

@@ -416,7 +416,7 @@ def test_batched_uneven_sizes(ot):
         gs.append(dev(g))
         phis.append(dev(np.zeros((N, M))))
     stats = (ot.ot_stats * len(sizes))()
-    rc = ot.ot_solve_batched(len(sizes), [p.h for p in plans], [t.data_ptr() for t in fs],
+    rc = ot.ot_solve_plans(len(sizes), [p.h for p in plans], [t.data_ptr() for t in fs],
                              [t.data_ptr() for t in gs], [t.data_ptr() for t in phis],
                              stats)
     assert rc == 0
