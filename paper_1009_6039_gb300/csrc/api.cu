@@ -2039,7 +2039,7 @@ extern "C" int ot_eval_residual(ot_plan* p, const double* f, const double* c, co
 
 static int upload_abar(ot_plan* p, const double* abar) {
   set_solver_scalars(p);
-  for (int a = 0; a < 5; ++a) p->hsc->abar[a] = abar[a];
+  for (int a = 0; a < 5; ++a) p->hsc->abar[a] = p->hsc->abar_n[a] = abar[a];
   CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
   return OT_OK;
 }

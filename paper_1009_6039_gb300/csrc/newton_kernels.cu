@@ -1118,6 +1118,8 @@ __global__ void k_gmres_init(const double* __restrict__ Fraw, const T* __restric
   if (threadIdx.x == 0) {
     const double beta = sqrt(v[0]);
     if (!restart) {
+      // a new Newton step: the last residual evaluated was the current iterate's
+      for (int a = 0; a < 5; ++a) sc->abar_n[a] = sc->abar[a];
       sc->bnorm = beta;
       sc->iters = 0;
       sc->cycles = 0;

@@ -29,6 +29,10 @@ struct DevScalars {
   int in_bad;
   // residual / coefficient evaluation
   double mean_fn, shift, res_inf, min_det, abar[5];
+  // the averaged coefficients of the current Newton iterate (Sec. 4.2), kept for theta =
+  // Lbar^{-1} sigma: the residual at a candidate iterate writes abar, and a rejected
+  // candidate must not change the operator of the step being halved
+  double abar_n[5];
   double res_l2sum;
   int k1_nonfinite;
   int admissible;

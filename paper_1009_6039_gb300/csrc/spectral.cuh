@@ -641,7 +641,8 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
   }
   T ab[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) ab[a] = sc ? (T)sc->abar[a] : (T)0;
+  for (int a = 0; a < 5; ++a)
+    ab[a] = sc ? (T)(MODE == COL_LBARINV ? sc->abar_n[a] : sc->abar[a]) : (T)0;
   const T inv = (T)inv_nm;
   C2<T> s[E], s0[E];
   if (active) {
@@ -1113,7 +1114,7 @@ __global__ void __launch_bounds__(256)
   fft_smem<float, E, -1>(fb, N, t, active, twN32);
   float ab[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar[a];
+  for (int a = 0; a < 5; ++a) ab[a] = (float)sc->abar_n[a];
   const float inv = (float)inv_nm;
   double2 s[E];
   if (active) {
@@ -1180,7 +1181,7 @@ __global__ void __launch_bounds__(256)
   fft_smem<float, E, -1>(fb, N, t, active, twN32);
   float ab[5];
 #pragma unroll
-  for (int a = 0; a < 5; ++a) ab[a] = MODE == COL_LBARINV ? (float)sc->abar[a] : 0.f;
+  for (int a = 0; a < 5; ++a) ab[a] = MODE == COL_LBARINV ? (float)sc->abar_n[a] : 0.f;
   const float inv = (float)inv_nm;
   float2 s[E];
   if (active) {
