@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--size", type=int, default=N_GRID)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-workload key of the single-pair line")
     ap.add_argument("--kernels-only", action="store_true",
                     help="warm-up and timed solves only (profiling target)")
     ap.add_argument("--workload", default="single", choices=["single", "batch"],
@@ -791,6 +793,12 @@ def run_ours(args):
                                    "ms_total_host_driven": st_p["ms_total"]},
                 "kernels": kernels,
                 "clocks": clk.summary()}
+        if not args.no_batch:
+            # the batched workload (one plan set, one graph launch per step), a few steps
+            import copy
+            bargs = copy.copy(args)
+            bargs.steps, bargs.warmup = 3, 1
+            line["batched_workload"] = run_batch(bargs)
         if cpu_jobs is not None:
             line["cpu_baseline"] = cpu_baseline_finish(*cpu_jobs, N)
         print(json.dumps(line), flush=True)

@@ -53,7 +53,7 @@ def solve_set(ot, pairs, **kw):
     fs = [dev(f) for f, _ in pairs]
     gs = [dev(g) for _, g in pairs]
     phis = [torch.zeros_like(t) for t in fs]
-    rc, st = ps.solve(fs, gs, phis)
+    rc, st = ps.solve(fs, gs, phis, raise_on=())
     ps.close()
     return rc, st, [p.cpu().numpy() for p in phis]
 
