@@ -793,7 +793,7 @@ def run_ours(args):
                                    "ms_total_host_driven": st_p["ms_total"]},
                 "kernels": kernels,
                 "clocks": clk.summary()}
-        if not args.no_batch:
+        if not args.no_batch and world == 1:
             # the batched workload (one plan set, one graph launch per step), a few steps
             import copy
             bargs = copy.copy(args)
