@@ -120,6 +120,10 @@ extern "C" {
 #define OT_OPT_TRANSPORT 23     /* 1: the solve ends with the transport distance d(f, g) of
                                    Sec. 5.2 (as ot_transport_outputs, on the translated f) in
                                    ot_stats.transport_dist; 0 (default): it is -1 */
+#define OT_OPT_TAU_SWITCH 24    /* tau schedule: 0 (default) off; s > 0: once max|F| < s the
+                                   damping is 1 for the rest of the solve (a larger tau for
+                                   the start, tau = 1 near convergence; the remarks of Sec. 3.3
+                                   and the tau study of Sec. 5.1) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,
@@ -320,6 +324,20 @@ int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
  * round-off 2^-48).  OT_EINVAL for null f, phi or dist or an unready plan. */
 int ot_transport_outputs(ot_plan* plan, const double* f, const double* phi, double* dist,
                          double* div_out);
+
+/* Spectral radius of the inverse of the discretised linearised operator at the iterate phi
+ * (the stability measure of Sec. 5.1, about 0.03 in the paper's experiments), by the power
+ * iteration the paper uses: b_(k+1) = A^{-1} b_k / ||A^{-1} b_k||_2 with A^{-1} b = Lbar^{-1}
+ * sigma, sigma from GMRES(m) on L Lbar^{-1} sigma = b at the plan's eta, m and symbols (the
+ * Fourier method of Sec. 4.2), L = D_phi M of Eq. (linearmaeq) for the densities f, g
+ * (translated as by the solve when OT_OPT_TRANSLATE is set).  b0: device N x M start vector
+ * (projected to mean zero: the operator acts on mean-zero potentials, Sec. 3.1); rho (HOST,
+ * iters doubles) receives ||A^{-1} b_k||_2 for the unit vectors b_k, k = 0..iters-1, whose
+ * last entries approximate the spectral radius.  Uses the plan's workspace (the plan's next
+ * solve starts afresh).  OT_EINVAL for null pointers, iters < 1 or invalid densities. */
+int ot_inverse_spectral_radius(ot_plan* plan, const double* f, const double* g,
+                               const double* phi, const double* b0, int32_t iters,
+                               double* rho);
 
 /* ---- Learned warm start -----------------------------------------------------------------
  * Not in the paper, which starts Newton from u0 = 0 and needs only an admissible start,

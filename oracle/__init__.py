@@ -27,7 +27,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tol", ctypes.c_double), ("eta", ctypes.c_double),
                 ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("max_newton", ctypes.c_int), ("translate_inputs", ctypes.c_int),
-                ("safeguard", ctypes.c_int)]
+                ("safeguard", ctypes.c_int), ("tau_switch", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -212,7 +212,7 @@ def gmres_op(coef, abar, h, m=10, eta=1e-4, max_restarts=50):
 
 
 def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_newton=200,
-          u0=None, translate_inputs=True, safeguard=True):
+          u0=None, translate_inputs=True, safeguard=True, tau_switch=0.0):
     """Damped Newton solve.  Returns (u, stats dict, res history, gmres history)."""
     f, g = _f64(f), _f64(g)
     N, M = f.shape
@@ -221,6 +221,7 @@ def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_n
     o.tau, o.tol, o.eta, o.restart = tau, tol, eta, restart
     o.max_restarts, o.max_newton = max_restarts, max_newton
     o.translate_inputs, o.safeguard = int(translate_inputs), int(safeguard)
+    o.tau_switch = float(tau_switch)
     u = np.zeros((N, M)) if u0 is None else _f64(u0).copy()
     st = Stats()
     hres = np.zeros(max_newton + 1)
@@ -230,6 +231,32 @@ def solve(f, g, tau=2.0, tol=1e-10, eta=1e-4, restart=10, max_restarts=50, max_n
     d = {k: getattr(st, k) for k, _ in Stats._fields_}
     n = d["newton_iters"]
     return u, d, hres[:n + 1].copy(), hgm[:n].copy()
+
+
+def inverse_spectral_radius(f, g, u, b0, iters=5, eta=1e-4, restart=10, max_restarts=50,
+                            translate_inputs=True):
+    """Sec. 5.1: power iteration on the inverse of the discretised linearised operator at the
+    iterate u, b_(k+1) = A^{-1} b_k / ||A^{-1} b_k||_2, where A^{-1} b = Lbar^{-1} sigma and
+    sigma solves L Lbar^{-1} sigma = b by GMRES(m) (the Fourier method of Sec. 4.2, with the
+    symbols the fd_symbols switch selects).  b0 is projected to mean zero (the operator acts on
+    mean-zero potentials, Sec. 3.1).  Returns the norms ||A^{-1} b_k|| of the unit b_k."""
+    f, g, u = _f64(f), _f64(g), _f64(u)
+    if translate_inputs:
+        f = f - f.mean() + 1.0
+        g = g - g.mean() + 1.0
+    c = bspline_coeffs(g)
+    _, coef, _ = residual(f, c, u)
+    abar = np.array([simpson_mean(coef[q]) for q in range(5)])
+    b = _f64(b0) - np.mean(b0)
+    b = b / np.linalg.norm(b)
+    rho = []
+    for _ in range(iters):
+        sigma, _ = gmres_op(coef, abar, b, m=restart, eta=eta, max_restarts=max_restarts)
+        th = apply_lbar_inv(abar, sigma)
+        r = float(np.linalg.norm(th))
+        rho.append(r)
+        b = th / r
+    return np.array(rho)
 
 
 def fd_poisson(src, lowpass=False):

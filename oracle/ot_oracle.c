@@ -832,6 +832,7 @@ void orc_default_opts(orc_opts *o) {
   o->max_newton = 200;
   o->translate_inputs = 1;
   o->safeguard = 1;
+  o->tau_switch = 0.0;
 }
 
 /* Convexity of the iterate: the proof of convergence keeps I + D^2 u_n positive definite
@@ -884,6 +885,7 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
   orc_bspline_coeffs(g, N, M, c);
   double scal[5];
   orc_residual(f, c, u, N, M, F, coef, scal);
+  double tau = o->tau;
   for (int n = 0;; ++n) {
     st->mean_fn = scal[0];
     st->res_inf = scal[1];
@@ -899,9 +901,10 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
       status = ORC_ENOCONV;
       break;
     }
+    if (o->tau_switch > 0.0 && scal[1] < o->tau_switch) tau = 1.0; /* kept from here on */
     double abar[5];
     for (int q = 0; q < 5; ++q) abar[q] = orc_simpson_mean(coef + q * P, N, M);
-    for (long p = 0; p < P; ++p) h[p] = F[p] / o->tau;
+    for (long p = 0; p < P; ++p) h[p] = F[p] / tau;
     int it, cy;
     double rr;
     orc_gmres_op(coef, abar, h, N, M, o->restart, o->eta, o->max_restarts, sigma, &it, &cy,

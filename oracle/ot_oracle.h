@@ -21,6 +21,9 @@ typedef struct {
   int max_newton;      /* Newton step cap */
   int translate_inputs;/* apply Eq. (translation) to f and g on entry */
   int safeguard;       /* halve a step that loses convexity (larger effective tau) */
+  double tau_switch;   /* tau schedule (0 = off): once max|F| < tau_switch the damping is 1
+                          for the rest of the solve (a larger tau for the start, tau = 1 near
+                          convergence: the remarks of Sec. 3.3 and the tau study of Sec. 5.1) */
 } orc_opts;
 
 typedef struct {

@@ -23,7 +23,7 @@ OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
 OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
-OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT = 22, 23
+OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH = 22, 23, 24
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -38,7 +38,8 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_pla
            "ot_ws_poisson", "ot_transport_outputs", "ot_ws_trainer_create", "ot_ws_trainer_set_stream",
            "ot_ws_trainer_grad", "ot_ws_trainer_step", "ot_ws_trainer_get_params",
            "ot_ws_trainer_destroy", "ot_solve_plans", "ot_plan_set_create",
-           "ot_batch_set_option", "ot_batch_set_stream", "ot_plan_set_destroy"]
+           "ot_batch_set_option", "ot_batch_set_stream", "ot_plan_set_destroy",
+           "ot_inverse_spectral_radius"]
 
 
 class ot_stats(ctypes.Structure):
@@ -84,6 +85,7 @@ def _load():
         "ot_batch_set_option": ([vp, i32, d], ctypes.c_int),
         "ot_batch_set_stream": ([vp, vp], ctypes.c_int),
         "ot_plan_set_destroy": ([vp], None),
+        "ot_inverse_spectral_radius": ([vp, vp, vp, vp, vp, i32, vp], ctypes.c_int),
         "ot_plan_destroy": ([vp], None),
         "ot_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "ot_prefilter": ([vp, vp, vp], ctypes.c_int),
@@ -187,6 +189,11 @@ def ot_solve_batched(pset, count, N, M, f_ptrs, g_ptrs, phi_ptrs, stats=None):
 
 def ot_plan_set_destroy(pset):
     _lib.ot_plan_set_destroy(pset)
+
+
+def ot_inverse_spectral_radius(plan, f_ptr, g_ptr, phi_ptr, b0_ptr, iters, rho_host_ptr):
+    return _lib.ot_inverse_spectral_radius(plan, f_ptr, g_ptr, phi_ptr, b0_ptr, int(iters),
+                                           rho_host_ptr)
 
 
 def ot_plan_destroy(plan):
@@ -403,7 +410,8 @@ class Plan:
              "fft_variant": OT_OPT_FFT_VARIANT, "symbols": OT_OPT_SYMBOLS,
              "forcing": OT_OPT_FORCING, "tau_retry": OT_OPT_TAU_RETRY,
              "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR,
-             "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT}
+             "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT,
+             "tau_switch": OT_OPT_TAU_SWITCH}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)
@@ -505,6 +513,18 @@ class Plan:
     def ws_poisson(self, src, u, lowpass=False):
         shp = (self.N, self.M)
         _check(ot_ws_poisson(self.h, _dev(src, shp), lowpass, _dev(u, shp)), "ot_ws_poisson")
+
+    def inverse_spectral_radius(self, f, g, phi, b0, iters=5):
+        """Power iteration on the inverse of the linearised operator at phi (Sec. 5.1):
+        the norms ||A^{-1} b_k|| (numpy array of iters values)."""
+        import numpy as np
+        shp = (self.N, self.M)
+        rho = np.zeros(int(iters))
+        _check(ot_inverse_spectral_radius(self.h, _dev(f, shp), _dev(g, shp), _dev(phi, shp),
+                                          _dev(b0, shp), iters,
+                                          ctypes.c_void_p(rho.ctypes.data)),
+               "ot_inverse_spectral_radius")
+        return rho
 
     def transport_outputs(self, f, phi, div=None):
         """d(f, g) = mean |grad phi|^2 f (Sec. 5.2); fills div (device N x M) with

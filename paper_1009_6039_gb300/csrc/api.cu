@@ -47,6 +47,7 @@ struct ot_plan {
   int symbols = 0;  // OT_OPT_SYMBOLS: 0 spectral (Sec. 4.2), 1 the stencils' symbols
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
   int tau_retry = 0;  // OT_OPT_TAU_RETRY: re-solves with doubled tau after a divergence
+  double tau_switch = 0.0;  // OT_OPT_TAU_SWITCH: tau schedule (tau -> 1 below this max|F|)
   int op_simple = 0;  // OT_OPT_OPERATOR: 1 drops the grad g term of the linearisation
   int ws_stall = 0;   // OT_OPT_WS_TEST_STALL: the next ot_ws_mlp_forward stalls (test hook)
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
@@ -744,6 +745,10 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
         if (p->ready) RET(fill_symbols(p));
       }
       return OT_OK;
+    case OT_OPT_TAU_SWITCH:
+      if (!(v >= 0.0)) return OT_EINVAL;
+      p->tau_switch = v;
+      return OT_OK;
     case OT_OPT_PHASE_TIMES:
       if (v != 0 && v != 1) return OT_EINVAL;
       if (p->phase_times != (int)v) {
@@ -796,6 +801,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_WS_TEST_STALL: *v = p->ws_stall; return OT_OK;
     case OT_OPT_OPERATOR: *v = p->op_simple; return OT_OK;
     case OT_OPT_PHASE_TIMES: *v = p->phase_times; return OT_OK;
+    case OT_OPT_TAU_SWITCH: *v = p->tau_switch; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -1141,6 +1147,7 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->res_prev = 0.0;
   p->hsc->forcing = p->forcing;
   p->hsc->stamp_cls = -1;
+  p->hsc->tau_switch = p->tau_switch;
   p->hsc->in_plain = p->translate ? 0 : 1;
 }
 
@@ -1313,6 +1320,7 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
   RET(read_scalars(p));
   int status = OT_OK;
   double s = 1.0;
+  bool tau_one = false;
   for (int n = 0;; ++n) {
     const DevScalars* h = p->hsc;
     st->res_inf = h->res_inf;
@@ -1326,6 +1334,13 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
     if (n >= p->max_newton) {
       status = OT_ENOCONV;
       break;
+    }
+    if (p->tau_switch > 0.0 && h->res_inf < p->tau_switch && !tau_one) {
+      // tau schedule: the damping of the remaining steps is 1
+      static const double one = 1.0;
+      CK(cudaMemcpyAsync(&p->sc->tau, &one, sizeof(double), cudaMemcpyHostToDevice,
+                         p->stream));
+      tau_one = true;
     }
     int rc = run_gmres<T>(p);
     if (rc != OT_OK) return rc;
@@ -2508,6 +2523,9 @@ extern "C" int ot_batch_set_option(ot_plan_set* s, int32_t key, double v) {
     case OT_OPT_MAX_RESTARTS:
       if (v < (key == OT_OPT_MAX_NEWTON ? 0 : 1) || v != (double)(int)v) return OT_EINVAL;
       break;
+    case OT_OPT_TAU_SWITCH:
+      if (!(v >= 0.0)) return OT_EINVAL;
+      break;
     case OT_OPT_SAFEGUARD:
     case OT_OPT_TRANSLATE:
     case OT_OPT_SYMBOLS:
@@ -2705,4 +2723,82 @@ extern "C" int ot_solve_batched(ot_plan_set* s, int32_t count, const int32_t* N,
       o.ms_residual = o.ms_fft = o.ms_krylov = o.ms_update = o.ms_other = -1.0;
     }
   return first;
+}
+
+// ------------------------------------------------------------------------------------------
+// Spectral radius of the inverse of the discretised linearised operator (Sec. 5.1): power
+// iteration b_(k+1) = A^{-1} b_k / ||A^{-1} b_k||_2, A^{-1} b = Lbar^{-1} sigma with sigma
+// from GMRES(m) on L Lbar^{-1} sigma = b (the Fourier method of Sec. 4.2 at the plan's eta),
+// L the linearisation at the iterate phi; b_0 projected to mean zero (the operator acts on
+// mean-zero potentials, Sec. 3.1).  Host-driven: one synchronisation per GMRES cycle and per
+// iteration.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+static int inverse_radius_impl(ot_plan* p, const double* f, const double* g, const double* phi,
+                               const double* b0, int iters, double* rho) {
+  const int N = p->N, M = p->M;
+  const long P = (long)N * M;
+  RET(run_autotune(p));
+  set_solver_scalars(p);
+  p->hsc->forcing = 0;
+  CK(cudaMemcpyAsync(p->sc, p->hsc, sizeof(DevScalars), cudaMemcpyHostToDevice, p->stream));
+  if (p->translate) {
+    LAUNCH(p, OT_PROF_OTHER, -1, 2,
+           launch_translate_inputs(f, g, p->f, p->g, N, M, p->partials, p->sc, p->stream));
+  } else {
+    CK(cudaMemcpyAsync(p->f, f, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->g, g, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_input_stats(p->f, p->g, N, M, p->partials, p->sc, p->stream));
+  }
+  RET(read_scalars(p));
+  if (p->hsc->in_bad) return OT_EINVAL;
+  RET(run_prefilter(p, p->g, p->c));
+  CK(cudaMemcpyAsync(p->u, phi, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
+         residual_launch<T>(p, p->f, p->c, p->u, p->Fraw, nullptr, 0));
+  double* b = p->ucand;
+  double* th = p->uout;
+  CK(cudaMemcpyAsync(b, b0, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 2,
+         launch_subtract_mean(b, N, M, p->partials, p->sc, p->dmean, p->stream));
+  LAUNCH(p, OT_PROF_OTHER, -1, 2, launch_normalize(b, P, p->partials, p->sc, p->stream));
+  static const double zero = 0.0, one = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    // right-hand side b: the GMRES start reads (Fraw + shift) / tau
+    CK(cudaMemcpyAsync(p->Fraw, b, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaMemcpyAsync(&p->sc->shift, &zero, sizeof(double), cudaMemcpyHostToDevice,
+                       p->stream));
+    CK(cudaMemcpyAsync(&p->sc->tau, &one, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    RET(run_gmres<T>(p));
+    if (sizeof(T) == 4) {
+      // theta in double-float from the FP32 sigma (the solve's theta passes)
+      LAUNCH(p, OT_PROF_ROW_R2C, -1, 1,
+             launch_row_r2c<float>((const float*)p->sigma, 0, nullptr, nullptr,
+                                   (C2<float>*)p->spec, N, M, p->tb32, nullptr, p->stream));
+      LAUNCH(p, OT_PROF_COL_LBARINV, -1, 1,
+             launch_col_lbarinv_dd((const float2*)p->spec, (ddc*)p->q64, N, M, p->tb32,
+                                   p->tbdd, p->sc, p->stream));
+      LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+             launch_row_c2r_update_dd((const ddc*)p->q64, nullptr, th, 1.0, N, M, p->tbdd,
+                                      nullptr, p->stream));
+    } else {
+      RET(run_lbar_inv<double>(p, (const double*)p->sigma, nullptr, nullptr, 0.0, th));
+    }
+    LAUNCH(p, OT_PROF_OTHER, -1, 2, launch_normalize(th, P, p->partials, p->sc, p->stream));
+    RET(read_scalars(p));
+    rho[k] = p->hsc->pw_norm;
+    std::swap(b, th);
+  }
+  return OT_OK;
+}
+
+extern "C" int ot_inverse_spectral_radius(ot_plan* p, const double* f, const double* g,
+                                          const double* phi, const double* b0, int32_t iters,
+                                          double* rho) {
+  if (!p || !p->ready || p->slab_base || !f || !g || !phi || !b0 || !rho || iters < 1)
+    return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  return p->precision ? inverse_radius_impl<float>(p, f, g, phi, b0, iters, rho)
+                      : inverse_radius_impl<double>(p, f, g, phi, b0, iters, rho);
 }

@@ -1566,6 +1566,8 @@ __device__ int ctl_apply(int op, DevScalars* sc, int add, bool handles) {
   int cont = 0;
   switch (op) {
     case CTL_NEWTON: {
+      // tau schedule: the damping drops to 1 for good once max|F| < tau_switch
+      if (sc->tau_switch > 0.0 && sc->res_inf < sc->tau_switch) sc->tau = 1.0;
       if (sc->in_bad) {
         sc->status = OT_STATUS_EINVAL;
       } else if (!sc->admissible) {
@@ -1736,6 +1738,38 @@ cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* parti
   const dim3 nb = bgrid(dim3(reduce_blocks()), bat);
   k_sum_sel<<<nb, 256, 0, st>>>(u, (long)N * M, partials, sc, mean_out, bat);
   k_sub_sel<<<nb, 256, 0, st>>>(u, out, (long)N * M, sc, mean_out, bat);
+  return cudaGetLastError();
+}
+
+// 2-norm and normalisation of a vector (the power iteration of the inverse operator)
+__global__ void k_norm2(const double* __restrict__ x, long P, double* partials, DevScalars* sc) {
+  double v[1] = {0.0};
+  const int kind[1] = {0};
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    v[0] += x[p] * x[p];
+  block_reduce<1>(v, kind);
+  if (!publish_partials<1>(v, partials, &sc->ticket[TK_NORM])) return;
+  reduce_partials<1>(v, kind, partials, gridDim.x);
+  if (threadIdx.x == 0) {
+    sc->pw_norm = sqrt(v[0]);
+    sc->ticket[TK_NORM] = 0;
+  }
+}
+
+__global__ void k_scale_by_norm(double* __restrict__ x, long P, const DevScalars* __restrict__ sc) {
+  const double n = sc->pw_norm;
+  const double s = n > 0.0 ? 1.0 / n : 0.0;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x)
+    x[p] *= s;
+}
+
+cudaError_t launch_normalize(double* x, long P, double* partials, DevScalars* sc,
+                             cudaStream_t st) {
+  const int nb = reduce_blocks();
+  k_norm2<<<nb, 256, 0, st>>>(x, P, partials, sc);
+  k_scale_by_norm<<<nb, 256, 0, st>>>(x, P, sc);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct DevScalars {
   double relres;
   int j, jend, m, cycle_done, converged, iters, cycles;
   double eta, tau;
+  double tau_switch;  // tau schedule: tau becomes 1 once res_inf < tau_switch (0: off)
   // Newton control, resident on the device for the graph-launched solve
   double tol, step_s;
   // inexact-Newton forcing: forcing = 1 sets eta per step from eta_max and the residual
@@ -78,6 +79,7 @@ struct DevScalars {
   int active, in_cycle, halve;
   int excluded;       // the pair sits out this launch of the batched graph (a retry of others)
   double gauge_mean;  // mean removed by the final gauge of a batched solve
+  double pw_norm;     // 2-norm of the last vector normalised by launch_normalize
   // ticket counters of the last-block reductions
   unsigned int ticket[8];
 };
@@ -274,6 +276,9 @@ cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevS
 cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
                                DevScalars* sc, double* mean_out, cudaStream_t st,
                                Bat bat = Bat());
+// x <- x / ||x||_2 (two launches: the norm into sc->pw_norm, then the scaling; x = 0 stays 0)
+cudaError_t launch_normalize(double* x, long P, double* partials, DevScalars* sc,
+                             cudaStream_t st);
 // batched solve: dst (pair 0's plane, advanced by the slab per pair) <- tab[pair]; and the
 // reverse (tab[pair] <- src of pair), skipping excluded pairs (sc: pair 0's scalars)
 cudaError_t launch_gather(const double* const* tab, double* dst, long P, Bat bat,

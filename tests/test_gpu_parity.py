@@ -621,3 +621,24 @@ def test_untranslated_inputs_are_checked(ot):
         bad[3, 3] = -0.5
         with pytest.raises(ot.OTError):
             _gpu_solve(ot, bad, f, "fp64", translate=0, graph=graph)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_inverse_spectral_radius_matches_oracle(ot, prec):
+    # Sec. 5.1's power iteration on the inverse of the linearised operator, at the
+    # manufactured solution and at a blob pair's start, from the same seeded b0 (uniform in
+    # [0, 1] like the paper's): the norms follow the oracle's step for step (FP64: the GMRES
+    # solves agree to round-off; mixed: FP32 Krylov vectors and transforms, 1e-5)
+    cases = [(I.manufactured(32, 32)[:2], I.manufactured(32, 32)[2]),
+             (I.blob_pair(48, 64, s=1001), np.zeros((48, 64)))]
+    for (f, g), u in cases:
+        N, M = f.shape
+        b0 = I.SplitMix64(80).uniform(N * M).reshape(N, M)
+        for symbols in (0, 1):
+            with O.fd_symbols(symbols):
+                ref = O.inverse_spectral_radius(f, g, u, b0, iters=6, eta=1e-6)
+            p = plan(ot, N, M, prec, eta=1e-6, symbols=symbols)
+            rho = p.inverse_spectral_radius(dev(f), dev(g), dev(u), dev(b0), iters=6)
+            p.close()
+            tol = 1e-9 if prec == "fp64" else 1e-5
+            assert np.abs(rho - ref).max() <= tol * ref.max(), (rho, ref)

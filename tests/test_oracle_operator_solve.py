@@ -316,3 +316,58 @@ def test_invalid_inputs_rejected():
     assert st["status"] == O.ORC_EINVAL
     _, st, _, _ = O.solve(f, np.ones((16, 16)), tau=0.5)
     assert st["status"] == O.ORC_EINVAL
+
+
+def test_tau_schedule():
+    # tau schedule (remarks of Sec. 3.3, the tau study of Sec. 5.1): the damping is tau until
+    # max|F| < tau_switch, then 1.  Pins: switch 0 is the fixed-tau solve and a switch above
+    # the first residual the tau = 1 solve, step for step; with a switch in between the
+    # residual history equals the fixed-tau one up to the first step below the switch, and
+    # the solve reaches the same root in fewer steps than the fixed tau
+    f, g = I.blob_pair(64, 64, s=1001)
+    kw = dict(tol=1e-10, eta=1e-2, max_newton=400)
+    with O.fd_symbols():
+        u2, s2, h2, _ = O.solve(f, g, tau=2.0, **kw)
+        u1, s1, h1, _ = O.solve(f, g, tau=1.0, **kw)
+        u0, s0, h0, _ = O.solve(f, g, tau=2.0, tau_switch=0.0, **kw)
+        ub, sb, hb, _ = O.solve(f, g, tau=2.0, tau_switch=1e9, **kw)
+        us, ss, hs, _ = O.solve(f, g, tau=2.0, tau_switch=0.1, **kw)
+    assert np.array_equal(u0, u2) and s0 == s2
+    assert np.array_equal(ub, u1) and sb == s1
+    k = int(np.argmax(h2 < 0.1))
+    assert k > 0 and np.array_equal(hs[:k + 1], h2[:k + 1])
+    assert not np.array_equal(hs[k + 1:k + 3], h2[k + 1:k + 3])
+    assert ss["status"] == 0 and ss["newton_iters"] < s2["newton_iters"]
+    assert np.abs(us - u2).max() <= 1e-10
+
+
+def test_inverse_spectral_radius_of_the_laplacian():
+    # g = 1 at u = 0: the coefficients are a = I, b = 0, so L = Lbar is the Laplacian and the
+    # inverse's spectral radius (on mean-zero functions) is 1 / |s2(1)|: 1 / (4 pi^2) with
+    # the spectral symbols of Sec. 4.2, 1 / |(-2 cos 2t + 32 cos t - 30) N^2 / 12|, t = 2 pi / N,
+    # with the 4th-order stencils' (the largest eigenvalue is that of the four modes k = (+-1,
+    # 0), (0, +-1); the next is half of it, so the power iteration gains a bit per step)
+    N = 32
+    f = I.blob_density(N, N, 3)
+    g = np.ones((N, N))
+    b0 = I.SplitMix64(77).uniform(N * N).reshape(N, N)
+    rho = O.inverse_spectral_radius(f, g, np.zeros((N, N)), b0, iters=45, eta=1e-12)
+    assert abs(rho[-1] - 1.0 / (4.0 * np.pi ** 2)) <= 1e-9 * rho[-1]
+    t = 2.0 * np.pi / N
+    s2 = (-2.0 * np.cos(2 * t) + 32.0 * np.cos(t) - 30.0) * N * N / 12.0
+    with O.fd_symbols():
+        rho_fd = O.inverse_spectral_radius(f, g, np.zeros((N, N)), b0, iters=45, eta=1e-12)
+    assert abs(rho_fd[-1] - 1.0 / abs(s2)) <= 1e-9 * rho_fd[-1]
+    assert rho_fd[-1] > rho[-1]  # the stencil symbol is smaller in magnitude at k = 1
+
+
+def test_inverse_spectral_radius_of_the_manufactured_example():
+    # Sec. 5.1 reports about 0.03 for its manufactured example at every Newton step; with this
+    # build's constants (g = 1 + 0.5 cos 2 pi x cos 2 pi y, so a ~ g in [0.5, 1.5]) the radius
+    # at the solution is of the order of 1 / (4 pi^2 min a): between 0.015 and 0.06
+    N = 32
+    f, g, phi = I.manufactured(N, N)
+    b0 = I.SplitMix64(78).uniform(N * N).reshape(N, N)
+    rho = O.inverse_spectral_radius(f, g, phi, b0, iters=8)
+    assert 0.015 < rho[-1] < 0.06
+    assert abs(rho[-1] - rho[-2]) <= 0.05 * rho[-1]  # settled after a few iterations
