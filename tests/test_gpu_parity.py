@@ -642,3 +642,21 @@ def test_inverse_spectral_radius_matches_oracle(ot, prec):
             p.close()
             tol = 1e-9 if prec == "fp64" else 1e-5
             assert np.abs(rho - ref).max() <= tol * ref.max(), (rho, ref)
+
+
+@pytest.mark.parametrize("prec,graph", [("fp64", 1), ("fp64", 0), ("mixed", 1)])
+def test_tau_schedule_matches_oracle(ot, prec, graph):
+    # OT_OPT_TAU_SWITCH: tau = 2 until max|F| < 0.1, then 1 (the oracle's schedule); the FP64
+    # path takes the oracle's Newton steps, both reach its root
+    f, g = I.blob_pair(64, 64, s=1001)
+    with O.fd_symbols():
+        u_ref, st_ref, _, _ = O.solve(f, g, tau=2.0, tol=1e-10, eta=1e-2, max_newton=400,
+                                      tau_switch=0.1)
+    rc, st, phi = _gpu_solve(ot, f, g, prec, tau=2.0, tol=1e-10, eta=1e-2, symbols=1,
+                             max_newton=400, tau_switch=0.1, graph=graph)
+    assert st_ref["status"] == 0 and rc == 0
+    if prec == "fp64":
+        assert st["newton_iters"] == st_ref["newton_iters"]
+        assert np.abs(phi - u_ref).max() <= 1e-10
+    else:
+        assert np.abs(phi - u_ref).max() <= 1e-6
