@@ -75,6 +75,8 @@ def lib():
         _lib.orc_fd_poisson.argtypes = [vp, i, i, i, vp]
         _lib.orc_set_fd_symbols.argtypes = [i]
         _lib.orc_set_simplified.argtypes = [i]
+        _lib.orc_set_interp.argtypes = [i]
+        _lib.orc_get_interp.restype = i
         _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
     return _lib
 
@@ -293,6 +295,30 @@ class fd_symbols:
     def __exit__(self, *exc):
         lib().orc_set_fd_symbols(0)
         return False
+
+
+class interpolation:
+    """Context manager: g at the displaced points by bilinear (mode 1) or nearest-node
+    (mode 2) interpolation of the grid values, grad g by the same rule on the grid's 4th-order
+    centred differences (Sec. 4 intro; Sec. 5.2 and 5.3); the solve then skips the B-spline
+    prefilter and residual() takes the grid values of g in place of coefficients."""
+
+    def __init__(self, mode):
+        self.mode = {"bspline": 0, "bilinear": 1, "nearest": 2}.get(mode, mode)
+
+    def __enter__(self):
+        lib().orc_set_interp(int(self.mode))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_interp(0)
+        return False
+
+
+def interp_coeffs(g):
+    """What residual() takes for g in the current interpolation mode: the B-spline
+    coefficients (default) or the grid values themselves (bilinear, nearest)."""
+    return bspline_coeffs(g) if lib().orc_get_interp() == 0 else _f64(g).copy()
 
 
 class simplified_operator:

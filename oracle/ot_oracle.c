@@ -399,10 +399,59 @@ void orc_bspline_eval(const double *c, int N, int M, double x, double y, double 
 static int g_simplified = 0;
 void orc_set_simplified(int on) { g_simplified = on ? 1 : 0; }
 
+/* Interpolation of g at the displaced points (Sec. 4 intro: closest-neighbour interpolation
+ * used for the images of Sec. 5.2, linear interpolation named as the alternative and used
+ * in Sec. 5.3): 0 = the periodic cubic B-spline interpolant of the coefficients c (default),
+ * 1 = bilinear, 2 = nearest node.  In modes 1 and 2, c holds the grid values of g itself
+ * (no prefilter), G(T) interpolates them and grad G(T) interpolates, by the same rule, the
+ * grid gradient of g by the 4th-order centred differences. */
+static int g_interp = 0;
+void orc_set_interp(int mode) { g_interp = (mode == 1 || mode == 2) ? mode : 0; }
+int orc_get_interp(void) { return g_interp; }
+
+static void interp_eval_grid(const double *c, const double *gxg, const double *gyg, int N,
+                             int M, double gx_pos, double gy_pos, double *val, double *dgdx,
+                             double *dgdy) {
+  if (g_interp == 2) { /* nearest node: round half up */
+    long jn = wrap((long)floor(gx_pos + 0.5), M), in = wrap((long)floor(gy_pos + 0.5), N);
+    long q = in * M + jn;
+    *val = c[q];
+    *dgdx = gxg[q];
+    *dgdy = gyg[q];
+    return;
+  }
+  /* bilinear on the cell (i0, j0) .. (i0 + 1, j0 + 1) */
+  double fj = floor(gx_pos), fi = floor(gy_pos);
+  double tx = gx_pos - fj, ty = gy_pos - fi;
+  long j0 = wrap((long)fj, M), i0 = wrap((long)fi, N);
+  long j1 = wrap(j0 + 1, M), i1 = wrap(i0 + 1, N);
+  double w[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
+  long q[4] = {i0 * M + j0, i0 * M + j1, i1 * M + j0, i1 * M + j1};
+  double v = 0.0, a = 0.0, b = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    v += w[k] * c[q[k]];
+    a += w[k] * gxg[q[k]];
+    b += w[k] * gyg[q[k]];
+  }
+  *val = v;
+  *dgdx = a;
+  *dgdy = b;
+}
+
 int orc_residual(const double *f, const double *c, const double *u, int N, int M, double *F,
                  double *coef, double *scal) {
   long P = (long)N * M;
   double *fn = (double *)malloc(sizeof(double) * P);
+  double *gxg = NULL, *gyg = NULL;
+  if (g_interp) { /* grid gradient of g (c holds g in these modes) */
+    gxg = (double *)malloc(sizeof(double) * P);
+    gyg = (double *)malloc(sizeof(double) * P);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < M; ++j) {
+        gxg[(long)i * M + j] = d1x(c, N, M, i, j);
+        gyg[(long)i * M + j] = d1y(c, N, M, i, j);
+      }
+  }
   double sum_fn = 0.0, min_det = INFINITY;
   long nonfinite = 0;
   for (int i = 0; i < N; ++i)
@@ -412,8 +461,12 @@ int orc_residual(const double *f, const double *c, const double *u, int N, int M
       double uxx = d2x(u, N, M, i, j), uyy = d2y(u, N, M, i, j);
       double uxy = dxy(u, N, M, i, j);
       double G, Gx, Gy;
-      orc_bspline_eval_grid(c, N, M, (double)j + (double)M * ux, (double)i + (double)N * uy,
-                            &G, &Gx, &Gy);
+      if (g_interp)
+        interp_eval_grid(c, gxg, gyg, N, M, (double)j + (double)M * ux,
+                         (double)i + (double)N * uy, &G, &Gx, &Gy);
+      else
+        orc_bspline_eval_grid(c, N, M, (double)j + (double)M * ux, (double)i + (double)N * uy,
+                              &G, &Gx, &Gy);
       double det = (1.0 + uxx) * (1.0 + uyy) - uxy * uxy;
       fn[p] = G * det;
       if (!isfinite(fn[p])) nonfinite++;
@@ -444,6 +497,8 @@ int orc_residual(const double *f, const double *c, const double *u, int N, int M
     scal[4] = (double)nonfinite;
   }
   free(fn);
+  free(gxg);
+  free(gyg);
   return 0;
 }
 
@@ -882,7 +937,10 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
     memcpy(f, f_in, sizeof(double) * P);
     memcpy(g, g_in, sizeof(double) * P);
   }
-  orc_bspline_coeffs(g, N, M, c);
+  if (g_interp)
+    memcpy(c, g, sizeof(double) * P); /* nearest / bilinear: the grid values themselves */
+  else
+    orc_bspline_coeffs(g, N, M, c);
   double scal[5];
   orc_residual(f, c, u, N, M, F, coef, scal);
   double tau = o->tau;

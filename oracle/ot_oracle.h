@@ -70,6 +70,9 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
 void orc_set_fd_symbols(int on);
 /* 1: residual coefficients b1 = b2 = 0 (the simplified operator of the Sec. 3.3 remark) */
 void orc_set_simplified(int on);
+/* interpolation of g: 0 cubic B-spline (default), 1 bilinear, 2 nearest node */
+void orc_set_interp(int mode);
+int orc_get_interp(void);
 
 /* learned warm start: FD Poisson solve and network features */
 #define ORC_WS_K 16
