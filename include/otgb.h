@@ -124,6 +124,15 @@ extern "C" {
                                    damping is 1 for the rest of the solve (a larger tau for
                                    the start, tau = 1 near convergence; the remarks of Sec. 3.3
                                    and the tau study of Sec. 5.1) */
+#define OT_OPT_INTERP 25        /* g and grad g at the displaced points x + grad phi: 0
+                                   (default) the periodic cubic B-spline interpolant of g and
+                                   its exact gradient; 1 bilinear, 2 nearest grid node (Sec. 4:
+                                   closest-neighbour interpolation for images, Sec. 5.2;
+                                   linear, Sec. 5.3) of the grid values of g and, by the same
+                                   rule, of its grid gradient by the 4th-order centred
+                                   differences (then no prefilter: ot_prefilter copies g and
+                                   ot_eval_residual takes g for c); not with the learned warm
+                                   start (OT_EINVAL) nor in plan sets */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

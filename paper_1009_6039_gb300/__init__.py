@@ -23,7 +23,7 @@ OT_OPT_PRECISION, OT_OPT_SAFEGUARD, OT_OPT_TRANSLATE, OT_OPT_WARM_START = 5, 6, 
 OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11, 12, 13
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
 OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
-OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH = 22, 23, 24
+OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH, OT_OPT_INTERP = 22, 23, 24, 25
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -411,7 +411,7 @@ class Plan:
              "forcing": OT_OPT_FORCING, "tau_retry": OT_OPT_TAU_RETRY,
              "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR,
              "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT,
-             "tau_switch": OT_OPT_TAU_SWITCH}
+             "tau_switch": OT_OPT_TAU_SWITCH, "interp": OT_OPT_INTERP}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

@@ -48,6 +48,11 @@ struct ot_plan {
   int forcing = 0;  // OT_OPT_FORCING: 0 fixed eta, 1 Eisenstat-Walker with eta as the cap
   int tau_retry = 0;  // OT_OPT_TAU_RETRY: re-solves with doubled tau after a divergence
   double tau_switch = 0.0;  // OT_OPT_TAU_SWITCH: tau schedule (tau -> 1 below this max|F|)
+  // OT_OPT_INTERP: interpolation of g (0 cubic B-spline, 1 bilinear, 2 nearest node); the
+  // latter two use the grid gradient of g (2 planes, FP64 and FP32)
+  int interp = 0;
+  double* gxy = nullptr;
+  float* gxy32 = nullptr;
   int op_simple = 0;  // OT_OPT_OPERATOR: 1 drops the grad g term of the linearisation
   int ws_stall = 0;   // OT_OPT_WS_TEST_STALL: the next ot_ws_mlp_forward stalls (test hook)
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
@@ -124,11 +129,21 @@ template <typename T>
 static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
                                    const double* ua, double* Fraw, const double* ub = nullptr,
                                    int sel = 0) {
+  const size_t P = (size_t)p->N * p->M;
+  Interp ip;
+  if (p->interp) {
+    ip.mode = p->interp;
+    ip.gx = p->gxy;
+    ip.gy = p->gxy + P;
+    ip.gx32 = p->gxy32;
+    ip.gy32 = p->gxy32 + P;
+  }
   if (sizeof(T) == 4)
     return launch_residual_dd(p->fdd, p->cdd, ua, p->N, p->M, Fraw, (float*)p->coef,
-                              p->partials, p->sc, p->stream, ub, sel, p->op_simple, btc(p));
+                              p->partials, p->sc, p->stream, ub, sel, p->op_simple, btc(p),
+                              ip);
   return launch_residual<double>(f, c, ua, p->N, p->M, Fraw, (double*)p->coef, p->partials,
-                                 p->sc, p->stream, ub, sel, nullptr, p->op_simple);
+                                 p->sc, p->stream, ub, sel, nullptr, p->op_simple, ip);
 }
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
@@ -324,6 +339,10 @@ static void free_buffers(ot_plan* p) {
   p->ws_X = p->ws_s = p->ws_c32 = nullptr;
   if (p->hsc) cudaFreeHost(p->hsc);
   if (p->hinit) cudaFreeHost(p->hinit);
+  if (p->gxy) cudaFree(p->gxy);
+  if (p->gxy32) cudaFree(p->gxy32);
+  p->gxy = nullptr;
+  p->gxy32 = nullptr;
   p->hinit = nullptr;
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
@@ -497,6 +516,8 @@ static int alloc_tables(ot_plan* p) {
   return OT_OK;
 }
 
+static int alloc_grad_planes(ot_plan* p);
+
 static int alloc_buffers(ot_plan* p) {
   free_buffers(p);
   const size_t P = (size_t)p->N * p->M;
@@ -528,6 +549,7 @@ static int alloc_buffers(ot_plan* p) {
     p->q64 = nullptr;
   }
   RET(alloc_tables(p));
+  if (p->interp) RET(alloc_grad_planes(p));
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
   size_t nk = (size_t)p->kblocks * OTGB_MAXM;
   if (nk > np) np = nk;
@@ -540,6 +562,14 @@ static int alloc_buffers(ot_plan* p) {
   CK(cudaMallocHost(&p->hinit, sizeof(DevScalars)));
   memset(p->hinit, 0, sizeof(DevScalars));
   p->ready = true;
+  return OT_OK;
+}
+
+// grid-gradient planes of g for the nearest / bilinear interpolation modes
+static int alloc_grad_planes(ot_plan* p) {
+  const size_t P = (size_t)p->N * p->M;
+  CK(cudaMalloc(&p->gxy, 2 * P * sizeof(double)));
+  CK(cudaMalloc(&p->gxy32, 2 * P * sizeof(float)));
   return OT_OK;
 }
 
@@ -670,7 +700,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       return OT_OK;
     case OT_OPT_WARM_START:
       if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
-      if (v == 2 && !p->ws_have) return OT_EINVAL;
+      if (v == 2 && (!p->ws_have || p->interp)) return OT_EINVAL;
       p->warm_start = (int)v;
       free_graph(p);
       return OT_OK;
@@ -749,6 +779,15 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (!(v >= 0.0)) return OT_EINVAL;
       p->tau_switch = v;
       return OT_OK;
+    case OT_OPT_INTERP:
+      if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
+      if (v != 0 && p->warm_start == 2) return OT_EINVAL;  // the features sample the B-spline
+      if ((int)v != p->interp) {
+        p->interp = (int)v;
+        free_graph(p);
+      }
+      if (p->interp && p->ready && !p->gxy) RET(alloc_grad_planes(p));
+      return OT_OK;
     case OT_OPT_PHASE_TIMES:
       if (v != 0 && v != 1) return OT_EINVAL;
       if (p->phase_times != (int)v) {
@@ -802,6 +841,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_OPERATOR: *v = p->op_simple; return OT_OK;
     case OT_OPT_PHASE_TIMES: *v = p->phase_times; return OT_OK;
     case OT_OPT_TAU_SWITCH: *v = p->tau_switch; return OT_OK;
+    case OT_OPT_INTERP: *v = p->interp; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -944,6 +984,18 @@ static int read_scalars(ot_plan* p) {
 // c = B-spline coefficients of g in FP64 (recursive filters along y and x; p->Fraw is free
 // scratch before the first residual); the mixed mode also keeps c and f as (hi, lo) floats
 static int run_prefilter(ot_plan* p, const double* g, double* c) {
+  if (p->interp) {
+    // nearest / bilinear: the grid values themselves and their gradient
+    const long P = (long)p->N * p->M;
+    if (c != g) CK(cudaMemcpyAsync(c, g, P * 8, cudaMemcpyDeviceToDevice, p->stream));
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_grad4(g, p->N, p->M, p->gxy, p->gxy + P, p->gxy32, p->gxy32 + P, p->stream));
+    if (p->precision) {
+      LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(c, p->cdd, P, p->stream));
+      LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(p->f, p->fdd, P, p->stream));
+    }
+    return OT_OK;
+  }
   LAUNCH(p, OT_PROF_OTHER, -1, 2,
          launch_prefilter(g, p->Fraw, c, p->precision ? p->cdd : nullptr, p->N, p->M,
                           p->stream, btc(p)));
@@ -2023,6 +2075,9 @@ static int eval_residual_impl(ot_plan* p, const double* f, const double* c, cons
     LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(c, p->cdd, P, p->stream));
     LAUNCH(p, OT_PROF_OTHER, -1, 1, launch_split_dd(f, p->fdd, P, p->stream));
   }
+  if (p->interp)  // c holds g: its grid gradient for the interpolated grad g
+    LAUNCH(p, OT_PROF_OTHER, -1, 1,
+           launch_grad4(c, N, M, p->gxy, p->gxy + P, p->gxy32, p->gxy32 + P, p->stream));
   LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
          residual_launch<T>(p, f, c, u, p->Fraw, nullptr, 0));
   LAUNCH(p, OT_PROF_OTHER, -1, 1,

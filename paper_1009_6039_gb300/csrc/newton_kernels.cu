@@ -468,6 +468,11 @@ struct ResidConsts {
   double MNh;               // M N / 144
   double w3M, w3N;          // 1/(3M), 1/(3N): Simpson weights (2 or 4) x these
   int nob;                  // 1: the simplified operator (b = 0, Sec. 3.3 remark)
+  // interpolation of g (Sec. 4 intro; Sec. 5.2, 5.3): 0 cubic B-spline of the coefficients c;
+  // 1 bilinear, 2 nearest node of the grid values (then c = g) and of the grid gradient gx, gy
+  int interp;
+  const double* gx;
+  const double* gy;
 };
 
 template <typename G>
@@ -563,7 +568,26 @@ __global__ void __launch_bounds__(RTX * RTY / RPT)
     ii[3] = wrap_near(i0 + 2, N);
     double G = 0.0;
     T Gx, Gy;
-    if (sizeof(T) == 8) {
+    if (K.interp == 2) {  // nearest node (round half up)
+      const size_t q = (size_t)wrapi((int)floor(gyp + 0.5), N) * M + wrapi((int)floor(gxp + 0.5), M);
+      G = __ldg(c + q);
+      Gx = (T)__ldg(K.gx + q);
+      Gy = (T)__ldg(K.gy + q);
+    } else if (K.interp == 1) {  // bilinear on the cell (i0, j0) .. (i0 + 1, j0 + 1)
+      const double w[4] = {(1.0 - tx_) * (1.0 - ty_), tx_ * (1.0 - ty_), (1.0 - tx_) * ty_,
+                           tx_ * ty_};
+      const size_t q[4] = {(size_t)ii[1] * M + jj[1], (size_t)ii[1] * M + jj[2],
+                           (size_t)ii[2] * M + jj[1], (size_t)ii[2] * M + jj[2]};
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        G += w[k] * __ldg(c + q[k]);
+        a += w[k] * __ldg(K.gx + q[k]);
+        b += w[k] * __ldg(K.gy + q[k]);
+      }
+      Gx = (T)a;
+      Gy = (T)b;
+    } else if (sizeof(T) == 8) {
       double wxv[4], dwx[4], wyv[4], dwy[4];
       bspline_w<double>(tx_, wxv, dwx);
       bspline_w<double>(ty_, wyv, dwy);
@@ -698,6 +722,9 @@ struct ResidConstsDD {
   float M, N;
   float w3M, w3N;            // 1/(3M), 1/(3N)
   int nob;                   // 1: the simplified operator (b = 0)
+  int interp;                // as ResidConsts::interp (then cdd = g as (hi, lo) pairs)
+  const float* gx;           // grid gradient of g (FP32: the Jacobian only)
+  const float* gy;
 };
 
 __device__ __forceinline__ dd ldd(const float2* __restrict__ a, size_t i) {
@@ -816,33 +843,61 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
     ii[1] = i0;
     ii[2] = wrap_near(i0 + 1, N);
     ii[3] = wrap_near(i0 + 2, N);
-    dd wxv[4], wyv[4];
-    bspline6_dd(tx_, wxv);
-    bspline6_dd(ty_, wyv);
-    // gradient weights in FP32 (Jacobian only)
-    float wxf[4], dwx[4], wyf[4], dwy[4];
-    bspline_w<float>(tx_.hi, wxf, dwx);
-    bspline_w<float>(ty_.hi, wyf, dwy);
-    dd G36 = dd{0.f, 0.f};
-    float gx = 0.f, gy = 0.f;
+    dd G;
+    float Gx, Gy;
+    if (K.interp == 2) {  // nearest node (round half up on the fraction)
+      const bool upx = tx_.hi > 0.5f || (tx_.hi == 0.5f && tx_.lo >= 0.0f);
+      const bool upy = ty_.hi > 0.5f || (ty_.hi == 0.5f && ty_.lo >= 0.0f);
+      const int jn = wrapi(fj + (upx ? 1 : 0), M);
+      const int in = wrapi(fi + (upy ? 1 : 0), N);
+      const size_t q = (size_t)in * M + jn;
+      G = ldd(cdd, q);
+      Gx = __ldg(K.gx + q);
+      Gy = __ldg(K.gy + q);
+    } else if (K.interp == 1) {  // bilinear on the cell (i0, j0) .. (i0 + 1, j0 + 1)
+      const dd sx = dd_add_f(dd{-tx_.hi, -tx_.lo}, 1.0f), sy = dd_add_f(dd{-ty_.hi, -ty_.lo}, 1.0f);
+      const size_t q00 = (size_t)ii[1] * M + jj[1], q01 = (size_t)ii[1] * M + jj[2];
+      const size_t q10 = (size_t)ii[2] * M + jj[1], q11 = (size_t)ii[2] * M + jj[2];
+      const dd r0 = dd_fma(ldd(cdd, q01), tx_, dd_mul(ldd(cdd, q00), sx));
+      const dd r1 = dd_fma(ldd(cdd, q11), tx_, dd_mul(ldd(cdd, q10), sx));
+      G = dd_fma(r1, ty_, dd_mul(r0, sy));
+      const float ax = tx_.hi, ay = ty_.hi;
+      const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay), w10 = (1.f - ax) * ay,
+                  w11 = ax * ay;
+      Gx = w00 * __ldg(K.gx + q00) + w01 * __ldg(K.gx + q01) + w10 * __ldg(K.gx + q10) +
+           w11 * __ldg(K.gx + q11);
+      Gy = w00 * __ldg(K.gy + q00) + w01 * __ldg(K.gy + q01) + w10 * __ldg(K.gy + q10) +
+           w11 * __ldg(K.gy + q11);
+    } else {
+      dd wxv[4], wyv[4];
+      bspline6_dd(tx_, wxv);
+      bspline6_dd(ty_, wyv);
+      // gradient weights in FP32 (Jacobian only)
+      float wxf[4], dwx[4], wyf[4], dwy[4];
+      bspline_w<float>(tx_.hi, wxf, dwx);
+      bspline_w<float>(ty_.hi, wyf, dwy);
+      dd G36 = dd{0.f, 0.f};
+      float gx = 0.f, gy = 0.f;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const size_t row = (size_t)ii[b] * M;
-      dd sv = dd{0.f, 0.f};
-      float svf = 0.f, sdf = 0.f;
+      for (int b = 0; b < 4; ++b) {
+        const size_t row = (size_t)ii[b] * M;
+        dd sv = dd{0.f, 0.f};
+        float svf = 0.f, sdf = 0.f;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const dd cv = ldd(cdd, row + jj[a]);
-        sv = dd_fma(cv, wxv[a], sv);
-        svf = fmaf(cv.hi, wxf[a], svf);
-        sdf = fmaf(cv.hi, dwx[a], sdf);
+        for (int a = 0; a < 4; ++a) {
+          const dd cv = ldd(cdd, row + jj[a]);
+          sv = dd_fma(cv, wxv[a], sv);
+          svf = fmaf(cv.hi, wxf[a], svf);
+          sdf = fmaf(cv.hi, dwx[a], sdf);
+        }
+        G36 = dd_fma(sv, wyv[b], G36);
+        gx = fmaf(sdf, wyf[b], gx);
+        gy = fmaf(svf, dwy[b], gy);
       }
-      G36 = dd_fma(sv, wyv[b], G36);
-      gx = fmaf(sdf, wyf[b], gx);
-      gy = fmaf(svf, dwy[b], gy);
+      G = dd_mul(G36, K.inv36);
+      Gx = gx * K.M;
+      Gy = gy * K.N;
     }
-    const dd G = dd_mul(G36, K.inv36);
-    const float Gx = gx * K.M, Gy = gy * K.N;
     const dd det = dd_sub(dd_mul(dd_add_f(uxx, 1.0f), dd_add_f(uyy, 1.0f)), dd_mul(uxy, uxy));
     const dd fn = dd_mul(G, det);
     const size_t p = (size_t)i * M + j;
@@ -933,7 +988,7 @@ static dd host_dd(double v) {
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
                                DevScalars* sc, cudaStream_t st, const double* ub, int sel,
-                               int simplified, Bat bat) {
+                               int simplified, Bat bat, Interp ip) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConstsDD K;
   K.Mh = host_dd((double)M / 12.0);
@@ -947,6 +1002,10 @@ cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const doubl
   K.w3M = (float)(1.0 / (3.0 * (double)M));
   K.w3N = (float)(1.0 / (3.0 * (double)N));
   K.nob = simplified ? 1 : 0;
+  K.interp = ip.mode;
+  K.gx = ip.gx32;
+  K.gy = ip.gy32;
+  if (ip.mode && !(ip.gx32 && ip.gy32)) return cudaErrorInvalidValue;
   k_residual_dd<<<bgrid(grid, bat), RTX * RTY / RPT, 0, st>>>(fdd, cdd, ua, ub, sel, N, M, K,
                                                                 Fraw, coef, partials, sc, bat);
   return cudaGetLastError();
@@ -960,7 +1019,7 @@ template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
                             cudaStream_t st, const double* ub, int sel, const float* c32,
-                            int simplified) {
+                            int simplified, Interp ip) {
   dim3 grid((M + RTX - 1) / RTX, (N + RTY - 1) / RTY);
   ResidConsts K;
   K.Mh = (double)M / 12.0;
@@ -971,6 +1030,10 @@ cudaError_t launch_residual(const double* f, const double* c, const double* ua, 
   K.w3M = 1.0 / (3.0 * (double)M);
   K.w3N = 1.0 / (3.0 * (double)N);
   K.nob = simplified ? 1 : 0;
+  K.interp = ip.mode;
+  K.gx = ip.gx;
+  K.gy = ip.gy;
+  if (ip.mode && !(ip.gx && ip.gy)) return cudaErrorInvalidValue;
   if (sizeof(T) == 4 && !c32) return cudaErrorInvalidValue;
   k_residual<T><<<grid, RTX * RTY / RPT, 0, st>>>(f, c, c32, ua, ub, sel, N, M, K, Fraw, coef,
                                                   partials, sc);
@@ -1741,6 +1804,37 @@ cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* parti
   return cudaGetLastError();
 }
 
+// grid gradient of g by the 4th-order centred differences (periodic), FP64 and FP32 copies:
+// the nearest-node and bilinear interpolation modes interpolate it at the displaced points
+__global__ void k_grad4(const double* __restrict__ g, int N, int M, double* __restrict__ gx,
+                        double* __restrict__ gy, float* __restrict__ gx32,
+                        float* __restrict__ gy32) {
+  const long P = (long)N * M;
+  const double sx = (double)M / 12.0, sy = (double)N / 12.0;
+  for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
+       p += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(p / M), j = (int)(p - (long)i * M);
+    const double* row = g + (size_t)i * M;
+    const int jm1 = wrapi(j - 1, M), jm2 = wrapi(j - 2, M), jp1 = wrapi(j + 1, M),
+              jp2 = wrapi(j + 2, M);
+    const int im1 = wrapi(i - 1, N), im2 = wrapi(i - 2, N), ip1 = wrapi(i + 1, N),
+              ip2 = wrapi(i + 2, N);
+    const double a = (-row[jp2] + 8.0 * row[jp1] - 8.0 * row[jm1] + row[jm2]) * sx;
+    const double b = (-g[(size_t)ip2 * M + j] + 8.0 * g[(size_t)ip1 * M + j] -
+                      8.0 * g[(size_t)im1 * M + j] + g[(size_t)im2 * M + j]) * sy;
+    gx[p] = a;
+    gy[p] = b;
+    gx32[p] = (float)a;
+    gy32[p] = (float)b;
+  }
+}
+
+cudaError_t launch_grad4(const double* g, int N, int M, double* gx, double* gy, float* gx32,
+                         float* gy32, cudaStream_t st) {
+  k_grad4<<<reduce_blocks(), 256, 0, st>>>(g, N, M, gx, gy, gx32, gy32);
+  return cudaGetLastError();
+}
+
 // 2-norm and normalisation of a vector (the power iteration of the inverse operator)
 __global__ void k_norm2(const double* __restrict__ x, long P, double* partials, DevScalars* sc) {
   double v[1] = {0.0};
@@ -1831,7 +1925,8 @@ cudaError_t launch_convert(const void* in, int in_d, void* out, int out_d, long 
 #define OTGB_INST_NEWTON(T)                                                                   \
   template cudaError_t launch_residual<T>(const double*, const double*, const double*, int,   \
                                           int, double*, T*, double*, DevScalars*,             \
-                                          cudaStream_t, const double*, int, const float*, int); \
+                                          cudaStream_t, const double*, int, const float*, int,  \
+                                          Interp);                                            \
   template cudaError_t launch_gmres_init<T>(const double*, const T*, T*, long, int, double*,  \
                                             DevScalars*, int, cudaStream_t, T*, Bat);         \
   template cudaError_t launch_gmres_dots<T>(const T*, const T*, long, double*, DevScalars*,   \

@@ -250,6 +250,18 @@ cudaError_t launch_input_stats(const double* f, const double* g, int N, int M,
                                Bat bat = Bat());
 // phase stamp (OT_OPT_PHASE_TIMES): cls opens a phase, -1 closes the last one
 cudaError_t launch_stamp(DevScalars* sc, int cls, cudaStream_t st);
+// interpolation of g at the displaced points: mode 0 cubic B-spline of the coefficients c;
+// 1 bilinear, 2 nearest node of the grid values (c = g) and of the grid gradient (gx, gy in
+// FP64 for the FP64 kernel, gx32, gy32 for the double-float one)
+struct Interp {
+  int mode = 0;
+  const double* gx = nullptr;
+  const double* gy = nullptr;
+  const float* gx32 = nullptr;
+  const float* gy32 = nullptr;
+};
+cudaError_t launch_grad4(const double* g, int N, int M, double* gx, double* gy, float* gx32,
+                         float* gy32, cudaStream_t st);
 // u = ub ? (upar ^ sel ? ub : ua) : ua   (sel 0: current iterate, 1: candidate);
 // simplified: b = 0 in the coefficients (the operator without the grad g term)
 // c32 (optional, FP32 copy of c): used for the gradient of the interpolant in FP32 mode
@@ -257,12 +269,14 @@ template <typename T>
 cudaError_t launch_residual(const double* f, const double* c, const double* ua, int N, int M,
                             double* Fraw, T* coef, double* partials, DevScalars* sc,
                             cudaStream_t st, const double* ub = nullptr, int sel = 0,
-                            const float* c32 = nullptr, int simplified = 0);
+                            const float* c32 = nullptr, int simplified = 0,
+                            Interp ip = Interp());
 // mixed mode: the residual in double-float arithmetic from (hi, lo) float pairs of f and c
 cudaError_t launch_residual_dd(const float2* fdd, const float2* cdd, const double* ua, int N,
                                int M, double* Fraw, float* coef, double* partials,
                                DevScalars* sc, cudaStream_t st, const double* ub = nullptr,
-                               int sel = 0, int simplified = 0, Bat bat = Bat());
+                               int sel = 0, int simplified = 0, Bat bat = Bat(),
+                               Interp ip = Interp());
 // out[k] = (hi, lo) float pair of in[k]
 cudaError_t launch_split_dd(const double* in, float2* out, long n, cudaStream_t st,
                             Bat bat = Bat());

@@ -660,3 +660,43 @@ def test_tau_schedule_matches_oracle(ot, prec, graph):
         assert np.abs(phi - u_ref).max() <= 1e-10
     else:
         assert np.abs(phi - u_ref).max() <= 1e-6
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_interpolation_modes_residual_and_solve(ot, mode, prec):
+    # OT_OPT_INTERP 1 (bilinear) / 2 (nearest node): g and its grid gradient interpolated at
+    # the displaced points (Sec. 4 intro, Sec. 5.2, 5.3), against the oracle's modes.  The
+    # displacement of u spans several cells so that cell and node choices vary.  Residual: as
+    # test_residual_and_coefficients (FP64 round-off; mixed: double-float value, FP32
+    # gradient); nearest: the node decision is taken in FP64 on both sides, so a disagreement
+    # could only come from a tie within round-off (none in these fields)
+    N, M = 64, 96
+    f = I.blob_density(N, M, 61)
+    g = I.blob_density(N, M, 62)
+    u = smooth_field(N, M, amp=3e-3, kmax=3)
+    name = {1: "bilinear", 2: "nearest"}[mode]
+    with O.interpolation(name):
+        F_ref, coef_ref, s_ref = O.residual(f, g, u)
+    p = plan(ot, N, M, prec, interp=mode)
+    fd, gd, ud = dev(f), dev(g), dev(u)
+    Fd, coefd = dev(np.zeros((N, M))), dev(np.zeros((5, N, M)))
+    scal = np.zeros(10)
+    assert ot.ot_eval_residual(p.h, ptr(fd), ptr(gd), ptr(ud), ptr(Fd), ptr(coefd),
+                               hptr(scal)) == 0
+    p.close()
+    eps = np.finfo(float).eps if prec == "fp64" else 2.0 ** -48
+    tol = 32 * eps * np.abs(u).max() * max(N, M) ** 2 * np.abs(g).max() + 64 * eps * 10
+    assert np.abs(Fd.cpu().numpy() - F_ref).max() <= tol
+    assert abs(scal[3] - s_ref["min_det"]) <= tol
+    cs = np.abs(coef_ref).max()
+    ctol = (1e-12 if prec == "fp64" else 2e-6) * cs
+    assert np.abs(coefd.cpu().numpy() - coef_ref).max() <= ctol
+    # a blob pair solved in the mode reaches the oracle's root in that mode
+    fb, gb = I.blob_pair(48, 64, s=1005)
+    with O.interpolation(name), O.fd_symbols():
+        u_ref, st_ref, _, _ = O.solve(fb, gb, tau=1.0, tol=1e-9, eta=1e-2, max_newton=300)
+    rc, st, phi = _gpu_solve(ot, fb, gb, prec, tau=1.0, tol=1e-9, eta=1e-2, symbols=1,
+                             max_newton=300, interp=mode)
+    assert st_ref["status"] == 0 and rc == 0
+    assert np.abs(phi - u_ref).max() <= (1e-10 if prec == "fp64" else 1e-6)
