@@ -692,11 +692,18 @@ def test_interpolation_modes_residual_and_solve(ot, mode, prec):
     cs = np.abs(coef_ref).max()
     ctol = (1e-12 if prec == "fp64" else 2e-6) * cs
     assert np.abs(coefd.cpu().numpy() - coef_ref).max() <= ctol
-    # a blob pair solved in the mode reaches the oracle's root in that mode
+    # a blob pair in the mode: bilinear reaches the oracle's root; with the nearest node the
+    # residual is piecewise constant in u and the iteration stalls near its floor, so (as the
+    # paper's image runs, a fixed number of steps) both take 4 Newton steps and the iterates
+    # are compared
     fb, gb = I.blob_pair(48, 64, s=1005)
+    kw = dict(tau=1.0, tol=1e-9, eta=1e-2, max_newton=300 if mode == 1 else 4)
     with O.interpolation(name), O.fd_symbols():
-        u_ref, st_ref, _, _ = O.solve(fb, gb, tau=1.0, tol=1e-9, eta=1e-2, max_newton=300)
-    rc, st, phi = _gpu_solve(ot, fb, gb, prec, tau=1.0, tol=1e-9, eta=1e-2, symbols=1,
-                             max_newton=300, interp=mode)
-    assert st_ref["status"] == 0 and rc == 0
+        u_ref, st_ref, _, _ = O.solve(fb, gb, **kw)
+    rc, st, phi = _gpu_solve(ot, fb, gb, prec, symbols=1, interp=mode, **kw)
+    if mode == 1:
+        assert st_ref["status"] == 0 and rc == 0
+    else:
+        assert st_ref["status"] == O.ORC_ENOCONV and rc == ot.OT_ENOCONV
+        assert st["newton_iters"] == 4 and st["res_inf"] < 0.5 * st_ref["res_inf"] + 1.0
     assert np.abs(phi - u_ref).max() <= (1e-10 if prec == "fp64" else 1e-6)
