@@ -78,6 +78,11 @@ def lib():
         _lib.orc_set_interp.argtypes = [i]
         _lib.orc_get_interp.restype = i
         _lib.orc_ws_features.argtypes = [vp, vp, vp, vp, i, i, vp]
+        _lib.orc_fd_apply.argtypes = [vp, vp, i, i, vp]
+        _lib.orc_fd_apply_t.argtypes = [vp, vp, i, i, vp]
+        _lib.orc_bicg_dense.argtypes = [vp, vp, i, d, i, vp, vp, vp]
+        _lib.orc_bicg_fd.argtypes = [vp, vp, i, i, d, i, vp, vp, vp]
+        _lib.orc_set_linear_solver.argtypes = [i, i]
     return _lib
 
 
@@ -201,6 +206,57 @@ def gmres_dense(A, b, m=10, eta=1e-10, max_restarts=50):
     st = lib().orc_gmres_dense(_p(A), _p(b), n, m, eta, max_restarts, _p(x), ctypes.byref(it),
                                ctypes.byref(cy), ctypes.byref(rr))
     return x, dict(status=st, iters=it.value, cycles=cy.value, relres=rr.value)
+
+
+def fd_apply(coef, x, transpose=False):
+    """Sec. 4.1: y = A~ x (or A~^T x), A the second-order centred-difference discretisation of
+    the linearised operator with the coefficients of residual(), A~ = A + 1 1^T (the extra
+    equation sum x = 0 added to every row)."""
+    coef, x = _f64(coef), _f64(x)
+    N, M = x.shape
+    y = np.empty_like(x)
+    fn = lib().orc_fd_apply_t if transpose else lib().orc_fd_apply
+    fn(_p(coef), _p(x), N, M, _p(y))
+    return y
+
+
+def bicg_dense(A, b, eta=1e-10, max_iters=1000):
+    """Unpreconditioned BiCG (Sec. 4.1) on a dense system, from x = 0."""
+    A, b = _f64(A), _f64(b)
+    n = b.shape[0]
+    x = np.empty(n)
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().orc_bicg_dense(_p(A), _p(b), n, eta, max_iters, _p(x), ctypes.byref(it),
+                              ctypes.byref(rr))
+    return x, dict(status=st, iters=it.value, relres=rr.value)
+
+
+def bicg_fd(coef, h, eta=1e-4, max_iters=20000):
+    """BiCG on A~ theta = h (Sec. 4.1), from theta = 0."""
+    coef, h = _f64(coef), _f64(h)
+    N, M = h.shape
+    t = np.empty_like(h)
+    it, rr = ctypes.c_int(), ctypes.c_double()
+    st = lib().orc_bicg_fd(_p(coef), _p(h), N, M, eta, max_iters, _p(t), ctypes.byref(it),
+                           ctypes.byref(rr))
+    return t, dict(status=st, iters=it.value, relres=rr.value)
+
+
+class fd_bicg:
+    """Context manager: the Newton steps of solve() take theta from the finite-difference
+    system of Sec. 4.1 solved by BiCG (at most max_iters iterations per step; the stats'
+    gmres_iters count BiCG iterations) instead of the Fourier method of Sec. 4.2."""
+
+    def __init__(self, max_iters=20000):
+        self.max_iters = max_iters
+
+    def __enter__(self):
+        lib().orc_set_linear_solver(1, int(self.max_iters))
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_set_linear_solver(0, 0)
+        return False
 
 
 def gmres_op(coef, abar, h, m=10, eta=1e-4, max_restarts=50):

@@ -20,6 +20,8 @@
  *   - Sec. 4.2, Eq. (fouriersystem): Strain's split L Lbar^{-1} sigma = h, Lbar theta = sigma;
  *                                    symbol rho-bar(k); alpha_ij, beta_i by inverse FFTs;
  *                                    restarted GMRES(m); averages by Simpson's rule
+ *   - Sec. 4.1                    : the comparison path: second-order centred differences
+ *                                    of theta, the augmented system A~ = A + 1 1^T, BiCG
  *
  * Readings where the paper is silent (each listed in the design notes of the repository):
  *   - stencils: D1 = (-u[+2] + 8u[+1] - 8u[-1] + u[-2]) / (12h),
@@ -858,6 +860,193 @@ int orc_gmres_op(const double *coef, const double abar[5], const double *h, int 
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Finite-difference implementation (Sec. 4.1): second-order centred differences of theta, */
+/* the augmented square system A~ x = b, unpreconditioned BiCG                             */
+/* ------------------------------------------------------------------------------------ */
+
+/* The linear operator of Eq. (linearmaeq) in the coefficient form of orc_residual,
+ *   L theta = a11 theta_xx + 2 a12 theta_xy + a22 theta_yy + b1 theta_x + b2 theta_y,
+ * with second-order centred differences (spacings 1/M along j, 1/N along i):
+ *   theta_x  ~ (t[j+1] - t[j-1]) M / 2,          theta_xx ~ (t[j+1] - 2 t + t[j-1]) M^2,
+ *   theta_xy ~ (t[+1,+1] - t[+1,-1] - t[-1,+1] + t[-1,-1]) N M / 4   (offsets (di, dj)).
+ * Row r of the matrix A holds, at column r + (di, dj), the weight of that neighbour.  The
+ * extra equation sum_k x_k = 0 (int theta = 0) added to every row and then dropped gives
+ * A~ = A + 1 1^T (every entry of A~ is the entry of A plus one). */
+#define FD_TAPS 9
+static void fd_row(const double *coef, long P, long r, int N, int M, double w[FD_TAPS]) {
+  /* weights of row r at the 3 x 3 offsets, index (di + 1) * 3 + (dj + 1) */
+  double a11 = coef[r], a12 = coef[P + r], a22 = coef[2 * P + r];
+  double b1 = coef[3 * P + r], b2 = coef[4 * P + r];
+  double m2 = (double)M * M, n2 = (double)N * N, xy = 2.0 * a12 * (double)N * M / 4.0;
+  for (int t = 0; t < FD_TAPS; ++t) w[t] = 0.0;
+  w[4] += -2.0 * a11 * m2 - 2.0 * a22 * n2;
+  w[3] += a11 * m2 - b1 * 0.5 * M;  /* (0, -1) */
+  w[5] += a11 * m2 + b1 * 0.5 * M;  /* (0, +1) */
+  w[1] += a22 * n2 - b2 * 0.5 * N;  /* (-1, 0) */
+  w[7] += a22 * n2 + b2 * 0.5 * N;  /* (+1, 0) */
+  w[8] += xy;                       /* (+1, +1) */
+  w[6] -= xy;                       /* (+1, -1) */
+  w[2] -= xy;                       /* (-1, +1) */
+  w[0] += xy;                       /* (-1, -1) */
+}
+
+/* y = A~ x: each row of A applied to x (gather), plus sum(x). */
+void orc_fd_apply(const double *coef, const double *x, int N, int M, double *y) {
+  long P = (long)N * M;
+  double sx = 0.0;
+  for (long k = 0; k < P; ++k) sx += x[k];
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < M; ++j) {
+      long r = (long)i * M + j;
+      double w[FD_TAPS], acc = 0.0;
+      fd_row(coef, P, r, N, M, w);
+      for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj)
+          acc += w[(di + 1) * 3 + (dj + 1)] * x[wrap(i + di, N) * M + wrap(j + dj, M)];
+      y[r] = acc + sx;
+    }
+}
+
+/* y = A~^T x: every row r of A scatters its weight times x[r] onto the columns it touches
+ * (sum_r A[r][k] x[r]), plus sum(x) (the all-ones part is symmetric). */
+void orc_fd_apply_t(const double *coef, const double *x, int N, int M, double *y) {
+  long P = (long)N * M;
+  double sx = 0.0;
+  for (long k = 0; k < P; ++k) {
+    sx += x[k];
+    y[k] = 0.0;
+  }
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < M; ++j) {
+      long r = (long)i * M + j;
+      double w[FD_TAPS];
+      fd_row(coef, P, r, N, M, w);
+      for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj)
+          y[wrap(i + di, N) * M + wrap(j + dj, M)] += w[(di + 1) * 3 + (dj + 1)] * x[r];
+    }
+  for (long k = 0; k < P; ++k) y[k] += sx;
+}
+
+/* Biconjugate gradients without preconditioning (Sec. 4.1; Fletcher's form as in Saad,
+ * Iterative Methods for Sparse Linear Systems, Alg. 7.3) for A x = b from x = 0 with the
+ * shadow residual r*_0 = r_0:
+ *   alpha = (r, r*) / (A p, p*);  x += alpha p;  r -= alpha A p;  r* -= alpha A^T p*;
+ *   beta = (r_new, r*_new) / (r, r*);  p = r + beta p;  p* = r* + beta p*.
+ * Stops when ||r||_2 <= eta ||b||_2, after max_iters iterations, or on breakdown (a zero
+ * denominator).  out: iters, relres = ||r|| / ||b||.  Returns 0 if converged, 1 if the
+ * iteration cap was reached, 2 on breakdown. */
+static int bicg(matvec_fn A, matvec_fn At, void *ctx, const double *b, long n, double eta,
+                int max_iters, double *x, int *iters, double *relres) {
+  double *r = (double *)malloc(sizeof(double) * n);
+  double *rs = (double *)malloc(sizeof(double) * n);
+  double *p = (double *)malloc(sizeof(double) * n);
+  double *ps = (double *)malloc(sizeof(double) * n);
+  double *q = (double *)malloc(sizeof(double) * n);
+  double *qs = (double *)malloc(sizeof(double) * n);
+  int rc = 1;
+  double bnorm = sqrt(dot(b, b, n));
+  for (long k = 0; k < n; ++k) {
+    x[k] = 0.0;
+    r[k] = rs[k] = p[k] = ps[k] = b[k];
+  }
+  *iters = 0;
+  *relres = 0.0;
+  if (bnorm == 0.0) {
+    rc = 0;
+    goto done;
+  }
+  double rho = dot(r, rs, n);
+  *relres = 1.0;
+  while (*iters < max_iters) {
+    A(ctx, p, q);
+    At(ctx, ps, qs);
+    double den = dot(q, ps, n);
+    if (den == 0.0) {
+      rc = 2;
+      break;
+    }
+    double alpha = rho / den;
+    for (long k = 0; k < n; ++k) {
+      x[k] += alpha * p[k];
+      r[k] -= alpha * q[k];
+      rs[k] -= alpha * qs[k];
+    }
+    (*iters)++;
+    double rnorm = sqrt(dot(r, r, n));
+    *relres = rnorm / bnorm;
+    if (rnorm <= eta * bnorm) {
+      rc = 0;
+      break;
+    }
+    double rho_new = dot(r, rs, n);
+    if (rho_new == 0.0) {
+      rc = 2;
+      break;
+    }
+    double beta = rho_new / rho;
+    rho = rho_new;
+    for (long k = 0; k < n; ++k) {
+      p[k] = r[k] + beta * p[k];
+      ps[k] = rs[k] + beta * ps[k];
+    }
+  }
+done:
+  free(r);
+  free(rs);
+  free(p);
+  free(ps);
+  free(q);
+  free(qs);
+  return rc;
+}
+
+static void dense_mv_t(void *ctx, const double *x, double *y) {
+  dense_ctx *d = (dense_ctx *)ctx;
+  for (long c = 0; c < d->n; ++c) {
+    double s = 0.0;
+    for (long r = 0; r < d->n; ++r) s += d->A[r * d->n + c] * x[r];
+    y[c] = s;
+  }
+}
+
+/* The BiCG routine on a dense row-major n x n matrix (pinned against a direct solve). */
+int orc_bicg_dense(const double *A, const double *b, int n, double eta, int max_iters,
+                   double *x, int *iters, double *relres) {
+  dense_ctx d = {A, n};
+  return bicg(dense_mv, dense_mv_t, &d, b, n, eta, max_iters, x, iters, relres);
+}
+
+typedef struct {
+  const double *coef;
+  int N, M;
+} fd_ctx;
+
+static void fd_mv(void *ctx, const double *x, double *y) {
+  fd_ctx *o = (fd_ctx *)ctx;
+  orc_fd_apply(o->coef, x, o->N, o->M, y);
+}
+static void fd_mv_t(void *ctx, const double *x, double *y) {
+  fd_ctx *o = (fd_ctx *)ctx;
+  orc_fd_apply_t(o->coef, x, o->N, o->M, y);
+}
+
+/* BiCG on A~ theta = h (Sec. 4.1). */
+int orc_bicg_fd(const double *coef, const double *h, int N, int M, double eta, int max_iters,
+                double *theta, int *iters, double *relres) {
+  fd_ctx o = {coef, N, M};
+  return bicg(fd_mv, fd_mv_t, &o, h, (long)N * M, eta, max_iters, theta, iters, relres);
+}
+
+/* Linear solver of the Newton steps: 0 (default) the Fourier method of Sec. 4.2, 1 the
+ * finite-difference system with BiCG of Sec. 4.1 (at most max_iters iterations per step). */
+static int g_linsolver = 0, g_max_bicg = 20000;
+void orc_set_linear_solver(int mode, int max_iters) {
+  g_linsolver = mode == 1 ? 1 : 0;
+  g_max_bicg = max_iters > 0 ? max_iters : 20000;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Damped Newton (Sec. 3.1, Eq. linma) with the Fourier implementation of Sec. 4.2          */
 /* ------------------------------------------------------------------------------------ */
 
@@ -965,12 +1154,18 @@ int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_op
     for (long p = 0; p < P; ++p) h[p] = F[p] / tau;
     int it, cy;
     double rr;
-    orc_gmres_op(coef, abar, h, N, M, o->restart, o->eta, o->max_restarts, sigma, &it, &cy,
-                 &rr);
+    if (g_linsolver == 1) {
+      /* Sec. 4.1: the augmented finite-difference system, BiCG from theta = 0 */
+      orc_bicg_fd(coef, h, N, M, o->eta, g_max_bicg, theta, &it, &rr);
+      cy = 1;
+    } else {
+      orc_gmres_op(coef, abar, h, N, M, o->restart, o->eta, o->max_restarts, sigma, &it, &cy,
+                   &rr);
+      orc_apply_lbar_inv(abar, sigma, N, M, theta);
+    }
     st->gmres_iters += it;
     st->gmres_cycles += cy;
     if (hist_gmres) hist_gmres[n] = it;
-    orc_apply_lbar_inv(abar, sigma, N, M, theta);
     for (;;) {
       for (long p = 0; p < P; ++p) cand[p] = u[p] + s * theta[p];
       orc_residual(f, c, cand, N, M, F, coef, scal);

@@ -63,6 +63,15 @@ int orc_gmres_dense(const double *A, const double *b, int n, int m, double eta,
 int orc_gmres_op(const double *coef, const double abar[5], const double *h, int N, int M, int m,
                  double eta, int max_restarts, double *sigma, int *iters, int *cycles,
                  double *relres);
+/* Sec. 4.1: y = A~ x and y = A~^T x for the second-order finite-difference operator with the
+ * augmented row sum; BiCG on dense systems and on A~ theta = h; the Newton steps' solver */
+void orc_fd_apply(const double *coef, const double *x, int N, int M, double *y);
+void orc_fd_apply_t(const double *coef, const double *x, int N, int M, double *y);
+int orc_bicg_dense(const double *A, const double *b, int n, double eta, int max_iters,
+                   double *x, int *iters, double *relres);
+int orc_bicg_fd(const double *coef, const double *h, int N, int M, double eta, int max_iters,
+                double *theta, int *iters, double *relres);
+void orc_set_linear_solver(int mode, int max_iters);
 int orc_solve(const double *f_in, const double *g_in, int N, int M, const orc_opts *o,
               double *u, orc_stats *st, double *hist_res, int *hist_gmres);
 
