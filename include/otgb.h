@@ -133,6 +133,19 @@ extern "C" {
                                    differences (then no prefilter: ot_prefilter copies g and
                                    ot_eval_residual takes g for c); not with the learned warm
                                    start (OT_EINVAL) nor in plan sets */
+#define OT_OPT_LINEAR_SOLVER 26 /* linear solver of the Newton steps: 0 (default) the Fourier
+                                   method of Sec. 4.2 (Strain's preconditioned GMRES(m)); 1 the
+                                   paper's comparison path of Sec. 4.1: second-order centred
+                                   differences of theta, the extra equation sum theta = 0
+                                   added to every row (A~ = A + 1 1^T), unpreconditioned BiCG
+                                   from theta = 0 to ||r|| <= eta ||b||.  FP64 only (OT_EINVAL
+                                   in the mixed mode, and OPT_PRECISION = 1 is refused while it
+                                   is set); the solve then runs host-driven whatever
+                                   OT_OPT_GRAPH says (the state read once per 16 iterations);
+                                   gmres_iters / gmres_cycles of ot_stats count BiCG iterations
+                                   and BiCG runs, and its launches are profiled as
+                                   OT_PROF_GMRES_OTHER.  Setting 1 allocates 7 FP64 planes */
+#define OT_OPT_MAX_BICG 27      /* BiCG iterations per Newton step, >= 1 (default 20000) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,
@@ -333,6 +346,21 @@ int ot_fft_inverse(ot_plan* plan, const double* spec, double* x);
  * round-off 2^-48).  OT_EINVAL for null f, phi or dist or an unready plan. */
 int ot_transport_outputs(ot_plan* plan, const double* f, const double* phi, double* dist,
                          double* div_out);
+
+/* Finite-difference comparison path (Sec. 4.1), step level; both need OT_OPT_LINEAR_SOLVER
+ * = 1 on the plan (else OT_EINVAL).  coef: device, the 5 coefficient planes of
+ * ot_eval_residual (a11, a12, a22, b1, b2).
+ * ot_fd_apply: y = A~ x (transpose = 0) or A~^T x (1), A the second-order centred-difference
+ * discretisation of a11 d_xx + 2 a12 d_xy + a22 d_yy + b1 d_x + b2 d_y, A~ = A + 1 1^T; x, y:
+ * device N x M.
+ * ot_fd_bicg: theta (device, written) from A~ theta = h (device) by BiCG from 0, stopping at
+ * ||r||_2 <= eta ||h||_2 or after max_iters iterations; iters, relres (HOST, may be NULL):
+ * the iterations run and ||r|| / ||h||.  OT_OK when converged, OT_ENOCONV at the cap,
+ * OT_EDIVERGED on a breakdown (a zero BiCG denominator).  Uses the plan's workspace. */
+int ot_fd_apply(ot_plan* plan, const double* coef, const double* x, int32_t transpose,
+                double* y);
+int ot_fd_bicg(ot_plan* plan, const double* coef, const double* h, double eta,
+               int32_t max_iters, double* theta, int32_t* iters, double* relres);
 
 /* Spectral radius of the inverse of the discretised linearised operator at the iterate phi
  * (the stability measure of Sec. 5.1, about 0.03 in the paper's experiments), by the power

@@ -24,6 +24,7 @@ OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11,
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
 OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
 OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH, OT_OPT_INTERP = 22, 23, 24, 25
+OT_OPT_LINEAR_SOLVER, OT_OPT_MAX_BICG = 26, 27
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -39,7 +40,7 @@ EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_pla
            "ot_ws_trainer_grad", "ot_ws_trainer_step", "ot_ws_trainer_get_params",
            "ot_ws_trainer_destroy", "ot_solve_plans", "ot_plan_set_create",
            "ot_batch_set_option", "ot_batch_set_stream", "ot_plan_set_destroy",
-           "ot_inverse_spectral_radius"]
+           "ot_inverse_spectral_radius", "ot_fd_apply", "ot_fd_bicg"]
 
 
 class ot_stats(ctypes.Structure):
@@ -86,6 +87,8 @@ def _load():
         "ot_batch_set_stream": ([vp, vp], ctypes.c_int),
         "ot_plan_set_destroy": ([vp], None),
         "ot_inverse_spectral_radius": ([vp, vp, vp, vp, vp, i32, vp], ctypes.c_int),
+        "ot_fd_apply": ([vp, vp, vp, i32, vp], ctypes.c_int),
+        "ot_fd_bicg": ([vp, vp, vp, d, i32, vp, vp, vp], ctypes.c_int),
         "ot_plan_destroy": ([vp], None),
         "ot_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "ot_prefilter": ([vp, vp, vp], ctypes.c_int),
@@ -194,6 +197,16 @@ def ot_plan_set_destroy(pset):
 def ot_inverse_spectral_radius(plan, f_ptr, g_ptr, phi_ptr, b0_ptr, iters, rho_host_ptr):
     return _lib.ot_inverse_spectral_radius(plan, f_ptr, g_ptr, phi_ptr, b0_ptr, int(iters),
                                            rho_host_ptr)
+
+
+def ot_fd_apply(plan, coef_ptr, x_ptr, transpose, y_ptr):
+    return _lib.ot_fd_apply(plan, coef_ptr, x_ptr, int(transpose), y_ptr)
+
+
+def ot_fd_bicg(plan, coef_ptr, h_ptr, eta, max_iters, theta_ptr, iters_host_ptr,
+               relres_host_ptr):
+    return _lib.ot_fd_bicg(plan, coef_ptr, h_ptr, float(eta), int(max_iters), theta_ptr,
+                           iters_host_ptr, relres_host_ptr)
 
 
 def ot_plan_destroy(plan):
@@ -411,7 +424,8 @@ class Plan:
              "forcing": OT_OPT_FORCING, "tau_retry": OT_OPT_TAU_RETRY,
              "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR,
              "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT,
-             "tau_switch": OT_OPT_TAU_SWITCH, "interp": OT_OPT_INTERP}
+             "tau_switch": OT_OPT_TAU_SWITCH, "interp": OT_OPT_INTERP,
+             "linear_solver": OT_OPT_LINEAR_SOLVER, "max_bicg": OT_OPT_MAX_BICG}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)
@@ -525,6 +539,24 @@ class Plan:
                                           ctypes.c_void_p(rho.ctypes.data)),
                "ot_inverse_spectral_radius")
         return rho
+
+    def fd_apply(self, coef, x, y, transpose=False):
+        """y = A~ x or A~^T x, the finite-difference operator of Sec. 4.1 (needs
+        linear_solver=1); coef: device (5, N, M)."""
+        shp = (self.N, self.M)
+        _check(ot_fd_apply(self.h, _dev(coef, (5,) + shp), _dev(x, shp), int(bool(transpose)),
+                           _dev(y, shp)), "ot_fd_apply")
+
+    def fd_bicg(self, coef, h, theta, eta=1e-4, max_iters=20000):
+        """BiCG on A~ theta = h (Sec. 4.1): returns (status, iterations, ||r|| / ||h||)."""
+        shp = (self.N, self.M)
+        it = ctypes.c_int32()
+        rr = ctypes.c_double()
+        rc = ot_fd_bicg(self.h, _dev(coef, (5,) + shp), _dev(h, shp), eta, max_iters,
+                        _dev(theta, shp), ctypes.byref(it), ctypes.byref(rr))
+        if rc not in (OT_OK, OT_ENOCONV, OT_EDIVERGED):
+            _check(rc, "ot_fd_bicg")
+        return rc, it.value, rr.value
 
     def transport_outputs(self, f, phi, div=None):
         """d(f, g) = mean |grad phi|^2 f (Sec. 5.2); fills div (device N x M) with

@@ -53,6 +53,11 @@ struct ot_plan {
   int interp = 0;
   double* gxy = nullptr;
   float* gxy32 = nullptr;
+  // OT_OPT_LINEAR_SOLVER = 1: the finite-difference system of Sec. 4.1 with BiCG (FP64,
+  // host-driven); its 7 vector planes and the iteration cap OT_OPT_MAX_BICG
+  int linsolver = 0;
+  int max_bicg = 20000;
+  double* fdv = nullptr;
   int op_simple = 0;  // OT_OPT_OPERATOR: 1 drops the grad g term of the linearisation
   int ws_stall = 0;   // OT_OPT_WS_TEST_STALL: the next ot_ws_mlp_forward stalls (test hook)
   // mixed mode: f and the B-spline coefficients as (hi, lo) float pairs (double-float
@@ -341,8 +346,10 @@ static void free_buffers(ot_plan* p) {
   if (p->hinit) cudaFreeHost(p->hinit);
   if (p->gxy) cudaFree(p->gxy);
   if (p->gxy32) cudaFree(p->gxy32);
+  if (p->fdv) cudaFree(p->fdv);
   p->gxy = nullptr;
   p->gxy32 = nullptr;
+  p->fdv = nullptr;
   p->hinit = nullptr;
   p->f = p->g = p->c = p->u = p->ucand = p->Fraw = nullptr;
   p->coef = p->V = p->w = p->sigma = p->spec = p->q0 = p->q1 = p->q2 = nullptr;
@@ -517,6 +524,7 @@ static int alloc_tables(ot_plan* p) {
 }
 
 static int alloc_grad_planes(ot_plan* p);
+static int alloc_fd_planes(ot_plan* p);
 
 static int alloc_buffers(ot_plan* p) {
   free_buffers(p);
@@ -550,6 +558,7 @@ static int alloc_buffers(ot_plan* p) {
   }
   RET(alloc_tables(p));
   if (p->interp) RET(alloc_grad_planes(p));
+  if (p->linsolver) RET(alloc_fd_planes(p));
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
   size_t nk = (size_t)p->kblocks * OTGB_MAXM;
   if (nk > np) np = nk;
@@ -563,6 +572,18 @@ static int alloc_buffers(ot_plan* p) {
   memset(p->hinit, 0, sizeof(DevScalars));
   p->ready = true;
   return OT_OK;
+}
+
+// the BiCG vectors of the finite-difference path: x, r, r*, p, p*, q, q* (FP64 planes)
+static int alloc_fd_planes(ot_plan* p) {
+  const size_t P = (size_t)p->N * p->M;
+  CK(cudaMalloc(&p->fdv, 7 * P * sizeof(double)));
+  return OT_OK;
+}
+static FdBufs fdbufs(const ot_plan* p) {
+  const size_t P = (size_t)p->N * p->M;
+  double* b = p->fdv;
+  return FdBufs{b, b + P, b + 2 * P, b + 3 * P, b + 4 * P, b + 5 * P, b + 6 * P};
 }
 
 // grid-gradient planes of g for the nearest / bilinear interpolation modes
@@ -683,6 +704,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       return OT_OK;
     case OT_OPT_PRECISION: {
       if (v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && p->linsolver) return OT_EINVAL;  // the FD path is FP64
       if ((int)v != p->precision) {
         p->precision = (int)v;
         return alloc_buffers(p);
@@ -788,6 +810,16 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       }
       if (p->interp && p->ready && !p->gxy) RET(alloc_grad_planes(p));
       return OT_OK;
+    case OT_OPT_LINEAR_SOLVER:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && p->precision) return OT_EINVAL;
+      p->linsolver = (int)v;
+      if (p->linsolver && p->ready && !p->fdv) RET(alloc_fd_planes(p));
+      return OT_OK;
+    case OT_OPT_MAX_BICG:
+      if (v < 1 || v > 1e9 || v != (double)(int)v) return OT_EINVAL;
+      p->max_bicg = (int)v;
+      return OT_OK;
     case OT_OPT_PHASE_TIMES:
       if (v != 0 && v != 1) return OT_EINVAL;
       if (p->phase_times != (int)v) {
@@ -842,6 +874,8 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_PHASE_TIMES: *v = p->phase_times; return OT_OK;
     case OT_OPT_TAU_SWITCH: *v = p->tau_switch; return OT_OK;
     case OT_OPT_INTERP: *v = p->interp; return OT_OK;
+    case OT_OPT_LINEAR_SOLVER: *v = p->linsolver; return OT_OK;
+    case OT_OPT_MAX_BICG: *v = p->max_bicg; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -1316,6 +1350,26 @@ static int run_warmstart(ot_plan* p, double* u, int stall = 0) {
   return OT_OK;
 }
 
+// theta of a Newton step from the finite-difference system of Sec. 4.1 (A~ theta = h, h =
+// (f - f~_n) / tau unless given) by BiCG from theta = 0, into fdbufs(p).x: the iterations run
+// in chunks of self-skipping launches, with the state read once per chunk
+static constexpr int kBicgChunk = 16;
+static int run_bicg(ot_plan* p, const double* h) {
+  const long P = (long)p->N * p->M;
+  const FdBufs b = fdbufs(p);
+  LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
+         launch_bicg_init(p->Fraw, h, b, P, p->partials, p->sc, p->max_bicg, p->stream));
+  for (;;) {
+    for (int k = 0; k < kBicgChunk; ++k)
+      LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 3,
+             launch_bicg_iteration((const double*)p->coef, b, p->N, p->M, p->partials, p->sc,
+                                   p->stream));
+    RET(read_scalars(p));
+    if (p->hsc->bicg_done) break;
+  }
+  return OT_OK;
+}
+
 template <typename T>
 static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double* phi,
                       ot_stats* st) {
@@ -1394,13 +1448,23 @@ static int solve_impl(ot_plan* p, const double* f_in, const double* g_in, double
                          p->stream));
       tau_one = true;
     }
-    int rc = run_gmres<T>(p);
-    if (rc != OT_OK) return rc;
-    st->gmres_iters += p->hsc->iters;
-    st->gmres_cycles += p->hsc->cycles;
+    if (p->linsolver) {
+      RET(run_bicg(p, nullptr));
+      st->gmres_iters += p->hsc->bicg_iters;
+      st->gmres_cycles += 1;
+    } else {
+      int rc = run_gmres<T>(p);
+      if (rc != OT_OK) return rc;
+      st->gmres_iters += p->hsc->iters;
+      st->gmres_cycles += p->hsc->cycles;
+    }
     bool accepted = false;
     for (;;) {
-      RET(run_theta<T>(p, p->u, p->ucand, s, false));
+      if (p->linsolver)
+        LAUNCH(p, OT_PROF_ROW_C2R_UPDATE, -1, 1,
+               launch_axpy_to(p->u, fdbufs(p).x, s, p->ucand, P, p->stream));
+      else
+        RET(run_theta<T>(p, p->u, p->ucand, s, false));
       LAUNCH(p, OT_PROF_RESIDUAL, -1, 1,
              residual_launch<T>(p, p->f, p->c, p->ucand, p->Fraw, nullptr, 0));
       RET(read_scalars(p));
@@ -1911,9 +1975,16 @@ static int host_solve(ot_plan* p, const double* f, const double* g, double* phi,
   return rc;
 }
 
+// A solve through the captured graph (else host-driven): the graph option on, no profile,
+// and not the finite-difference comparison path, which runs host-driven (one read per BiCG
+// chunk)
+static bool graph_path(const ot_plan* p) {
+  return p->use_graph && !p->profile && !p->linsolver;
+}
+
 static int solve_once(ot_plan* p, const double* f, const double* g, double* phi,
                       ot_stats* st) {
-  if (p->use_graph && !p->profile)
+  if (graph_path(p))
     return p->precision ? solve_graph_impl<float>(p, f, g, phi, st)
                         : solve_graph_impl<double>(p, f, g, phi, st);
   return host_solve(p, f, g, phi, st);
@@ -1950,7 +2021,7 @@ extern "C" int ot_solve_host(ot_plan* p, const double* f, const double* g, doubl
   // stage f, g in the plan's translated-density buffers (translated in place)
   CK(cudaMemcpyAsync(p->f, f, bytes, cudaMemcpyHostToDevice, p->stream));
   CK(cudaMemcpyAsync(p->g, g, bytes, cudaMemcpyHostToDevice, p->stream));
-  const bool graph = p->use_graph && !p->profile;
+  const bool graph = graph_path(p);
   if (p->warm_start == 1)
     CK(cudaMemcpyAsync(graph ? p->uout : p->u, phi, bytes, cudaMemcpyHostToDevice, p->stream));
   int rc;
@@ -2003,7 +2074,7 @@ extern "C" int ot_solve_plans(int32_t count, ot_plan* const* plans, const double
   // graphs, initial scalars and ordering after each plan's own stream
   for (auto p : uniq) {
     CK(cudaSetDevice(p->device));
-    if (!p->use_graph || p->profile) continue;
+    if (!graph_path(p)) continue;
     RET(p->precision ? ensure_graph<float>(p) : ensure_graph<double>(p));
     graph_scalars(p, p->hinit);
     cudaEvent_t e;
@@ -2016,7 +2087,7 @@ extern "C" int ot_solve_plans(int32_t count, ot_plan* const* plans, const double
   for (int k = 0; k < count; ++k) {
     ot_plan* p = plans[k];
     CK(cudaSetDevice(p->device));
-    if (!p->use_graph || p->profile) {  // host-driven plans: one after another
+    if (!graph_path(p)) {  // host-driven plans: one after another
       ot_stats tmp;
       int rc = ot_solve(p, f[k], g[k], phi[k], &tmp);
       g_batch_slots[k].status = rc;
@@ -2032,11 +2103,11 @@ extern "C" int ot_solve_plans(int32_t count, ot_plan* const* plans, const double
   }
   for (auto p : uniq) {
     CK(cudaSetDevice(p->device));
-    if (p->use_graph && !p->profile) CK(cudaStreamSynchronize(p->cs[0]));
+    if (graph_path(p)) CK(cudaStreamSynchronize(p->cs[0]));
   }
   for (int k = 0; k < count; ++k) {
     ot_plan* p = plans[k];
-    if (p->use_graph && !p->profile) {
+    if (graph_path(p)) {
       ot_stats tmp;
       memset(&tmp, 0, sizeof(tmp));
       graph_collect(p, &g_batch_slots[k], g_batch_means[k], &tmp);
@@ -2846,6 +2917,46 @@ static int inverse_radius_impl(ot_plan* p, const double* f, const double* g, con
     std::swap(b, th);
   }
   return OT_OK;
+}
+
+// ---- finite-difference comparison path (Sec. 4.1), step level ---------------------------
+extern "C" int ot_fd_apply(ot_plan* p, const double* coef, const double* x, int32_t transpose,
+                           double* y) {
+  if (!p || !p->ready || !coef || !x || !y || (transpose != 0 && transpose != 1))
+    return OT_EINVAL;
+  if (!p->fdv) return OT_EINVAL;  // OT_OPT_LINEAR_SOLVER = 1 allocates the vectors
+  CK(cudaSetDevice(p->device));
+  CK(cudaMemsetAsync(&p->sc->bicg_done, 0, sizeof(int), p->stream));
+  CK(cudaMemsetAsync(&p->sc->bicg_rho, 0, sizeof(double), p->stream));
+  CK(launch_fd_apply(coef, x, transpose, y, fdbufs(p).q, p->N, p->M, p->partials, p->sc,
+                     p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  return OT_OK;
+}
+
+extern "C" int ot_fd_bicg(ot_plan* p, const double* coef, const double* h, double eta,
+                          int32_t max_iters, double* theta, int32_t* iters, double* relres) {
+  if (!p || !p->ready || !coef || !h || !theta || !(eta >= 0.0) || max_iters < 1)
+    return OT_EINVAL;
+  if (!p->fdv) return OT_EINVAL;
+  CK(cudaSetDevice(p->device));
+  const long P = (long)p->N * p->M;
+  // the plan's coefficient planes and eta are the solve's: stage them
+  CK(cudaMemcpyAsync(p->coef, coef, 5 * P * sizeof(double), cudaMemcpyDeviceToDevice,
+                     p->stream));
+  CK(cudaMemcpyAsync(&p->sc->eta, &eta, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  const int keep = p->max_bicg;
+  p->max_bicg = max_iters;
+  const int rc = run_bicg(p, h);
+  p->max_bicg = keep;
+  RET(rc);
+  CK(cudaMemcpyAsync(theta, fdbufs(p).x, P * sizeof(double), cudaMemcpyDeviceToDevice,
+                     p->stream));
+  RET(read_scalars(p));
+  const DevScalars* hs = p->hsc;
+  if (iters) *iters = hs->bicg_iters;
+  if (relres) *relres = hs->bicg_b2 > 0.0 ? sqrt(hs->bicg_r2 / hs->bicg_b2) : 0.0;
+  return hs->bicg_status == 0 ? OT_OK : (hs->bicg_status == 1 ? OT_ENOCONV : OT_EDIVERGED);
 }
 
 extern "C" int ot_inverse_spectral_radius(ot_plan* p, const double* f, const double* g,

@@ -80,8 +80,13 @@ struct DevScalars {
   int excluded;       // the pair sits out this launch of the batched graph (a retry of others)
   double gauge_mean;  // mean removed by the final gauge of a batched solve
   double pw_norm;     // 2-norm of the last vector normalised by launch_normalize
+  // BiCG on the finite-difference system (Sec. 4.1): rho = (r, r*), alpha, beta, ||b||^2,
+  // ||r||^2, the sums of p and p* (the all-ones part of A~ = A + 1 1^T); status 0 converged,
+  // 1 iteration cap, 2 breakdown; done stops the self-skipping iteration kernels
+  double bicg_rho, bicg_alpha, bicg_beta, bicg_b2, bicg_r2, bicg_sp, bicg_sps;
+  int bicg_done, bicg_iters, bicg_max, bicg_status;
   // ticket counters of the last-block reductions
-  unsigned int ticket[8];
+  unsigned int ticket[12];
 };
 // phases of OT_OPT_PHASE_TIMES
 enum { PH_RESIDUAL = 0, PH_FFT = 1, PH_KRYLOV = 2, PH_UPDATE = 3, PH_OTHER = 4, PH_COUNT = 5 };
@@ -138,7 +143,8 @@ enum {
   TK_INIT = 4,
   TK_NORM = 5,
   TK_WS = 6,
-  TK_TRANSPORT = 7
+  TK_TRANSPORT = 7,
+  TK_BICG = 8
 };
 
 // Spectral kernels (instantiated for float and double) --------------------------------
@@ -293,6 +299,25 @@ cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* parti
 // x <- x / ||x||_2 (two launches: the norm into sc->pw_norm, then the scaling; x = 0 stays 0)
 cudaError_t launch_normalize(double* x, long P, double* partials, DevScalars* sc,
                              cudaStream_t st);
+// Finite-difference comparison path (Sec. 4.1): the BiCG vectors (FP64 planes) ...
+struct FdBufs {
+  double *x, *r, *rs, *p, *ps, *q, *qs;
+};
+// ... set up from b = h (when given) or (F_raw + shift) / tau, x = 0 ...
+cudaError_t launch_bicg_init(const double* Fraw, const double* h, FdBufs b, long P,
+                             double* partials, DevScalars* sc, int max_iters,
+                             cudaStream_t st);
+// ... and one BiCG iteration on A~ x = b (three launches that skip themselves once
+// sc->bicg_done is set); coef: the residual's 5 coefficient planes
+cudaError_t launch_bicg_iteration(const double* coef, FdBufs b, int N, int M,
+                                  double* partials, DevScalars* sc, cudaStream_t st);
+// y = A~ x or A~^T x (tmp: a scratch plane; needs sc->bicg_done = 0)
+cudaError_t launch_fd_apply(const double* coef, const double* x, int transpose, double* y,
+                            double* tmp, int N, int M, double* partials, DevScalars* sc,
+                            cudaStream_t st);
+// u_out = u_in + s theta
+cudaError_t launch_axpy_to(const double* u_in, const double* th, double s, double* u_out,
+                           long P, cudaStream_t st);
 // batched solve: dst (pair 0's plane, advanced by the slab per pair) <- tab[pair]; and the
 // reverse (tab[pair] <- src of pair), skipping excluded pairs (sc: pair 0's scalars)
 cudaError_t launch_gather(const double* const* tab, double* dst, long P, Bat bat,

@@ -1,0 +1,138 @@
+"""GPU parity of the finite-difference comparison path (Sec. 4.1) against the oracle: the
+operator A~ = A + 1 1^T and its transpose, the BiCG solve of A~ theta = h, and the Newton
+solve with OT_OPT_LINEAR_SOLVER = 1.
+
+Bounds: the operator is a 9-point stencil sum in FP64 (the oracle gathers A x and scatters
+A^T x, the kernel gathers both, so the summation order differs): a few ulps of the largest
+term, coef_max (M^2 + N^2 + M N) x_max, plus the row sum's P ulps.  BiCG results are compared
+through what defines them: both solutions satisfy ||A~ theta - h|| <= eta ||h|| (checked with
+the oracle's operator), so ||A~ (theta_gpu - theta_oracle)|| <= 2 eta ||h||; BiCG's iteration
+count follows round-off on the rougher systems and is compared within 25 %.
+The Newton root is unique (F alone defines it): 1e-10 as for the Fourier path.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import ot_inputs as I
+from gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ot():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1009_6039_gb300 as m
+    return m
+
+
+def coefficients(N, M, s=31):
+    # the coefficients of a real residual evaluation (a blob pair at a small iterate)
+    f, g = I.blob_pair(N, M, s=s)
+    c = O.bspline_coeffs(g)
+    u = 2e-4 * I.SplitMix64(s + 1).uniform(N * M).reshape(N, M)
+    u -= u.mean()
+    F, coef, _ = O.residual(f, c, u)
+    return coef, F
+
+
+@pytest.mark.parametrize("N,M", [(8, 16), (32, 32), (48, 96), (256, 256), (12, 512)])
+def test_fd_operator_and_transpose(ot, N, M):
+    coef, _ = coefficients(N, M)
+    x = I.SplitMix64(7).uniform(N * M).reshape(N, M) - 0.3
+    p = ot.Plan(N, M, precision="fp64", linear_solver=1)
+    cd, xd = dev(coef), dev(x)
+    scale = np.abs(coef).max() * (M * M + N * N + M * N) * np.abs(x).max()
+    for tr in (False, True):
+        y = dev(np.zeros((N, M)))
+        p.fd_apply(cd, xd, y, transpose=tr)
+        ref = O.fd_apply(coef, x, transpose=tr)
+        err = np.abs(y.cpu().numpy() - ref).max()
+        assert err <= 64 * 2.0 ** -52 * (scale + N * M * np.abs(x).max()), (tr, err, scale)
+    p.close()
+
+
+@pytest.mark.parametrize("case,N", [("manufactured", 32), ("noise", 64), ("manufactured", 128),
+                                    ("noise", 128)])
+def test_fd_bicg_matches_oracle(ot, case, N):
+    # Newton-step systems: the manufactured pair at half its solution (tau = 2) and the
+    # noise + blob pair at u = 0 (tau = 1)
+    if case == "manufactured":
+        f, g, phi = I.manufactured(N, N)
+        F, coef, _ = O.residual(f, O.bspline_coeffs(g), 0.5 * phi)
+        h = F / 2.0
+    else:
+        f, g = I.noise_blob_pair(N, N, s=3000)
+        F, coef, _ = O.residual(f, O.bspline_coeffs(g), np.zeros((N, N)))
+        h = F
+    eta = 1e-8
+    ref, st_ref = O.bicg_fd(coef, h, eta=eta, max_iters=20000)
+    assert st_ref["status"] == 0
+    p = ot.Plan(N, N, precision="fp64", linear_solver=1)
+    th = dev(np.zeros((N, N)))
+    rc, it, rr = p.fd_bicg(dev(coef), dev(h), th, eta=eta, max_iters=20000)
+    assert rc == ot.OT_OK and rr <= eta
+    t = th.cpu().numpy()
+    hn = np.linalg.norm(h)
+    # the GPU's theta solves the system to eta by the oracle's own operator (the recursive
+    # residual BiCG tests and the true one agree to within a few 1e-9 here), and the two
+    # solutions differ by no more than their residuals allow
+    assert np.linalg.norm(O.fd_apply(coef, t) - h) / hn <= 2 * eta
+    assert np.linalg.norm(O.fd_apply(coef, t - ref)) / hn <= 4 * eta
+    # unpreconditioned BiCG converges erratically on the noise pair's systems, and its
+    # count follows round-off (the oracle itself takes 860 iterations on x86-64 and 971 on
+    # aarch64 at 128^2, from inputs that differ in the last bits): compared within 25 %
+    assert abs(it - st_ref["iters"]) <= max(3, st_ref["iters"] // 4), (it, st_ref["iters"])
+    # the iteration cap
+    rc, it, rr = p.fd_bicg(dev(coef), dev(h), th, eta=eta, max_iters=3)
+    _, st3 = O.bicg_fd(coef, h, eta=eta, max_iters=3)
+    assert rc == ot.OT_ENOCONV and it == 3 and st3["status"] == 1
+    p.close()
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_fd_newton_solve_matches_oracle(ot, graph):
+    # the manufactured pair (tau = 2) and a blob pair with the safeguard (tau = 4): the
+    # Newton steps with theta from the finite-difference system reach the oracle's root with
+    # its Newton count; the graph option is ignored (the FD path runs host-driven)
+    cases = [(I.manufactured(32, 32)[:2], 2.0), (I.blob_pair(32, 32, s=1000), 4.0)]
+    for (f, g), tau in cases:
+        with O.fd_bicg():
+            u_ref, st_ref, _, _ = O.solve(f, g, tau=tau, tol=1e-10, eta=1e-4, max_newton=400)
+        assert st_ref["status"] == 0
+        p = ot.Plan(32, 32, precision="fp64", tau=tau, tol=1e-10, eta=1e-4, max_newton=400,
+                    linear_solver=1, graph=graph)
+        phi = dev(np.zeros((32, 32)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["res_inf"] < 1e-10
+        # BiCG stops at eta = 1e-4, so round-off moves theta at that level and a long
+        # safeguarded run (the blob pair: 124 steps) may take a slightly different path
+        assert abs(st["newton_iters"] - st_ref["newton_iters"]) <= 3
+        assert abs(st["step_halvings"] - st_ref["step_halvings"]) <= 2
+        assert abs(st["gmres_iters"] - st_ref["gmres_iters"]) <= 0.1 * st_ref["gmres_iters"]
+        assert st["gmres_cycles"] == st["newton_iters"]
+        assert np.abs(phi.cpu().numpy() - u_ref).max() <= 1e-10
+
+
+def test_fd_option_rules(ot):
+    p = ot.Plan(16, 16, precision="mixed")
+    assert ot.ot_plan_set_option(p.h, ot.OT_OPT_LINEAR_SOLVER, 1) == ot.OT_EINVAL
+    p.close()
+    p = ot.Plan(16, 16, precision="fp64", linear_solver=1)
+    assert ot.ot_plan_set_option(p.h, ot.OT_OPT_PRECISION, 1) == ot.OT_EINVAL
+    assert ot.ot_plan_set_option(p.h, ot.OT_OPT_MAX_BICG, 0) == ot.OT_EINVAL
+    assert p.get("linear_solver") == 1
+    p.close()
+    # the step-level calls need the option (its vectors)
+    p = ot.Plan(16, 16, precision="fp64")
+    z = dev(np.zeros((16, 16)))
+    c = dev(np.zeros((5, 16, 16)))
+    with pytest.raises(RuntimeError):
+        p.fd_apply(c, z, z)
+    p.close()
