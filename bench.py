@@ -68,6 +68,9 @@ def parse():
                          "autotuning; for profiler runs, where the autotuner's event timing is "
                          "distorted")
     ap.add_argument("--batch-pairs", type=int, default=512)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the warm-start evaluation, the Table 1 comparison and the "
+                         "spectral radius keys")
     return ap.parse_args()
 
 
@@ -491,6 +494,111 @@ def run_config2(ot, stream, flush, reps=3):
     return out
 
 
+def _timed_solve(p, fd, gd, phi, stream):
+    """One solve with CUDA events on the stream; returns (ms, stats)."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phi.zero_()
+    e0.record(stream)
+    rc, st = p.solve(fd, gd, phi)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), st
+
+
+C5_TRAIN_SEED = 20000
+C5_EVAL_SEED = 90000
+
+
+def run_config5(ot, stream, train_counts=(4, 16, 64), eval_pairs=8, fit_steps=1500):
+    """The learned warm start on the 256^2 blob-mixture generator: networks trained on
+    train_counts pairs (seeds 20000...) solved by this solver, evaluated on held-out pairs
+    (seeds 90000...) at 256^2 and 512^2 against the zero start of the same solve (mixed,
+    stencil symbols, tau = 1, eta = 0.1, tol 1e-8, as the batched workload); Newton steps,
+    GMRES iterations and device time per solve."""
+    import numpy as np
+    import torch
+    import ot_inputs as I
+    from paper_1009_6039_gb300 import warmstart as WS
+    settings = dict(tau=1.0, tol=1e-8, eta=0.1, symbols=1, max_newton=1000)
+    Ntr = 256
+    t0 = time.perf_counter()
+    train = [I.blob_pair(Ntr, Ntr, s=C5_TRAIN_SEED + k) for k in range(max(train_counts))]
+    X, t = WS.training_data(train, Ntr, Ntr, tau=1.0, tol=1e-8, eta=0.1, max_newton=1000,
+                            symbols=1)
+    t_data = time.perf_counter() - t0
+    rows_per_pair = Ntr * Ntr
+    nets = {}
+    for k in train_counts:
+        t1 = time.perf_counter()
+        nets[k] = WS.fit(X[:k * rows_per_pair], t[:k * rows_per_pair], steps=fit_steps,
+                         batch=32768, seed=1)
+        torch.cuda.synchronize()
+        nets[k] = (nets[k], time.perf_counter() - t1)
+    del X, t
+    out = {"generator": "blob_pair (config-2 densities)", "settings": "mixed, stencil symbols, "
+           "tau=1, eta=0.1, tol 1e-8; warm start = learned network + admissibility scale",
+           "train_size": Ntr, "train_seeds": "%d..%d" % (C5_TRAIN_SEED,
+                                                         C5_TRAIN_SEED + max(train_counts) - 1),
+           "eval_seeds": "%d..%d" % (C5_EVAL_SEED, C5_EVAL_SEED + eval_pairs - 1),
+           "fit_steps": fit_steps, "solve_and_features_s": round(t_data, 2),
+           "fit_s": {str(k): round(v[1], 2) for k, v in nets.items()}, "eval": {}}
+    for n in (256, 512):
+        pairs = [I.blob_pair(n, n, s=C5_EVAL_SEED + k) for k in range(eval_pairs)]
+        dev_pairs = [(torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()) for f, g in pairs]
+        phi = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        res = {}
+        for mode in ["zero"] + ["learned_%d_pairs" % k for k in train_counts]:
+            p = ot.Plan(n, n, precision="mixed", stream=stream, **settings)
+            if mode != "zero":
+                p.set_weights(nets[int(mode.split("_")[1])][0]).set(warm_start=2)
+            p.solve(dev_pairs[0][0], dev_pairs[0][1], phi)  # graph capture, autotune
+            ms, newton, gm, halv, conv = [], [], [], [], 0
+            for fd, gd in dev_pairs:
+                m, st = _timed_solve(p, fd, gd, phi, stream)
+                ms.append(m)
+                newton.append(st["newton_iters"])
+                gm.append(st["gmres_iters"])
+                halv.append(st["step_halvings"])
+                conv += st["status"] == 0
+            p.close()
+            res[mode] = {"ms_per_solve": round(float(np.mean(ms)), 3),
+                         "newton_iters_mean": float(np.mean(newton)),
+                         "gmres_iters_mean": float(np.mean(gm)),
+                         "step_halvings_mean": float(np.mean(halv)),
+                         "converged": "%d/%d" % (conv, eval_pairs)}
+        out["eval"]["%d" % n] = res
+    return out
+
+
+def run_table1(ot, stream, sizes=(16, 32, 64, 128, 256), steps=20):
+    """The experiment of Table 1 (Sec. 5.1) on the GPU in FP64: the manufactured example,
+    up to 20 Newton steps at tau = 1 with the linear solves to a relative tolerance of 0.1
+    (stopping at max|F| < 1e-12, past which the right-hand side is round-off), by the Fourier
+    method (GMRES, Sec. 4.2) and by the finite-difference system with BiCG (Sec. 4.1);
+    average Krylov iterations per Newton step and device time of the whole solve."""
+    import torch
+    import ot_inputs as I
+    out = {"settings": "manufactured pair, FP64, tau=1, eta=0.1, at most %d Newton steps "
+                       "(tol 1e-12), spectral symbols for the Fourier method" % steps}
+    for n in sizes:
+        f, g, _ = I.manufactured(n, n)
+        fd, gd = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        phi = torch.zeros_like(fd)
+        row = {}
+        for name, extra in (("fourier_gmres", {}), ("fd_bicg", {"linear_solver": 1})):
+            p = ot.Plan(n, n, precision="fp64", stream=stream, tau=1.0, tol=1e-12, eta=0.1,
+                        max_newton=steps, **extra)
+            p.solve(fd, gd, phi)
+            ms, st = _timed_solve(p, fd, gd, phi, stream)
+            p.close()
+            row[name] = {"avg_iters_per_newton": st["gmres_iters"] / max(1, st["newton_iters"]),
+                         "ms_total": round(ms, 3), "newton_iters": st["newton_iters"],
+                         "res_inf": st["res_inf"]}
+        out["%d" % n] = row
+    return out
+
+
 def run_ours(args):
     rank, world, local = dist_env()
     cpu_jobs = None
@@ -688,6 +796,7 @@ def run_ours(args):
 
     # plain FP64 GPU path on the same pair (for the mixed-vs-FP64 comparison)
     fp64 = None
+    spectral_radius = None
     if not args.no_fp64:
         p64 = ot.Plan(N, M, tau=TAU, tol=TOL, eta=ETA, precision="fp64", stream=stream,
                       symbols=SYMBOLS)  # phi0 = 0
@@ -709,6 +818,15 @@ def run_ours(args):
                 "newton_iters": st64["newton_iters"], "gmres_iters": st64["gmres_iters"],
                 "res_inf": st64["res_inf"],
                 "phi_mixed_vs_fp64_inf": float((phi_mixed - phi64).abs().max().item())}
+        # the stability measure of Sec. 5.1 at the root: five power iterations on the
+        # inverse of the linearised operator (start vector uniform in [0, 1], as there)
+        if not args.no_extras:
+            b0 = torch.from_numpy(
+                I.SplitMix64(4242).uniform(N * M).reshape(N, M)).cuda()
+            rho = p64.inverse_spectral_radius(fd, gd, phi64, b0, iters=5)
+            spectral_radius = {"rho_k": [float(r) for r in rho], "iterate": "the FP64 root",
+                               "operator": "stencil symbols (the timed configuration)",
+                               "paper": "about 0.03 after about 5 iterations (Sec. 5.1)"}
         p64.close()
 
     # the 256^2 blob-mixture pair on the plain FP64 path (tau = 4, tol 1e-10, the paper's
@@ -716,6 +834,36 @@ def run_ours(args):
     config2 = None
     if not args.no_fp64:
         config2 = run_config2(ot, stream, flush)
+    config5 = table1 = None
+    if not args.no_extras and world == 1:
+        config5 = run_config5(ot, stream)
+        table1 = run_table1(ot, stream)
+
+    # where the device time of a graph-launched solve goes: the per-phase times of one solve
+    # (stamp kernels at the phase changes), and the solve time with every Arnoldi step
+    # captured as a plain self-skipping kernel instead of IF nodes after the fourth
+    phases = None
+    if not args.no_extras:
+        plan.set(phase_times=1)
+        phi.zero_()
+        flush.zero_()
+        rc_ph, st_ph = plan.solve(fd, gd, phi)
+        torch.cuda.synchronize()
+        plan.set(phase_times=0)
+        phases = {k: round(st_ph[k], 4) for k in ("ms_residual", "ms_fft", "ms_krylov",
+                                                   "ms_update", "ms_other", "ms_total")}
+        graph_shape = {}
+        for unc in (0, 4, 10):
+            plan.set(uncond_steps=unc)
+            plan.solve(fd, gd, phi)
+            tms = []
+            for _ in range(5):
+                flush.zero_()
+                m_, _ = _timed_solve(plan, fd, gd, phi, stream)
+                tms.append(m_)
+            graph_shape[str(unc)] = round(statistics.median(tms), 4)
+        plan.set(uncond_steps=4)
+        phases["ms_per_solve_by_uncond_steps"] = graph_shape
 
     # roofline of the dominant kernel class: per-solve launches from the profiled solve,
     # per-launch duration from back-to-back relaunches on this stream (CUDA events)
@@ -783,6 +931,10 @@ def run_ours(args):
                 "all_converged": ok, "quality": quality, "fp64_gpu": fp64,
                 "mixed_zero_start": zero_start, "paper_symbols_arm": paper_arm,
                 "config2_fp64_blob256": config2,
+                "warm_start_eval_blob": config5,
+                "table1_fourier_vs_fd_bicg": table1,
+                "spectral_radius": spectral_radius,
+                "phase_times_one_solve": phases,
                 "warm_start": ws_info,
                 "e2e": {"value": e2e_value, "unit": "solves/s",
                         "h2d_bytes_per_step": 2 * P * 8, "d2h_bytes_per_step": P * 8,

@@ -24,7 +24,7 @@ OT_OPT_TAU, OT_OPT_TOL, OT_OPT_PROFILE, OT_OPT_GRAPH, OT_OPT_REORTH = 9, 10, 11,
 OT_OPT_THETA_FP64, OT_OPT_AUTOTUNE, OT_OPT_FFT_VARIANT, OT_OPT_SYMBOLS = 14, 15, 16, 17
 OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19, 20, 21
 OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH, OT_OPT_INTERP = 22, 23, 24, 25
-OT_OPT_LINEAR_SOLVER, OT_OPT_MAX_BICG = 26, 27
+OT_OPT_LINEAR_SOLVER, OT_OPT_MAX_BICG, OT_OPT_UNCOND_STEPS = 26, 27, 28
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -425,7 +425,8 @@ class Plan:
              "ws_test_stall": OT_OPT_WS_TEST_STALL, "operator": OT_OPT_OPERATOR,
              "phase_times": OT_OPT_PHASE_TIMES, "transport": OT_OPT_TRANSPORT,
              "tau_switch": OT_OPT_TAU_SWITCH, "interp": OT_OPT_INTERP,
-             "linear_solver": OT_OPT_LINEAR_SOLVER, "max_bicg": OT_OPT_MAX_BICG}
+             "linear_solver": OT_OPT_LINEAR_SOLVER, "max_bicg": OT_OPT_MAX_BICG,
+             "uncond_steps": OT_OPT_UNCOND_STEPS}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

@@ -55,6 +55,9 @@ struct ot_plan {
   float* gxy32 = nullptr;
   // OT_OPT_LINEAR_SOLVER = 1: the finite-difference system of Sec. 4.1 with BiCG (FP64,
   // host-driven); its 7 vector planes and the iteration cap OT_OPT_MAX_BICG
+  // OT_OPT_UNCOND_STEPS: Arnoldi steps per GMRES cycle captured as plain self-skipping
+  // kernels rather than IF nodes (graph)
+  int uncond = 4;
   int linsolver = 0;
   int max_bicg = 20000;
   double* fdv = nullptr;
@@ -153,8 +156,6 @@ static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
 
-// Arnoldi steps per GMRES cycle captured as plain kernels rather than IF nodes (graph)
-constexpr int kUncondSteps = 4;
 
 static cudaEvent_t ev_get(ot_plan* p) {
   if (!p->pool.empty()) {
@@ -820,6 +821,13 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (v < 1 || v > 1e9 || v != (double)(int)v) return OT_EINVAL;
       p->max_bicg = (int)v;
       return OT_OK;
+    case OT_OPT_UNCOND_STEPS:
+      if (v < 0 || v > OTGB_MAXM || v != (double)(int)v) return OT_EINVAL;
+      if (p->uncond != (int)v) {
+        p->uncond = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_PHASE_TIMES:
       if (v != 0 && v != 1) return OT_EINVAL;
       if (p->phase_times != (int)v) {
@@ -876,6 +884,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_INTERP: *v = p->interp; return OT_OK;
     case OT_OPT_LINEAR_SOLVER: *v = p->linsolver; return OT_OK;
     case OT_OPT_MAX_BICG: *v = p->max_bicg; return OT_OK;
+    case OT_OPT_UNCOND_STEPS: *v = p->uncond; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -901,6 +910,47 @@ extern "C" int ot_plan_get_profile(ot_plan* p, double* ms, int64_t* launches, in
     if (launches) launches[k] = p->prof_n[k];
   }
   if (total_launches) *total_launches = p->launches;
+  return OT_OK;
+}
+
+// Device time of `reps` back-to-back launches issued by one() on p->stream, captured and
+// replayed as one CUDA graph (total in *ms).  Kernels launched one by one into a stream are
+// paced on this system at multiples of about 2 us each, which rounds every short kernel up
+// to that grid; inside a graph they follow each other a fraction of a microsecond apart, as
+// in the captured solve.  p->stream is switched to the plan's capture stream while one()
+// is recorded.
+template <typename F>
+static int graph_time(ot_plan* p, F&& one, int reps, float* ms) {
+  if (!p->cs[0]) CK(cudaStreamCreateWithFlags(&p->cs[0], cudaStreamNonBlocking));
+  cudaStream_t run = p->stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+  CK(cudaEventRecord(a, run));
+  CK(cudaStreamWaitEvent(p->cs[0], a, 0));
+  cudaEventDestroy(a);
+  a = nullptr;
+  p->stream = p->cs[0];
+  cudaError_t e = cudaStreamBeginCapture(p->cs[0], cudaStreamCaptureModeRelaxed);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(p->cs[0], &g);
+  p->stream = run;
+  if (e == cudaSuccess) e = e2;
+  cudaGraphExec_t ge = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, run);  // upload and warm
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, run);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, run);
+  if (e == cudaSuccess) e = cudaEventRecord(b, run);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  CK(e);
   return OT_OK;
 }
 
@@ -970,17 +1020,8 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
     CK(cudaStreamSynchronize(p->stream));
   }
   CK(one());  // warm
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
-  CK(cudaEventRecord(a, p->stream));
-  for (int r = 0; r < reps; ++r) CK(one());
-  CK(cudaEventRecord(b, p->stream));
-  CK(cudaEventSynchronize(b));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
+  RET(graph_time(p, one, reps, &ms));
   *ms_per_launch = ms / reps;
   return OT_OK;
 }
@@ -1620,7 +1661,7 @@ static int capture_solve(ot_plan* p) {
   // (a conditional IF node costs ~5 us per execution, more than the early-exiting launches
   // of the few steps a short cycle leaves); later steps sit in IF nodes.  A batched plan runs
   // every step as a plain launch (the cycles of its pairs end at different steps).
-  const int K = batched ? p->m : (p->m < kUncondSteps ? p->m : kUncondSteps);
+  const int K = batched ? p->m : (p->m < p->uncond ? p->m : p->uncond);
   for (int j = 0; j < p->m; ++j) {
     if (j < K) {
       p->h_step[j] = 0;
@@ -1678,8 +1719,8 @@ static int capture_solve(ot_plan* p) {
 // ------------------------------------------------------------------------------------------
 // Autotuner of the FP32 matvec passes: each variant (generic / concurrent transforms /
 // warp-synchronous radix-32 / 4 elements per thread) of the row R2C, column and row combine
-// passes is launched back to back on the plan's own buffers and timed with CUDA events; the
-// fastest is kept, and the choice is cached per (N, M) for the process.
+// passes is launched back to back on the plan's own buffers inside a captured graph and timed
+// with CUDA events; the fastest is kept, and the choice is cached per (N, M) for the process.
 // ------------------------------------------------------------------------------------------
 static std::mutex g_tune_mutex;
 static std::vector<std::vector<int>> g_tune_cache;  // {N, M, r2c, col, comb, col_q, mv_reg}
@@ -1709,45 +1750,41 @@ static int run_autotune(ot_plan* p) {
   CK(cudaMemsetAsync(p->q2, 0, P * 4, st));
   CK(cudaMemsetAsync(p->coef, 0, 5 * P * 4, st));
   CK(cudaMemsetAsync(p->sc, 0, sizeof(DevScalars), st));
-  cudaEvent_t a, b;
-  CK(cudaEventCreate(&a));
-  CK(cudaEventCreate(&b));
   SpecTables& tb = p->tb32;
   auto timed = [&](int cls) -> float {
     auto one = [&]() -> cudaError_t {
       if (tb.mv_reg) {
         if (cls == 0)
           return launch_mvT_r2c((const float*)p->V, P, nullptr, nullptr, (float2*)p->spec, N,
-                                M, tb, nullptr, st);
+                                M, tb, nullptr, p->stream);
         if (cls == 1)
           return launch_mvT_col((const float2*)p->spec, (float2*)p->q0, (float2*)p->q1,
-                                (float2*)p->q2, N, M, tb, p->sc, nullptr, st);
+                                (float2*)p->q2, N, M, tb, p->sc, nullptr, p->stream);
         return launch_mvT_combine((const float2*)p->q0, (const float2*)p->q1,
                                   (const float2*)p->q2, (const float*)p->coef, (float*)p->w, N,
-                                  M, tb, nullptr, st);
+                                  M, tb, nullptr, p->stream);
       }
       if (cls == 0)
         return launch_row_r2c<float>((const float*)p->V, P, nullptr, nullptr,
-                                     (C2<float>*)p->spec, N, M, tb, nullptr, st);
+                                     (C2<float>*)p->spec, N, M, tb, nullptr, p->stream);
       if (cls == 1)
         return launch_col<float>(COL_MATVEC, (C2<float>*)p->spec, (C2<float>*)p->q0,
                                  (C2<float>*)p->q1, (C2<float>*)p->q2, N, M, tb, p->sc,
-                                 nullptr, st);
+                                 nullptr, p->stream);
       return launch_row_c2r<float>(ROWINV_COMBINE, (C2<float>*)p->q0, (C2<float>*)p->q1,
                                    (C2<float>*)p->q2, (const float*)p->coef, (float*)p->w,
-                                   nullptr, nullptr, 0.0, 1.0, N, M, tb, nullptr, st);
+                                   nullptr, nullptr, 0.0, 1.0, N, M, tb, nullptr, p->stream);
     };
-    // 3 warm-up and 30 timed launches: the candidates are within a few percent of each other
-    // at the sizes of interest, and 10 launches let launch jitter flip the choice
+    // 3 warm-up launches, then 30 timed launches replayed as one graph: the candidates are
+    // within a few percent of each other at the sizes of interest, and stream launches are
+    // paced on a ~2 us grid that would hide their differences
     for (int r = 0; r < 3; ++r)
       if (one() != cudaSuccess) return 1e30f;
-    cudaEventRecord(a, st);
-    for (int r = 0; r < 30; ++r)
-      if (one() != cudaSuccess) return 1e30f;
-    cudaEventRecord(b, st);
-    if (cudaEventSynchronize(b) != cudaSuccess) return 1e30f;
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
+    if (graph_time(p, one, 30, &ms) != OT_OK) {
+      cudaGetLastError();
+      return 1e30f;
+    }
     return ms;
   };
   tb.col_q = 0;
@@ -1801,8 +1838,6 @@ static int run_autotune(ot_plan* p) {
   }
 
   cudaGetLastError();
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   p->tuned = 1;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune_cache.push_back({N, M, tb.var_r2c, tb.var_col, tb.var_comb, tb.col_q, tb.mv_reg});
@@ -1884,7 +1919,7 @@ static void graph_scalars(ot_plan* p, DevScalars* h) {
   h->h_restart = p->h_restart;
   h->h_halve = p->h_halve;
   for (int k = 0; k < OTGB_MAXM; ++k) h->h_step[k] = p->h_step[k];
-  h->steps_uncond = p->m < kUncondSteps ? p->m : kUncondSteps;
+  h->steps_uncond = p->m < p->uncond ? p->m : p->uncond;
 }
 
 // Enqueue one graph-launched solve on stream xs: inputs into the plan's buffers, the initial

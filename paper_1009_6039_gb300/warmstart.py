@@ -27,13 +27,15 @@ def init_params(seed):
     return p
 
 
-def training_data(pairs, N, M, tau=2.0, tol=1e-8, eta=0.1, max_newton=400):
+def training_data(pairs, N, M, tau=2.0, tol=1e-8, eta=0.1, max_newton=400, symbols=0):
     """(X, t): features (n*N*M x 16) and targets (n*N*M) as float32 CUDA tensors, from the
     converged potentials of the pairs (numpy float64 (N, M) arrays); pairs whose solve does
-    not converge are skipped."""
+    not converge are skipped.  The solver settings change the path, not the root (the
+    target): symbols = 1 (the stencils' symbols) converges in fewer steps."""
     import torch
     P = N * M
-    plan = Plan(N, M, tau=tau, tol=tol, eta=eta, precision="mixed", max_newton=max_newton)
+    plan = Plan(N, M, tau=tau, tol=tol, eta=eta, precision="mixed", max_newton=max_newton,
+                symbols=symbols)
     Xs, ts = [], []
     for f, g in pairs:
         fd = torch.from_numpy(np.ascontiguousarray(f, dtype=np.float64)).cuda()

@@ -136,3 +136,25 @@ def test_fd_option_rules(ot):
     with pytest.raises(RuntimeError):
         p.fd_apply(c, z, z)
     p.close()
+
+
+def test_table1_shape_on_the_gpu(ot):
+    # the experiment of Table 1 (Sec. 5.1): up to 20 Newton steps at tau = 1 with the linear
+    # solves to 0.1 (stopping at max|F| < 1e-12: past that the right-hand side is round-off);
+    # the average BiCG count of the finite-difference system grows with N (the paper: 14.21,
+    # 17.79, 31.11 for N = 16, 32, 64) while the Fourier method's GMRES count stays nearly
+    # constant (5.32, 6.37, 7.32)
+    avg = {"gmres": [], "bicg": []}
+    for n in (16, 32, 64):
+        f, g, _ = I.manufactured(n, n)
+        for key, extra in (("gmres", {}), ("bicg", {"linear_solver": 1})):
+            p = ot.Plan(n, n, precision="fp64", tau=1.0, tol=1e-12, eta=0.1, max_newton=20,
+                        **extra)
+            phi = dev(np.zeros((n, n)))
+            rc, st = p.solve(dev(f), dev(g), phi)
+            p.close()
+            assert rc in (ot.OT_OK, ot.OT_ENOCONV) and st["newton_iters"] > 0
+            avg[key].append(st["gmres_iters"] / st["newton_iters"])
+    b, gm = avg["bicg"], avg["gmres"]
+    assert b[0] < b[1] < b[2] and b[2] / b[0] > 2.0, b
+    assert max(gm) / min(gm) < 1.5, gm
