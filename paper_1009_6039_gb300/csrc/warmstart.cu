@@ -363,20 +363,18 @@ __host__ __device__ constexpr int op_offset(int r, int k) {
   return (k >> 4) * 4096 + (r >> 3) * 256 + ((k >> 3) & 1) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// warpgroups of the tensor-core network kernel (readout columns split WS_WG ways)
-#ifndef WS_WG
-#define WS_WG 4
-#endif
+// chains of the tensor-core network kernel: independent warpgroups, each with its own
+// 128-row tile, activation buffer, TMEM accumulator (128 columns) and mbarrier
+constexpr int WS_CH = 4;
 
 constexpr int SM_W0 = 0;                       // 4 KB
 constexpr int SM_W1 = SM_W0 + 4096;            // 32 KB
 constexpr int SM_W2 = SM_W1 + 32768;           // 32 KB
-constexpr int SM_A = SM_W2 + 32768;            // 32 KB activations / X tile
-constexpr int SM_BIAS = SM_A + 32768;          // b0, b1, b2, w3 (4 x 128 FP32), b3
-constexpr int SM_BAR = SM_BIAS + 4 * 128 * 4 + 16;
-constexpr int SM_TMEM = SM_BAR + 8;
-constexpr int SM_RED = SM_TMEM + 8;            // per-warpgroup partial outputs (4 x 128 FP32)
-constexpr int SM_TOTAL = SM_RED + 4 * 128 * 4 + 128;  // + alignment slack
+constexpr int SM_A = SM_W2 + 32768;            // WS_CH x 32 KB activations / X tiles
+constexpr int SM_BIAS = SM_A + WS_CH * 32768;  // b0, b1, b2, w3 (4 x 128 FP32), b3
+constexpr int SM_BAR = SM_BIAS + 4 * 128 * 4 + 16;  // WS_CH mbarriers
+constexpr int SM_TMEM = SM_BAR + 8 * WS_CH;
+constexpr int SM_TOTAL = SM_TMEM + 8 + 128;    // + alignment slack
 constexpr int PACKED_W_BYTES = SM_A - SM_W0;   // 69632: W0, W1, W2 in operand layout
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -454,19 +452,6 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// warp 0 waits (the other warps sleep in the barrier instead of polling, leaving the issue
-// slots to the other CTA's readout); the result is made visible to every thread
-__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t par, int warp) {
-  bool ok = true;
-  if (warp == 0) {
-    ok = bar_wait(bar, par);
-    fence_before();
-  }
-  ok = __syncthreads_and(ok);
-  fence_after();
-  return ok;
-}
-
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -484,14 +469,39 @@ __device__ __forceinline__ void st_row8(unsigned char* base, int r, int k0, cons
   *reinterpret_cast<uint4*>(base + op_offset(r, k0)) = q;
 }
 
-// layer readout of this thread's row r over the NC 32-column chunks of the accumulator from
-// column c0: bias + SiLU -> BF16 A tile of the next layer
-template <int NC>
-__device__ __forceinline__ void readout_hidden(uint32_t trow, const float* bias,
-                                               unsigned char* sA, int r, int c0) {
+// wait for this chain's MMA group (all its threads poll with a suspend hint, bounded)
+__device__ __forceinline__ bool chain_wait(uint32_t bar, uint32_t par) {
+  const bool ok = bar_wait(bar, par);
+  fence_after();
+  return ok;
+}
+
+// barrier of one chain (warpgroup g: 128 threads, named barrier 1 + g)
+__device__ __forceinline__ void chain_sync(int g) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
+}
+
+// the same barrier, returning whether every thread of the chain passed ok: the chain takes
+// one decision after a bounded wait, even if its threads' waits ended differently
+__device__ __forceinline__ bool chain_all(int g, bool ok) {
+  uint32_t res;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(res)
+      : "r"((uint32_t)ok), "r"(1 + g)
+      : "memory");
+  return res != 0;
+}
+
+// layer readout of this thread's row r (all 128 columns of the chain's accumulator, 32 at a
+// time): bias + SiLU -> BF16 A tile of the next layer
+__device__ __forceinline__ void readout_row(uint32_t trow, const float* bias, unsigned char* sA,
+                                            int r) {
 #pragma unroll 1
-  for (int c = 0; c < NC; ++c) {
-    const int col = c0 + 32 * c;
+  for (int col = 0; col < 128; col += 32) {
     float v[32];
     tmem_ld32(trow + col, v);
 #pragma unroll
@@ -501,26 +511,26 @@ __device__ __forceinline__ void readout_hidden(uint32_t trow, const float* bias,
   }
 }
 
-// One CTA per 128-row tile at a time (persistent over tiles), WG warpgroups: the readouts,
-// which bound the kernel (SiLU and BF16 packing of 128 x 128 values per layer), are split
-// by columns over the warpgroups -- warp w reads TMEM lanes 32 (w % 4) .. (its rows) and
-// warpgroup w / 4 the columns 128/WG (w / 4) ..; thread 0 issues the MMAs.
-// stall != 0 (a test of the failure path): the first tile's first MMA group is not issued,
-// so the wait for it runs out; the kernel then sets *err, frees its TMEM and returns
-template <int WG>
-__global__ void __launch_bounds__(128 * WG, 2)
+// One persistent CTA per SM holds the weights once and runs WS_CH independent chains, one
+// per warpgroup: chain g takes 128-row tiles (thread r of the warpgroup owns row r, which
+// is TMEM lane r, in accumulator columns 128 g ..), and per tile issues its three MMA
+// groups from its first thread and reads each result back with its 128 threads.  The
+// chains synchronise only within themselves (named barriers), so one chain's MMAs run
+// while the others read out (the readout -- bias, SiLU, BF16 packing -- bounds the kernel).
+// stall != 0 (a test of the failure path): chain 0 does not issue its first MMA group, so
+// its wait runs out; the kernel then sets *err and the chain stops (after a bounded wait
+// for anything it has in flight); the others finish, and the TMEM is freed at the end.
+__global__ void __launch_bounds__(128 * WS_CH, 1)
     k_ws_mlp_tc(const unsigned char* __restrict__ wpack, const float* __restrict__ params,
                 const float* __restrict__ X, long rows, float* __restrict__ out,
                 int* __restrict__ err, int stall) {
-  constexpr int NT = 128 * WG, NC = 4 / WG;
+  constexpr int NT = 128 * WS_CH;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* sm =
       (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   const int tid = threadIdx.x, warp = tid >> 5, g = warp >> 2, r = tid & 127;
-  const int c0 = 32 * NC * g;  // first accumulator column of this warpgroup
   float* sb = reinterpret_cast<float*>(sm + SM_BIAS);
-  float* red = reinterpret_cast<float*>(sm + SM_RED);
-  const uint32_t bar = smem_u32(sm + SM_BAR);
+  const uint32_t bar = smem_u32(sm + SM_BAR + 8 * g);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
 
   // weights (pre-packed BF16 operand layout) and FP32 biases into shared memory
@@ -538,12 +548,13 @@ __global__ void __launch_bounds__(128 * WG, 2)
   }
   if (warp == 0) {
     asm volatile(
-        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-            smem_u32(tmem_slot))
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(tmem_slot)),
+        "r"(128 * WS_CH)
         : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
+  if (r == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -551,103 +562,91 @@ __global__ void __launch_bounds__(128 * WG, 2)
   fence_before();
   __syncthreads();
   fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  unsigned char* sA = sm + SM_A;
+  const uint32_t tbase = *tmem_slot;
+  const uint32_t tacc = tbase + 128 * g;                              // this chain's columns
+  const uint32_t trow = tacc + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
+  unsigned char* sA = sm + SM_A + 32768 * g;
   const uint32_t aA = smem_u32(sA), aW0 = smem_u32(sm + SM_W0), aW1 = smem_u32(sm + SM_W1),
                  aW2 = smem_u32(sm + SM_W2);
   uint32_t phase = 0;
   bool ok = true;
+  bool inflight = false;
   const long ntiles = (rows + 127) / 128;
-  for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  for (long tile = (long)blockIdx.x * WS_CH + g; tile < ntiles && ok;
+       tile += (long)gridDim.x * WS_CH) {
     const long row = tile * 128 + r;
-    // X row -> BF16 (K block 0 of the A operand), 8 features per warpgroup
-    for (int part = g; part < 2; part += WG) {
-      float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // X row -> BF16 (K block 0 of the A operand)
+    {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = 0.f;
       if (row < rows) {
-        const float4* xr = reinterpret_cast<const float4*>(X + row * 16 + 8 * part);
-        const float4 a = __ldg(xr), b = __ldg(xr + 1);
-        v[0] = a.x;
-        v[1] = a.y;
-        v[2] = a.z;
-        v[3] = a.w;
-        v[4] = b.x;
-        v[5] = b.y;
-        v[6] = b.z;
-        v[7] = b.w;
+        const float4* xr = reinterpret_cast<const float4*>(X + row * 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 a = __ldg(xr + q);
+          v[4 * q] = a.x;
+          v[4 * q + 1] = a.y;
+          v[4 * q + 2] = a.z;
+          v[4 * q + 3] = a.w;
+        }
       }
-      st_row8(sA, r, 8 * part, v);
+      st_row8(sA, r, 0, v);
+      st_row8(sA, r, 8, v + 8);
     }
-    // layer 0: D = X W0^T
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    if (tid == 0 && !(stall && tile == blockIdx.x)) {
-      fence_after();
-      mma_bf16(tmem, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
-      mma_commit(bar);
-    }
-    ok = block_wait(bar, phase, warp);
-    if (!ok) break;
-    phase ^= 1;
-    readout_hidden<NC>(trow, sb, sA, r, c0);
-    // layers 1 and 2: D = A W^T, K = 128 in eight K blocks of 16
+    // layer 0: D = X W0^T; layers 1 and 2: D = A W^T, K = 128 in eight K blocks of 16
 #pragma unroll 1
-    for (int layer = 1; layer <= 2 && ok; ++layer) {
+    for (int layer = 0; layer <= 2; ++layer) {
       fence_async_smem();
       fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      chain_sync(g);
+      if (r == 0 && !(stall && g == 0 && tile == (long)blockIdx.x * WS_CH)) {
         fence_after();
-        const uint32_t aW = layer == 1 ? aW1 : aW2;
+        if (layer == 0) {
+          mma_bf16(tacc, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
+        } else {
+          const uint32_t aW = layer == 1 ? aW1 : aW2;
 #pragma unroll
-        for (int kb = 0; kb < 8; ++kb)
-          mma_bf16(tmem, mdesc(aA + kb * 4096, 128, 256), mdesc(aW + kb * 4096, 128, 256),
-                   kb > 0 ? 1u : 0u);
+          for (int kb = 0; kb < 8; ++kb)
+            mma_bf16(tacc, mdesc(aA + kb * 4096, 128, 256), mdesc(aW + kb * 4096, 128, 256),
+                     kb > 0 ? 1u : 0u);
+        }
         mma_commit(bar);
       }
-      ok = block_wait(bar, phase, warp);
+      inflight = true;
+      ok = chain_all(g, chain_wait(bar, phase));
       if (!ok) break;
+      inflight = false;
       phase ^= 1;
-      if (layer == 1) {
-        readout_hidden<NC>(trow, sb + 128, sA, r, c0);
+      if (layer < 2) {
+        readout_row(trow, sb + 128 * layer, sA, r);
       } else {
-        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32, each warpgroup
-        // over its columns, then the WG partial sums of the row added in warpgroup order
-        float acc = 0.f;
+        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32 over the row
+        float acc = sb[512];
 #pragma unroll 1
-        for (int c = 0; c < NC; ++c) {
-          const int col = c0 + 32 * c;
+        for (int col = 0; col < 128; col += 32) {
           float v[32];
           tmem_ld32(trow + col, v);
 #pragma unroll
           for (int q = 0; q < 32; ++q)
             acc = fmaf(sb[384 + col + q], silu_f(v[q] + sb[256 + col + q]), acc);
         }
-        red[g * 128 + r] = acc;
-        __syncthreads();
-        if (g == 0) {
-          float s = sb[512];
-#pragma unroll
-          for (int q = 0; q < WG; ++q) s += red[q * 128 + r];
-          if (row < rows) out[row] = s;
-        }
+        if (row < rows) out[row] = acc;
       }
     }
-    fence_before();
-    __syncthreads();
   }
   if (!ok) {
-    if (err) atomicExch(err, 1);
-    // let an MMA still in flight finish before its TMEM goes away (bounded; with `stall`
-    // nothing is in flight and this wait runs out too)
-    if (warp == 0) bar_wait(bar, phase);
+    if (r == 0 && err) atomicExch(err, 1);
+    // let an MMA group still in flight finish before its TMEM goes away (bounded; with
+    // `stall` nothing is in flight and this wait runs out too)
+    if (inflight) bar_wait(bar, phase);
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(128 * WS_CH)
                  : "memory");
 }
 
@@ -1005,17 +1004,17 @@ cudaError_t launch_ws_mlp(const unsigned char* wpack, const float* params, const
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(k_ws_mlp_tc<WS_WG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
+    cudaError_t e = cudaFuncSetAttribute(k_ws_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SM_TOTAL);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  // two CTAs per SM (shared memory and TMEM allow two), so one CTA's readout overlaps the
-  // other's MMAs
+  // one CTA per SM (its shared memory and the 512 TMEM columns of its four chains fill it)
   const long tiles = (rows + 127) / 128;
-  const long grid = tiles < 2L * sms ? tiles : 2L * sms;
-  k_ws_mlp_tc<WS_WG><<<(unsigned)grid, 128 * WS_WG, SM_TOTAL, st>>>(wpack, params, X, rows, out,
-                                                                   err, stall);
+  const long ctas = (tiles + WS_CH - 1) / WS_CH;
+  const long grid = ctas < (long)sms ? ctas : (long)sms;
+  k_ws_mlp_tc<<<(unsigned)grid, 128 * WS_CH, SM_TOTAL, st>>>(wpack, params, X, rows, out, err,
+                                                            stall);
   return cudaGetLastError();
 }
 
