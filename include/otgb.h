@@ -148,9 +148,10 @@ extern "C" {
 #define OT_OPT_MAX_BICG 27      /* BiCG iterations per Newton step, >= 1 (default 20000) */
 #define OT_OPT_UNCOND_STEPS 28  /* graph structure: the first s Arnoldi steps of every GMRES
                                    cycle are captured as plain kernels that skip themselves
-                                   once the cycle has ended, the later ones as conditional IF
-                                   nodes (0 <= s <= 16, default 4; a plan set captures
-                                   every step plainly).  Same arithmetic for every s */
+                                   once the cycle has ended, the later ones as the body of one
+                                   conditional WHILE node, a step per iteration (0 <= s <= 16,
+                                   default 4; a plan set captures every step plainly).  Same
+                                   arithmetic for every s */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -1187,7 +1187,9 @@ __device__ void arnoldi_close(DevScalars* sc, int j, double hn, bool weak) {
     if (j + 1 == m) sc->cycle_done = 1;
   }
   sc->j = j + 1;
-  if (sc->graph && j + 1 < m && sc->h_step[j + 1])
+  // the handle of step j + 1 (the tail WHILE of the captured cycle for j + 1 >= its plain
+  // steps, including j + 1 = m, where the cycle is done and the loop ends)
+  if (sc->graph && j + 1 < OTGB_MAXM && sc->h_step[j + 1])
     cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
 }
 
@@ -1243,7 +1245,7 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
   }
   if (done) sc->cycle_done = 1;
   sc->j = j + 1;
-  if (graph && j + 1 < m && hnext) cudaGraphSetConditional(hnext, done ? 0u : 1u);
+  if (graph && hnext) cudaGraphSetConditional(hnext, done ? 0u : 1u);
 }
 
 // Per-thread partial sums are kept in the vector precision T (a thread covers a few vectors
