@@ -222,8 +222,8 @@ __device__ __forceinline__ void stockham_stage_multi(C2<T>* const (&bufs)[NB], i
 }
 
 template <typename T, int E, int SIGN, int NB>
-__device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, int t,
-                                               bool active, const C2<T>* __restrict__ twb) {
+__device__ __forceinline__ void fft_smem_multi_rt(C2<T>* const (&bufs)[NB], int L, int t,
+                                                  bool active, const C2<T>* __restrict__ twb) {
   const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
   int Ns = 1;
   int rem = L;
@@ -253,8 +253,8 @@ __device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, 
 // Full unnormalised transform X_k = sum_n x_n exp(SIGN 2 pi i k n / L), in place in buf.
 // Radix sequence: [3,] then 8s (E = 8) or 4s (E = 12), then the remaining 4 or 2.
 template <typename T, int E, int SIGN>
-__device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
-                                         const C2<T>* __restrict__ twb) {
+__device__ __forceinline__ void fft_smem_rt(C2<T>* buf, int L, int t, bool active,
+                                            const C2<T>* __restrict__ twb) {
   const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
   int Ns = 1;
   int rem = L;
@@ -279,6 +279,101 @@ __device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
       rem /= 2;
     }
   }
+}
+
+// The same transforms with the length fixed at compile time (power-of-two L): the stage
+// sequence (radix 8 or 4 while the remainder allows, then 4 or 2), the spans, the thread
+// counts and the shared-memory indices fold into constants, which removes most of the
+// integer work of a stage.  The arithmetic and its order are those of the run-time version,
+// so the results are bit for bit the same.
+template <typename T, int E, int R, int SIGN, int L, int Ns, bool PIN, bool POUT, int NB>
+__device__ __forceinline__ void stockham_stage_c(C2<T>* const (&bufs)[NB], int t, bool active,
+                                                 const C2<T>* __restrict__ st) {
+  constexpr int TPT = L / E;
+  constexpr int LR = L / R;
+  constexpr int a = Ns == 1 ? 0 : __builtin_ctz(Ns);
+  C2<T> v[NB][E];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int src = spad(j + r * LR, PIN);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q][b * R + r] = bufs[q][src];
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < E / R; ++b) {
+      const int j = t + b * TPT;
+      const int qd = j >> a;
+      const int k = j & (Ns - 1);
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C2<T> w = st[(Ns - 1) + (r - 1) * Ns + k];
+          if (SIGN > 0) w.y = -w.y;
+#pragma unroll
+          for (int q = 0; q < NB; ++q) v[q][b * R + r] = cmul<T>(v[q][b * R + r], w);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) Bfly<T, R, SIGN>::run(&v[q][b * R]);
+      const int d = qd * (Ns * R) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int dst = spad(d + r * Ns, POUT);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) bufs[q][dst] = v[q][b * R + r];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int E, int SIGN, int L, int Ns, int REM, int NB>
+__device__ __forceinline__ void fft_smem_c(C2<T>* const (&bufs)[NB], int t, bool active,
+                                           const C2<T>* __restrict__ tw) {
+  if constexpr (REM > 1) {
+    constexpr int R = (E % 8 == 0 && REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2);
+    stockham_stage_c<T, E, R, SIGN, L, Ns, (Ns > 1), (REM / R > 1), NB>(bufs, t, active, tw);
+    fft_smem_c<T, E, SIGN, L, Ns * R, REM / R, NB>(bufs, t, active, tw);
+  }
+}
+
+// dispatch on the length: the compile-time transforms for the 4-element-per-thread kernels
+// at the power-of-two lengths 256 .. 2048, the run-time ones otherwise
+template <typename T, int E, int SIGN, int NB>
+__device__ __forceinline__ void fft_smem_multi(C2<T>* const (&bufs)[NB], int L, int t,
+                                               bool active, const C2<T>* __restrict__ twb) {
+  if constexpr (E == 4) {
+    const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
+    switch (L) {
+      case 256: fft_smem_c<T, E, SIGN, 256, 1, 256, NB>(bufs, t, active, tw); return;
+      case 512: fft_smem_c<T, E, SIGN, 512, 1, 512, NB>(bufs, t, active, tw); return;
+      case 1024: fft_smem_c<T, E, SIGN, 1024, 1, 1024, NB>(bufs, t, active, tw); return;
+      case 2048: fft_smem_c<T, E, SIGN, 2048, 1, 2048, NB>(bufs, t, active, tw); return;
+      default: break;
+    }
+  }
+  fft_smem_multi_rt<T, E, SIGN, NB>(bufs, L, t, active, twb);
+}
+
+template <typename T, int E, int SIGN>
+__device__ __forceinline__ void fft_smem(C2<T>* buf, int L, int t, bool active,
+                                         const C2<T>* __restrict__ twb) {
+  if constexpr (E == 4) {
+    if (L >= 256 && L <= 2048 && (L & (L - 1)) == 0) {
+      C2<T>* const bufs[1] = {buf};
+      fft_smem_multi<T, E, SIGN, 1>(bufs, L, t, active, twb);
+      return;
+    }
+  }
+  fft_smem_rt<T, E, SIGN>(buf, L, t, active, twb);
 }
 
 // ---------------------------------------------------------------------------------------
