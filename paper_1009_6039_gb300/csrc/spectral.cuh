@@ -286,8 +286,10 @@ __device__ __forceinline__ void fft_smem_rt(C2<T>* buf, int L, int t, bool activ
 // counts and the shared-memory indices fold into constants, which removes most of the
 // integer work of a stage.  The arithmetic and its order are those of the run-time version,
 // so the results are bit for bit the same.
-template <typename T, int E, int R, int SIGN, int L, int Ns, bool PIN, bool POUT, int NB>
-__device__ __forceinline__ void stockham_stage_c(C2<T>* const (&bufs)[NB], int t, bool active,
+template <typename T, int E, int R, int SIGN, int L, int Ns, bool PIN, bool POUT, int NB,
+          bool INPLACE>
+__device__ __forceinline__ void stockham_stage_c(C2<T>* const (&in)[NB], C2<T>* const (&out)[NB],
+                                                 int t, bool active,
                                                  const C2<T>* __restrict__ st) {
   constexpr int TPT = L / E;
   constexpr int LR = L / R;
@@ -301,11 +303,13 @@ __device__ __forceinline__ void stockham_stage_c(C2<T>* const (&bufs)[NB], int t
       for (int r = 0; r < R; ++r) {
         const int src = spad(j + r * LR, PIN);
 #pragma unroll
-        for (int q = 0; q < NB; ++q) v[q][b * R + r] = bufs[q][src];
+        for (int q = 0; q < NB; ++q) v[q][b * R + r] = in[q][src];
       }
     }
   }
-  __syncthreads();
+  // in place, the stores must wait for every thread's loads; from one buffer into the
+  // other, the stage needs only the barrier at its end
+  if (INPLACE) __syncthreads();
   if (active) {
 #pragma unroll
     for (int b = 0; b < E / R; ++b) {
@@ -328,21 +332,87 @@ __device__ __forceinline__ void stockham_stage_c(C2<T>* const (&bufs)[NB], int t
       for (int r = 0; r < R; ++r) {
         const int dst = spad(d + r * Ns, POUT);
 #pragma unroll
-        for (int q = 0; q < NB; ++q) bufs[q][dst] = v[q][b * R + r];
+        for (int q = 0; q < NB; ++q) out[q][dst] = v[q][b * R + r];
       }
     }
   }
   __syncthreads();
 }
 
+// radix of the stage with remainder REM (E elements per thread): 8 or 4 while the remainder
+// allows, then 4 or 2 -- the sequence of the run-time transforms
+template <int E, int REM>
+__host__ __device__ constexpr int stage_radix() {
+  return (E % 8 == 0 && REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2);
+}
+template <int E, int REM>
+__host__ __device__ constexpr int stage_count() {
+  if constexpr (REM > 1)
+    return 1 + stage_count<E, REM / stage_radix<E, REM>()>();
+  else
+    return 0;
+}
+
 template <typename T, int E, int SIGN, int L, int Ns, int REM, int NB>
 __device__ __forceinline__ void fft_smem_c(C2<T>* const (&bufs)[NB], int t, bool active,
                                            const C2<T>* __restrict__ tw) {
   if constexpr (REM > 1) {
-    constexpr int R = (E % 8 == 0 && REM % 8 == 0) ? 8 : (REM % 4 == 0 ? 4 : 2);
-    stockham_stage_c<T, E, R, SIGN, L, Ns, (Ns > 1), (REM / R > 1), NB>(bufs, t, active, tw);
+    constexpr int R = stage_radix<E, REM>();
+    stockham_stage_c<T, E, R, SIGN, L, Ns, (Ns > 1), (REM / R > 1), NB, true>(bufs, bufs, t,
+                                                                             active, tw);
     fft_smem_c<T, E, SIGN, L, Ns * R, REM / R, NB>(bufs, t, active, tw);
   }
+}
+
+// Ping-pong form: the stages alternate between bufs and the scratch buffers (one barrier a
+// stage); with an odd number of stages the first runs in place, so that the result ends in
+// bufs.  Same arithmetic and order as above.
+template <typename T, int E, int SIGN, int L, int Ns, int REM, int NB, bool FROM_A>
+__device__ __forceinline__ void fft_smem_pp_rec(C2<T>* const (&a)[NB], C2<T>* const (&b)[NB],
+                                                int t, bool active,
+                                                const C2<T>* __restrict__ tw) {
+  if constexpr (REM > 1) {
+    constexpr int R = stage_radix<E, REM>();
+    if constexpr (FROM_A)
+      stockham_stage_c<T, E, R, SIGN, L, Ns, (Ns > 1), (REM / R > 1), NB, false>(a, b, t,
+                                                                                active, tw);
+    else
+      stockham_stage_c<T, E, R, SIGN, L, Ns, (Ns > 1), (REM / R > 1), NB, false>(b, a, t,
+                                                                                active, tw);
+    fft_smem_pp_rec<T, E, SIGN, L, Ns * R, REM / R, NB, !FROM_A>(a, b, t, active, tw);
+  }
+}
+
+template <typename T, int E, int SIGN, int L, int NB>
+__device__ __forceinline__ void fft_smem_c_pp(C2<T>* const (&a)[NB], C2<T>* const (&b)[NB],
+                                              int t, bool active,
+                                              const C2<T>* __restrict__ tw) {
+  if constexpr (stage_count<E, L>() % 2 == 1) {
+    constexpr int R0 = stage_radix<E, L>();
+    stockham_stage_c<T, E, R0, SIGN, L, 1, false, (L / R0 > 1), NB, true>(a, a, t, active, tw);
+    fft_smem_pp_rec<T, E, SIGN, L, R0, L / R0, NB, true>(a, b, t, active, tw);
+  } else {
+    fft_smem_pp_rec<T, E, SIGN, L, 1, L, NB, true>(a, b, t, active, tw);
+  }
+}
+
+// with scratch buffers (as many as bufs, each of FB(L) elements): the ping-pong transforms
+// for the 4-element kernels at power-of-two lengths 256 .. 2048, else the in-place ones
+template <typename T, int E, int SIGN, int NB>
+__device__ __forceinline__ void fft_smem_multi_pp(C2<T>* const (&bufs)[NB],
+                                                  C2<T>* const (&scratch)[NB], int L, int t,
+                                                  bool active, const C2<T>* __restrict__ twb) {
+  if constexpr (E == 4) {
+    const C2<T>* __restrict__ tw = twb + (size_t)stage_table_slot<E>() * L;
+    switch (L) {
+      case 256: fft_smem_c_pp<T, E, SIGN, 256, NB>(bufs, scratch, t, active, tw); return;
+      case 512: fft_smem_c_pp<T, E, SIGN, 512, NB>(bufs, scratch, t, active, tw); return;
+      case 1024: fft_smem_c_pp<T, E, SIGN, 1024, NB>(bufs, scratch, t, active, tw); return;
+      case 2048: fft_smem_c_pp<T, E, SIGN, 2048, NB>(bufs, scratch, t, active, tw); return;
+      default: break;
+    }
+  }
+  fft_smem_multi_rt<T, E, SIGN, NB>(bufs, L, t, active, twb);
 }
 
 // dispatch on the length: the compile-time transforms for the 4-element-per-thread kernels
@@ -785,7 +855,9 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
   __syncthreads();
   if (NBUF == 3) {
     // Q0 = S (Nyquist channel premultiplied), Q1 = (i s1(k2)) S, Q2 = s2(k2) S into the
-    // three buffers, then the three inverse transforms interleaved
+    // three buffers, then the three inverse transforms interleaved (in place: ping-pong
+    // stages cost this kernel more in registers, capped at 64 for two blocks per SM, than
+    // they save in barriers)
     if (active) {
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -852,9 +924,10 @@ __device__ __forceinline__ C2<T> row_symbol_apply(C2<T> X, int k, int kind,
 }
 
 // the FP32 row combine with 4 elements per thread runs its five transforms interleaved
+// (5 buffers per row, and 5 scratch buffers for the ping-pong stages)
 template <typename T, int E, int MODE>
 __host__ __device__ constexpr int row_nbuf() {
-  return (MODE == ROWINV_COMBINE && sizeof(T) == 4 && E == 4) ? 5 : 1;
+  return (MODE == ROWINV_COMBINE && sizeof(T) == 4 && E == 4) ? 10 : 1;
 }
 
 // complex-to-real pre-processing on a packed row in buf (in place):
@@ -874,6 +947,36 @@ __device__ __forceinline__ void c2r_preprocess(C2<T>* buf, int L, int t, int TPT
         C2<T> Ov = cmul<T>(dv, cconj<T>(twM[k]));
         buf[k] = mk2<T>(Ev.x - Ov.y, Ev.y + Ov.x);
         if (2 * k != L) buf[L - k] = mk2<T>(Ev.x + Ov.y, -Ev.y + Ov.x);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// the same for NB rows at once (one pass, one barrier)
+template <typename T, int NB>
+__device__ __forceinline__ void c2r_preprocess_multi(C2<T>* const (&bufs)[NB], int L, int t,
+                                                     int TPT, bool active,
+                                                     const C2<T>* __restrict__ twM) {
+  if (active) {
+    for (int k = t; k <= L / 2; k += TPT) {
+      if (k == 0) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const C2<T> x = bufs[b][0];
+          bufs[b][0] = mk2<T>(x.x + x.y, x.x - x.y);
+        }
+      } else {
+        const C2<T> w = cconj<T>(twM[k]);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const C2<T> xk = bufs[b][k], xm = bufs[b][L - k];
+          const C2<T> Ev = mk2<T>(xk.x + xm.x, xk.y - xm.y);
+          const C2<T> dv = mk2<T>(xk.x - xm.x, xk.y + xm.y);
+          const C2<T> Ov = cmul<T>(dv, w);
+          bufs[b][k] = mk2<T>(Ev.x - Ov.y, Ev.y + Ov.x);
+          if (2 * k != L) bufs[b][L - k] = mk2<T>(Ev.x + Ov.y, -Ev.y + Ov.x);
+        }
       }
     }
   }
@@ -922,7 +1025,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = mk2<T>((T)0, (T)0);
 
-  if (NBUF == 5) {
+  if (NBUF == 10) {
     // the five terms' transforms interleaved: d_xx Q0, d_x Q0, d_x Q1, Q1, Q2 in buffers 0..4
     if (active) {
       const size_t o = (size_t)row * L;
@@ -938,11 +1041,12 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_c2r(const C2<T>* _
       }
     }
     __syncthreads();
-#pragma unroll 1
-    for (int b = 0; b < 5; ++b) c2r_preprocess<T>(buf + b * FB(L), L, t, TPT, active, twM);
     C2<T>* const bufs[5] = {buf, buf + FB(L), buf + 2 * FB(L), buf + 3 * FB(L),
                             buf + 4 * FB(L)};
-    fft_smem_multi<T, E, +1, 5>(bufs, L, t, active, twL);
+    C2<T>* const scr[5] = {buf + 5 * FB(L), buf + 6 * FB(L), buf + 7 * FB(L),
+                           buf + 8 * FB(L), buf + 9 * FB(L)};
+    c2r_preprocess_multi<T, 5>(bufs, L, t, TPT, active, twM);
+    fft_smem_multi_pp<T, E, +1, 5>(bufs, scr, L, t, active, twL);
     if (!active) return;
     const size_t o = (size_t)row * M;
     const C2<T>* c0 = reinterpret_cast<const C2<T>*>(coef + o);
