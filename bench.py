@@ -852,6 +852,16 @@ def run_ours(args):
         plan.set(phase_times=0)
         phases = {k: round(st_ph[k], 4) for k in ("ms_residual", "ms_fft", "ms_krylov",
                                                    "ms_update", "ms_other", "ms_total")}
+        # the same solve stamped at every change of kernel class: device ms per class
+        plan.set(phase_times=2)
+        phi.zero_()
+        flush.zero_()
+        rc_c, st_c = plan.solve(fd, gd, phi)
+        torch.cuda.synchronize()
+        prof_c, _ = plan.profile()
+        plan.set(phase_times=0)
+        phases["by_kernel_class_ms"] = {k: round(v[0], 4) for k, v in prof_c.items()}
+        phases["by_kernel_class_total_ms"] = round(st_c["ms_total"], 4)
         graph_shape = {}
         for unc in (0, 4, 10):
             plan.set(uncond_steps=unc)
@@ -864,6 +874,32 @@ def run_ours(args):
             graph_shape[str(unc)] = round(statistics.median(tms), 4)
         plan.set(uncond_steps=4)
         phases["ms_per_solve_by_uncond_steps"] = graph_shape
+        kb_shape = {}
+        kb0 = int(plan.get("krylov_blocks"))
+        for kb in (1, 2, 4):
+            plan.set(krylov_blocks=kb)
+            plan.solve(fd, gd, phi)
+            tms = []
+            for _ in range(5):
+                flush.zero_()
+                m_, _ = _timed_solve(plan, fd, gd, phi, stream)
+                tms.append(m_)
+            kb_shape[str(kb)] = round(statistics.median(tms), 4)
+        plan.set(krylov_blocks=kb0)
+        phases["ms_per_solve_by_krylov_blocks_per_sm"] = kb_shape
+        l2_shape = {}
+        l20 = int(plan.get("l2_persist"))
+        for l2 in (0, 1):
+            plan.set(l2_persist=l2)
+            plan.solve(fd, gd, phi)
+            tms = []
+            for _ in range(5):
+                flush.zero_()
+                m_, _ = _timed_solve(plan, fd, gd, phi, stream)
+                tms.append(m_)
+            l2_shape[str(l2)] = round(statistics.median(tms), 4)
+        plan.set(l2_persist=l20)
+        phases["ms_per_solve_by_l2_persist"] = l2_shape
 
     # roofline of the dominant kernel class: per-solve launches from the profiled solve,
     # per-launch duration from back-to-back relaunches on this stream (CUDA events)
@@ -871,12 +907,12 @@ def run_ours(args):
     s0 = stats[0]
     timed = {}
     for k in ("residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
-              "row_c2r_update", "gmres_dots"):
+              "row_c2r_update", "gmres_dots", "gmres_update"):
         timed[k] = plan.time_kernel(k, reps=30)
     per_solve = {k: timed[k] * prof[k][1] for k in timed}
     dom = max(per_solve, key=per_solve.get)
     dom_ms = timed[dom]
-    avg_basis = 2  # the multi-dot is timed at Arnoldi step j = 2 (V_0..V_2 and w)
+    avg_basis = 5  # the multi-dot and update are timed at Arnoldi step j = 4 (V_0..V_4, w)
     bytes_launch = algorithmic_bytes(dom, P, T, avg_basis)
     peak, peak_src = peaks()
     if dom == "residual":

@@ -116,7 +116,12 @@ extern "C" {
                                    ot_stats) with a one-thread stamp kernel (%globaltimer) at
                                    every phase change, in the graph and the host-driven solve
                                    alike (a few microseconds per phase change; the stamps are
-                                   not in kernel_launches); 0 (default): those fields are -1 */
+                                   not in kernel_launches); 2: the same at every change of
+                                   kernel class (OT_PROF_*): the phase fields are then the
+                                   sums of their classes (theta's row R2C counted with the
+                                   transforms) and ot_plan_get_profile returns the device ms
+                                   per class of the last solve (launch counts 0); 0
+                                   (default): those fields are -1 */
 #define OT_OPT_TRANSPORT 23     /* 1: the solve ends with the transport distance d(f, g) of
                                    Sec. 5.2 (as ot_transport_outputs, on the translated f) in
                                    ot_stats.transport_dist; 0 (default): it is -1 */
@@ -152,6 +157,16 @@ extern "C" {
                                    conditional WHILE node, a step per iteration (0 <= s <= 16,
                                    default 4; a plan set captures every step plainly).  Same
                                    arithmetic for every s */
+#define OT_OPT_KRYLOV_BLOCKS 29 /* blocks of 256 threads per SM for the GMRES vector kernels
+                                   (multi-dot, update, init, combine), 1..8 (default 1); the
+                                   block partial sums change with it, so results differ in
+                                   the last bits between settings (each is deterministic) */
+#define OT_OPT_L2_PERSIST 30    /* 1: the graph-launched solve marks the GMRES basis V_0..V_m
+                                   as persisting L2 lines (an access-policy window on its
+                                   kernels; the process's persisting-L2 limit is raised to
+                                   the window, at most the device maximum), so that the
+                                   transform passes between two Arnoldi steps do not evict it;
+                                   0 (default): no window.  Same arithmetic either way */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,
@@ -297,11 +312,13 @@ int ot_plan_get_profile(ot_plan* plan, double* ms, int64_t* launches, int32_t n,
                         int64_t* total_launches);
 int ot_plan_reset_profile(ot_plan* plan);
 
-/* Steady-state duration of one kernel class (OT_PROF_RESIDUAL .. OT_PROF_GMRES_DOTS; the
- * multi-dot is timed at Arnoldi step j = 2): after a solve, relaunches that kernel `reps`
- * times back to back on the plan's own buffers (overwriting workspace only: the residual,
- * spectra, w, the candidate iterate and the device scalars) between two CUDA events on the
- * plan's stream; *ms receives the mean time per launch. */
+/* Steady-state duration of one kernel class (OT_PROF_RESIDUAL .. OT_PROF_GMRES_UPDATE; the
+ * multi-dot and the Arnoldi update are timed at step j = 4 of an open cycle, reset by a
+ * one-thread kernel before each launch whose own time is subtracted): after a solve,
+ * captures `reps` back-to-back launches of that kernel on the plan's own buffers
+ * (overwriting workspace only: the residual, spectra, w, the basis, the candidate iterate
+ * and the device scalars) into a CUDA graph and times one replay between two CUDA events on
+ * the plan's stream; *ms receives the mean time per launch. */
 int ot_plan_time_kernel(ot_plan* plan, int32_t kernel_class, int32_t reps, double* ms);
 
 /* ---- Step-level entry points: one stage of a Newton step each, on device buffers ---- */

@@ -58,6 +58,8 @@ struct ot_plan {
   // OT_OPT_UNCOND_STEPS: Arnoldi steps per GMRES cycle captured as plain self-skipping
   // kernels rather than IF nodes (graph)
   int uncond = 4;
+  int kbps = 1;  // OT_OPT_KRYLOV_BLOCKS: blocks per SM of the GMRES vector kernels
+  int l2persist = 0;  // OT_OPT_L2_PERSIST: the Krylov basis as persisting L2 lines (graph)
   int linsolver = 0;
   int max_bicg = 20000;
   double* fdv = nullptr;
@@ -276,7 +278,9 @@ static void note_ws_timeout(ot_stats* st, int line) {
 // a stamp kernel before the first launch of a new phase (the host tracks the phase of the
 // launch sequence it issues or captures; -1 = unknown, e.g. at a conditional body's start)
 static int stamp_phase(ot_plan* p, int cls) {
-  const int ph = p->phase_force >= 0 ? p->phase_force : phase_of(cls);
+  // OT_OPT_PHASE_TIMES = 2: a stamp at every change of kernel class (code 100 + class)
+  const int ph = p->phase_times == 2 ? 100 + (cls < 0 ? OT_PROF_OTHER : cls)
+                                     : (p->phase_force >= 0 ? p->phase_force : phase_of(cls));
   if (ph == p->last_phase) return OT_OK;
   CK(launch_stamp(p->sc, ph, p->stream));
   p->last_phase = ph;
@@ -519,13 +523,15 @@ static int alloc_tables(ot_plan* p) {
   int sms = 0;
   CK(cudaGetDevice(&p->device));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  p->kblocks = (sms > 0 ? sms : 148);  // GMRES vector kernels: 1 block of 256 per SM
+  // GMRES vector kernels: OT_OPT_KRYLOV_BLOCKS blocks of 256 threads per SM
+  p->kblocks = (sms > 0 ? sms : 148) * p->kbps;
   p->sms = sms > 0 ? sms : 148;
   return OT_OK;
 }
 
 static int alloc_grad_planes(ot_plan* p);
 static int alloc_fd_planes(ot_plan* p);
+constexpr int kMaxKrylovBlocksPerSm = 8;
 
 static int alloc_buffers(ot_plan* p) {
   free_buffers(p);
@@ -561,7 +567,7 @@ static int alloc_buffers(ot_plan* p) {
   if (p->interp) RET(alloc_grad_planes(p));
   if (p->linsolver) RET(alloc_fd_planes(p));
   size_t np = (size_t)residual_partial_blocks(p->N, p->M) * 10;
-  size_t nk = (size_t)p->kblocks * OTGB_MAXM;
+  size_t nk = (size_t)p->sms * kMaxKrylovBlocksPerSm * OTGB_MAXM;  // any OT_OPT_KRYLOV_BLOCKS
   if (nk > np) np = nk;
   CK(cudaMalloc(&p->partials, np * 8));
   CK(cudaMalloc(&p->dmean, 8));
@@ -821,6 +827,21 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       if (v < 1 || v > 1e9 || v != (double)(int)v) return OT_EINVAL;
       p->max_bicg = (int)v;
       return OT_OK;
+    case OT_OPT_KRYLOV_BLOCKS:
+      if (v < 1 || v > kMaxKrylovBlocksPerSm || v != (double)(int)v) return OT_EINVAL;
+      if (p->kbps != (int)v) {
+        p->kbps = (int)v;
+        p->kblocks = p->sms * p->kbps;
+        free_graph(p);
+      }
+      return OT_OK;
+    case OT_OPT_L2_PERSIST:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->l2persist != (int)v) {
+        p->l2persist = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_UNCOND_STEPS:
       if (v < 0 || v > OTGB_MAXM || v != (double)(int)v) return OT_EINVAL;
       if (p->uncond != (int)v) {
@@ -829,7 +850,7 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
       }
       return OT_OK;
     case OT_OPT_PHASE_TIMES:
-      if (v != 0 && v != 1) return OT_EINVAL;
+      if (v != 0 && v != 1 && v != 2) return OT_EINVAL;
       if (p->phase_times != (int)v) {
         p->phase_times = (int)v;
         free_graph(p);
@@ -885,6 +906,8 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_LINEAR_SOLVER: *v = p->linsolver; return OT_OK;
     case OT_OPT_MAX_BICG: *v = p->max_bicg; return OT_OK;
     case OT_OPT_UNCOND_STEPS: *v = p->uncond; return OT_OK;
+    case OT_OPT_KRYLOV_BLOCKS: *v = p->kbps; return OT_OK;
+    case OT_OPT_L2_PERSIST: *v = p->l2persist; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -960,7 +983,12 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
   const int N = p->N, M = p->M;
   const size_t P = (size_t)N * M;
   const bool reg = sizeof(T) == 4 && tb.mv_reg && tb.t2rA;
+  const int jstep = p->m > 4 ? 4 : p->m - 1;
+  // the relaunched kernels run outside the solve graph: no kernel may set its conditional
+  // handles (the graph may have been destroyed since the solve that left them)
+  CK(cudaMemsetAsync((char*)p->sc + offsetof(DevScalars, graph), 0, sizeof(int), p->stream));
   auto one = [&]() -> cudaError_t {
+    if (cls == -1) return launch_set_step(p->sc, jstep, p->stream);
     if (reg && cls == OT_PROF_ROW_R2C)
       return launch_mvT_r2c((const float*)p->V, P, nullptr, nullptr, (float2*)p->spec, N, M, tb,
                             nullptr, p->stream);
@@ -1005,29 +1033,38 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
                                  nullptr, p->u, p->ucand, 0.5, 1.0, N, M, tb, nullptr,
                                  p->stream);
       case OT_PROF_GMRES_DOTS:
-        return launch_gmres_dots<T>((const T*)p->V, (const T*)p->w, (long)P, p->partials,
-                                    p->sc, p->kblocks, p->stream);
+      case OT_PROF_GMRES_UPDATE: {
+        // a representative Arnoldi step: j = 4 (five basis vectors), the cycle put back open
+        // before every launch (the step's close moves j on and may end the cycle); the
+        // one-thread reset is timed alone and subtracted below
+        cudaError_t e = launch_set_step(p->sc, jstep, p->stream);
+        if (e != cudaSuccess) return e;
+        if (cls == OT_PROF_GMRES_DOTS)
+          return launch_gmres_dots<T>((const T*)p->V, (const T*)p->w, (long)P, p->partials,
+                                      p->sc, p->kblocks, p->stream);
+        return launch_gmres_update<T>((T*)p->V, (const T*)p->w, (long)P, p->partials, p->sc,
+                                      p->kblocks, p->stream, 3);
+      }
     }
     return cudaErrorInvalidValue;
   };
-  if (cls == OT_PROF_GMRES_DOTS) {
-    // a representative Arnoldi step: j = 2 (three basis vectors), cycle open
-    int jv[2] = {p->m > 2 ? 2 : p->m - 1, 0};
-    CK(cudaMemcpyAsync((char*)p->sc + offsetof(DevScalars, j), &jv[0], sizeof(int),
-                       cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync((char*)p->sc + offsetof(DevScalars, cycle_done), &jv[1], sizeof(int),
-                       cudaMemcpyHostToDevice, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
-  }
   CK(one());  // warm
   float ms = 0.f;
   RET(graph_time(p, one, reps, &ms));
+  if (cls == OT_PROF_GMRES_DOTS || cls == OT_PROF_GMRES_UPDATE) {
+    float ms0 = 0.f;
+    const int keep = cls;
+    cls = -1;  // the reset alone
+    RET(graph_time(p, one, reps, &ms0));
+    cls = keep;
+    ms -= ms0;
+  }
   *ms_per_launch = ms / reps;
   return OT_OK;
 }
 
 extern "C" int ot_plan_time_kernel(ot_plan* p, int32_t cls, int32_t reps, double* ms) {
-  if (!p || !ms || reps < 1 || cls < 0 || cls > OT_PROF_GMRES_DOTS) return OT_EINVAL;
+  if (!p || !ms || reps < 1 || cls < 0 || cls > OT_PROF_GMRES_UPDATE) return OT_EINVAL;
   CK(cudaSetDevice(p->device));
   return p->precision ? time_kernel_impl<float>(p, cls, reps, ms)
                       : time_kernel_impl<double>(p, cls, reps, ms);
@@ -1286,6 +1323,17 @@ static void fill_common_stats(ot_plan* p, const DevScalars* h, ot_stats* st) {
   double* ms[PH_COUNT] = {&st->ms_residual, &st->ms_fft, &st->ms_krylov, &st->ms_update,
                           &st->ms_other};
   for (int k = 0; k < PH_COUNT; ++k) *ms[k] = p->phase_times ? 1e-6 * (double)h->phase_ns[k] : -1.0;
+  if (p->phase_times == 2) {
+    // per kernel class: the phases are the sums of their classes (the row R2C of theta
+    // counts with the transforms here), and the profile getters return the classes
+    for (int k = 0; k < PH_COUNT; ++k) *ms[k] = 0.0;
+    for (int c = 0; c < OT_PROF_CLASSES; ++c) {
+      const double v = 1e-6 * (double)h->class_ns[c];
+      *ms[phase_of(c)] += v;
+      p->prof_ms[c] = v;
+      p->prof_n[c] = 0;
+    }
+  }
 }
 
 static int run_autotune(ot_plan* p);
@@ -1862,12 +1910,44 @@ static void abandon_captures(ot_plan* p) {
   cudaGetLastError();
 }
 
+// OT_OPT_L2_PERSIST: the GMRES basis V_0..V_m (read again by every Arnoldi step's multi-dot
+// and update) as persisting L2 lines for the kernels of the captured graph, so that the
+// transform passes' traffic between two steps does not evict it: an access-policy window on
+// the capture streams (captured into every kernel node), with the process's persisting-L2
+// limit raised to the window's size (at most the device's maximum).  Off: no window.
+static int apply_l2_window(ot_plan* p, size_t elem) {
+  cudaStreamAttrValue a;
+  memset(&a, 0, sizeof(a));
+  if (p->l2persist && !p->slab_base) {
+    const size_t vbytes = (size_t)(p->m + 1) * p->N * p->M * elem;
+    int maxp = 0, maxw = 0;
+    CK(cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, p->device));
+    CK(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, p->device));
+    const size_t win = std::min(vbytes, (size_t)maxw);
+    const size_t want = std::min(win, (size_t)maxp);
+    size_t cur = 0;
+    CK(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    if (cur < want) CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    if (win > 0 && want > 0) {
+      a.accessPolicyWindow.base_ptr = p->V;
+      a.accessPolicyWindow.num_bytes = win;
+      a.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)want / (double)win);
+      a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+      a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    }
+  }
+  for (int k = 0; k < 4; ++k)
+    CK(cudaStreamSetAttribute(p->cs[k], cudaStreamAttributeAccessPolicyWindow, &a));
+  return OT_OK;
+}
+
 template <typename T>
 static int build_graph(ot_plan* p) {
   RET(run_autotune(p));
   free_graph(p);
   for (int k = 0; k < 4; ++k)
     if (!p->cs[k]) CK(cudaStreamCreateWithFlags(&p->cs[k], cudaStreamNonBlocking));
+  RET(apply_l2_window(p, sizeof(T)));
   cudaStream_t saved = p->stream;
   const int saved_prof = p->profile;
   const long long saved_launches = p->launches;

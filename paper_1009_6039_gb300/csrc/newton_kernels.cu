@@ -349,6 +349,7 @@ __global__ void k_stamp(DevScalars* sc, int cls) {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   const int prev = sc->stamp_cls;
   if (prev >= 0 && prev < PH_COUNT && t > sc->stamp_t) sc->phase_ns[prev] += t - sc->stamp_t;
+  if (prev >= 100 && prev < 116 && t > sc->stamp_t) sc->class_ns[prev - 100] += t - sc->stamp_t;
   sc->stamp_t = t;
   sc->stamp_cls = cls;
 }
@@ -1259,6 +1260,10 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
   for (int i = 0; i <= J; ++i) acc[i] = (T)0;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  // two iterations in flight per thread for the shorter bases: the pass is bound by the
+  // latency of its loads, not by bandwidth
+  constexpr int UNR = J <= 8 ? 2 : 1;
+#pragma unroll UNR
   for (long q = tid; q < PV; q += nth) {
     T wv[W];
     vld<T>(w, q, wv);
@@ -1364,6 +1369,8 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   constexpr int W = Vec16<T>::W;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  constexpr int UNR = J <= 8 ? 2 : 1;
+#pragma unroll UNR
   for (long q = tid; q < PV; q += nth) {
     T x[W];
     vld<T>(src, q, x);
@@ -1781,6 +1788,21 @@ __global__ void k_scale_by_norm(double* __restrict__ x, long P, const DevScalars
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P;
        p += (long)gridDim.x * blockDim.x)
     x[p] *= s;
+}
+
+// kernel timing: put an Arnoldi step back to step j of an open cycle, outside any graph
+// (the step's close must not touch the conditional handles of the plan's solve graph, which
+// may have been destroyed since)
+__global__ void k_set_step(DevScalars* sc, int j) {
+  sc->j = j;
+  sc->cycle_done = 0;
+  sc->graph = 0;
+  sc->ticket[TK_DOTS] = 0;
+}
+
+cudaError_t launch_set_step(DevScalars* sc, int j, cudaStream_t st) {
+  k_set_step<<<1, 1, 0, st>>>(sc, j);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_normalize(double* x, long P, double* partials, DevScalars* sc,

@@ -70,6 +70,8 @@ struct DevScalars {
   // stamp opened (PH_* below); stamp_cls = -1 before the first stamp
   unsigned long long stamp_t;
   unsigned long long phase_ns[5];
+  // OT_OPT_PHASE_TIMES = 2: the same per kernel class (stamp codes 100 + class)
+  unsigned long long class_ns[16];
   int stamp_cls;
   // 1 while the input statistics run without the translation (OT_OPT_TRANSLATE = 0): the
   // inputs must then be positive as given
@@ -296,6 +298,8 @@ cudaError_t launch_subtract_mean(double* u, int N, int M, double* partials, DevS
 cudaError_t launch_final_gauge(UPair u, double* out, int N, int M, double* partials,
                                DevScalars* sc, double* mean_out, cudaStream_t st,
                                Bat bat = Bat());
+// kernel timing: sc->j = j, cycle open (one thread)
+cudaError_t launch_set_step(DevScalars* sc, int j, cudaStream_t st);
 // x <- x / ||x||_2 (two launches: the norm into sc->pw_norm, then the scaling; x = 0 stays 0)
 cudaError_t launch_normalize(double* x, long P, double* partials, DevScalars* sc,
                              cudaStream_t st);

@@ -608,6 +608,31 @@ def test_solve_fills_every_stats_field(ot, graph):
     assert st2["mass_defect_f"] == st["mass_defect_f"]
 
 
+def test_per_class_device_times(ot):
+    # OT_OPT_PHASE_TIMES = 2: stamps at every change of kernel class; the profile returns
+    # the device ms per class of the last (graph-launched) solve, the phase fields are the
+    # sums of their classes, and the result is that of the unstamped solve
+    N = M = 64
+    f, g = I.noise_blob_pair(N, M, s=3701)
+    p = plan(ot, N, M, "mixed", tau=1.0, tol=1e-8, eta=1e-2, symbols=1, phase_times=2)
+    phi = dev(np.zeros((N, M)))
+    rc, st = p.solve(dev(f), dev(g), phi)
+    assert rc == 0
+    prof, _ = p.profile()
+    for k in ("residual", "row_r2c", "col_matvec", "row_c2r_combine", "gmres_dots",
+              "gmres_update", "col_lbarinv", "row_c2r_update"):
+        assert prof[k][0] > 0.0, (k, prof)
+    fft = prof["row_r2c"][0] + prof["col_matvec"][0] + prof["row_c2r_combine"][0]
+    assert abs(st["ms_fft"] - fft) <= 1e-9 + 1e-9 * fft
+    assert abs(st["ms_residual"] - prof["residual"][0]) <= 1e-9
+    assert sum(v[0] for v in prof.values()) <= 1.05 * st["ms_total"] + 0.02
+    p.set(phase_times=0)
+    phi2 = dev(np.zeros((N, M)))
+    rc2, st2 = p.solve(dev(f), dev(g), phi2)
+    p.close()
+    assert rc2 == 0 and np.array_equal(phi2.cpu().numpy(), phi.cpu().numpy())
+
+
 def test_untranslated_inputs_are_checked(ot):
     # OT_OPT_TRANSLATE = 0: inputs are used as given, so they must be positive as they are;
     # the statistics still report the mass defects
