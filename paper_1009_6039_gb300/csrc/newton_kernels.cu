@@ -1285,6 +1285,19 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
   }
   double v[J + 1];
   if constexpr (sizeof(T) == 4) {
+    if (pass == 0 && !sc->reorth) {
+      // single-reduction step in FP32: the block's sums go to its partials and the update
+      // kernel finishes the step (every block of it sums the partials in the same order;
+      // its block 0 closes the step) -- no last-block pass and no serial close here
+      block_sum_f<J + 1>(acc);
+      if (threadIdx.x == 0) {
+        float* pf = reinterpret_cast<float*>(partials);
+#pragma unroll
+        for (int a = 0; a <= J; ++a) pf[(size_t)blockIdx.x * (J + 1) + a] = acc[a];
+        if (blockIdx.x == 0) sc->jd = J - 1;
+      }
+      return;
+    }
     if (!grid_sum_f<J + 1>(acc, partials, &sc->ticket[TK_DOTS])) return;
 #pragma unroll
     for (int i = 0; i <= J; ++i) v[i] = (double)acc[i];
@@ -1359,16 +1372,61 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
                                          double* partials, DevScalars* sc, int mode) {
   const int j = J - 1, m = sc->m;
   T coefs[J];
+  double hv[J], hn = 0.0;
+  bool weak = false;
+  if (sizeof(T) == 4 && mode == 3) {
+    // finish the multi-dot of step j: the (J + 1) sums over the dots kernel's blocks, each
+    // taken by one warp in a fixed order (lane-strided, then a shuffle tree), so that every
+    // block obtains the same values; h_i = scale_i V_i.w, and ||w - sum h_i v_i||^2 =
+    // w.w - sum h_i^2 (Pythagoras, v_i orthonormal): below 1e-6 w.w the step is weak and
+    // the cycle ends (the restart's explicit residual decides)
+    __shared__ double sv[OTGB_MAXM + 1];
+    const float* pf = reinterpret_cast<const float*>(partials);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = gridDim.x;
+    for (int a = wid; a <= J; a += nw) {
+      double x = 0.0;
+      for (int b = lane; b < nb; b += 32) x += (double)pf[(size_t)b * (J + 1) + a];
 #pragma unroll
-  for (int i = 0; i < J; ++i)
-    coefs[i] = (T)((mode == 2 ? sc->h2[i] : (mode == 3 ? sc->hcol[i] : sc->H[i * m + j])) *
-                   sc->scale[i]);
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) sv[a] = x;
+    }
+    __syncthreads();
+    double hs = 0.0;
+#pragma unroll
+    for (int i = 0; i < J; ++i) {
+      hv[i] = sc->scale[i] * sv[i];
+      hs += hv[i] * hv[i];
+    }
+    const double ww = sv[J], hn2 = ww - hs;
+    weak = !(hn2 > 1e-6 * ww);
+    hn = weak ? 0.0 : sqrt(hn2);
+#pragma unroll
+    for (int i = 0; i < J; ++i) coefs[i] = (T)(hv[i] * sc->scale[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < J; ++i)
+      coefs[i] = (T)((mode == 2 ? sc->h2[i] : (mode == 3 ? sc->hcol[i] : sc->H[i * m + j])) *
+                     sc->scale[i]);
+  }
   T* Vn = V + (size_t)(j + 1) * P;
   const T* src = (mode == 2) ? Vn : w;
   T acc = (T)0;
   constexpr int W = Vec16<T>::W;
-  const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
+  // FP32 mode 3: block 0 closes the step (one thread's serial FP64 work and round trips)
+  // while the other blocks form v_(j+1); otherwise every block takes part
+  const bool closer = sizeof(T) == 4 && mode == 3 && gridDim.x > 1;
+  if (closer && blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < J; ++i) sc->hcol[i] = hv[i];
+      arnoldi_close_j<J>(sc, hv, hn, weak);
+    }
+    return;
+  }
+  const long bid = closer ? blockIdx.x - 1 : blockIdx.x, nbk = closer ? gridDim.x - 1 : gridDim.x;
+  const long tid = bid * (long)blockDim.x + threadIdx.x;
+  const long nth = nbk * blockDim.x, PV = nvec(P, W);
   constexpr int UNR = J <= 8 ? 2 : 1;
 #pragma unroll UNR
   for (long q = tid; q < PV; q += nth) {
@@ -1392,9 +1450,16 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     Vn[p] = x;
     acc += x * x;
   }
-  // mode 1: first of two passes, the norm follows the second; mode 3: the norm and the
-  // rotation were finished by the multi-dot (Pythagoras)
-  if (mode == 1 || mode == 3) return;
+  // mode 1: first of two passes, the norm follows the second; mode 3: the step was closed
+  // by block 0 above (FP32) or by the multi-dot (FP64)
+  if (mode == 1 || mode == 3) {
+    if (sizeof(T) == 4 && mode == 3 && !closer && blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < J; ++i) sc->hcol[i] = hv[i];
+      arnoldi_close_j<J>(sc, hv, hn, weak);
+    }
+    return;
+  }
   double v[1] = {(double)acc};
   if constexpr (sizeof(T) == 4) {
     float a[1] = {acc};
@@ -1420,8 +1485,10 @@ __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long 
   partials = badv(partials, bat);
   sc = badv(sc, bat);
   if (bskip(sc, bat) || sc->cycle_done) return;
-  // mode 3 runs after the multi-dot closed the step (sc->j already advanced)
-  switch (mode == 3 ? sc->j - 1 : sc->j) {
+  // mode 3 follows the multi-dot of step jd (FP32: the update closes the step itself and
+  // advances sc->j, so it reads the step from jd; FP64: the multi-dot closed it and advanced
+  // sc->j)
+  switch (mode == 3 ? (sizeof(T) == 4 ? sc->jd : sc->j - 1) : sc->j) {
 #define OTGB_UPD_CASE(k) \
   case k:                \
     update_j<T, k + 1>(V, w, P, partials, sc, mode); break;
@@ -1795,6 +1862,7 @@ __global__ void k_scale_by_norm(double* __restrict__ x, long P, const DevScalars
 // may have been destroyed since)
 __global__ void k_set_step(DevScalars* sc, int j) {
   sc->j = j;
+  sc->jd = j;
   sc->cycle_done = 0;
   sc->graph = 0;
   sc->ticket[TK_DOTS] = 0;

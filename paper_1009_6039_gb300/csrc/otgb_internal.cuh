@@ -45,6 +45,7 @@ struct DevScalars {
   double hcol[OTGB_MAXM];       // column j of H before the rotations (the update's weights)
   double relres;
   int j, jend, m, cycle_done, converged, iters, cycles;
+  int jd;  // FP32 single-reduction step: the step index of the last multi-dot (for the update)
   double eta, tau;
   double tau_switch;  // tau schedule: tau becomes 1 once res_inf < tau_switch (0: off)
   // Newton control, resident on the device for the graph-launched solve
