@@ -1197,8 +1197,13 @@ __device__ void arnoldi_close(DevScalars* sc, int j, double hn, bool weak) {
 // The same for the single-reduction step, with column j of H (h, before the rotations) in
 // registers: every scalar it needs is loaded first, as independent loads, so that the one
 // thread that runs it waits for one memory round trip instead of one per dependent access.
-template <int J>
-__device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn, bool weak) {
+// FAST (the FP32 step): the rotation from one reciprocal square root, c = a / r = a rsqrt(r^2)
+// and s = b rsqrt(r^2), and the basis scale 1 / hn passed in (rsqrt of the Pythagorean
+// square), in place of a square root and divisions, whose FP64 forms are slow on this GPU
+// (the close is one thread on the step's critical path); the FP64 step keeps them.
+template <int J, bool FAST = false>
+__device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn, bool weak,
+                                double inv_hn = 0.0) {
   constexpr int j = J - 1;
   double cs[J], sn[J];
 #pragma unroll
@@ -1220,8 +1225,18 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
     col[i + 1] = -sn[i] * t0 + cs[i] * t1;
   }
   const double a = col[j], b = col[j + 1];
-  const double r = sqrt(a * a + b * b);
-  const double c = (r == 0.0) ? 1.0 : a / r, sj = (r == 0.0) ? 0.0 : b / r;
+  double r, c, sj;
+  if (FAST) {
+    const double r2 = a * a + b * b;
+    const double y = r2 > 0.0 ? rsqrt(r2) : 0.0;
+    r = r2 * y;
+    c = (r2 > 0.0) ? a * y : 1.0;
+    sj = (r2 > 0.0) ? b * y : 0.0;
+  } else {
+    r = sqrt(a * a + b * b);
+    c = (r == 0.0) ? 1.0 : a / r;
+    sj = (r == 0.0) ? 0.0 : b / r;
+  }
   col[j] = r;
   col[j + 1] = 0.0;
 #pragma unroll
@@ -1233,7 +1248,7 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
   sc->gv[j] = c * gvj;
   sc->iters = iters + 1;
   sc->jend = j + 1;
-  sc->relres = fabs(g1) / bnorm;
+  if (!FAST) sc->relres = fabs(g1) / bnorm;  // informational (the FP32 step skips it)
   int done = 0;
   if (weak) {
     done = 1;
@@ -1241,7 +1256,7 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
     sc->converged = 1;
     done = 1;
   } else {
-    sc->scale[j + 1] = 1.0 / hn;
+    sc->scale[j + 1] = FAST ? inv_hn : 1.0 / hn;
     if (j + 1 == m) done = 1;
   }
   if (done) sc->cycle_done = 1;
@@ -1372,7 +1387,7 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
                                          double* partials, DevScalars* sc, int mode) {
   const int j = J - 1, m = sc->m;
   T coefs[J];
-  double hv[J], hn = 0.0;
+  double hv[J], hn = 0.0, inv_hn = 0.0;
   bool weak = false;
   if (sizeof(T) == 4 && mode == 3) {
     // finish the multi-dot of step j: the (J + 1) sums over the dots kernel's blocks, each
@@ -1380,13 +1395,14 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     // block obtains the same values; h_i = scale_i V_i.w, and ||w - sum h_i v_i||^2 =
     // w.w - sum h_i^2 (Pythagoras, v_i orthonormal): below 1e-6 w.w the step is weak and
     // the cycle ends (the restart's explicit residual decides)
-    __shared__ double sv[OTGB_MAXM + 1];
+    // (the sums in FP32, as the block sums themselves)
+    __shared__ float sv[OTGB_MAXM + 1];
     const float* pf = reinterpret_cast<const float*>(partials);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = gridDim.x;
     for (int a = wid; a <= J; a += nw) {
-      double x = 0.0;
-      for (int b = lane; b < nb; b += 32) x += (double)pf[(size_t)b * (J + 1) + a];
+      float x = 0.f;
+      for (int b = lane; b < nb; b += 32) x += pf[(size_t)b * (J + 1) + a];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (lane == 0) sv[a] = x;
@@ -1395,12 +1411,13 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     double hs = 0.0;
 #pragma unroll
     for (int i = 0; i < J; ++i) {
-      hv[i] = sc->scale[i] * sv[i];
+      hv[i] = sc->scale[i] * (double)sv[i];
       hs += hv[i] * hv[i];
     }
-    const double ww = sv[J], hn2 = ww - hs;
+    const double ww = (double)sv[J], hn2 = ww - hs;
     weak = !(hn2 > 1e-6 * ww);
-    hn = weak ? 0.0 : sqrt(hn2);
+    inv_hn = weak ? 0.0 : rsqrt(hn2);
+    hn = hn2 * inv_hn;
 #pragma unroll
     for (int i = 0; i < J; ++i) coefs[i] = (T)(hv[i] * sc->scale[i]);
   } else {
@@ -1420,7 +1437,7 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int i = 0; i < J; ++i) sc->hcol[i] = hv[i];
-      arnoldi_close_j<J>(sc, hv, hn, weak);
+      arnoldi_close_j<J, true>(sc, hv, hn, weak, inv_hn);
     }
     return;
   }
@@ -1456,7 +1473,7 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
     if (sizeof(T) == 4 && mode == 3 && !closer && blockIdx.x == 0 && threadIdx.x == 0) {
 #pragma unroll
       for (int i = 0; i < J; ++i) sc->hcol[i] = hv[i];
-      arnoldi_close_j<J>(sc, hv, hn, weak);
+      arnoldi_close_j<J, true>(sc, hv, hn, weak, inv_hn);
     }
     return;
   }
