@@ -1268,17 +1268,14 @@ __device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn,
 // of 16 bytes); partials are combined across threads and blocks in FP64.
 template <typename T, int J>
 __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restrict__ w, long P,
-                                       double* partials, DevScalars* sc, int pass) {
+                                       double* partials, DevScalars* sc, int pass,
+                                       bool split) {
   constexpr int W = Vec16<T>::W;
   T acc[J + 1];  // V_i . w (i < J) and w . w
 #pragma unroll
   for (int i = 0; i <= J; ++i) acc[i] = (T)0;
   const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
   const long nth = (long)gridDim.x * blockDim.x, PV = nvec(P, W);
-  // two iterations in flight per thread for the shorter bases: the pass is bound by the
-  // latency of its loads, not by bandwidth
-  constexpr int UNR = J <= 8 ? 2 : 1;
-#pragma unroll UNR
   for (long q = tid; q < PV; q += nth) {
     T wv[W];
     vld<T>(w, q, wv);
@@ -1300,10 +1297,10 @@ __device__ __forceinline__ void dots_j(const T* __restrict__ V, const T* __restr
   }
   double v[J + 1];
   if constexpr (sizeof(T) == 4) {
-    if (pass == 0 && !sc->reorth) {
-      // single-reduction step in FP32: the block's sums go to its partials and the update
-      // kernel finishes the step (every block of it sums the partials in the same order;
-      // its block 0 closes the step) -- no last-block pass and no serial close here
+    if (split && pass == 0 && !sc->reorth) {
+      // single-reduction step in FP32 (split): the block's sums go to its partials and the
+      // update kernel finishes the step (every block of it sums the partials in the same
+      // order; its block 0 closes the step) -- no last-block pass and no serial close here
       block_sum_f<J + 1>(acc);
       if (threadIdx.x == 0) {
         float* pf = reinterpret_cast<float*>(partials);
@@ -1370,10 +1367,13 @@ __global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, l
   sc = badv(sc, bat);
   if (bskip(sc, bat) || sc->cycle_done) return;
   if (pass) w = V + (size_t)(sc->j + 1) * P;
+  // the split step (close in the update) serves single problems; a plan set's classes keep
+  // the close in the multi-dot's last block (measured faster for their small per-pair grids)
+  const bool split = !bat.on;
   switch (sc->j) {
 #define OTGB_DOTS_CASE(k) \
   case k:                 \
-    dots_j<T, k + 1>(V, w, P, partials, sc, pass); break;
+    dots_j<T, k + 1>(V, w, P, partials, sc, pass, split); break;
     OTGB_DOTS_CASE(0) OTGB_DOTS_CASE(1) OTGB_DOTS_CASE(2) OTGB_DOTS_CASE(3)
     OTGB_DOTS_CASE(4) OTGB_DOTS_CASE(5) OTGB_DOTS_CASE(6) OTGB_DOTS_CASE(7)
     OTGB_DOTS_CASE(8) OTGB_DOTS_CASE(9) OTGB_DOTS_CASE(10) OTGB_DOTS_CASE(11)
@@ -1384,12 +1384,13 @@ __global__ void k_gmres_dots(const T* __restrict__ V, const T* __restrict__ w, l
 
 template <typename T, int J>
 __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict__ w, long P,
-                                         double* partials, DevScalars* sc, int mode) {
+                                         double* partials, DevScalars* sc, int mode,
+                                         bool split) {
   const int j = J - 1, m = sc->m;
   T coefs[J];
   double hv[J], hn = 0.0, inv_hn = 0.0;
   bool weak = false;
-  if (sizeof(T) == 4 && mode == 3) {
+  if (sizeof(T) == 4 && mode == 3 && split) {
     // finish the multi-dot of step j: the (J + 1) sums over the dots kernel's blocks, each
     // taken by one warp in a fixed order (lane-strided, then a shuffle tree), so that every
     // block obtains the same values; h_i = scale_i V_i.w, and ||w - sum h_i v_i||^2 =
@@ -1432,7 +1433,7 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   constexpr int W = Vec16<T>::W;
   // FP32 mode 3: block 0 closes the step (one thread's serial FP64 work and round trips)
   // while the other blocks form v_(j+1); otherwise every block takes part
-  const bool closer = sizeof(T) == 4 && mode == 3 && gridDim.x > 1;
+  const bool closer = sizeof(T) == 4 && mode == 3 && split && gridDim.x > 1;
   if (closer && blockIdx.x == 0) {
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -1444,8 +1445,6 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   const long bid = closer ? blockIdx.x - 1 : blockIdx.x, nbk = closer ? gridDim.x - 1 : gridDim.x;
   const long tid = bid * (long)blockDim.x + threadIdx.x;
   const long nth = nbk * blockDim.x, PV = nvec(P, W);
-  constexpr int UNR = J <= 8 ? 2 : 1;
-#pragma unroll UNR
   for (long q = tid; q < PV; q += nth) {
     T x[W];
     vld<T>(src, q, x);
@@ -1470,7 +1469,8 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   // mode 1: first of two passes, the norm follows the second; mode 3: the step was closed
   // by block 0 above (FP32) or by the multi-dot (FP64)
   if (mode == 1 || mode == 3) {
-    if (sizeof(T) == 4 && mode == 3 && !closer && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sizeof(T) == 4 && mode == 3 && split && !closer && blockIdx.x == 0 &&
+        threadIdx.x == 0) {
 #pragma unroll
       for (int i = 0; i < J; ++i) sc->hcol[i] = hv[i];
       arnoldi_close_j<J, true>(sc, hv, hn, weak, inv_hn);
@@ -1502,13 +1502,14 @@ __global__ void k_gmres_update(T* __restrict__ V, const T* __restrict__ w, long 
   partials = badv(partials, bat);
   sc = badv(sc, bat);
   if (bskip(sc, bat) || sc->cycle_done) return;
-  // mode 3 follows the multi-dot of step jd (FP32: the update closes the step itself and
-  // advances sc->j, so it reads the step from jd; FP64: the multi-dot closed it and advanced
-  // sc->j)
-  switch (mode == 3 ? (sizeof(T) == 4 ? sc->jd : sc->j - 1) : sc->j) {
+  // mode 3 follows the multi-dot of step jd (FP32, single problem: the update closes the
+  // step itself and advances sc->j, so it reads the step from jd; FP64 and plan-set classes:
+  // the multi-dot closed it and advanced sc->j)
+  const bool split = sizeof(T) == 4 && !bat.on;
+  switch (mode == 3 ? (split ? sc->jd : sc->j - 1) : sc->j) {
 #define OTGB_UPD_CASE(k) \
   case k:                \
-    update_j<T, k + 1>(V, w, P, partials, sc, mode); break;
+    update_j<T, k + 1>(V, w, P, partials, sc, mode, split); break;
     OTGB_UPD_CASE(0) OTGB_UPD_CASE(1) OTGB_UPD_CASE(2) OTGB_UPD_CASE(3)
     OTGB_UPD_CASE(4) OTGB_UPD_CASE(5) OTGB_UPD_CASE(6) OTGB_UPD_CASE(7)
     OTGB_UPD_CASE(8) OTGB_UPD_CASE(9) OTGB_UPD_CASE(10) OTGB_UPD_CASE(11)
