@@ -792,6 +792,16 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
   const int cs = NBUF * FB(N);
   C2<T>* buf = sm + q * cs;
 
+  // the interleaved FP32 matvec pass keeps its stage twiddle table in shared memory (after
+  // the columns' buffers): every stage reads R - 1 twiddles per butterfly, and from global
+  // memory those loads sat on the stage chain's critical path
+  const C2<T>* twS = twN;
+  if (NBUF == 3) {
+    C2<T>* tws = sm + Q * cs;
+    const C2<T>* src = twN + (size_t)stage_table_slot<E>() * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tws[i] = src[i];
+    twS = tws - (size_t)stage_table_slot<E>() * N;  // the fft routines add the slot back
+  }
   col_load<T, E>(spec, sm, N, Lc, Q, col0, cs);
   __syncthreads();
   if (MODE == COL_INV) {
@@ -799,7 +809,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
     col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
     return;
   }
-  fft_smem<T, E, -1>(buf, N, t, active, twN);
+  fft_smem<T, E, -1>(buf, N, t, active, twS);
   if (MODE == COL_FWD) {
     col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
     return;
@@ -871,7 +881,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value, (E == 4 && sizeof(T) == 
     }
     __syncthreads();
     C2<T>* const bufs[3] = {buf, buf + FB(N), buf + 2 * FB(N)};
-    fft_smem_multi<T, E, +1, 3>(bufs, N, t, active, twN);
+    fft_smem_multi<T, E, +1, 3>(bufs, N, t, active, twS);
     col_store<T, E>(out0, sm, N, Lc, Q, col0, cs);
     col_store<T, E>(out1, sm + FB(N), N, Lc, Q, col0, cs);
     col_store<T, E>(out2, sm + 2 * FB(N), N, Lc, Q, col0, cs);
@@ -1793,7 +1803,8 @@ cudaError_t col_E(const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>* o2, int N, int
     while (Q > 1 && (Q * TPT > MaxThreads<T>::value || (size_t)Q * colb > 160 * 1024)) Q /= 2;
   }
   if (Q > Lc) Q = Lc;
-  const size_t sm = (size_t)Q * colb;
+  size_t sm = (size_t)Q * colb;
+  if (col_nbuf<T, E, MODE>() == 3) sm += (size_t)N * sizeof(C2<T>);  // stage twiddle table
   cudaError_t e = prepare_launch(k_col<T, E, MODE>, Q * TPT, sm);
   if (e != cudaSuccess) return e;
   k_col<T, E, MODE><<<bgrid(dim3((Lc + Q - 1) / Q), bat), Q * TPT, sm, st>>>(
