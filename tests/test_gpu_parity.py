@@ -645,6 +645,30 @@ def test_per_class_device_times(ot):
     assert rc2 == 0 and np.array_equal(phi2.cpu().numpy(), phi.cpu().numpy())
 
 
+def test_graph_shape_options_keep_the_result(ot):
+    # OT_OPT_UNCOND_STEPS (plain Arnoldi steps before the WHILE tail) and OT_OPT_L2_PERSIST
+    # change the graph, not the arithmetic: bit-identical potentials and counts;
+    # OT_OPT_KRYLOV_BLOCKS changes the block partial sums of the Krylov reductions: the same
+    # root within the mixed-mode bound
+    N = M = 128
+    f, g = I.noise_blob_pair(N, M, s=3702)
+    base = dict(tau=1.0, tol=1e-8, eta=1e-2, symbols=1)
+    results = {}
+    for key, val in (("uncond_steps", 4), ("uncond_steps", 0), ("uncond_steps", 10),
+                     ("l2_persist", 1), ("krylov_blocks", 2), ("krylov_blocks", 4)):
+        p = plan(ot, N, M, "mixed", **base, **{key: val})
+        phi = dev(np.zeros((N, M)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["res_inf"] < 1e-8, (key, val, st)
+        results[(key, val)] = (phi.cpu().numpy(), st["newton_iters"], st["gmres_iters"])
+    ref = results[("uncond_steps", 4)]
+    for k in (("uncond_steps", 0), ("uncond_steps", 10), ("l2_persist", 1)):
+        assert np.array_equal(results[k][0], ref[0]) and results[k][1:] == ref[1:], k
+    for k in (("krylov_blocks", 2), ("krylov_blocks", 4)):
+        assert np.abs(results[k][0] - ref[0]).max() <= 1e-6, k
+
+
 def test_untranslated_inputs_are_checked(ot):
     # OT_OPT_TRANSLATE = 0: inputs are used as given, so they must be positive as they are;
     # the statistics still report the mass defects
