@@ -189,6 +189,10 @@ extern "C" {
 #define OT_PROF_OTHER 9            /* input translation, prefilter, final reductions */
 #define OT_PROF_WARMSTART 10       /* learned warm start (features, network, Poisson solves) */
 #define OT_PROF_CLASSES 11
+/* ot_plan_time_kernel only (not a profile class): the learned warm start's network kernel
+ * (BF16 tcgen05) on the plan's feature planes, one row per grid point; needs a plan with
+ * weights set that has run a solve with the learned warm start */
+#define OT_TIME_WS_NETWORK 32
 
 typedef struct ot_plan ot_plan;
 
@@ -312,7 +316,8 @@ int ot_plan_get_profile(ot_plan* plan, double* ms, int64_t* launches, int32_t n,
                         int64_t* total_launches);
 int ot_plan_reset_profile(ot_plan* plan);
 
-/* Steady-state duration of one kernel class (OT_PROF_RESIDUAL .. OT_PROF_GMRES_UPDATE; the
+/* Steady-state duration of one kernel class (OT_PROF_RESIDUAL .. OT_PROF_GMRES_UPDATE, or
+ * OT_TIME_WS_NETWORK; the
  * multi-dot and the Arnoldi update are timed at step j = 4 of an open cycle, reset by a
  * one-thread kernel before each launch whose own time is subtracted): after a solve,
  * captures `reps` back-to-back launches of that kernel on the plan's own buffers

@@ -29,6 +29,7 @@ OT_OPT_KRYLOV_BLOCKS, OT_OPT_L2_PERSIST = 29, 30
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
+OT_TIME_WS_NETWORK = 32  # ot_plan_time_kernel only: the warm start's network kernel
 
 EXPORTS = ["ot_plan_create", "ot_plan_set_option", "ot_plan_get_option", "ot_plan_set_stream",
            "ot_solve", "ot_solve_host", "ot_solve_batched", "ot_plan_destroy", "ot_strerror",
@@ -471,10 +472,11 @@ class Plan:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(PROF_CLASSES)}, int(tot[0])
 
     def time_kernel(self, name, reps=50):
-        """Mean ms per launch of one kernel class, relaunched back to back after a solve."""
+        """Mean ms per launch of one kernel class (a PROF_CLASSES name, or "ws_network"),
+        relaunched back to back after a solve."""
         ms = ctypes.c_double()
-        _check(ot_plan_time_kernel(self.h, PROF_CLASSES.index(name), reps, ctypes.byref(ms)),
-               "time_kernel")
+        cls = OT_TIME_WS_NETWORK if name == "ws_network" else PROF_CLASSES.index(name)
+        _check(ot_plan_time_kernel(self.h, cls, reps, ctypes.byref(ms)), "time_kernel")
         return ms.value
 
     def reset_profile(self):

@@ -1032,6 +1032,9 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
         return launch_row_c2r<T>(ROWINV_UPDATE, (C2<T>*)p->q0, nullptr, nullptr, nullptr,
                                  nullptr, p->u, p->ucand, 0.5, 1.0, N, M, tb, nullptr,
                                  p->stream);
+      case OT_TIME_WS_NETWORK:
+        return launch_ws_mlp(p->ws_wpack, p->ws_params, p->ws_X, (long)P, p->ws_s,
+                             &p->sc->ws_err, p->sms, p->stream, 0);
       case OT_PROF_GMRES_DOTS:
       case OT_PROF_GMRES_UPDATE: {
         // a representative Arnoldi step: j = 4 (five basis vectors), the cycle put back open
@@ -1064,7 +1067,12 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
 }
 
 extern "C" int ot_plan_time_kernel(ot_plan* p, int32_t cls, int32_t reps, double* ms) {
-  if (!p || !ms || reps < 1 || cls < 0 || cls > OT_PROF_GMRES_UPDATE) return OT_EINVAL;
+  if (!p || !ms || reps < 1) return OT_EINVAL;
+  if (cls == OT_TIME_WS_NETWORK) {
+    if (!p->ws_have || !p->ws_X || !p->ws_s) return OT_EINVAL;
+  } else if (cls < 0 || cls > OT_PROF_GMRES_UPDATE) {
+    return OT_EINVAL;
+  }
   CK(cudaSetDevice(p->device));
   return p->precision ? time_kernel_impl<float>(p, cls, reps, ms)
                       : time_kernel_impl<double>(p, cls, reps, ms);

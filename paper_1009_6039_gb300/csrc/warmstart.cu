@@ -452,7 +452,55 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// SiLU z / (1 + e^-z) of four values (two packed pairs) with one reciprocal.  The readout
+// of the tensor-core network is bound by instruction issue and the special-function unit
+// (an exponential and a reciprocal per value): the elementwise steps run as packed FP32
+// pairs (FADD2 / FMUL2), and Montgomery's simultaneous inversion (1 / (d0 d1 d2 d3) and the
+// partial products give every 1/d_i) leaves a quarter reciprocal per value, at a few ulp of
+// extra error.  The exponent 2^t, t = -z log2(e), is capped at 2^30 so that the product of
+// four denominators stays finite (below z = -20.8 the value is then -|z| 2^-30 instead of
+// -|z| e^-|z|, both negligible against the O(1) activations they are summed with).
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void silu_x4(float2& z01, float2& z23) {
+  const float2 nl = make_float2(-1.4426950408889634f, -1.4426950408889634f);
+  const float2 one = make_float2(1.0f, 1.0f);
+  const float2 t01 = __fmul2_rn(z01, nl), t23 = __fmul2_rn(z23, nl);
+  const float2 d01 = __fadd2_rn(
+      make_float2(ex2_ftz(fminf(t01.x, 30.0f)), ex2_ftz(fminf(t01.y, 30.0f))), one);
+  const float2 d23 = __fadd2_rn(
+      make_float2(ex2_ftz(fminf(t23.x, 30.0f)), ex2_ftz(fminf(t23.y, 30.0f))), one);
+  const float ab = d01.x * d01.y, cd = d23.x * d23.y;
+  const float rp = rcp_ftz(ab * cd);
+  const float iab = cd * rp, icd = ab * rp;
+  z01 = __fmul2_rn(z01, make_float2(d01.y * iab, d01.x * iab));
+  z23 = __fmul2_rn(z23, make_float2(d23.y * icd, d23.x * icd));
+}
+
+// bias + SiLU of 32 accumulator values (bias: 32 FP32 values in shared memory, 16-byte
+// aligned), in place
+__device__ __forceinline__ void bias_silu32(float (&v)[32], const float* bias) {
+  const float4* b4 = reinterpret_cast<const float4*>(bias);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 b = b4[q];
+    float2 z01 = __fadd2_rn(make_float2(v[4 * q], v[4 * q + 1]), make_float2(b.x, b.y));
+    float2 z23 = __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(b.z, b.w));
+    silu_x4(z01, z23);
+    v[4 * q] = z01.x;
+    v[4 * q + 1] = z01.y;
+    v[4 * q + 2] = z23.x;
+    v[4 * q + 3] = z23.y;
+  }
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -504,8 +552,7 @@ __device__ __forceinline__ void readout_row(uint32_t trow, const float* bias, un
   for (int col = 0; col < 128; col += 32) {
     float v[32];
     tmem_ld32(trow + col, v);
-#pragma unroll
-    for (int q = 0; q < 32; ++q) v[q] = silu_f(v[q] + bias[col + q]);
+    bias_silu32(v, bias + col);
 #pragma unroll
     for (int q = 0; q < 4; ++q) st_row8(sA, r, col + 8 * q, v + 8 * q);
   }
@@ -621,17 +668,24 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
       if (layer < 2) {
         readout_row(trow, sb + 128 * layer, sA, r);
       } else {
-        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32 over the row
-        float acc = sb[512];
+        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32 over the row (two
+        // packed partial sums, even and odd j)
+        float2 acc2 = make_float2(0.0f, 0.0f);
 #pragma unroll 1
         for (int col = 0; col < 128; col += 32) {
           float v[32];
           tmem_ld32(trow + col, v);
+          bias_silu32(v, sb + 256 + col);
+          const float4* w4 = reinterpret_cast<const float4*>(sb + 384 + col);
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            acc = fmaf(sb[384 + col + q], silu_f(v[q] + sb[256 + col + q]), acc);
+          for (int q = 0; q < 8; ++q) {
+            const float4 w = w4[q];
+            acc2 = __ffma2_rn(make_float2(w.x, w.y), make_float2(v[4 * q], v[4 * q + 1]), acc2);
+            acc2 = __ffma2_rn(make_float2(w.z, w.w), make_float2(v[4 * q + 2], v[4 * q + 3]),
+                              acc2);
+          }
         }
-        if (row < rows) out[row] = acc;
+        if (row < rows) out[row] = sb[512] + (acc2.x + acc2.y);
       }
     }
   }

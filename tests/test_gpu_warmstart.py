@@ -223,6 +223,32 @@ def test_warm_started_solve(ot, prec):
     assert out[(2, 1)][1]["newton_iters"] == out[(2, 0)][1]["newton_iters"]
 
 
+def test_network_kernel_timing_class(ot):
+    # ot_plan_time_kernel(OT_TIME_WS_NETWORK) relaunches the network kernel on the solve's
+    # features: a positive time, and a later solve is unchanged (only workspace is written);
+    # a plan without weights refuses the class
+    import ctypes
+    N = M = 64
+    f, g = I.noise_blob_pair(N, M, s=3300)
+    p = ot.Plan(N, M, tau=2.0, tol=1e-8, precision="mixed", eta=0.1)
+    p.set_weights(random_params(13, scale=0.01)).set(warm_start=2)
+    phi1 = dev(np.zeros((N, M)))
+    assert p.solve(dev(f), dev(g), phi1)[0] == 0
+    ms = p.time_kernel("ws_network", reps=5)
+    assert 0.0 < ms < 50.0
+    phi2 = dev(np.zeros((N, M)))
+    assert p.solve(dev(f), dev(g), phi2)[0] == 0
+    assert np.array_equal(phi1.cpu().numpy(), phi2.cpu().numpy())
+    q = ot.Plan(N, M, tau=2.0, tol=1e-8, precision="mixed", eta=0.1)
+    assert q.solve(dev(f), dev(g), dev(np.zeros((N, M))))[0] == 0
+    out = ctypes.c_double()
+    assert ot.ot_plan_time_kernel(q.h, ot.OT_TIME_WS_NETWORK, 5, ctypes.byref(out)) == \
+        ot.OT_EINVAL
+    assert ot.ot_plan_time_kernel(q.h, 11, 5, ctypes.byref(out)) == ot.OT_EINVAL
+    p.close()
+    q.close()
+
+
 def test_weights_file_round_trip(ot, tmp_path):
     params = random_params(14)
     path = str(tmp_path / "w.otws")
