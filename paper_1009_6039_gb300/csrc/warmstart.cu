@@ -350,8 +350,11 @@ __global__ void k_ws_scale(double* __restrict__ u, long P, const double* __restr
 //
 // One CTA of 128 threads takes 128-row tiles of X: thread r owns row r, which is TMEM lane
 // r of the accumulator (warp w reads lanes 32w..32w+31).  Per tile: X (converted to BF16)
-// -> MMA with W0 (K = 16) -> TMEM -> bias + SiLU -> BF16 activations in shared memory ->
-// 8 MMAs with W1 (K = 128) -> ... -> W2 -> bias + SiLU -> dot with w3 in FP32 -> s.
+// -> MMA with W0 (K = 16) -> TMEM -> SiLU -> BF16 activations in shared memory -> 8 MMAs
+// with W1 (K = 128) -> ... -> W2 -> SiLU -> dot with w3 in FP32 -> s.  The biases b0, b1,
+// b2 ride in the matrix products: one more K block per layer, whose B rows hold the bias
+// split into two BF16 parts (hi = bf16(b), lo = bf16(b - hi), b to 2^-17 relative) against
+// an A block of ones in its first two columns, so that the accumulator holds z = a W^T + b.
 //
 // Operands are K-major BF16 in the no-swizzle canonical layout: 8-row x 16-byte core
 // matrices, the two core matrices of a 16-wide K block 128 bytes apart (LBO) and
@@ -367,15 +370,17 @@ __host__ __device__ constexpr int op_offset(int r, int k) {
 // 128-row tile, activation buffer, TMEM accumulator (128 columns) and mbarrier
 constexpr int WS_CH = 4;
 
-constexpr int SM_W0 = 0;                       // 4 KB
-constexpr int SM_W1 = SM_W0 + 4096;            // 32 KB
-constexpr int SM_W2 = SM_W1 + 32768;           // 32 KB
-constexpr int SM_A = SM_W2 + 32768;            // WS_CH x 32 KB activations / X tiles
-constexpr int SM_BIAS = SM_A + WS_CH * 32768;  // b0, b1, b2, w3 (4 x 128 FP32), b3
-constexpr int SM_BAR = SM_BIAS + 4 * 128 * 4 + 16;  // WS_CH mbarriers
+// packed weights (operand layout, each layer's bias block after its weight K blocks)
+constexpr int SM_W0 = 0;                       // W0 (K = 16) + bias block: 8 KB
+constexpr int SM_W1 = SM_W0 + 8192;            // W1 (K = 128) + bias block: 36 KB
+constexpr int SM_W2 = SM_W1 + 36864;           // W2 + bias block: 36 KB
+constexpr int SM_ONES = SM_W2 + 36864;         // the A block of ones: 4 KB
+constexpr int SM_A = SM_ONES + 4096;           // WS_CH x 32 KB activations / X tiles
+constexpr int SM_BIAS = SM_A + WS_CH * 32768;  // w3 (128 FP32), b3
+constexpr int SM_BAR = SM_BIAS + 128 * 4 + 16; // WS_CH mbarriers
 constexpr int SM_TMEM = SM_BAR + 8 * WS_CH;
 constexpr int SM_TOTAL = SM_TMEM + 8 + 128;    // + alignment slack
-constexpr int PACKED_W_BYTES = SM_A - SM_W0;   // 69632: W0, W1, W2 in operand layout
+constexpr int PACKED_W_BYTES = SM_A - SM_W0;   // 86016: W0, W1, W2 with biases, ones
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -424,8 +429,10 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par) {
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// TMEM load of 32 columns of this warp's 32 lanes (one FP32 value per column for this
+// thread's lane) without its wait: the values arrive in r later, and tmem_wait_ld(r) is the
+// point from which they may be read (its in-out operands keep every use of r behind it)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
       "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
@@ -437,7 +444,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
         "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+        "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+        "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+        "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+        "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+        "+r"(r[31])
+      :
+      : "memory");
+}
+
+// the load and its wait: 32 FP32 values of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  tmem_ld32_async(taddr, r);
+  tmem_wait_ld(r);
 #pragma unroll
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
@@ -452,14 +477,18 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// SiLU z / (1 + e^-z) of four values (two packed pairs) with one reciprocal.  The readout
-// of the tensor-core network is bound by instruction issue and the special-function unit
-// (an exponential and a reciprocal per value): the elementwise steps run as packed FP32
-// pairs (FADD2 / FMUL2), and Montgomery's simultaneous inversion (1 / (d0 d1 d2 d3) and the
-// partial products give every 1/d_i) leaves a quarter reciprocal per value, at a few ulp of
-// extra error.  The exponent 2^t, t = -z log2(e), is capped at 2^30 so that the product of
-// four denominators stays finite (below z = -20.8 the value is then -|z| 2^-30 instead of
-// -|z| e^-|z|, both negligible against the O(1) activations they are summed with).
+// SiLU of four values (two packed pairs) with one reciprocal.  The readout of the
+// tensor-core network is bound by instruction issue and the special-function unit (an
+// exponential and a reciprocal per value): the elementwise steps run as packed FP32 pairs
+// (FMUL2), and Montgomery's simultaneous inversion (1 / (d0 d1 d2 d3) and the partial
+// products give every 1/d_i) leaves a quarter reciprocal per value, at a few ulp of extra
+// error.  The packed weights and biases carry a factor 2^-30 (exact in BF16 and FP32), so
+// the accumulator holds z' = 2^-30 z, and with d' = min(2^-30 (1 + e^-z), 1) -- one
+// saturating FMA, which also caps the denominator so that the product of four stays finite
+// and normal -- SiLU(z) = z / (1 + e^-z) = z' / d'.  Below z = -20.8 the cap makes the value
+// -|z| 2^-30 instead of -|z| e^-|z|, both negligible against the O(1) activations they are
+// summed with.
+constexpr float kZScale = 0x1p-30f;  // z' = kZScale z
 __device__ __forceinline__ float ex2_ftz(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -470,30 +499,31 @@ __device__ __forceinline__ float rcp_ftz(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// d' = saturate(e 2^-30 + 2^-30): 2^-30 (1 + e) capped at 1 (+inf -> 1)
+__device__ __forceinline__ float den_sat(float e) {
+  float y;
+  asm("fma.rn.sat.f32 %0, %1, %2, %2;" : "=f"(y) : "f"(e), "f"(kZScale));
+  return y;
+}
 __device__ __forceinline__ void silu_x4(float2& z01, float2& z23) {
-  const float2 nl = make_float2(-1.4426950408889634f, -1.4426950408889634f);
-  const float2 one = make_float2(1.0f, 1.0f);
+  // t = -z log2(e) = z' (-log2(e) / kZScale)
+  const float2 nl = make_float2(-1.4426950408889634f / kZScale, -1.4426950408889634f / kZScale);
   const float2 t01 = __fmul2_rn(z01, nl), t23 = __fmul2_rn(z23, nl);
-  const float2 d01 = __fadd2_rn(
-      make_float2(ex2_ftz(fminf(t01.x, 30.0f)), ex2_ftz(fminf(t01.y, 30.0f))), one);
-  const float2 d23 = __fadd2_rn(
-      make_float2(ex2_ftz(fminf(t23.x, 30.0f)), ex2_ftz(fminf(t23.y, 30.0f))), one);
-  const float ab = d01.x * d01.y, cd = d23.x * d23.y;
+  const float d0 = den_sat(ex2_ftz(t01.x)), d1 = den_sat(ex2_ftz(t01.y));
+  const float d2 = den_sat(ex2_ftz(t23.x)), d3 = den_sat(ex2_ftz(t23.y));
+  const float ab = d0 * d1, cd = d2 * d3;
   const float rp = rcp_ftz(ab * cd);
   const float iab = cd * rp, icd = ab * rp;
-  z01 = __fmul2_rn(z01, make_float2(d01.y * iab, d01.x * iab));
-  z23 = __fmul2_rn(z23, make_float2(d23.y * icd, d23.x * icd));
+  z01 = __fmul2_rn(z01, make_float2(d1 * iab, d0 * iab));
+  z23 = __fmul2_rn(z23, make_float2(d3 * icd, d2 * icd));
 }
 
-// bias + SiLU of 32 accumulator values (bias: 32 FP32 values in shared memory, 16-byte
-// aligned), in place
-__device__ __forceinline__ void bias_silu32(float (&v)[32], const float* bias) {
-  const float4* b4 = reinterpret_cast<const float4*>(bias);
+// SiLU of 32 accumulator values (the bias is already in them), in place
+__device__ __forceinline__ void silu32(float (&v)[32]) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float4 b = b4[q];
-    float2 z01 = __fadd2_rn(make_float2(v[4 * q], v[4 * q + 1]), make_float2(b.x, b.y));
-    float2 z23 = __fadd2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]), make_float2(b.z, b.w));
+    float2 z01 = make_float2(v[4 * q], v[4 * q + 1]);
+    float2 z23 = make_float2(v[4 * q + 2], v[4 * q + 3]);
     silu_x4(z01, z23);
     v[4 * q] = z01.x;
     v[4 * q + 1] = z01.y;
@@ -544,15 +574,32 @@ __device__ __forceinline__ bool chain_all(int g, bool ok) {
   return res != 0;
 }
 
+// one row of X (16 FP32 features; zeros past the last row)
+__device__ __forceinline__ void load_x_row(const float* __restrict__ X, long row, long rows,
+                                           float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = 0.f;
+  if (row < rows) {
+    const float4* xr = reinterpret_cast<const float4*>(X + row * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 a = __ldg(xr + q);
+      v[4 * q] = a.x;
+      v[4 * q + 1] = a.y;
+      v[4 * q + 2] = a.z;
+      v[4 * q + 3] = a.w;
+    }
+  }
+}
+
 // layer readout of this thread's row r (all 128 columns of the chain's accumulator, 32 at a
-// time): bias + SiLU -> BF16 A tile of the next layer
-__device__ __forceinline__ void readout_row(uint32_t trow, const float* bias, unsigned char* sA,
-                                            int r) {
+// time): SiLU -> BF16 A tile of the next layer
+__device__ __forceinline__ void readout_row(uint32_t trow, unsigned char* sA, int r) {
 #pragma unroll 1
   for (int col = 0; col < 128; col += 32) {
     float v[32];
     tmem_ld32(trow + col, v);
-    bias_silu32(v, bias + col);
+    silu32(v);
 #pragma unroll
     for (int q = 0; q < 4; ++q) st_row8(sA, r, col + 8 * q, v + 8 * q);
   }
@@ -580,18 +627,14 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
   const uint32_t bar = smem_u32(sm + SM_BAR + 8 * g);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
 
-  // weights (pre-packed BF16 operand layout) and FP32 biases into shared memory
+  // weights with their bias blocks and the block of ones (pre-packed BF16 operand layout),
+  // and w3, b3 in FP32, into shared memory
   {
     const uint4* src = reinterpret_cast<const uint4*>(wpack);
     uint4* dst = reinterpret_cast<uint4*>(sm + SM_W0);
     for (int q = tid; q < PACKED_W_BYTES / 16; q += NT) dst[q] = src[q];
-    for (int q = tid; q < H; q += NT) {
-      sb[q] = params[H * K + q];                            // b0
-      sb[128 + q] = params[H * K + H + H * H + q];          // b1
-      sb[256 + q] = params[H * K + 2 * H + 2 * H * H + q];  // b2
-      sb[384 + q] = params[H * K + 3 * H + 2 * H * H + q];  // w3
-    }
-    if (tid == 0) sb[512] = params[H * K + 4 * H + 2 * H * H];  // b3
+    for (int q = tid; q < H; q += NT) sb[q] = params[H * K + 3 * H + 2 * H * H + q];  // w3
+    if (tid == 0) sb[128] = params[H * K + 4 * H + 2 * H * H];                       // b3
   }
   if (warp == 0) {
     asm volatile(
@@ -614,34 +657,31 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
   const uint32_t trow = tacc + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
   unsigned char* sA = sm + SM_A + 32768 * g;
   const uint32_t aA = smem_u32(sA), aW0 = smem_u32(sm + SM_W0), aW1 = smem_u32(sm + SM_W1),
-                 aW2 = smem_u32(sm + SM_W2);
+                 aW2 = smem_u32(sm + SM_W2), aOnes = smem_u32(sm + SM_ONES);
   uint32_t phase = 0;
   bool ok = true;
   bool inflight = false;
   const long ntiles = (rows + 127) / 128;
-  for (long tile = (long)blockIdx.x * WS_CH + g; tile < ntiles && ok;
-       tile += (long)gridDim.x * WS_CH) {
+  const long tstride = (long)gridDim.x * WS_CH;
+  // X row -> BF16 (K block 0 of the A operand): the first tile's here, every later tile's
+  // under the previous tile's last matrix product (below)
+  {
+    const long row0 = ((long)blockIdx.x * WS_CH + g) * 128 + r;
+    float v[16];
+    load_x_row(X, row0, rows, v);
+    st_row8(sA, r, 0, v);
+    st_row8(sA, r, 8, v + 8);
+  }
+  for (long tile = (long)blockIdx.x * WS_CH + g; tile < ntiles && ok; tile += tstride) {
     const long row = tile * 128 + r;
-    // X row -> BF16 (K block 0 of the A operand)
+    // the X row two tiles ahead towards L2 (its register load one tile ahead then finds it
+    // there)
     {
-      float v[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) v[q] = 0.f;
-      if (row < rows) {
-        const float4* xr = reinterpret_cast<const float4*>(X + row * 16);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 a = __ldg(xr + q);
-          v[4 * q] = a.x;
-          v[4 * q + 1] = a.y;
-          v[4 * q + 2] = a.z;
-          v[4 * q + 3] = a.w;
-        }
-      }
-      st_row8(sA, r, 0, v);
-      st_row8(sA, r, 8, v + 8);
+      const long prow = row + 2 * tstride * 128;
+      if (prow < rows) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + prow * 16));
     }
-    // layer 0: D = X W0^T; layers 1 and 2: D = A W^T, K = 128 in eight K blocks of 16
+    // layer 0: D = X W0^T + b0; layers 1 and 2: D = A W^T + b, K = 128 in eight K blocks of
+    // 16, each layer closed by the bias block against the block of ones
 #pragma unroll 1
     for (int layer = 0; layer <= 2; ++layer) {
       fence_async_smem();
@@ -651,32 +691,41 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
         fence_after();
         if (layer == 0) {
           mma_bf16(tacc, mdesc(aA, 128, 256), mdesc(aW0, 128, 256), 0);
+          mma_bf16(tacc, mdesc(aOnes, 128, 256), mdesc(aW0 + 4096, 128, 256), 1);
         } else {
           const uint32_t aW = layer == 1 ? aW1 : aW2;
 #pragma unroll
           for (int kb = 0; kb < 8; ++kb)
             mma_bf16(tacc, mdesc(aA + kb * 4096, 128, 256), mdesc(aW + kb * 4096, 128, 256),
                      kb > 0 ? 1u : 0u);
+          mma_bf16(tacc, mdesc(aOnes, 128, 256), mdesc(aW + 8 * 4096, 128, 256), 1);
         }
         mma_commit(bar);
       }
       inflight = true;
+      // the next tile's X row, loaded while the last product of this tile runs
+      float xn[16];
+      if (layer == 2) load_x_row(X, row + tstride * 128, rows, xn);
       ok = chain_all(g, chain_wait(bar, phase));
       if (!ok) break;
       inflight = false;
       phase ^= 1;
+      if (layer == 2) {  // the A tile is free again: the next tile's X into it
+        st_row8(sA, r, 0, xn);
+        st_row8(sA, r, 8, xn + 8);
+      }
       if (layer < 2) {
-        readout_row(trow, sb + 128 * layer, sA, r);
+        readout_row(trow, sA, r);
       } else {
-        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j + b2_j) in FP32 over the row (two
-        // packed partial sums, even and odd j)
+        // last hidden layer: s = b3 + sum_j w3_j SiLU(z_j) in FP32 over the row (two packed
+        // partial sums, even and odd j)
         float2 acc2 = make_float2(0.0f, 0.0f);
 #pragma unroll 1
         for (int col = 0; col < 128; col += 32) {
           float v[32];
           tmem_ld32(trow + col, v);
-          bias_silu32(v, sb + 256 + col);
-          const float4* w4 = reinterpret_cast<const float4*>(sb + 384 + col);
+          silu32(v);
+          const float4* w4 = reinterpret_cast<const float4*>(sb + col);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const float4 w = w4[q];
@@ -685,7 +734,7 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
                               acc2);
           }
         }
-        if (row < rows) out[row] = sb[512] + (acc2.x + acc2.y);
+        if (row < rows) out[row] = sb[128] + (acc2.x + acc2.y);
       }
     }
   }
@@ -704,11 +753,23 @@ __global__ void __launch_bounds__(128 * WS_CH, 1)
                  : "memory");
 }
 
-// FP32 parameters -> BF16 W0, W1, W2 in the operand layout (rows = output units)
+// FP32 parameters -> the packed operands: W0, W1, W2 in the operand layout (rows = output
+// units), each followed by its bias block (column K_l: bf16(b), column K_l + 1: the BF16
+// remainder, zeros after), all times kZScale (a power of two: the BF16 values are the
+// unscaled ones' times kZScale exactly); then the block of ones (columns 0 and 1 of every
+// row)
 __global__ void k_ws_pack(const float* __restrict__ params, unsigned char* __restrict__ wpack) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // one 8-element group
-  const int n0 = H * K / 8, n1 = H * H / 8;
-  if (idx >= n0 + 2 * n1) return;
+  const int n0 = H * (K + 16) / 8, n1 = H * (H + 16) / 8, n3 = 128 * 16 / 8;
+  if (idx >= n0 + 2 * n1 + n3) return;
+  float v[8];
+  if (idx >= n0 + 2 * n1) {  // the block of ones
+    const int g = idx - n0 - 2 * n1, row = g / 2, k0 = (g % 2) * 8;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (k0 + q < 2) ? 1.0f : 0.0f;
+    st_row8(wpack + SM_ONES, row, k0, v);
+    return;
+  }
   int layer, g = idx;
   if (g < n0) {
     layer = 0;
@@ -719,13 +780,23 @@ __global__ void k_ws_pack(const float* __restrict__ params, unsigned char* __res
     layer = 2;
     g -= n0 + n1;
   }
-  const int kd = layer == 0 ? K : H;
-  const int row = g / (kd / 8), k0 = (g % (kd / 8)) * 8;
+  const int kd = layer == 0 ? K : H;  // weight columns; the bias block follows
+  const int row = g / ((kd + 16) / 8), k0 = (g % ((kd + 16) / 8)) * 8;
   const float* w = params + (layer == 0 ? 0 : (layer == 1 ? H * K + H : H * K + 2 * H + H * H));
-  float v[8];
+  if (k0 < kd) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = w[row * kd + k0 + q];
-  unsigned char* base = wpack + (layer == 0 ? 0 : (layer == 1 ? 4096 : 4096 + 32768));
+    for (int q = 0; q < 8; ++q) v[q] = w[row * kd + k0 + q] * kZScale;
+  } else {
+    const float b = w[H * kd + row] * kZScale;  // the layer's bias follows its weights
+    const float hi = __bfloat162float(__float2bfloat16_rn(b));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = 0.0f;
+    if (k0 == kd) {
+      v[0] = hi;
+      v[1] = b - hi;
+    }
+  }
+  unsigned char* base = wpack + (layer == 0 ? SM_W0 : (layer == 1 ? SM_W1 : SM_W2));
   st_row8(base, row, k0, v);
 }
 
@@ -1044,7 +1115,7 @@ cudaError_t launch_transport(const double* f, const double* u, int N, int M, dou
 size_t ws_packed_bytes() { return PACKED_W_BYTES; }
 
 cudaError_t launch_ws_pack(const float* params, unsigned char* wpack, cudaStream_t st) {
-  const int n = (H * K + 2 * H * H) / 8;
+  const int n = (H * (K + 16) + 2 * H * (H + 16) + 128 * 16) / 8;
   k_ws_pack<<<(n + 255) / 256, 256, 0, st>>>(params, wpack);
   return cudaGetLastError();
 }
