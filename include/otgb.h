@@ -167,6 +167,11 @@ extern "C" {
                                    the window, at most the device maximum), so that the
                                    transform passes between two Arnoldi steps do not evict it;
                                    0 (default): no window.  Same arithmetic either way */
+#define OT_OPT_FUSED_UPDATE 31  /* mixed mode, single problem: 1 (default) runs each Arnoldi
+                                   step's update fused with the row transform pass of the
+                                   next step's product (the update forms v_(j+1) row by row
+                                   and transforms it in place of a separate row pass); 0: two
+                                   launches.  Same arithmetic either way (bit for bit) */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -60,6 +60,7 @@ struct ot_plan {
   int uncond = 4;
   int kbps = 1;  // OT_OPT_KRYLOV_BLOCKS: blocks per SM of the GMRES vector kernels
   int l2persist = 0;  // OT_OPT_L2_PERSIST: the Krylov basis as persisting L2 lines (graph)
+  int fused_update = 1;  // OT_OPT_FUSED_UPDATE: Arnoldi update fused with the next row pass
   int linsolver = 0;
   int max_bicg = 20000;
   double* fdv = nullptr;
@@ -157,6 +158,18 @@ static cudaError_t residual_launch(ot_plan* p, const double* f, const double* c,
 }
 
 static bool reorth_on(const ot_plan* p) { return p->reorth == 1; }
+
+// whether this plan's Arnoldi steps run the update fused with the next product's row pass
+// (FP32 single problem, the row pass in a form the fused kernel has, no reorthogonalisation,
+// not the register-resident passes); the steps then leave out their own row pass, and each
+// cycle starts with the row pass of v_0
+template <typename T>
+static bool fused_update_on(ot_plan* p) {
+  if (sizeof(T) != 4 || !p->fused_update || p->slab_base || reorth_on(p)) return false;
+  const SpecTables& tb = tables<T>(p);
+  if (tb.mv_reg && tb.t2rA) return false;
+  return update_r2c_fits(p->N, p->M, tb.var_r2c);
+}
 
 
 static cudaEvent_t ev_get(ot_plan* p) {
@@ -842,6 +855,13 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
         free_graph(p);
       }
       return OT_OK;
+    case OT_OPT_FUSED_UPDATE:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->fused_update != (int)v) {
+        p->fused_update = (int)v;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_UNCOND_STEPS:
       if (v < 0 || v > OTGB_MAXM || v != (double)(int)v) return OT_EINVAL;
       if (p->uncond != (int)v) {
@@ -908,6 +928,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_UNCOND_STEPS: *v = p->uncond; return OT_OK;
     case OT_OPT_KRYLOV_BLOCKS: *v = p->kbps; return OT_OK;
     case OT_OPT_L2_PERSIST: *v = p->l2persist; return OT_OK;
+    case OT_OPT_FUSED_UPDATE: *v = p->fused_update; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the
@@ -1045,6 +1066,10 @@ static int time_kernel_impl(ot_plan* p, int cls, int reps, double* ms_per_launch
         if (cls == OT_PROF_GMRES_DOTS)
           return launch_gmres_dots<T>((const T*)p->V, (const T*)p->w, (long)P, p->partials,
                                       p->sc, p->kblocks, p->stream);
+        if (fused_update_on<T>(p))  // the update as the solve runs it: with the row pass
+          return launch_gmres_update_r2c((float*)p->V, (const float*)p->w, (long)P,
+                                         p->partials, p->kblocks, p->sc, (float2*)p->spec, N,
+                                         M, p->tb32, p->stream);
         return launch_gmres_update<T>((T*)p->V, (const T*)p->w, (long)P, p->partials, p->sc,
                                       p->kblocks, p->stream, 3);
       }
@@ -1128,7 +1153,7 @@ static int run_prefilter(ot_plan* p, const double* g, double* c) {
 // w = L Lbar^{-1} x, x = V + (*jptr) P scaled by scale[*jptr] when jptr is given
 template <typename T>
 static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* scale, T* w,
-                      const int* skip, int tag) {
+                      const int* skip, int tag, bool rows_done = false) {
   const size_t P = (size_t)p->N * p->M;
   const SpecTables& tb = tables<T>(p);
   const DevScalars* msc = p->slab_base ? p->sc : nullptr;
@@ -1146,9 +1171,10 @@ static int run_matvec(ot_plan* p, const T* x, const int* jptr, const double* sca
                               p->M, tb, skip, p->stream));
     return OT_OK;
   }
-  LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
-         launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip,
-                           p->stream, btc(p), msc));
+  if (!rows_done)  // else the fused update of the previous step left the row pass's spectrum
+    LAUNCH(p, OT_PROF_ROW_R2C, tag, 1,
+           launch_row_r2c<T>(x, P, jptr, scale, (C2<T>*)p->spec, p->N, p->M, tb, skip,
+                             p->stream, btc(p), msc));
   LAUNCH(p, OT_PROF_COL_MATVEC, tag, 1,
          launch_col<T>(COL_MATVEC, (C2<T>*)p->spec, (C2<T>*)p->q0, (C2<T>*)p->q1,
                        (C2<T>*)p->q2, p->N, p->M, tb, p->sc, skip, p->stream, btc(p)));
@@ -1252,7 +1278,8 @@ static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
   const long P = (long)p->N * p->M;
   T* V = (T*)p->V;
   T* w = (T*)p->w;
-  RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j));
+  const bool fused = fused_update_on<T>(p);
+  RET(run_matvec<T>(p, V, &p->sc->j, p->sc->scale, w, skip, j, fused));
   LAUNCH(p, OT_PROF_GMRES_DOTS, j, 1,
          launch_gmres_dots<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 0, btc(p)));
   if (reorth_on(p)) {
@@ -1265,6 +1292,12 @@ static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
     LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
            launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 2,
                                   btc(p)));
+  } else if (fused) {
+    // the update's block 0 closes the step; its other blocks form v_(j+1) row by row and
+    // run the next product's row pass on it
+    LAUNCH(p, OT_PROF_GMRES_UPDATE, j, 1,
+           launch_gmres_update_r2c((float*)V, (const float*)w, P, p->partials, p->kblocks,
+                                   p->sc, (float2*)p->spec, p->N, p->M, p->tb32, p->stream));
   } else {
     // the multi-dot closes the step (norm by Pythagoras, Givens); the update only forms
     // v_(j+1) and is skipped when the cycle ends
@@ -1272,6 +1305,18 @@ static int run_arnoldi_step(ot_plan* p, int j, const int* skip) {
            launch_gmres_update<T>(V, w, P, p->partials, p->sc, p->kblocks, p->stream, 3,
                                   btc(p)));
   }
+  return OT_OK;
+}
+
+// the row pass of a cycle's v_0 where the steps run the fused update (which leaves the row
+// pass of every later basis vector)
+template <typename T>
+static int run_cycle_rows(ot_plan* p, const int* skip) {
+  if (!fused_update_on<T>(p)) return OT_OK;
+  LAUNCH(p, OT_PROF_ROW_R2C, 0, 1,
+         launch_row_r2c<T>((const T*)p->V, (size_t)p->N * p->M, &p->sc->j, p->sc->scale,
+                           (C2<T>*)p->spec, p->N, p->M, tables<T>(p), skip, p->stream, btc(p),
+                           nullptr));
   return OT_OK;
 }
 
@@ -1288,6 +1333,7 @@ static int run_gmres(ot_plan* p) {
   LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
          launch_gmres_init<T>(p->Fraw, w, V, P, 0, p->partials, p->sc, p->kblocks, p->stream));
   for (int cyc = 0; cyc < p->max_restarts; ++cyc) {
+    RET(run_cycle_rows<T>(p, skip));
     for (int j = 0; j < p->m; ++j) RET(run_arnoldi_step<T>(p, j, skip));
     LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1, launch_gmres_finish(p->sc, p->stream));
     LAUNCH(p, OT_PROF_GMRES_OTHER, -1, 1,
@@ -1721,6 +1767,7 @@ static int capture_solve(ot_plan* p) {
   // plan runs every step as a plain launch (the cycles of its pairs end at different steps).
   const int K = batched ? p->m : (p->m < p->uncond ? p->m : p->uncond);
   for (int k = 0; k < OTGB_MAXM; ++k) p->h_step[k] = 0;
+  RET(run_cycle_rows<T>(p, &p->sc->cycle_done));
   for (int j = 0; j < K; ++j) RET(run_arnoldi_step<T>(p, j, &p->sc->cycle_done));
   if (K < p->m) {
     unsigned long long h_tail = 0;

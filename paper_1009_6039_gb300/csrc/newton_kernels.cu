@@ -9,6 +9,7 @@
 
 #include "dd.cuh"
 #include "otgb_internal.cuh"
+#include "gmres_dev.cuh"
 #include "reduce.cuh"
 
 namespace otgb {
@@ -1194,76 +1195,6 @@ __device__ void arnoldi_close(DevScalars* sc, int j, double hn, bool weak) {
     cudaGraphSetConditional(sc->h_step[j + 1], sc->cycle_done ? 0u : 1u);
 }
 
-// The same for the single-reduction step, with column j of H (h, before the rotations) in
-// registers: every scalar it needs is loaded first, as independent loads, so that the one
-// thread that runs it waits for one memory round trip instead of one per dependent access.
-// FAST (the FP32 step): the rotation from one reciprocal square root, c = a / r = a rsqrt(r^2)
-// and s = b rsqrt(r^2), and the basis scale 1 / hn passed in (rsqrt of the Pythagorean
-// square), in place of a square root and divisions, whose FP64 forms are slow on this GPU
-// (the close is one thread on the step's critical path); the FP64 step keeps them.
-template <int J, bool FAST = false>
-__device__ void arnoldi_close_j(DevScalars* sc, const double (&h)[J], double hn, bool weak,
-                                double inv_hn = 0.0) {
-  constexpr int j = J - 1;
-  double cs[J], sn[J];
-#pragma unroll
-  for (int i = 0; i < j; ++i) {
-    cs[i] = sc->cs[i];
-    sn[i] = sc->sn[i];
-  }
-  const double gvj = sc->gv[j], bnorm = sc->bnorm, eta = sc->eta;
-  const int m = sc->m, iters = sc->iters, graph = sc->graph;
-  const unsigned long long hnext = j + 1 < OTGB_MAXM ? sc->h_step[j + 1] : 0ull;
-  double col[J + 1];
-#pragma unroll
-  for (int i = 0; i < J; ++i) col[i] = h[i];
-  col[J] = hn;
-#pragma unroll
-  for (int i = 0; i < j; ++i) {  // previous rotations on column j
-    const double t0 = col[i], t1 = col[i + 1];
-    col[i] = cs[i] * t0 + sn[i] * t1;
-    col[i + 1] = -sn[i] * t0 + cs[i] * t1;
-  }
-  const double a = col[j], b = col[j + 1];
-  double r, c, sj;
-  if (FAST) {
-    const double r2 = a * a + b * b;
-    const double y = r2 > 0.0 ? rsqrt(r2) : 0.0;
-    r = r2 * y;
-    c = (r2 > 0.0) ? a * y : 1.0;
-    sj = (r2 > 0.0) ? b * y : 0.0;
-  } else {
-    r = sqrt(a * a + b * b);
-    c = (r == 0.0) ? 1.0 : a / r;
-    sj = (r == 0.0) ? 0.0 : b / r;
-  }
-  col[j] = r;
-  col[j + 1] = 0.0;
-#pragma unroll
-  for (int i = 0; i <= J; ++i) sc->H[i * m + j] = col[i];
-  sc->cs[j] = c;
-  sc->sn[j] = sj;
-  const double g1 = -sj * gvj;
-  sc->gv[j + 1] = g1;
-  sc->gv[j] = c * gvj;
-  sc->iters = iters + 1;
-  sc->jend = j + 1;
-  if (!FAST) sc->relres = fabs(g1) / bnorm;  // informational (the FP32 step skips it)
-  int done = 0;
-  if (weak) {
-    done = 1;
-  } else if (fabs(g1) <= eta * bnorm || hn == 0.0) {
-    sc->converged = 1;
-    done = 1;
-  } else {
-    sc->scale[j + 1] = FAST ? inv_hn : 1.0 / hn;
-    if (j + 1 == m) done = 1;
-  }
-  if (done) sc->cycle_done = 1;
-  sc->j = j + 1;
-  if (graph && hnext) cudaGraphSetConditional(hnext, done ? 0u : 1u);
-}
-
 // Per-thread partial sums are kept in the vector precision T (a thread covers a few vectors
 // of 16 bytes); partials are combined across threads and blocks in FP64.
 template <typename T, int J>
@@ -1391,36 +1322,10 @@ __device__ __forceinline__ void update_j(T* __restrict__ V, const T* __restrict_
   double hv[J], hn = 0.0, inv_hn = 0.0;
   bool weak = false;
   if (sizeof(T) == 4 && mode == 3 && split) {
-    // finish the multi-dot of step j: the (J + 1) sums over the dots kernel's blocks, each
-    // taken by one warp in a fixed order (lane-strided, then a shuffle tree), so that every
-    // block obtains the same values; h_i = scale_i V_i.w, and ||w - sum h_i v_i||^2 =
-    // w.w - sum h_i^2 (Pythagoras, v_i orthonormal): below 1e-6 w.w the step is weak and
-    // the cycle ends (the restart's explicit residual decides)
-    // (the sums in FP32, as the block sums themselves)
-    __shared__ float sv[OTGB_MAXM + 1];
-    const float* pf = reinterpret_cast<const float*>(partials);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nb = gridDim.x;
-    for (int a = wid; a <= J; a += nw) {
-      float x = 0.f;
-      for (int b = lane; b < nb; b += 32) x += pf[(size_t)b * (J + 1) + a];
+    float cf[J];
+    finish_multidot_f32<J>(partials, gridDim.x, sc, hv, hn, inv_hn, weak, cf);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) sv[a] = x;
-    }
-    __syncthreads();
-    double hs = 0.0;
-#pragma unroll
-    for (int i = 0; i < J; ++i) {
-      hv[i] = sc->scale[i] * (double)sv[i];
-      hs += hv[i] * hv[i];
-    }
-    const double ww = (double)sv[J], hn2 = ww - hs;
-    weak = !(hn2 > 1e-6 * ww);
-    inv_hn = weak ? 0.0 : rsqrt(hn2);
-    hn = hn2 * inv_hn;
-#pragma unroll
-    for (int i = 0; i < J; ++i) coefs[i] = (T)(hv[i] * sc->scale[i]);
+    for (int i = 0; i < J; ++i) coefs[i] = (T)cf[i];
   } else {
 #pragma unroll
     for (int i = 0; i < J; ++i)

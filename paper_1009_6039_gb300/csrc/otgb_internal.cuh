@@ -349,6 +349,14 @@ cudaError_t launch_gmres_dots(const T* V, const T* w, long P, double* partials, 
 template <typename T>
 cudaError_t launch_gmres_update(T* V, const T* w, long P, double* partials, DevScalars* sc,
                                 int nblocks, cudaStream_t st, int mode = 0, Bat bat = Bat());
+// FP32, single problem: the split update of step jd (block 0 closes the step) fused with the
+// row real-to-complex pass of step jd + 1's product on v_(jd+1) / hn (gmres_fused.cu); nb:
+// the multi-dot's block count.  update_r2c_fits: whether the fused form exists for this size
+// and row-pass variant.
+bool update_r2c_fits(int N, int M, int var_r2c);
+cudaError_t launch_gmres_update_r2c(float* V, const float* w, long P, const double* partials,
+                                    int nb, DevScalars* sc, float2* spec, int N, int M,
+                                    const SpecTables& tb, cudaStream_t st);
 cudaError_t launch_gmres_finish(DevScalars* sc, cudaStream_t st, Bat bat = Bat());
 template <typename T>
 cudaError_t launch_gmres_combine(const T* V, T* sigma, long P, const DevScalars* sc,

@@ -672,6 +672,29 @@ template <typename T> struct MaxThreads {
   static constexpr int value = sizeof(T) == 8 ? 256 : 512;
 };
 
+// The real-to-complex split of one row: buf holds the length-L complex transform Z of the
+// row's M = 2L real values packed as z_n = x_2n + i x_(2n+1); out receives the half
+// spectrum X_0..X_(L-1) (X_0 and the Nyquist value X_L packed as (X_0, X_L), both real).
+template <typename T>
+__device__ __forceinline__ void r2c_split_store(const C2<T>* buf, C2<T>* __restrict__ out, int L,
+                                                int t, int TPT, const C2<T>* __restrict__ twM) {
+  for (int k = t; k <= L / 2; k += TPT) {
+    if (k == 0) {
+      C2<T> z = buf[0];
+      out[0] = mk2<T>(z.x + z.y, z.x - z.y);
+    } else {
+      C2<T> zk = buf[k], zm = buf[L - k];
+      // E = (Zk + conj Zm)/2, O = -i (Zk - conj Zm)/2, X_k = E + W_M^k O,
+      // X_{L-k} = conj(E - W_M^k O)
+      C2<T> Ev = mk2<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
+      C2<T> Ov = mk2<T>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
+      C2<T> wo = cmul<T>(twM[k], Ov);
+      out[k] = cadd<T>(Ev, wo);
+      if (2 * k != L) out[L - k] = cconj<T>(csub<T>(Ev, wo));
+    }
+  }
+}
+
 template <typename T, int E>
 __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __restrict__ xbase, size_t x_stride,
                           const int* __restrict__ jptr, const double* __restrict__ scale,
@@ -708,24 +731,7 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_r2c(const T* __res
   }
   __syncthreads();
   fft_smem<T, E, -1>(buf, L, t, active, twL);
-  if (active) {
-    C2<T>* out = spec + (size_t)row * L;
-    for (int k = t; k <= L / 2; k += TPT) {
-      if (k == 0) {
-        C2<T> z = buf[0];
-        out[0] = mk2<T>(z.x + z.y, z.x - z.y);
-      } else {
-        C2<T> zk = buf[k], zm = buf[L - k];
-        // E = (Zk + conj Zm)/2, O = -i (Zk - conj Zm)/2, X_k = E + W_M^k O,
-        // X_{L-k} = conj(E - W_M^k O)
-        C2<T> Ev = mk2<T>((T)0.5 * (zk.x + zm.x), (T)0.5 * (zk.y - zm.y));
-        C2<T> Ov = mk2<T>((T)0.5 * (zk.y + zm.y), (T)-0.5 * (zk.x - zm.x));
-        C2<T> wo = cmul<T>(twM[k], Ov);
-        out[k] = cadd<T>(Ev, wo);
-        if (2 * k != L) out[L - k] = cconj<T>(csub<T>(Ev, wo));
-      }
-    }
-  }
+  if (active) r2c_split_store<T>(buf, spec + (size_t)row * L, L, t, TPT, twM);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -669,6 +669,33 @@ def test_graph_shape_options_keep_the_result(ot):
         assert np.abs(results[k][0] - ref[0]).max() <= 1e-6, k
 
 
+@pytest.mark.parametrize("N,M", [(128, 128), (48, 64), (64, 256)])
+@pytest.mark.parametrize("variant", [0, 3])
+def test_fused_update_keeps_the_result(ot, N, M, variant):
+    # OT_OPT_FUSED_UPDATE: the Arnoldi update fused with the next product's row pass (row
+    # pass variant 0: 8 elements per thread, 3: 4) against the two separate launches:
+    # bit-identical potentials and counts, graph and host-driven, over several restart
+    # cycles (eta 1e-4, m = 5: cycles end at their last step as well as on convergence)
+    f, g = I.noise_blob_pair(N, M, s=3703)
+    base = dict(tau=1.0, tol=1e-8, eta=1e-4, symbols=1, restart=5, fft_variant=variant)
+    results = {}
+    for fused in (1, 0):
+        for graph in (1, 0):
+            p = plan(ot, N, M, "mixed", graph=graph, fused_update=fused, **base)
+            phi = dev(np.zeros((N, M)))
+            rc, st = p.solve(dev(f), dev(g), phi)
+            assert rc == 0 and st["res_inf"] < 1e-8, (fused, graph, st)
+            if fused and graph:
+                assert p.time_kernel("gmres_update", reps=3) > 0.0
+            p.close()
+            results[(fused, graph)] = (phi.cpu().numpy(), st["newton_iters"],
+                                       st["gmres_iters"], st["step_halvings"])
+    ref = results[(0, 1)]
+    assert ref[2] > 5 * ref[1]  # cycles restarted
+    for k, r in results.items():
+        assert np.array_equal(r[0], ref[0]) and r[1:] == ref[1:], k
+
+
 def test_untranslated_inputs_are_checked(ot):
     # OT_OPT_TRANSLATE = 0: inputs are used as given, so they must be positive as they are;
     # the statistics still report the mass defects
