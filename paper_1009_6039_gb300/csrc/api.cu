@@ -1358,6 +1358,8 @@ static void set_solver_scalars(ot_plan* p) {
   p->hsc->step_s = 1.0;
   p->hsc->safeguard = p->safeguard;
   p->hsc->reorth = reorth_on(p) ? 1 : 0;
+  p->hsc->step_kernels =
+      reorth_on(p) ? 7 : ((p->precision && fused_update_on<float>(p)) ? 4 : 5);
   p->hsc->max_newton = p->max_newton;
   p->hsc->max_restarts = p->max_restarts;
   p->hsc->ws_alpha = -1.0;
@@ -1757,8 +1759,10 @@ static int capture_solve(ot_plan* p) {
   RET(add_conditional(p->cs[1], cudaGraphCondTypeWhile, &p->h_cycle, &b2));
   RET(begin_body(p, 2, b2));
   p->cur_mask = MASK_CYCLE;
+  // (the count: this kernel, and the row pass of v_0 that a fused-update cycle starts with)
   LAUNCH(p, OT_PROF_OTHER, -1, 1,
-         launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream, batched ? 1 + 5 * p->m : 1, btc(p)));
+         launch_ctl(CTL_CYCLE_BEGIN, p->sc, p->stream,
+                    batched ? 1 + 5 * p->m : (fused_update_on<T>(p) ? 2 : 1), btc(p)));
   // The first K steps of a cycle are plain kernels that skip themselves once the cycle is
   // done; the rest run as the body of one WHILE node, one step (its index read on the
   // device) per iteration, the node's handle set by each step's Givens close.  Measured on

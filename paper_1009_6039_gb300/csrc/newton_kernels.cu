@@ -1597,7 +1597,7 @@ __device__ int ctl_apply(int op, DevScalars* sc, int add, bool handles) {
     case CTL_CYCLE_END: {
       // the unconditional Arnoldi steps a short cycle left also launched (and skipped)
       if (handles && sc->jend < sc->steps_uncond)
-        sc->kcount += (sc->reorth ? 7LL : 5LL) * (sc->steps_uncond - sc->jend);
+        sc->kcount += (long long)sc->step_kernels * (sc->steps_uncond - sc->jend);
       cont = (!sc->converged && sc->cycles < sc->max_restarts) ? 1 : 0;
       sc->in_cycle = cont;
       if (handles) {
@@ -1628,8 +1628,9 @@ __device__ int ctl_apply(int op, DevScalars* sc, int add, bool handles) {
       }
       break;
     case CTL_GMRES_DONE:
-      // Arnoldi steps: 3 matvec passes + dots + update (+ dots + update when reorthogonal.)
-      if (handles) sc->kcount += (sc->reorth ? 7LL : 5LL) * sc->iters;
+      // Arnoldi steps: 3 matvec passes + dots + update (+ dots + update when reorthogonal.;
+      // the fused update carries the next step's first matvec pass)
+      if (handles) sc->kcount += (long long)sc->step_kernels * sc->iters;
       sc->gmres_iters_total += sc->iters;
       sc->gmres_cycles_total += sc->cycles;
       break;

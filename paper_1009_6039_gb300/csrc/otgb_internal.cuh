@@ -57,6 +57,7 @@ struct DevScalars {
   int newton_n, halvings, status, upar, safeguard, max_newton, max_restarts;
   int gmres_iters_total, gmres_cycles_total, graph, reorth;
   int steps_uncond;  // graph: Arnoldi steps 0..steps_uncond-1 of a cycle are not IF nodes
+  int step_kernels;  // kernels per Arnoldi step: 5, 7 reorthogonalised, 4 fused update
   long long kcount;  // kernels executed by the graph-launched solve
   // conditional-node handles of the captured solve (0 outside a graph)
   unsigned long long h_newton, h_cycle, h_restart, h_halve, h_step[OTGB_MAXM];
