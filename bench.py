@@ -867,7 +867,8 @@ def run_ours(args):
         phases["by_kernel_class_ms"] = {k: round(v[0], 4) for k, v in prof_c.items()}
         phases["by_kernel_class_total_ms"] = round(st_c["ms_total"], 4)
         graph_shape = {}
-        for unc in (0, 4, 10):
+        unc0 = int(plan.get("uncond_steps"))
+        for unc in (0, 4, 7, 10):
             plan.set(uncond_steps=unc)
             plan.solve(fd, gd, phi)
             tms = []
@@ -876,7 +877,7 @@ def run_ours(args):
                 m_, _ = _timed_solve(plan, fd, gd, phi, stream)
                 tms.append(m_)
             graph_shape[str(unc)] = round(statistics.median(tms), 4)
-        plan.set(uncond_steps=4)
+        plan.set(uncond_steps=unc0)
         phases["ms_per_solve_by_uncond_steps"] = graph_shape
         kb_shape = {}
         kb0 = int(plan.get("krylov_blocks"))

@@ -155,10 +155,10 @@ extern "C" {
                                    cycle are captured as plain kernels that skip themselves
                                    once the cycle has ended, the later ones as the body of one
                                    conditional WHILE node, a step per iteration (0 <= s <= 16,
-                                   default 4; a plan set captures every step plainly).  Same
+                                   default 7; a plan set captures every step plainly).  Same
                                    arithmetic for every s */
 #define OT_OPT_KRYLOV_BLOCKS 29 /* blocks of 256 threads per SM for the GMRES vector kernels
-                                   (multi-dot, update, init, combine), 1..8 (default 1); the
+                                   (multi-dot, update, init, combine), 1..8 (default 2); the
                                    block partial sums change with it, so results differ in
                                    the last bits between settings (each is deterministic) */
 #define OT_OPT_L2_PERSIST 30    /* 1: the graph-launched solve marks the GMRES basis V_0..V_m

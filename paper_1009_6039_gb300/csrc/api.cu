@@ -57,8 +57,8 @@ struct ot_plan {
   // host-driven); its 7 vector planes and the iteration cap OT_OPT_MAX_BICG
   // OT_OPT_UNCOND_STEPS: Arnoldi steps per GMRES cycle captured as plain self-skipping
   // kernels rather than IF nodes (graph)
-  int uncond = 4;
-  int kbps = 1;  // OT_OPT_KRYLOV_BLOCKS: blocks per SM of the GMRES vector kernels
+  int uncond = 7;
+  int kbps = 2;  // OT_OPT_KRYLOV_BLOCKS: blocks per SM of the GMRES vector kernels
   int l2persist = 0;  // OT_OPT_L2_PERSIST: the Krylov basis as persisting L2 lines (graph)
   int fused_update = 1;  // OT_OPT_FUSED_UPDATE: Arnoldi update fused with the next row pass
   int linsolver = 0;
