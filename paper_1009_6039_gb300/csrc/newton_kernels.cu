@@ -311,6 +311,88 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same two passes in double-float arithmetic for the mixed mode (FP64 runs at a small
+// fraction of the FP32 rate on this GPU, and the FP64 recursions had become the largest of a
+// solve's one-off kernels): the columns' pass reads g in FP64 and leaves the dd result in
+// `mid`, the rows' pass reads that and writes c as dd (hi, lo) and as its FP64 sum.  The
+// recursions, the chunking and the warm-up length are those of the FP64 kernel; each step
+// z cp + s is a dd product and sum (relative error ~2^-47 per step, damped by |z| = 0.27).
+template <bool XPASS>
+__global__ void __launch_bounds__(256)
+    k_prefilter_tile_dd(const double* __restrict__ s64, const float2* __restrict__ sdd,
+                        float2* __restrict__ out_dd, double* __restrict__ out64, int N, int M,
+                        double z, double A, Bat bat) {
+  extern __shared__ __align__(16) float2 smq[];  // [k][line] as (hi, lo)
+  s64 = badv(s64, bat);
+  sdd = badv(sdd, bat);
+  out_dd = badv(out_dd, bat);
+  out64 = badv(out64, bat);
+  const int tid = threadIdx.x;
+  const int L = XPASS ? M : N, nlines = XPASS ? N : M;
+  const long ls = XPASS ? M : 1, ps = XPASS ? 1 : M;
+  const int line0 = blockIdx.x * PT_LN, p0 = blockIdx.y * PT_TP;
+  const int tpl = min(PT_TP, L - p0), nk = tpl + 2 * PRE_K;
+  for (int e = tid; e < nk * PT_LN; e += blockDim.x) {
+    const int k = XPASS ? e % nk : e / PT_LN, ln = XPASS ? e / nk : e % PT_LN;
+    const int line = line0 + ln;
+    const int pt = ((p0 - PRE_K + k) % L + L) % L;
+    float2 x = make_float2(0.f, 0.f);
+    if (line < nlines) {
+      const long o = line * ls + pt * ps;
+      if (s64) {
+        const dd d = dd_from_double(s64[o]);
+        x = make_float2(d.hi, d.lo);
+      } else {
+        x = sdd[o];
+      }
+    }
+    smq[k * PT_SW + ln] = x;
+  }
+  __syncthreads();
+  const dd zd = dd(z), Ad = dd(A);
+  const int ln = tid % PT_LN, c0 = (tid / PT_LN) * PRE_CH, n = min(PRE_CH, tpl - c0);
+  dd v[PRE_CH];
+  auto at = [&](int k) {
+    const float2 q = smq[k * PT_SW + ln];
+    return dd{q.x, q.y};
+  };
+  if (n > 0) {
+    dd cp{0.f, 0.f}, ca{0.f, 0.f};
+    for (int k = c0; k < c0 + PRE_K; ++k) cp = dd_add(dd_mul(zd, cp), at(k));
+    for (int k = c0 + n + 2 * PRE_K - 1; k >= c0 + n + PRE_K; --k)
+      ca = dd_add(dd_mul(zd, ca), at(k));
+#pragma unroll
+    for (int i = 0; i < PRE_CH; ++i)
+      if (i < n) {
+        cp = dd_add(dd_mul(zd, cp), at(c0 + PRE_K + i));
+        v[i] = cp;
+      }
+#pragma unroll
+    for (int i = PRE_CH - 1; i >= 0; --i)
+      if (i < n) {
+        const dd xi = at(c0 + PRE_K + i);
+        ca = dd_add(dd_mul(zd, ca), xi);
+        v[i] = dd_mul(Ad, dd_sub(dd_add(v[i], ca), xi));
+      }
+  }
+  __syncthreads();  // every chunk has read its neighbours' points
+  if (n > 0) {
+#pragma unroll
+    for (int i = 0; i < PRE_CH; ++i)
+      if (i < n) smq[(c0 + PRE_K + i) * PT_SW + ln] = make_float2(v[i].hi, v[i].lo);
+  }
+  __syncthreads();
+  for (int e = tid; e < tpl * PT_LN; e += blockDim.x) {
+    const int k = XPASS ? e % tpl : e / PT_LN, l2 = XPASS ? e / tpl : e % PT_LN;
+    const int line = line0 + l2;
+    if (line >= nlines) continue;
+    const float2 r = smq[(k + PRE_K) * PT_SW + l2];
+    const long o = line * ls + (long)(p0 + k) * ps;
+    out_dd[o] = r;
+    if (out64) out64[o] = (double)r.x + (double)r.y;
+  }
+}
+
 cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2* cdd, int N,
                              int M, cudaStream_t st, Bat bat) {
   static bool attr_set[64] = {false};
@@ -323,6 +405,12 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_prefilter_tile<true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_prefilter_tile_dd<false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_prefilter_tile_dd<true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, PT_SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -330,9 +418,17 @@ cudaError_t launch_prefilter(const double* g, double* scratch, double* c, float2
   const double A = 6.0 * z / (z * z - 1.0);
   // columns (along y), then rows (along x)
   const dim3 gy((M + PT_LN - 1) / PT_LN, (N + PT_TP - 1) / PT_TP);
+  const dim3 gx((N + PT_LN - 1) / PT_LN, (M + PT_TP - 1) / PT_TP);
+  if (cdd) {  // mixed mode: double-float passes (the scratch plane holds the dd middle)
+    float2* mid = reinterpret_cast<float2*>(scratch);
+    k_prefilter_tile_dd<false><<<bgrid(gy, bat), 256, PT_SMEM, st>>>(g, nullptr, mid, nullptr,
+                                                                      N, M, z, A, bat);
+    k_prefilter_tile_dd<true><<<bgrid(gx, bat), 256, PT_SMEM, st>>>(nullptr, mid, cdd, c, N, M,
+                                                                     z, A, bat);
+    return cudaGetLastError();
+  }
   k_prefilter_tile<false><<<bgrid(gy, bat), 256, PT_SMEM, st>>>(g, scratch, nullptr, N, M, z, A,
                                                                  bat);
-  const dim3 gx((N + PT_LN - 1) / PT_LN, (M + PT_TP - 1) / PT_TP);
   k_prefilter_tile<true><<<bgrid(gx, bat), 256, PT_SMEM, st>>>(scratch, c, cdd, N, M, z, A, bat);
   return cudaGetLastError();
 }

@@ -71,9 +71,12 @@ def test_fft_forward_inverse(ot, N, M, prec):
 
 @pytest.mark.parametrize("N,M", [(8, 16), (12, 24), (16, 16), (24, 48), (128, 48), (192, 384),
                                  (256, 256), (1024, 1024)])
-def test_prefilter(ot, N, M):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_prefilter(ot, N, M, prec):
+    # FP64 recursions, or (mixed) the same recursions in double-float: both to FP64-level
+    # accuracy against the oracle's exact periodic inverse (|c| ~ 1.5, dd unit round-off 2^-48)
     g = 1 + 0.5 * RNG.random((N, M))
-    p = plan(ot, N, M, "mixed")  # the prefilter is FP64 in both modes
+    p = plan(ot, N, M, prec)
     gd, cd = dev(g), dev(np.zeros((N, M)))
     assert ot.ot_prefilter(p.h, ptr(gd), ptr(cd)) == 0
     assert np.abs(cd.cpu().numpy() - O.bspline_coeffs(g)).max() <= 1e-13
