@@ -198,8 +198,9 @@ def variant_names(v):
         return {"code": v, "row_r2c": "k_mvT_r2c<M/2>", "col_matvec": "k_mvT_col<N>",
                 "row_c2r_combine": "k_mvT_combine<M/2>", "col_q4": False,
                 "register_resident": True}
-    return {"code": v, "row_r2c": row[r], "col_matvec": col[c], "row_c2r_combine": comb[b],
-            "col_q4": bool(v & 64)}
+    return {"code": v, "row_r2c": row[r],
+            "col_matvec": "k_col_pair<N>" if v & 256 else col[c],
+            "row_c2r_combine": comb[b], "col_q4": bool(v & 64)}
 
 
 def traffic_for(kernel_cls, size):

@@ -179,7 +179,9 @@ extern "C" {
                                    synchronous radix-32, 3 = generic with 4 elements per
                                    thread (where the size allows, else a variant that does);
                                    + 64: the generic column pass with 4 columns per block;
-                                   turns OT_OPT_AUTOTUNE off */
+                                   + 256: the column pass on column pairs with packed FP32
+                                   arithmetic (N a power of two in 256..2048, M a multiple
+                                   of 4; elsewhere c = 3); turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

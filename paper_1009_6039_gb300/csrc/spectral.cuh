@@ -84,6 +84,52 @@ template <typename T, int SIGN> struct Bfly<T, 4, SIGN> {
   }
 };
 
+// FP32: a complex number is a register pair, so complex additions and subtractions are
+// single packed instructions (add/sub.rn.f32x2: per lane the same IEEE operation as the
+// scalar forms, so the results are bit for bit those of the scalar butterflies); the
+// multiplication by +-i mixes the lanes and stays scalar.
+__device__ __forceinline__ float2 padd2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 psub2(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+template <int SIGN> struct Bfly<float, 2, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = padd2(a, b);
+    v[1] = psub2(a, b);
+  }
+};
+
+template <int SIGN> struct Bfly<float, 4, SIGN> {
+  __device__ __forceinline__ static void run(float2* v) {
+    const float2 t0 = padd2(v[0], v[2]), t1 = psub2(v[0], v[2]);
+    const float2 t2 = padd2(v[1], v[3]), d = psub2(v[1], v[3]);
+    v[0] = padd2(t0, t2);
+    v[2] = psub2(t0, t2);
+    // t3 = SIGN i d; v1 = t1 + t3, v3 = t1 - t3
+    if (SIGN > 0) {
+      v[1] = make_float2(t1.x - d.y, t1.y + d.x);
+      v[3] = make_float2(t1.x + d.y, t1.y - d.x);
+    } else {
+      v[1] = make_float2(t1.x + d.y, t1.y - d.x);
+      v[3] = make_float2(t1.x - d.y, t1.y + d.x);
+    }
+  }
+};
+
 template <typename T, int SIGN> struct Bfly<T, 8, SIGN> {
   __device__ __forceinline__ static void run(C2<T>* v) {
     C2<T> e[4] = {v[0], v[2], v[4], v[6]};
@@ -1941,7 +1987,14 @@ cudaError_t launch_col(int mode, const C2<T>* spec, C2<T>* o0, C2<T>* o1, C2<T>*
       return col_E<T, 12, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st, bat);
     return col_E<T, 8, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st, bat);
   }
-  if (sizeof(T) == 4 && mode == COL_MATVEC && tb.var_col == VAR_E4 && fft_E(N) == 8 && N >= 4)
+  if constexpr (sizeof(T) == 4) {
+    if (mode == COL_MATVEC && tb.var_col == VAR_PAIR && col_pair_supported(N, M))
+      return launch_col_pair(reinterpret_cast<const float2*>(spec),
+                             reinterpret_cast<float2*>(o0), reinterpret_cast<float2*>(o1),
+                             reinterpret_cast<float2*>(o2), N, M, tb, sc, skip, st);
+  }
+  if (sizeof(T) == 4 && mode == COL_MATVEC &&
+      (tb.var_col == VAR_E4 || tb.var_col == VAR_PAIR) && fft_E(N) == 8 && N >= 4)
     return col_E<T, 4, COL_MATVEC>(spec, o0, o1, o2, N, M, tb, sc, skip, st);
   if (fft_E(N) == 12) return col_dispatch<T, 12>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);
   return col_dispatch<T, 8>(mode, spec, o0, o1, o2, N, M, tb, sc, skip, st);

@@ -1,0 +1,327 @@
+// Column pass of the FP32 matvec (Sec. 4.2) on column pairs with packed FP32 arithmetic.
+//
+// The pass computes what k_col<float, E, COL_MATVEC> computes -- per column of the packed
+// N x M/2 half spectrum: the forward column FFT, S = rho-bar sigma-hat / (N M), and the
+// inverse column FFTs of S (its Nyquist channel premultiplied), (i s1(k2)) S and s2(k2) S --
+// but one block takes two neighbouring columns c0 = 2b and c0 + 1 and holds them side by
+// side: the element n of a transform pair is the 16-byte word (a.x, b.x, a.y, b.y) of the
+// two columns' values a and b.  The real parts and the imaginary parts of the pair are then
+// register pairs, so every complex addition of a butterfly is one packed instruction
+// (add/sub.rn.f32x2) for both columns, and every twiddle multiplication two packed
+// multiply-adds per part, with the twiddle broadcast to both lanes; the multiplication by
+// +-i exchanges the parts and costs nothing.  A thread holds 4 elements (radix-4 stages,
+// one radix-2 stage for odd powers of two), the length is fixed at compile time
+// (256 ... 2048), and the stages run out of place between two buffer sets (one barrier a
+// stage).  Shared memory is addressed through an XOR swizzle of the 16-byte element index,
+// i ^ ((i >> 2) & 7), under which every stage's reads and writes of a quarter warp fall in
+// distinct bank groups.  The symbol multiplies are the scalar operations of k_col.
+#include "spectral.cuh"
+
+namespace otgb {
+namespace {
+
+typedef unsigned long long u64;
+// two complex numbers, one per column: re = (a.x, b.x), im = (a.y, b.y)
+struct __align__(16) PC {
+  u64 re, im;
+};
+
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// a * b + c per lane
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 2) & 7); }
+
+// v * w (SIGN < 0) or v * conj(w) (SIGN > 0); wx = (w.x, w.x), wy = (w.y, w.y), nwy = -wy
+template <int SIGN>
+__device__ __forceinline__ PC cmulp(PC v, u64 wx, u64 wy, u64 nwy) {
+  PC r;
+  if (SIGN < 0) {
+    r.re = fma2(v.im, nwy, mul2(v.re, wx));
+    r.im = fma2(v.re, wy, mul2(v.im, wx));
+  } else {
+    r.re = fma2(v.im, wy, mul2(v.re, wx));
+    r.im = fma2(v.re, nwy, mul2(v.im, wx));
+  }
+  return r;
+}
+
+template <int R, int SIGN> struct BflyP;
+template <int SIGN> struct BflyP<2, SIGN> {
+  __device__ __forceinline__ static void run(PC* v) {
+    const PC a = v[0], b = v[1];
+    v[0].re = add2(a.re, b.re);
+    v[0].im = add2(a.im, b.im);
+    v[1].re = sub2(a.re, b.re);
+    v[1].im = sub2(a.im, b.im);
+  }
+};
+template <int SIGN> struct BflyP<4, SIGN> {
+  __device__ __forceinline__ static void run(PC* v) {
+    const u64 t0r = add2(v[0].re, v[2].re), t0i = add2(v[0].im, v[2].im);
+    const u64 t1r = sub2(v[0].re, v[2].re), t1i = sub2(v[0].im, v[2].im);
+    const u64 t2r = add2(v[1].re, v[3].re), t2i = add2(v[1].im, v[3].im);
+    const u64 dr = sub2(v[1].re, v[3].re), di = sub2(v[1].im, v[3].im);
+    v[0].re = add2(t0r, t2r);
+    v[0].im = add2(t0i, t2i);
+    v[2].re = sub2(t0r, t2r);
+    v[2].im = sub2(t0i, t2i);
+    // t3 = SIGN i d: v1 = t1 + t3, v3 = t1 - t3
+    if (SIGN > 0) {
+      v[1].re = sub2(t1r, di);
+      v[1].im = add2(t1i, dr);
+      v[3].re = add2(t1r, di);
+      v[3].im = sub2(t1i, dr);
+    } else {
+      v[1].re = add2(t1r, di);
+      v[1].im = sub2(t1i, dr);
+      v[3].re = sub2(t1r, di);
+      v[3].im = add2(t1i, dr);
+    }
+  }
+};
+
+template <int REM>
+__host__ __device__ constexpr int pstage_count() {
+  if constexpr (REM > 1)
+    return 1 + pstage_count<REM / (REM % 4 == 0 ? 4 : 2)>();
+  else
+    return 0;
+}
+
+// One out-of-place stage of radix R (span Ns) on NP transform pairs of length L, 4 elements
+// per thread; tw: the stage-ordered twiddles as (w.x, w.x, w.y, w.y) words.
+template <int R, int SIGN, int L, int Ns, int NP>
+__device__ __forceinline__ void pstage(PC* const (&in)[NP], PC* const (&out)[NP], int t,
+                                       const ulonglong2* __restrict__ tw) {
+  constexpr int E = 4, TPT = L / E, LR = L / R;
+  constexpr int a = Ns == 1 ? 0 : __builtin_ctz(Ns);
+  PC v[NP][E];
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = t + b * TPT;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int src = swz(j + r * LR);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) v[q][b * R + r] = in[q][src];
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < E / R; ++b) {
+    const int j = t + b * TPT;
+    const int qd = j >> a;
+    const int k = j & (Ns - 1);
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const ulonglong2 w = tw[(Ns - 1) + (r - 1) * Ns + k];
+        const u64 nwy = sub2(0ull, w.y);  // (0, 0) - (w.y, w.y)
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+          v[q][b * R + r] = cmulp<SIGN>(v[q][b * R + r], w.x, w.y, nwy);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) BflyP<R, SIGN>::run(&v[q][b * R]);
+    const int d = qd * (Ns * R) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int dst = swz(d + r * Ns);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) out[q][dst] = v[q][b * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+// the transform: stages alternating between a and b, starting from a; the result ends in a
+// for an even number of stages, in b for an odd one
+template <int SIGN, int L, int Ns, int REM, int NP, bool FROM_A>
+__device__ __forceinline__ void pfft_rec(PC* const (&a)[NP], PC* const (&b)[NP], int t,
+                                         const ulonglong2* __restrict__ tw) {
+  if constexpr (REM > 1) {
+    constexpr int R = REM % 4 == 0 ? 4 : 2;
+    if constexpr (FROM_A)
+      pstage<R, SIGN, L, Ns, NP>(a, b, t, tw);
+    else
+      pstage<R, SIGN, L, Ns, NP>(b, a, t, tw);
+    pfft_rec<SIGN, L, Ns * R, REM / R, NP, !FROM_A>(a, b, t, tw);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
+    k_col_pair(const float2* __restrict__ spec, float2* __restrict__ out0,
+               float2* __restrict__ out1, float2* __restrict__ out2, int M, float inv,
+               const float2* __restrict__ twN, const DevScalars* __restrict__ sc,
+               const int* __restrict__ skip, const float2* __restrict__ symx,
+               const float2* __restrict__ symy) {
+  if (skip && *skip) return;
+  constexpr int TPT = N / 4;
+  constexpr bool ODD = pstage_count<N>() % 2 == 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* tw4 = reinterpret_cast<ulonglong2*>(smem_raw);
+  PC* pb = reinterpret_cast<PC*>(smem_raw + (size_t)N * sizeof(ulonglong2));
+  PC* const P[6] = {pb, pb + N, pb + 2 * N, pb + 3 * N, pb + 4 * N, pb + 5 * N};
+  const int Lc = M / 2;
+  const int c0 = 2 * blockIdx.x;
+  const int t = threadIdx.x;
+
+  // the stage twiddles of the 4-element transforms, broadcast to both lanes
+  const float2* __restrict__ st = twN + (size_t)stage_table_slot<4>() * N;
+  for (int i = t; i < N; i += TPT) {
+    const float2 w = st[i];
+    tw4[i] = make_ulonglong2(pk(w.x, w.x), pk(w.y, w.y));
+  }
+  // the column pair: one 16-byte load per row, regrouped into (re, im) pairs
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int n = t + e * TPT;
+    const float4 x = *reinterpret_cast<const float4*>(spec + (size_t)n * Lc + c0);
+    PC v;
+    v.re = pk(x.x, x.z);
+    v.im = pk(x.y, x.w);
+    P[0][swz(n)] = v;
+  }
+  __syncthreads();
+
+  // forward column transforms of both columns (from P0, scratch P3)
+  {
+    PC* const a[1] = {P[0]};
+    PC* const b[1] = {P[3]};
+    pfft_rec<-1, N, 1, N, 1, true>(a, b, t, tw4);
+  }
+  PC* const F = ODD ? P[3] : P[0];
+  // the inverse transforms start in the set that does not hold F
+  PC* const I0 = ODD ? P[0] : P[3];
+  PC* const I1 = ODD ? P[1] : P[4];
+  PC* const I2 = ODD ? P[2] : P[5];
+
+  float ab[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) ab[q] = sc ? (float)sc->abar[q] : 0.f;
+  const float2 sxa = symx[c0], sxb = symx[c0 + 1];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int k = t + e * TPT;
+    const PC z = F[swz(k)];
+    float2 za, zb;
+    upk(z.re, za.x, zb.x);
+    upk(z.im, za.y, zb.y);
+    const float2 sy = symy[k];
+    float2 sa, s0a;
+    if (c0 == 0) {
+      // the two real columns k1 = 0 and k1 = M/2 carried as X0 + i XL (as in k_col)
+      const PC pz = F[swz((N - k) % N)];
+      float2 p, pbv;
+      upk(pz.re, p.x, pbv.x);
+      upk(pz.im, p.y, pbv.y);
+      float2 A = mk2<float>(0.5f * (za.x + p.x), 0.5f * (za.y - p.y));
+      float2 B = mk2<float>(0.5f * (za.y + p.y), -0.5f * (za.x - p.x));
+      A = cmul<float>(rho_bar<float>(ab, symx[0], sy), A);
+      B = cmul<float>(rho_bar<float>(ab, symx[M / 2], sy), B);
+      const float2 Bn = cscale<float>(B, symx[M / 2].y);
+      s0a = cscale<float>(mk2<float>(A.x - Bn.y, A.y + Bn.x), inv);
+      sa = cscale<float>(mk2<float>(A.x - B.y, A.y + B.x), inv);
+    } else {
+      sa = cscale<float>(cmul<float>(rho_bar<float>(ab, sxa, sy), za), inv);
+      s0a = sa;
+    }
+    const float2 sb = cscale<float>(cmul<float>(rho_bar<float>(ab, sxb, sy), zb), inv);
+    const int d = swz(k);
+    PC q;
+    q.re = pk(s0a.x, sb.x);
+    q.im = pk(s0a.y, sb.y);
+    I0[d] = q;
+    q.re = pk(-sy.x * sa.y, -sy.x * sb.y);
+    q.im = pk(sy.x * sa.x, sy.x * sb.x);
+    I1[d] = q;
+    q.re = pk(sa.x * sy.y, sb.x * sy.y);
+    q.im = pk(sa.y * sy.y, sb.y * sy.y);
+    I2[d] = q;
+  }
+  __syncthreads();
+
+  // the three inverse transforms interleaved
+  PC* const ia[3] = {I0, I1, I2};
+  PC* const ib[3] = {ODD ? P[3] : P[0], ODD ? P[4] : P[1], ODD ? P[5] : P[2]};
+  pfft_rec<+1, N, 1, N, 3, true>(ia, ib, t, tw4);
+  PC* const* res = ODD ? ib : ia;
+  float2* const outs[3] = {out0, out1, out2};
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int n = t + e * TPT;
+      const PC v = res[o][swz(n)];
+      float4 x;
+      upk(v.re, x.x, x.z);
+      upk(v.im, x.y, x.w);
+      *reinterpret_cast<float4*>(outs[o] + (size_t)n * Lc + c0) = x;
+    }
+  }
+}
+
+template <int N>
+cudaError_t col_pair_N(const float2* spec, float2* o0, float2* o1, float2* o2, int M,
+                       const SpecTables& tb, const DevScalars* sc, const int* skip,
+                       cudaStream_t st) {
+  const size_t sm = (size_t)N * sizeof(ulonglong2) + 6 * (size_t)N * sizeof(PC);
+  cudaError_t e = prepare_launch(k_col_pair<N>, N / 4, sm);
+  if (e != cudaSuccess) return e;
+  k_col_pair<N><<<M / 4, N / 4, sm, st>>>(
+      spec, o0, o1, o2, M, (float)(1.0 / ((double)N * (double)M)), (const float2*)tb.twN, sc,
+      skip, (const float2*)tb.symx, (const float2*)tb.symy);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool col_pair_supported(int N, int M) {
+  return (N == 256 || N == 512 || N == 1024 || N == 2048) && M >= 4 && M % 4 == 0;
+}
+
+cudaError_t launch_col_pair(const float2* spec, float2* o0, float2* o1, float2* o2, int N,
+                            int M, const SpecTables& tb, const DevScalars* sc, const int* skip,
+                            cudaStream_t st) {
+  if (!col_pair_supported(N, M)) return cudaErrorInvalidValue;
+  // 16-byte loads and stores of a column pair need 16-byte aligned planes
+  if (((uintptr_t)spec | (uintptr_t)o0 | (uintptr_t)o1 | (uintptr_t)o2) & 15)
+    return cudaErrorMisalignedAddress;
+  switch (N) {
+    case 256: return col_pair_N<256>(spec, o0, o1, o2, M, tb, sc, skip, st);
+    case 512: return col_pair_N<512>(spec, o0, o1, o2, M, tb, sc, skip, st);
+    case 1024: return col_pair_N<1024>(spec, o0, o1, o2, M, tb, sc, skip, st);
+    case 2048: return col_pair_N<2048>(spec, o0, o1, o2, M, tb, sc, skip, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace otgb

@@ -23,6 +23,9 @@ def test_variant_names_decode_the_option_encoding():
     assert v["col_matvec"] == "k_col_matvec_par<float, 8>"
     assert v["row_c2r_combine"] == "k_row_combine_w<float>"
     assert v["col_q4"] is False
+    v = bench.variant_names(3 + 4 * 3 + 16 * 2 + 256)
+    assert v["col_matvec"] == "k_col_pair<N>" and v["row_r2c"] == "k_row_r2c<float, 4>"
+    assert v["row_c2r_combine"] == "k_row_combine_w<float>" and v["code"] == 303
 
 
 def test_algorithmic_bytes():
