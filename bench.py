@@ -200,7 +200,8 @@ def variant_names(v):
                 "register_resident": True}
     return {"code": v, "row_r2c": row[r],
             "col_matvec": "k_col_pair<N>" if v & 256 else col[c],
-            "row_c2r_combine": comb[b], "col_q4": bool(v & 64)}
+            "row_c2r_combine": "k_comb_pair<M/2>" if v & 512 else comb[b],
+            "col_q4": bool(v & 64)}
 
 
 def traffic_for(kernel_cls, size):

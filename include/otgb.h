@@ -181,7 +181,9 @@ extern "C" {
                                    + 64: the generic column pass with 4 columns per block;
                                    + 256: the column pass on column pairs with packed FP32
                                    arithmetic (N a power of two in 256..2048, M a multiple
-                                   of 4; elsewhere c = 3); turns OT_OPT_AUTOTUNE off */
+                                   of 4; elsewhere c = 3); + 512: the combine pass on row
+                                   pairs (M/2 a power of two in 256..1024, N even; elsewhere
+                                   b = 3); turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

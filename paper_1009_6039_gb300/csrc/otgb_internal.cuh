@@ -180,7 +180,8 @@ struct SpecTables {
   // -1 default, 0 generic (8 or 12 elements per thread, one transform after the other),
   // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32,
   // 3 generic with 4 elements per thread (radix 4, twice the threads; power-of-two lengths),
-  // 4 (column pass only) column pairs with packed FP32 arithmetic (spectral_pair.cu)
+  // 4 (column and combine passes) column / row pairs with packed FP32 arithmetic
+  // (spectral_pair.cu)
   int var_r2c = -1, var_col = -1, var_comb = -1;
   // generic column matvec pass: columns per block (0: the default heuristic)
   int col_q = 0;
@@ -196,6 +197,11 @@ struct SpecTables {
 };
 enum { VAR_DEFAULT = -1, VAR_GENERIC = 0, VAR_PAR = 1, VAR_WARP = 2, VAR_E4 = 3, VAR_PAIR = 4 };
 
+// the FP32 row combine pass on row pairs (M / 2 a power of two in 256..1024, N even)
+bool comb_pair_supported(int N, int M);
+cudaError_t launch_comb_pair(const float2* q0, const float2* q1, const float2* q2,
+                             const float* coef, float* out, int N, int M, const SpecTables& tb,
+                             const int* skip, cudaStream_t st);
 // the FP32 column matvec pass on column pairs (power-of-two N in 256..2048, M % 4 == 0)
 bool col_pair_supported(int N, int M);
 cudaError_t launch_col_pair(const float2* spec, float2* o0, float2* o1, float2* o2, int N,

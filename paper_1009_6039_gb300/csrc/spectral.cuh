@@ -2072,8 +2072,16 @@ cudaError_t launch_row_c2r(int mode, const C2<T>* q0, const C2<T>* q1, const C2<
     return row_c2r_E<T, 8, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
                                            tb, skip, st, sc, bat);
   }
-  if (sizeof(T) == 4 && mode == ROWINV_COMBINE && tb.var_comb == VAR_E4 && fft_E(M / 2) == 8 &&
-      M / 2 >= 4)
+  if constexpr (sizeof(T) == 4) {
+    if (mode == ROWINV_COMBINE && tb.var_comb == VAR_PAIR && comb_pair_supported(N, M))
+      return launch_comb_pair(reinterpret_cast<const float2*>(q0),
+                              reinterpret_cast<const float2*>(q1),
+                              reinterpret_cast<const float2*>(q2),
+                              reinterpret_cast<const float*>(coef), reinterpret_cast<float*>(out),
+                              N, M, tb, skip, st);
+  }
+  if (sizeof(T) == 4 && mode == ROWINV_COMBINE &&
+      (tb.var_comb == VAR_E4 || tb.var_comb == VAR_PAIR) && fft_E(M / 2) == 8 && M / 2 >= 4)
     return row_c2r_E<T, 4, ROWINV_COMBINE>(q0, q1, q2, coef, out, u_in, u_out, step, os, N, M,
                                            tb, skip, st, sc);
   if (fft_E(M / 2) == 12)

@@ -115,9 +115,10 @@ __host__ __device__ constexpr int pstage_count() {
     return 0;
 }
 
-// One out-of-place stage of radix R (span Ns) on NP transform pairs of length L, 4 elements
-// per thread; tw: the stage-ordered twiddles as (w.x, w.x, w.y, w.y) words.
-template <int R, int SIGN, int L, int Ns, int NP>
+// One stage of radix R (span Ns) on NP transform pairs of length L, 4 elements per thread;
+// tw: the stage-ordered twiddles as (w.x, w.x, w.y, w.y) words.  Out of place (one barrier)
+// or in place (INPLACE: the stores wait for every thread's loads).
+template <int R, int SIGN, int L, int Ns, int NP, bool INPLACE = false>
 __device__ __forceinline__ void pstage(PC* const (&in)[NP], PC* const (&out)[NP], int t,
                                        const ulonglong2* __restrict__ tw) {
   constexpr int E = 4, TPT = L / E, LR = L / R;
@@ -133,6 +134,7 @@ __device__ __forceinline__ void pstage(PC* const (&in)[NP], PC* const (&out)[NP]
       for (int q = 0; q < NP; ++q) v[q][b * R + r] = in[q][src];
     }
   }
+  if (INPLACE) __syncthreads();
 #pragma unroll
   for (int b = 0; b < E / R; ++b) {
     const int j = t + b * TPT;
@@ -176,6 +178,28 @@ __device__ __forceinline__ void pfft_rec(PC* const (&a)[NP], PC* const (&b)[NP],
   }
 }
 
+// the same transform in place
+template <int SIGN, int L, int Ns, int REM, int NP>
+__device__ __forceinline__ void pfft_inplace(PC* const (&a)[NP], int t,
+                                             const ulonglong2* __restrict__ tw) {
+  if constexpr (REM > 1) {
+    constexpr int R = REM % 4 == 0 ? 4 : 2;
+    pstage<R, SIGN, L, Ns, NP, true>(a, a, t, tw);
+    pfft_inplace<SIGN, L, Ns * R, REM / R, NP>(a, t, tw);
+  }
+}
+
+// the stage twiddles of the 4-element transforms of length L, broadcast to both lanes
+template <int L>
+__device__ __forceinline__ void load_tw4(ulonglong2* tw4, const float2* __restrict__ twb, int t,
+                                         int nthreads) {
+  const float2* __restrict__ st = twb + (size_t)stage_table_slot<4>() * L;
+  for (int i = t; i < L; i += nthreads) {
+    const float2 w = st[i];
+    tw4[i] = make_ulonglong2(pk(w.x, w.x), pk(w.y, w.y));
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
     k_col_pair(const float2* __restrict__ spec, float2* __restrict__ out0,
@@ -194,12 +218,7 @@ __global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
   const int c0 = 2 * blockIdx.x;
   const int t = threadIdx.x;
 
-  // the stage twiddles of the 4-element transforms, broadcast to both lanes
-  const float2* __restrict__ st = twN + (size_t)stage_table_slot<4>() * N;
-  for (int i = t; i < N; i += TPT) {
-    const float2 w = st[i];
-    tw4[i] = make_ulonglong2(pk(w.x, w.x), pk(w.y, w.y));
-  }
+  load_tw4<N>(tw4, twN, t, TPT);
   // the column pair: one 16-byte load per row, regrouped into (re, im) pairs
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -289,6 +308,167 @@ __global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Row combine pass of the FP32 matvec on row pairs (Sec. 4.2): the five complex-to-real
+// row transforms d_xx Q0, d_x Q0, d_x Q1, Q1, Q2 of two neighbouring rows r0 = 2b and
+// r0 + 1, held side by side as in k_col_pair, weighted by a11, b1, 2 a12, b2, a22 and summed
+// into w = L Lbar^{-1} sigma.  The row symbols, the complex-to-real pre-processing, the
+// transforms and the weighting all run on the packed pairs; the stages run in place (two
+// barriers a stage), which keeps a block at 48 KB of shared memory at length 512, so that
+// the N / 2 blocks of a 1024 x 1024 grid run in one wave.
+// ---------------------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(L / 4, L <= 512 ? 4 : 2)
+    k_comb_pair(const float2* __restrict__ q0, const float2* __restrict__ q1,
+                const float2* __restrict__ q2, const float* __restrict__ coef,
+                float* __restrict__ out, int N, const float2* __restrict__ twL,
+                const float2* __restrict__ twM, const int* __restrict__ skip,
+                const float2* __restrict__ symx) {
+  if (skip && *skip) return;
+  constexpr int TPT = L / 4;
+  constexpr int M = 2 * L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* tw4 = reinterpret_cast<ulonglong2*>(smem_raw);
+  PC* pb = reinterpret_cast<PC*>(smem_raw + (size_t)L * sizeof(ulonglong2));
+  PC* const B[5] = {pb, pb + L, pb + 2 * L, pb + 3 * L, pb + 4 * L};
+  const int r0 = 2 * blockIdx.x;
+  const int t = threadIdx.x;
+  load_tw4<L>(tw4, twL, t, TPT);
+
+  // the five terms of both rows: d_xx Q0, d_x Q0, d_x Q1, Q1, Q2 (row symbols of k1 = k; the
+  // packed entry k = 0 holds (X0, X_L): d_x is 0 on both, d_xx keeps the Nyquist channel,
+  // which Q0 carries premultiplied)
+  const size_t oa = (size_t)r0 * L, ob = oa + L;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int k = t + e * TPT;
+    const float2 a0 = q0[oa + k], b0 = q0[ob + k];
+    const float2 a1 = q1[oa + k], b1 = q1[ob + k];
+    const float2 a2 = q2[oa + k], b2 = q2[ob + k];
+    PC x0, x1, x2;
+    x0.re = pk(a0.x, b0.x);
+    x0.im = pk(a0.y, b0.y);
+    x1.re = pk(a1.x, b1.x);
+    x1.im = pk(a1.y, b1.y);
+    x2.re = pk(a2.x, b2.x);
+    x2.im = pk(a2.y, b2.y);
+    PC dxx, dx0, dx1;
+    if (k == 0) {
+      dxx.re = 0ull;
+      dxx.im = x0.im;
+      dx0.re = dx0.im = dx1.re = dx1.im = 0ull;
+    } else {
+      const float2 sx = symx[k];
+      const u64 s2 = pk(sx.y, sx.y), s1 = pk(sx.x, sx.x), ns1 = pk(-sx.x, -sx.x);
+      dxx.re = mul2(x0.re, s2);
+      dxx.im = mul2(x0.im, s2);
+      dx0.re = mul2(x0.im, ns1);
+      dx0.im = mul2(x0.re, s1);
+      dx1.re = mul2(x1.im, ns1);
+      dx1.im = mul2(x1.re, s1);
+    }
+    const int d = swz(k);
+    B[0][d] = dxx;
+    B[1][d] = dx0;
+    B[2][d] = dx1;
+    B[3][d] = x1;
+    B[4][d] = x2;
+  }
+  __syncthreads();
+
+  // complex-to-real pre-processing: Z_k = (X_k + conj X_(L-k)) + i (X_k - conj X_(L-k))
+  // conj(W_M^k), Z_(L-k) likewise, each pair (k, L - k) by one thread
+  for (int k = t; k <= L / 2; k += TPT) {
+    if (k == 0) {
+      const int d = swz(0);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const PC x = B[q][d];
+        PC z;
+        z.re = add2(x.re, x.im);
+        z.im = sub2(x.re, x.im);
+        B[q][d] = z;
+      }
+    } else {
+      const float2 w = twM[k];
+      const u64 wx = pk(w.x, w.x), wy = pk(w.y, w.y), nwy = pk(-w.y, -w.y);
+      const int dk = swz(k), dm = swz(L - k);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const PC xk = B[q][dk], xm = B[q][dm];
+        PC E, D;
+        E.re = add2(xk.re, xm.re);
+        E.im = sub2(xk.im, xm.im);
+        D.re = sub2(xk.re, xm.re);
+        D.im = add2(xk.im, xm.im);
+        const PC O = cmulp<+1>(D, wx, wy, nwy);
+        PC zk;
+        zk.re = sub2(E.re, O.im);
+        zk.im = add2(E.im, O.re);
+        B[q][dk] = zk;
+        if (2 * k != L) {
+          PC zm;
+          zm.re = add2(E.re, O.im);
+          zm.im = sub2(O.re, E.im);
+          B[q][dm] = zm;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  pfft_inplace<+1, L, 1, L, 5>(B, t, tw4);
+
+  // w = a11 y0 + b1 y1 + 2 a12 y2 + b2 y3 + a22 y4 on both rows (the coefficient planes a11,
+  // a12, a22, b1, b2 in that order)
+  const size_t P = (size_t)N * M;
+  const size_t ra = (size_t)r0 * M, rb = ra + M;
+  const float2* c0 = reinterpret_cast<const float2*>(coef);
+  const float2* c1 = reinterpret_cast<const float2*>(coef + P);
+  const float2* c2 = reinterpret_cast<const float2*>(coef + 2 * P);
+  const float2* c3 = reinterpret_cast<const float2*>(coef + 3 * P);
+  const float2* c4 = reinterpret_cast<const float2*>(coef + 4 * P);
+  float2* ov = reinterpret_cast<float2*>(out);
+  const u64 two = pk(2.f, 2.f);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int n = t + e * TPT;
+    const int d = swz(n);
+    const size_t ia = ra / 2 + n, ib = rb / 2 + n;
+    const float2 a11a = c0[ia], a11b = c0[ib], a12a = c1[ia], a12b = c1[ib];
+    const float2 a22a = c2[ia], a22b = c2[ib], b1a = c3[ia], b1b = c3[ib];
+    const float2 b2a = c4[ia], b2b = c4[ib];
+    const PC y0 = B[0][d], y1 = B[1][d], y2 = B[2][d], y3 = B[3][d], y4 = B[4][d];
+    u64 rr = mul2(pk(a11a.x, a11b.x), y0.re);
+    rr = fma2(pk(b1a.x, b1b.x), y1.re, rr);
+    rr = fma2(mul2(two, pk(a12a.x, a12b.x)), y2.re, rr);
+    rr = fma2(pk(b2a.x, b2b.x), y3.re, rr);
+    rr = fma2(pk(a22a.x, a22b.x), y4.re, rr);
+    u64 ri = mul2(pk(a11a.y, a11b.y), y0.im);
+    ri = fma2(pk(b1a.y, b1b.y), y1.im, ri);
+    ri = fma2(mul2(two, pk(a12a.y, a12b.y)), y2.im, ri);
+    ri = fma2(pk(b2a.y, b2b.y), y3.im, ri);
+    ri = fma2(pk(a22a.y, a22b.y), y4.im, ri);
+    float2 wa, wb;
+    upk(rr, wa.x, wb.x);
+    upk(ri, wa.y, wb.y);
+    ov[ia] = wa;
+    ov[ib] = wb;
+  }
+}
+
+template <int L>
+cudaError_t comb_pair_L(const float2* q0, const float2* q1, const float2* q2, const float* coef,
+                        float* out, int N, const SpecTables& tb, const int* skip,
+                        cudaStream_t st) {
+  const size_t sm = (size_t)L * sizeof(ulonglong2) + 5 * (size_t)L * sizeof(PC);
+  cudaError_t e = prepare_launch(k_comb_pair<L>, L / 4, sm);
+  if (e != cudaSuccess) return e;
+  k_comb_pair<L><<<N / 2, L / 4, sm, st>>>(q0, q1, q2, coef, out, N, (const float2*)tb.twL,
+                                           (const float2*)tb.twM, skip,
+                                           (const float2*)tb.symx);
+  return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t col_pair_N(const float2* spec, float2* o0, float2* o1, float2* o2, int M,
                        const SpecTables& tb, const DevScalars* sc, const int* skip,
@@ -303,6 +483,23 @@ cudaError_t col_pair_N(const float2* spec, float2* o0, float2* o1, float2* o2, i
 }
 
 }  // namespace
+
+bool comb_pair_supported(int N, int M) {
+  const int L = M / 2;
+  return (L == 256 || L == 512 || L == 1024) && M == 2 * L && N >= 2 && N % 2 == 0;
+}
+
+cudaError_t launch_comb_pair(const float2* q0, const float2* q1, const float2* q2,
+                             const float* coef, float* out, int N, int M, const SpecTables& tb,
+                             const int* skip, cudaStream_t st) {
+  if (!comb_pair_supported(N, M)) return cudaErrorInvalidValue;
+  switch (M / 2) {
+    case 256: return comb_pair_L<256>(q0, q1, q2, coef, out, N, tb, skip, st);
+    case 512: return comb_pair_L<512>(q0, q1, q2, coef, out, N, tb, skip, st);
+    case 1024: return comb_pair_L<1024>(q0, q1, q2, coef, out, N, tb, skip, st);
+  }
+  return cudaErrorInvalidValue;
+}
 
 bool col_pair_supported(int N, int M) {
   return (N == 256 || N == 512 || N == 1024 || N == 2048) && M >= 4 && M % 4 == 0;

@@ -199,7 +199,7 @@ def test_longest_transforms(ot, N, M, prec):
                                  (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
                                      3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64, 128,
-                                     3 + 4 * 3 + 16 * 3 + 256])
+                                     3 + 4 * 3 + 16 * 3 + 256, 63 + 256 + 512])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
     # (at 1024^2 the concurrent column pass, launched first, needs more shared memory than
@@ -244,12 +244,15 @@ def test_register_resident_matvec(ot, N, M):
         p.close()
 
 
-@pytest.mark.parametrize("N,M", [(256, 24), (256, 512), (512, 256), (1024, 64), (2048, 128)])
+@pytest.mark.parametrize("N,M", [(256, 24), (256, 512), (512, 256), (1024, 64), (2048, 128),
+                                 (8, 512), (12, 1024), (48, 2048)])
 def test_column_pair_pass(ot, N, M):
-    # the column matvec pass on column pairs with packed FP32 arithmetic (OT_OPT_FFT_VARIANT
-    # bit 256) at every column length it covers (256 .. 2048; the pair with the packed
-    # DC / Nyquist column included), both symbol sets: the oracle's operator within the FP32
-    # bounds of the other variants, and the choice read back through the option
+    # the column matvec pass on column pairs and the combine pass on row pairs, with packed
+    # FP32 arithmetic (OT_OPT_FFT_VARIANT bits 256 and 512), at every length they cover
+    # (columns of 256 .. 2048, rows of 512 .. 2048 points; the pair with the packed DC /
+    # Nyquist column included; sizes that only one of them covers take another variant for
+    # the other pass), both symbol sets: the oracle's operator within the FP32 bounds of the
+    # other variants, and the choice read back through the option
     f = I.blob_density(N, M, 27)
     g = I.blob_density(N, M, 28)
     u = smooth_field(N, M, amp=2e-3)
@@ -259,8 +262,8 @@ def test_column_pair_pass(ot, N, M):
     for symbols in (0, 1):
         with O.fd_symbols(symbols):
             w_ref = O.apply_op(coef, abar, sigma)
-        p = plan(ot, N, M, "mixed", fft_variant=63 + 256, symbols=symbols)
-        assert int(p.get("fft_variant")) & 256
+        p = plan(ot, N, M, "mixed", fft_variant=63 + 256 + 512, symbols=symbols)
+        assert int(p.get("fft_variant")) & 768 == 768
         cd, sd, wd = dev(coef), dev(sigma), dev(np.zeros((N, M)))
         assert ot.ot_apply_operator(p.h, ptr(cd), hptr(abar), ptr(sd), ptr(wd)) == 0
         assert np.abs(wd.cpu().numpy() - w_ref).max() <= 5e-6 * np.abs(w_ref).max()
@@ -277,7 +280,7 @@ def test_autotuned_solve_matches_fixed_variant(ot):
         rc, st = p.solve(dev(f), dev(g), phi)
         # the variants in use read back in the encoding the option takes
         v = p.get("fft_variant")
-        assert v == 0 if "fft_variant" in kw else 0 <= v <= 511
+        assert v == 0 if "fft_variant" in kw else 0 <= v <= 1023
         assert p.get("tau") == 4.0 and p.get("precision") == 1
         p.close()
         assert rc == 0 and st["status"] == 0
@@ -506,8 +509,8 @@ def test_warm_start_from_solution_takes_no_step(ot):
 
 
 @pytest.mark.parametrize("N,M,variant", [(256, 256, 0), (192, 384, 0), (1024, 1024, 0),
-                                         (1024, 1024, 128), (1024, 1024, 63 + 256),
-                                         (2048, 256, 63 + 256)])
+                                         (1024, 1024, 128), (1024, 1024, 63 + 256 + 512),
+                                         (2048, 256, 63 + 256), (256, 2048, 63 + 512)])
 def test_fp32_operator_norm_accuracy(ot, N, M, variant):
     # The FP32 operator must stay at FP32 round-off in the 2-norm (a few 1e-7 per FFT pass,
     # ~1e-6 for the whole matvec), also for inputs whose spectrum spans many decades
