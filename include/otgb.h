@@ -172,6 +172,16 @@ extern "C" {
                                    next step's product (the update forms v_(j+1) row by row
                                    and transforms it in place of a separate row pass); 0: two
                                    launches.  Same arithmetic either way (bit for bit) */
+#define OT_OPT_THETA_PAIRS 32   /* mixed mode, double-float theta (OT_OPT_THETA_FP64 = 2),
+                                   single problem: 1 (default) runs theta's column and row
+                                   passes and the learned start's Poisson solves on column /
+                                   row pairs with packed FP32 arithmetic where the sizes allow
+                                   (N a power of two in 256..2048 and M a multiple of 4 for the
+                                   column pass, M/2 a power of two in 256..1024 and N even for
+                                   the row pass); 0: one column / row per thread group.  The
+                                   double-float inverse transforms are the same arithmetic per
+                                   column either way; the FP32 forward column transform
+                                   rounds differently */
 #define OT_OPT_FFT_VARIANT 16   /* mixed mode: fix the FP32 transform kernels instead of
                                    autotuning: value r + 4 c + 16 b with r (row R2C), c
                                    (column matvec) and b (row combine) each 0 = generic,

@@ -26,6 +26,7 @@ OT_OPT_FORCING, OT_OPT_TAU_RETRY, OT_OPT_WS_TEST_STALL, OT_OPT_OPERATOR = 18, 19
 OT_OPT_PHASE_TIMES, OT_OPT_TRANSPORT, OT_OPT_TAU_SWITCH, OT_OPT_INTERP = 22, 23, 24, 25
 OT_OPT_LINEAR_SOLVER, OT_OPT_MAX_BICG, OT_OPT_UNCOND_STEPS = 26, 27, 28
 OT_OPT_KRYLOV_BLOCKS, OT_OPT_L2_PERSIST, OT_OPT_FUSED_UPDATE = 29, 30, 31
+OT_OPT_THETA_PAIRS = 32
 PROF_CLASSES = ["residual", "row_r2c", "col_matvec", "row_c2r_combine", "col_lbarinv",
                 "row_c2r_update", "gmres_dots", "gmres_update", "gmres_other", "other",
                 "warmstart"]
@@ -429,7 +430,8 @@ class Plan:
              "tau_switch": OT_OPT_TAU_SWITCH, "interp": OT_OPT_INTERP,
              "linear_solver": OT_OPT_LINEAR_SOLVER, "max_bicg": OT_OPT_MAX_BICG,
              "uncond_steps": OT_OPT_UNCOND_STEPS, "krylov_blocks": OT_OPT_KRYLOV_BLOCKS,
-             "l2_persist": OT_OPT_L2_PERSIST, "fused_update": OT_OPT_FUSED_UPDATE}
+             "l2_persist": OT_OPT_L2_PERSIST, "fused_update": OT_OPT_FUSED_UPDATE,
+             "theta_pairs": OT_OPT_THETA_PAIRS}
 
     def __init__(self, N, M, tau=2.0, tol=1e-8, stream=None, **opts):
         rc, h = ot_plan_create(N, M, tau, tol)

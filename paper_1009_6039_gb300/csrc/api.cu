@@ -61,6 +61,7 @@ struct ot_plan {
   int kbps = 2;  // OT_OPT_KRYLOV_BLOCKS: blocks per SM of the GMRES vector kernels
   int l2persist = 0;  // OT_OPT_L2_PERSIST: the Krylov basis as persisting L2 lines (graph)
   int fused_update = 1;  // OT_OPT_FUSED_UPDATE: Arnoldi update fused with the next row pass
+  int theta_pairs = 1;   // OT_OPT_THETA_PAIRS: theta's double-float passes on pairs
   int linsolver = 0;
   int max_bicg = 20000;
   double* fdv = nullptr;
@@ -522,6 +523,7 @@ static int alloc_tables(ot_plan* p) {
   }
   CK(cudaMalloc(&p->twdd, ntw * 16));
   CK(cudaMemcpy(p->twdd, twd.data(), ntw * 16, cudaMemcpyHostToDevice));
+  p->tb32.theta_pair = p->tbdd.theta_pair = p->theta_pairs;
   p->tbdd.twL = p->twdd;
   p->tbdd.twM = (const ddc*)p->twdd + 4 * L;
   p->tbdd.twN = (const ddc*)p->twdd + 5 * L;
@@ -864,6 +866,14 @@ extern "C" int ot_plan_set_option(ot_plan* p, int32_t key, double v) {
         free_graph(p);
       }
       return OT_OK;
+    case OT_OPT_THETA_PAIRS:
+      if (v != 0 && v != 1) return OT_EINVAL;
+      if (p->theta_pairs != (int)v) {
+        p->theta_pairs = (int)v;
+        p->tb32.theta_pair = p->tbdd.theta_pair = p->theta_pairs;
+        free_graph(p);
+      }
+      return OT_OK;
     case OT_OPT_UNCOND_STEPS:
       if (v < 0 || v > OTGB_MAXM || v != (double)(int)v) return OT_EINVAL;
       if (p->uncond != (int)v) {
@@ -931,6 +941,7 @@ extern "C" int ot_plan_get_option(ot_plan* p, int32_t key, double* v) {
     case OT_OPT_KRYLOV_BLOCKS: *v = p->kbps; return OT_OK;
     case OT_OPT_L2_PERSIST: *v = p->l2persist; return OT_OK;
     case OT_OPT_FUSED_UPDATE: *v = p->fused_update; return OT_OK;
+    case OT_OPT_THETA_PAIRS: *v = p->theta_pairs; return OT_OK;
     case OT_OPT_TRANSPORT: *v = p->transport; return OT_OK;
     case OT_OPT_FFT_VARIANT: {
       // the variants in use, in the encoding ot_plan_set_option takes; -1 before the

@@ -190,6 +190,9 @@ struct SpecTables {
   // Exchange twiddles W_L^{t ka} of the two-level transforms, for the row length L = M/2
   // (t2r) and the column length N (t2c): A at [ka * (L/32) + t], B at [t * 32 + ka].
   int mv_reg = 0;
+  // theta's double-float column / row passes and the warm start's Poisson solves on column /
+  // row pairs with packed arithmetic where the sizes allow (spectral_pair_dd.cu)
+  int theta_pair = 0;
   const void* t2rA = nullptr;
   const void* t2rB = nullptr;
   const void* t2cA = nullptr;
@@ -202,6 +205,14 @@ bool comb_pair_supported(int N, int M);
 cudaError_t launch_comb_pair(const float2* q0, const float2* q1, const float2* q2,
                              const float* coef, float* out, int N, int M, const SpecTables& tb,
                              const int* skip, cudaStream_t st);
+// theta's double-float column pass (modes COL_LBARINV, COL_POISSON, COL_POISSON_LP) on
+// column pairs and its row pass + update on row pairs (the sizes of the FP32 pair passes)
+cudaError_t launch_col_lbarinv_pair(const float2* spec, ddc* out, int N, int M,
+                                    const SpecTables& tb32, const SpecTables& tbdd,
+                                    const DevScalars* sc, cudaStream_t st, int mode);
+cudaError_t launch_row_update_pair(const ddc* q, const double* u_in, double* u_out,
+                                   double step, int N, int M, const SpecTables& tbdd,
+                                   const DevScalars* sc, cudaStream_t st);
 // the FP32 column matvec pass on column pairs (power-of-two N in 256..2048, M % 4 == 0)
 bool col_pair_supported(int N, int M);
 cudaError_t launch_col_pair(const float2* spec, float2* o0, float2* o1, float2* o2, int N,

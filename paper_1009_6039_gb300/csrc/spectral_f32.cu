@@ -23,6 +23,8 @@ static cudaError_t col_lbarinv_dd_mode(const float2* spec, ddc* out, int N, int 
 cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
                                   const SpecTables& tb32, const SpecTables& tbdd,
                                   const DevScalars* sc, cudaStream_t st, int mode, Bat bat) {
+  if (!bat.on && tb32.theta_pair && col_pair_supported(N, M) && (mode != COL_LBARINV || sc))
+    return launch_col_lbarinv_pair(spec, out, N, M, tb32, tbdd, sc, st, mode);
   switch (mode) {
     case COL_LBARINV:
       return col_lbarinv_dd_mode<COL_LBARINV>(spec, out, N, M, tb32, tbdd, sc, st, bat);
@@ -36,6 +38,8 @@ cudaError_t launch_col_lbarinv_dd(const float2* spec, ddc* out, int N, int M,
 cudaError_t launch_row_c2r_update_dd(const ddc* q, const double* u_in, double* u_out,
                                      double step, int N, int M, const SpecTables& tbdd,
                                      const DevScalars* sc, cudaStream_t st, Bat bat) {
+  if (!bat.on && tbdd.theta_pair && comb_pair_supported(N, M))
+    return launch_row_update_pair(q, u_in, u_out, step, N, M, tbdd, sc, st);
   if (fft_E(M / 2) == 12)
     return row_c2r_update_dd_E<12>(q, u_in, u_out, step, N, M, tbdd, sc, st, bat);
   if (M / 2 >= 16 && (M / 2) / 4 <= 256)

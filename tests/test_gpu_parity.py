@@ -565,6 +565,28 @@ def test_theta_precision_modes(ot):
 
 
 
+@pytest.mark.parametrize("N,M", [(256, 256), (512, 1024), (2048, 64)])
+def test_theta_pairs_keep_the_root(ot, N, M):
+    # theta's double-float passes on column / row pairs (OT_OPT_THETA_PAIRS, the default)
+    # against one column / row per thread group: the double-float inverse transforms are the
+    # same arithmetic and only the FP32 forward column transform rounds differently, so both
+    # take the same Newton path to the same root (within the double-float / FP64 bound of the
+    # theta modes)
+    f, g = I.noise_blob_pair(N, M, s=3710)
+    out = {}
+    for pairs in (1, 0):
+        p = plan(ot, N, M, "mixed", tau=1.0, tol=1e-8, eta=1e-2, symbols=1, theta_pairs=pairs,
+                 max_newton=300)
+        assert p.get("theta_pairs") == pairs
+        phi = dev(np.zeros((N, M)))
+        rc, st = p.solve(dev(f), dev(g), phi)
+        p.close()
+        assert rc == 0 and st["res_inf"] < 1e-8
+        out[pairs] = (phi.cpu().numpy(), st)
+    assert abs(out[1][1]["newton_iters"] - out[0][1]["newton_iters"]) <= 1
+    assert np.abs(out[1][0] - out[0][0]).max() <= 1e-9
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_stencil_symbol_solve_matches_oracle(ot, prec):
     # with the stencils' symbols the operator is the exact linearisation of F; at tau = 1

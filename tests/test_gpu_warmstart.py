@@ -58,6 +58,18 @@ def random_params(seed, scale=1.0):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("lowpass", [False, True])
 def test_fd_poisson(ot, N, M, prec, lowpass):
+    _check_fd_poisson(ot, N, M, prec, lowpass)
+
+
+@pytest.mark.parametrize("N,M", [(1024, 512), (256, 2048), (2048, 64)])
+@pytest.mark.parametrize("lowpass", [False, True])
+def test_fd_poisson_on_pairs(ot, N, M, lowpass):
+    # the mixed mode's double-float passes on column / row pairs (columns of 256 .. 2048
+    # points, rows of 512 .. 2048 points)
+    _check_fd_poisson(ot, N, M, "mixed", lowpass)
+
+
+def _check_fd_poisson(ot, N, M, prec, lowpass):
     src = np.random.default_rng(N * M).standard_normal((N, M))
     p = ot.Plan(N, M, precision=prec)
     u = dev(np.zeros((N, M)))
