@@ -198,7 +198,7 @@ def variant_names(v):
         return {"code": v, "row_r2c": "k_mvT_r2c<M/2>", "col_matvec": "k_mvT_col<N>",
                 "row_c2r_combine": "k_mvT_combine<M/2>", "col_q4": False,
                 "register_resident": True}
-    return {"code": v, "row_r2c": row[r],
+    return {"code": v, "row_r2c": "k_row_r2c_pair<M/2>" if v & 1024 else row[r],
             "col_matvec": "k_col_pair<N>" if v & 256 else col[c],
             "row_c2r_combine": "k_comb_pair<M/2>" if v & 512 else comb[b],
             "col_q4": bool(v & 64)}

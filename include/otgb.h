@@ -193,7 +193,9 @@ extern "C" {
                                    arithmetic (N a power of two in 256..2048, M a multiple
                                    of 4; elsewhere c = 3); + 512: the combine pass on row
                                    pairs (M/2 a power of two in 256..1024, N even; elsewhere
-                                   b = 3); turns OT_OPT_AUTOTUNE off */
+                                   b = 3); + 1024: the row R2C pass and the fused Arnoldi
+                                   update on row pairs (the same sizes; elsewhere r = 3);
+                                   turns OT_OPT_AUTOTUNE off */
 
 /* Kernel classes of the profile (ot_plan_get_profile). */
 #define OT_PROF_RESIDUAL 0         /* residual + coefficients (Eq. ma2, linearmaeq) */

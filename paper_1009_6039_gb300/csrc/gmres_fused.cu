@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(512)
 static int update_r2c_E(int M, int var_r2c) {
   const int L = M / 2;
   if (L < 8 || fft_E(L) != 8) return 0;
-  if (var_r2c == VAR_E4) return 4;
+  if (var_r2c == VAR_E4 || var_r2c == VAR_PAIR) return 4;
   if (var_r2c == VAR_DEFAULT || var_r2c == VAR_GENERIC) return 8;
   return 0;
 }
@@ -110,6 +110,7 @@ static int update_r2c_rows(int N, int M, int E) {
 }
 
 bool update_r2c_fits(int N, int M, int var_r2c) {
+  if (var_r2c == VAR_PAIR && comb_pair_supported(N, M)) return true;
   const int E = update_r2c_E(M, var_r2c);
   return E != 0 && update_r2c_rows(N, M, E) > 0;
 }
@@ -132,6 +133,9 @@ static cudaError_t update_r2c_launch(float* V, const float* w, long P, const dou
 cudaError_t launch_gmres_update_r2c(float* V, const float* w, long P, const double* partials,
                                     int nb, DevScalars* sc, float2* spec, int N, int M,
                                     const SpecTables& tb, cudaStream_t st) {
+  // the row pair pass's fused form (the same transform and split as that pass)
+  if (tb.var_r2c == VAR_PAIR && comb_pair_supported(N, M))
+    return launch_gmres_update_r2c_pair(V, w, P, partials, nb, sc, spec, N, M, tb, st);
   switch (update_r2c_E(M, tb.var_r2c)) {
     case 4: return update_r2c_launch<4>(V, w, P, partials, nb, sc, spec, N, M, tb, st);
     case 8: return update_r2c_launch<8>(V, w, P, partials, nb, sc, spec, N, M, tb, st);

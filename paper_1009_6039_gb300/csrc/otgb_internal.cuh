@@ -180,8 +180,7 @@ struct SpecTables {
   // -1 default, 0 generic (8 or 12 elements per thread, one transform after the other),
   // 1 concurrent transforms in separate thread groups, 2 warp-synchronous radix-32,
   // 3 generic with 4 elements per thread (radix 4, twice the threads; power-of-two lengths),
-  // 4 (column and combine passes) column / row pairs with packed FP32 arithmetic
-  // (spectral_pair.cu)
+  // 4 column / row pairs with packed FP32 arithmetic (spectral_pair.cu, row_pair.cu)
   int var_r2c = -1, var_col = -1, var_comb = -1;
   // generic column matvec pass: columns per block (0: the default heuristic)
   int col_q = 0;
@@ -205,6 +204,15 @@ bool comb_pair_supported(int N, int M);
 cudaError_t launch_comb_pair(const float2* q0, const float2* q1, const float2* q2,
                              const float* coef, float* out, int N, int M, const SpecTables& tb,
                              const int* skip, cudaStream_t st);
+// the FP32 row real-to-complex pass on row pairs, and the Arnoldi update fused with it
+// (the sizes of the combine pair pass)
+cudaError_t launch_row_r2c_pair(const float* x, size_t xs, const int* jptr, const double* scale,
+                                float2* spec, int N, int M, const SpecTables& tb,
+                                const int* skip, cudaStream_t st);
+cudaError_t launch_gmres_update_r2c_pair(float* V, const float* w, long P,
+                                         const double* partials, int nb, DevScalars* sc,
+                                         float2* spec, int N, int M, const SpecTables& tb,
+                                         cudaStream_t st);
 // theta's double-float column pass (modes COL_LBARINV, COL_POISSON, COL_POISSON_LP) on
 // column pairs and its row pass + update on row pairs (the sizes of the FP32 pair passes)
 cudaError_t launch_col_lbarinv_pair(const float2* spec, ddc* out, int N, int M,

@@ -14,6 +14,7 @@
 //   row_c2r COMBINE  five row inverse transforms (d_xx Q0, d_x Q0, d_x Q1, Q1, Q2) weighted
 //                    by a11, b1, 2 a12, b2, a22 and summed: w = L Lbar^{-1} sigma.
 #pragma once
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -1762,63 +1763,56 @@ __global__ void __launch_bounds__(320)
 // ---------------------------------------------------------------------------------------
 inline int fft_E(int L) { return (L % 3 == 0) ? 12 : 8; }
 
-// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the current device.
-// The attribute belongs to the kernel (and device), so the record of sizes already set is
-// keyed by the kernel's address: kernels that share a signature must not share it.
-inline cudaError_t set_smem_fn(const void* fn, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  struct Done {
-    const void* fn;
-    int dev;
-    size_t bytes;
-  };
-  static std::mutex mu;
-  static std::vector<Done> done;
-  std::lock_guard<std::mutex> lock(mu);
-  Done* rec = nullptr;
-  for (auto& d : done)
-    if (d.fn == fn && d.dev == dev) rec = &d;
-  if (rec && rec->bytes >= bytes) return cudaSuccess;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  if (rec)
-    rec->bytes = bytes;
-  else
-    done.push_back({fn, dev, bytes});
-  return cudaSuccess;
-}
-
-// The largest block a kernel can be launched with (its launch bounds and registers), queried
-// once per kernel and device.
-inline int max_block_threads(const void* fn) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+// A kernel's launch limits, queried once per kernel and device: the largest block (its
+// launch bounds and registers) and its static shared memory.
+struct KernelLimits {
+  int threads = 0;
+  size_t static_smem = 0;
+  size_t dyn_set = 0;  // the dynamic shared-memory limit raised so far (0: the default)
+};
+inline KernelLimits* kernel_limits(const void* fn, int dev) {
   struct Rec {
     const void* fn;
-    int dev, threads;
+    int dev;
+    KernelLimits lim;
   };
-  static std::mutex mu;
-  static std::vector<Rec> recs;
-  std::lock_guard<std::mutex> lock(mu);
-  for (const auto& r : recs)
-    if (r.fn == fn && r.dev == dev) return r.threads;
+  static std::deque<Rec> recs;  // (stable addresses as it grows)
+  for (auto& r : recs)
+    if (r.fn == fn && r.dev == dev) return &r.lim;
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return 0;
-  recs.push_back({fn, dev, a.maxThreadsPerBlock});
-  return a.maxThreadsPerBlock;
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return nullptr;
+  recs.push_back({fn, dev, KernelLimits{a.maxThreadsPerBlock, a.sharedSizeBytes, 0}});
+  return &recs.back().lim;
 }
 
 // Check a launch configuration on the host and raise the kernel's shared-memory limit: a
-// block larger than the kernel allows is returned as an error here, never launched (a
-// launch the runtime rejects inside a stream capture invalidates the capture).
+// block larger than the kernel allows, or more shared memory (static + dynamic) than a block
+// can have, is returned as an error here, never launched (a launch the runtime rejects inside
+// a stream capture invalidates the capture).  The dynamic limit is raised whenever static and
+// dynamic shared memory together pass the default 48 KB.  The limits and the attribute belong
+// to the kernel (and device): the records are keyed by the kernel's address.
+inline cudaError_t prepare_launch_fn(const void* fn, long threads, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  KernelLimits* lim = kernel_limits(fn, dev);
+  if (!lim) return cudaErrorInvalidDeviceFunction;
+  if (threads < 1 || threads > lim->threads) return cudaErrorInvalidConfiguration;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (lim->static_smem + bytes > (size_t)optin) return cudaErrorInvalidConfiguration;
+  if (lim->static_smem + bytes <= 48 * 1024 || lim->dyn_set >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  lim->dyn_set = bytes;
+  return cudaSuccess;
+}
 template <typename K>
 inline cudaError_t prepare_launch(K kernel, long threads, size_t bytes) {
-  const void* fn = reinterpret_cast<const void*>(kernel);
-  if (threads < 1 || threads > max_block_threads(fn)) return cudaErrorInvalidConfiguration;
-  return set_smem_fn(fn, bytes);
+  return prepare_launch_fn(reinterpret_cast<const void*>(kernel), threads, bytes);
 }
 
 template <typename T, int E>
@@ -1911,9 +1905,15 @@ cudaError_t launch_row_r2c(const T* x, size_t xs, const int* jptr, const double*
       return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st, bat, msc);
     return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st, bat, msc);
   }
+  if constexpr (sizeof(T) == 4) {
+    if (tb.var_r2c == VAR_PAIR && !msc && comb_pair_supported(N, M))
+      return launch_row_r2c_pair(reinterpret_cast<const float*>(x), xs, jptr, scale,
+                                 reinterpret_cast<float2*>(spec), N, M, tb, skip, st);
+  }
   if (sizeof(T) == 4 && tb.var_r2c == VAR_WARP && warp_fft_ok(M / 2))
     return row_r2c_w_launch<T>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
-  if (sizeof(T) == 4 && tb.var_r2c == VAR_E4 && fft_E(M / 2) == 8 && M / 2 >= 4)
+  if (sizeof(T) == 4 && (tb.var_r2c == VAR_E4 || tb.var_r2c == VAR_PAIR) && fft_E(M / 2) == 8 &&
+      M / 2 >= 4)
     return row_r2c_E<T, 4>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   if (fft_E(M / 2) == 12) return row_r2c_E<T, 12>(x, xs, jptr, scale, spec, N, M, tb, skip, st);
   return row_r2c_E<T, 8>(x, xs, jptr, scale, spec, N, M, tb, skip, st);

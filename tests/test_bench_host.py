@@ -28,6 +28,7 @@ def test_variant_names_decode_the_option_encoding():
     assert v["row_c2r_combine"] == "k_row_combine_w<float>" and v["code"] == 303
     v = bench.variant_names(3 + 4 * 3 + 16 * 3 + 256 + 512)
     assert v["col_matvec"] == "k_col_pair<N>" and v["row_c2r_combine"] == "k_comb_pair<M/2>"
+    assert bench.variant_names(3 + 4 * 3 + 16 * 3 + 1792)["row_r2c"] == "k_row_r2c_pair<M/2>"
 
 
 def test_algorithmic_bytes():

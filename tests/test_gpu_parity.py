@@ -199,7 +199,8 @@ def test_longest_transforms(ot, N, M, prec):
                                  (1024, 1024)])
 @pytest.mark.parametrize("variant", [0, 0 + 4 * 1 + 16 * 1, 2 + 4 * 2 + 16 * 2,
                                      3 + 4 * 3 + 16 * 3, 2 + 4 * 0 + 16 * 1, 64, 128,
-                                     3 + 4 * 3 + 16 * 3 + 256, 63 + 256 + 512])
+                                     3 + 4 * 3 + 16 * 3 + 256, 63 + 256 + 512,
+                                     63 + 256 + 512 + 1024])
 def test_fp32_kernel_variants(ot, N, M, variant):
     # every FP32 transform kernel variant the autotuner can pick computes the same operator
     # (at 1024^2 the concurrent column pass, launched first, needs more shared memory than
@@ -280,7 +281,7 @@ def test_autotuned_solve_matches_fixed_variant(ot):
         rc, st = p.solve(dev(f), dev(g), phi)
         # the variants in use read back in the encoding the option takes
         v = p.get("fft_variant")
-        assert v == 0 if "fft_variant" in kw else 0 <= v <= 1023
+        assert v == 0 if "fft_variant" in kw else 0 <= v <= 2047
         assert p.get("tau") == 4.0 and p.get("precision") == 1
         p.close()
         assert rc == 0 and st["status"] == 0
@@ -725,11 +726,12 @@ def test_graph_shape_options_keep_the_result(ot):
         assert np.abs(results[k][0] - ref[0]).max() <= 1e-6, k
 
 
-@pytest.mark.parametrize("N,M", [(128, 128), (48, 64), (64, 256)])
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("N,M", [(128, 128), (48, 64), (64, 256), (64, 512), (16, 2048)])
+@pytest.mark.parametrize("variant", [0, 3, 3 + 1024])
 def test_fused_update_keeps_the_result(ot, N, M, variant):
     # OT_OPT_FUSED_UPDATE: the Arnoldi update fused with the next product's row pass (row
-    # pass variant 0: 8 elements per thread, 3: 4) against the two separate launches:
+    # pass variant 0: 8 elements per thread, 3: 4, + 1024: on row pairs where the row length
+    # allows, else 4) against the two separate launches:
     # bit-identical potentials and counts, graph and host-driven, over several restart
     # cycles (eta 1e-4, m = 5: cycles end at their last step as well as on convergence)
     f, g = I.noise_blob_pair(N, M, s=3703)
