@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include "dd.cuh"
+#include "dd2.cuh"
 #include "otgb_internal.cuh"
 #include "gmres_dev.cuh"
 #include "reduce.cuh"
@@ -763,6 +764,31 @@ __device__ __forceinline__ void bspline6_dd(dd t, dd w[4]) {
   w[2] = dd_add_f(dd_neg(dd_add(dd_add(w[0], w[1]), w[3])), 6.0f);
 }
 
+// the same weights for two positions at once (t.h, t.l: the lanes' high and low words), each
+// lane bit for bit bspline6_dd's
+__device__ __forceinline__ void bspline6_dd2(pair::D2 t, pair::D2 w[4]) {
+  using namespace pair;
+  const u64 one = pk(1.0f, 1.0f);
+  // dd_add_f(a, b) = fast_two_sum(s.hi, s.lo + a.lo) with s = two_sum(a.hi, b)
+  auto add_f = [](D2 a, u64 b) {
+    const D2 s = two_sum2(a.h, b);
+    return fast_two_sum2(s.h, add2(s.l, a.l));
+  };
+  // dd_mul_f(a, b) = fast_two_sum(p, fma(a.lo, b, fma(a.hi, b, -p))) with p = a.hi b
+  auto mul_f = [](D2 a, u64 b) {
+    const u64 p = mul2(a.h, b);
+    u64 e = fma2(a.h, b, neg2(p));
+    e = fma2(a.l, b, e);
+    return fast_two_sum2(p, e);
+  };
+  const D2 s = add_f(d2_neg(t), one);
+  const D2 t2 = d2_mul(t, t), t3 = d2_mul(t2, t);
+  w[0] = d2_mul(d2_mul(s, s), s);
+  w[1] = add_f(d2_sub(mul_f(t3, pk(3.0f, 3.0f)), mul_f(t2, pk(6.0f, 6.0f))), pk(4.0f, 4.0f));
+  w[3] = t3;
+  w[2] = add_f(d2_neg(d2_add(d2_add(w[0], w[1]), w[3])), pk(6.0f, 6.0f));
+}
+
 // floor of a dd position p (|p| < 2^23): integer part k and fraction t in [0, 1) as dd.
 // p.hi - floor(p.hi) is not exact for -1 < p.hi < 0 (the result needs more bits than
 // p.hi), so the subtraction is an error-free dd add.
@@ -889,34 +915,58 @@ __global__ void __launch_bounds__(RTX * RTY / RPT, 3)
       Gy = w00 * __ldg(K.gy + q00) + w01 * __ldg(K.gy + q01) + w10 * __ldg(K.gy + q10) +
            w11 * __ldg(K.gy + q11);
     } else {
-      dd wxv[4], wyv[4];
-      bspline6_dd(tx_, wxv);
-      bspline6_dd(ty_, wyv);
+      // packed pairs (dd2.cuh): the x and y value weights in the two lanes of one call, then
+      // the 16-tap gather over row pairs (b, b + 2), each lane a row's double-float sum in the
+      // scalar order; the two lanes' partial sums of G (rows 0, 1 and rows 2, 3) are added last
+      using namespace pair;
+      dd wxs[4], wys[4];
+      bspline6_dd(tx_, wxs);
+      bspline6_dd(ty_, wys);
+      D2 wv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) wv[a] = D2{pk(wxs[a].hi, wys[a].hi), pk(wxs[a].lo, wys[a].lo)};
       // gradient weights in FP32 (Jacobian only)
       float wxf[4], dwx[4], wyf[4], dwy[4];
       bspline_w<float>(tx_.hi, wxf, dwx);
       bspline_w<float>(ty_.hi, wyf, dwy);
-      dd G36 = dd{0.f, 0.f};
-      float gx = 0.f, gy = 0.f;
+      D2 G36p{0ull, 0ull};
+      u64 gxp = 0ull, gyp = 0ull;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const size_t row = (size_t)ii[b] * M;
-        dd sv = dd{0.f, 0.f};
-        float svf = 0.f, sdf = 0.f;
+      for (int b = 0; b < 2; ++b) {
+        const size_t ra = (size_t)ii[b] * M, rb = (size_t)ii[b + 2] * M;
+        D2 sv{0ull, 0ull};
+        u64 svf = 0ull, sdf = 0ull;
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const dd cv = ldd(cdd, row + jj[a]);
-          sv = dd_fma(cv, wxv[a], sv);
-          svf = fmaf(cv.hi, wxf[a], svf);
-          sdf = fmaf(cv.hi, dwx[a], sdf);
+          const float2 ca = __ldg(cdd + ra + jj[a]), cb = __ldg(cdd + rb + jj[a]);
+          const D2 cv{pk(ca.x, cb.x), pk(ca.y, cb.y)};
+          float xh, xl, yh, yl;  // the x weight, broadcast to both lanes
+          upk(wv[a].h, xh, yh);
+          upk(wv[a].l, xl, yl);
+          sv = d2_add(d2_mul(cv, D2{pk(xh, xh), pk(xl, xl)}), sv);
+          svf = fma2(cv.h, pk(wxf[a], wxf[a]), svf);
+          sdf = fma2(cv.h, pk(dwx[a], dwx[a]), sdf);
         }
-        G36 = dd_fma(sv, wyv[b], G36);
-        gx = fmaf(sdf, wyf[b], gx);
-        gy = fmaf(svf, dwy[b], gy);
+        float xh0, yh0, xl0, yl0, xh2, yh2, xl2, yl2;  // the y weights of rows b and b + 2
+        upk(wv[b].h, xh0, yh0);
+        upk(wv[b].l, xl0, yl0);
+        upk(wv[b + 2].h, xh2, yh2);
+        upk(wv[b + 2].l, xl2, yl2);
+        const D2 wyp{pk(yh0, yh2), pk(yl0, yl2)};
+        G36p = d2_add(d2_mul(sv, wyp), G36p);
+        gxp = fma2(sdf, pk(wyf[b], wyf[b + 2]), gxp);
+        gyp = fma2(svf, pk(dwy[b], dwy[b + 2]), gyp);
       }
+      dd g01, g23;
+      upk(G36p.h, g01.hi, g23.hi);
+      upk(G36p.l, g01.lo, g23.lo);
+      const dd G36 = dd_add(g01, g23);
+      float gx01, gx23, gy01, gy23;
+      upk(gxp, gx01, gx23);
+      upk(gyp, gy01, gy23);
       G = dd_mul(G36, K.inv36);
-      Gx = gx * K.M;
-      Gy = gy * K.N;
+      Gx = (gx01 + gx23) * K.M;
+      Gy = (gy01 + gy23) * K.N;
     }
     const dd det = dd_sub(dd_mul(dd_add_f(uxx, 1.0f), dd_add_f(uyy, 1.0f)), dd_mul(uxy, uxy));
     const dd fn = dd_mul(G, det);

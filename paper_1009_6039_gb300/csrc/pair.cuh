@@ -1,51 +1,20 @@
-// Packed FP32 pairs for the transform passes that hold two columns (or rows) side by side:
-// the PTX add/sub/mul/fma.rn.f32x2 instructions on register pairs (per lane the IEEE
-// round-to-nearest operation of the scalar form), complex pairs (PC: the real parts of two
+// Packed FP32 pairs for the transform passes that hold two columns (or rows) side by side
+// (the f32x2 instructions of f32x2.cuh): complex pairs (PC: the real parts of two
 // complex numbers in one register pair, the imaginary parts in another), their butterflies
 // and Stockham stages of 4 elements per thread, and the 16-byte-element shared-memory swizzle
 // i ^ ((i >> 2) & 7), under which every stage's reads and writes of a quarter warp fall in
 // distinct bank groups (checked for the radix-4 / radix-2 stages of lengths 256 .. 2048).
 #pragma once
+#include "f32x2.cuh"
 #include "spectral.cuh"
 
 namespace otgb {
 namespace pair {
 
-typedef unsigned long long u64;
 // two complex numbers, one per column: re = (a.x, b.x), im = (a.y, b.y)
 struct __align__(16) PC {
   u64 re, im;
 };
-
-__device__ __forceinline__ u64 pk(float lo, float hi) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void upk(u64 v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ u64 add2(u64 a, u64 b) {
-  u64 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
-  u64 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
-  u64 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-// a * b + c per lane
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
 
 __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 2) & 7); }
 

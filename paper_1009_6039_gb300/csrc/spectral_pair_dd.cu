@@ -11,41 +11,13 @@
 // column pass's forward transform and symbol step are FP32 (the forward on packed pairs as in
 // k_col_pair).  Double-float elements live in two shared-memory planes, the high words
 // (re, im) and the low words, 16 bytes per element each, under the swizzle of pair.cuh.
+#include "dd2.cuh"
 #include "pair.cuh"
 
 namespace otgb {
 namespace {
 
 using namespace pair;
-
-__device__ __forceinline__ u64 neg2(u64 a) { return mul2(a, pk(-1.f, -1.f)); }
-
-// two double-float numbers, one per lane
-struct D2 {
-  u64 h, l;
-};
-__device__ __forceinline__ D2 two_sum2(u64 a, u64 b) {
-  const u64 s = add2(a, b);
-  const u64 bb = sub2(s, a);
-  return D2{s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
-}
-__device__ __forceinline__ D2 fast_two_sum2(u64 a, u64 b) {
-  const u64 s = add2(a, b);
-  return D2{s, sub2(b, sub2(s, a))};
-}
-__device__ __forceinline__ D2 d2_add(D2 a, D2 b) {
-  const D2 s = two_sum2(a.h, b.h);
-  return fast_two_sum2(s.h, add2(s.l, add2(a.l, b.l)));
-}
-__device__ __forceinline__ D2 d2_neg(D2 a) { return D2{neg2(a.h), neg2(a.l)}; }
-__device__ __forceinline__ D2 d2_sub(D2 a, D2 b) { return d2_add(a, d2_neg(b)); }
-__device__ __forceinline__ D2 d2_mul(D2 a, D2 b) {
-  const u64 p = mul2(a.h, b.h);
-  u64 e = fma2(a.h, b.h, neg2(p));
-  e = fma2(a.h, b.l, e);
-  e = fma2(a.l, b.h, e);
-  return fast_two_sum2(p, e);
-}
 
 // two double-float complex numbers
 struct DC {
