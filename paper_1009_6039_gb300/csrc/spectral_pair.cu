@@ -40,16 +40,19 @@ __global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
   const int c0 = 2 * blockIdx.x;
   const int t = threadIdx.x;
 
+  // the column pair: one 16-byte load per row, issued before the twiddle table is built so
+  // that both sets of loads are in flight together, then regrouped into (re, im) pairs
+  float4 xs[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    xs[e] = *reinterpret_cast<const float4*>(spec + (size_t)(t + e * TPT) * Lc + c0);
   load_tw4<N>(tw4, twN, t, TPT);
-  // the column pair: one 16-byte load per row, regrouped into (re, im) pairs
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int n = t + e * TPT;
-    const float4 x = *reinterpret_cast<const float4*>(spec + (size_t)n * Lc + c0);
     PC v;
-    v.re = pk(x.x, x.z);
-    v.im = pk(x.y, x.w);
-    P[0][swz(n)] = v;
+    v.re = pk(xs[e].x, xs[e].z);
+    v.im = pk(xs[e].y, xs[e].w);
+    P[0][swz(t + e * TPT)] = v;
   }
   __syncthreads();
 
@@ -155,18 +158,29 @@ __global__ void __launch_bounds__(L / 4, L <= 512 ? 4 : 2)
   PC* const B[5] = {pb, pb + L, pb + 2 * L, pb + 3 * L, pb + 4 * L};
   const int r0 = 2 * blockIdx.x;
   const int t = threadIdx.x;
-  load_tw4<L>(tw4, twL, t, TPT);
-
   // the five terms of both rows: d_xx Q0, d_x Q0, d_x Q1, Q1, Q2 (row symbols of k1 = k; the
   // packed entry k = 0 holds (X0, X_L): d_x is 0 on both, d_xx keeps the Nyquist channel,
-  // which Q0 carries premultiplied)
+  // which Q0 carries premultiplied); the rows' loads are issued before the twiddle table is
+  // built, so that both sets of loads are in flight together
   const size_t oa = (size_t)r0 * L, ob = oa + L;
+  float2 ld[4][6];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int k = t + e * TPT;
-    const float2 a0 = q0[oa + k], b0 = q0[ob + k];
-    const float2 a1 = q1[oa + k], b1 = q1[ob + k];
-    const float2 a2 = q2[oa + k], b2 = q2[ob + k];
+    ld[e][0] = q0[oa + k];
+    ld[e][1] = q0[ob + k];
+    ld[e][2] = q1[oa + k];
+    ld[e][3] = q1[ob + k];
+    ld[e][4] = q2[oa + k];
+    ld[e][5] = q2[ob + k];
+  }
+  load_tw4<L>(tw4, twL, t, TPT);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int k = t + e * TPT;
+    const float2 a0 = ld[e][0], b0 = ld[e][1];
+    const float2 a1 = ld[e][2], b1 = ld[e][3];
+    const float2 a2 = ld[e][4], b2 = ld[e][5];
     PC x0, x1, x2;
     x0.re = pk(a0.x, b0.x);
     x0.im = pk(a0.y, b0.y);
