@@ -187,16 +187,19 @@ __global__ void __launch_bounds__(N / 4, N <= 1024 ? 2 : 1)
   const int Lc = M / 2;
   const int c0 = 2 * blockIdx.x;
   const int t = threadIdx.x;
+  // the column pair's loads first, so that they are in flight with the twiddle tables' loads
+  float4 xs[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    xs[e] = *reinterpret_cast<const float4*>(spec + (size_t)(t + e * TPT) * Lc + c0);
   load_tw4<N>(tw4, twN32, t, TPT);
   load_twdd<N>(th, tl, twNdd, t, TPT);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int n = t + e * TPT;
-    const float4 x = *reinterpret_cast<const float4*>(spec + (size_t)n * Lc + c0);
     PC v;
-    v.re = pk(x.x, x.z);
-    v.im = pk(x.y, x.w);
-    F0[swz(n)] = v;
+    v.re = pk(xs[e].x, xs[e].z);
+    v.im = pk(xs[e].y, xs[e].w);
+    F0[swz(t + e * TPT)] = v;
   }
   __syncthreads();
   {
@@ -298,14 +301,18 @@ __global__ void __launch_bounds__(L / 4, L <= 512 ? 4 : 2)
   const DBuf A{tl + L, tl + 2 * L};
   const int r0 = 2 * blockIdx.x;
   const int t = threadIdx.x;
-  load_twdd<L>(th, tl, twL, t, TPT);
+  // the rows' loads first, so that they are in flight with the twiddle table's loads
   const ddc* qa = q + (size_t)r0 * L;
   const ddc* qb = qa + L;
+  ddc ra[4], rb[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    const int k = t + e * TPT;
-    dst(A, swz(k), dc_from(qa[k], qb[k]));
+    ra[e] = qa[t + e * TPT];
+    rb[e] = qb[t + e * TPT];
   }
+  load_twdd<L>(th, tl, twL, t, TPT);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) dst(A, swz(t + e * TPT), dc_from(ra[e], rb[e]));
   __syncthreads();
   // complex-to-real pre-processing (as c2r_preprocess on dd): each pair (k, L - k) by one
   // thread
